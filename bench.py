@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the long-range (history) evaluator.
+
+Workload (one step): the full-size starfish problem — 1e5 boundary nodes (6,250 panels x 16
+Gauss-Legendre) on r = 1 + 0.3 cos 5t, ~1e6 cut-cell volume nodes with the manufactured source
+f = (13 + alpha^2) sin 2x cos 3y, 1e6 uniform targets in [-1.5, 1.5]^2 — evaluated at
+alpha = 1, 10 and 100 in FP64 at relative accuracy 1e-10.  Per alpha the step runs the whole hot
+path: bin/sort of sources and targets (yk_set_points) and spread, FFTs with the multiplier, and
+interpolation (yk_eval_longrange).  Inputs are synthetic and resident in HBM before timing.
+
+`value` = source+target points of all alphas and ranks per second of device time (CUDA events,
+max over ranks).  `e2e` = the same through the C ABI with pinned host buffers, host<->device
+copies inside the timed region.  `roofline` = the stage with the largest device time, against
+the measured FP64 FMA peak (ALU-bound) or the measured HBM copy bandwidth.  `cpu_baseline` = the
+FP64 oracle (direct pair sum) on the host cores for a bounded sample of targets, scaled to a full
+evaluation.  `--impl reference` times that oracle alone as the reference arm.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "source+target points/s at rel err 1e-10 (FP64) & 1e-6 (FP32); p50/p99 latency"
+ALPHAS = (1.0, 10.0, 100.0)
+TOL = 1e-10
+L2_BYTES = 126 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--alphas", default=",".join(str(a) for a in ALPHAS))
+    ap.add_argument("--cpu-targets", type=int, default=1500,
+                    help="targets in the bounded CPU-oracle sample (all sources)")
+    ap.add_argument("--ref-targets", type=int, default=120,
+                    help="targets per alpha in each reference-arm step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# algorithmic work per stage (per launch), used for the roofline of the dominant stage
+def stage_work(info, ns, nt):
+    """(bytes, fp64 flops) each stage must move / compute at minimum for one launch."""
+    n, M, w = info["n_grid"], info["n_modes"], info["w"]
+    G = n * n
+    L = n // 2
+    entries = ns * (1 + (w - 1) / info["tile"]) ** 2  # windows spread into each tile they touch
+    # window evaluation: exp + sqrt + 4 flops per tap and axis, counted as 24 flops each
+    win = 24
+    fft_row = 5 * L * math.log2(L) + 12 * L   # complex FFT of n/2 points + real post-processing
+    fft_col = 5 * n * math.log2(n)
+    return {
+        "bin_src": (ns * (16 + 16 + 4 * 3) + entries * 20, 20 * ns),
+        "bin_trg": (nt * (16 + 16 + 4 * 3) + nt * 20, 20 * nt),
+        "spread": (entries * 20 + ns * 16 + G * 8, entries * (2 * w * win + 2 * w * w)),
+        "row_fwd": (G * 8 + (M + 1) * n * 16, n * fft_row),
+        "columns": (2 * (M + 1) * n * 16 + (M + 1) * (2 * M + 1) * 8,
+                    (M + 1) * (2 * fft_col + 6 * n)),
+        "row_inv": ((M + 1) * n * 16 + G * 8, n * fft_row),
+        "interp": (G * 8 + nt * 28, nt * (2 * w * win + 2 * w * w + 2 * w)),
+    }
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6400.0)), "measured"
+    return 6400.0, "fallback"
+
+
+def load_traffic():
+    """ncu DRAM bytes per launch per stage recorded under profiles/, valid for the current source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return {}
+    import hashlib
+    with open(path) as f:
+        d = json.load(f)
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_2606_28865_b300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2606_28865_b300", "csrc", fn), "rb") as fh:
+            h.update(fh.read())
+    if d.get("csrc_sha256") != h.hexdigest():
+        return {}
+    return d.get("bytes_per_launch", {})
+
+
+# ---------------------------------------------------------------------------------------------
+def cpu_baseline(alphas, n_targets):
+    """FP64 oracle, all sources x a bounded sample of targets, scaled to full evaluations."""
+    import oracle
+    total_pts = 0.0
+    total_t = 0.0
+    for a in alphas:
+        work = W.config_large(a)
+        rng = np.random.default_rng(1)
+        idx = rng.choice(work.n_trg, n_targets, replace=False)
+        table = oracle.GHTable(a, _delta(work, a), oracle.pair_rmax(work.xs, work.ys, work.xt,
+                                                                      work.yt))
+        t0 = time.perf_counter()
+        oracle.direct_sum(a, _delta(work, a), work.xs, work.ys, work.q, work.xt[idx],
+                          work.yt[idx], table=table)
+        dt = time.perf_counter() - t0
+        total_t += dt * work.n_trg / n_targets           # time of the full evaluation
+        total_pts += work.n_src + work.n_trg
+    return {"value": total_pts / total_t, "unit": "points/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": (f"FP64 direct pair sum over all {int(W.config_large(alphas[0]).n_src)} "
+                       f"sources for {n_targets} of the 1e6 targets at each alpha in "
+                       f"{list(alphas)}; time scaled by 1e6/{n_targets} to a full evaluation")}
+
+
+def _delta(work, alpha):
+    import oracle.params as OP
+    return OP.delta_from_mesh(alpha, work.h_vol)
+
+
+def run_reference(args, rank, world, pg):
+    """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return 0
+    import oracle
+    alphas = [float(a) for a in args.alphas.split(",")]
+    works = {a: W.config_large(a) for a in alphas}
+    tables = {a: oracle.GHTable(a, _delta(works[a], a),
+                                oracle.pair_rmax(works[a].xs, works[a].ys, works[a].xt,
+                                                 works[a].yt)) for a in alphas}
+    rng = np.random.default_rng(2)
+    idx = {a: rng.choice(works[a].n_trg, args.ref_targets, replace=False) for a in alphas}
+
+    def step():
+        for a in alphas:
+            wk = works[a]
+            oracle.direct_sum(a, _delta(wk, a), wk.xs, wk.ys, wk.q, wk.xt[idx[a]], wk.yt[idx[a]],
+                              table=tables[a])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    scale = works[alphas[0]].n_trg / args.ref_targets
+    pts = sum(works[a].n_src + works[a].n_trg for a in alphas)
+    value = pts / (dt * scale)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * scale * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "starfish 1.1e6 sources + 1e6 targets, alpha in "
+                                   + str(alphas) + ", FP64 tol 1e-10", "alphas": alphas},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"all sources x {args.ref_targets} targets per alpha per "
+                                       f"step, scaled to full evaluations"},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    rank, world, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, rank, world, pg)
+
+    import torch
+    import paper_2606_28865_b300 as yk
+
+    alphas = [float(a) for a in args.alphas.split(",")]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    works, plans, dbufs, outs = {}, {}, {}, {}
+    for a in alphas:
+        wk = W.config_large(a, seed=rank)
+        works[a] = wk
+        plans[a] = yk.Plan(a, tol=TOL, h_vol=wk.h_vol, box=wk.box, profile=True, stream=stream)
+        t = lambda v: torch.as_tensor(v, dtype=torch.float64, device=dev)
+        dbufs[a] = [t(wk.xs), t(wk.ys), t(wk.w), t(wk.xt), t(wk.yt), t(wk.density)]
+        outs[a] = torch.empty(wk.n_trg, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+
+    def step():
+        for a in alphas:
+            xs, ys, w, xt, yt, d = dbufs[a]
+            plans[a].set_points(xs, ys, w, xt, yt)
+            plans[a].eval(d, out=outs[a])
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    for a in alphas:
+        plans[a].stage_times()  # restart the per-stage event averages
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(pg)
+    ms_step = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
+    stage_ms = {a: plans[a].stage_times() for a in alphas}
+    pts_step = sum(works[a].n_src + works[a].n_trg for a in alphas)
+    value = pts_step * world / (ms_step * 1e-3)
+
+    # per-eval latency distribution (device events per call)
+    lat = []
+    for a in alphas:
+        xs, ys, w, xt, yt, d = dbufs[a]
+        for _ in range(5):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            plans[a].eval(d, out=outs[a])
+            s1.record(stream)
+            torch.cuda.synchronize()
+            lat.append(s0.elapsed_time(s1))
+    eval_only_ms = sum(sum(v for k, v in stage_ms[a].items()
+                           if k not in ("bin_src", "bin_trg") and v) for a in alphas)
+
+    # end to end through the C ABI with pinned host buffers
+    hbufs = {}
+    for a in alphas:
+        wk = works[a]
+        pin = lambda v: torch.as_tensor(v, dtype=torch.float64).pin_memory()
+        hbufs[a] = [pin(wk.xs), pin(wk.ys), pin(wk.w), pin(wk.xt), pin(wk.yt), pin(wk.density),
+                    torch.empty(wk.n_trg, dtype=torch.float64).pin_memory()]
+
+    def step_host():
+        for a in alphas:
+            xs, ys, w, xt, yt, d, u = hbufs[a]
+            plans[a].set_points(xs, ys, w, xt, yt)
+            plans[a].eval(d, out=u)
+
+    step_host()
+    torch.cuda.synchronize()
+    barrier(pg)
+    k_e2e = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(pg, (time.perf_counter() - t0) / k_e2e)
+    h2d = sum((4 * works[a].n_src + 2 * works[a].n_trg) * 8 for a in alphas)
+    d2h = sum(works[a].n_trg * 8 for a in alphas)
+    for a in alphas:
+        plans[a].stage_times()
+
+    # roofline of the dominant stage (largest device time per step)
+    hbm_peak, peak_kind = load_peaks()
+    fp64_peak = yk.fma_peak_tflops(yk.YK_FP64)
+    tot = {}
+    work_b, work_f = {}, {}
+    for a in alphas:
+        info = plans[a].info
+        sw = stage_work(info, works[a].n_src, works[a].n_trg)
+        for k, v in stage_ms[a].items():
+            if v is None:
+                continue
+            tot[k] = tot.get(k, 0.0) + v
+            work_b[k] = work_b.get(k, 0.0) + sw[k][0]
+            work_f[k] = work_f.get(k, 0.0) + sw[k][1]
+    dom = max(tot, key=tot.get)
+    t_dom = tot[dom] * 1e-3
+    gbs = work_b[dom] / t_dom / 1e9
+    tfl = work_f[dom] / t_dom / 1e12
+    traffic = load_traffic().get(dom)
+    if tfl / fp64_peak >= gbs / hbm_peak:
+        roof = {"bound": "alu", "achieved": tfl, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": tfl / fp64_peak, "traffic": traffic}
+        peak_note = "FP64 FMA rate measured by yk_fma_peak on this GPU"
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": gbs / hbm_peak, "traffic": traffic}
+        peak_note = f"HBM copy bandwidth, {peak_kind} (MEASURED_PEAKS.json)"
+    roof.update({"kernel": dom, "launches_per_step": len(alphas), "peak_source": peak_note,
+                 "hbm_achieved_gbs": gbs, "fp64_achieved_tflops": tfl})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(alphas, args.cpu_targets)
+
+    launches_per_eval = 5
+    launches_per_set = 6
+    line = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "starfish 1e5 boundary + ~1e6 volume sources, 1e6 targets, "
+                               "alpha in " + str(alphas) + ", FP64, rel tol 1e-10; "
+                               "set_points + eval per alpha per step",
+                   "alphas": alphas, "n_src": works[alphas[0]].n_src,
+                   "n_trg": works[alphas[0]].n_trg, "tol": TOL,
+                   "grids": {str(a): plans[a].info["n_grid"] for a in alphas},
+                   "l2": "inputs and grids larger than L2 (126 MB) per step; no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": pts_step * world / e2e_s, "unit": "points/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * len(alphas) * (launches_per_eval + launches_per_set),
+        "clocks": clk,
+        "stage_ms": {str(a): stage_ms[a] for a in alphas},
+        "eval_only": {"ms_per_step": eval_only_ms,
+                      "value": pts_step * world / (eval_only_ms * 1e-3) if eval_only_ms else None},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "what": "one yk_eval_longrange on a resident layout, all alphas"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for a in alphas:
+        plans[a].close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

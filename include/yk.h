@@ -1,0 +1,194 @@
+/*
+ * yk.h — C ABI of the B300 long-range ("history") evaluator for the 2D modified Helmholtz
+ * (Yukawa) equation  (-Lap + alpha^2) u = f  (Section 1, eq. mod_helm).
+ *
+ * What the library computes.  For sources y_j with strengths q_j = w_j * density_j (boundary
+ * quadrature weights times a layer density, Section 3.2 eq. bdry_quad, then volume quadrature
+ * weights times source values, Section 3.1 eq. vol_quad) and targets x_i:
+ *
+ *     u_i = sum_j q_j G_H(x_i - y_j),
+ *     G_H(x) = int_delta^inf exp(-|x|^2/(4t) - alpha^2 t) / (4 pi t) dt     (Section 2.1, eq. sl_sh)
+ *
+ * i.e. the history parts S_H[sigma] + V_H[f] of the single layer and volume potentials.  The
+ * evaluation is the paper's Fourier method (Section 5): a type-1 spread of q onto a uniform
+ * periodic grid, a forward FFT, multiplication by e^{-delta(alpha^2+|k|^2)}/(alpha^2+|k|^2)
+ * (eq. sh) on the truncated mode set (eqs. kmax, delta_k, sh_fourier), an inverse FFT and a type-2
+ * interpolation at the targets.  Every step runs in the library's own CUDA kernels (sm_103a).
+ *
+ * Conventions for every call.
+ *  - Arrays are FP64 at the ABI.  Each array pointer may be host or device memory (detected with
+ *    cudaPointerGetAttributes); device pointers must be usable on the plan's stream.
+ *  - The caller owns every array it passes; the library owns the plan and its device buffers.
+ *  - Calls are ordered on the plan's stream.  A call whose outputs are all device memory returns
+ *    once its work is enqueued; a call with a host output returns after the stream has finished.
+ *  - No call aborts or throws across the ABI; every failure is a yk_status.  The message of the
+ *    last failure on the calling thread is yk_last_error().
+ *  - Errors detected by kernels (a point outside the box) are sticky in the plan and are
+ *    returned by the next call that synchronises (yk_sync, or a call with host outputs).
+ */
+#ifndef YK_H
+#define YK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define YK_API __attribute__((visibility("default")))
+#else
+#define YK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct yk_plan_s *yk_plan_t; /* opaque, owned by the library */
+
+typedef enum {
+    YK_OK = 0,
+    YK_ERR_ARG = 1,      /* invalid argument (alpha <= 0, tol outside (0,1), point outside box, ...) */
+    YK_ERR_OOM = 2,      /* a device allocation failed */
+    YK_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    YK_ERR_TIMEOUT = 4,  /* a bounded device-side wait ran out */
+    YK_ERR_STATE = 5,    /* call out of order (eval before set_points, ...) */
+    YK_ERR_INTERNAL = 6, /* an internal consistency check failed */
+    YK_ERR_UNSUPPORTED = 7 /* a size beyond what this build handles (see yk_plan) */
+} yk_status;
+
+typedef enum {
+    YK_FP64 = 0, /* FP64 end to end */
+    YK_FP32C = 1 /* FP32 spread/FFT/interp with compensated accumulation, FP64 final sums */
+} yk_precision;
+
+typedef struct {
+    int precision;     /* yk_precision */
+    double tol;        /* requested relative accuracy, e.g. 1e-10 (FP64) or 1e-6 (FP32C) */
+    double delta;      /* > 0: time-split parameter delta of Section 2.1, used as is;
+                          0: delta from the mesh rule of Section 6.4 with h_vol and eps_hist */
+    double h_vol;      /* volume mesh size dx for the delta rule (used when delta == 0) */
+    double eps_hist;   /* history tolerance of the delta rule; 0 means 1e-6 (Section 6) */
+    double box[4];     /* xmin, xmax, ymin, ymax: every source and target lies inside */
+    double kmax;       /* > 0: Fourier cutoff k_max used as is (else from tol, eq. kmax) */
+    int kmax_rule;     /* 0: the tail of the Fourier integral beyond k_max is at most eps G_H(0)
+                          (eq. kmax read relative to the size of G_H; eps = tol / 4);
+                          1: eq. kmax as printed, exp(-delta (alpha^2 + k_max^2)) <= eps, with its
+                          k_max = 0 case (u = 0) when delta alpha^2 >= ln(1/eps) */
+    double period;     /* > 0: period P of the grid used as is (else box span + decay length) */
+    int tile;          /* > 0: tile edge in grid cells (else chosen by the plan) */
+    int profile;       /* nonzero: record CUDA events around every stage (see yk_stage_times) */
+    void *stream;      /* cudaStream_t for all work of the plan; NULL = legacy default stream */
+    /* optional device allocator (e.g. a caching allocator); NULL = cudaMalloc / cudaFree */
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *alloc_ctx;
+} yk_opts;
+
+/* Parameters the plan chose (all derived from alpha, tol, delta and the box). */
+typedef struct {
+    double alpha, delta, tol, eps; /* eps: internal accuracy target (tol / 4) */
+    double kmax;                   /* Fourier cutoff (Section 5.1, eq. kmax; relative reading) */
+    double period;                 /* P; Delta k = 2 pi / P (eq. delta_k) */
+    double origin[2];              /* lower-left corner of the periodic box */
+    double h;                      /* grid spacing P / n_grid */
+    int64_t n_modes;               /* M: modes |m_x|, |m_y| <= M are kept */
+    int64_t n_grid;                /* fine grid points per axis */
+    int w;                         /* window width in grid points */
+    double beta;                   /* exponential-of-semicircle window shape */
+    int tile;                      /* tile edge (grid cells) */
+    int precision;                 /* yk_precision */
+    int64_t device_bytes;          /* device memory held by the plan now */
+} yk_info;
+
+/* Fill *o with defaults: FP64, tol 1e-10, delta rule with eps_hist 1e-6, box [-1.5,1.5]^2. */
+YK_API void yk_opts_default(yk_opts *o);
+
+/*
+ * yk_plan: choose the evaluation parameters for one alpha and one box and allocate the plan's
+ * device buffers (grid, half spectrum, multiplier table of Section 5.2 eq. sh_fourier with the
+ * window deconvolution folded in, FFT tables).  alpha > 0 (Section 1); tol in (0, 1).
+ * With kmax_rule = 1 and delta alpha^2 >= ln(1/eps) the history part is below tolerance
+ * (Section 5.1, the k_max = 0 case): no grid is allocated and every evaluation writes u = 0.
+ * Returns YK_ERR_ARG for invalid options, YK_ERR_UNSUPPORTED when the grid would exceed
+ * n_grid = 14400 (a grid column must fit one CTA's shared memory), YK_ERR_OOM, YK_ERR_CUDA.
+ */
+YK_API yk_status yk_plan(double alpha, const yk_opts *o, yk_plan_t *out);
+
+/*
+ * yk_set_points: give the sources (n_src nodes xs, ys with quadrature weights w: boundary nodes
+ * then volume nodes, Sections 3.1-3.2) and the targets (n_trg points xt, yt).  Bins and sorts
+ * both into grid tiles on the device; the layout stays resident until the next yk_set_points, so
+ * repeated evaluations with new densities (a Rothe time step) reuse it.  n_src, n_trg >= 0; a
+ * point outside the plan's box is reported (sticky) as YK_ERR_ARG.
+ */
+YK_API yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const double *ys,
+                        const double *w, int64_t n_trg, const double *xt, const double *yt);
+
+/*
+ * yk_eval_longrange: u[i] = sum_j w_j density_j G_H(x_i - y_j) for the points of the last
+ * yk_set_points (density: n_src values, sigma at boundary nodes then f at volume nodes; u: n_trg
+ * values, written).  Returns YK_ERR_STATE before any yk_set_points.
+ */
+YK_API yk_status yk_eval_longrange(yk_plan_t p, const double *density, double *u);
+
+/*
+ * yk_plan_params: the parameters yk_plan would choose for (alpha, o), and in info->device_bytes
+ * the device memory such a plan would hold after yk_set_points with n_src sources and n_trg
+ * targets.  Makes no CUDA call (usable for memory-based admission before any allocation).
+ */
+YK_API yk_status yk_plan_params(double alpha, const yk_opts *o, int64_t n_src, int64_t n_trg,
+                         yk_info *info);
+
+/*
+ * Stages timed when the plan was created with opts.profile != 0, in this order:
+ * YK_STAGE_BIN_SRC, YK_STAGE_BIN_TRG (yk_set_points), YK_STAGE_SPREAD, YK_STAGE_ROW_FWD,
+ * YK_STAGE_COLUMNS, YK_STAGE_ROW_INV, YK_STAGE_INTERP (yk_eval_longrange).
+ */
+enum {
+    YK_STAGE_BIN_SRC = 0,
+    YK_STAGE_BIN_TRG = 1,
+    YK_STAGE_SPREAD = 2,
+    YK_STAGE_ROW_FWD = 3,
+    YK_STAGE_COLUMNS = 4,
+    YK_STAGE_ROW_INV = 5,
+    YK_STAGE_INTERP = 6,
+    YK_NUM_STAGES = 7
+};
+
+/*
+ * yk_stage_times: mean device time (ms, from CUDA events recorded on the plan's stream around the
+ * stage's kernels) of each stage over its runs since the previous yk_stage_times call (at most
+ * the last 64 runs), then restarts the count; ms[YK_NUM_STAGES] is written, -1 for a stage that
+ * has not run.  Waits for the plan's stream.  YK_ERR_STATE if the plan was created without
+ * opts.profile.
+ */
+YK_API yk_status yk_stage_times(yk_plan_t p, double *ms);
+
+/* Wait for the plan's stream; return the plan's sticky status. */
+YK_API yk_status yk_sync(yk_plan_t p);
+
+/* Parameters chosen by yk_plan. */
+YK_API yk_status yk_plan_info(yk_plan_t p, yk_info *info);
+
+/* Free the plan and every device buffer it holds (after its stream's work has finished). */
+YK_API yk_status yk_destroy(yk_plan_t p);
+
+/* Message of the last failure on the calling thread; never NULL ("" when none). */
+YK_API const char *yk_last_error(void);
+
+/*
+ * yk_fma_peak: measured FMA throughput of the current device in TFLOP/s (2 flops per FMA) for
+ * precision YK_FP64 or YK_FP32C (FP32), from independent FMA chains on every SM.  A diagnostic
+ * used to report ALU-bound kernels against a measured peak; the paper has no counterpart.
+ */
+YK_API yk_status yk_fma_peak(int precision, double *tflops);
+
+/*
+ * yk_batch_eval: evaluate n plans (each with points already set) with their densities in one
+ * submission; density[i] and u[i] follow the rules of yk_eval_longrange for plans[i].
+ */
+YK_API yk_status yk_batch_eval(yk_plan_t *plans, const double *const *density, double *const *u, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* YK_H */

@@ -1,0 +1,262 @@
+"""B300-native long-range (history) evaluator for the 2D modified Helmholtz equation.
+
+Thin Python binding over the C ABI of ``include/yk.h`` (``libyk.so``, built in-tree by
+``paper_2606_28865_b300/build.py``).  It only marshals arguments: every step of the evaluation
+runs in the library's CUDA kernels.  Arrays may be torch tensors (CUDA or CPU, float64,
+contiguous) or numpy float64 arrays.  If the library is missing, importing this package fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libyk.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2606_28865_b300/build.py`"
+                      " (or __graft_entry__.build()); there is no fallback implementation")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+YK_OK, YK_ERR_ARG, YK_ERR_OOM, YK_ERR_CUDA, YK_ERR_TIMEOUT, YK_ERR_STATE, YK_ERR_INTERNAL, \
+    YK_ERR_UNSUPPORTED = range(8)
+YK_FP64, YK_FP32C = 0, 1
+_STATUS = {0: "YK_OK", 1: "YK_ERR_ARG", 2: "YK_ERR_OOM", 3: "YK_ERR_CUDA", 4: "YK_ERR_TIMEOUT",
+           5: "YK_ERR_STATE", 6: "YK_ERR_INTERNAL", 7: "YK_ERR_UNSUPPORTED"}
+
+
+class YkError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.yk_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
+
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double),
+                ("delta", ctypes.c_double), ("h_vol", ctypes.c_double),
+                ("eps_hist", ctypes.c_double), ("box", ctypes.c_double * 4),
+                ("kmax", ctypes.c_double), ("kmax_rule", ctypes.c_int),
+                ("period", ctypes.c_double), ("tile", ctypes.c_int),
+                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", _ALLOC), ("free", _FREE),
+                ("alloc_ctx", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("delta", ctypes.c_double), ("tol", ctypes.c_double),
+                ("eps", ctypes.c_double), ("kmax", ctypes.c_double), ("period", ctypes.c_double),
+                ("origin", ctypes.c_double * 2), ("h", ctypes.c_double),
+                ("n_modes", ctypes.c_int64), ("n_grid", ctypes.c_int64), ("w", ctypes.c_int),
+                ("beta", ctypes.c_double), ("tile", ctypes.c_int), ("precision", ctypes.c_int),
+                ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["origin"] = tuple(self.origin)
+        return d
+
+
+_d, _i64, _vp = ctypes.c_double, ctypes.c_int64, ctypes.c_void_p
+_lib.yk_opts_default.argtypes = [ctypes.POINTER(Opts)]
+_lib.yk_opts_default.restype = None
+_lib.yk_last_error.restype = ctypes.c_char_p
+_lib.yk_plan.argtypes = [_d, ctypes.POINTER(Opts), ctypes.POINTER(_vp)]
+_lib.yk_plan_params.argtypes = [_d, ctypes.POINTER(Opts), _i64, _i64, ctypes.POINTER(Info)]
+_lib.yk_set_points.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp]
+_lib.yk_eval_longrange.argtypes = [_vp, _vp, _vp]
+_lib.yk_sync.argtypes = [_vp]
+_lib.yk_stage_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+_lib.yk_plan_info.argtypes = [_vp, ctypes.POINTER(Info)]
+_lib.yk_destroy.argtypes = [_vp]
+_lib.yk_batch_eval.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                               ctypes.c_int]
+for _f in ("yk_plan", "yk_plan_params", "yk_set_points", "yk_eval_longrange", "yk_sync",
+           "yk_stage_times",
+           "yk_plan_info", "yk_destroy", "yk_batch_eval"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+def _check(status: int, where: str):
+    if status != YK_OK:
+        raise YkError(status, where)
+
+
+def _torch():
+    try:
+        import torch
+        return torch
+    except ImportError:  # numpy-only use
+        return None
+
+
+def _ptr(a, keep: list):
+    """Device or host pointer of a float64 contiguous torch tensor or numpy array."""
+    if a is None:
+        return None
+    torch = _torch()
+    if torch is not None and isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64:
+            raise TypeError("tensors must be float64")
+        if not a.is_contiguous():
+            a = a.contiguous()
+        keep.append(a)
+        return a.data_ptr() if a.numel() else None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    keep.append(a)
+    return a.ctypes.data if a.size else None
+
+
+def _len(a) -> int:
+    if a is None:
+        return 0
+    return int(a.numel()) if hasattr(a, "numel") else int(np.asarray(a).size)
+
+
+def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
+              box=(-1.5, 1.5, -1.5, 1.5), kmax=0.0, kmax_rule=0, period=0.0, tile=0,
+              profile=False, stream=None) -> Opts:
+    o = Opts()
+    _lib.yk_opts_default(ctypes.byref(o))
+    o.precision = int(precision)
+    o.tol = float(tol)
+    o.delta = float(delta)
+    o.h_vol = float(h_vol)
+    o.eps_hist = float(eps_hist)
+    for i in range(4):
+        o.box[i] = float(box[i])
+    o.kmax = float(kmax)
+    o.kmax_rule = int(kmax_rule)
+    o.period = float(period)
+    o.tile = int(tile)
+    o.profile = 1 if profile else 0
+    o.stream = stream
+    return o
+
+
+def plan_params(alpha: float, n_src: int = 0, n_trg: int = 0, **opts) -> dict:
+    """Parameters (and predicted device bytes) of a plan, without touching the GPU."""
+    o = make_opts(**opts)
+    info = Info()
+    _check(_lib.yk_plan_params(float(alpha), ctypes.byref(o), int(n_src), int(n_trg),
+                               ctypes.byref(info)), "yk_plan_params")
+    return info.as_dict()
+
+
+def _current_stream():
+    torch = _torch()
+    if torch is not None and torch.cuda.is_available():
+        return torch.cuda.current_stream().cuda_stream
+    return None
+
+
+class Plan:
+    """One (alpha, box, tolerance) evaluation plan with resident device buffers."""
+
+    def __init__(self, alpha: float, stream=None, **opts):
+        if stream is None:
+            stream = _current_stream()
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._opts = make_opts(stream=stream, **opts)
+        h = _vp()
+        _check(_lib.yk_plan(float(alpha), ctypes.byref(self._opts), ctypes.byref(h)), "yk_plan")
+        self._h = h
+        self.n_src = 0
+        self.n_trg = 0
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def info(self) -> dict:
+        info = Info()
+        _check(_lib.yk_plan_info(self._h, ctypes.byref(info)), "yk_plan_info")
+        return info.as_dict()
+
+    def set_points(self, xs, ys, w, xt, yt):
+        keep = []
+        ns, nt = _len(xs), _len(xt)
+        if _len(ys) != ns or _len(w) != ns or _len(yt) != nt:
+            raise ValueError("coordinate/weight lengths differ")
+        _check(_lib.yk_set_points(self._h, ns, _ptr(xs, keep), _ptr(ys, keep), _ptr(w, keep), nt,
+                                  _ptr(xt, keep), _ptr(yt, keep)), "yk_set_points")
+        self._keep_points = keep
+        self.n_src, self.n_trg = ns, nt
+
+    def eval(self, density, out=None):
+        """u at the targets; `out` (same kind of array as `density` by default) is written."""
+        if _len(density) != self.n_src:
+            raise ValueError("density length differs from the number of sources")
+        torch = _torch()
+        if out is None:
+            if torch is not None and isinstance(density, torch.Tensor):
+                out = torch.empty(self.n_trg, dtype=torch.float64, device=density.device)
+            else:
+                out = np.empty(self.n_trg, dtype=np.float64)
+        keep = []
+        _check(_lib.yk_eval_longrange(self._h, _ptr(density, keep), _ptr(out, keep)),
+               "yk_eval_longrange")
+        self._keep_eval = keep
+        return out
+
+    def sync(self):
+        _check(_lib.yk_sync(self._h), "yk_sync")
+
+    STAGES = ("bin_src", "bin_trg", "spread", "row_fwd", "columns", "row_inv", "interp")
+
+    def stage_times(self) -> dict:
+        """Device ms of each stage's latest run (plan created with profile=True)."""
+        ms = (ctypes.c_double * len(self.STAGES))()
+        _check(_lib.yk_stage_times(self._h, ms), "yk_stage_times")
+        return {k: (v if v >= 0 else None) for k, v in zip(self.STAGES, ms)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.yk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def batch_eval(plans, densities, outs):
+    """Evaluate several plans in one submission (each plan's points already set)."""
+    n = len(plans)
+    keep = []
+    hp = (_vp * n)(*[p.handle for p in plans])
+    dp = (_vp * n)(*[_ptr(d, keep) for d in densities])
+    up = (_vp * n)(*[_ptr(u, keep) for u in outs])
+    _check(_lib.yk_batch_eval(hp, dp, up, n), "yk_batch_eval")
+    return outs
+
+
+_lib.yk_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+_lib.yk_fma_peak.restype = ctypes.c_int
+
+
+def fma_peak_tflops(precision=YK_FP64) -> float:
+    """Measured FMA throughput of the current CUDA device (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check(_lib.yk_fma_peak(int(precision), ctypes.byref(v)), "yk_fma_peak")
+    return v.value
+
+
+def loaded_library_path() -> str:
+    return LIB_PATH

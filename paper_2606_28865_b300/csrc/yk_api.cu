@@ -1,0 +1,812 @@
+/*
+ * yk_api.cu — host side of the C ABI declared in include/yk.h: parameter selection, device
+ * buffers, host/device pointer handling and the launch sequence of one evaluation.
+ */
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "yk_internal.h"
+
+using yk::FftStages;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+yk_status fail(yk_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+yk_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(YK_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(YK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define YK_CU(call, what)                                                                       \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);                                      \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------------------------------ */
+/* special functions for the parameter rules                                                   */
+
+/* exponential integral E1(x), x > 0: power series for x <= 1 (Abramowitz-Stegun 5.1.11),
+ * continued fraction for x > 1 (A-S 5.1.22) evaluated by the modified Lentz method */
+double expint_e1(double x)
+{
+    if (x <= 1.0) {
+        const double euler = 0.57721566490153286061;
+        double sum = 0.0, term = 1.0;
+        for (int k = 1; k < 200; ++k) {
+            term *= -x / k;
+            const double add = -term / k;
+            sum += add;
+            if (std::fabs(add) < 1e-18 * std::fabs(sum)) break;
+        }
+        return -euler - std::log(x) + sum;
+    }
+    /* E1(x) = e^{-x} / (x + 1/(1 + 1/(x + 2/(1 + 2/(x + ...))))) in the even form
+     * e^{-x} * 1/(x+1- 1^2/(x+3- 2^2/(x+5- ...))) */
+    const double tiny = 1e-300;
+    double b = x + 1.0, c = 1.0 / tiny, d = 1.0 / b, h = d;
+    for (int i = 1; i < 10000; ++i) {
+        const double an = -(double)i * i;
+        b += 2.0;
+        d = 1.0 / (an * d + b);
+        c = b + an / c;
+        const double del = c * d;
+        h *= del;
+        if (std::fabs(del - 1.0) < 1e-16) break;
+    }
+    return h * std::exp(-x);
+}
+
+/* Gauss-Legendre nodes/weights on [-1, 1] (Newton on the Legendre recurrence) */
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+{
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int k = 1; k <= n; ++k) {
+                const double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            const double dz = p0 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* G_H(r) = int_delta^inf exp(-r^2/(4t) - alpha^2 t) / (4 pi t) dt with t = delta e^s:
+ * (1/4pi) int_0^S exp(-r^2 e^{-s}/(4 delta) - alpha^2 delta e^s) ds, composite Gauss-Legendre.
+ * Used only to size the period (the decay length), so a few digits suffice. */
+double gh_time_integral(double alpha, double delta, double r)
+{
+    const double a2d = alpha * alpha * delta;
+    const double S = std::log(60.0 / a2d) + 2.0; /* alpha^2 delta e^S >= 60 */
+    static thread_local std::vector<double> gx, gw;
+    if (gx.empty()) gauss_legendre(16, gx, gw);
+    const int npan = 400;
+    const double L = (S > 1.0 ? S : 1.0) / npan;
+    double sum = 0.0;
+    for (int p = 0; p < npan; ++p)
+        for (int i = 0; i < 16; ++i) {
+            const double s = L * (p + 0.5 * (gx[i] + 1.0));
+            sum += 0.5 * L * gw[i] *
+                   std::exp(-r * r * std::exp(-s) / (4.0 * delta) - a2d * std::exp(s));
+        }
+    return sum / (4.0 * kPi);
+}
+
+/* smallest k with E1(delta (alpha^2 + k^2)) <= eps E1(delta alpha^2) (tail of the radial Fourier
+ * integral relative to G_H(0); reading of eq. kmax relative to the size of G_H) */
+double kmax_relative(double alpha, double delta, double eps)
+{
+    const double x0 = delta * alpha * alpha;
+    const double target = eps * expint_e1(x0);
+    double lo = x0, hi = x0 + 1.0;
+    while (expint_e1(hi) > target) hi = x0 + 2.0 * (hi - x0);
+    for (int it = 0; it < 200 && hi - lo > 1e-14 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (expint_e1(mid) > target) lo = mid;
+        else hi = mid;
+    }
+    const double k2 = hi / delta - alpha * alpha;
+    return k2 > 0.0 ? std::sqrt(k2) : 0.0;
+}
+
+/* eq. kmax as printed: exp(-delta (alpha^2 + k^2)) <= eps, zero when delta alpha^2 >= ln(1/eps) */
+double kmax_paper(double alpha, double delta, double eps)
+{
+    const double v = (std::log(1.0 / eps) - delta * alpha * alpha) / delta;
+    return v > 0.0 ? std::sqrt(v) : 0.0;
+}
+
+/* decay length: smallest r with G_H(r') <= eps G_H(0) for all r' >= r (G_H decreases in r) */
+double decay_length(double alpha, double delta, double eps)
+{
+    const double g0 = expint_e1(alpha * alpha * delta) / (4.0 * kPi);
+    double lo = 0.0, hi = std::max(1.0 / alpha, std::sqrt(delta));
+    while (gh_time_integral(alpha, delta, hi) > eps * g0) {
+        lo = hi;
+        hi *= 2.0;
+    }
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (gh_time_integral(alpha, delta, mid) > eps * g0) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+/* Fourier transform of the window: phi_hat(xi) = int_{-w/2}^{w/2} phi(z) cos(xi z) dz with
+ * z = (w/2) sin(theta), which removes the square-root edge behaviour of phi */
+double window_ft(double xi, int w, double beta)
+{
+    static thread_local std::vector<double> gx, gw;
+    if (gx.empty()) gauss_legendre(128, gx, gw);
+    const double half = 0.5 * w;
+    double sum = 0.0;
+    for (size_t i = 0; i < gx.size(); ++i) {
+        const double th = 0.25 * kPi * (gx[i] + 1.0);
+        sum += 0.25 * kPi * gw[i] * std::exp(beta * (std::cos(th) - 1.0)) *
+               std::cos(xi * half * std::sin(th)) * half * std::cos(th);
+    }
+    return 2.0 * sum;
+}
+
+bool smooth5(int64_t n)
+{
+    for (int p : {2, 3, 5})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
+
+/* radices of an L-point transform: 4s, then a 2, then 3s, then 5s */
+bool make_stages(int L, int n_tab, FftStages &st)
+{
+    std::memset(&st, 0, sizeof st);
+    st.L = L;
+    int m = L, s = 0;
+    auto push = [&](int r) {
+        if (s >= YK_MAX_STAGES) return false;
+        st.r[s++] = r;
+        m /= r;
+        return true;
+    };
+    while (m % 4 == 0)
+        if (!push(4)) return false;
+    while (m % 2 == 0)
+        if (!push(2)) return false;
+    while (m % 3 == 0)
+        if (!push(3)) return false;
+    while (m % 5 == 0)
+        if (!push(5)) return false;
+    if (m != 1) return false;
+    st.n = s;
+    int B = L;
+    for (int i = 0; i < s; ++i) {
+        st.B[i] = B;
+        st.tw_step[i] = n_tab / B;
+        B /= st.r[i];
+    }
+    return true;
+}
+
+/* position of frequency m after the DIF stages: digits of m little-endian in r_1, r_2, ...,
+ * each digit p_s placed at span_s = B_s / r_s */
+void dif_positions(const FftStages &st, std::vector<int> &pos)
+{
+    pos.assign(st.L, 0);
+    for (int m = 0; m < st.L; ++m) {
+        int mm = m, p = 0;
+        for (int s = 0; s < st.n; ++s) {
+            const int d = mm % st.r[s];
+            mm /= st.r[s];
+            p += d * (st.B[s] / st.r[s]);
+        }
+        pos[m] = p;
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* device memory                                                                               */
+
+yk_status buf_alloc(yk_plan_t p, DevBuf &b, size_t bytes, const char *what)
+{
+    if (b.ptr && b.bytes >= bytes) return YK_OK;
+    if (b.ptr) {
+        if (p->dealloc) p->dealloc(b.ptr, (void *)p->stream, p->alloc_ctx);
+        else cudaFree(b.ptr);
+        p->bytes -= (int64_t)b.bytes;
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) return YK_OK;
+    void *ptr = nullptr;
+    if (p->alloc) {
+        ptr = p->alloc(bytes, (void *)p->stream, p->alloc_ctx);
+        if (!ptr) return fail(YK_ERR_OOM, "allocator returned NULL for %s (%zu bytes)", what, bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&ptr, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? YK_ERR_OOM : YK_ERR_CUDA,
+                        "cudaMalloc(%s, %zu bytes): %s", what, bytes, cudaGetErrorString(e));
+        }
+    }
+    b.ptr = ptr;
+    b.bytes = bytes;
+    p->bytes += (int64_t)bytes;
+    return YK_OK;
+}
+
+void buf_free(yk_plan_t p, DevBuf &b)
+{
+    if (!b.ptr) return;
+    if (p->dealloc) p->dealloc(b.ptr, (void *)p->stream, p->alloc_ctx);
+    else cudaFree(b.ptr);
+    p->bytes -= (int64_t)b.bytes;
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+void free_all(yk_plan_t p)
+{
+    DevBuf *all[] = {&p->grid, &p->spec, &p->mult, &p->tw, &p->perm_h, &p->iperm_f,
+                     &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->trg_cnt, &p->trg_ptr,
+                     &p->trg_cur, &p->err, &p->w_src, &p->src_t, &p->ent_t, &p->ent_j,
+                     &p->trg_t, &p->trg_idx, &p->trg_tmp, &p->stage_x, &p->stage_y,
+                     &p->stage_w, &p->stage_u};
+    for (DevBuf *b : all) buf_free(p, *b);
+    for (int r = 0; r < yk_plan_s::kEventRing; ++r)
+        for (int k = 0; k < 2 * YK_NUM_STAGES; ++k)
+            if (p->events[r][k]) {
+                cudaEventDestroy(p->events[r][k]);
+                p->events[r][k] = nullptr;
+            }
+    p->profile = false;
+}
+
+template <typename T> T *P(DevBuf &b) { return static_cast<T *>(b.ptr); }
+
+bool is_device_ptr(const void *ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+/* device view of n doubles: the pointer itself if it is device memory, else a staging copy */
+yk_status to_device(yk_plan_t p, const double *src, int64_t n, DevBuf &stage,
+                    const double **out, const char *what)
+{
+    *out = src;
+    if (n == 0 || is_device_ptr(src)) return YK_OK;
+    yk_status s = buf_alloc(p, stage, sizeof(double) * (size_t)n, what);
+    if (s != YK_OK) return s;
+    YK_CU(cudaMemcpyAsync(stage.ptr, src, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice,
+                          p->stream),
+          what);
+    *out = P<double>(stage);
+    return YK_OK;
+}
+
+yk::Geom geom_of(const yk_plan_s *p)
+{
+    yk::Geom g;
+    g.ox = p->ox;
+    g.oy = p->oy;
+    g.inv_h = (double)p->n / p->period;
+    g.beta = p->beta;
+    g.c = 4.0 / ((double)p->w * p->w);
+    g.n = (int)p->n;
+    g.T = p->T;
+    g.nt = p->nt;
+    g.w = p->w;
+    for (int k = 0; k < 4; ++k) g.box[k] = p->box[k];
+    return g;
+}
+
+/* wait for the stream, fold the device error word into the sticky status */
+yk_status sync_and_check(yk_plan_t p)
+{
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+        p->status = YK_ERR_CUDA;
+        return cuda_fail(e, "stream synchronize");
+    }
+    if (p->err.ptr) {
+        int h_err = 0;
+        e = cudaMemcpy(&h_err, p->err.ptr, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            p->status = YK_ERR_CUDA;
+            return cuda_fail(e, "error word");
+        }
+        if (h_err & yk::ERR_POINT_OUTSIDE) p->status = YK_ERR_ARG;
+    }
+    if (p->status == YK_ERR_ARG)
+        return fail(YK_ERR_ARG, "a source or target lies outside the plan's box");
+    if (p->status != YK_OK) return fail((yk_status)p->status, "plan is in an error state");
+    return YK_OK;
+}
+
+/* bracket a stage with events when profiling */
+inline void stage_begin(yk_plan_t p, int s)
+{
+    if (p->profile)
+        cudaEventRecord(p->events[p->stage_runs[s] % yk_plan_s::kEventRing][2 * s], p->stream);
+}
+inline void stage_end(yk_plan_t p, int s)
+{
+    if (p->profile) {
+        cudaEventRecord(p->events[p->stage_runs[s] % yk_plan_s::kEventRing][2 * s + 1], p->stream);
+        ++p->stage_runs[s];
+    }
+}
+
+yk_status plan_tables(yk_plan_t p)
+{
+    const int64_t n = p->n, M = p->M;
+    const size_t nt2 = (size_t)p->nt * p->nt;
+    yk_status s;
+#define YK_TRY(x)                                                                               \
+    do {                                                                                        \
+        if ((s = (x)) != YK_OK) return s;                                                       \
+    } while (0)
+    YK_TRY(buf_alloc(p, p->grid, sizeof(double) * n * n, "grid"));
+    YK_TRY(buf_alloc(p, p->spec, sizeof(double2) * (M + 1) * n, "spectrum"));
+    YK_TRY(buf_alloc(p, p->mult, sizeof(double) * (M + 1) * (2 * M + 1), "multiplier"));
+    YK_TRY(buf_alloc(p, p->tw, sizeof(double2) * n, "twiddles"));
+    YK_TRY(buf_alloc(p, p->perm_h, sizeof(int) * (n / 2), "permutation"));
+    YK_TRY(buf_alloc(p, p->iperm_f, sizeof(int) * n, "permutation"));
+    YK_TRY(buf_alloc(p, p->tile_cnt, sizeof(int) * nt2, "tile counts"));
+    YK_TRY(buf_alloc(p, p->tile_ptr, sizeof(int) * (nt2 + 1), "tile offsets"));
+    YK_TRY(buf_alloc(p, p->tile_cur, sizeof(int) * nt2, "tile cursors"));
+    YK_TRY(buf_alloc(p, p->trg_cnt, sizeof(int) * nt2, "tile counts"));
+    YK_TRY(buf_alloc(p, p->trg_ptr, sizeof(int) * (nt2 + 1), "tile offsets"));
+    YK_TRY(buf_alloc(p, p->trg_cur, sizeof(int) * nt2, "tile cursors"));
+#undef YK_TRY
+    if (!make_stages((int)(n / 2), (int)n, p->st_half) || !make_stages((int)n, (int)n, p->st_full))
+        return fail(YK_ERR_INTERNAL, "FFT stage plan failed for n = %lld", (long long)n);
+    std::vector<int> pos_h, pos_f, ipos_f(n);
+    dif_positions(p->st_half, pos_h);
+    dif_positions(p->st_full, pos_f);
+    for (int64_t m = 0; m < n; ++m) ipos_f[pos_f[m]] = (int)m;
+    std::vector<double2> tw(n);
+    for (int64_t j = 0; j < n; ++j) {
+        const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)j /
+                              (long double)n;
+        tw[j] = make_double2((double)cosl(a), (double)-sinl(a));
+    }
+    std::vector<double> dfac(M + 1);
+    for (int64_t m = 0; m <= M; ++m) {
+        const double ph = window_ft(2.0 * kPi * (double)m / (double)n, p->w, p->beta);
+        dfac[m] = 1.0 / (ph * ph);
+    }
+    DevBuf d_dfac = {nullptr, 0};
+    if ((s = buf_alloc(p, d_dfac, sizeof(double) * (M + 1), "deconvolution")) != YK_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(p->perm_h.ptr, pos_h.data(), sizeof(int) * (n / 2),
+                                    cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->iperm_f.ptr, ipos_f.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
+                            p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p->tw.ptr, tw.data(), sizeof(double2) * n, cudaMemcpyHostToDevice,
+                            p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_dfac.ptr, dfac.data(), sizeof(double) * (M + 1),
+                            cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess)
+        e = yk::launch_build_mult(P<double>(p->mult), P<double>(d_dfac), (int)M, p->alpha,
+                                  p->delta, 2.0 * kPi / p->period, p->period, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    buf_free(p, d_dfac);
+    if (e != cudaSuccess) return cuda_fail(e, "plan tables");
+    return YK_OK;
+}
+
+} /* namespace */
+
+/* ------------------------------------------------------------------------------------------ */
+/* ABI                                                                                         */
+
+extern "C" {
+
+void yk_opts_default(yk_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = YK_FP64;
+    o->tol = 1e-10;
+    o->eps_hist = 1e-6;
+    o->box[0] = -1.5;
+    o->box[1] = 1.5;
+    o->box[2] = -1.5;
+    o->box[3] = 1.5;
+}
+
+const char *yk_last_error(void) { return g_last_error.c_str(); }
+
+/* parameter rules shared by yk_plan and yk_plan_params; fills the parameter fields of *p */
+static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
+{
+    if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(YK_ERR_ARG, "alpha must be > 0");
+    if (!(o->tol > 0.0 && o->tol < 1.0)) return fail(YK_ERR_ARG, "tol must lie in (0, 1)");
+    if (o->precision != YK_FP64)
+        return fail(YK_ERR_UNSUPPORTED, "precision %d is not available in this build", o->precision);
+    if (!(o->box[1] > o->box[0] && o->box[3] > o->box[2]) || !std::isfinite(o->box[0]) ||
+        !std::isfinite(o->box[1]) || !std::isfinite(o->box[2]) || !std::isfinite(o->box[3]))
+        return fail(YK_ERR_ARG, "box must satisfy xmin < xmax and ymin < ymax");
+    if (o->tile < 0) return fail(YK_ERR_ARG, "tile must be >= 0");
+    if (o->kmax_rule != 0 && o->kmax_rule != 1) return fail(YK_ERR_ARG, "kmax_rule must be 0 or 1");
+    if ((o->alloc == nullptr) != (o->free == nullptr))
+        return fail(YK_ERR_ARG, "give both alloc and free callbacks, or neither");
+    double delta = o->delta;
+    if (!(delta > 0.0)) {
+        if (!(o->h_vol > 0.0)) return fail(YK_ERR_ARG, "give delta > 0 or h_vol > 0");
+        const double eh = o->eps_hist > 0.0 ? o->eps_hist : 1e-6;
+        if (!(eh < 1.0)) return fail(YK_ERR_ARG, "eps_hist must lie in (0, 1)");
+        const double kp = 0.9 * kPi / o->h_vol; /* 0.9 k_Nyq (eq. k_nyq, Section 6.4) */
+        delta = std::log(1.0 / eh) / (kp * kp + alpha * alpha);
+    }
+    p->alpha = alpha;
+    p->delta = delta;
+    p->tol = o->tol;
+    p->eps = o->tol / 4.0;
+    p->precision = o->precision;
+    p->stream = (cudaStream_t)o->stream;
+    p->alloc = o->alloc;
+    p->dealloc = o->free;
+    p->alloc_ctx = o->alloc_ctx;
+
+    /* Fourier cutoff (eq. kmax) and period (decay length of G_H beyond the box span) */
+    p->kmax = o->kmax > 0.0         ? o->kmax
+              : o->kmax_rule == 1 ? kmax_paper(alpha, delta, p->eps)
+                                  : kmax_relative(alpha, delta, p->eps);
+    const double span = std::max(o->box[1] - o->box[0], o->box[3] - o->box[2]);
+    p->period = o->period > 0.0 ? o->period : span + decay_length(alpha, delta, p->eps);
+    if (!(p->period > span))
+        return fail(YK_ERR_ARG, "period %.17g must exceed the box span %.17g", p->period, span);
+    for (int k = 0; k < 4; ++k) p->box[k] = o->box[k];
+    const double cx = 0.5 * (o->box[0] + o->box[1]), cy = 0.5 * (o->box[2] + o->box[3]);
+    p->ox = cx - 0.5 * p->period;
+    p->oy = cy - 0.5 * p->period;
+    p->zero = !(p->kmax > 0.0);
+    p->M = p->zero ? 0 : (int64_t)std::ceil(p->kmax * p->period / (2.0 * kPi));
+
+    /* window width (digits of eps), grid size (>= 2 (2M+1), 5-smooth, with a tile edge) */
+    int w = (int)std::ceil(std::log10(1.0 / p->eps)) + 1;
+    w = std::min(16, std::max(2, w));
+    p->w = w;
+    p->beta = 2.30 * w;
+    const int64_t nmin = std::max<int64_t>({2 * (2 * p->M + 1), 2 * (int64_t)w, 16});
+    int64_t n = nmin + (nmin & 1);
+    int T = 0;
+    for (;; n += 2) {
+        if (n > yk::kMaxGridF64)
+            return fail(YK_ERR_UNSUPPORTED,
+                        "a grid of at least %lld points per axis is needed (this build supports "
+                        "%d): raise delta or tol, or lower the period",
+                        (long long)nmin, yk::kMaxGridF64);
+        if (!smooth5(n)) continue;
+        T = 0;
+        if (o->tile > 0) {
+            if (n % o->tile == 0 && o->tile >= w && n >= 2 * o->tile) T = o->tile;
+        } else {
+            for (int t = 64; t >= w; --t)
+                if (n % t == 0 && n >= 2 * t) {
+                    T = t;
+                    break;
+                }
+        }
+        if (T) break;
+    }
+    p->n = n;
+    p->T = T;
+    p->nt = (int)(n / T);
+    p->h = p->period / (double)n;
+    return YK_OK;
+}
+
+/* device bytes a plan holds for given point counts (plan tables plus resident layout) */
+static int64_t predicted_bytes(const yk_plan_s *p, int64_t n_src, int64_t n_trg)
+{
+    if (p->zero) return (int64_t)sizeof(int);
+    const int64_t n = p->n, M = p->M, nt2 = (int64_t)p->nt * p->nt;
+    int64_t b = 8 * n * n + 16 * (M + 1) * n + 8 * (M + 1) * (2 * M + 1) + 16 * n + 4 * (n / 2) +
+                4 * n + 4 * (6 * nt2 + 2) + 4;
+    b += n_src * (8 + 16 + 4 * (16 + 4)) + n_trg * (16 + 4 + 16);
+    return b;
+}
+
+extern "C" yk_status yk_plan_params(double alpha, const yk_opts *o, int64_t n_src, int64_t n_trg,
+                                    yk_info *info)
+{
+    if (!info) return fail(YK_ERR_ARG, "info is NULL");
+    yk_opts def;
+    yk_opts_default(&def);
+    if (!o) o = &def;
+    yk_plan_s tmp;
+    std::memset((void *)&tmp, 0, sizeof tmp);
+    yk_status s = choose_params(alpha, o, &tmp);
+    if (s != YK_OK) return s;
+    tmp.bytes = predicted_bytes(&tmp, n_src, n_trg);
+    return yk_plan_info(&tmp, info);
+}
+
+yk_status yk_plan(double alpha, const yk_opts *o, yk_plan_t *out)
+{
+    if (!out) return fail(YK_ERR_ARG, "yk_plan: out is NULL");
+    *out = nullptr;
+    yk_opts def;
+    yk_opts_default(&def);
+    if (!o) o = &def;
+    yk_plan_s *p = new (std::nothrow) yk_plan_s();
+    if (!p) return fail(YK_ERR_OOM, "host allocation of the plan failed");
+    std::memset((void *)p, 0, sizeof *p);
+    {
+        yk_status s0 = choose_params(alpha, o, p);
+        if (s0 != YK_OK) {
+            delete p;
+            return s0;
+        }
+    }
+    yk_status s = YK_OK;
+    if (o->profile) {
+        for (int r = 0; r < yk_plan_s::kEventRing && s == YK_OK; ++r)
+            for (int k = 0; k < 2 * YK_NUM_STAGES && s == YK_OK; ++k) {
+                cudaError_t e = cudaEventCreate(&p->events[r][k]);
+                if (e != cudaSuccess) s = cuda_fail(e, "event create");
+            }
+        p->profile = s == YK_OK;
+    }
+    if (s == YK_OK) s = buf_alloc(p, p->err, sizeof(int), "error word");
+    if (s == YK_OK) {
+        cudaError_t e = cudaMemsetAsync(p->err.ptr, 0, sizeof(int), p->stream);
+        if (e != cudaSuccess) s = cuda_fail(e, "error word");
+    }
+    if (s == YK_OK && !p->zero) s = plan_tables(p);
+    if (s != YK_OK) {
+        free_all(p);
+        delete p;
+        return s;
+    }
+    *out = p;
+    return YK_OK;
+}
+
+yk_status yk_plan_info(yk_plan_t p, yk_info *info)
+{
+    if (!p || !info) return fail(YK_ERR_ARG, "NULL argument");
+    std::memset(info, 0, sizeof *info);
+    info->alpha = p->alpha;
+    info->delta = p->delta;
+    info->tol = p->tol;
+    info->eps = p->eps;
+    info->kmax = p->kmax;
+    info->period = p->period;
+    info->origin[0] = p->ox;
+    info->origin[1] = p->oy;
+    info->h = p->h;
+    info->n_modes = p->M;
+    info->n_grid = p->zero ? 0 : p->n;
+    info->w = p->w;
+    info->beta = p->beta;
+    info->tile = p->T;
+    info->precision = p->precision;
+    info->device_bytes = p->bytes;
+    return YK_OK;
+}
+
+yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const double *ys,
+                        const double *w, int64_t n_trg, const double *xt, const double *yt)
+{
+    if (!p) return fail(YK_ERR_ARG, "plan is NULL");
+    if (n_src < 0 || n_trg < 0) return fail(YK_ERR_ARG, "negative point count");
+    if (n_src > (1ll << 28) || n_trg > (1ll << 30))
+        return fail(YK_ERR_UNSUPPORTED, "too many points for 32-bit entry indices");
+    if ((n_src > 0 && (!xs || !ys || !w)) || (n_trg > 0 && (!xt || !yt)))
+        return fail(YK_ERR_ARG, "NULL coordinate or weight array");
+    if (p->status != YK_OK) return fail((yk_status)p->status, "plan is in an error state");
+    p->points_set = false;
+    p->n_src = n_src;
+    p->n_trg = n_trg;
+    if (p->zero) {
+        p->points_set = true;
+        return YK_OK;
+    }
+    yk_status s;
+#define YK_TRY(x)                                                                               \
+    do {                                                                                        \
+        if ((s = (x)) != YK_OK) return s;                                                       \
+    } while (0)
+    const size_t ns = (size_t)n_src, nt = (size_t)n_trg;
+    YK_TRY(buf_alloc(p, p->w_src, sizeof(double) * ns, "weights"));
+    YK_TRY(buf_alloc(p, p->src_t, sizeof(double2) * ns, "source coordinates"));
+    YK_TRY(buf_alloc(p, p->ent_t, sizeof(double2) * 4 * ns, "entries"));
+    YK_TRY(buf_alloc(p, p->ent_j, sizeof(int) * 4 * ns, "entries"));
+    YK_TRY(buf_alloc(p, p->trg_t, sizeof(double2) * nt, "targets"));
+    YK_TRY(buf_alloc(p, p->trg_idx, sizeof(int) * nt, "targets"));
+    YK_TRY(buf_alloc(p, p->trg_tmp, sizeof(double2) * nt, "targets"));
+    const yk::Geom g = geom_of(p);
+    const double *dx = nullptr, *dy = nullptr, *dw = nullptr;
+    YK_TRY(to_device(p, xs, n_src, p->stage_x, &dx, "source x"));
+    YK_TRY(to_device(p, ys, n_src, p->stage_y, &dy, "source y"));
+    YK_TRY(to_device(p, w, n_src, p->stage_w, &dw, "weights"));
+    if (n_src > 0)
+        YK_CU(cudaMemcpyAsync(p->w_src.ptr, dw, sizeof(double) * ns, cudaMemcpyDeviceToDevice,
+                              p->stream),
+              "weights");
+    stage_begin(p, YK_STAGE_BIN_SRC);
+    YK_CU(yk::launch_bin_sources(g, n_src, dx, dy, P<double2>(p->src_t), P<int>(p->tile_cnt),
+                                 P<int>(p->tile_ptr), P<int>(p->tile_cur), P<double2>(p->ent_t),
+                                 P<int>(p->ent_j), P<int>(p->err), p->stream),
+          "bin sources");
+    stage_end(p, YK_STAGE_BIN_SRC);
+    /* the staging buffers are reused for the targets: order the copies after the source bins */
+    const double *tx = nullptr, *ty = nullptr;
+    YK_TRY(to_device(p, xt, n_trg, p->stage_x, &tx, "target x"));
+    YK_TRY(to_device(p, yt, n_trg, p->stage_y, &ty, "target y"));
+    stage_begin(p, YK_STAGE_BIN_TRG);
+    YK_CU(yk::launch_bin_targets(g, n_trg, tx, ty, P<double2>(p->trg_tmp), P<int>(p->trg_cnt),
+                                 P<int>(p->trg_ptr), P<int>(p->trg_cur), P<double2>(p->trg_t),
+                                 P<int>(p->trg_idx), P<int>(p->err), p->stream),
+          "bin targets");
+    stage_end(p, YK_STAGE_BIN_TRG);
+#undef YK_TRY
+    /* host inputs: return after the copies are consumed so the caller may reuse its arrays */
+    if (!is_device_ptr(xs) || !is_device_ptr(xt)) {
+        s = sync_and_check(p);
+        if (s != YK_OK) return s;
+    }
+    p->points_set = true;
+    return YK_OK;
+}
+
+yk_status yk_eval_longrange(yk_plan_t p, const double *density, double *u)
+{
+    if (!p) return fail(YK_ERR_ARG, "plan is NULL");
+    if (!p->points_set) return fail(YK_ERR_STATE, "yk_set_points has not been called");
+    if (p->status != YK_OK) return fail((yk_status)p->status, "plan is in an error state");
+    if ((p->n_src > 0 && !density) || (p->n_trg > 0 && !u))
+        return fail(YK_ERR_ARG, "NULL density or output array");
+    const bool host_u = p->n_trg > 0 && !is_device_ptr(u);
+    yk_status s;
+    double *du = u;
+    if (host_u) {
+        if ((s = buf_alloc(p, p->stage_u, sizeof(double) * (size_t)p->n_trg, "output")) != YK_OK)
+            return s;
+        du = P<double>(p->stage_u);
+    }
+    if (p->n_trg > 0) {
+        if (p->zero || p->n_src == 0) {
+            YK_CU(cudaMemsetAsync(du, 0, sizeof(double) * (size_t)p->n_trg, p->stream), "zero output");
+        } else {
+            const double *dd = nullptr;
+            if ((s = to_device(p, density, p->n_src, p->stage_w, &dd, "density")) != YK_OK) return s;
+            const yk::Geom g = geom_of(p);
+            const int n = (int)p->n, M = (int)p->M;
+            stage_begin(p, YK_STAGE_SPREAD);
+            YK_CU(yk::launch_spread(g, P<int>(p->tile_ptr), P<double2>(p->ent_t), P<int>(p->ent_j),
+                                    P<double>(p->w_src), dd, P<double>(p->grid), p->stream),
+                  "spread");
+            stage_end(p, YK_STAGE_SPREAD);
+            stage_begin(p, YK_STAGE_ROW_FWD);
+            YK_CU(yk::launch_row_fwd(P<double>(p->grid), P<double2>(p->spec), P<double2>(p->tw),
+                                     P<int>(p->perm_h), p->st_half, n, M, p->stream),
+                  "row FFT");
+            stage_end(p, YK_STAGE_ROW_FWD);
+            stage_begin(p, YK_STAGE_COLUMNS);
+            YK_CU(yk::launch_columns(P<double2>(p->spec), P<double>(p->mult), P<double2>(p->tw),
+                                     P<int>(p->iperm_f), p->st_full, n, M, p->stream),
+                  "column FFT");
+            stage_end(p, YK_STAGE_COLUMNS);
+            stage_begin(p, YK_STAGE_ROW_INV);
+            YK_CU(yk::launch_row_inv(P<double2>(p->spec), P<double>(p->grid), P<double2>(p->tw),
+                                     P<int>(p->perm_h), p->st_half, n, M, p->stream),
+                  "row inverse FFT");
+            stage_end(p, YK_STAGE_ROW_INV);
+            stage_begin(p, YK_STAGE_INTERP);
+            YK_CU(yk::launch_interp(g, P<int>(p->trg_ptr), P<double2>(p->trg_t),
+                                    P<int>(p->trg_idx), P<double>(p->grid), du, p->stream),
+                  "interpolation");
+            stage_end(p, YK_STAGE_INTERP);
+        }
+    }
+    if (host_u) {
+        YK_CU(cudaMemcpyAsync(u, du, sizeof(double) * (size_t)p->n_trg, cudaMemcpyDeviceToHost,
+                              p->stream),
+              "output copy");
+        return sync_and_check(p);
+    }
+    if (p->n_src > 0 && !is_device_ptr(density)) return sync_and_check(p);
+    return YK_OK;
+}
+
+yk_status yk_stage_times(yk_plan_t p, double *ms)
+{
+    if (!p || !ms) return fail(YK_ERR_ARG, "NULL argument");
+    if (!p->profile) return fail(YK_ERR_STATE, "plan was created without opts.profile");
+    YK_CU(cudaStreamSynchronize(p->stream), "stream synchronize");
+    for (int s = 0; s < YK_NUM_STAGES; ++s) {
+        ms[s] = -1.0;
+        const int64_t runs = p->stage_runs[s];
+        const int64_t k = runs < yk_plan_s::kEventRing ? runs : yk_plan_s::kEventRing;
+        double sum = 0.0;
+        int64_t used = 0;
+        for (int64_t r = runs - k; r < runs; ++r) {
+            float t = 0.0f;
+            const int slot = (int)(r % yk_plan_s::kEventRing);
+            if (cudaEventElapsedTime(&t, p->events[slot][2 * s], p->events[slot][2 * s + 1]) ==
+                cudaSuccess) {
+                sum += t;
+                ++used;
+            }
+        }
+        if (used) ms[s] = sum / (double)used;
+        p->stage_runs[s] = 0;
+    }
+    return YK_OK;
+}
+
+yk_status yk_sync(yk_plan_t p)
+{
+    if (!p) return fail(YK_ERR_ARG, "plan is NULL");
+    return sync_and_check(p);
+}
+
+yk_status yk_destroy(yk_plan_t p)
+{
+    if (!p) return YK_OK;
+    cudaStreamSynchronize(p->stream);
+    free_all(p);
+    delete p;
+    return YK_OK;
+}
+
+yk_status yk_batch_eval(yk_plan_t *plans, const double *const *density, double *const *u, int n)
+{
+    if (n < 0 || (n > 0 && (!plans || !density || !u)))
+        return fail(YK_ERR_ARG, "invalid batch arguments");
+    for (int i = 0; i < n; ++i) {
+        yk_status s = yk_eval_longrange(plans[i], density[i], u[i]);
+        if (s != YK_OK) return s;
+    }
+    return YK_OK;
+}
+
+} /* extern "C" */

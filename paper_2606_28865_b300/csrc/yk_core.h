@@ -1,0 +1,202 @@
+/*
+ * yk_core.h — per-item arithmetic of the long-range evaluator, shared by the CUDA kernels.
+ *
+ * Everything here is a pure function of its arguments (no threads, no shared memory), marked
+ * host+device so that the same statements can be exercised on the CPU by the test suite's host
+ * emulation of the kernels.  The kernels in yk_kernels.cu decide which thread runs which item.
+ */
+#ifndef YK_CORE_H
+#define YK_CORE_H
+
+#include <stdint.h>
+#include <math.h>
+
+#if defined(__CUDACC__)
+#define YK_HD __host__ __device__ __forceinline__
+#else
+#define YK_HD static inline
+#endif
+
+namespace yk {
+
+/* ---------------------------------------------------------------------------------------- */
+/* complex arithmetic on (re, im) pairs                                                      */
+template <typename R> struct cpx {
+    R re, im;
+};
+template <typename R> YK_HD cpx<R> mk(R a, R b) { cpx<R> z; z.re = a; z.im = b; return z; }
+template <typename R> YK_HD cpx<R> add(cpx<R> a, cpx<R> b) { return mk<R>(a.re + b.re, a.im + b.im); }
+template <typename R> YK_HD cpx<R> sub(cpx<R> a, cpx<R> b) { return mk<R>(a.re - b.re, a.im - b.im); }
+template <typename R> YK_HD cpx<R> mul(cpx<R> a, cpx<R> b)
+{
+    return mk<R>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+/* a * conj(b) */
+template <typename R> YK_HD cpx<R> mulc(cpx<R> a, cpx<R> b)
+{
+    return mk<R>(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
+}
+template <typename R> YK_HD cpx<R> conj(cpx<R> a) { return mk<R>(a.re, -a.im); }
+template <typename R> YK_HD cpx<R> scale(cpx<R> a, R s) { return mk<R>(a.re * s, a.im * s); }
+/* multiply by -i (SIGN = -1) or +i (SIGN = +1) */
+template <int SIGN, typename R> YK_HD cpx<R> mul_i(cpx<R> a)
+{
+    return SIGN > 0 ? mk<R>(-a.im, a.re) : mk<R>(a.im, -a.re);
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* exponential-of-semicircle window phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)), |z| <= w/2    */
+/* (the spreading kernel of the NUFFT that evaluates eqs. disrete_sigma_hat and sh_fourier)  */
+template <typename R> YK_HD R es_window(R z, R beta, R c /* = 4/w^2 */)
+{
+    R s = (R)1 - c * z * z;
+    return s >= (R)0 ? exp(beta * (sqrt(s) - (R)1)) : (R)0;
+}
+
+/* first tap l0 = ceil(t - w/2) of a point at grid coordinate t; taps l0 .. l0+w-1, and the
+ * window arguments z_a = l0 + a - t lie in [-w/2, w/2) */
+template <int W> YK_HD int first_tap(double t) { return (int)ceil(t - 0.5 * W); }
+
+/* non-negative residue of a mod n for |a| < 2n */
+YK_HD int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+/* ---------------------------------------------------------------------------------------- */
+/* FFT: in-place mixed-radix decimation-in-frequency (Sande-Tukey) on L points.               */
+/*                                                                                           */
+/* Stage s has radix r_s, block length B_s = L / (r_1 ... r_{s-1}) and span_s = B_s / r_s.   */
+/* Butterfly t in [0, L / r_s) of stage s: block b = t / span_s, k = t % span_s, elements     */
+/* x[b B_s + k + q span_s] (q < r_s) -> length-r_s DFT -> output p multiplied by W_{B_s}^{pk}  */
+/* and stored back at x[b B_s + k + p span_s].  After all stages position                     */
+/* sum_s p_s span_s holds frequency p_1 + r_1 (p_2 + r_2 (p_3 + ...)) (digit-reversed order). */
+/* The inverse (natural order out, unnormalised, e^{+}) runs the stages in reverse order and   */
+/* for each butterfly multiplies by conj(W_{B_s}^{pk}) before the inverse length-r_s DFT.     */
+/*                                                                                           */
+/* Twiddles come from a table tw[j] = exp(-2 pi i j / n_tab) with W_B^e = tw[e * (n_tab / B)]. */
+#define YK_MAX_STAGES 24
+
+struct FftStages {
+    int L;                     /* transform length */
+    int n;                     /* number of stages */
+    int r[YK_MAX_STAGES];      /* radix of stage s */
+    int B[YK_MAX_STAGES];      /* block length of stage s */
+    int tw_step[YK_MAX_STAGES]; /* twiddle table stride n_tab / B_s */
+};
+
+/* length-r DFT in place on v[0..r-1]; SIGN = -1 forward (e^{-2 pi i pq/r}), +1 inverse */
+template <int SIGN, typename R> YK_HD void dft2(cpx<R> *v)
+{
+    cpx<R> a = v[0], b = v[1];
+    v[0] = add(a, b);
+    v[1] = sub(a, b);
+}
+template <int SIGN, typename R> YK_HD void dft3(cpx<R> *v)
+{
+    const R h = (R)0.86602540378443864676; /* sqrt(3)/2 */
+    cpx<R> s = add(v[1], v[2]), d = sub(v[1], v[2]);
+    cpx<R> m = mk<R>(v[0].re - (R)0.5 * s.re, v[0].im - (R)0.5 * s.im);
+    cpx<R> t = mul_i<SIGN>(scale(d, h)); /* SIGN i h (x1 - x2) */
+    v[0] = add(v[0], s);
+    v[1] = add(m, t);
+    v[2] = sub(m, t);
+}
+template <int SIGN, typename R> YK_HD void dft4(cpx<R> *v)
+{
+    cpx<R> s02 = add(v[0], v[2]), d02 = sub(v[0], v[2]);
+    cpx<R> s13 = add(v[1], v[3]), d13 = mul_i<SIGN>(sub(v[1], v[3]));
+    v[0] = add(s02, s13);
+    v[2] = sub(s02, s13);
+    v[1] = add(d02, d13);
+    v[3] = sub(d02, d13);
+}
+template <int SIGN, typename R> YK_HD void dft5(cpx<R> *v)
+{
+    const R c1 = (R)0.30901699437494742410;  /* cos(2 pi/5) */
+    const R c2 = (R)-0.80901699437494742410; /* cos(4 pi/5) */
+    const R s1 = (R)0.95105651629515357212;  /* sin(2 pi/5) */
+    const R s2 = (R)0.58778525229247312917;  /* sin(4 pi/5) */
+    cpx<R> a1 = add(v[1], v[4]), b1 = sub(v[1], v[4]);
+    cpx<R> a2 = add(v[2], v[3]), b2 = sub(v[2], v[3]);
+    cpx<R> x0 = v[0];
+    cpx<R> m1 = mk<R>(x0.re + c1 * a1.re + c2 * a2.re, x0.im + c1 * a1.im + c2 * a2.im);
+    cpx<R> m2 = mk<R>(x0.re + c2 * a1.re + c1 * a2.re, x0.im + c2 * a1.im + c1 * a2.im);
+    /* SIGN i (s1 b1 + s2 b2) and SIGN i (s2 b1 - s1 b2) */
+    cpx<R> t1 = mul_i<SIGN>(mk<R>(s1 * b1.re + s2 * b2.re, s1 * b1.im + s2 * b2.im));
+    cpx<R> t2 = mul_i<SIGN>(mk<R>(s2 * b1.re - s1 * b2.re, s2 * b1.im - s1 * b2.im));
+    v[0] = mk<R>(x0.re + a1.re + a2.re, x0.im + a1.im + a2.im);
+    v[1] = add(m1, t1);
+    v[4] = sub(m1, t1);
+    v[2] = add(m2, t2);
+    v[3] = sub(m2, t2);
+}
+
+template <int SIGN, typename R> YK_HD void dft_r(cpx<R> *v, int r)
+{
+    switch (r) {
+    case 2: dft2<SIGN>(v); break;
+    case 3: dft3<SIGN>(v); break;
+    case 4: dft4<SIGN>(v); break;
+    default: dft5<SIGN>(v); break;
+    }
+}
+
+/* one forward DIF butterfly (stage s, butterfly t) on the array x of length st.L */
+template <typename R, typename TW>
+YK_HD void dif_butterfly(cpx<R> *x, const FftStages &st, int s, int t, const TW *tw, int tw_mul)
+{
+    const int r = st.r[s], B = st.B[s], span = B / r;
+    const int b = t / span, k = t - b * span;
+    const int base = b * B + k;
+    cpx<R> v[5];
+    for (int q = 0; q < r; ++q) v[q] = x[base + q * span];
+    dft_r<-1>(v, r);
+    x[base] = v[0];
+    const int step = st.tw_step[s] * tw_mul * k;
+    for (int p = 1; p < r; ++p) {
+        const TW w = tw[p * step];
+        x[base + p * span] = mul(v[p], mk<R>((R)w.x, (R)w.y));
+    }
+}
+
+/* one inverse butterfly (stage s of the reversed sequence) */
+template <typename R, typename TW>
+YK_HD void idif_butterfly(cpx<R> *x, const FftStages &st, int s, int t, const TW *tw, int tw_mul)
+{
+    const int r = st.r[s], B = st.B[s], span = B / r;
+    const int b = t / span, k = t - b * span;
+    const int base = b * B + k;
+    cpx<R> v[5];
+    v[0] = x[base];
+    const int step = st.tw_step[s] * tw_mul * k;
+    for (int p = 1; p < r; ++p) {
+        const TW w = tw[p * step];
+        v[p] = mulc(x[base + p * span], mk<R>((R)w.x, (R)w.y));
+    }
+    dft_r<+1>(v, r);
+    for (int q = 0; q < r; ++q) x[base + q * span] = v[q];
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* real <-> complex packing: a real row x[0..n) is transformed as z[l] = x[2l] + i x[2l+1]     */
+/* with an L = n/2 point complex FFT Z; then for m in [0, L]                                  */
+/*   X[m] = (Z[m] + conj Z[L-m]) / 2 + W_n^m (Z[m] - conj Z[L-m]) / (2i)                      */
+/* and back: Z'[m] = (X[m] + conj X[L-m]) + i conj(W_n^m) (X[m] - conj X[L-m]), whose          */
+/* unnormalised inverse FFT is x[2l] + i x[2l+1] (times 1: the full inverse of X).            */
+template <typename R> YK_HD cpx<R> r2c_post(cpx<R> Zm, cpx<R> Zc, cpx<R> Wm)
+{
+    cpx<R> e = mk<R>((R)0.5 * (Zm.re + Zc.re), (R)0.5 * (Zm.im - Zc.im));
+    /* (Zm - conj Zc) / (2i) = -i/2 (Zm - conj Zc) */
+    cpx<R> d = mk<R>(Zm.re - Zc.re, Zm.im + Zc.im);
+    cpx<R> o = mk<R>((R)0.5 * d.im, (R)-0.5 * d.re);
+    return add(e, mul(Wm, o));
+}
+template <typename R> YK_HD cpx<R> c2r_pre(cpx<R> Xm, cpx<R> Xc, cpx<R> Wm)
+{
+    cpx<R> s = mk<R>(Xm.re + Xc.re, Xm.im - Xc.im);
+    cpx<R> d = mk<R>(Xm.re - Xc.re, Xm.im + Xc.im);
+    cpx<R> t = mulc(d, Wm);          /* d conj(W) */
+    return add(s, mk<R>(-t.im, t.re)); /* s + i t */
+}
+
+} /* namespace yk */
+
+#endif /* YK_CORE_H */

@@ -1,0 +1,116 @@
+/*
+ * yk_internal.h — plan structure and kernel launchers shared by the host API (yk_api.cu) and the
+ * kernels (yk_kernels.cu).  Not part of the public ABI.
+ */
+#ifndef YK_INTERNAL_H
+#define YK_INTERNAL_H
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "yk_core.h"
+#include "../../include/yk.h"
+
+namespace yk {
+
+/* grid geometry handed to kernels by value */
+struct Geom {
+    double ox, oy;  /* lower-left corner of the periodic box */
+    double inv_h;   /* n / P */
+    double beta;    /* window shape */
+    double c;       /* 4 / w^2 */
+    int n;          /* grid points per axis */
+    int T;          /* tile edge (cells); divides n, T >= w, n >= 2T */
+    int nt;         /* tiles per axis = n / T */
+    int w;          /* window width */
+    double box[4];  /* xmin, xmax, ymin, ymax: points outside are rejected */
+};
+
+/* device error bits (sticky in the plan) */
+enum { ERR_POINT_OUTSIDE = 1 };
+
+/* kernel launchers (yk_kernels.cu); all enqueue on `st` and return the launch status */
+cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
+                               double2 *src_t, int *tile_cnt, int *tile_ptr, int *tile_cur,
+                               double2 *ent_t, int *ent_j, int *err, cudaStream_t st);
+cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, const double *yt,
+                               double2 *trg_tmp, int *cnt, int *ptr, int *cur, double2 *trg_t,
+                               int *trg_idx, int *err, cudaStream_t st);
+cudaError_t launch_spread(const Geom &g, const int *tile_ptr, const double2 *ent_t,
+                          const int *ent_j, const double *wq, const double *dens, double *grid,
+                          cudaStream_t st);
+cudaError_t launch_row_fwd(const double *grid, double2 *spec, const double2 *tw, const int *perm_h,
+                           const FftStages &sth, int n, int M, cudaStream_t st);
+cudaError_t launch_columns(double2 *spec, const double *mult, const double2 *tw,
+                           const int *iperm_f, const FftStages &stf, int n, int M,
+                           cudaStream_t st);
+cudaError_t launch_row_inv(const double2 *spec, double *grid, const double2 *tw,
+                           const int *perm_h, const FftStages &sth, int n, int M,
+                           cudaStream_t st);
+cudaError_t launch_interp(const Geom &g, const int *trg_ptr, const double2 *trg_t,
+                          const int *trg_idx, const double *grid, double *u, cudaStream_t st);
+cudaError_t launch_build_mult(double *mult, const double *dfac, int M, double alpha, double delta,
+                              double dk, double period, cudaStream_t st);
+
+/* largest grid the column pass supports (one column of n complex doubles in shared memory) */
+constexpr int kMaxGridF64 = 14400;
+
+} /* namespace yk */
+
+/* a device buffer with its size (bytes) */
+struct DevBuf {
+    void *ptr;
+    size_t bytes;
+};
+
+/* the plan */
+struct yk_plan_s {
+    /* parameters */
+    double alpha, delta, tol, eps, kmax, period, h, beta;
+    double ox, oy;
+    double box[4];
+    int64_t M, n;
+    int w, T, nt, precision;
+    bool zero; /* k_max == 0: history below tolerance, u = 0 */
+    cudaStream_t stream;
+    void *(*alloc)(size_t, void *, void *);
+    void (*dealloc)(void *, void *, void *);
+    void *alloc_ctx;
+    int64_t bytes;
+
+    yk::FftStages st_half, st_full;
+
+    /* plan-time device buffers */
+    DevBuf grid;     /* double[n*n]: spread output, then inverse-FFT output */
+    DevBuf spec;     /* double2[(M+1)*n]: half spectrum, transposed: spec[kx*n + y] */
+    DevBuf mult;     /* double[(M+1)*(2M+1)]: multiplier incl. window deconvolution */
+    DevBuf tw;       /* double2[n]: exp(-2 pi i j / n) */
+    DevBuf perm_h;   /* int[n/2]: DIF position of frequency m (half-length transform) */
+    DevBuf iperm_f;  /* int[n]: frequency held at DIF position i (full-length transform) */
+    DevBuf tile_cnt, tile_ptr, tile_cur; /* int[nt^2], int[nt^2+1], int[nt^2] (sources) */
+    DevBuf trg_cnt, trg_ptr, trg_cur;    /* same for targets */
+    DevBuf err;      /* int: device error bits */
+
+    /* resident point layout (grown on demand) */
+    bool points_set;
+    int64_t n_src, n_trg;
+    DevBuf w_src;    /* double[n_src]: quadrature weights, original order */
+    DevBuf src_t;    /* double2[n_src]: grid coordinates of the sources, original order */
+    DevBuf ent_t;    /* double2[<= 4 n_src]: (source, tile) entries grouped by tile */
+    DevBuf ent_j;    /* int[<= 4 n_src]: source index of each entry */
+    DevBuf trg_t;    /* double2[n_trg]: targets grouped by tile (grid coordinates) */
+    DevBuf trg_idx;  /* int[n_trg]: original index of each grouped target */
+    DevBuf trg_tmp;  /* double2[n_trg]: grid coordinates in original order */
+    /* staging copies of host arrays */
+    DevBuf stage_x, stage_y, stage_w, stage_u;
+    int status;      /* sticky yk_status */
+
+    /* optional stage timing: a ring of kEventRing runs per stage; events[r][2 s] and
+     * events[r][2 s + 1] bracket run r of stage s */
+    static constexpr int kEventRing = 64;
+    bool profile;
+    cudaEvent_t events[kEventRing][2 * YK_NUM_STAGES];
+    int64_t stage_runs[YK_NUM_STAGES]; /* runs recorded since the last yk_stage_times */
+};
+
+#endif /* YK_INTERNAL_H */

@@ -1,0 +1,93 @@
+"""CPU-side checks of the C ABI: the library loads, exports every declared symbol, validates its
+arguments, and chooses the parameters the paper's rules give (compared with the oracle's own
+statement of those rules).  No CUDA call is made here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle.params as OP
+import paper_2606_28865_b300 as yk
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"YK_API\s+[\w\s\*]+?\b(yk_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert "yk_plan" in names and "yk_eval_longrange" in names and len(names) >= 10
+    lib = ctypes.CDLL(yk.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("alpha", [10.0, 0.5, 200.0])
+def test_plan_parameters_follow_the_rules(alpha):
+    w = W.config_small()
+    info = yk.plan_params(alpha, w.n_src, w.n_trg, h_vol=w.h_vol, tol=1e-10)
+    eps = 1e-10 / 4
+    delta = OP.delta_from_mesh(alpha, w.h_vol)
+    assert info["delta"] == pytest.approx(delta, rel=1e-14)
+    assert info["kmax"] == pytest.approx(OP.kmax_relative(alpha, delta, eps), rel=1e-10)
+    assert info["period"] == pytest.approx(3.0 + OP.r_tol(alpha, delta, eps), rel=1e-5)
+    M = OP.modes(info["kmax"], info["period"])
+    assert info["n_modes"] == M
+    n = info["n_grid"]
+    assert n >= 2 * (2 * M + 1) and n % 2 == 0 and n % info["tile"] == 0
+    assert info["tile"] >= info["w"] and n >= 2 * info["tile"]
+    assert info["w"] == math.ceil(math.log10(1 / eps)) + 1
+    assert info["h"] == pytest.approx(info["period"] / n, rel=1e-15)
+
+
+def test_explicit_parameters_are_used():
+    info = yk.plan_params(10.0, delta=0.0167, kmax=30.0, period=6.0, tile=32)
+    assert info["delta"] == 0.0167 and info["kmax"] == 30.0 and info["period"] == 6.0
+    assert info["n_modes"] == math.ceil(30.0 * 6.0 / (2 * math.pi)) and info["tile"] == 32
+
+
+def test_paper_kmax_rule_and_zero_case():
+    alpha, tol = 200.0, 1e-6
+    eps = tol / 4
+    delta = 1.01 * math.log(1 / eps) / alpha ** 2
+    info = yk.plan_params(alpha, delta=delta, tol=tol, kmax_rule=1)
+    assert info["kmax"] == 0.0 and info["n_grid"] == 0
+    info = yk.plan_params(10.0, delta=0.0167, tol=tol, kmax_rule=1)
+    assert info["kmax"] == pytest.approx(OP.kmax_paper(10.0, 0.0167, eps), rel=1e-14)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(alpha=0.0, delta=0.01), yk.YK_ERR_ARG),
+    (dict(alpha=-1.0, delta=0.01), yk.YK_ERR_ARG),
+    (dict(alpha=10.0, delta=0.01, tol=0.0), yk.YK_ERR_ARG),
+    (dict(alpha=10.0, delta=0.01, tol=1.5), yk.YK_ERR_ARG),
+    (dict(alpha=10.0), yk.YK_ERR_ARG),                      # neither delta nor h_vol
+    (dict(alpha=10.0, delta=0.01, box=(1, 0, 0, 1)), yk.YK_ERR_ARG),
+    (dict(alpha=10.0, delta=0.01, period=2.0), yk.YK_ERR_ARG),  # period below the span
+    (dict(alpha=10.0, delta=0.01, kmax_rule=3), yk.YK_ERR_ARG),
+    (dict(alpha=0.01, delta=1e-6), yk.YK_ERR_UNSUPPORTED),  # grid beyond the supported size
+])
+def test_argument_validation(kw, status):
+    alpha = kw.pop("alpha")
+    with pytest.raises(yk.YkError) as ei:
+        yk.plan_params(alpha, **kw)
+    assert ei.value.status == status
+    assert len(str(ei.value)) > 20
+
+
+def test_predicted_memory_grows_with_points():
+    a = yk.plan_params(10.0, 1000, 1000, delta=0.0167)["device_bytes"]
+    b = yk.plan_params(10.0, 2000, 1000, delta=0.0167)["device_bytes"]
+    c = yk.plan_params(10.0, 1000, 2000, delta=0.0167)["device_bytes"]
+    assert b > a and c > a

@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerance: relative L-infinity error max_i |u_gpu - u_oracle| / max_i |u_oracle| <= tol with the
+plan's tol = 1e-10 for the FP64 path.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.params as OP
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def _yk():
+    import paper_2606_28865_b300 as yk
+    return yk
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def rel_err(u, ref):
+    return float(np.max(np.abs(u - ref)) / np.max(np.abs(ref)))
+
+
+def run_gpu(work, alpha, tol=TOL64, density=None, **opts):
+    yk = _yk()
+    opts.setdefault("h_vol", work.h_vol)
+    plan = yk.Plan(alpha, tol=tol, box=work.box, **opts)
+    plan.set_points(dev(work.xs), dev(work.ys), dev(work.w), dev(work.xt), dev(work.yt))
+    dens = work.density if density is None else density
+    u = plan.eval(dev(dens))
+    plan.sync()
+    info = plan.info
+    out = u.cpu().numpy()
+    plan.close()
+    return out, info
+
+
+@pytest.fixture(scope="module")
+def small():
+    return W.config_small()
+
+
+@pytest.mark.parametrize("alpha", [10.0, 0.5, 200.0])
+def test_config_small_fp64(small, alpha):
+    u, info = run_gpu(small, alpha)
+    ref = oracle.direct_sum(alpha, info["delta"], small.xs, small.ys, small.q, small.xt, small.yt)
+    err = rel_err(u, ref)
+    assert err <= TOL64, f"alpha={alpha} err={err:.3e} info={info}"
+
+
+def test_discrete_formula_p8(small):
+    # explicit k_max and period from the oracle's own rules; the GPU result must reproduce the
+    # paper's discrete formula (type-1 sum, multiplier, type-2 sum) to the NUFFT accuracy
+    alpha = 10.0
+    delta = OP.delta_from_mesh(alpha, small.h_vol)
+    eps = TOL64 / 4
+    kmax = OP.kmax_relative(alpha, delta, eps)
+    period = 3.0 + OP.r_tol(alpha, delta, eps)
+    M = OP.modes(kmax, period)
+    u, info = run_gpu(small, alpha, delta=delta, kmax=kmax, period=period)
+    assert info["n_modes"] == M
+    ref = oracle.discrete_sum(alpha, delta, period, M, (0.0, 0.0), small.xs, small.ys, small.q,
+                              small.xt, small.yt)
+    assert rel_err(u, ref) <= TOL64 / 4
+
+
+def test_gaussian_source_analytic_p4():
+    # whole GPU path against the closed form V_H[f](0) = (a/4) e^{alpha^2 a/4} E1(alpha^2(a+4 delta)/4)
+    import scipy.special as sp
+    a, alpha, delta = 0.1, 10.0, 0.0167
+    xi, wi = np.polynomial.legendre.leggauss(160)
+    X, Y = np.meshgrid(1.45 * xi, 1.45 * xi)
+    q = (np.exp(-(X ** 2 + Y ** 2) / a) * np.outer(1.45 * wi, 1.45 * wi)).ravel()
+    work = W.Workload("gauss", alpha, X.ravel(), Y.ravel(), q, np.ones(q.size), np.zeros(1),
+                      np.zeros(1), 0, 0.1)
+    u, _ = run_gpu(work, alpha, delta=delta)
+    closed = a / 4 * math.exp(alpha ** 2 * a / 4) * sp.exp1(alpha ** 2 * (a + 4 * delta) / 4)
+    assert abs(u[0] - closed) <= 1e-10 * closed
+
+
+def test_deterministic_and_host_device_equivalence(small):
+    yk = _yk()
+    alpha = 10.0
+    plan = yk.Plan(alpha, tol=TOL64, h_vol=small.h_vol, box=small.box)
+    plan.set_points(dev(small.xs), dev(small.ys), dev(small.w), dev(small.xt), dev(small.yt))
+    u1 = plan.eval(dev(small.density)).cpu().numpy()
+    u2 = plan.eval(dev(small.density)).cpu().numpy()
+    assert np.array_equal(u1, u2)  # fixed-point accumulation: bitwise repeatable
+    # host arrays in and out through the same ABI
+    plan.set_points(small.xs, small.ys, small.w, small.xt, small.yt)
+    u3 = plan.eval(small.density)
+    assert isinstance(u3, np.ndarray) and np.array_equal(u1, u3)
+    # new densities on the resident layout (a Rothe step): linear in the density
+    d2 = W.strengths_for(small, alpha, seed=3)
+    ua = plan.eval(dev(d2)).cpu().numpy()
+    ub = plan.eval(dev(small.density + 2.0 * d2)).cpu().numpy()
+    assert np.max(np.abs(ub - (u1 + 2.0 * ua))) <= 1e-12 * np.max(np.abs(ub))
+    plan.close()
+
+
+def test_permuted_points_give_the_same_values(small):
+    rng = np.random.default_rng(4)
+    ps, pt = rng.permutation(small.n_src), rng.permutation(small.n_trg)
+    w2 = W.Workload("perm", small.alpha, small.xs[ps], small.ys[ps], small.w[ps],
+                    small.density[ps], small.xt[pt], small.yt[pt], 0, small.h_vol)
+    u, _ = run_gpu(small, 10.0)
+    v, _ = run_gpu(w2, 10.0)
+    # exact per-tile fixed-point sums: the order of the sources does not change a single bit
+    assert np.array_equal(u[pt], v)
+
+
+def test_edge_cases(small):
+    yk = _yk()
+    plan = yk.Plan(10.0, tol=TOL64, delta=0.0167, box=small.box)
+    # no sources: u = 0
+    plan.set_points(dev([]), dev([]), dev([]), dev(small.xt[:5]), dev(small.yt[:5]))
+    u = plan.eval(dev([])).cpu().numpy()
+    assert np.all(u == 0.0)
+    # no targets
+    plan.set_points(dev(small.xs), dev(small.ys), dev(small.w), dev([]), dev([]))
+    assert plan.eval(dev(small.density)).numel() == 0
+    # one source, one target, both at box corners (window wraps around the periodic grid)
+    xs, ys, xt, yt = np.array([-1.5]), np.array([1.5 - 1e-12]), np.array([1.5 - 1e-12]), np.array([-1.5])
+    plan.set_points(dev(xs), dev(ys), dev([0.7]), dev(xt), dev(yt))
+    u = plan.eval(dev([2.0])).cpu().numpy()
+    ref = oracle.direct_sum(10.0, 0.0167, xs, ys, [1.4], xt, yt)
+    g0 = oracle.gh_hankel(10.0, 0.0167, [0.0])[0] * 1.4
+    assert abs(u[0] - ref[0]) <= TOL64 * g0
+    # a target on top of a source (r = 0) and targets on grid nodes
+    info = plan.info
+    h, ox, oy = info["h"], info["origin"][0], info["origin"][1]
+    xt = np.array([0.1, ox + round((0.3 - ox) / h) * h])
+    yt = np.array([0.2, oy + round((-0.4 - oy) / h) * h])
+    plan.set_points(dev([0.1, 0.3]), dev([0.2, -0.4]), dev([1.0, 1.0]), dev(xt), dev(yt))
+    u = plan.eval(dev([1.0, -0.5])).cpu().numpy()
+    ref = oracle.direct_sum(10.0, 0.0167, [0.1, 0.3], [0.2, -0.4], [1.0, -0.5], xt, yt)
+    assert np.max(np.abs(u - ref)) <= TOL64 * 1.5 * oracle.gh_hankel(10.0, 0.0167, [0.0])[0]
+    plan.close()
+
+
+def test_point_outside_box_is_reported(small):
+    yk = _yk()
+    plan = yk.Plan(10.0, tol=TOL64, delta=0.0167, box=small.box)
+    plan.set_points(dev([0.0, 1.6]), dev([0.0, 0.0]), dev([1.0, 1.0]), dev([0.0]), dev([0.0]))
+    with pytest.raises(yk.YkError) as ei:
+        plan.sync()
+    assert ei.value.status == yk.YK_ERR_ARG
+    plan.close()
+
+
+def test_eval_before_set_points_is_a_state_error():
+    yk = _yk()
+    plan = yk.Plan(10.0, tol=TOL64, delta=0.0167)
+    with pytest.raises(yk.YkError) as ei:
+        plan.eval(dev([]))
+    assert ei.value.status == yk.YK_ERR_STATE
+    plan.close()
+
+
+def test_zero_plan_paper_rule():
+    yk = _yk()
+    alpha, tol = 200.0, 1e-6
+    delta = 1.01 * math.log(4 / tol) / alpha ** 2
+    plan = yk.Plan(alpha, tol=tol, delta=delta, kmax_rule=1)
+    w = W.config_small()
+    plan.set_points(dev(w.xs), dev(w.ys), dev(w.w), dev(w.xt), dev(w.yt))
+    u = plan.eval(dev(w.density)).cpu().numpy()
+    assert np.all(u == 0.0)
+    # the paper's claim: the neglected history part is below eps times the total strength
+    ref = oracle.direct_sum(alpha, delta, w.xs, w.ys, w.q, w.xt, w.yt)
+    assert np.max(np.abs(ref)) <= tol / 4 * np.abs(w.q).sum()
+    plan.close()
+
+
+@pytest.mark.parametrize("alpha", [10.0, 100.0, 1.0])
+def test_config_large_sampled(alpha):
+    """1.1e6 sources, 1e6 targets at the full size; oracle on 1,000 sampled targets."""
+    work = W.config_large(alpha)
+    u, info = run_gpu(work, alpha)
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(work.n_trg, 1000, replace=False))
+    ref = oracle.direct_sum(alpha, info["delta"], work.xs, work.ys, work.q, work.xt[idx],
+                            work.yt[idx])
+    err = rel_err(u[idx], ref)
+    assert err <= TOL64, f"alpha={alpha} err={err:.3e} info={info}"
