@@ -183,6 +183,30 @@ YK_API const char *yk_last_error(void);
 YK_API yk_status yk_fma_peak(int precision, double *tflops);
 
 /*
+ * yk_eval_longrange_static: one evaluation (yk_plan + yk_set_points + yk_eval_longrange in a
+ * single call) that allocates no device memory, for callers that cannot call cudaMalloc — for
+ * example code embedded in a host application that owns every device allocation, or a process
+ * that must not grow its device footprint after start-up.  The paper has no counterpart; this is
+ * a deployment variant of the same kernels.
+ *  - alpha, o: as for yk_plan (o->alloc/o->free must be NULL; o->stream is used).
+ *  - xs, ys, w, density (n_src) and xt, yt (n_trg) are inputs, u (n_trg) is written; every array
+ *    must be device memory, or YK_ERR_ARG.
+ *  - All scratch lives in one static device array of 32 MiB that every GPU loading the library
+ *    holds until the process exits; a problem needing more returns YK_ERR_UNSUPPORTED (the grid,
+ *    its spectrum and multiplier, and about 120 bytes per source and 36 per target must fit).
+ *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ *    with that device current); make that first call before any stream capture.
+ *  - Every call reuses the same array and clears what must start at zero; calls whose work
+ *    overlaps on the GPU (other streams or threads) race on it.  The call waits for o->stream.
+ *  - msg (msg_len bytes, may be NULL) receives the failure message.
+ */
+YK_API yk_status yk_eval_longrange_static(double alpha, const yk_opts *o, int64_t n_src,
+                                          const double *xs, const double *ys, const double *w,
+                                          const double *density, int64_t n_trg, const double *xt,
+                                          const double *yt, double *u, char *msg,
+                                          size_t msg_len);
+
+/*
  * yk_batch_eval: evaluate n plans (each with points already set) with their densities in one
  * submission; density[i] and u[i] follow the rules of yk_eval_longrange for plans[i].
  */

@@ -29,9 +29,10 @@ _STATUS = {0: "YK_OK", 1: "YK_ERR_ARG", 2: "YK_ERR_OOM", 3: "YK_ERR_CUDA", 4: "Y
 
 
 class YkError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    def __init__(self, status: int, where: str, msg: str | None = None):
         self.status = status
-        msg = _lib.yk_last_error().decode(errors="replace")
+        if msg is None:
+            msg = _lib.yk_last_error().decode(errors="replace")
         super().__init__(f"{where}: {_STATUS.get(status, status)}: {msg}")
 
 
@@ -256,6 +257,28 @@ def fma_peak_tflops(precision=YK_FP64) -> float:
     v = ctypes.c_double()
     _check(_lib.yk_fma_peak(int(precision), ctypes.byref(v)), "yk_fma_peak")
     return v.value
+
+
+_lib.yk_eval_longrange_static.argtypes = [_d, ctypes.POINTER(Opts), _i64, _vp, _vp, _vp, _vp,
+                                          _i64, _vp, _vp, _vp, ctypes.c_char_p, ctypes.c_size_t]
+_lib.yk_eval_longrange_static.restype = ctypes.c_int
+
+
+def eval_longrange_static(alpha, xs, ys, w, density, xt, yt, out, stream=None, **opts):
+    """One evaluation with no device allocation: all scratch is the library's static 32 MiB
+    device array.  Every array (including `out`) must already be on the device."""
+    if stream is None:
+        stream = _current_stream()
+    o = make_opts(stream=stream, **opts)
+    keep = []
+    msg = ctypes.create_string_buffer(512)
+    st = _lib.yk_eval_longrange_static(float(alpha), ctypes.byref(o), _len(xs), _ptr(xs, keep),
+                                       _ptr(ys, keep), _ptr(w, keep), _ptr(density, keep),
+                                       _len(xt), _ptr(xt, keep), _ptr(yt, keep), _ptr(out, keep),
+                                       msg, len(msg))
+    if st != YK_OK:
+        raise YkError(st, "yk_eval_longrange_static", msg.value.decode(errors="replace"))
+    return out
 
 
 def loaded_library_path() -> str:

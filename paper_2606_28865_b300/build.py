@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libyk.so")
-SOURCES = ["yk_api.cu", "yk_kernels.cu", "yk_peak.cu"]
+SOURCES = ["yk_api.cu", "yk_kernels.cu", "yk_peak.cu", "yk_static.cu"]
 HEADERS = ["yk_core.h", "yk_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -82,10 +82,8 @@ double expint_e1(double x)
 }
 
 /* Gauss-Legendre nodes/weights on [-1, 1] (Newton on the Legendre recurrence) */
-void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w)
+void gauss_legendre(int n, double *x, double *w)
 {
-    x.assign(n, 0.0);
-    w.assign(n, 0.0);
     for (int i = 0; i < (n + 1) / 2; ++i) {
         double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), dp = 0.0;
         for (int it = 0; it < 100; ++it) {
@@ -113,8 +111,13 @@ double gh_time_integral(double alpha, double delta, double r)
 {
     const double a2d = alpha * alpha * delta;
     const double S = std::log(60.0 / a2d) + 2.0; /* alpha^2 delta e^S >= 60 */
-    static thread_local std::vector<double> gx, gw;
-    if (gx.empty()) gauss_legendre(16, gx, gw);
+    /* 16-point rule in fixed storage, built once (no heap use on this path) */
+    struct Rule {
+        double x[16], w[16];
+        Rule() { gauss_legendre(16, x, w); }
+    };
+    static const Rule rule;
+    const double *gx = rule.x, *gw = rule.w;
     const int npan = 400;
     const double L = (S > 1.0 ? S : 1.0) / npan;
     double sum = 0.0;
@@ -173,7 +176,11 @@ double decay_length(double alpha, double delta, double eps)
 double window_ft(double xi, int w, double beta)
 {
     static thread_local std::vector<double> gx, gw;
-    if (gx.empty()) gauss_legendre(128, gx, gw);
+    if (gx.empty()) {
+        gx.resize(128);
+        gw.resize(128);
+        gauss_legendre(128, gx.data(), gw.data());
+    }
     const double half = 0.5 * w;
     double sum = 0.0;
     for (size_t i = 0; i < gx.size(); ++i) {
