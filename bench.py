@@ -41,7 +41,7 @@ L2_BYTES = 126 * 1024 * 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--alphas", default=",".join(str(a) for a in ALPHAS))
@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--ref-targets", type=int, default=120,
                     help="targets per alpha in each reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32c", action="store_true", help="skip the FP32C measurement")
     return ap.parse_args()
 
 
@@ -95,7 +96,7 @@ class ClockSampler:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.p = None
@@ -373,6 +374,50 @@ def main():
     roof.update({"kernel": dom, "launches_per_step": len(alphas), "peak_source": peak_note,
                  "hbm_achieved_gbs": gbs, "fp64_achieved_tflops": tfl})
 
+    # the FP32C form of the same workload (FP32 spread/FFT/interp, two-sum grid sums, FP64
+    # final sums at the targets; relative accuracy 1e-6)
+    fp32c = None
+    if not args.no_fp32c:
+        plans32 = {a: yk.Plan(a, tol=1e-6, precision=yk.YK_FP32C, h_vol=works[a].h_vol,
+                              box=works[a].box, profile=True, stream=stream) for a in alphas}
+
+        def step32():
+            for a in alphas:
+                xs, ys, w, xt, yt, d = dbufs[a]
+                plans32[a].set_points(xs, ys, w, xt, yt)
+                plans32[a].eval(d, out=outs[a])
+
+        for _ in range(max(3, args.warmup)):
+            step32()
+        torch.cuda.synchronize()
+        for a in alphas:
+            plans32[a].stage_times()
+        barrier(pg)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step32()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
+        st32 = {str(a): plans32[a].stage_times() for a in alphas}
+        lat32 = []
+        for a in alphas:
+            for _ in range(5):
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                plans32[a].eval(dbufs[a][5], out=outs[a])
+                s1.record(stream)
+                torch.cuda.synchronize()
+                lat32.append(s0.elapsed_time(s1))
+        fp32c = {"value": pts_step * world / (ms32 * 1e-3), "unit": "points/s",
+                 "ms_per_step": ms32, "tol": 1e-6, "dtype": "f32 (two-sum grid, f64 final sums)",
+                 "grids": {str(a): plans32[a].info["n_grid"] for a in alphas},
+                 "stage_ms": st32,
+                 "latency_ms": {"p50": float(np.percentile(lat32, 50)),
+                                "p99": float(np.percentile(lat32, 99))}}
+        for a in alphas:
+            plans32[a].close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(alphas, args.cpu_targets)
@@ -403,6 +448,7 @@ def main():
                       "value": pts_step * world / (eval_only_ms * 1e-3) if eval_only_ms else None},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "what": "one yk_eval_longrange on a resident layout, all alphas"},
+        "fp32c": fp32c,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -290,7 +290,8 @@ void buf_free(yk_plan_t p, DevBuf &b)
 void free_all(yk_plan_t p)
 {
     DevBuf *all[] = {&p->grid, &p->spec, &p->mult, &p->tw, &p->perm_h, &p->iperm_f,
-                     &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->trg_cnt, &p->trg_ptr,
+                     &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->tile_order, &p->trg_cnt,
+                     &p->trg_ptr,
                      &p->trg_cur, &p->err, &p->w_src, &p->src_t, &p->ent_t, &p->ent_j,
                      &p->trg_t, &p->trg_idx, &p->trg_tmp, &p->stage_x, &p->stage_y,
                      &p->stage_w, &p->stage_u};
@@ -394,15 +395,18 @@ yk_status plan_tables(yk_plan_t p)
     do {                                                                                        \
         if ((s = (x)) != YK_OK) return s;                                                       \
     } while (0)
-    YK_TRY(buf_alloc(p, p->grid, sizeof(double) * n * n, "grid"));
-    YK_TRY(buf_alloc(p, p->spec, sizeof(double2) * (M + 1) * n, "spectrum"));
-    YK_TRY(buf_alloc(p, p->mult, sizeof(double) * (M + 1) * (2 * M + 1), "multiplier"));
-    YK_TRY(buf_alloc(p, p->tw, sizeof(double2) * n, "twiddles"));
+    const bool f32 = p->precision == YK_FP32C;
+    const size_t rb = f32 ? sizeof(float) : sizeof(double);
+    YK_TRY(buf_alloc(p, p->grid, rb * n * n, "grid"));
+    YK_TRY(buf_alloc(p, p->spec, 2 * rb * (M + 1) * n, "spectrum"));
+    YK_TRY(buf_alloc(p, p->mult, rb * (M + 1) * (2 * M + 1), "multiplier"));
+    YK_TRY(buf_alloc(p, p->tw, 2 * rb * n, "twiddles"));
     YK_TRY(buf_alloc(p, p->perm_h, sizeof(int) * (n / 2), "permutation"));
     YK_TRY(buf_alloc(p, p->iperm_f, sizeof(int) * n, "permutation"));
     YK_TRY(buf_alloc(p, p->tile_cnt, sizeof(int) * nt2, "tile counts"));
     YK_TRY(buf_alloc(p, p->tile_ptr, sizeof(int) * (nt2 + 1), "tile offsets"));
     YK_TRY(buf_alloc(p, p->tile_cur, sizeof(int) * nt2, "tile cursors"));
+    YK_TRY(buf_alloc(p, p->tile_order, sizeof(int) * nt2, "tile order"));
     YK_TRY(buf_alloc(p, p->trg_cnt, sizeof(int) * nt2, "tile counts"));
     YK_TRY(buf_alloc(p, p->trg_ptr, sizeof(int) * (nt2 + 1), "tile offsets"));
     YK_TRY(buf_alloc(p, p->trg_cur, sizeof(int) * nt2, "tile cursors"));
@@ -413,11 +417,14 @@ yk_status plan_tables(yk_plan_t p)
     dif_positions(p->st_half, pos_h);
     dif_positions(p->st_full, pos_f);
     for (int64_t m = 0; m < n; ++m) ipos_f[pos_f[m]] = (int)m;
-    std::vector<double2> tw(n);
+    /* twiddles from long double, rounded once to the table's type */
+    std::vector<double2> tw(f32 ? 0 : n);
+    std::vector<float2> tw32(f32 ? n : 0);
     for (int64_t j = 0; j < n; ++j) {
         const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)j /
                               (long double)n;
-        tw[j] = make_double2((double)cosl(a), (double)-sinl(a));
+        if (f32) tw32[j] = make_float2((float)cosl(a), (float)-sinl(a));
+        else tw[j] = make_double2((double)cosl(a), (double)-sinl(a));
     }
     std::vector<double> dfac(M + 1);
     for (int64_t m = 0; m <= M; ++m) {
@@ -432,14 +439,19 @@ yk_status plan_tables(yk_plan_t p)
         e = cudaMemcpyAsync(p->iperm_f.ptr, ipos_f.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
                             p->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(p->tw.ptr, tw.data(), sizeof(double2) * n, cudaMemcpyHostToDevice,
-                            p->stream);
+        e = cudaMemcpyAsync(p->tw.ptr, f32 ? (const void *)tw32.data() : (const void *)tw.data(),
+                            2 * rb * n, cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_dfac.ptr, dfac.data(), sizeof(double) * (M + 1),
                             cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess)
-        e = yk::launch_build_mult(P<double>(p->mult), P<double>(d_dfac), (int)M, p->alpha,
-                                  p->delta, 2.0 * kPi / p->period, p->period, p->stream);
+    if (e == cudaSuccess) {
+        if (f32)
+            e = yk::launch_build_mult32(P<float>(p->mult), P<double>(d_dfac), (int)M, p->alpha,
+                                        p->delta, 2.0 * kPi / p->period, p->period, p->stream);
+        else
+            e = yk::launch_build_mult(P<double>(p->mult), P<double>(d_dfac), (int)M, p->alpha,
+                                      p->delta, 2.0 * kPi / p->period, p->period, p->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     buf_free(p, d_dfac);
     if (e != cudaSuccess) return cuda_fail(e, "plan tables");
@@ -473,8 +485,8 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
 {
     if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(YK_ERR_ARG, "alpha must be > 0");
     if (!(o->tol > 0.0 && o->tol < 1.0)) return fail(YK_ERR_ARG, "tol must lie in (0, 1)");
-    if (o->precision != YK_FP64)
-        return fail(YK_ERR_UNSUPPORTED, "precision %d is not available in this build", o->precision);
+    if (o->precision != YK_FP64 && o->precision != YK_FP32C)
+        return fail(YK_ERR_ARG, "precision must be YK_FP64 or YK_FP32C");
     if (!(o->box[1] > o->box[0] && o->box[3] > o->box[2]) || !std::isfinite(o->box[0]) ||
         !std::isfinite(o->box[1]) || !std::isfinite(o->box[2]) || !std::isfinite(o->box[3]))
         return fail(YK_ERR_ARG, "box must satisfy xmin < xmax and ymin < ymax");
@@ -524,17 +536,19 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
     int64_t n = nmin + (nmin & 1);
     int T = 0;
     for (;; n += 2) {
-        if (n > yk::kMaxGridF64)
+        const int nmax = o->precision == YK_FP32C ? yk::kMaxGridF32 : yk::kMaxGridF64;
+        if (n > nmax)
             return fail(YK_ERR_UNSUPPORTED,
                         "a grid of at least %lld points per axis is needed (this build supports "
-                        "%d): raise delta or tol, or lower the period",
-                        (long long)nmin, yk::kMaxGridF64);
+                        "%d at this precision): raise delta or tol, or lower the period",
+                        (long long)nmin, nmax);
         if (!smooth5(n)) continue;
         T = 0;
         if (o->tile > 0) {
             if (n % o->tile == 0 && o->tile >= w && n >= 2 * o->tile) T = o->tile;
         } else {
-            for (int t = 64; t >= w; --t)
+            const int tmax = o->precision == YK_FP32C ? 32 : 64;
+            for (int t = tmax; t >= w; --t)
                 if (n % t == 0 && n >= 2 * t) {
                     T = t;
                     break;
@@ -554,8 +568,9 @@ static int64_t predicted_bytes(const yk_plan_s *p, int64_t n_src, int64_t n_trg)
 {
     if (p->zero) return (int64_t)sizeof(int);
     const int64_t n = p->n, M = p->M, nt2 = (int64_t)p->nt * p->nt;
-    int64_t b = 8 * n * n + 16 * (M + 1) * n + 8 * (M + 1) * (2 * M + 1) + 16 * n + 4 * (n / 2) +
-                4 * n + 4 * (6 * nt2 + 2) + 4;
+    const int64_t r = p->precision == YK_FP32C ? 4 : 8; /* bytes of the real type */
+    int64_t b = r * n * n + 2 * r * (M + 1) * n + r * (M + 1) * (2 * M + 1) + 2 * r * n +
+                4 * (n / 2) + 4 * n + 4 * (7 * nt2 + 2) + 4;
     b += n_src * (8 + 16 + 4 * (16 + 4)) + n_trg * (16 + 4 + 16);
     return b;
 }
@@ -681,8 +696,12 @@ yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const doub
     stage_begin(p, YK_STAGE_BIN_SRC);
     YK_CU(yk::launch_bin_sources(g, n_src, dx, dy, P<double2>(p->src_t), P<int>(p->tile_cnt),
                                  P<int>(p->tile_ptr), P<int>(p->tile_cur), P<double2>(p->ent_t),
-                                 P<int>(p->ent_j), P<int>(p->err), p->stream),
+                                 P<int>(p->ent_j), P<int>(p->err), p->stream,
+                                 p->precision == YK_FP32C),
           "bin sources");
+    YK_CU(yk::launch_tile_order(P<int>(p->tile_ptr), p->nt * p->nt, P<int>(p->tile_order),
+                                p->stream),
+          "tile order");
     stage_end(p, YK_STAGE_BIN_SRC);
     /* the staging buffers are reused for the targets: order the copies after the source bins */
     const double *tx = nullptr, *ty = nullptr;
@@ -691,7 +710,8 @@ yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const doub
     stage_begin(p, YK_STAGE_BIN_TRG);
     YK_CU(yk::launch_bin_targets(g, n_trg, tx, ty, P<double2>(p->trg_tmp), P<int>(p->trg_cnt),
                                  P<int>(p->trg_ptr), P<int>(p->trg_cur), P<double2>(p->trg_t),
-                                 P<int>(p->trg_idx), P<int>(p->err), p->stream),
+                                 P<int>(p->trg_idx), P<int>(p->err), p->stream,
+                                 p->precision == YK_FP32C),
           "bin targets");
     stage_end(p, YK_STAGE_BIN_TRG);
 #undef YK_TRY
@@ -727,31 +747,65 @@ yk_status yk_eval_longrange(yk_plan_t p, const double *density, double *u)
             if ((s = to_device(p, density, p->n_src, p->stage_w, &dd, "density")) != YK_OK) return s;
             const yk::Geom g = geom_of(p);
             const int n = (int)p->n, M = (int)p->M;
-            stage_begin(p, YK_STAGE_SPREAD);
-            YK_CU(yk::launch_spread(g, P<int>(p->tile_ptr), P<double2>(p->ent_t), P<int>(p->ent_j),
-                                    P<double>(p->w_src), dd, P<double>(p->grid), p->stream),
-                  "spread");
-            stage_end(p, YK_STAGE_SPREAD);
-            stage_begin(p, YK_STAGE_ROW_FWD);
-            YK_CU(yk::launch_row_fwd(P<double>(p->grid), P<double2>(p->spec), P<double2>(p->tw),
-                                     P<int>(p->perm_h), p->st_half, n, M, p->stream),
-                  "row FFT");
-            stage_end(p, YK_STAGE_ROW_FWD);
-            stage_begin(p, YK_STAGE_COLUMNS);
-            YK_CU(yk::launch_columns(P<double2>(p->spec), P<double>(p->mult), P<double2>(p->tw),
-                                     P<int>(p->iperm_f), p->st_full, n, M, p->stream),
-                  "column FFT");
-            stage_end(p, YK_STAGE_COLUMNS);
-            stage_begin(p, YK_STAGE_ROW_INV);
-            YK_CU(yk::launch_row_inv(P<double2>(p->spec), P<double>(p->grid), P<double2>(p->tw),
-                                     P<int>(p->perm_h), p->st_half, n, M, p->stream),
-                  "row inverse FFT");
-            stage_end(p, YK_STAGE_ROW_INV);
-            stage_begin(p, YK_STAGE_INTERP);
-            YK_CU(yk::launch_interp(g, P<int>(p->trg_ptr), P<double2>(p->trg_t),
-                                    P<int>(p->trg_idx), P<double>(p->grid), du, p->stream),
-                  "interpolation");
-            stage_end(p, YK_STAGE_INTERP);
+            if (p->precision == YK_FP32C) {
+                stage_begin(p, YK_STAGE_SPREAD);
+                YK_CU(yk::launch_spread32(g, P<int>(p->tile_ptr), P<int>(p->tile_order),
+                                          P<double2>(p->ent_t),
+                                          P<int>(p->ent_j), P<double>(p->w_src), dd,
+                                          P<float>(p->grid), p->stream),
+                      "spread");
+                stage_end(p, YK_STAGE_SPREAD);
+                stage_begin(p, YK_STAGE_ROW_FWD);
+                YK_CU(yk::launch_row_fwd32(P<float>(p->grid), P<float2>(p->spec),
+                                           P<float2>(p->tw), P<int>(p->perm_h), p->st_half, n, M,
+                                           p->stream),
+                      "row FFT");
+                stage_end(p, YK_STAGE_ROW_FWD);
+                stage_begin(p, YK_STAGE_COLUMNS);
+                YK_CU(yk::launch_columns32(P<float2>(p->spec), P<float>(p->mult),
+                                           P<float2>(p->tw), P<int>(p->iperm_f), p->st_full, n, M,
+                                           p->stream),
+                      "column FFT");
+                stage_end(p, YK_STAGE_COLUMNS);
+                stage_begin(p, YK_STAGE_ROW_INV);
+                YK_CU(yk::launch_row_inv32(P<float2>(p->spec), P<float>(p->grid),
+                                           P<float2>(p->tw), P<int>(p->perm_h), p->st_half, n, M,
+                                           p->stream),
+                      "row inverse FFT");
+                stage_end(p, YK_STAGE_ROW_INV);
+                stage_begin(p, YK_STAGE_INTERP);
+                YK_CU(yk::launch_interp32(g, P<int>(p->trg_ptr), P<double2>(p->trg_t),
+                                          P<int>(p->trg_idx), P<float>(p->grid), du, p->stream),
+                      "interpolation");
+                stage_end(p, YK_STAGE_INTERP);
+            } else {
+                stage_begin(p, YK_STAGE_SPREAD);
+                YK_CU(yk::launch_spread(g, P<int>(p->tile_ptr), P<int>(p->tile_order),
+                                        P<double2>(p->ent_t), P<int>(p->ent_j),
+                                        P<double>(p->w_src), dd, P<double>(p->grid), p->stream),
+                      "spread");
+                stage_end(p, YK_STAGE_SPREAD);
+                stage_begin(p, YK_STAGE_ROW_FWD);
+                YK_CU(yk::launch_row_fwd(P<double>(p->grid), P<double2>(p->spec), P<double2>(p->tw),
+                                         P<int>(p->perm_h), p->st_half, n, M, p->stream),
+                      "row FFT");
+                stage_end(p, YK_STAGE_ROW_FWD);
+                stage_begin(p, YK_STAGE_COLUMNS);
+                YK_CU(yk::launch_columns(P<double2>(p->spec), P<double>(p->mult), P<double2>(p->tw),
+                                         P<int>(p->iperm_f), p->st_full, n, M, p->stream),
+                      "column FFT");
+                stage_end(p, YK_STAGE_COLUMNS);
+                stage_begin(p, YK_STAGE_ROW_INV);
+                YK_CU(yk::launch_row_inv(P<double2>(p->spec), P<double>(p->grid), P<double2>(p->tw),
+                                         P<int>(p->perm_h), p->st_half, n, M, p->stream),
+                      "row inverse FFT");
+                stage_end(p, YK_STAGE_ROW_INV);
+                stage_begin(p, YK_STAGE_INTERP);
+                YK_CU(yk::launch_interp(g, P<int>(p->trg_ptr), P<double2>(p->trg_t),
+                                        P<int>(p->trg_idx), P<double>(p->grid), du, p->stream),
+                      "interpolation");
+                stage_end(p, YK_STAGE_INTERP);
+            }
         }
     }
     if (host_u) {

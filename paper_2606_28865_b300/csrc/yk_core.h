@@ -2,8 +2,8 @@
  * yk_core.h — per-item arithmetic of the long-range evaluator, shared by the CUDA kernels.
  *
  * Everything here is a pure function of its arguments (no threads, no shared memory), marked
- * host+device so that the same statements can be exercised on the CPU by the test suite's host
- * emulation of the kernels.  The kernels in yk_kernels.cu decide which thread runs which item.
+ * host+device so that host code (plan set-up) can use the same statements.  The kernels in
+ * yk_kernels.cu decide which thread runs which item.
  */
 #ifndef YK_CORE_H
 #define YK_CORE_H
@@ -51,6 +51,15 @@ template <typename R> YK_HD R es_window(R z, R beta, R c /* = 4/w^2 */)
 {
     R s = (R)1 - c * z * z;
     return s >= (R)0 ? exp(beta * (sqrt(s) - (R)1)) : (R)0;
+}
+
+/* the same window with the exponent written as -beta c z^2 / (1 + sqrt(1 - c z^2)): no
+ * cancellation in sqrt(.) - 1, so in FP32 the relative error of phi stays a few ulp instead of
+ * beta ulp (used by the FP32 path, where it decides whether 1e-6 is reachable) */
+template <typename R> YK_HD R es_window_stable(R z, R beta, R c)
+{
+    const R u = c * z * z;
+    return u <= (R)1 ? exp(-beta * u / ((R)1 + sqrt((R)1 - u))) : (R)0;
 }
 
 /* first tap l0 = ceil(t - w/2) of a point at grid coordinate t; taps l0 .. l0+w-1, and the

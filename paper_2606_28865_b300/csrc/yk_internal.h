@@ -29,16 +29,23 @@ struct Geom {
 /* device error bits (sticky in the plan) */
 enum { ERR_POINT_OUTSIDE = 1 };
 
-/* kernel launchers (yk_kernels.cu); all enqueue on `st` and return the launch status */
+/* kernel launchers (yk_kernels.cu); all enqueue on `st` and return the launch status.
+ * f32 selects the FP32C entry layout (first tap + FP32 offset) for the binned points. */
 cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
                                double2 *src_t, int *tile_cnt, int *tile_ptr, int *tile_cur,
-                               double2 *ent_t, int *ent_j, int *err, cudaStream_t st);
+                               double2 *ent_t, int *ent_j, int *err, cudaStream_t st, bool f32);
 cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, const double *yt,
                                double2 *trg_tmp, int *cnt, int *ptr, int *cur, double2 *trg_t,
-                               int *trg_idx, int *err, cudaStream_t st);
-cudaError_t launch_spread(const Geom &g, const int *tile_ptr, const double2 *ent_t,
-                          const int *ent_j, const double *wq, const double *dens, double *grid,
-                          cudaStream_t st);
+                               int *trg_idx, int *err, cudaStream_t st, bool f32);
+/* heavy-first tile order (order[i] = tile the i-th spread CTA takes); order may be NULL in the
+ * spread launchers, meaning tile i for CTA i */
+cudaError_t launch_tile_order(const int *tile_ptr, int ntiles, int *order, cudaStream_t st);
+cudaError_t launch_spread(const Geom &g, const int *tile_ptr, const int *order,
+                          const double2 *ent_t, const int *ent_j, const double *wq,
+                          const double *dens, double *grid, cudaStream_t st);
+cudaError_t launch_spread32(const Geom &g, const int *tile_ptr, const int *order,
+                            const double2 *ent_t, const int *ent_j, const double *wq,
+                            const double *dens, float *grid, cudaStream_t st);
 cudaError_t launch_row_fwd(const double *grid, double2 *spec, const double2 *tw, const int *perm_h,
                            const FftStages &sth, int n, int M, cudaStream_t st);
 cudaError_t launch_columns(double2 *spec, const double *mult, const double2 *tw,
@@ -47,13 +54,25 @@ cudaError_t launch_columns(double2 *spec, const double *mult, const double2 *tw,
 cudaError_t launch_row_inv(const double2 *spec, double *grid, const double2 *tw,
                            const int *perm_h, const FftStages &sth, int n, int M,
                            cudaStream_t st);
+cudaError_t launch_row_fwd32(const float *grid, float2 *spec, const float2 *tw, const int *perm_h,
+                             const FftStages &sth, int n, int M, cudaStream_t st);
+cudaError_t launch_columns32(float2 *spec, const float *mult, const float2 *tw,
+                             const int *iperm_f, const FftStages &stf, int n, int M,
+                             cudaStream_t st);
+cudaError_t launch_row_inv32(const float2 *spec, float *grid, const float2 *tw, const int *perm_h,
+                             const FftStages &sth, int n, int M, cudaStream_t st);
 cudaError_t launch_interp(const Geom &g, const int *trg_ptr, const double2 *trg_t,
                           const int *trg_idx, const double *grid, double *u, cudaStream_t st);
+cudaError_t launch_interp32(const Geom &g, const int *trg_ptr, const double2 *trg_t,
+                            const int *trg_idx, const float *grid, double *u, cudaStream_t st);
 cudaError_t launch_build_mult(double *mult, const double *dfac, int M, double alpha, double delta,
                               double dk, double period, cudaStream_t st);
+cudaError_t launch_build_mult32(float *mult, const double *dfac, int M, double alpha,
+                                double delta, double dk, double period, cudaStream_t st);
 
-/* largest grid the column pass supports (one column of n complex doubles in shared memory) */
+/* largest grid the column pass supports (one column of n complex values in shared memory) */
 constexpr int kMaxGridF64 = 14400;
+constexpr int kMaxGridF32 = 28800;
 
 } /* namespace yk */
 
@@ -81,13 +100,15 @@ struct yk_plan_s {
     yk::FftStages st_half, st_full;
 
     /* plan-time device buffers */
-    DevBuf grid;     /* double[n*n]: spread output, then inverse-FFT output */
-    DevBuf spec;     /* double2[(M+1)*n]: half spectrum, transposed: spec[kx*n + y] */
-    DevBuf mult;     /* double[(M+1)*(2M+1)]: multiplier incl. window deconvolution */
-    DevBuf tw;       /* double2[n]: exp(-2 pi i j / n) */
+    /* real type R = double (FP64) or float (FP32C) */
+    DevBuf grid;     /* R[n*n]: spread output, then inverse-FFT output */
+    DevBuf spec;     /* R2[(M+1)*n]: half spectrum, transposed: spec[kx*n + y] */
+    DevBuf mult;     /* R[(M+1)*(2M+1)]: multiplier incl. window deconvolution */
+    DevBuf tw;       /* R2[n]: exp(-2 pi i j / n) */
     DevBuf perm_h;   /* int[n/2]: DIF position of frequency m (half-length transform) */
     DevBuf iperm_f;  /* int[n]: frequency held at DIF position i (full-length transform) */
     DevBuf tile_cnt, tile_ptr, tile_cur; /* int[nt^2], int[nt^2+1], int[nt^2] (sources) */
+    DevBuf tile_order; /* int[nt^2]: heavy-first processing order of the source tiles */
     DevBuf trg_cnt, trg_ptr, trg_cur;    /* same for targets */
     DevBuf err;      /* int: device error bits */
 
@@ -96,9 +117,10 @@ struct yk_plan_s {
     int64_t n_src, n_trg;
     DevBuf w_src;    /* double[n_src]: quadrature weights, original order */
     DevBuf src_t;    /* double2[n_src]: grid coordinates of the sources, original order */
-    DevBuf ent_t;    /* double2[<= 4 n_src]: (source, tile) entries grouped by tile */
+    DevBuf ent_t;    /* 16 B x (<= 4 n_src): (source, tile) entries grouped by tile; FP64: grid
+                        coordinate (double2); FP32C: first tap and FP32 offset (int2 + float2) */
     DevBuf ent_j;    /* int[<= 4 n_src]: source index of each entry */
-    DevBuf trg_t;    /* double2[n_trg]: targets grouped by tile (grid coordinates) */
+    DevBuf trg_t;    /* 16 B x n_trg: targets grouped by tile (same two layouts as ent_t) */
     DevBuf trg_idx;  /* int[n_trg]: original index of each grouped target */
     DevBuf trg_tmp;  /* double2[n_trg]: grid coordinates in original order */
     /* staging copies of host arrays */

@@ -201,6 +201,7 @@ extern "C" YK_API yk_status yk_eval_longrange_static(double alpha, const yk_opts
     yk_opts_default(&def);
     if (!o) o = &def;
     if (o->alloc || o->free) return static_fail(YK_ERR_ARG, "allocator callbacks are not used here");
+    if (o->precision != YK_FP64) return static_fail(YK_ERR_UNSUPPORTED, "FP64 only");
     if (n_src < 0 || n_trg < 0) return static_fail(YK_ERR_ARG, "negative point count");
     if (n_src > (1ll << 28) || n_trg > (1ll << 30))
         return static_fail(YK_ERR_UNSUPPORTED, "too many points for 32-bit entry indices");
@@ -292,13 +293,13 @@ extern "C" YK_API yk_status yk_eval_longrange_static(double alpha, const yk_opts
     if (e == cudaSuccess)
         e = yk::launch_bin_sources(g, n_src, xs, ys, (double2 *)at(o_srct), (int *)at(o_tcnt),
                                    (int *)at(o_tptr), (int *)at(o_tcur), (double2 *)at(o_entt),
-                                   (int *)at(o_entj), (int *)at(o_err), st);
+                                   (int *)at(o_entj), (int *)at(o_err), st, false);
     if (e == cudaSuccess)
         e = yk::launch_bin_targets(g, n_trg, xt, yt, (double2 *)at(o_tmp), (int *)at(o_gcnt),
                                    (int *)at(o_gptr), (int *)at(o_gcur), (double2 *)at(o_trgt),
-                                   (int *)at(o_trgi), (int *)at(o_err), st);
+                                   (int *)at(o_trgi), (int *)at(o_err), st, false);
     if (e == cudaSuccess)
-        e = yk::launch_spread(g, (const int *)at(o_tptr), (const double2 *)at(o_entt),
+        e = yk::launch_spread(g, (const int *)at(o_tptr), nullptr, (const double2 *)at(o_entt),
                               (const int *)at(o_entj), w, density, (double *)at(o_grid), st);
     if (e == cudaSuccess)
         e = yk::launch_row_fwd((const double *)at(o_grid), (double2 *)at(o_spec),

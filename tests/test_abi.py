@@ -91,3 +91,15 @@ def test_predicted_memory_grows_with_points():
     b = yk.plan_params(10.0, 2000, 1000, delta=0.0167)["device_bytes"]
     c = yk.plan_params(10.0, 1000, 2000, delta=0.0167)["device_bytes"]
     assert b > a and c > a
+
+
+def test_fp32c_parameters():
+    w = W.config_small()
+    info = yk.plan_params(10.0, w.n_src, w.n_trg, h_vol=w.h_vol, tol=1e-6,
+                          precision=yk.YK_FP32C)
+    eps = 1e-6 / 4
+    assert info["precision"] == yk.YK_FP32C and info["w"] == math.ceil(math.log10(1 / eps)) + 1
+    f64 = yk.plan_params(10.0, w.n_src, w.n_trg, h_vol=w.h_vol, tol=1e-6)
+    assert f64["n_grid"] == info["n_grid"] and f64["device_bytes"] > info["device_bytes"]
+    with pytest.raises(yk.YkError):
+        yk.plan_params(10.0, delta=0.01, precision=7)
