@@ -51,6 +51,10 @@ def parse():
                     help="targets per alpha in each reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32c", action="store_true", help="skip the FP32C measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch section")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
+    ap.add_argument("--serve-requests", type=int, default=4000,
+                    help="requests of the Rothe stream (Poisson, 2000 req/s)")
     return ap.parse_args()
 
 
@@ -253,6 +257,90 @@ def run_reference(args, rank, world, pg):
 
 
 # ---------------------------------------------------------------------------------------------
+def batch_section(yk, torch, rank):
+    """256 uneven instances (points log-uniform in [1e3, 2e5], random starfish, alpha log-uniform
+    in [1, 300]): plain per-call evaluation vs one persistent launch replayed from a graph."""
+    works = W.batch_instances(256, seed=rank)
+    dev = torch.device("cuda")
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    bufs = [(t(wk.xs), t(wk.ys), t(wk.w), t(wk.xt), t(wk.yt), t(wk.density),
+             torch.empty(wk.n_trg, dtype=torch.float64, device=dev)) for wk in works]
+    pts = sum(wk.n_src + wk.n_trg for wk in works)
+    stream = torch.cuda.current_stream()
+    out = {"instances": len(works), "points": pts,
+           "workload": "256 random starfish instances, points log-uniform in [1e3, 2e5], "
+                       "alpha log-uniform in [1, 300], targets at the volume nodes"}
+    for prec, tol, key in ((yk.YK_FP32C, 1e-6, "fp32c"), (yk.YK_FP64, 1e-10, "fp64")):
+        # autotune the tile edge on eight instances spread over the size range; plans of the
+        # same (window, grid band, density band) then take the tuned edge
+        t_tune = time.perf_counter()
+        order = np.argsort([wk.n_src for wk in works])
+        for k in order[:: max(1, len(works) // 8)]:
+            wk, bf = works[k], bufs[k]
+            yk.autotune(wk.alpha, bf[0], bf[1], bf[2], bf[5], bf[3], bf[4], tol=tol,
+                        precision=prec, h_vol=wk.h_vol, box=wk.box)
+        t_tune = time.perf_counter() - t_tune
+        plans = []
+        for wk, bf in zip(works, bufs):
+            p = yk.Plan(wk.alpha, tol=tol, precision=prec, h_vol=wk.h_vol, box=wk.box,
+                        use_tuned=True, n_src_hint=wk.n_src)
+            p.set_points(*bf[:5])
+            plans.append(p)
+        torch.cuda.synchronize()
+
+        def per_call():
+            for p, bf in zip(plans, bufs):
+                p.eval(bf[5], out=bf[6])
+
+        reps = 3
+        per_call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            per_call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_call = e0.elapsed_time(e1) / reps
+        b = yk.Batch(plans, use_graph=True)
+        dens = [bf[5] for bf in bufs]
+        outs = [bf[6] for bf in bufs]
+        b.run(dens, outs)
+        b.sync()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            b.run(dens, outs)
+        b.sync()
+        ms_batch = (time.perf_counter() - t0) / reps * 1e3
+        out[key] = {"per_call_ms": ms_call, "per_call_points_per_s": pts / (ms_call * 1e-3),
+                    "batch_ms": ms_batch, "batch_points_per_s": pts / (ms_batch * 1e-3),
+                    "tol": tol, "autotune_s": t_tune}
+        b.close()
+        for p in plans:
+            p.close()
+    return out
+
+
+def serving_section(yk, n_req):
+    """Rothe stream: 64 simulations (points log-uniform in [1e3, 1e6], dt log-uniform in
+    [1e-4, 1e-1]), Poisson arrivals at 2000 req/s: FP32C continuous batching vs the plain FP64
+    per-call form on the same arrivals."""
+    from paper_2606_28865_b300.serving import RotheServer
+    geoms, reqs = W.rothe_stream(n_req=n_req, rate=2000.0, n_geom=64, seed=0)
+    out = {"workload": f"{n_req} requests, Poisson 2000 req/s, 64 resident geometries",
+           "points_total": int(sum(geoms[r["geom"]].n_src + geoms[r["geom"]].n_trg
+                                   for r in reqs))}
+    for key, prec, batch in (("fp32c_batched", yk.YK_FP32C, True),
+                             ("fp64_per_call", yk.YK_FP64, False)):
+        srv = RotheServer(geoms, precision=prec, max_inflight=64, n_streams=4, batch=batch)
+        srv.warm(range(len(geoms)))
+        st = srv.serve(reqs)
+        st.pop("results", None)
+        out[key] = st
+        srv.close()
+    return out
+
+
 def main():
     args = parse()
     rank, world, local, pg = dist_setup(args)
@@ -418,12 +506,15 @@ def main():
         for a in alphas:
             plans32[a].close()
 
+    batch = None if args.no_batch else batch_section(yk, torch, rank)
+    serving = None if args.no_serving else serving_section(yk, args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(alphas, args.cpu_targets)
 
     launches_per_eval = 5
-    launches_per_set = 6
+    launches_per_set = 7  # count, scan, fill for sources and for targets, tile order
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
@@ -442,6 +533,7 @@ def main():
         "e2e": {"value": pts_step * world / e2e_s, "unit": "points/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * len(alphas) * (launches_per_eval + launches_per_set),
+        "gpu_launches_what": "library kernels in the timed FP64 region (11 + tile order per alpha)",
         "clocks": clk,
         "stage_ms": {str(a): stage_ms[a] for a in alphas},
         "eval_only": {"ms_per_step": eval_only_ms,
@@ -449,6 +541,8 @@ def main():
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "what": "one yk_eval_longrange on a resident layout, all alphas"},
         "fp32c": fp32c,
+        "batch": batch,
+        "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

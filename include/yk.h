@@ -81,6 +81,9 @@ typedef struct {
     void *(*alloc)(size_t bytes, void *stream, void *ctx);
     void (*free)(void *ptr, void *stream, void *ctx);
     void *alloc_ctx;
+    int use_tuned;      /* nonzero (and tile == 0): take the tile edge yk_autotune recorded for
+                           this precision, window, grid size and n_src_hint */
+    int64_t n_src_hint; /* expected number of sources (selects the autotuner's density band) */
 } yk_opts;
 
 /* Parameters the plan chose (all derived from alpha, tol, delta and the box). */
@@ -176,6 +179,30 @@ YK_API yk_status yk_destroy(yk_plan_t p);
 YK_API const char *yk_last_error(void);
 
 /*
+ * Autotuner.  yk_autotune times every admissible tile edge for (alpha, o) on the caller's points
+ * (all arrays device memory; density n_src values) and records the fastest in a process-wide
+ * cache used by plans created with o->use_tuned.  The paper has no counterpart.
+ */
+#define YK_TUNE_MAX 16
+typedef struct {
+    int n_tried;              /* candidates timed */
+    int tile[YK_TUNE_MAX];    /* candidate tile edges */
+    double ms[YK_TUNE_MAX];   /* device ms of one evaluation (sum of its stages) per candidate */
+    int best_tile;
+    double best_ms;
+    int64_t n_grid;
+} yk_tune_result;
+
+YK_API yk_status yk_autotune(double alpha, const yk_opts *o, int64_t n_src, const double *xs,
+                             const double *ys, const double *w, const double *density,
+                             int64_t n_trg, const double *xt, const double *yt,
+                             yk_tune_result *res);
+/* write / read / clear the tuned-tile cache (a small text file: key columns and the tile) */
+YK_API yk_status yk_tune_cache_save(const char *path);
+YK_API yk_status yk_tune_cache_load(const char *path);
+YK_API void yk_tune_cache_clear(void);
+
+/*
  * yk_fma_peak: measured FMA throughput of the current device in TFLOP/s (2 flops per FMA) for
  * precision YK_FP64 or YK_FP32C (FP32), from independent FMA chains on every SM.  A diagnostic
  * used to report ALU-bound kernels against a measured peak; the paper has no counterpart.
@@ -207,10 +234,56 @@ YK_API yk_status yk_eval_longrange_static(double alpha, const yk_opts *o, int64_
                                           size_t msg_len);
 
 /*
- * yk_batch_eval: evaluate n plans (each with points already set) with their densities in one
- * submission; density[i] and u[i] follow the rules of yk_eval_longrange for plans[i].
+ * Batches: many evaluations (uneven sizes, different alpha, FP64 and FP32C mixed) in one
+ * persistent launch per precision.  The plans' stages become one work list (all spreads, then all
+ * row FFTs, columns, inverse rows and interpolations); CTAs pull items with an atomic counter, and
+ * an item waits for the previous stage of its own instance with a bounded poll, so a stall is
+ * reported as YK_ERR_TIMEOUT instead of hanging.  The launch is captured once into a CUDA graph
+ * and replayed by later yk_batch_run calls.  Not in the paper: a serving-side layer over the same
+ * stages (Section 5.2).
  */
-YK_API yk_status yk_batch_eval(yk_plan_t *plans, const double *const *density, double *const *u, int n);
+typedef struct yk_batch_s *yk_batch_t;
+
+typedef struct {
+    void *stream;       /* cudaStream_t of the batch; NULL = stream of plans[0], and if that is
+                           the legacy default stream, a blocking stream owned by the batch */
+    int use_graph;      /* nonzero (default): capture the launch once, replay it afterwards */
+    int64_t spin_limit; /* polls (about 0.2 us apart) an item may wait for its predecessors before
+                           the batch fails with YK_ERR_TIMEOUT; 0 = 5e6 (about a second) */
+    int inject_stall;   /* test hook: one dependency is never met, so a wait must time out */
+} yk_batch_opts;
+
+YK_API void yk_batch_opts_default(yk_batch_opts *o);
+
+/*
+ * yk_batch_create: a batch over n plans whose points are set (yk_set_points).  The plans stay
+ * owned by the caller and must outlive the batch; calling yk_set_points on one of them later makes
+ * the next yk_batch_run rebuild the work list.  YK_ERR_STATE if a plan has no points.
+ */
+YK_API yk_status yk_batch_create(yk_plan_t *plans, int n, const yk_batch_opts *o,
+                                 yk_batch_t *out);
+
+/*
+ * yk_batch_set_plans: point an existing batch at another set of plans (same rules as
+ * yk_batch_create), reusing its device buffers; waits for the batch's previous run.
+ */
+YK_API yk_status yk_batch_set_plans(yk_batch_t b, yk_plan_t *plans, int n);
+
+/*
+ * yk_batch_run: enqueue one evaluation of every plan on the batch stream: u[i] (n_trg of plan i,
+ * written) from density[i] (n_src of plan i).  All arrays must be device memory ready on the
+ * batch stream; returns after enqueueing.  Instances may not share output arrays.
+ */
+YK_API yk_status yk_batch_run(yk_batch_t b, const double *const *density, double *const *u);
+
+/* Wait for the batch stream; YK_ERR_TIMEOUT if a bounded wait ran out during the last run. */
+YK_API yk_status yk_batch_sync(yk_batch_t b);
+
+YK_API yk_status yk_batch_destroy(yk_batch_t b);
+
+/* yk_batch_eval: create (without graph), run, sync and destroy in one call. */
+YK_API yk_status yk_batch_eval(yk_plan_t *plans, const double *const *density, double *const *u,
+                               int n);
 
 #ifdef __cplusplus
 }

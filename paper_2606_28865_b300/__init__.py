@@ -46,8 +46,9 @@ class Opts(ctypes.Structure):
                 ("eps_hist", ctypes.c_double), ("box", ctypes.c_double * 4),
                 ("kmax", ctypes.c_double), ("kmax_rule", ctypes.c_int),
                 ("period", ctypes.c_double), ("tile", ctypes.c_int),
-                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", _ALLOC), ("free", _FREE),
-                ("alloc_ctx", ctypes.c_void_p)]
+                ("profile", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", _ALLOC),
+                ("free", _FREE), ("alloc_ctx", ctypes.c_void_p), ("use_tuned", ctypes.c_int),
+                ("n_src_hint", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -122,7 +123,7 @@ def _len(a) -> int:
 
 def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
               box=(-1.5, 1.5, -1.5, 1.5), kmax=0.0, kmax_rule=0, period=0.0, tile=0,
-              profile=False, stream=None) -> Opts:
+              profile=False, stream=None, use_tuned=False, n_src_hint=0) -> Opts:
     o = Opts()
     _lib.yk_opts_default(ctypes.byref(o))
     o.precision = int(precision)
@@ -138,6 +139,8 @@ def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
     o.tile = int(tile)
     o.profile = 1 if profile else 0
     o.stream = stream
+    o.use_tuned = 1 if use_tuned else 0
+    o.n_src_hint = int(n_src_hint)
     return o
 
 
@@ -237,6 +240,75 @@ class Plan:
         self.close()
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("use_graph", ctypes.c_int),
+                ("spin_limit", ctypes.c_int64), ("inject_stall", ctypes.c_int)]
+
+
+_lib.yk_batch_opts_default.argtypes = [ctypes.POINTER(BatchOpts)]
+_lib.yk_batch_opts_default.restype = None
+_lib.yk_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(BatchOpts),
+                                 ctypes.POINTER(_vp)]
+_lib.yk_batch_run.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]
+_lib.yk_batch_set_plans.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int]
+_lib.yk_batch_sync.argtypes = [_vp]
+_lib.yk_batch_destroy.argtypes = [_vp]
+for _f in ("yk_batch_create", "yk_batch_set_plans", "yk_batch_run", "yk_batch_sync",
+           "yk_batch_destroy"):
+    getattr(_lib, _f).restype = ctypes.c_int
+
+
+class Batch:
+    """Many plans evaluated in one persistent launch (captured once in a CUDA graph)."""
+
+    def __init__(self, plans, use_graph=True, spin_limit=0, inject_stall=False, stream=None):
+        o = BatchOpts()
+        _lib.yk_batch_opts_default(ctypes.byref(o))
+        if stream is None:
+            stream = _current_stream()
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        o.stream = stream
+        o.use_graph = 1 if use_graph else 0
+        o.spin_limit = int(spin_limit)
+        o.inject_stall = 1 if inject_stall else 0
+        self.plans = list(plans)
+        hp = (_vp * len(self.plans))(*[p.handle for p in self.plans])
+        h = _vp()
+        _check(_lib.yk_batch_create(hp, len(self.plans), ctypes.byref(o), ctypes.byref(h)),
+               "yk_batch_create")
+        self._h = h
+
+    def set_plans(self, plans):
+        """Re-target the batch at other plans (its device buffers are reused)."""
+        self.plans = list(plans)
+        hp = (_vp * len(self.plans))(*[p.handle for p in self.plans])
+        _check(_lib.yk_batch_set_plans(self._h, hp, len(self.plans)), "yk_batch_set_plans")
+
+    def run(self, densities, outs):
+        n = len(self.plans)
+        keep = []
+        dp = (_vp * n)(*[_ptr(d, keep) for d in densities])
+        up = (_vp * n)(*[_ptr(u, keep) for u in outs])
+        _check(_lib.yk_batch_run(self._h, dp, up), "yk_batch_run")
+        self._keep = keep
+        return outs
+
+    def sync(self):
+        _check(_lib.yk_batch_sync(self._h), "yk_batch_sync")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.yk_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def batch_eval(plans, densities, outs):
     """Evaluate several plans in one submission (each plan's points already set)."""
     n = len(plans)
@@ -279,6 +351,47 @@ def eval_longrange_static(alpha, xs, ys, w, density, xt, yt, out, stream=None, *
     if st != YK_OK:
         raise YkError(st, "yk_eval_longrange_static", msg.value.decode(errors="replace"))
     return out
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("n_tried", ctypes.c_int), ("tile", ctypes.c_int * 16),
+                ("ms", ctypes.c_double * 16), ("best_tile", ctypes.c_int),
+                ("best_ms", ctypes.c_double), ("n_grid", ctypes.c_int64)]
+
+
+_lib.yk_autotune.argtypes = [_d, ctypes.POINTER(Opts), _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp,
+                             ctypes.POINTER(TuneResult)]
+_lib.yk_autotune.restype = ctypes.c_int
+_lib.yk_tune_cache_save.argtypes = [ctypes.c_char_p]
+_lib.yk_tune_cache_save.restype = ctypes.c_int
+_lib.yk_tune_cache_load.argtypes = [ctypes.c_char_p]
+_lib.yk_tune_cache_load.restype = ctypes.c_int
+_lib.yk_tune_cache_clear.restype = None
+
+
+def autotune(alpha, xs, ys, w, density, xt, yt, **opts) -> dict:
+    """Time every admissible tile edge on these points; the winner is cached for plans created
+    with use_tuned=True.  Arrays must be device tensors."""
+    o = make_opts(stream=_current_stream(), **opts)
+    keep = []
+    r = TuneResult()
+    _check(_lib.yk_autotune(float(alpha), ctypes.byref(o), _len(xs), _ptr(xs, keep),
+                            _ptr(ys, keep), _ptr(w, keep), _ptr(density, keep), _len(xt),
+                            _ptr(xt, keep), _ptr(yt, keep), ctypes.byref(r)), "yk_autotune")
+    return {"best_tile": r.best_tile, "best_ms": r.best_ms, "n_grid": r.n_grid,
+            "tried": {r.tile[k]: r.ms[k] for k in range(r.n_tried)}}
+
+
+def tune_cache_save(path: str):
+    _check(_lib.yk_tune_cache_save(path.encode()), "yk_tune_cache_save")
+
+
+def tune_cache_load(path: str):
+    _check(_lib.yk_tune_cache_load(path.encode()), "yk_tune_cache_load")
+
+
+def tune_cache_clear():
+    _lib.yk_tune_cache_clear()
 
 
 def loaded_library_path() -> str:

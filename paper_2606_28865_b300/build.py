@@ -6,8 +6,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libyk.so")
-SOURCES = ["yk_api.cu", "yk_kernels.cu", "yk_peak.cu", "yk_static.cu"]
-HEADERS = ["yk_core.h", "yk_internal.h"]
+SOURCES = ["yk_api.cu", "yk_kernels.cu", "yk_batch.cu", "yk_peak.cu", "yk_static.cu", "yk_tune.cu"]
+HEADERS = ["yk_core.h", "yk_internal.h", "yk_stages.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

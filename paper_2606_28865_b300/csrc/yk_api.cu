@@ -461,6 +461,44 @@ yk_status plan_tables(yk_plan_t p)
 } /* namespace */
 
 /* ------------------------------------------------------------------------------------------ */
+/* evaluation descriptor for the batch kernel                                                  */
+
+void yk_set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
+{
+    yk_plan_s *p = const_cast<yk_plan_s *>(pc);
+    if (p->zero || p->n_src == 0 || p->n_trg == 0) return false;
+    std::memset((void *)d, 0, sizeof *d);
+    d->g = geom_of(p);
+    d->sth = p->st_half;
+    d->stf = p->st_full;
+    d->n = (int)p->n;
+    d->M = (int)p->M;
+    d->f32 = p->precision == YK_FP32C;
+    d->rows = yk::rows_per_item(d->n, d->f32);
+    d->tile_ptr = P<int>(p->tile_ptr);
+    d->order = P<int>(p->tile_order);
+    d->ent_t = P<double2>(p->ent_t);
+    d->ent_j = P<int>(p->ent_j);
+    d->wq = P<double>(p->w_src);
+    d->trg_ptr = P<int>(p->trg_ptr);
+    d->trg_t = P<double2>(p->trg_t);
+    d->trg_idx = P<int>(p->trg_idx);
+    d->grid = p->grid.ptr;
+    d->spec = p->spec.ptr;
+    d->mult = p->mult.ptr;
+    d->tw = p->tw.ptr;
+    d->perm_h = P<int>(p->perm_h);
+    d->iperm_f = P<int>(p->iperm_f);
+    for (int s = 0; s < yk::ST_COUNT; ++s) {
+        d->items[s] = yk::stage_items(*d, s);
+        d->smem[s] = yk::stage_smem(*d, s);
+    }
+    return true;
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* ABI                                                                                         */
 
 extern "C" {
@@ -548,10 +586,12 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
             if (n % o->tile == 0 && o->tile >= w && n >= 2 * o->tile) T = o->tile;
         } else {
             const int tmax = o->precision == YK_FP32C ? 32 : 64;
+            const int pref = o->use_tuned ? yk_tuned_tile(o->precision, w, n, o->n_src_hint) : 0;
             for (int t = tmax; t >= w; --t)
                 if (n % t == 0 && n >= 2 * t) {
-                    T = t;
-                    break;
+                    /* largest admissible edge, or the one nearest the tuned edge */
+                    if (!T || (pref > 0 && std::abs(t - pref) < std::abs(T - pref))) T = t;
+                    if (!pref) break;
                 }
         }
         if (T) break;
@@ -665,6 +705,7 @@ yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const doub
         return fail(YK_ERR_ARG, "NULL coordinate or weight array");
     if (p->status != YK_OK) return fail((yk_status)p->status, "plan is in an error state");
     p->points_set = false;
+    ++p->layout_version;
     p->n_src = n_src;
     p->n_trg = n_trg;
     if (p->zero) {
@@ -856,17 +897,6 @@ yk_status yk_destroy(yk_plan_t p)
     cudaStreamSynchronize(p->stream);
     free_all(p);
     delete p;
-    return YK_OK;
-}
-
-yk_status yk_batch_eval(yk_plan_t *plans, const double *const *density, double *const *u, int n)
-{
-    if (n < 0 || (n > 0 && (!plans || !density || !u)))
-        return fail(YK_ERR_ARG, "invalid batch arguments");
-    for (int i = 0; i < n; ++i) {
-        yk_status s = yk_eval_longrange(plans[i], density[i], u[i]);
-        if (s != YK_OK) return s;
-    }
     return YK_OK;
 }
 

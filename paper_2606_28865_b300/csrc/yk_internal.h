@@ -26,8 +26,42 @@ struct Geom {
     double box[4];  /* xmin, xmax, ymin, ymax: points outside are rejected */
 };
 
-/* device error bits (sticky in the plan) */
-enum { ERR_POINT_OUTSIDE = 1 };
+/* device error bits (sticky in the plan / batch) */
+enum { ERR_POINT_OUTSIDE = 1, ERR_WAIT_TIMEOUT = 2 };
+
+/* stages of one evaluation, in order (the batch kernel's per-instance counters follow them) */
+enum { ST_SPREAD = 0, ST_ROW_FWD = 1, ST_COLUMNS = 2, ST_ROW_INV = 3, ST_INTERP = 4, ST_COUNT = 5 };
+
+/* Everything a stage needs about one evaluation: the plan's grid and tables, the resident point
+ * layout and this evaluation's density and output.  Handed by value to the per-stage kernels and
+ * stored in device memory (one per instance) for the batch kernel. */
+struct Inst {
+    Geom g;
+    FftStages sth, stf;       /* n/2-point (rows) and n-point (columns) transforms */
+    int n, M, rows, f32;      /* rows: grid rows per row-FFT work item */
+    const int *tile_ptr;      /* source entries of tile t: [tile_ptr[t], tile_ptr[t+1]) */
+    const int *order;         /* heavy-first tile order, or NULL */
+    const double2 *ent_t;     /* entries (FP64: grid coordinate; FP32C: first tap + offset) */
+    const int *ent_j;         /* source index of each entry */
+    const double *wq;         /* quadrature weights (original order) */
+    const int *trg_ptr;       /* targets of tile t: [trg_ptr[t], trg_ptr[t+1]) */
+    const double2 *trg_t;     /* targets grouped by tile */
+    const int *trg_idx;       /* original index of each grouped target */
+    const double *dens;       /* density of this evaluation (n_src, device) */
+    double *u;                /* output (n_trg, device) */
+    void *grid;               /* R[n*n] */
+    void *spec;               /* R2[(M+1)*n] */
+    const void *mult;         /* R[(M+1)*(2M+1)] */
+    const void *tw;           /* R2[n] */
+    const int *perm_h, *iperm_f;
+    int items[ST_COUNT];      /* work items of each stage */
+    int smem[ST_COUNT];       /* dynamic shared memory of each stage (bytes) */
+};
+
+/* shared-memory and work-item sizes of each stage (host side of the kernels' layouts) */
+int stage_smem(const Inst &d, int stage);
+int stage_items(const Inst &d, int stage);
+int rows_per_item(int n, bool f32);
 
 /* kernel launchers (yk_kernels.cu); all enqueue on `st` and return the launch status.
  * f32 selects the FP32C entry layout (first tap + FP32 offset) for the binned points. */
@@ -114,6 +148,7 @@ struct yk_plan_s {
 
     /* resident point layout (grown on demand) */
     bool points_set;
+    int64_t layout_version; /* incremented by every yk_set_points */
     int64_t n_src, n_trg;
     DevBuf w_src;    /* double[n_src]: quadrature weights, original order */
     DevBuf src_t;    /* double2[n_src]: grid coordinates of the sources, original order */
@@ -134,5 +169,16 @@ struct yk_plan_s {
     cudaEvent_t events[kEventRing][2 * YK_NUM_STAGES];
     int64_t stage_runs[YK_NUM_STAGES]; /* runs recorded since the last yk_stage_times */
 };
+
+
+/* describe one evaluation of plan p (density and output filled in later); false when the plan
+ * needs no kernels (k_max = 0, no sources or no targets: u = 0) */
+bool yk_fill_inst(const yk_plan_s *p, yk::Inst *d);
+
+/* tile edge recorded by the autotuner for this key (0: none) */
+int yk_tuned_tile(int precision, int w, int64_t n, int64_t n_src_hint);
+
+/* set the calling thread's message returned by yk_last_error */
+void yk_set_last_error(const char *msg);
 
 #endif /* YK_INTERNAL_H */

@@ -1,5 +1,7 @@
 /*
- * yk_kernels.cu — sm_103a kernels of the long-range evaluator (FP64 and FP32C paths).
+ * yk_kernels.cu — sm_103a kernels of the long-range evaluator (FP64 and FP32C paths): the binning
+ * kernels and one kernel per evaluation stage, each a thin wrapper (one CTA per work item) around
+ * the stage bodies in yk_stages.cuh.
  *
  *   bin        sources -> (source, tile) entries for every tile a source's w x w window touches;
  *              targets -> the tile of their grid cell (counting sort: count, scan, fill)
@@ -18,46 +20,18 @@
  */
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
-#include "yk_internal.h"
+#include "yk_stages.cuh"
 
 namespace yk {
 
 namespace {
 
-template <typename R> struct V2;
-template <> struct V2<double> {
-    using T = double2;
-    static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
-};
-template <> struct V2<float> {
-    using T = float2;
-    static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
-};
-
 /* a point is accepted when it lies in the plan's box (closed) */
 __device__ __forceinline__ bool in_box(const Geom &g, double x, double y)
 {
     return x >= g.box[0] && x <= g.box[1] && y >= g.box[2] && y <= g.box[3];
-}
-
-constexpr double kMagic = 6755399441055744.0; /* 1.5 * 2^52: fma(a, b, kMagic) rounds a*b to an integer */
-
-__device__ __forceinline__ double block_max(double v, double *red)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        v = lane < nw ? red[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) red[0] = v;
-    }
-    __syncthreads();
-    v = red[0];
-    __syncthreads();
-    return v;
 }
 
 /* entry layouts: FP64 keeps the grid coordinate t (double2); FP32C keeps the first tap l0 and
@@ -217,389 +191,42 @@ __global__ void __launch_bounds__(1024) k_tile_order(const int *__restrict__ ptr
 }
 
 /* ----------------------------------------------------------------------------------------- */
-/* spread (type 1)                                                                            */
+/* per-stage kernels: one CTA per work item                                                   */
 
-template <int W>
-__global__ void __launch_bounds__(256)
-    k_spread(const int *__restrict__ tile_ptr, const int *__restrict__ order,
-             const double2 *__restrict__ ent_t, const int *__restrict__ ent_j,
-             const double *__restrict__ wq, const double *__restrict__ dens, Geom g,
-             double *__restrict__ grid)
+template <int W> __global__ void __launch_bounds__(256) k_spread(Inst d)
 {
-    extern __shared__ unsigned long long acc[]; /* T x T fixed-point accumulators */
-    __shared__ double red[32];
-    __shared__ int s_k;
-    const int T = g.T, tile = order ? order[blockIdx.x] : blockIdx.x;
-    const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
-    const int X0 = txi * T, Y0 = tyi * T;
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) acc[i] = 0ull;
-    const int beg = tile_ptr[tile], end = tile_ptr[tile + 1];
-
-    /* per-tile scale 2^k: every product |q| phi phi <= max|q| stays below 2^51 (so one fma
-     * with 1.5 * 2^52 rounds it to an integer) and the sum of all of them below 2^62 */
-    double mq = 0.0;
-    for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
-        const int j = ent_j[e];
-        mq = fmax(mq, fabs(wq[j] * dens[j]));
-    }
-    mq = block_max(mq, red);
-    if (threadIdx.x == 0) {
-        int e2 = 0;
-        if (mq > 0.0) frexp(mq, &e2);
-        const int cbits = 32 - __clz(end - beg);
-        s_k = min(51, 62 - cbits) - e2;
-    }
-    __syncthreads();
-    const int kexp = s_k;
-    const long long magic_bits = __double_as_longlong(kMagic);
-
-    if (mq > 0.0) {
-        for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
-            const double2 t = ent_t[e];
-            const int j = ent_j[e];
-            const double qs = ldexp(wq[j] * dens[j], kexp);
-            const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
-            double fx[W], fy[W];
-#pragma unroll
-            for (int a = 0; a < W; ++a) {
-                fx[a] = es_window<double>((double)(lx + a) - t.x, g.beta, g.c);
-                fy[a] = es_window<double>((double)(ly + a) - t.y, g.beta, g.c);
-            }
-            int dx0 = (lx - X0) % g.n;
-            if (dx0 < 0) dx0 += g.n;
-            int dy0 = (ly - Y0) % g.n;
-            if (dy0 < 0) dy0 += g.n;
-#pragma unroll
-            for (int c = 0; c < W; ++c) {
-                int yy = dy0 + c;
-                if (yy >= g.n) yy -= g.n;
-                if (yy < T) {
-                    const double qy = qs * fy[c];
-#pragma unroll
-                    for (int a = 0; a < W; ++a) {
-                        int xx = dx0 + a;
-                        if (xx >= g.n) xx -= g.n;
-                        if (xx < T) {
-                            const long long iv =
-                                __double_as_longlong(fma(qy, fx[a], kMagic)) - magic_bits;
-                            atomicAdd(&acc[yy * T + xx], (unsigned long long)iv);
-                        }
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-        const int r = i / T, c = i - r * T;
-        grid[(size_t)(Y0 + r) * g.n + X0 + c] =
-            mq > 0.0 ? ldexp((double)(long long)acc[i], -kexp) : 0.0;
-    }
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_spread64<W>(d, blockIdx.x, sm);
 }
-
-/* FP32C spread: FP32 window values and products, compensated (two-sum) accumulation.  Each warp
- * owns a private hi + lo copy of the tile; it evaluates the windows of 32 entries (one per lane),
- * then walks them one entry at a time with one lane per tap, so the taps a warp updates together
- * are distinct cells and no atomics are needed.  The warps' copies are combined in a fixed order
- * with two-sum at the end. */
-constexpr int kSpreadWarps = 8;
-
-template <int W>
-__global__ void __launch_bounds__(32 * kSpreadWarps)
-    k_spread32(const int *__restrict__ tile_ptr, const int *__restrict__ order,
-               const int4 *__restrict__ ent, const int *__restrict__ ent_j,
-               const double *__restrict__ wq, const double *__restrict__ dens, Geom g,
-               float *__restrict__ grid)
+template <int W> __global__ void __launch_bounds__(32 * kSpreadWarps) k_spread32(Inst d)
 {
-    extern __shared__ __align__(16) unsigned char sm32[];
-    const int T = g.T, PT = T + 1; /* padded pitch (float2 units) */
-    float2 *acc = reinterpret_cast<float2 *>(sm32);                 /* [warps][T][PT] */
-    float *wbuf = reinterpret_cast<float *>(acc + kSpreadWarps * T * PT); /* [warps][32][2W] */
-    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * 2 * W); /* [warps][32][2] */
-    const int tile = order ? order[blockIdx.x] : blockIdx.x;
-    const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
-    const int X0 = txi * T, Y0 = tyi * T;
-    for (int i = threadIdx.x; i < kSpreadWarps * T * PT; i += blockDim.x)
-        acc[i] = make_float2(0.0f, 0.0f);
-    __syncthreads();
-    const int beg = tile_ptr[tile], end = tile_ptr[tile + 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *mine = acc + warp * T * PT;
-    float *wb = wbuf + warp * 32 * 2 * W;
-    int *ob = obuf + warp * 64;
-    const float beta = (float)g.beta, cw = (float)g.c;
-    for (int b0 = beg + warp * 32; b0 < end; b0 += kSpreadWarps * 32) {
-        const int e = b0 + lane;
-        if (e < end) {
-            const int4 r = ent[e];
-            const int j = ent_j[e];
-            const float q = (float)(wq[j] * dens[j]);
-            const float sx = __int_as_float(r.z), sy = __int_as_float(r.w);
-#pragma unroll
-            for (int a = 0; a < W; ++a) {
-                wb[lane * 2 * W + a] = q * es_window_stable<float>(sy + (float)a, beta, cw);
-                wb[lane * 2 * W + W + a] = es_window_stable<float>(sx + (float)a, beta, cw);
-            }
-            int dx0 = (r.x - X0) % g.n;
-            if (dx0 < 0) dx0 += g.n;
-            int dy0 = (r.y - Y0) % g.n;
-            if (dy0 < 0) dy0 += g.n;
-            ob[2 * lane] = dx0;
-            ob[2 * lane + 1] = dy0;
-        }
-        __syncwarp();
-        const int cnt = min(32, end - b0);
-        for (int k = 0; k < cnt; ++k) {
-            const int dx0 = ob[2 * k], dy0 = ob[2 * k + 1];
-            const float *wk = wb + k * 2 * W;
-#pragma unroll
-            for (int t0 = 0; t0 < W * W; t0 += 32) {
-                const int t = t0 + lane;
-                if (t < W * W) {
-                    const int c = t / W, a = t - c * W;
-                    int yy = dy0 + c;
-                    if (yy >= g.n) yy -= g.n;
-                    int xx = dx0 + a;
-                    if (xx >= g.n) xx -= g.n;
-                    if (yy < T && xx < T) {
-                        const float v = wk[c] * wk[W + a];
-                        float2 cell = mine[yy * PT + xx];
-                        const float s = __fadd_rn(cell.x, v);
-                        const float bp = __fsub_rn(s, cell.x);
-                        const float err =
-                            __fadd_rn(__fsub_rn(cell.x, __fsub_rn(s, bp)), __fsub_rn(v, bp));
-                        cell.x = s;
-                        cell.y = __fadd_rn(cell.y, err);
-                        mine[yy * PT + xx] = cell;
-                    }
-                }
-            }
-            __syncwarp(); /* the next entry may touch the same cells through other lanes */
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-        const int rr = i / T, cc = i - rr * T;
-        float hi = 0.0f, lo = 0.0f;
-        for (int w = 0; w < kSpreadWarps; ++w) {
-            const float2 p = acc[w * T * PT + rr * PT + cc];
-            const float s = __fadd_rn(hi, p.x);
-            const float bp = __fsub_rn(s, hi);
-            lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p.x, bp)), p.y));
-            hi = s;
-        }
-        grid[(size_t)(Y0 + rr) * g.n + X0 + cc] = hi + lo;
-    }
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_spread32<W>(d, blockIdx.x, sm);
 }
-
-/* ----------------------------------------------------------------------------------------- */
-/* FFT passes                                                                                 */
-
-template <typename R, typename TW>
-__device__ __forceinline__ void fft_fwd(cpx<R> *x, const FftStages &st, const TW *tw, int nrows,
-                                        int rowlen)
+template <typename R> __global__ void __launch_bounds__(256) k_row_fwd(Inst d)
 {
-    for (int s = 0; s < st.n; ++s) {
-        const int nb = st.L / st.r[s];
-        for (int i = threadIdx.x; i < nrows * nb; i += blockDim.x) {
-            const int r = i / nb, t = i - r * nb;
-            dif_butterfly<R>(x + (size_t)r * rowlen, st, s, t, tw, 1);
-        }
-        __syncthreads();
-    }
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_row_fwd<R>(d, blockIdx.x, sm);
 }
-
-template <typename R, typename TW>
-__device__ __forceinline__ void fft_inv(cpx<R> *x, const FftStages &st, const TW *tw, int nrows,
-                                        int rowlen)
+template <typename R> __global__ void __launch_bounds__(512) k_columns(Inst d)
 {
-    for (int s = st.n - 1; s >= 0; --s) {
-        const int nb = st.L / st.r[s];
-        for (int i = threadIdx.x; i < nrows * nb; i += blockDim.x) {
-            const int r = i / nb, t = i - r * nb;
-            idif_butterfly<R>(x + (size_t)r * rowlen, st, s, t, tw, 1);
-        }
-        __syncthreads();
-    }
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_columns<R>(d, blockIdx.x, sm);
 }
-
-template <typename R>
-__global__ void __launch_bounds__(256)
-    k_row_fwd(const R *__restrict__ grid, typename V2<R>::T *__restrict__ spec,
-              const typename V2<R>::T *__restrict__ tw, const int *__restrict__ perm_h,
-              FftStages st, int n, int M, int rows)
+template <typename R> __global__ void __launch_bounds__(256) k_row_inv(Inst d)
 {
-    using C2 = typename V2<R>::T;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cpx<R> *x = reinterpret_cast<cpx<R> *>(smraw);
-    const int L = n >> 1;
-    const int y0 = blockIdx.x * rows;
-    const int nr = min(rows, n - y0);
-    for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
-        const int r = i / L, l = i - r * L;
-        const C2 v = reinterpret_cast<const C2 *>(grid + (size_t)(y0 + r) * n)[l];
-        x[i] = mk<R>(v.x, v.y);
-    }
-    __syncthreads();
-    fft_fwd<R>(x, st, tw, nr, L);
-    for (int i = threadIdx.x; i < nr * (M + 1); i += blockDim.x) {
-        const int m = i / nr, r = i - m * nr;
-        const cpx<R> Zm = x[r * L + perm_h[m]];
-        const cpx<R> Zc = x[r * L + perm_h[m == 0 ? 0 : L - m]];
-        const C2 wm = tw[m];
-        const cpx<R> X = r2c_post<R>(Zm, Zc, mk<R>(wm.x, wm.y));
-        spec[(size_t)m * n + y0 + r] = V2<R>::make(X.re, X.im);
-    }
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_row_inv<R>(d, blockIdx.x, sm);
 }
-
-template <typename R>
-__global__ void __launch_bounds__(512)
-    k_columns(typename V2<R>::T *__restrict__ spec, const R *__restrict__ mult,
-              const typename V2<R>::T *__restrict__ tw, const int *__restrict__ iperm_f,
-              FftStages st, int n, int M)
+template <int W> __global__ void __launch_bounds__(256) k_interp(Inst d)
 {
-    using C2 = typename V2<R>::T;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cpx<R> *x = reinterpret_cast<cpx<R> *>(smraw);
-    const int kx = blockIdx.x;
-    C2 *col = spec + (size_t)kx * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const C2 v = col[i];
-        x[i] = mk<R>(v.x, v.y);
-    }
-    __syncthreads();
-    fft_fwd<R>(x, st, tw, 1, n);
-    const R *mrow = mult + (size_t)kx * (2 * M + 1);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int m = iperm_f[i];
-        const int my = m <= (n >> 1) ? m : m - n;
-        if (my >= -M && my <= M) x[i] = scale(x[i], mrow[my + M]);
-        else x[i] = mk<R>((R)0, (R)0);
-    }
-    __syncthreads();
-    fft_inv<R>(x, st, tw, 1, n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = V2<R>::make(x[i].re, x[i].im);
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_interp64<W>(d, blockIdx.x, sm);
 }
-
-template <typename R>
-__global__ void __launch_bounds__(256)
-    k_row_inv(const typename V2<R>::T *__restrict__ spec, R *__restrict__ grid,
-              const typename V2<R>::T *__restrict__ tw, const int *__restrict__ perm_h,
-              FftStages st, int n, int M, int rows)
+template <int W> __global__ void __launch_bounds__(256) k_interp32(Inst d)
 {
-    using C2 = typename V2<R>::T;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cpx<R> *x = reinterpret_cast<cpx<R> *>(smraw);
-    const int L = n >> 1;
-    const int y0 = blockIdx.x * rows;
-    const int nr = min(rows, n - y0);
-    for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
-        const int m = i / nr, r = i - m * nr;
-        const int mc = L - m; /* in (0, L]; X[L] is zero because M < L */
-        C2 a = V2<R>::make((R)0, (R)0), b = V2<R>::make((R)0, (R)0);
-        if (m <= M) a = spec[(size_t)m * n + y0 + r];
-        if (mc <= M) b = spec[(size_t)mc * n + y0 + r];
-        const C2 wm = tw[m];
-        x[r * L + perm_h[m]] = c2r_pre<R>(mk<R>(a.x, a.y), mk<R>(b.x, b.y), mk<R>(wm.x, wm.y));
-    }
-    __syncthreads();
-    fft_inv<R>(x, st, tw, nr, L);
-    for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
-        const int r = i / L, l = i - r * L;
-        reinterpret_cast<C2 *>(grid + (size_t)(y0 + r) * n)[l] = V2<R>::make(x[i].re, x[i].im);
-    }
-}
-
-/* ----------------------------------------------------------------------------------------- */
-/* interpolation (type 2)                                                                     */
-
-template <typename R>
-__device__ __forceinline__ void stage_halo(R *sg, const R *__restrict__ grid, const Geom &g,
-                                           int X0, int Y0, int P)
-{
-    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
-        const int r = i / P, c = i - r * P;
-        int gy = (Y0 + r) % g.n;
-        if (gy < 0) gy += g.n;
-        int gx = (X0 + c) % g.n;
-        if (gx < 0) gx += g.n;
-        sg[i] = grid[(size_t)gy * g.n + gx];
-    }
-}
-
-template <int W>
-__global__ void __launch_bounds__(256)
-    k_interp(const int *__restrict__ trg_ptr, const double2 *__restrict__ trg_t,
-             const int *__restrict__ trg_idx, Geom g, const double *__restrict__ grid,
-             double *__restrict__ u)
-{
-    extern __shared__ double sg[];
-    const int T = g.T, P = T + W, lo = W / 2;
-    const int tile = blockIdx.x;
-    const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
-    const int beg = trg_ptr[tile], end = trg_ptr[tile + 1];
-    if (beg == end) return;
-    const int X0 = txi * T - lo, Y0 = tyi * T - lo;
-    stage_halo<double>(sg, grid, g, X0, Y0, P);
-    __syncthreads();
-    for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
-        const double2 t = trg_t[e];
-        const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
-        double fx[W], fy[W];
-#pragma unroll
-        for (int a = 0; a < W; ++a) {
-            fx[a] = es_window<double>((double)(lx + a) - t.x, g.beta, g.c);
-            fy[a] = es_window<double>((double)(ly + a) - t.y, g.beta, g.c);
-        }
-        const double *base = sg + (ly - Y0) * P + (lx - X0);
-        double acc = 0.0;
-#pragma unroll
-        for (int c = 0; c < W; ++c) {
-            double row = 0.0;
-#pragma unroll
-            for (int a = 0; a < W; ++a) row = fma(fx[a], base[c * P + a], row);
-            acc = fma(fy[c], row, acc);
-        }
-        u[trg_idx[e]] = acc;
-    }
-}
-
-template <int W>
-__global__ void __launch_bounds__(256)
-    k_interp32(const int *__restrict__ trg_ptr, const int4 *__restrict__ trg,
-               const int *__restrict__ trg_idx, Geom g, const float *__restrict__ grid,
-               double *__restrict__ u)
-{
-    extern __shared__ float sgf[];
-    const int T = g.T, P = T + W, lo = W / 2;
-    const int tile = blockIdx.x;
-    const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
-    const int beg = trg_ptr[tile], end = trg_ptr[tile + 1];
-    if (beg == end) return;
-    const int X0 = txi * T - lo, Y0 = tyi * T - lo;
-    stage_halo<float>(sgf, grid, g, X0, Y0, P);
-    __syncthreads();
-    const float beta = (float)g.beta, c = (float)g.c;
-    for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
-        const int4 r = trg[e];
-        const float sx = __int_as_float(r.z), sy = __int_as_float(r.w);
-        float fx[W], fy[W];
-#pragma unroll
-        for (int a = 0; a < W; ++a) {
-            fx[a] = es_window_stable<float>(sx + (float)a, beta, c);
-            fy[a] = es_window_stable<float>(sy + (float)a, beta, c);
-        }
-        const float *base = sgf + (r.y - Y0) * P + (r.x - X0);
-        double acc = 0.0;
-#pragma unroll
-        for (int cc = 0; cc < W; ++cc) {
-            float row = 0.0f;
-#pragma unroll
-            for (int a = 0; a < W; ++a) row = fmaf(fx[a], base[cc * P + a], row);
-            acc = fma((double)fy[cc], (double)row, acc);
-        }
-        u[trg_idx[e]] = acc;
-    }
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_interp32<W>(d, blockIdx.x, sm);
 }
 
 /* ----------------------------------------------------------------------------------------- */
@@ -627,14 +254,54 @@ template <typename K> cudaError_t set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-inline int rows_per_cta(int n, size_t cbytes)
+/* an Inst holding only what one launcher needs */
+Inst blank_inst(int n, int M)
 {
-    const int bytes_per_row = (n / 2) * (int)cbytes;
+    Inst d;
+    memset(&d, 0, sizeof d);
+    d.n = n;
+    d.M = M;
+    return d;
+}
+
+} /* namespace */
+
+/* ----------------------------------------------------------------------------------------- */
+/* stage geometry                                                                              */
+
+int rows_per_item(int n, bool f32)
+{
+    const int bytes_per_row = (n / 2) * (f32 ? 8 : 16);
     int r = (96 * 1024) / bytes_per_row;
     return r < 1 ? 1 : (r > 16 ? 16 : r);
 }
 
-} /* namespace */
+int stage_items(const Inst &d, int stage)
+{
+    switch (stage) {
+    case ST_SPREAD:
+    case ST_INTERP: return d.g.nt * d.g.nt;
+    case ST_ROW_FWD:
+    case ST_ROW_INV: return (d.n + d.rows - 1) / d.rows;
+    default: return d.M + 1;
+    }
+}
+
+int stage_smem(const Inst &d, int stage)
+{
+    const int T = d.g.T, W = d.g.w;
+    const int c = d.f32 ? 8 : 16; /* bytes of a complex value */
+    switch (stage) {
+    case ST_SPREAD:
+        return d.f32 ? (int)(sizeof(float2) * kSpreadWarps * T * (T + 1) +
+                             sizeof(float) * kSpreadWarps * 32 * 2 * W + sizeof(int) * kSpreadWarps * 64)
+                     : (int)(sizeof(unsigned long long) * T * T);
+    case ST_ROW_FWD:
+    case ST_ROW_INV: return c * d.rows * (d.n / 2);
+    case ST_COLUMNS: return c * d.n;
+    default: return (d.f32 ? 4 : 8) * (T + W) * (T + W);
+    }
+}
 
 /* ----------------------------------------------------------------------------------------- */
 /* launchers                                                                                  */
@@ -723,13 +390,21 @@ cudaError_t launch_spread(const Geom &g, const int *tile_ptr, const int *order,
                           const double2 *ent_t, const int *ent_j, const double *wq,
                           const double *dens, double *grid, cudaStream_t st)
 {
-    const size_t smem = sizeof(unsigned long long) * g.T * g.T;
-    const int ntiles = g.nt * g.nt;
+    Inst d = blank_inst(g.n, 0);
+    d.g = g;
+    d.tile_ptr = tile_ptr;
+    d.order = order;
+    d.ent_t = ent_t;
+    d.ent_j = ent_j;
+    d.wq = wq;
+    d.dens = dens;
+    d.grid = grid;
+    const size_t smem = stage_smem(d, ST_SPREAD);
     cudaError_t e = cudaSuccess;
-#define YK_CALL(W)                                                                          \
-    e = set_smem(k_spread<W>, smem);                                                        \
-    if (e != cudaSuccess) return e;                                                         \
-    k_spread<W><<<ntiles, 256, smem, st>>>(tile_ptr, order, ent_t, ent_j, wq, dens, g, grid)
+#define YK_CALL(W)                                                                              \
+    e = set_smem(k_spread<W>, smem);                                                            \
+    if (e != cudaSuccess) return e;                                                             \
+    k_spread<W><<<g.nt * g.nt, 256, smem, st>>>(d)
     YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     return cudaGetLastError();
@@ -739,123 +414,142 @@ cudaError_t launch_spread32(const Geom &g, const int *tile_ptr, const int *order
                             const double2 *ent_t, const int *ent_j, const double *wq,
                             const double *dens, float *grid, cudaStream_t st)
 {
-    const size_t smem = sizeof(float2) * kSpreadWarps * g.T * (g.T + 1) +
-                        sizeof(float) * kSpreadWarps * 32 * 2 * g.w +
-                        sizeof(int) * kSpreadWarps * 64;
-    const int ntiles = g.nt * g.nt;
-    const int4 *ent = reinterpret_cast<const int4 *>(ent_t);
+    Inst d = blank_inst(g.n, 0);
+    d.g = g;
+    d.f32 = 1;
+    d.tile_ptr = tile_ptr;
+    d.order = order;
+    d.ent_t = ent_t;
+    d.ent_j = ent_j;
+    d.wq = wq;
+    d.dens = dens;
+    d.grid = grid;
+    const size_t smem = stage_smem(d, ST_SPREAD);
     cudaError_t e = cudaSuccess;
-#define YK_CALL(W)                                                                          \
-    e = set_smem(k_spread32<W>, smem);                                                      \
-    if (e != cudaSuccess) return e;                                                         \
-    k_spread32<W><<<ntiles, 32 * kSpreadWarps, smem, st>>>(tile_ptr, order, ent, ent_j, wq, dens, \
-                                                           g, grid)
+#define YK_CALL(W)                                                                              \
+    e = set_smem(k_spread32<W>, smem);                                                          \
+    if (e != cudaSuccess) return e;                                                             \
+    k_spread32<W><<<g.nt * g.nt, 32 * kSpreadWarps, smem, st>>>(d)
     YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_row_fwd_t(const R *grid, typename V2<R>::T *spec, const typename V2<R>::T *tw,
-                             const int *perm_h, const FftStages &sth, int n, int M,
-                             cudaStream_t st)
+cudaError_t launch_fft_t(int stage, const void *grid_in, void *grid_out, void *spec,
+                         const void *mult, const void *tw, const int *perm_h, const int *iperm_f,
+                         const FftStages &sth, const FftStages &stf, int n, int M,
+                         cudaStream_t st)
 {
-    const int rows = rows_per_cta(n, sizeof(cpx<R>));
-    const size_t smem = sizeof(cpx<R>) * (size_t)rows * (n / 2);
-    cudaError_t e = set_smem(k_row_fwd<R>, smem);
-    if (e != cudaSuccess) return e;
-    k_row_fwd<R><<<(n + rows - 1) / rows, 256, smem, st>>>(grid, spec, tw, perm_h, sth, n, M, rows);
-    return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_columns_t(typename V2<R>::T *spec, const R *mult, const typename V2<R>::T *tw,
-                             const int *iperm_f, const FftStages &stf, int n, int M,
-                             cudaStream_t st)
-{
-    const size_t smem = sizeof(cpx<R>) * (size_t)n;
-    cudaError_t e = set_smem(k_columns<R>, smem);
-    if (e != cudaSuccess) return e;
-    k_columns<R><<<M + 1, 512, smem, st>>>(spec, mult, tw, iperm_f, stf, n, M);
-    return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_row_inv_t(const typename V2<R>::T *spec, R *grid, const typename V2<R>::T *tw,
-                             const int *perm_h, const FftStages &sth, int n, int M,
-                             cudaStream_t st)
-{
-    const int rows = rows_per_cta(n, sizeof(cpx<R>));
-    const size_t smem = sizeof(cpx<R>) * (size_t)rows * (n / 2);
-    cudaError_t e = set_smem(k_row_inv<R>, smem);
-    if (e != cudaSuccess) return e;
-    k_row_inv<R><<<(n + rows - 1) / rows, 256, smem, st>>>(spec, grid, tw, perm_h, sth, n, M, rows);
+    Inst d = blank_inst(n, M);
+    d.f32 = sizeof(R) == 4;
+    d.rows = rows_per_item(n, d.f32);
+    d.grid = stage == ST_ROW_FWD ? const_cast<void *>(grid_in) : grid_out;
+    d.spec = spec;
+    d.mult = mult;
+    d.tw = tw;
+    d.perm_h = perm_h;
+    d.iperm_f = iperm_f;
+    d.sth = sth;
+    d.stf = stf;
+    const size_t smem = stage_smem(d, stage);
+    const int items = stage_items(d, stage);
+    cudaError_t e = cudaSuccess;
+    if (stage == ST_ROW_FWD) {
+        if ((e = set_smem(k_row_fwd<R>, smem)) != cudaSuccess) return e;
+        k_row_fwd<R><<<items, 256, smem, st>>>(d);
+    } else if (stage == ST_COLUMNS) {
+        if ((e = set_smem(k_columns<R>, smem)) != cudaSuccess) return e;
+        k_columns<R><<<items, 512, smem, st>>>(d);
+    } else {
+        if ((e = set_smem(k_row_inv<R>, smem)) != cudaSuccess) return e;
+        k_row_inv<R><<<items, 256, smem, st>>>(d);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_row_fwd(const double *grid, double2 *spec, const double2 *tw, const int *perm_h,
                            const FftStages &sth, int n, int M, cudaStream_t st)
 {
-    return launch_row_fwd_t<double>(grid, spec, tw, perm_h, sth, n, M, st);
+    return launch_fft_t<double>(ST_ROW_FWD, grid, nullptr, spec, nullptr, tw, perm_h, nullptr,
+                                sth, sth, n, M, st);
 }
 cudaError_t launch_columns(double2 *spec, const double *mult, const double2 *tw,
                            const int *iperm_f, const FftStages &stf, int n, int M,
                            cudaStream_t st)
 {
-    return launch_columns_t<double>(spec, mult, tw, iperm_f, stf, n, M, st);
+    return launch_fft_t<double>(ST_COLUMNS, nullptr, nullptr, spec, mult, tw, nullptr, iperm_f,
+                                stf, stf, n, M, st);
 }
 cudaError_t launch_row_inv(const double2 *spec, double *grid, const double2 *tw,
                            const int *perm_h, const FftStages &sth, int n, int M,
                            cudaStream_t st)
 {
-    return launch_row_inv_t<double>(spec, grid, tw, perm_h, sth, n, M, st);
+    return launch_fft_t<double>(ST_ROW_INV, nullptr, grid, const_cast<double2 *>(spec), nullptr,
+                                tw, perm_h, nullptr, sth, sth, n, M, st);
 }
 cudaError_t launch_row_fwd32(const float *grid, float2 *spec, const float2 *tw, const int *perm_h,
                              const FftStages &sth, int n, int M, cudaStream_t st)
 {
-    return launch_row_fwd_t<float>(grid, spec, tw, perm_h, sth, n, M, st);
+    return launch_fft_t<float>(ST_ROW_FWD, grid, nullptr, spec, nullptr, tw, perm_h, nullptr, sth,
+                               sth, n, M, st);
 }
 cudaError_t launch_columns32(float2 *spec, const float *mult, const float2 *tw,
                              const int *iperm_f, const FftStages &stf, int n, int M,
                              cudaStream_t st)
 {
-    return launch_columns_t<float>(spec, mult, tw, iperm_f, stf, n, M, st);
+    return launch_fft_t<float>(ST_COLUMNS, nullptr, nullptr, spec, mult, tw, nullptr, iperm_f,
+                               stf, stf, n, M, st);
 }
 cudaError_t launch_row_inv32(const float2 *spec, float *grid, const float2 *tw, const int *perm_h,
                              const FftStages &sth, int n, int M, cudaStream_t st)
 {
-    return launch_row_inv_t<float>(spec, grid, tw, perm_h, sth, n, M, st);
+    return launch_fft_t<float>(ST_ROW_INV, nullptr, grid, const_cast<float2 *>(spec), nullptr,
+                               tw, perm_h, nullptr, sth, sth, n, M, st);
+}
+
+template <bool F32>
+cudaError_t launch_interp_t(const Geom &g, const int *trg_ptr, const double2 *trg_t,
+                            const int *trg_idx, const void *grid, double *u, cudaStream_t st)
+{
+    Inst d = blank_inst(g.n, 0);
+    d.g = g;
+    d.f32 = F32;
+    d.trg_ptr = trg_ptr;
+    d.trg_t = trg_t;
+    d.trg_idx = trg_idx;
+    d.grid = const_cast<void *>(grid);
+    d.u = u;
+    const size_t smem = stage_smem(d, ST_INTERP);
+    cudaError_t e = cudaSuccess;
+    if (F32) {
+#define YK_CALL(W)                                                                              \
+    e = set_smem(k_interp32<W>, smem);                                                          \
+    if (e != cudaSuccess) return e;                                                             \
+    k_interp32<W><<<g.nt * g.nt, 256, smem, st>>>(d)
+        YK_W_DISPATCH(g.w, YK_CALL)
+#undef YK_CALL
+    } else {
+#define YK_CALL(W)                                                                              \
+    e = set_smem(k_interp<W>, smem);                                                            \
+    if (e != cudaSuccess) return e;                                                             \
+    k_interp<W><<<g.nt * g.nt, 256, smem, st>>>(d)
+        YK_W_DISPATCH(g.w, YK_CALL)
+#undef YK_CALL
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_interp(const Geom &g, const int *trg_ptr, const double2 *trg_t,
                           const int *trg_idx, const double *grid, double *u, cudaStream_t st)
 {
-    const size_t smem = sizeof(double) * (size_t)(g.T + g.w) * (g.T + g.w);
-    const int ntiles = g.nt * g.nt;
-    cudaError_t e = cudaSuccess;
-#define YK_CALL(W)                                                                          \
-    e = set_smem(k_interp<W>, smem);                                                        \
-    if (e != cudaSuccess) return e;                                                         \
-    k_interp<W><<<ntiles, 256, smem, st>>>(trg_ptr, trg_t, trg_idx, g, grid, u)
-    YK_W_DISPATCH(g.w, YK_CALL)
-#undef YK_CALL
-    return cudaGetLastError();
+    return launch_interp_t<false>(g, trg_ptr, trg_t, trg_idx, grid, u, st);
 }
 
 cudaError_t launch_interp32(const Geom &g, const int *trg_ptr, const double2 *trg_t,
                             const int *trg_idx, const float *grid, double *u, cudaStream_t st)
 {
-    const size_t smem = sizeof(float) * (size_t)(g.T + g.w) * (g.T + g.w);
-    const int ntiles = g.nt * g.nt;
-    const int4 *trg = reinterpret_cast<const int4 *>(trg_t);
-    cudaError_t e = cudaSuccess;
-#define YK_CALL(W)                                                                          \
-    e = set_smem(k_interp32<W>, smem);                                                      \
-    if (e != cudaSuccess) return e;                                                         \
-    k_interp32<W><<<ntiles, 256, smem, st>>>(trg_ptr, trg, trg_idx, g, grid, u)
-    YK_W_DISPATCH(g.w, YK_CALL)
-#undef YK_CALL
-    return cudaGetLastError();
+    return launch_interp_t<true>(g, trg_ptr, trg_t, trg_idx, grid, u, st);
 }
 
 cudaError_t launch_build_mult(double *mult, const double *dfac, int M, double alpha, double delta,

@@ -1,0 +1,495 @@
+/*
+ * yk_stages.cuh — device bodies of the evaluation stages, one work item each (a spread tile, a
+ * block of grid rows, a grid column, an interpolation tile).  Called by the per-stage kernels of
+ * yk_kernels.cu (one CTA per item) and by the persistent batch kernel of yk_batch.cu (CTAs pull
+ * items of many instances from a queue).  Every function is entered by all threads of the CTA
+ * and uses `sm` (dynamic shared memory of at least stage_smem() bytes).
+ */
+#ifndef YK_STAGES_CUH
+#define YK_STAGES_CUH
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "yk_internal.h"
+
+namespace yk {
+
+template <typename R> struct V2;
+template <> struct V2<double> {
+    using T = double2;
+    static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
+template <> struct V2<float> {
+    using T = float2;
+    static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+
+constexpr double kMagic = 6755399441055744.0; /* 1.5 * 2^52: fma(a, b, kMagic) rounds a*b to an integer */
+constexpr int kSpreadWarps = 8;               /* warps per CTA of the FP32C spread */
+
+__device__ __forceinline__ double block_max(double v, double *red)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) red[0] = v;
+    }
+    __syncthreads();
+    v = red[0];
+    __syncthreads();
+    return v;
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* spread (type 1, Section 5.2 eq. disrete_sigma_hat): one output tile per item                */
+
+/* FP64: 64-bit fixed point.  Per-tile scale 2^k: every product |q| phi phi <= max|q| stays below
+ * 2^51 (so one fma with 1.5 * 2^52 rounds it to an integer) and the sum of all of them below
+ * 2^62; integer sums are exact, so the tile does not depend on the order of its entries. */
+template <int W> __device__ void st_spread64(const Inst &d, int item, unsigned char *sm)
+{
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(sm); /* T x T */
+    __shared__ double red[32];
+    __shared__ int s_k;
+    const Geom &g = d.g;
+    const int T = g.T, tile = d.order ? d.order[item] : item;
+    const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
+    const int X0 = txi * T, Y0 = tyi * T;
+    const double *__restrict__ wq = d.wq;
+    const double *__restrict__ dens = d.dens;
+    double *__restrict__ grid = static_cast<double *>(d.grid);
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) acc[i] = 0ull;
+    const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
+    double mq = 0.0;
+    for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
+        const int j = d.ent_j[e];
+        mq = fmax(mq, fabs(wq[j] * dens[j]));
+    }
+    mq = block_max(mq, red);
+    if (threadIdx.x == 0) {
+        int e2 = 0;
+        if (mq > 0.0) frexp(mq, &e2);
+        const int cbits = 32 - __clz(end - beg);
+        s_k = min(51, 62 - cbits) - e2;
+    }
+    __syncthreads();
+    const int kexp = s_k;
+    const long long magic_bits = __double_as_longlong(kMagic);
+    if (mq > 0.0) {
+        for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
+            const double2 t = d.ent_t[e];
+            const int j = d.ent_j[e];
+            const double qs = ldexp(wq[j] * dens[j], kexp);
+            const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
+            double fx[W], fy[W];
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                fx[a] = es_window<double>((double)(lx + a) - t.x, g.beta, g.c);
+                fy[a] = es_window<double>((double)(ly + a) - t.y, g.beta, g.c);
+            }
+            int dx0 = (lx - X0) % g.n;
+            if (dx0 < 0) dx0 += g.n;
+            int dy0 = (ly - Y0) % g.n;
+            if (dy0 < 0) dy0 += g.n;
+#pragma unroll
+            for (int c = 0; c < W; ++c) {
+                int yy = dy0 + c;
+                if (yy >= g.n) yy -= g.n;
+                if (yy < T) {
+                    const double qy = qs * fy[c];
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        int xx = dx0 + a;
+                        if (xx >= g.n) xx -= g.n;
+                        if (xx < T) {
+                            const long long iv =
+                                __double_as_longlong(fma(qy, fx[a], kMagic)) - magic_bits;
+                            atomicAdd(&acc[yy * T + xx], (unsigned long long)iv);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        const int r = i / T, c = i - r * T;
+        grid[(size_t)(Y0 + r) * g.n + X0 + c] =
+            mq > 0.0 ? ldexp((double)(long long)acc[i], -kexp) : 0.0;
+    }
+    __syncthreads(); /* shared memory is reused by the next item */
+}
+
+/* FP32C: FP32 window values and products, compensated (two-sum) accumulation.  Each warp owns a
+ * private hi + lo copy of the tile; it evaluates the windows of 32 entries (one per lane), then
+ * walks them one entry at a time with one lane per tap, so the taps a warp updates together are
+ * distinct cells and no atomics are needed.  The copies are combined in a fixed order at the end.
+ * Needs blockDim.x == 32 * kSpreadWarps. */
+template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned char *sm)
+{
+    const Geom &g = d.g;
+    const int T = g.T, PT = T + 1; /* padded pitch (float2 units) */
+    float2 *acc = reinterpret_cast<float2 *>(sm);                          /* [warps][T][PT] */
+    float *wbuf = reinterpret_cast<float *>(acc + kSpreadWarps * T * PT);  /* [warps][32][2W] */
+    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * 2 * W); /* [warps][32][2] */
+    const int tile = d.order ? d.order[item] : item;
+    const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
+    const int X0 = txi * T, Y0 = tyi * T;
+    const int4 *__restrict__ ent = reinterpret_cast<const int4 *>(d.ent_t);
+    float *__restrict__ grid = static_cast<float *>(d.grid);
+    for (int i = threadIdx.x; i < kSpreadWarps * T * PT; i += blockDim.x)
+        acc[i] = make_float2(0.0f, 0.0f);
+    __syncthreads();
+    const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2 *mine = acc + warp * T * PT;
+    float *wb = wbuf + warp * 32 * 2 * W;
+    int *ob = obuf + warp * 64;
+    const float beta = (float)g.beta, cw = (float)g.c;
+    for (int b0 = beg + warp * 32; b0 < end; b0 += kSpreadWarps * 32) {
+        const int e = b0 + lane;
+        if (e < end) {
+            const int4 r = ent[e];
+            const int j = d.ent_j[e];
+            const float q = (float)(d.wq[j] * d.dens[j]);
+            const float sx = __int_as_float(r.z), sy = __int_as_float(r.w);
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                wb[lane * 2 * W + a] = q * es_window_stable<float>(sy + (float)a, beta, cw);
+                wb[lane * 2 * W + W + a] = es_window_stable<float>(sx + (float)a, beta, cw);
+            }
+            int dx0 = (r.x - X0) % g.n;
+            if (dx0 < 0) dx0 += g.n;
+            int dy0 = (r.y - Y0) % g.n;
+            if (dy0 < 0) dy0 += g.n;
+            ob[2 * lane] = dx0;
+            ob[2 * lane + 1] = dy0;
+        }
+        __syncwarp();
+        const int cnt = min(32, end - b0);
+        for (int k = 0; k < cnt; ++k) {
+            const int dx0 = ob[2 * k], dy0 = ob[2 * k + 1];
+            const float *wk = wb + k * 2 * W;
+#pragma unroll
+            for (int t0 = 0; t0 < W * W; t0 += 32) {
+                const int t = t0 + lane;
+                if (t < W * W) {
+                    const int c = t / W, a = t - c * W;
+                    int yy = dy0 + c;
+                    if (yy >= g.n) yy -= g.n;
+                    int xx = dx0 + a;
+                    if (xx >= g.n) xx -= g.n;
+                    if (yy < T && xx < T) {
+                        const float v = wk[c] * wk[W + a];
+                        float2 cell = mine[yy * PT + xx];
+                        const float s = __fadd_rn(cell.x, v);
+                        const float bp = __fsub_rn(s, cell.x);
+                        const float err =
+                            __fadd_rn(__fsub_rn(cell.x, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+                        cell.x = s;
+                        cell.y = __fadd_rn(cell.y, err);
+                        mine[yy * PT + xx] = cell;
+                    }
+                }
+            }
+            __syncwarp(); /* the next entry may touch the same cells through other lanes */
+        }
+        __syncwarp(); /* window buffers are rewritten by the next batch of entries */
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        const int rr = i / T, cc = i - rr * T;
+        float hi = 0.0f, lo = 0.0f;
+        for (int w = 0; w < kSpreadWarps; ++w) {
+            const float2 p = acc[w * T * PT + rr * PT + cc];
+            const float s = __fadd_rn(hi, p.x);
+            const float bp = __fsub_rn(s, hi);
+            lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)),
+                                                   __fsub_rn(p.x, bp)),
+                                         p.y));
+            hi = s;
+        }
+        grid[(size_t)(Y0 + rr) * g.n + X0 + cc] = hi + lo;
+    }
+    __syncthreads();
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* FFT passes (mixed-radix DIF in shared memory, see yk_core.h)                               */
+
+template <typename R, typename TW>
+__device__ __forceinline__ void fft_fwd(cpx<R> *x, const FftStages &st, const TW *tw, int nrows,
+                                        int rowlen)
+{
+    for (int s = 0; s < st.n; ++s) {
+        const int nb = st.L / st.r[s];
+        for (int i = threadIdx.x; i < nrows * nb; i += blockDim.x) {
+            const int r = i / nb, t = i - r * nb;
+            dif_butterfly<R>(x + (size_t)r * rowlen, st, s, t, tw, 1);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R, typename TW>
+__device__ __forceinline__ void fft_inv(cpx<R> *x, const FftStages &st, const TW *tw, int nrows,
+                                        int rowlen)
+{
+    for (int s = st.n - 1; s >= 0; --s) {
+        const int nb = st.L / st.r[s];
+        for (int i = threadIdx.x; i < nrows * nb; i += blockDim.x) {
+            const int r = i / nb, t = i - r * nb;
+            idif_butterfly<R>(x + (size_t)r * rowlen, st, s, t, tw, 1);
+        }
+        __syncthreads();
+    }
+}
+
+/* rows [item*rows, ...): real-to-complex FFT, keep m_x <= M, store transposed spec[m_x*n + y] */
+template <typename R> __device__ void st_row_fwd(const Inst &d, int item, unsigned char *sm)
+{
+    using C2 = typename V2<R>::T;
+    cpx<R> *x = reinterpret_cast<cpx<R> *>(sm);
+    const int n = d.n, M = d.M, L = n >> 1;
+    const R *__restrict__ grid = static_cast<const R *>(d.grid);
+    C2 *__restrict__ spec = static_cast<C2 *>(d.spec);
+    const C2 *__restrict__ tw = static_cast<const C2 *>(d.tw);
+    const int y0 = item * d.rows;
+    const int nr = min(d.rows, n - y0);
+    for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
+        const int r = i / L, l = i - r * L;
+        const C2 v = reinterpret_cast<const C2 *>(grid + (size_t)(y0 + r) * n)[l];
+        x[i] = mk<R>(v.x, v.y);
+    }
+    __syncthreads();
+    fft_fwd<R>(x, d.sth, tw, nr, L);
+    for (int i = threadIdx.x; i < nr * (M + 1); i += blockDim.x) {
+        const int m = i / nr, r = i - m * nr;
+        const cpx<R> Zm = x[r * L + d.perm_h[m]];
+        const cpx<R> Zc = x[r * L + d.perm_h[m == 0 ? 0 : L - m]];
+        const C2 wm = tw[m];
+        const cpx<R> X = r2c_post<R>(Zm, Zc, mk<R>(wm.x, wm.y));
+        spec[(size_t)m * n + y0 + r] = V2<R>::make(X.re, X.im);
+    }
+    __syncthreads();
+}
+
+/* column m_x = item: FFT along y, multiply by the symbol (eq. sh_fourier), zero |m_y| > M,
+ * inverse FFT along y, in place */
+template <typename R> __device__ void st_columns(const Inst &d, int item, unsigned char *sm)
+{
+    using C2 = typename V2<R>::T;
+    cpx<R> *x = reinterpret_cast<cpx<R> *>(sm);
+    const int n = d.n, M = d.M, kx = item;
+    const C2 *__restrict__ tw = static_cast<const C2 *>(d.tw);
+    C2 *col = static_cast<C2 *>(d.spec) + (size_t)kx * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const C2 v = col[i];
+        x[i] = mk<R>(v.x, v.y);
+    }
+    __syncthreads();
+    fft_fwd<R>(x, d.stf, tw, 1, n);
+    const R *mrow = static_cast<const R *>(d.mult) + (size_t)kx * (2 * M + 1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int m = d.iperm_f[i];
+        const int my = m <= (n >> 1) ? m : m - n;
+        if (my >= -M && my <= M) x[i] = scale(x[i], mrow[my + M]);
+        else x[i] = mk<R>((R)0, (R)0);
+    }
+    __syncthreads();
+    fft_inv<R>(x, d.stf, tw, 1, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = V2<R>::make(x[i].re, x[i].im);
+    __syncthreads();
+}
+
+/* rows [item*rows, ...): gather m_x <= M, complex-to-real inverse FFT, write the real rows */
+template <typename R> __device__ void st_row_inv(const Inst &d, int item, unsigned char *sm)
+{
+    using C2 = typename V2<R>::T;
+    cpx<R> *x = reinterpret_cast<cpx<R> *>(sm);
+    const int n = d.n, M = d.M, L = n >> 1;
+    const C2 *__restrict__ spec = static_cast<const C2 *>(d.spec);
+    const C2 *__restrict__ tw = static_cast<const C2 *>(d.tw);
+    R *__restrict__ grid = static_cast<R *>(d.grid);
+    const int y0 = item * d.rows;
+    const int nr = min(d.rows, n - y0);
+    for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
+        const int m = i / nr, r = i - m * nr;
+        const int mc = L - m; /* in (0, L]; X[L] is zero because M < L */
+        C2 a = V2<R>::make((R)0, (R)0), b = V2<R>::make((R)0, (R)0);
+        if (m <= M) a = spec[(size_t)m * n + y0 + r];
+        if (mc <= M) b = spec[(size_t)mc * n + y0 + r];
+        const C2 wm = tw[m];
+        x[r * L + d.perm_h[m]] = c2r_pre<R>(mk<R>(a.x, a.y), mk<R>(b.x, b.y), mk<R>(wm.x, wm.y));
+    }
+    __syncthreads();
+    fft_inv<R>(x, d.sth, tw, nr, L);
+    for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
+        const int r = i / L, l = i - r * L;
+        reinterpret_cast<C2 *>(grid + (size_t)(y0 + r) * n)[l] = V2<R>::make(x[i].re, x[i].im);
+    }
+    __syncthreads();
+}
+
+/* ----------------------------------------------------------------------------------------- */
+/* interpolation (type 2): one target tile per item                                           */
+
+template <typename R>
+__device__ __forceinline__ void stage_halo(R *sg, const R *__restrict__ grid, const Geom &g,
+                                           int X0, int Y0, int P)
+{
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int r = i / P, c = i - r * P;
+        int gy = (Y0 + r) % g.n;
+        if (gy < 0) gy += g.n;
+        int gx = (X0 + c) % g.n;
+        if (gx < 0) gx += g.n;
+        sg[i] = grid[(size_t)gy * g.n + gx];
+    }
+}
+
+template <int W> __device__ void st_interp64(const Inst &d, int item, unsigned char *sm)
+{
+    double *sg = reinterpret_cast<double *>(sm);
+    const Geom &g = d.g;
+    const int T = g.T, P = T + W, lo = W / 2;
+    const int tyi = item / g.nt, txi = item - tyi * g.nt;
+    const int beg = d.trg_ptr[item], end = d.trg_ptr[item + 1];
+    if (beg == end) return; /* uniform across the CTA */
+    const int X0 = txi * T - lo, Y0 = tyi * T - lo;
+    stage_halo<double>(sg, static_cast<const double *>(d.grid), g, X0, Y0, P);
+    __syncthreads();
+    for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
+        const double2 t = d.trg_t[e];
+        const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
+        double fx[W], fy[W];
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            fx[a] = es_window<double>((double)(lx + a) - t.x, g.beta, g.c);
+            fy[a] = es_window<double>((double)(ly + a) - t.y, g.beta, g.c);
+        }
+        const double *base = sg + (ly - Y0) * P + (lx - X0);
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            double row = 0.0;
+#pragma unroll
+            for (int a = 0; a < W; ++a) row = fma(fx[a], base[c * P + a], row);
+            acc = fma(fy[c], row, acc);
+        }
+        d.u[d.trg_idx[e]] = acc;
+    }
+    __syncthreads();
+}
+
+/* FP32C: FP32 window values and row sums, rows combined in FP64 */
+template <int W> __device__ void st_interp32(const Inst &d, int item, unsigned char *sm)
+{
+    float *sg = reinterpret_cast<float *>(sm);
+    const Geom &g = d.g;
+    const int T = g.T, P = T + W, lo = W / 2;
+    const int tyi = item / g.nt, txi = item - tyi * g.nt;
+    const int beg = d.trg_ptr[item], end = d.trg_ptr[item + 1];
+    if (beg == end) return;
+    const int X0 = txi * T - lo, Y0 = tyi * T - lo;
+    stage_halo<float>(sg, static_cast<const float *>(d.grid), g, X0, Y0, P);
+    __syncthreads();
+    const int4 *__restrict__ trg = reinterpret_cast<const int4 *>(d.trg_t);
+    const float beta = (float)g.beta, cw = (float)g.c;
+    for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
+        const int4 r = trg[e];
+        const float sx = __int_as_float(r.z), sy = __int_as_float(r.w);
+        float fx[W], fy[W];
+#pragma unroll
+        for (int a = 0; a < W; ++a) {
+            fx[a] = es_window_stable<float>(sx + (float)a, beta, cw);
+            fy[a] = es_window_stable<float>(sy + (float)a, beta, cw);
+        }
+        const float *base = sg + (r.y - Y0) * P + (r.x - X0);
+        double acc = 0.0;
+#pragma unroll
+        for (int cc = 0; cc < W; ++cc) {
+            float row = 0.0f;
+#pragma unroll
+            for (int a = 0; a < W; ++a) row = fmaf(fx[a], base[cc * P + a], row);
+            acc = fma((double)fy[cc], (double)row, acc);
+        }
+        d.u[d.trg_idx[e]] = acc;
+    }
+    __syncthreads();
+}
+
+/* window width as a template parameter */
+#define YK_W_SWITCH(W_, CALL)                                                                    \
+    switch (W_) {                                                                                \
+    case 2: CALL(2); break;                                                                      \
+    case 3: CALL(3); break;                                                                      \
+    case 4: CALL(4); break;                                                                      \
+    case 5: CALL(5); break;                                                                      \
+    case 6: CALL(6); break;                                                                      \
+    case 7: CALL(7); break;                                                                      \
+    case 8: CALL(8); break;                                                                      \
+    case 9: CALL(9); break;                                                                      \
+    case 10: CALL(10); break;                                                                    \
+    case 11: CALL(11); break;                                                                    \
+    case 12: CALL(12); break;                                                                    \
+    case 13: CALL(13); break;                                                                    \
+    case 14: CALL(14); break;                                                                    \
+    case 15: CALL(15); break;                                                                    \
+    default: CALL(16); break;                                                                    \
+    }
+
+/* run one work item of stage `stage` for instance d (all threads of the CTA) */
+template <typename R>
+__device__ __forceinline__ void run_stage(const Inst &d, int stage, int item, unsigned char *sm);
+
+template <>
+__device__ __forceinline__ void run_stage<double>(const Inst &d, int stage, int item,
+                                                  unsigned char *sm)
+{
+    switch (stage) {
+    case ST_SPREAD: {
+#define YK_C(W) st_spread64<W>(d, item, sm)
+        YK_W_SWITCH(d.g.w, YK_C)
+#undef YK_C
+    } break;
+    case ST_ROW_FWD: st_row_fwd<double>(d, item, sm); break;
+    case ST_COLUMNS: st_columns<double>(d, item, sm); break;
+    case ST_ROW_INV: st_row_inv<double>(d, item, sm); break;
+    default: {
+#define YK_C(W) st_interp64<W>(d, item, sm)
+        YK_W_SWITCH(d.g.w, YK_C)
+#undef YK_C
+    } break;
+    }
+}
+
+template <>
+__device__ __forceinline__ void run_stage<float>(const Inst &d, int stage, int item,
+                                                 unsigned char *sm)
+{
+    switch (stage) {
+    case ST_SPREAD: {
+#define YK_C(W) st_spread32<W>(d, item, sm)
+        YK_W_SWITCH(d.g.w, YK_C)
+#undef YK_C
+    } break;
+    case ST_ROW_FWD: st_row_fwd<float>(d, item, sm); break;
+    case ST_COLUMNS: st_columns<float>(d, item, sm); break;
+    case ST_ROW_INV: st_row_inv<float>(d, item, sm); break;
+    default: {
+#define YK_C(W) st_interp32<W>(d, item, sm)
+        YK_W_SWITCH(d.g.w, YK_C)
+#undef YK_C
+    } break;
+    }
+}
+
+} /* namespace yk */
+
+#endif /* YK_STAGES_CUH */

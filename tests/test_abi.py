@@ -103,3 +103,30 @@ def test_fp32c_parameters():
     assert f64["n_grid"] == info["n_grid"] and f64["device_bytes"] > info["device_bytes"]
     with pytest.raises(yk.YkError):
         yk.plan_params(10.0, delta=0.01, precision=7)
+
+
+def test_tuned_tile_cache_roundtrip(tmp_path):
+    # a cached tile steers the plan's choice to the admissible divisor nearest to it
+    yk.tune_cache_clear()
+    base = yk.plan_params(10.0, 100000, 100000, delta=3.9e-5, tol=1e-10)
+    n, w = base["n_grid"], base["w"]
+    divisors = [t for t in range(w, 65) if n % t == 0 and n >= 2 * t]
+    assert base["tile"] == max(divisors)
+    want = min(divisors)
+    import math as _m
+    dens = 100000 / (n * n)
+    band = lambda v: int(_m.floor(2 * _m.log2(v) + 0.5))
+    f = tmp_path / "tune.txt"
+    f.write_text(f"# precision w n_band density_band tile\n0 {w} {band(n)} {band(dens)} {want}\n")
+    yk.tune_cache_load(str(f))
+    tuned = yk.plan_params(10.0, 100000, 100000, delta=3.9e-5, tol=1e-10, use_tuned=True,
+                           n_src_hint=100000)
+    assert tuned["tile"] == want and tuned["n_grid"] == n
+    untuned = yk.plan_params(10.0, 100000, 100000, delta=3.9e-5, tol=1e-10)
+    assert untuned["tile"] == max(divisors)
+    g = tmp_path / "saved.txt"
+    yk.tune_cache_save(str(g))
+    assert f"{want}" in g.read_text().split("\n")[1]
+    yk.tune_cache_clear()
+    assert yk.plan_params(10.0, 100000, 100000, delta=3.9e-5, tol=1e-10, use_tuned=True,
+                          n_src_hint=100000)["tile"] == max(divisors)

@@ -301,22 +301,27 @@ def batch_instances(n_inst=256, seed=0, n_lo=1e3, n_hi=2e5, a_lo=1.0, a_hi=300.0
 
 def rothe_stream(n_req=20000, rate=2000.0, n_geom=64, seed=0, n_lo=1e3, n_hi=1e6,
                  dt_lo=1e-4, dt_hi=1e-1):
-    """Request stream for Rothe time stepping: Poisson arrivals, each request one step on one of
-    n_geom resident geometries, alpha^2 = 1/dt with dt log-uniform.
+    """Request stream for Rothe time stepping.
 
-    Returns (geometries, requests) with requests a list of dicts {t_arrive, geom, alpha, seed}.
+    n_geom simulations, each a random starfish geometry with a point count log-uniform in
+    [n_lo, n_hi] and its own time step dt log-uniform in [dt_lo, dt_hi] (alpha = dt^{-1/2},
+    fixed for the simulation).  Requests arrive as a Poisson process of the given rate; each is
+    one time step of one simulation (new strengths on that resident geometry).
+
+    Returns (geometries, requests): geometries[g].alpha is its alpha; requests are dicts
+    {t_arrive, geom, seed}.
     """
     rng = np.random.default_rng(seed)
     geoms = []
     for g in range(n_geom):
         n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
-        geoms.append(random_instance(rng, n, 1.0))
+        dt = math.exp(rng.uniform(math.log(dt_lo), math.log(dt_hi)))
+        geoms.append(random_instance(rng, n, 1.0 / math.sqrt(dt)))
     t = np.cumsum(rng.exponential(1.0 / rate, n_req))
     reqs = []
     for i in range(n_req):
-        dt = math.exp(rng.uniform(math.log(dt_lo), math.log(dt_hi)))
         reqs.append(dict(t_arrive=float(t[i]), geom=int(rng.integers(0, n_geom)),
-                         alpha=1.0 / math.sqrt(dt), seed=int(rng.integers(0, 2 ** 31))))
+                         seed=int(rng.integers(0, 2 ** 31))))
     return geoms, reqs
 
 
