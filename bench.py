@@ -140,8 +140,8 @@ def stage_work(info, ns, nt):
     G = n * n
     L = n // 2
     entries = ns * (1 + (w - 1) / info["tile"]) ** 2  # windows spread into each tile they touch
-    # window evaluation: exp + sqrt + 4 flops per tap and axis, counted as 24 flops each
-    win = 24
+    # window value per tap and axis: a Horner polynomial of degree w + 1 (2 flops per step)
+    win = 2 * (w + 1)
     fft_row = 5 * L * math.log2(L) + 12 * L   # complex FFT of n/2 points + real post-processing
     fft_col = 5 * n * math.log2(n)
     return {

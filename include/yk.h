@@ -84,6 +84,9 @@ typedef struct {
     int use_tuned;      /* nonzero (and tile == 0): take the tile edge yk_autotune recorded for
                            this precision, window, grid size and n_src_hint */
     int64_t n_src_hint; /* expected number of sources (selects the autotuner's density band) */
+    int fft_fp64;       /* FP64 path only: nonzero runs the FFT passes in FP64 arithmetic; the
+                           default (0) runs them in double-float (FP32 pairs, ~48-bit mantissa,
+                           error ~1e-14), which B300 executes much faster than FP64 */
 } yk_opts;
 
 /* Parameters the plan chose (all derived from alpha, tol, delta and the box). */

@@ -48,7 +48,7 @@ class Opts(ctypes.Structure):
                 ("period", ctypes.c_double), ("tile", ctypes.c_int),
                 ("profile", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", _ALLOC),
                 ("free", _FREE), ("alloc_ctx", ctypes.c_void_p), ("use_tuned", ctypes.c_int),
-                ("n_src_hint", ctypes.c_int64)]
+                ("n_src_hint", ctypes.c_int64), ("fft_fp64", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -123,7 +123,8 @@ def _len(a) -> int:
 
 def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
               box=(-1.5, 1.5, -1.5, 1.5), kmax=0.0, kmax_rule=0, period=0.0, tile=0,
-              profile=False, stream=None, use_tuned=False, n_src_hint=0) -> Opts:
+              profile=False, stream=None, use_tuned=False, n_src_hint=0,
+              fft_fp64=False) -> Opts:
     o = Opts()
     _lib.yk_opts_default(ctypes.byref(o))
     o.precision = int(precision)
@@ -141,6 +142,7 @@ def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
     o.stream = stream
     o.use_tuned = 1 if use_tuned else 0
     o.n_src_hint = int(n_src_hint)
+    o.fft_fp64 = 1 if fft_fp64 else 0
     return o
 
 

@@ -191,6 +191,42 @@ double window_ft(double xi, int w, double beta)
     return 2.0 * sum;
 }
 
+/* per-tap window polynomials: tap a covers z = u - w/2 + a, u in [0, 1); with x = 2u - 1 the
+ * window there is interpolated at deg+1 Chebyshev points and the series converted to powers of
+ * x, all in long double; out[k * w + a] = coefficient of x^k for tap a */
+void window_polys(int w, double beta, int deg, std::vector<double> &out)
+{
+    const int m = deg + 1;
+    const long double pi = 3.14159265358979323846264338327950288L;
+    out.assign((size_t)m * w, 0.0);
+    for (int a = 0; a < w; ++a) {
+        std::vector<long double> f(m), c(m, 0.0L), mono(m, 0.0L), t0(m, 0.0L), t1(m, 0.0L), t2(m);
+        for (int j = 0; j < m; ++j) {
+            const long double x = cosl(pi * (j + 0.5L) / m);
+            const long double z = 0.5L * (x + 1.0L) - 0.5L * w + a;
+            const long double v = (2.0L * z / w) * (2.0L * z / w);
+            f[j] = v <= 1.0L ? expl(-(long double)beta * v / (1.0L + sqrtl(1.0L - v))) : 0.0L;
+        }
+        for (int k = 0; k < m; ++k) {
+            long double sum = 0.0L;
+            for (int j = 0; j < m; ++j) sum += f[j] * cosl(pi * k * (j + 0.5L) / m);
+            c[k] = 2.0L * sum / m;
+        }
+        c[0] *= 0.5L;
+        /* sum_k c_k T_k(x) in powers of x via T_{k+1} = 2x T_k - T_{k-1} */
+        t0[0] = 1.0L;
+        if (m > 1) t1[1] = 1.0L;
+        for (int i = 0; i < m; ++i) mono[i] += c[0] * t0[i];
+        for (int k = 1; k < m; ++k) {
+            for (int i = 0; i < m; ++i) mono[i] += c[k] * t1[i];
+            for (int i = 0; i < m; ++i) t2[i] = -t0[i] + (i > 0 ? 2.0L * t1[i - 1] : 0.0L);
+            t0 = t1;
+            t1 = t2;
+        }
+        for (int k = 0; k < m; ++k) out[(size_t)k * w + a] = (double)mono[k];
+    }
+}
+
 bool smooth5(int64_t n)
 {
     for (int p : {2, 3, 5})
@@ -226,6 +262,7 @@ bool make_stages(int L, int n_tab, FftStages &st)
         st.tw_step[i] = n_tab / B;
         B /= st.r[i];
     }
+    yk::fft_fill_magic(st);
     return true;
 }
 
@@ -289,7 +326,7 @@ void buf_free(yk_plan_t p, DevBuf &b)
 
 void free_all(yk_plan_t p)
 {
-    DevBuf *all[] = {&p->grid, &p->spec, &p->mult, &p->tw, &p->perm_h, &p->iperm_f,
+    DevBuf *all[] = {&p->grid, &p->spec, &p->mult, &p->tw, &p->perm_h, &p->iperm_f, &p->win,
                      &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->tile_order, &p->trg_cnt,
                      &p->trg_ptr,
                      &p->trg_cur, &p->err, &p->w_src, &p->src_t, &p->ent_t, &p->ent_j,
@@ -417,19 +454,41 @@ yk_status plan_tables(yk_plan_t p)
     dif_positions(p->st_half, pos_h);
     dif_positions(p->st_full, pos_f);
     for (int64_t m = 0; m < n; ++m) ipos_f[pos_f[m]] = (int)m;
-    /* twiddles from long double, rounded once to the table's type */
+    /* twiddles from long double, rounded once to the table's type (FP32C: float pairs; FP64 with
+     * double-float FFT: hi/lo float pairs per component; FP64: doubles) */
     std::vector<double2> tw(f32 ? 0 : n);
     std::vector<float2> tw32(f32 ? n : 0);
     for (int64_t j = 0; j < n; ++j) {
         const long double a = 2.0L * 3.14159265358979323846264338327950288L * (long double)j /
                               (long double)n;
-        if (f32) tw32[j] = make_float2((float)cosl(a), (float)-sinl(a));
-        else tw[j] = make_double2((double)cosl(a), (double)-sinl(a));
+        const long double c = cosl(a), sn = -sinl(a);
+        if (f32) {
+            tw32[j] = make_float2((float)c, (float)sn);
+        } else if (p->fft_df) {
+            float v[4];
+            v[0] = (float)c;
+            v[1] = (float)(c - (long double)v[0]);
+            v[2] = (float)sn;
+            v[3] = (float)(sn - (long double)v[2]);
+            std::memcpy(&tw[j], v, sizeof v);
+        } else {
+            tw[j] = make_double2((double)c, (double)sn);
+        }
     }
     std::vector<double> dfac(M + 1);
     for (int64_t m = 0; m <= M; ++m) {
         const double ph = window_ft(2.0 * kPi * (double)m / (double)n, p->w, p->beta);
         dfac[m] = 1.0 / (ph * ph);
+    }
+    if (!f32) {
+        /* FP64 windows as per-tap polynomials of degree w + 1 */
+        p->wdeg = p->w + 1;
+        std::vector<double> poly;
+        window_polys(p->w, p->beta, p->wdeg, poly);
+        if ((s = buf_alloc(p, p->win, sizeof(double) * poly.size(), "window")) != YK_OK) return s;
+        cudaError_t ew = cudaMemcpy(p->win.ptr, poly.data(), sizeof(double) * poly.size(),
+                                    cudaMemcpyHostToDevice);
+        if (ew != cudaSuccess) return cuda_fail(ew, "window table");
     }
     DevBuf d_dfac = {nullptr, 0};
     if ((s = buf_alloc(p, d_dfac, sizeof(double) * (M + 1), "deconvolution")) != YK_OK) return s;
@@ -448,6 +507,9 @@ yk_status plan_tables(yk_plan_t p)
         if (f32)
             e = yk::launch_build_mult32(P<float>(p->mult), P<double>(d_dfac), (int)M, p->alpha,
                                         p->delta, 2.0 * kPi / p->period, p->period, p->stream);
+        else if (p->fft_df)
+            e = yk::launch_build_mult_df(p->mult.ptr, P<double>(d_dfac), (int)M, p->alpha,
+                                         p->delta, 2.0 * kPi / p->period, p->period, p->stream);
         else
             e = yk::launch_build_mult(P<double>(p->mult), P<double>(d_dfac), (int)M, p->alpha,
                                       p->delta, 2.0 * kPi / p->period, p->period, p->stream);
@@ -476,6 +538,7 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->n = (int)p->n;
     d->M = (int)p->M;
     d->f32 = p->precision == YK_FP32C;
+    d->fft_df = p->fft_df;
     d->rows = yk::rows_per_item(d->n, d->f32);
     d->tile_ptr = P<int>(p->tile_ptr);
     d->order = P<int>(p->tile_order);
@@ -491,6 +554,8 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->tw = p->tw.ptr;
     d->perm_h = P<int>(p->perm_h);
     d->iperm_f = P<int>(p->iperm_f);
+    d->win = P<double>(p->win);
+    d->wdeg = p->wdeg;
     for (int s = 0; s < yk::ST_COUNT; ++s) {
         d->items[s] = yk::stage_items(*d, s);
         d->smem[s] = yk::stage_smem(*d, s);
@@ -545,6 +610,7 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
     p->tol = o->tol;
     p->eps = o->tol / 4.0;
     p->precision = o->precision;
+    p->fft_df = (o->precision == YK_FP64 && !o->fft_fp64) ? 1 : 0;
     p->stream = (cudaStream_t)o->stream;
     p->alloc = o->alloc;
     p->dealloc = o->free;
@@ -611,6 +677,7 @@ static int64_t predicted_bytes(const yk_plan_s *p, int64_t n_src, int64_t n_trg)
     const int64_t r = p->precision == YK_FP32C ? 4 : 8; /* bytes of the real type */
     int64_t b = r * n * n + 2 * r * (M + 1) * n + r * (M + 1) * (2 * M + 1) + 2 * r * n +
                 4 * (n / 2) + 4 * n + 4 * (7 * nt2 + 2) + 4;
+    if (p->precision == YK_FP64) b += 8 * (int64_t)(p->w + 2) * p->w;
     b += n_src * (8 + 16 + 4 * (16 + 4)) + n_trg * (16 + 4 + 16);
     return b;
 }
@@ -786,66 +853,16 @@ yk_status yk_eval_longrange(yk_plan_t p, const double *density, double *u)
         } else {
             const double *dd = nullptr;
             if ((s = to_device(p, density, p->n_src, p->stage_w, &dd, "density")) != YK_OK) return s;
-            const yk::Geom g = geom_of(p);
-            const int n = (int)p->n, M = (int)p->M;
-            if (p->precision == YK_FP32C) {
-                stage_begin(p, YK_STAGE_SPREAD);
-                YK_CU(yk::launch_spread32(g, P<int>(p->tile_ptr), P<int>(p->tile_order),
-                                          P<double2>(p->ent_t),
-                                          P<int>(p->ent_j), P<double>(p->w_src), dd,
-                                          P<float>(p->grid), p->stream),
-                      "spread");
-                stage_end(p, YK_STAGE_SPREAD);
-                stage_begin(p, YK_STAGE_ROW_FWD);
-                YK_CU(yk::launch_row_fwd32(P<float>(p->grid), P<float2>(p->spec),
-                                           P<float2>(p->tw), P<int>(p->perm_h), p->st_half, n, M,
-                                           p->stream),
-                      "row FFT");
-                stage_end(p, YK_STAGE_ROW_FWD);
-                stage_begin(p, YK_STAGE_COLUMNS);
-                YK_CU(yk::launch_columns32(P<float2>(p->spec), P<float>(p->mult),
-                                           P<float2>(p->tw), P<int>(p->iperm_f), p->st_full, n, M,
-                                           p->stream),
-                      "column FFT");
-                stage_end(p, YK_STAGE_COLUMNS);
-                stage_begin(p, YK_STAGE_ROW_INV);
-                YK_CU(yk::launch_row_inv32(P<float2>(p->spec), P<float>(p->grid),
-                                           P<float2>(p->tw), P<int>(p->perm_h), p->st_half, n, M,
-                                           p->stream),
-                      "row inverse FFT");
-                stage_end(p, YK_STAGE_ROW_INV);
-                stage_begin(p, YK_STAGE_INTERP);
-                YK_CU(yk::launch_interp32(g, P<int>(p->trg_ptr), P<double2>(p->trg_t),
-                                          P<int>(p->trg_idx), P<float>(p->grid), du, p->stream),
-                      "interpolation");
-                stage_end(p, YK_STAGE_INTERP);
-            } else {
-                stage_begin(p, YK_STAGE_SPREAD);
-                YK_CU(yk::launch_spread(g, P<int>(p->tile_ptr), P<int>(p->tile_order),
-                                        P<double2>(p->ent_t), P<int>(p->ent_j),
-                                        P<double>(p->w_src), dd, P<double>(p->grid), p->stream),
-                      "spread");
-                stage_end(p, YK_STAGE_SPREAD);
-                stage_begin(p, YK_STAGE_ROW_FWD);
-                YK_CU(yk::launch_row_fwd(P<double>(p->grid), P<double2>(p->spec), P<double2>(p->tw),
-                                         P<int>(p->perm_h), p->st_half, n, M, p->stream),
-                      "row FFT");
-                stage_end(p, YK_STAGE_ROW_FWD);
-                stage_begin(p, YK_STAGE_COLUMNS);
-                YK_CU(yk::launch_columns(P<double2>(p->spec), P<double>(p->mult), P<double2>(p->tw),
-                                         P<int>(p->iperm_f), p->st_full, n, M, p->stream),
-                      "column FFT");
-                stage_end(p, YK_STAGE_COLUMNS);
-                stage_begin(p, YK_STAGE_ROW_INV);
-                YK_CU(yk::launch_row_inv(P<double2>(p->spec), P<double>(p->grid), P<double2>(p->tw),
-                                         P<int>(p->perm_h), p->st_half, n, M, p->stream),
-                      "row inverse FFT");
-                stage_end(p, YK_STAGE_ROW_INV);
-                stage_begin(p, YK_STAGE_INTERP);
-                YK_CU(yk::launch_interp(g, P<int>(p->trg_ptr), P<double2>(p->trg_t),
-                                        P<int>(p->trg_idx), P<double>(p->grid), du, p->stream),
-                      "interpolation");
-                stage_end(p, YK_STAGE_INTERP);
+            yk::Inst d;
+            yk_fill_inst(p, &d);
+            d.dens = dd;
+            d.u = du;
+            static const char *names[yk::ST_COUNT] = {"spread", "row FFT", "column FFT",
+                                                      "row inverse FFT", "interpolation"};
+            for (int st = 0; st < yk::ST_COUNT; ++st) {
+                stage_begin(p, YK_STAGE_SPREAD + st);
+                YK_CU(yk::launch_stage(d, st, p->stream), names[st]);
+                stage_end(p, YK_STAGE_SPREAD + st);
             }
         }
     }

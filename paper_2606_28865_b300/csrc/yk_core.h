@@ -45,6 +45,58 @@ template <int SIGN, typename R> YK_HD cpx<R> mul_i(cpx<R> a)
 }
 
 /* ---------------------------------------------------------------------------------------- */
+/* double-float: a real number held as an unevaluated sum hi + lo of two FP32 values, |lo| <=   */
+/* ulp(hi)/2 (about 48 significant bits).  B300 runs FP32 at 64 times its FP64 rate, so FFT    */
+/* arithmetic of FP64 accuracy (relative error ~1e-14, far below the 1e-10 target) is cheaper  */
+/* in FP32 pairs than in FP64.  Addition uses the two-sum error-free transformation (Knuth),   */
+/* multiplication the FMA two-product; both renormalise with a fast two-sum.  Intrinsics with   */
+/* explicit rounding keep the compiler from contracting or reordering the error terms.         */
+#if defined(__CUDA_ARCH__)
+#define YK_FADD(a, b) __fadd_rn(a, b)
+#define YK_FSUB(a, b) __fsub_rn(a, b)
+#define YK_FMUL(a, b) __fmul_rn(a, b)
+#define YK_FFMA(a, b, c) __fmaf_rn(a, b, c)
+#else
+#define YK_FADD(a, b) ((a) + (b))
+#define YK_FSUB(a, b) ((a) - (b))
+#define YK_FMUL(a, b) ((a) * (b))
+#define YK_FFMA(a, b, c) fmaf(a, b, c)
+#endif
+
+struct df32 {
+    float hi, lo;
+    df32() = default;
+    YK_HD df32(float h, float l) : hi(h), lo(l) {}
+    /* from a double: hi = round(d), lo = round(d - hi) (constant-folded for literals) */
+    YK_HD explicit df32(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    YK_HD double to_double() const { return (double)hi + (double)lo; }
+};
+
+YK_HD df32 df_fast_two_sum(float a, float b)
+{
+    const float s = YK_FADD(a, b);
+    return df32(s, YK_FSUB(b, YK_FSUB(s, a)));
+}
+YK_HD df32 operator+(df32 a, df32 b)
+{
+    const float s = YK_FADD(a.hi, b.hi);
+    const float bb = YK_FSUB(s, a.hi);
+    float e = YK_FADD(YK_FSUB(a.hi, YK_FSUB(s, bb)), YK_FSUB(b.hi, bb));
+    e = YK_FADD(e, YK_FADD(a.lo, b.lo));
+    return df_fast_two_sum(s, e);
+}
+YK_HD df32 operator-(df32 a) { return df32(-a.hi, -a.lo); }
+YK_HD df32 operator-(df32 a, df32 b) { return a + (-b); }
+YK_HD df32 operator*(df32 a, df32 b)
+{
+    const float p = YK_FMUL(a.hi, b.hi);
+    float e = YK_FFMA(a.hi, b.hi, -p);
+    e = YK_FFMA(a.hi, b.lo, e);
+    e = YK_FFMA(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+/* ---------------------------------------------------------------------------------------- */
 /* exponential-of-semicircle window phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)), |z| <= w/2    */
 /* (the spreading kernel of the NUFFT that evaluates eqs. disrete_sigma_hat and sh_fourier)  */
 template <typename R> YK_HD R es_window(R z, R beta, R c /* = 4/w^2 */)
@@ -75,7 +127,7 @@ YK_HD int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 /* Stage s has radix r_s, block length B_s = L / (r_1 ... r_{s-1}) and span_s = B_s / r_s.   */
 /* Butterfly t in [0, L / r_s) of stage s: block b = t / span_s, k = t % span_s, elements     */
 /* x[b B_s + k + q span_s] (q < r_s) -> length-r_s DFT -> output p multiplied by W_{B_s}^{pk}  */
-/* and stored back at x[b B_s + k + p span_s].  After all stages position                     */
+/* and stored back at x[b B_s + k + p span_s] (fft_stage in yk_stages.cuh).  After all stages position                     */
 /* sum_s p_s span_s holds frequency p_1 + r_1 (p_2 + r_2 (p_3 + ...)) (digit-reversed order). */
 /* The inverse (natural order out, unnormalised, e^{+}) runs the stages in reverse order and   */
 /* for each butterfly multiplies by conj(W_{B_s}^{pk}) before the inverse length-r_s DFT.     */
@@ -89,7 +141,22 @@ struct FftStages {
     int r[YK_MAX_STAGES];      /* radix of stage s */
     int B[YK_MAX_STAGES];      /* block length of stage s */
     int tw_step[YK_MAX_STAGES]; /* twiddle table stride n_tab / B_s */
+    /* division by span_s = B_s / r_s and by nb_s = L / r_s (butterflies per row) as a multiply:
+     * q = umulhi(x, ceil(2^32 / d)) equals floor(x / d) for x d < 2^32 (all sizes here are far
+     * below 2^16); d = 1 is handled apart */
+    unsigned span_m[YK_MAX_STAGES], nb_m[YK_MAX_STAGES];
 };
+
+/* host side: fill the division multipliers of st (after r and B) */
+static inline void fft_fill_magic(FftStages &st)
+{
+    for (int s = 0; s < st.n; ++s) {
+        const unsigned long long span = (unsigned long long)(st.B[s] / st.r[s]);
+        const unsigned long long nb = (unsigned long long)(st.L / st.r[s]);
+        st.span_m[s] = span > 1 ? (unsigned)(((1ull << 32) + span - 1) / span) : 0u;
+        st.nb_m[s] = nb > 1 ? (unsigned)(((1ull << 32) + nb - 1) / nb) : 0u;
+    }
+}
 
 /* length-r DFT in place on v[0..r-1]; SIGN = -1 forward (e^{-2 pi i pq/r}), +1 inverse */
 template <int SIGN, typename R> YK_HD void dft2(cpx<R> *v)
@@ -136,52 +203,6 @@ template <int SIGN, typename R> YK_HD void dft5(cpx<R> *v)
     v[4] = sub(m1, t1);
     v[2] = add(m2, t2);
     v[3] = sub(m2, t2);
-}
-
-template <int SIGN, typename R> YK_HD void dft_r(cpx<R> *v, int r)
-{
-    switch (r) {
-    case 2: dft2<SIGN>(v); break;
-    case 3: dft3<SIGN>(v); break;
-    case 4: dft4<SIGN>(v); break;
-    default: dft5<SIGN>(v); break;
-    }
-}
-
-/* one forward DIF butterfly (stage s, butterfly t) on the array x of length st.L */
-template <typename R, typename TW>
-YK_HD void dif_butterfly(cpx<R> *x, const FftStages &st, int s, int t, const TW *tw, int tw_mul)
-{
-    const int r = st.r[s], B = st.B[s], span = B / r;
-    const int b = t / span, k = t - b * span;
-    const int base = b * B + k;
-    cpx<R> v[5];
-    for (int q = 0; q < r; ++q) v[q] = x[base + q * span];
-    dft_r<-1>(v, r);
-    x[base] = v[0];
-    const int step = st.tw_step[s] * tw_mul * k;
-    for (int p = 1; p < r; ++p) {
-        const TW w = tw[p * step];
-        x[base + p * span] = mul(v[p], mk<R>((R)w.x, (R)w.y));
-    }
-}
-
-/* one inverse butterfly (stage s of the reversed sequence) */
-template <typename R, typename TW>
-YK_HD void idif_butterfly(cpx<R> *x, const FftStages &st, int s, int t, const TW *tw, int tw_mul)
-{
-    const int r = st.r[s], B = st.B[s], span = B / r;
-    const int b = t / span, k = t - b * span;
-    const int base = b * B + k;
-    cpx<R> v[5];
-    v[0] = x[base];
-    const int step = st.tw_step[s] * tw_mul * k;
-    for (int p = 1; p < r; ++p) {
-        const TW w = tw[p * step];
-        v[p] = mulc(x[base + p * span], mk<R>((R)w.x, (R)w.y));
-    }
-    dft_r<+1>(v, r);
-    for (int q = 0; q < r; ++q) x[base + q * span] = v[q];
 }
 
 /* ---------------------------------------------------------------------------------------- */

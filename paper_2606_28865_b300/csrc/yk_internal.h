@@ -39,6 +39,7 @@ struct Inst {
     Geom g;
     FftStages sth, stf;       /* n/2-point (rows) and n-point (columns) transforms */
     int n, M, rows, f32;      /* rows: grid rows per row-FFT work item */
+    int fft_df;               /* FP64 path: FFT arithmetic in double-float (tables in that form) */
     const int *tile_ptr;      /* source entries of tile t: [tile_ptr[t], tile_ptr[t+1]) */
     const int *order;         /* heavy-first tile order, or NULL */
     const double2 *ent_t;     /* entries (FP64: grid coordinate; FP32C: first tap + offset) */
@@ -54,9 +55,16 @@ struct Inst {
     const void *mult;         /* R[(M+1)*(2M+1)] */
     const void *tw;           /* R2[n] */
     const int *perm_h, *iperm_f;
+    const double *win;        /* FP64 windows as polynomials: win[k * w + a] is the coefficient of
+                                 x^k for tap a, x = 2u - 1, u = l0 - t + w/2 in [0, 1); NULL: the
+                                 window formula is evaluated directly */
+    int wdeg;                 /* polynomial degree */
     int items[ST_COUNT];      /* work items of each stage */
     int smem[ST_COUNT];       /* dynamic shared memory of each stage (bytes) */
 };
+
+/* launch one stage of one evaluation (one CTA per work item) */
+cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st);
 
 /* shared-memory and work-item sizes of each stage (host side of the kernels' layouts) */
 int stage_smem(const Inst &d, int stage);
@@ -103,6 +111,9 @@ cudaError_t launch_build_mult(double *mult, const double *dfac, int M, double al
                               double dk, double period, cudaStream_t st);
 cudaError_t launch_build_mult32(float *mult, const double *dfac, int M, double alpha,
                                 double delta, double dk, double period, cudaStream_t st);
+/* multiplier as double-float pairs (FP64 path with double-float FFT arithmetic) */
+cudaError_t launch_build_mult_df(void *mult, const double *dfac, int M, double alpha,
+                                 double delta, double dk, double period, cudaStream_t st);
 
 /* largest grid the column pass supports (one column of n complex values in shared memory) */
 constexpr int kMaxGridF64 = 14400;
@@ -124,6 +135,7 @@ struct yk_plan_s {
     double box[4];
     int64_t M, n;
     int w, T, nt, precision;
+    int fft_df; /* FP64 path: FFT arithmetic in double-float (default) or in FP64 */
     bool zero; /* k_max == 0: history below tolerance, u = 0 */
     cudaStream_t stream;
     void *(*alloc)(size_t, void *, void *);
@@ -141,6 +153,8 @@ struct yk_plan_s {
     DevBuf tw;       /* R2[n]: exp(-2 pi i j / n) */
     DevBuf perm_h;   /* int[n/2]: DIF position of frequency m (half-length transform) */
     DevBuf iperm_f;  /* int[n]: frequency held at DIF position i (full-length transform) */
+    DevBuf win;      /* double[(wdeg+1) * w]: window polynomials of the FP64 path */
+    int wdeg;
     DevBuf tile_cnt, tile_ptr, tile_cur; /* int[nt^2], int[nt^2+1], int[nt^2] (sources) */
     DevBuf tile_order; /* int[nt^2]: heavy-first processing order of the source tiles */
     DevBuf trg_cnt, trg_ptr, trg_cur;    /* same for targets */

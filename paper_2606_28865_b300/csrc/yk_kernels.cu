@@ -290,16 +290,17 @@ int stage_items(const Inst &d, int stage)
 int stage_smem(const Inst &d, int stage)
 {
     const int T = d.g.T, W = d.g.w;
+    const int win_bytes = d.win ? (int)sizeof(double) * (d.wdeg + 1) * W : 0;
     const int c = d.f32 ? 8 : 16; /* bytes of a complex value */
     switch (stage) {
     case ST_SPREAD:
         return d.f32 ? (int)(sizeof(float2) * kSpreadWarps * T * (T + 1) +
                              sizeof(float) * kSpreadWarps * 32 * 2 * W + sizeof(int) * kSpreadWarps * 64)
-                     : (int)(sizeof(unsigned long long) * T * T);
+                     : (int)(sizeof(unsigned long long) * T * T + win_bytes);
     case ST_ROW_FWD:
     case ST_ROW_INV: return c * d.rows * (d.n / 2);
     case ST_COLUMNS: return c * d.n;
-    default: return (d.f32 ? 4 : 8) * (T + W) * (T + W);
+    default: return d.f32 ? 4 * (T + W) * (T + W) : 8 * (T + W) * (T + W) + win_bytes;
     }
 }
 
@@ -550,6 +551,70 @@ cudaError_t launch_interp32(const Geom &g, const int *trg_ptr, const double2 *tr
                             const int *trg_idx, const float *grid, double *u, cudaStream_t st)
 {
     return launch_interp_t<true>(g, trg_ptr, trg_t, trg_idx, grid, u, st);
+}
+
+cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st)
+{
+    const size_t smem = stage_smem(d, stage);
+    const int items = stage_items(d, stage);
+    if (items <= 0) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define YK_LAUNCH(K, THREADS)                                                                   \
+    do {                                                                                        \
+        if ((e = set_smem(K, smem)) != cudaSuccess) return e;                                   \
+        K<<<items, THREADS, smem, st>>>(d);                                                     \
+    } while (0)
+    switch (stage) {
+    case ST_SPREAD:
+        if (d.f32) {
+#define YK_CALL(W) YK_LAUNCH(k_spread32<W>, 32 * kSpreadWarps)
+            YK_W_DISPATCH(d.g.w, YK_CALL)
+#undef YK_CALL
+        } else {
+#define YK_CALL(W) YK_LAUNCH(k_spread<W>, 256)
+            YK_W_DISPATCH(d.g.w, YK_CALL)
+#undef YK_CALL
+        }
+        break;
+    case ST_ROW_FWD:
+        if (d.f32) YK_LAUNCH(k_row_fwd<float>, 256);
+        else if (d.fft_df) YK_LAUNCH(k_row_fwd<df32>, 256);
+        else YK_LAUNCH(k_row_fwd<double>, 256);
+        break;
+    case ST_COLUMNS:
+        if (d.f32) YK_LAUNCH(k_columns<float>, 512);
+        else if (d.fft_df) YK_LAUNCH(k_columns<df32>, 512);
+        else YK_LAUNCH(k_columns<double>, 512);
+        break;
+    case ST_ROW_INV:
+        if (d.f32) YK_LAUNCH(k_row_inv<float>, 256);
+        else if (d.fft_df) YK_LAUNCH(k_row_inv<df32>, 256);
+        else YK_LAUNCH(k_row_inv<double>, 256);
+        break;
+    default:
+        if (d.f32) {
+#define YK_CALL(W) YK_LAUNCH(k_interp32<W>, 256)
+            YK_W_DISPATCH(d.g.w, YK_CALL)
+#undef YK_CALL
+        } else {
+#define YK_CALL(W) YK_LAUNCH(k_interp<W>, 256)
+            YK_W_DISPATCH(d.g.w, YK_CALL)
+#undef YK_CALL
+        }
+        break;
+    }
+#undef YK_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t launch_build_mult_df(void *mult, const double *dfac, int M, double alpha,
+                                 double delta, double dk, double period, cudaStream_t st)
+{
+    const int64_t total = (int64_t)(M + 1) * (2 * M + 1);
+    k_build_mult<df32><<<(int)((total + 255) / 256), 256, 0, st>>>(static_cast<df32 *>(mult),
+                                                                   dfac, M, alpha, delta, dk,
+                                                                   period);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_build_mult(double *mult, const double *dfac, int M, double alpha, double delta,

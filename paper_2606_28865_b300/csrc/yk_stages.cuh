@@ -15,14 +15,58 @@
 
 namespace yk {
 
-template <typename R> struct V2;
-template <> struct V2<double> {
-    using T = double2;
-    static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+/* complex of double-floats as stored in memory (spectrum, twiddles) */
+struct __align__(16) dfc {
+    df32 x, y;
 };
-template <> struct V2<float> {
-    using T = float2;
-    static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+
+/* storage and conversions per arithmetic type R: FP64 path (double), FP32C path (float), and the
+ * FP64 path's FFT in double-float (df32: arithmetic in FP32 pairs, grid stored in FP64) */
+template <typename R> struct Tr;
+template <> struct Tr<double> {
+    using G = double;   /* grid value */
+    using G2 = double2; /* two grid values (a packed complex) */
+    using C2 = double2; /* stored complex */
+    static __device__ __forceinline__ cpx<double> from_g2(double2 v) { return mk<double>(v.x, v.y); }
+    static __device__ __forceinline__ double2 to_g2(cpx<double> z) { return make_double2(z.re, z.im); }
+    static __device__ __forceinline__ cpx<double> from_c2(double2 v) { return mk<double>(v.x, v.y); }
+    static __device__ __forceinline__ double2 to_c2(cpx<double> z) { return make_double2(z.re, z.im); }
+    static __device__ __forceinline__ double2 zero_c2() { return make_double2(0.0, 0.0); }
+};
+template <> struct Tr<float> {
+    using G = float;
+    using G2 = float2;
+    using C2 = float2;
+    static __device__ __forceinline__ cpx<float> from_g2(float2 v) { return mk<float>(v.x, v.y); }
+    static __device__ __forceinline__ float2 to_g2(cpx<float> z) { return make_float2(z.re, z.im); }
+    static __device__ __forceinline__ cpx<float> from_c2(float2 v) { return mk<float>(v.x, v.y); }
+    static __device__ __forceinline__ float2 to_c2(cpx<float> z) { return make_float2(z.re, z.im); }
+    static __device__ __forceinline__ float2 zero_c2() { return make_float2(0.0f, 0.0f); }
+};
+template <> struct Tr<df32> {
+    using G = double;
+    using G2 = double2;
+    using C2 = dfc;
+    static __device__ __forceinline__ cpx<df32> from_g2(double2 v) { return mk<df32>(df32(v.x), df32(v.y)); }
+    static __device__ __forceinline__ double2 to_g2(cpx<df32> z)
+    {
+        return make_double2(z.re.to_double(), z.im.to_double());
+    }
+    static __device__ __forceinline__ cpx<df32> from_c2(dfc v) { return mk<df32>(v.x, v.y); }
+    static __device__ __forceinline__ dfc to_c2(cpx<df32> z)
+    {
+        dfc r;
+        r.x = z.re;
+        r.y = z.im;
+        return r;
+    }
+    static __device__ __forceinline__ dfc zero_c2()
+    {
+        dfc r;
+        r.x = df32(0.0f, 0.0f);
+        r.y = df32(0.0f, 0.0f);
+        return r;
+    }
 };
 
 constexpr double kMagic = 6755399441055744.0; /* 1.5 * 2^52: fma(a, b, kMagic) rounds a*b to an integer */
@@ -45,6 +89,35 @@ __device__ __forceinline__ double block_max(double v, double *red)
     return v;
 }
 
+/* FP64 window values of the w taps of a point at grid coordinate t (first tap l0): by Horner on
+ * the per-tap polynomials staged in shared memory (cw, (deg+1) x W), or by the formula */
+template <int W>
+__device__ __forceinline__ void windows64(double *f, int l0, double t, const double *cw, int deg,
+                                          const Geom &g)
+{
+    if (cw) {
+        const double x = 2.0 * (((double)l0 - t) + 0.5 * W) - 1.0;
+#pragma unroll
+        for (int a = 0; a < W; ++a) f[a] = cw[deg * W + a];
+        for (int k = deg - 1; k >= 0; --k) {
+#pragma unroll
+            for (int a = 0; a < W; ++a) f[a] = fma(f[a], x, cw[k * W + a]);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < W; ++a) f[a] = es_window<double>((double)(l0 + a) - t, g.beta, g.c);
+    }
+}
+
+/* copy the window polynomials into shared memory (NULL when the formula is used) */
+__device__ __forceinline__ const double *stage_window(const Inst &d, double *dst)
+{
+    if (!d.win) return nullptr;
+    const int m = (d.wdeg + 1) * d.g.w;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = d.win[i];
+    return dst;
+}
+
 /* ----------------------------------------------------------------------------------------- */
 /* spread (type 1, Section 5.2 eq. disrete_sigma_hat): one output tile per item                */
 
@@ -64,6 +137,7 @@ template <int W> __device__ void st_spread64(const Inst &d, int item, unsigned c
     const double *__restrict__ dens = d.dens;
     double *__restrict__ grid = static_cast<double *>(d.grid);
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) acc[i] = 0ull;
+    const double *cw = stage_window(d, reinterpret_cast<double *>(acc + T * T));
     const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
     double mq = 0.0;
     for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
@@ -87,11 +161,8 @@ template <int W> __device__ void st_spread64(const Inst &d, int item, unsigned c
             const double qs = ldexp(wq[j] * dens[j], kexp);
             const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
             double fx[W], fy[W];
-#pragma unroll
-            for (int a = 0; a < W; ++a) {
-                fx[a] = es_window<double>((double)(lx + a) - t.x, g.beta, g.c);
-                fy[a] = es_window<double>((double)(ly + a) - t.y, g.beta, g.c);
-            }
+            windows64<W>(fx, lx, t.x, cw, d.wdeg, g);
+            windows64<W>(fy, ly, t.y, cw, d.wdeg, g);
             int dx0 = (lx - X0) % g.n;
             if (dx0 < 0) dx0 += g.n;
             int dy0 = (ly - Y0) % g.n;
@@ -222,49 +293,94 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
 /* ----------------------------------------------------------------------------------------- */
 /* FFT passes (mixed-radix DIF in shared memory, see yk_core.h)                               */
 
+/* floor(x / d) with the stage's multiplier (d = 1 when m == 0) */
+__device__ __forceinline__ int fdiv(int x, unsigned m) { return m ? (int)__umulhi((unsigned)x, m) : x; }
+
+/* one DIF stage with a compile-time radix: every butterfly of nrows rows (row stride rowlen) */
+template <int RADIX, bool INV, typename R, typename TW>
+__device__ __forceinline__ void fft_stage(cpx<R> *x, const FftStages &st, int s, const TW *tw,
+                                          int nrows, int rowlen)
+{
+    const int B = st.B[s], span = B / RADIX, nb = st.L / RADIX, step = st.tw_step[s];
+    const unsigned msp = st.span_m[s], mnb = st.nb_m[s];
+    for (int i = threadIdx.x; i < nrows * nb; i += blockDim.x) {
+        const int row = fdiv(i, mnb), t = i - row * nb;
+        const int b = fdiv(t, msp), k = t - b * span;
+        cpx<R> *xr = x + (size_t)row * rowlen + b * B + k;
+        cpx<R> v[RADIX];
+        if (!INV) {
+#pragma unroll
+            for (int q = 0; q < RADIX; ++q) v[q] = xr[q * span];
+            if (RADIX == 2) dft2<-1>(v);
+            else if (RADIX == 3) dft3<-1>(v);
+            else if (RADIX == 4) dft4<-1>(v);
+            else dft5<-1>(v);
+            xr[0] = v[0];
+#pragma unroll
+            for (int p = 1; p < RADIX; ++p) {
+                const TW w = tw[p * k * step];
+                xr[p * span] = mul(v[p], mk<R>((R)w.x, (R)w.y));
+            }
+        } else {
+            v[0] = xr[0];
+#pragma unroll
+            for (int p = 1; p < RADIX; ++p) {
+                const TW w = tw[p * k * step];
+                v[p] = mulc(xr[p * span], mk<R>((R)w.x, (R)w.y));
+            }
+            if (RADIX == 2) dft2<+1>(v);
+            else if (RADIX == 3) dft3<+1>(v);
+            else if (RADIX == 4) dft4<+1>(v);
+            else dft5<+1>(v);
+#pragma unroll
+            for (int q = 0; q < RADIX; ++q) xr[q * span] = v[q];
+        }
+    }
+    __syncthreads();
+}
+
+template <bool INV, typename R, typename TW>
+__device__ __forceinline__ void fft_stage_any(cpx<R> *x, const FftStages &st, int s, const TW *tw,
+                                              int nrows, int rowlen)
+{
+    switch (st.r[s]) {
+    case 2: fft_stage<2, INV, R>(x, st, s, tw, nrows, rowlen); break;
+    case 3: fft_stage<3, INV, R>(x, st, s, tw, nrows, rowlen); break;
+    case 4: fft_stage<4, INV, R>(x, st, s, tw, nrows, rowlen); break;
+    default: fft_stage<5, INV, R>(x, st, s, tw, nrows, rowlen); break;
+    }
+}
+
 template <typename R, typename TW>
 __device__ __forceinline__ void fft_fwd(cpx<R> *x, const FftStages &st, const TW *tw, int nrows,
                                         int rowlen)
 {
-    for (int s = 0; s < st.n; ++s) {
-        const int nb = st.L / st.r[s];
-        for (int i = threadIdx.x; i < nrows * nb; i += blockDim.x) {
-            const int r = i / nb, t = i - r * nb;
-            dif_butterfly<R>(x + (size_t)r * rowlen, st, s, t, tw, 1);
-        }
-        __syncthreads();
-    }
+    for (int s = 0; s < st.n; ++s) fft_stage_any<false, R>(x, st, s, tw, nrows, rowlen);
 }
 
 template <typename R, typename TW>
 __device__ __forceinline__ void fft_inv(cpx<R> *x, const FftStages &st, const TW *tw, int nrows,
                                         int rowlen)
 {
-    for (int s = st.n - 1; s >= 0; --s) {
-        const int nb = st.L / st.r[s];
-        for (int i = threadIdx.x; i < nrows * nb; i += blockDim.x) {
-            const int r = i / nb, t = i - r * nb;
-            idif_butterfly<R>(x + (size_t)r * rowlen, st, s, t, tw, 1);
-        }
-        __syncthreads();
-    }
+    for (int s = st.n - 1; s >= 0; --s) fft_stage_any<true, R>(x, st, s, tw, nrows, rowlen);
 }
 
 /* rows [item*rows, ...): real-to-complex FFT, keep m_x <= M, store transposed spec[m_x*n + y] */
 template <typename R> __device__ void st_row_fwd(const Inst &d, int item, unsigned char *sm)
 {
-    using C2 = typename V2<R>::T;
+    using T = Tr<R>;
+    using C2 = typename T::C2;
+    using G2 = typename T::G2;
     cpx<R> *x = reinterpret_cast<cpx<R> *>(sm);
     const int n = d.n, M = d.M, L = n >> 1;
-    const R *__restrict__ grid = static_cast<const R *>(d.grid);
+    const typename T::G *__restrict__ grid = static_cast<const typename T::G *>(d.grid);
     C2 *__restrict__ spec = static_cast<C2 *>(d.spec);
     const C2 *__restrict__ tw = static_cast<const C2 *>(d.tw);
     const int y0 = item * d.rows;
     const int nr = min(d.rows, n - y0);
     for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
         const int r = i / L, l = i - r * L;
-        const C2 v = reinterpret_cast<const C2 *>(grid + (size_t)(y0 + r) * n)[l];
-        x[i] = mk<R>(v.x, v.y);
+        x[i] = T::from_g2(reinterpret_cast<const G2 *>(grid + (size_t)(y0 + r) * n)[l]);
     }
     __syncthreads();
     fft_fwd<R>(x, d.sth, tw, nr, L);
@@ -272,9 +388,7 @@ template <typename R> __device__ void st_row_fwd(const Inst &d, int item, unsign
         const int m = i / nr, r = i - m * nr;
         const cpx<R> Zm = x[r * L + d.perm_h[m]];
         const cpx<R> Zc = x[r * L + d.perm_h[m == 0 ? 0 : L - m]];
-        const C2 wm = tw[m];
-        const cpx<R> X = r2c_post<R>(Zm, Zc, mk<R>(wm.x, wm.y));
-        spec[(size_t)m * n + y0 + r] = V2<R>::make(X.re, X.im);
+        spec[(size_t)m * n + y0 + r] = T::to_c2(r2c_post<R>(Zm, Zc, T::from_c2(tw[m])));
     }
     __syncthreads();
 }
@@ -283,15 +397,13 @@ template <typename R> __device__ void st_row_fwd(const Inst &d, int item, unsign
  * inverse FFT along y, in place */
 template <typename R> __device__ void st_columns(const Inst &d, int item, unsigned char *sm)
 {
-    using C2 = typename V2<R>::T;
+    using T = Tr<R>;
+    using C2 = typename T::C2;
     cpx<R> *x = reinterpret_cast<cpx<R> *>(sm);
     const int n = d.n, M = d.M, kx = item;
     const C2 *__restrict__ tw = static_cast<const C2 *>(d.tw);
     C2 *col = static_cast<C2 *>(d.spec) + (size_t)kx * n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const C2 v = col[i];
-        x[i] = mk<R>(v.x, v.y);
-    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = T::from_c2(col[i]);
     __syncthreads();
     fft_fwd<R>(x, d.stf, tw, 1, n);
     const R *mrow = static_cast<const R *>(d.mult) + (size_t)kx * (2 * M + 1);
@@ -299,39 +411,39 @@ template <typename R> __device__ void st_columns(const Inst &d, int item, unsign
         const int m = d.iperm_f[i];
         const int my = m <= (n >> 1) ? m : m - n;
         if (my >= -M && my <= M) x[i] = scale(x[i], mrow[my + M]);
-        else x[i] = mk<R>((R)0, (R)0);
+        else x[i] = T::from_c2(T::zero_c2());
     }
     __syncthreads();
     fft_inv<R>(x, d.stf, tw, 1, n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = V2<R>::make(x[i].re, x[i].im);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = T::to_c2(x[i]);
     __syncthreads();
 }
 
 /* rows [item*rows, ...): gather m_x <= M, complex-to-real inverse FFT, write the real rows */
 template <typename R> __device__ void st_row_inv(const Inst &d, int item, unsigned char *sm)
 {
-    using C2 = typename V2<R>::T;
+    using T = Tr<R>;
+    using C2 = typename T::C2;
+    using G2 = typename T::G2;
     cpx<R> *x = reinterpret_cast<cpx<R> *>(sm);
     const int n = d.n, M = d.M, L = n >> 1;
     const C2 *__restrict__ spec = static_cast<const C2 *>(d.spec);
     const C2 *__restrict__ tw = static_cast<const C2 *>(d.tw);
-    R *__restrict__ grid = static_cast<R *>(d.grid);
+    typename T::G *__restrict__ grid = static_cast<typename T::G *>(d.grid);
     const int y0 = item * d.rows;
     const int nr = min(d.rows, n - y0);
     for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
         const int m = i / nr, r = i - m * nr;
         const int mc = L - m; /* in (0, L]; X[L] is zero because M < L */
-        C2 a = V2<R>::make((R)0, (R)0), b = V2<R>::make((R)0, (R)0);
-        if (m <= M) a = spec[(size_t)m * n + y0 + r];
-        if (mc <= M) b = spec[(size_t)mc * n + y0 + r];
-        const C2 wm = tw[m];
-        x[r * L + d.perm_h[m]] = c2r_pre<R>(mk<R>(a.x, a.y), mk<R>(b.x, b.y), mk<R>(wm.x, wm.y));
+        const C2 a = m <= M ? spec[(size_t)m * n + y0 + r] : T::zero_c2();
+        const C2 b = mc <= M ? spec[(size_t)mc * n + y0 + r] : T::zero_c2();
+        x[r * L + d.perm_h[m]] = c2r_pre<R>(T::from_c2(a), T::from_c2(b), T::from_c2(tw[m]));
     }
     __syncthreads();
     fft_inv<R>(x, d.sth, tw, nr, L);
     for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
         const int r = i / L, l = i - r * L;
-        reinterpret_cast<C2 *>(grid + (size_t)(y0 + r) * n)[l] = V2<R>::make(x[i].re, x[i].im);
+        reinterpret_cast<G2 *>(grid + (size_t)(y0 + r) * n)[l] = T::to_g2(x[i]);
     }
     __syncthreads();
 }
@@ -363,16 +475,14 @@ template <int W> __device__ void st_interp64(const Inst &d, int item, unsigned c
     if (beg == end) return; /* uniform across the CTA */
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;
     stage_halo<double>(sg, static_cast<const double *>(d.grid), g, X0, Y0, P);
+    const double *cw = stage_window(d, sg + P * P);
     __syncthreads();
     for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
         const double2 t = d.trg_t[e];
         const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
         double fx[W], fy[W];
-#pragma unroll
-        for (int a = 0; a < W; ++a) {
-            fx[a] = es_window<double>((double)(lx + a) - t.x, g.beta, g.c);
-            fy[a] = es_window<double>((double)(ly + a) - t.y, g.beta, g.c);
-        }
+        windows64<W>(fx, lx, t.x, cw, d.wdeg, g);
+        windows64<W>(fy, ly, t.y, cw, d.wdeg, g);
         const double *base = sg + (ly - Y0) * P + (lx - X0);
         double acc = 0.0;
 #pragma unroll
@@ -458,9 +568,18 @@ __device__ __forceinline__ void run_stage<double>(const Inst &d, int stage, int 
         YK_W_SWITCH(d.g.w, YK_C)
 #undef YK_C
     } break;
-    case ST_ROW_FWD: st_row_fwd<double>(d, item, sm); break;
-    case ST_COLUMNS: st_columns<double>(d, item, sm); break;
-    case ST_ROW_INV: st_row_inv<double>(d, item, sm); break;
+    case ST_ROW_FWD:
+        if (d.fft_df) st_row_fwd<df32>(d, item, sm);
+        else st_row_fwd<double>(d, item, sm);
+        break;
+    case ST_COLUMNS:
+        if (d.fft_df) st_columns<df32>(d, item, sm);
+        else st_columns<double>(d, item, sm);
+        break;
+    case ST_ROW_INV:
+        if (d.fft_df) st_row_inv<df32>(d, item, sm);
+        else st_row_inv<double>(d, item, sm);
+        break;
     default: {
 #define YK_C(W) st_interp64<W>(d, item, sm)
         YK_W_SWITCH(d.g.w, YK_C)

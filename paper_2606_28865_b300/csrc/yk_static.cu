@@ -160,6 +160,7 @@ bool stages_for(int L, int n_tab, yk::FftStages &st)
         st.tw_step[i] = n_tab / B;
         B /= st.r[i];
     }
+    yk::fft_fill_magic(st);
     return true;
 }
 

@@ -193,3 +193,19 @@ def test_config_large_sampled(alpha):
                             work.yt[idx])
     err = rel_err(u[idx], ref)
     assert err <= TOL64, f"alpha={alpha} err={err:.3e} info={info}"
+
+
+@pytest.mark.parametrize("alpha", [10.0, 1.0])
+def test_fft_arithmetic_modes_agree(alpha):
+    """The FP64 path's FFT passes run in double-float by default; the FP64-arithmetic variant
+    must give the same potentials to well below the 1e-10 tolerance, and both match the oracle."""
+    work = W.config_large(alpha)
+    u_df, info = run_gpu(work, alpha)
+    u_64, _ = run_gpu(work, alpha, fft_fp64=True)
+    scale = np.max(np.abs(u_64))
+    assert np.max(np.abs(u_df - u_64)) <= 1e-12 * scale
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(work.n_trg, 300, replace=False))
+    ref = oracle.direct_sum(alpha, info["delta"], work.xs, work.ys, work.q, work.xt[idx],
+                            work.yt[idx])
+    assert rel_err(u_df[idx], ref) <= TOL64
