@@ -453,7 +453,8 @@ def main():
     gbs = work_b[dom] / t_dom / 1e9
     tfl = work_f[dom] / t_dom / 1e12
     traffic = load_traffic().get(dom)
-    df_stage = dom in ("row_fwd", "columns", "row_inv")  # FP64 path FFTs run in FP32 pairs
+    # the FP64 path computes spread, FFTs and interpolation in FP32 pairs (double-float)
+    df_stage = dom in ("spread", "row_fwd", "columns", "row_inv", "interp")
     alu_peak = fp32_peak / DF_COST if df_stage else fp64_peak
     if tfl / alu_peak >= gbs / hbm_peak:
         roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",

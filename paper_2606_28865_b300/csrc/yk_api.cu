@@ -194,11 +194,13 @@ double window_ft(double xi, int w, double beta)
 /* per-tap window polynomials: tap a covers z = u - w/2 + a, u in [0, 1); with x = 2u - 1 the
  * window there is interpolated at deg+1 Chebyshev points and the series converted to powers of
  * x, all in long double; out[k * w + a] = coefficient of x^k for tap a */
-void window_polys(int w, double beta, int deg, std::vector<double> &out)
+void window_polys(int w, double beta, int deg, std::vector<double> &out,
+                  std::vector<float2> &out_df)
 {
     const int m = deg + 1;
     const long double pi = 3.14159265358979323846264338327950288L;
     out.assign((size_t)m * w, 0.0);
+    out_df.assign((size_t)m * w, make_float2(0.0f, 0.0f));
     for (int a = 0; a < w; ++a) {
         std::vector<long double> f(m), c(m, 0.0L), mono(m, 0.0L), t0(m, 0.0L), t1(m, 0.0L), t2(m);
         for (int j = 0; j < m; ++j) {
@@ -223,7 +225,11 @@ void window_polys(int w, double beta, int deg, std::vector<double> &out)
             t0 = t1;
             t1 = t2;
         }
-        for (int k = 0; k < m; ++k) out[(size_t)k * w + a] = (double)mono[k];
+        for (int k = 0; k < m; ++k) {
+            out[(size_t)k * w + a] = (double)mono[k];
+            const float hi = (float)mono[k];
+            out_df[(size_t)k * w + a] = make_float2(hi, (float)(mono[k] - (long double)hi));
+        }
     }
 }
 
@@ -327,6 +333,7 @@ void buf_free(yk_plan_t p, DevBuf &b)
 void free_all(yk_plan_t p)
 {
     DevBuf *all[] = {&p->grid, &p->spec, &p->mult, &p->tw, &p->perm_h, &p->iperm_f, &p->win,
+                     &p->win_df,
                      &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->tile_order, &p->trg_cnt,
                      &p->trg_ptr,
                      &p->trg_cur, &p->err, &p->w_src, &p->src_t, &p->ent_t, &p->ent_j,
@@ -484,10 +491,16 @@ yk_status plan_tables(yk_plan_t p)
         /* FP64 windows as per-tap polynomials of degree w + 1 */
         p->wdeg = p->w + 1;
         std::vector<double> poly;
-        window_polys(p->w, p->beta, p->wdeg, poly);
+        std::vector<float2> poly_df;
+        window_polys(p->w, p->beta, p->wdeg, poly, poly_df);
         if ((s = buf_alloc(p, p->win, sizeof(double) * poly.size(), "window")) != YK_OK) return s;
+        if ((s = buf_alloc(p, p->win_df, sizeof(float2) * poly_df.size(), "window")) != YK_OK)
+            return s;
         cudaError_t ew = cudaMemcpy(p->win.ptr, poly.data(), sizeof(double) * poly.size(),
                                     cudaMemcpyHostToDevice);
+        if (ew == cudaSuccess)
+            ew = cudaMemcpy(p->win_df.ptr, poly_df.data(), sizeof(float2) * poly_df.size(),
+                            cudaMemcpyHostToDevice);
         if (ew != cudaSuccess) return cuda_fail(ew, "window table");
     }
     DevBuf d_dfac = {nullptr, 0};
@@ -555,6 +568,7 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->perm_h = P<int>(p->perm_h);
     d->iperm_f = P<int>(p->iperm_f);
     d->win = P<double>(p->win);
+    d->win_df = P<float2>(p->win_df);
     d->wdeg = p->wdeg;
     for (int s = 0; s < yk::ST_COUNT; ++s) {
         d->items[s] = yk::stage_items(*d, s);
@@ -651,7 +665,8 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
         if (o->tile > 0) {
             if (n % o->tile == 0 && o->tile >= w && n >= 2 * o->tile) T = o->tile;
         } else {
-            const int tmax = o->precision == YK_FP32C ? 32 : 64;
+            /* per-warp private tiles (FP32C and the double-float FP64 spread) need T <= 32 */
+            const int tmax = (o->precision == YK_FP32C || !o->fft_fp64) ? 32 : 64;
             const int pref = o->use_tuned ? yk_tuned_tile(o->precision, w, n, o->n_src_hint) : 0;
             for (int t = tmax; t >= w; --t)
                 if (n % t == 0 && n >= 2 * t) {

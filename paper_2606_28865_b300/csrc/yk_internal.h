@@ -59,6 +59,7 @@ struct Inst {
                                  x^k for tap a, x = 2u - 1, u = l0 - t + w/2 in [0, 1); NULL: the
                                  window formula is evaluated directly */
     int wdeg;                 /* polynomial degree */
+    const float2 *win_df;     /* the same coefficients as FP32 pairs (hi, lo), double-float path */
     int items[ST_COUNT];      /* work items of each stage */
     int smem[ST_COUNT];       /* dynamic shared memory of each stage (bytes) */
 };
@@ -154,6 +155,7 @@ struct yk_plan_s {
     DevBuf perm_h;   /* int[n/2]: DIF position of frequency m (half-length transform) */
     DevBuf iperm_f;  /* int[n]: frequency held at DIF position i (full-length transform) */
     DevBuf win;      /* double[(wdeg+1) * w]: window polynomials of the FP64 path */
+    DevBuf win_df;   /* float2[(wdeg+1) * w]: the same as FP32 pairs (double-float path) */
     int wdeg;
     DevBuf tile_cnt, tile_ptr, tile_cur; /* int[nt^2], int[nt^2+1], int[nt^2] (sources) */
     DevBuf tile_order; /* int[nt^2]: heavy-first processing order of the source tiles */

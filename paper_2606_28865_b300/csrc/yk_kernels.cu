@@ -203,17 +203,27 @@ template <int W> __global__ void __launch_bounds__(32 * kSpreadWarps) k_spread32
     extern __shared__ __align__(16) unsigned char sm[];
     st_spread32<W>(d, blockIdx.x, sm);
 }
-template <typename R> __global__ void __launch_bounds__(256) k_row_fwd(Inst d)
+template <int W> __global__ void __launch_bounds__(32 * kSpreadWarps) k_spread_df(Inst d)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_spread_df<W>(d, blockIdx.x, sm);
+}
+template <int W> __global__ void __launch_bounds__(256) k_interp_df(Inst d)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_interp_df<W>(d, blockIdx.x, sm);
+}
+template <typename R> __global__ void __launch_bounds__(512) k_row_fwd(Inst d)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     st_row_fwd<R>(d, blockIdx.x, sm);
 }
-template <typename R> __global__ void __launch_bounds__(512) k_columns(Inst d)
+template <typename R> __global__ void __launch_bounds__(1024) k_columns(Inst d)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     st_columns<R>(d, blockIdx.x, sm);
 }
-template <typename R> __global__ void __launch_bounds__(256) k_row_inv(Inst d)
+template <typename R> __global__ void __launch_bounds__(512) k_row_inv(Inst d)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     st_row_inv<R>(d, blockIdx.x, sm);
@@ -294,13 +304,19 @@ int stage_smem(const Inst &d, int stage)
     const int c = d.f32 ? 8 : 16; /* bytes of a complex value */
     switch (stage) {
     case ST_SPREAD:
+        if (d.fft_df)
+            return (int)(sizeof(df32) * kSpreadWarps * T * (T + 1) +
+                         sizeof(df32) * kSpreadWarps * 32 * 2 * W + sizeof(int) * kSpreadWarps * 64 +
+                         sizeof(df32) * (d.wdeg + 1) * W);
         return d.f32 ? (int)(sizeof(float2) * kSpreadWarps * T * (T + 1) +
                              sizeof(float) * kSpreadWarps * 32 * 2 * W + sizeof(int) * kSpreadWarps * 64)
                      : (int)(sizeof(unsigned long long) * T * T + win_bytes);
     case ST_ROW_FWD:
     case ST_ROW_INV: return c * d.rows * (d.n / 2);
     case ST_COLUMNS: return c * d.n;
-    default: return d.f32 ? 4 * (T + W) * (T + W) : 8 * (T + W) * (T + W) + win_bytes;
+    default:
+        if (d.fft_df) return 8 * (T + W) * (T + W) + (int)sizeof(df32) * (d.wdeg + 1) * W;
+        return d.f32 ? 4 * (T + W) * (T + W) : 8 * (T + W) * (T + W) + win_bytes;
     }
 }
 
@@ -458,13 +474,13 @@ cudaError_t launch_fft_t(int stage, const void *grid_in, void *grid_out, void *s
     cudaError_t e = cudaSuccess;
     if (stage == ST_ROW_FWD) {
         if ((e = set_smem(k_row_fwd<R>, smem)) != cudaSuccess) return e;
-        k_row_fwd<R><<<items, 256, smem, st>>>(d);
+        k_row_fwd<R><<<items, 512, smem, st>>>(d);
     } else if (stage == ST_COLUMNS) {
         if ((e = set_smem(k_columns<R>, smem)) != cudaSuccess) return e;
-        k_columns<R><<<items, 512, smem, st>>>(d);
+        k_columns<R><<<items, 1024, smem, st>>>(d);
     } else {
         if ((e = set_smem(k_row_inv<R>, smem)) != cudaSuccess) return e;
-        k_row_inv<R><<<items, 256, smem, st>>>(d);
+        k_row_inv<R><<<items, 512, smem, st>>>(d);
     }
     return cudaGetLastError();
 }
@@ -570,6 +586,10 @@ cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st)
 #define YK_CALL(W) YK_LAUNCH(k_spread32<W>, 32 * kSpreadWarps)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
+        } else if (d.fft_df) {
+#define YK_CALL(W) YK_LAUNCH(k_spread_df<W>, 32 * kSpreadWarps)
+            YK_W_DISPATCH(d.g.w, YK_CALL)
+#undef YK_CALL
         } else {
 #define YK_CALL(W) YK_LAUNCH(k_spread<W>, 256)
             YK_W_DISPATCH(d.g.w, YK_CALL)
@@ -577,23 +597,27 @@ cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st)
         }
         break;
     case ST_ROW_FWD:
-        if (d.f32) YK_LAUNCH(k_row_fwd<float>, 256);
-        else if (d.fft_df) YK_LAUNCH(k_row_fwd<df32>, 256);
-        else YK_LAUNCH(k_row_fwd<double>, 256);
+        if (d.f32) YK_LAUNCH(k_row_fwd<float>, 512);
+        else if (d.fft_df) YK_LAUNCH(k_row_fwd<df32>, 512);
+        else YK_LAUNCH(k_row_fwd<double>, 512);
         break;
     case ST_COLUMNS:
-        if (d.f32) YK_LAUNCH(k_columns<float>, 512);
-        else if (d.fft_df) YK_LAUNCH(k_columns<df32>, 512);
-        else YK_LAUNCH(k_columns<double>, 512);
+        if (d.f32) YK_LAUNCH(k_columns<float>, 1024);
+        else if (d.fft_df) YK_LAUNCH(k_columns<df32>, 1024);
+        else YK_LAUNCH(k_columns<double>, 1024);
         break;
     case ST_ROW_INV:
-        if (d.f32) YK_LAUNCH(k_row_inv<float>, 256);
-        else if (d.fft_df) YK_LAUNCH(k_row_inv<df32>, 256);
-        else YK_LAUNCH(k_row_inv<double>, 256);
+        if (d.f32) YK_LAUNCH(k_row_inv<float>, 512);
+        else if (d.fft_df) YK_LAUNCH(k_row_inv<df32>, 512);
+        else YK_LAUNCH(k_row_inv<double>, 512);
         break;
     default:
         if (d.f32) {
 #define YK_CALL(W) YK_LAUNCH(k_interp32<W>, 256)
+            YK_W_DISPATCH(d.g.w, YK_CALL)
+#undef YK_CALL
+        } else if (d.fft_df) {
+#define YK_CALL(W) YK_LAUNCH(k_interp_df<W>, 256)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
         } else {

@@ -44,13 +44,16 @@ template <> struct Tr<float> {
     static __device__ __forceinline__ float2 zero_c2() { return make_float2(0.0f, 0.0f); }
 };
 template <> struct Tr<df32> {
-    using G = double;
-    using G2 = double2;
+    using G = df32; /* the FP64 path's grid holds FP32 pairs in its 8-byte cells */
+    using G2 = dfc;
     using C2 = dfc;
-    static __device__ __forceinline__ cpx<df32> from_g2(double2 v) { return mk<df32>(df32(v.x), df32(v.y)); }
-    static __device__ __forceinline__ double2 to_g2(cpx<df32> z)
+    static __device__ __forceinline__ cpx<df32> from_g2(dfc v) { return mk<df32>(v.x, v.y); }
+    static __device__ __forceinline__ dfc to_g2(cpx<df32> z)
     {
-        return make_double2(z.re.to_double(), z.im.to_double());
+        dfc r;
+        r.x = z.re;
+        r.y = z.im;
+        return r;
     }
     static __device__ __forceinline__ cpx<df32> from_c2(dfc v) { return mk<df32>(v.x, v.y); }
     static __device__ __forceinline__ dfc to_c2(cpx<df32> z)
@@ -107,6 +110,31 @@ __device__ __forceinline__ void windows64(double *f, int l0, double t, const dou
 #pragma unroll
         for (int a = 0; a < W; ++a) f[a] = es_window<double>((double)(l0 + a) - t, g.beta, g.c);
     }
+}
+
+/* double-float window values of the w taps at x = 2u - 1 (u = l0 - t + w/2), Horner on the
+ * per-tap polynomials cw ((deg+1) x W double-float coefficients in shared memory) */
+template <int W>
+__device__ __forceinline__ df32 window_df(const df32 *cw, int deg, int a, df32 x)
+{
+    df32 p = cw[deg * W + a];
+    for (int k = deg - 1; k >= 0; --k) p = p * x + cw[k * W + a];
+    return p;
+}
+
+__device__ __forceinline__ df32 window_arg_df(int l0, double t, int W)
+{
+    return df32(2.0 * (((double)l0 - t) + 0.5 * W) - 1.0);
+}
+
+__device__ __forceinline__ df32 *stage_window_df(const Inst &d, df32 *dst)
+{
+    const int m = (d.wdeg + 1) * d.g.w;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const float2 c = d.win_df[i];
+        dst[i] = df32(c.x, c.y);
+    }
+    return dst;
 }
 
 /* copy the window polynomials into shared memory (NULL when the formula is used) */
@@ -213,10 +241,15 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
     const int X0 = txi * T, Y0 = tyi * T;
     const int4 *__restrict__ ent = reinterpret_cast<const int4 *>(d.ent_t);
     float *__restrict__ grid = static_cast<float *>(d.grid);
+    const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
+    if (beg == end) { /* no window reaches this tile */
+        for (int i = threadIdx.x; i < T * T; i += blockDim.x)
+            grid[(size_t)(Y0 + i / T) * g.n + X0 + i % T] = 0.0f;
+        return;
+    }
     for (int i = threadIdx.x; i < kSpreadWarps * T * PT; i += blockDim.x)
         acc[i] = make_float2(0.0f, 0.0f);
     __syncthreads();
-    const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2 *mine = acc + warp * T * PT;
     float *wb = wbuf + warp * 32 * 2 * W;
@@ -286,6 +319,86 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
             hi = s;
         }
         grid[(size_t)(Y0 + rr) * g.n + X0 + cc] = hi + lo;
+    }
+    __syncthreads();
+}
+
+/* FP64 path, double-float arithmetic: the FP32C scheme with FP32 pairs.  Each warp owns a
+ * private double-float copy of the tile; it evaluates the windows of 32 entries (lane per entry,
+ * Horner in double-float), then walks them one entry at a time with one lane per tap and adds the
+ * double-float products into its copy; the copies are summed in warp order and the tile is
+ * written as FP32 pairs.  Uses blockDim.x / 32 <= kSpreadWarps warps. */
+template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned char *sm)
+{
+    const Geom &g = d.g;
+    const int T = g.T, PT = T + 1, D = d.wdeg;
+    const int NW = blockDim.x >> 5;
+    df32 *acc = reinterpret_cast<df32 *>(sm);                        /* [warps][T][PT] */
+    df32 *wbuf = acc + kSpreadWarps * T * PT;                        /* [warps][32][2W] */
+    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * 2 * W); /* [warps][64] */
+    const int tile = d.order ? d.order[item] : item;
+    const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
+    const int X0 = txi * T, Y0 = tyi * T;
+    df32 *__restrict__ grid = static_cast<df32 *>(d.grid);
+    const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
+    if (beg == end) { /* no window reaches this tile */
+        for (int i = threadIdx.x; i < T * T; i += blockDim.x)
+            grid[(size_t)(Y0 + i / T) * g.n + X0 + i % T] = df32(0.0f, 0.0f);
+        return;
+    }
+    df32 *cw = stage_window_df(d, reinterpret_cast<df32 *>(obuf + kSpreadWarps * 64));
+    for (int i = threadIdx.x; i < NW * T * PT; i += blockDim.x) acc[i] = df32(0.0f, 0.0f);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    df32 *mine = acc + warp * T * PT;
+    df32 *wb = wbuf + warp * 32 * 2 * W;
+    int *ob = obuf + warp * 64;
+    for (int b0 = beg + warp * 32; b0 < end; b0 += NW * 32) {
+        const int e = b0 + lane;
+        if (e < end) {
+            const double2 t = d.ent_t[e];
+            const int j = d.ent_j[e];
+            const df32 q(d.wq[j] * d.dens[j]);
+            const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
+            const df32 ax = window_arg_df(lx, t.x, W), ay = window_arg_df(ly, t.y, W);
+            for (int a = 0; a < W; ++a) {
+                wb[lane * 2 * W + a] = q * window_df<W>(cw, D, a, ay);
+                wb[lane * 2 * W + W + a] = window_df<W>(cw, D, a, ax);
+            }
+            int dx0 = (lx - X0) % g.n;
+            if (dx0 < 0) dx0 += g.n;
+            int dy0 = (ly - Y0) % g.n;
+            if (dy0 < 0) dy0 += g.n;
+            ob[2 * lane] = dx0;
+            ob[2 * lane + 1] = dy0;
+        }
+        __syncwarp();
+        const int cnt = min(32, end - b0);
+        for (int k = 0; k < cnt; ++k) {
+            const int dx0 = ob[2 * k], dy0 = ob[2 * k + 1];
+            const df32 *wk = wb + k * 2 * W;
+#pragma unroll
+            for (int t0 = 0; t0 < W * W; t0 += 32) {
+                const int t = t0 + lane;
+                if (t < W * W) {
+                    const int c = t / W, a = t - c * W;
+                    int yy = dy0 + c;
+                    if (yy >= g.n) yy -= g.n;
+                    int xx = dx0 + a;
+                    if (xx >= g.n) xx -= g.n;
+                    if (yy < T && xx < T) mine[yy * PT + xx] = mine[yy * PT + xx] + wk[c] * wk[W + a];
+                }
+            }
+            __syncwarp(); /* the next entry may touch the same cells through other lanes */
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
+        const int rr = i / T, cc = i - rr * T;
+        df32 sum = acc[rr * PT + cc];
+        for (int w = 1; w < NW; ++w) sum = sum + acc[w * T * PT + rr * PT + cc];
+        grid[(size_t)(Y0 + rr) * g.n + X0 + cc] = sum;
     }
     __syncthreads();
 }
@@ -534,6 +647,42 @@ template <int W> __device__ void st_interp32(const Inst &d, int item, unsigned c
     __syncthreads();
 }
 
+/* FP64 path, double-float arithmetic: windows and tap sums in FP32 pairs, one conversion to
+ * double per target */
+template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned char *sm)
+{
+    const Geom &g = d.g;
+    const int T = g.T, P = T + W, lo = W / 2;
+    df32 *sg = reinterpret_cast<df32 *>(sm);
+    const int tyi = item / g.nt, txi = item - tyi * g.nt;
+    const int beg = d.trg_ptr[item], end = d.trg_ptr[item + 1];
+    if (beg == end) return;
+    const int X0 = txi * T - lo, Y0 = tyi * T - lo;
+    stage_halo<df32>(sg, static_cast<const df32 *>(d.grid), g, X0, Y0, P);
+    const df32 *cw = stage_window_df(d, sg + P * P);
+    __syncthreads();
+    const int D = d.wdeg;
+    for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
+        const double2 t = d.trg_t[e];
+        const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
+        const df32 ax = window_arg_df(lx, t.x, W), ay = window_arg_df(ly, t.y, W);
+        df32 fx[W];
+#pragma unroll
+        for (int a = 0; a < W; ++a) fx[a] = window_df<W>(cw, D, a, ax);
+        const df32 *base = sg + (ly - Y0) * P + (lx - X0);
+        df32 acc(0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < W; ++c) {
+            df32 row = fx[0] * base[c * P];
+#pragma unroll
+            for (int a = 1; a < W; ++a) row = row + fx[a] * base[c * P + a];
+            acc = acc + window_df<W>(cw, D, c, ay) * row;
+        }
+        d.u[d.trg_idx[e]] = acc.to_double();
+    }
+    __syncthreads();
+}
+
 /* window width as a template parameter */
 #define YK_W_SWITCH(W_, CALL)                                                                    \
     switch (W_) {                                                                                \
@@ -563,11 +712,17 @@ __device__ __forceinline__ void run_stage<double>(const Inst &d, int stage, int 
                                                   unsigned char *sm)
 {
     switch (stage) {
-    case ST_SPREAD: {
-#define YK_C(W) st_spread64<W>(d, item, sm)
-        YK_W_SWITCH(d.g.w, YK_C)
+    case ST_SPREAD:
+        if (d.fft_df) {
+#define YK_C(W) st_spread_df<W>(d, item, sm)
+            YK_W_SWITCH(d.g.w, YK_C)
 #undef YK_C
-    } break;
+        } else {
+#define YK_C(W) st_spread64<W>(d, item, sm)
+            YK_W_SWITCH(d.g.w, YK_C)
+#undef YK_C
+        }
+        break;
     case ST_ROW_FWD:
         if (d.fft_df) st_row_fwd<df32>(d, item, sm);
         else st_row_fwd<double>(d, item, sm);
@@ -580,11 +735,17 @@ __device__ __forceinline__ void run_stage<double>(const Inst &d, int stage, int 
         if (d.fft_df) st_row_inv<df32>(d, item, sm);
         else st_row_inv<double>(d, item, sm);
         break;
-    default: {
-#define YK_C(W) st_interp64<W>(d, item, sm)
-        YK_W_SWITCH(d.g.w, YK_C)
+    default:
+        if (d.fft_df) {
+#define YK_C(W) st_interp_df<W>(d, item, sm)
+            YK_W_SWITCH(d.g.w, YK_C)
 #undef YK_C
-    } break;
+        } else {
+#define YK_C(W) st_interp64<W>(d, item, sm)
+            YK_W_SWITCH(d.g.w, YK_C)
+#undef YK_C
+        }
+        break;
     }
 }
 

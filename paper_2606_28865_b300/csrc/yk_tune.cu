@@ -64,7 +64,7 @@ YK_API yk_status yk_autotune(double alpha, const yk_opts *o, int64_t n_src, cons
     if (s != YK_OK) return s;
     if (info.n_grid == 0 || n_src == 0 || n_trg == 0) return YK_OK; /* nothing to tune */
     const int64_t n = info.n_grid;
-    const int tmax = o->precision == YK_FP32C ? 32 : 64;
+    const int tmax = (o->precision == YK_FP32C || !o->fft_fp64) ? 32 : 64;
     std::vector<int> cand;
     for (int t = tmax; t >= info.w && (int)cand.size() < YK_TUNE_MAX; --t)
         if (n % t == 0 && n >= 2 * t) cand.push_back(t);

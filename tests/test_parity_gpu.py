@@ -95,11 +95,13 @@ def test_deterministic_and_host_device_equivalence(small):
     plan.set_points(dev(small.xs), dev(small.ys), dev(small.w), dev(small.xt), dev(small.yt))
     u1 = plan.eval(dev(small.density)).cpu().numpy()
     u2 = plan.eval(dev(small.density)).cpu().numpy()
-    assert np.array_equal(u1, u2)  # fixed-point accumulation: bitwise repeatable
-    # host arrays in and out through the same ABI
+    assert np.array_equal(u1, u2)  # same layout: bitwise repeatable
+    # host arrays in and out through the same ABI; binning again may order the sources of a
+    # tile differently, and the double-float tile sums then round differently (~1e-15)
     plan.set_points(small.xs, small.ys, small.w, small.xt, small.yt)
     u3 = plan.eval(small.density)
-    assert isinstance(u3, np.ndarray) and np.array_equal(u1, u3)
+    assert isinstance(u3, np.ndarray)
+    assert np.max(np.abs(u1 - u3)) <= 1e-13 * np.max(np.abs(u1))
     # new densities on the resident layout (a Rothe step): linear in the density
     d2 = W.strengths_for(small, alpha, seed=3)
     ua = plan.eval(dev(d2)).cpu().numpy()
@@ -115,8 +117,12 @@ def test_permuted_points_give_the_same_values(small):
                     small.density[ps], small.xt[pt], small.yt[pt], 0, small.h_vol)
     u, _ = run_gpu(small, 10.0)
     v, _ = run_gpu(w2, 10.0)
-    # exact per-tile fixed-point sums: the order of the sources does not change a single bit
-    assert np.array_equal(u[pt], v)
+    # the order of the sources only changes rounding in the tile sums
+    assert np.max(np.abs(u[pt] - v)) <= 1e-13 * np.max(np.abs(u))
+    # with FP64 arithmetic the tile sums are exact 64-bit fixed point: not a single bit changes
+    u64, _ = run_gpu(small, 10.0, fft_fp64=True)
+    v64, _ = run_gpu(w2, 10.0, fft_fp64=True)
+    assert np.array_equal(u64[pt], v64)
 
 
 def test_edge_cases(small):
