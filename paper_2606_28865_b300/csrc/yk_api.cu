@@ -449,7 +449,8 @@ yk_status plan_tables(yk_plan_t p)
     YK_TRY(buf_alloc(p, p->iperm_f, sizeof(int) * n, "permutation"));
     YK_TRY(buf_alloc(p, p->tile_cnt, sizeof(int) * nt2, "tile counts"));
     YK_TRY(buf_alloc(p, p->tile_ptr, sizeof(int) * (nt2 + 1), "tile offsets"));
-    YK_TRY(buf_alloc(p, p->tile_cur, sizeof(int) * nt2, "tile cursors"));
+    /* the source cursors double as the heavy-first ordering's 80-int scratch */
+    YK_TRY(buf_alloc(p, p->tile_cur, sizeof(int) * (nt2 > 80 ? nt2 : 80), "tile cursors"));
     YK_TRY(buf_alloc(p, p->tile_order, sizeof(int) * nt2, "tile order"));
     YK_TRY(buf_alloc(p, p->trg_cnt, sizeof(int) * nt2, "tile counts"));
     YK_TRY(buf_alloc(p, p->trg_ptr, sizeof(int) * (nt2 + 1), "tile offsets"));
@@ -822,8 +823,9 @@ yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const doub
                                  P<int>(p->ent_j), P<int>(p->err), p->stream,
                                  p->precision == YK_FP32C),
           "bin sources");
+    /* the cursors are free after the fill: they serve as the ordering's scratch */
     YK_CU(yk::launch_tile_order(P<int>(p->tile_ptr), p->nt * p->nt, P<int>(p->tile_order),
-                                p->stream),
+                                P<int>(p->tile_cur), p->stream),
           "tile order");
     stage_end(p, YK_STAGE_BIN_SRC);
     /* the staging buffers are reused for the targets: order the copies after the source bins */

@@ -82,7 +82,8 @@ cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, cons
                                int *trg_idx, int *err, cudaStream_t st, bool f32);
 /* heavy-first tile order (order[i] = tile the i-th spread CTA takes); order may be NULL in the
  * spread launchers, meaning tile i for CTA i */
-cudaError_t launch_tile_order(const int *tile_ptr, int ntiles, int *order, cudaStream_t st);
+cudaError_t launch_tile_order(const int *tile_ptr, int ntiles, int *order, int *scratch,
+                              cudaStream_t st);
 cudaError_t launch_spread(const Geom &g, const int *tile_ptr, const int *order,
                           const double2 *ent_t, const int *ent_j, const double *wq,
                           const double *dens, double *grid, cudaStream_t st);

@@ -51,30 +51,70 @@ template <int W> __device__ __forceinline__ double2 pack_f32c(double2 t)
 /* ----------------------------------------------------------------------------------------- */
 /* binning                                                                                    */
 
+/* Warp-aggregated atomics: consecutive points mostly fall into the same tile, so the lanes of a
+ * warp that share a key make one atomic add (by their lowest lane) instead of one each.  Lanes
+ * with valid == false take part in the match with a key of their own and do nothing. */
+__device__ __forceinline__ void agg_count(int *cnt, int key, bool valid)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(0xffffffffu, valid ? key : -1 - lane);
+    if (valid && lane == __ffs(grp) - 1) atomicAdd(&cnt[key], __popc(grp));
+}
+
+/* reserve one slot per lane in cur[key]; returns the lane's offset within its key's range */
+__device__ __forceinline__ int agg_reserve(int *cur, int key, bool valid)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned grp = __match_any_sync(0xffffffffu, valid ? key : -1 - lane);
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (valid && lane == leader) base = atomicAdd(&cur[key], __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    return base + __popc(grp & ((1u << lane) - 1u));
+}
+
+/* the (up to four) tiles a source's w x w window touches; -1 where there is none */
+template <int W> __device__ __forceinline__ void src_tiles(double2 t, const Geom &g, int tiles[4])
+{
+    const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
+    const int ax0 = wrap(lx, g.n) / g.T, ax1 = wrap(lx + W - 1, g.n) / g.T;
+    const int ay0 = wrap(ly, g.n) / g.T, ay1 = wrap(ly + W - 1, g.n) / g.T;
+    tiles[0] = ay0 * g.nt + ax0;
+    tiles[1] = ax1 != ax0 ? ay0 * g.nt + ax1 : -1;
+    tiles[2] = ay1 != ay0 ? ay1 * g.nt + ax0 : -1;
+    tiles[3] = (ay1 != ay0 && ax1 != ax0) ? ay1 * g.nt + ax1 : -1;
+}
+
+/* grid coordinates of a point and whether it lies in the plan's box (and so in the grid) */
+__device__ __forceinline__ bool grid_coords(const Geom &g, double x, double y, double2 &t)
+{
+    t = make_double2((x - g.ox) * g.inv_h, (y - g.oy) * g.inv_h);
+    return in_box(g, x, y) && t.x >= 0.0 && t.x < (double)g.n && t.y >= 0.0 && t.y < (double)g.n;
+}
+
+/* the block size of the binning kernels is a multiple of 32 and every lane reaches the warp
+ * collectives (no early return) */
 template <int W>
 __global__ void k_bin_src_count(int64_t ns, const double *__restrict__ xs,
                                 const double *__restrict__ ys, Geom g, double2 *__restrict__ src_t,
                                 int *__restrict__ cnt, int *__restrict__ err)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ns) return;
-    const double tx = (xs[j] - g.ox) * g.inv_h, ty = (ys[j] - g.oy) * g.inv_h;
-    if (!in_box(g, xs[j], ys[j]) ||
-        !(tx >= 0.0 && tx < (double)g.n && ty >= 0.0 && ty < (double)g.n)) {
-        atomicOr(err, ERR_POINT_OUTSIDE);
-        src_t[j] = make_double2(-1.0, -1.0);
-        return;
+    bool ok = false;
+    int tiles[4] = {-1, -1, -1, -1};
+    if (j < ns) {
+        double2 t;
+        ok = grid_coords(g, xs[j], ys[j], t);
+        if (!ok) {
+            atomicOr(err, ERR_POINT_OUTSIDE);
+            t = make_double2(-1.0, -1.0);
+        } else {
+            src_tiles<W>(t, g, tiles);
+        }
+        src_t[j] = t;
     }
-    src_t[j] = make_double2(tx, ty);
-    const int lx = first_tap<W>(tx), ly = first_tap<W>(ty);
-    const int ax0 = wrap(lx, g.n) / g.T, ax1 = wrap(lx + W - 1, g.n) / g.T;
-    const int ay0 = wrap(ly, g.n) / g.T, ay1 = wrap(ly + W - 1, g.n) / g.T;
-    atomicAdd(&cnt[ay0 * g.nt + ax0], 1);
-    if (ax1 != ax0) atomicAdd(&cnt[ay0 * g.nt + ax1], 1);
-    if (ay1 != ay0) {
-        atomicAdd(&cnt[ay1 * g.nt + ax0], 1);
-        if (ax1 != ax0) atomicAdd(&cnt[ay1 * g.nt + ax1], 1);
-    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) agg_count(cnt, tiles[r], tiles[r] >= 0);
 }
 
 template <int W, bool F32>
@@ -83,21 +123,21 @@ __global__ void k_bin_src_fill(int64_t ns, const double2 *__restrict__ src_t, Ge
                                double2 *__restrict__ ent_t, int *__restrict__ ent_j)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ns) return;
-    const double2 t = src_t[j];
-    if (t.x < 0.0) return;
-    const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
-    const int ax[2] = {wrap(lx, g.n) / g.T, wrap(lx + W - 1, g.n) / g.T};
-    const int ay[2] = {wrap(ly, g.n) / g.T, wrap(ly + W - 1, g.n) / g.T};
-    const int nx = ax[1] != ax[0] ? 2 : 1, ny = ay[1] != ay[0] ? 2 : 1;
+    int tiles[4] = {-1, -1, -1, -1};
+    double2 t = make_double2(-1.0, -1.0);
+    if (j < ns) t = src_t[j];
+    if (t.x >= 0.0) src_tiles<W>(t, g, tiles);
     const double2 rec = F32 ? pack_f32c<W>(t) : pack_f64<W>(t);
-    for (int b = 0; b < ny; ++b)
-        for (int a = 0; a < nx; ++a) {
-            const int tile = ay[b] * g.nt + ax[a];
-            const int slot = ptr[tile] + atomicAdd(&cur[tile], 1);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const bool v = tiles[r] >= 0;
+        const int off = agg_reserve(cur, tiles[r], v);
+        if (v) {
+            const int slot = ptr[tiles[r]] + off;
             ent_t[slot] = rec;
             ent_j[slot] = (int)j;
         }
+    }
 }
 
 __global__ void k_bin_trg_count(int64_t nt, const double *__restrict__ xt,
@@ -105,17 +145,18 @@ __global__ void k_bin_trg_count(int64_t nt, const double *__restrict__ xt,
                                 int *__restrict__ cnt, int *__restrict__ err)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nt) return;
-    const double tx = (xt[i] - g.ox) * g.inv_h, ty = (yt[i] - g.oy) * g.inv_h;
-    if (!in_box(g, xt[i], yt[i]) ||
-        !(tx >= 0.0 && tx < (double)g.n && ty >= 0.0 && ty < (double)g.n)) {
-        atomicOr(err, ERR_POINT_OUTSIDE);
-        tmp[i] = make_double2(-1.0, -1.0);
-        return;
+    int tile = -1;
+    if (i < nt) {
+        double2 t;
+        if (!grid_coords(g, xt[i], yt[i], t)) {
+            atomicOr(err, ERR_POINT_OUTSIDE);
+            t = make_double2(-1.0, -1.0);
+        } else {
+            tile = ((int)t.y / g.T) * g.nt + (int)t.x / g.T;
+        }
+        tmp[i] = t;
     }
-    tmp[i] = make_double2(tx, ty);
-    const int tile = ((int)ty / g.T) * g.nt + (int)tx / g.T;
-    atomicAdd(&cnt[tile], 1);
+    agg_count(cnt, tile, tile >= 0);
 }
 
 template <int W, bool F32>
@@ -124,70 +165,138 @@ __global__ void k_bin_trg_fill(int64_t nt, const double2 *__restrict__ tmp, Geom
                                double2 *__restrict__ trg_t, int *__restrict__ trg_idx)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nt) return;
-    const double2 t = tmp[i];
-    if (t.x < 0.0) return;
-    const int tile = ((int)t.y / g.T) * g.nt + (int)t.x / g.T;
-    const int slot = ptr[tile] + atomicAdd(&cur[tile], 1);
-    trg_t[slot] = F32 ? pack_f32c<W>(t) : pack_f64<W>(t);
-    trg_idx[slot] = (int)i;
+    double2 t = make_double2(-1.0, -1.0);
+    if (i < nt) t = tmp[i];
+    const bool v = t.x >= 0.0;
+    const int tile = v ? ((int)t.y / g.T) * g.nt + (int)t.x / g.T : -1;
+    const int off = agg_reserve(cur, tile, v);
+    if (v) {
+        const int slot = ptr[tile] + off;
+        trg_t[slot] = F32 ? pack_f32c<W>(t) : pack_f64<W>(t);
+        trg_idx[slot] = (int)i;
+    }
 }
 
-/* exclusive scan of cnt[0..count) into ptr[0..count] by one CTA of 1024 threads, each owning a
- * contiguous chunk */
-__global__ void __launch_bounds__(1024) k_scan(const int *__restrict__ cnt, int *__restrict__ ptr,
-                                               int count)
+/* exclusive scan of cnt[0..count) into ptr[0..count] in three passes over blocks of kScanBlock
+ * elements: block sums into bsum, a scan of the block sums (one CTA), then each block adds its
+ * offset.  bsum holds ceil(count / kScanBlock) ints. */
+constexpr int kScanBlock = 4096;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_tot, int &total)
 {
-    __shared__ int part[1024];
-    const int nthr = blockDim.x;
-    const int chunk = (count + nthr - 1) / nthr;
-    const int b = threadIdx.x * chunk, e = min(count, b + chunk);
-    int s = 0;
-    for (int i = b; i < e; ++i) s += cnt[i];
-    part[threadIdx.x] = s;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
     __syncthreads();
-    for (int off = 1; off < nthr; off <<= 1) {
-        int v = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
+    if (wid == 0) {
+        int w = lane < nw ? warp_tot[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) warp_tot[lane] = w;
     }
-    int run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
-    for (int i = b; i < e; ++i) {
-        ptr[i] = run;
-        run += cnt[i];
+    __syncthreads();
+    total = warp_tot[nw - 1];
+    const int excl = x - v + (wid > 0 ? warp_tot[wid - 1] : 0);
+    __syncthreads();
+    return excl;
+}
+
+/* pass 1 (blockDim 1024, 4 elements per thread): local exclusive prefix into ptr, block total */
+__global__ void __launch_bounds__(1024) k_scan_local(const int *__restrict__ cnt,
+                                                     int *__restrict__ ptr, int count,
+                                                     int *__restrict__ bsum)
+{
+    __shared__ int wt[32];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * 4;
+    int v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = base + k < count ? cnt[base + k] : 0;
+        s += v[k];
     }
-    if (threadIdx.x == nthr - 1) ptr[count] = part[nthr - 1];
+    int total = 0;
+    int run = block_exclusive_scan(s, wt, total);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < count) ptr[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+/* pass 2 (one CTA): exclusive scan of the block sums in place; ptr[count] = grand total */
+__global__ void __launch_bounds__(1024) k_scan_sums(int *__restrict__ bsum, int nb,
+                                                    int *__restrict__ ptr, int count)
+{
+    __shared__ int wt[32];
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int i = b0 + threadIdx.x;
+        const int v = i < nb ? bsum[i] : 0;
+        int total = 0;
+        const int ex = block_exclusive_scan(v, wt, total);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) ptr[count] = carry;
+}
+
+/* pass 3: add each block's offset */
+__global__ void __launch_bounds__(1024) k_scan_add(int *__restrict__ ptr, int count,
+                                                   const int *__restrict__ bsum)
+{
+    const int add = bsum[blockIdx.x];
+    const int base = blockIdx.x * kScanBlock + threadIdx.x * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (base + k < count) ptr[base + k] += add;
 }
 
 /* heavy-first processing order of the tiles: tiles bucketed by floor(log2(entries)) and listed
  * from the fullest bucket down, so that the costly tiles start first and the short ones fill the
- * tail (one CTA; the order inside a bucket does not affect any result) */
-__global__ void __launch_bounds__(1024) k_tile_order(const int *__restrict__ ptr, int ntiles,
-                                                     int *__restrict__ order)
+ * tail (the order inside a bucket does not affect any result).  scratch: 80 ints, zeroed. */
+__device__ __forceinline__ int tile_bucket(const int *ptr, int t)
 {
-    __shared__ int hist[33], base[33];
-    if (threadIdx.x < 33) hist[threadIdx.x] = 0;
+    const int c = ptr[t + 1] - ptr[t];
+    return c > 0 ? 32 - __clz(c) : 0;
+}
+
+__global__ void k_order_hist(const int *__restrict__ ptr, int ntiles, int *__restrict__ scratch)
+{
+    __shared__ int h[33];
+    if (threadIdx.x < 33) h[threadIdx.x] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const int c = ptr[t + 1] - ptr[t];
-        atomicAdd(&hist[c > 0 ? 32 - __clz(c) : 0], 1);
-    }
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+        atomicAdd(&h[tile_bucket(ptr, t)], 1);
     __syncthreads();
+    if (threadIdx.x < 33 && h[threadIdx.x]) atomicAdd(&scratch[threadIdx.x], h[threadIdx.x]);
+}
+
+__global__ void k_order_base(int *__restrict__ scratch)
+{
     if (threadIdx.x == 0) {
         int run = 0;
         for (int b = 32; b >= 0; --b) {
-            base[b] = run;
-            run += hist[b];
-            hist[b] = 0;
+            scratch[40 + b] = run; /* first position of bucket b */
+            run += scratch[b];
         }
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const int c = ptr[t + 1] - ptr[t];
-        const int b = c > 0 ? 32 - __clz(c) : 0;
-        order[base[b] + atomicAdd(&hist[b], 1)] = t;
-    }
+}
+
+__global__ void k_order_fill(const int *__restrict__ ptr, int ntiles, int *__restrict__ scratch,
+                             int *__restrict__ order)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool v = t < ntiles;
+    const int b = v ? tile_bucket(ptr, t) : 0;
+    const int off = agg_reserve(scratch + 40, b, v); /* scratch[40+b] doubles as the cursor */
+    if (v) order[off] = t;
 }
 
 /* ----------------------------------------------------------------------------------------- */
@@ -343,6 +452,20 @@ int stage_smem(const Inst &d, int stage)
     default: return cudaErrorInvalidValue;                                                       \
     }
 
+/* exclusive scan of cnt into ptr; cur (>= ceil(count / kScanBlock) ints) is scratch and is left
+ * zeroed for the fill pass */
+cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStream_t st)
+{
+    if (count <= 0) return cudaMemsetAsync(ptr, 0, sizeof(int), st);
+    const int nb = (count + kScanBlock - 1) / kScanBlock;
+    k_scan_local<<<nb, 1024, 0, st>>>(cnt, ptr, count, cur);
+    k_scan_sums<<<1, 1024, 0, st>>>(cur, nb, ptr, count);
+    k_scan_add<<<nb, 1024, 0, st>>>(ptr, count, cur);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(cur, 0, sizeof(int) * nb, st);
+    return e;
+}
+
 cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
                                double2 *src_t, int *tile_cnt, int *tile_ptr, int *tile_cur,
                                double2 *ent_t, int *ent_j, int *err, cudaStream_t st, bool f32)
@@ -358,7 +481,7 @@ cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, cons
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     }
-    k_scan<<<1, 1024, 0, st>>>(tile_cnt, tile_ptr, ntiles);
+    if ((e = launch_scan(tile_cnt, tile_ptr, ntiles, tile_cur, st)) != cudaSuccess) return e;
     if (ns > 0) {
 #define YK_CALL(W)                                                                              \
     if (f32)                                                                                    \
@@ -384,7 +507,7 @@ cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, cons
     if (e != cudaSuccess) return e;
     const int blocks = (int)((nt + 255) / 256);
     if (nt > 0) k_bin_trg_count<<<blocks, 256, 0, st>>>(nt, xt, yt, g, trg_tmp, cnt, err);
-    k_scan<<<1, 1024, 0, st>>>(cnt, ptr, ntiles);
+    if ((e = launch_scan(cnt, ptr, ntiles, cur, st)) != cudaSuccess) return e;
     if (nt > 0) {
 #define YK_CALL(W)                                                                              \
     if (f32)                                                                                    \
@@ -397,9 +520,16 @@ cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_order(const int *tile_ptr, int ntiles, int *order, cudaStream_t st)
+cudaError_t launch_tile_order(const int *tile_ptr, int ntiles, int *order, int *scratch,
+                              cudaStream_t st)
 {
-    k_tile_order<<<1, 1024, 0, st>>>(tile_ptr, ntiles, order);
+    if (ntiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(int) * 80, st);
+    if (e != cudaSuccess) return e;
+    const int blocks = (ntiles + 255) / 256;
+    k_order_hist<<<blocks < 148 ? blocks : 148, 256, 0, st>>>(tile_ptr, ntiles, scratch);
+    k_order_base<<<1, 32, 0, st>>>(scratch);
+    k_order_fill<<<blocks, 256, 0, st>>>(tile_ptr, ntiles, scratch, order);
     return cudaGetLastError();
 }
 
