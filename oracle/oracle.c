@@ -22,7 +22,18 @@
  *   c_m    = sum_j q_j exp(-i k_m . y_j),
  *   u(x)   = (Delta k)^2/(2pi)^2 sum_m exp(-delta(alpha^2+|k_m|^2))/(alpha^2+|k_m|^2) c_m e^{ik_m.x}
  *
- * evaluated as plain double loops.  Pins for both live in the tests (closed forms, identities,
+ * evaluated as plain double loops.
+ *
+ * Double layer (Section 2, eq. dlp; its split D = D_L + D_H in Section 2.1; Section 5.1, the D_H
+ * formula after eq. kmax_dlp): a dipole source at y with vector strength s = mu w nu contributes
+ *
+ *   s . grad_y G_H(x - y) = F_D(|x - y|) (x - y) . s,
+ *   F_D(r) = -G_H'(r) / r = int_delta^inf exp(-r^2/(4t) - alpha^2 t) / (8 pi t^2) dt
+ *          = (1/(2pi)) int_0^inf exp(-delta(alpha^2+k^2)) / (alpha^2+k^2) k^2 J1(k r)/r dk,
+ *
+ * tabulated the same way (J1 from the C library, k/2 at r = 0).  In the discrete formula the
+ * dipole's Fourier coefficient is -i (k . s) exp(-i k . y): differentiating exp(ik.(x-y)) with
+ * respect to the source point.  Pins for both live in the tests (closed forms, identities,
  * brute force); none of them re-types these formulas.
  */
 #define _DEFAULT_SOURCE 1 /* j0() is POSIX, not ISO C */
@@ -64,7 +75,7 @@ static void gauss_legendre(int n, double *x, double *w)
 /* ---------------------------------------------------------------------------------------- */
 /* Hankel quadrature of G_H: nodes k_i and combined weights c_i with G_H(r) = sum c_i J0(k_i r) */
 typedef struct {
-    int n;
+    int n, kind; /* kind 0: G_H = sum c_i J0(k_i r); kind 1: F_D = sum c_i J1(k_i r) / r */
     double *k, *c;
 } hankel_rule;
 
@@ -74,8 +85,9 @@ typedef struct {
  * has length min(sqrt(a^2+alpha^2), 2pi/r_max, 1/sqrt(delta)): the first bound keeps the poles
  * of 1/(alpha^2+k^2) at +-i alpha well outside each panel's Bernstein ellipse, the second puts at
  * most one period of J0(k r) in a panel, the third resolves the Gaussian factor. */
-static int hankel_build(double alpha, double delta, double rmax, hankel_rule *h)
+static int hankel_build(double alpha, double delta, double rmax, int kind, hankel_rule *h)
 {
+    h->kind = kind;
     double xg[OR_GL_N], wg[OR_GL_N];
     gauss_legendre(OR_GL_N, xg, wg);
     double kc = sqrt(45.0 / delta);
@@ -100,7 +112,8 @@ static int hankel_build(double alpha, double delta, double rmax, hankel_rule *h)
             double k = a + 0.5 * L * (xg[i] + 1.0);
             double s = alpha * alpha + k * k;
             h->k[p * OR_GL_N + i] = k;
-            h->c[p * OR_GL_N + i] = 0.5 * L * wg[i] * exp(-delta * s) / s * k / (2.0 * OR_PI);
+            h->c[p * OR_GL_N + i] =
+                0.5 * L * wg[i] * exp(-delta * s) / s * k * (kind ? k : 1.0) / (2.0 * OR_PI);
         }
         a += L;
     }
@@ -115,10 +128,13 @@ static void hankel_free(hankel_rule *h)
 
 static double hankel_eval(const hankel_rule *h, double r)
 {
-    /* Neumaier-compensated sum of c_i J0(k_i r) */
+    /* Neumaier-compensated sum of c_i J0(k_i r), or of c_i J1(k_i r) / r (k_i / 2 at r = 0) */
     double s = 0.0, comp = 0.0;
     for (int i = 0; i < h->n; ++i) {
-        double t = h->c[i] * j0(h->k[i] * r);
+        double b;
+        if (h->kind == 0) b = j0(h->k[i] * r);
+        else b = r > 0.0 ? j1(h->k[i] * r) / r : 0.5 * h->k[i];
+        double t = h->c[i] * b;
         double u = s + t;
         if (fabs(s) >= fabs(t)) comp += (s - u) + t;
         else comp += (t - u) + s;
@@ -127,22 +143,27 @@ static double hankel_eval(const hankel_rule *h, double r)
     return s + comp;
 }
 
-/* Direct Hankel-quadrature value of G_H at n radii (no table). */
-int or_gh_hankel(double alpha, double delta, int64_t n, const double *r, double *out)
+/* Direct Hankel-quadrature value of G_H (kind 0) or F_D (kind 1) at n radii (no table). */
+int or_kernel_hankel(double alpha, double delta, int kind, int64_t n, const double *r, double *out)
 {
     double rmax = 0.0;
     for (int64_t i = 0; i < n; ++i)
         if (r[i] > rmax) rmax = r[i];
     hankel_rule h;
-    if (hankel_build(alpha, delta, rmax, &h)) return -1;
+    if (hankel_build(alpha, delta, rmax, kind, &h)) return -1;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = 0; i < n; ++i) out[i] = hankel_eval(&h, r[i]);
     hankel_free(&h);
     return 0;
 }
 
+int or_gh_hankel(double alpha, double delta, int64_t n, const double *r, double *out)
+{
+    return or_kernel_hankel(alpha, delta, 0, n, r, out);
+}
+
 /* ---------------------------------------------------------------------------------------- */
-/* Piecewise Chebyshev table of G_H on [0, r_max].                                             */
+/* Piecewise Chebyshev table of G_H (or F_D) on [0, r_max].                                             */
 #define OR_CHEB_N 25 /* points (degree 24) */
 
 typedef struct {
@@ -184,11 +205,11 @@ typedef struct {
  * tol_rel * G_H(0), or when it is narrower than sqrt(delta)/256 (below that width G_H is a
  * low-degree polynomial and a larger tail is quadrature noise).  Initial panels: [0, s], then
  * geometric [s 2^i, s 2^{i+1}] (s = sqrt(delta)) up to r_max. */
-void *or_table_create(double alpha, double delta, double rmax, double tol_rel)
+void *or_table_create_kind(double alpha, double delta, double rmax, double tol_rel, int kind)
 {
-    if (!(alpha > 0) || !(delta > 0) || !(rmax > 0)) return NULL;
+    if (!(alpha > 0) || !(delta > 0) || !(rmax > 0) || (kind != 0 && kind != 1)) return NULL;
     hankel_rule h;
-    if (hankel_build(alpha, delta, rmax, &h)) return NULL;
+    if (hankel_build(alpha, delta, rmax, kind, &h)) return NULL;
     double g0 = hankel_eval(&h, 0.0);
     double thr = tol_rel * g0;
 
@@ -267,6 +288,11 @@ void *or_table_create(double alpha, double delta, double rmax, double tol_rel)
     return T;
 }
 
+void *or_table_create(double alpha, double delta, double rmax, double tol_rel)
+{
+    return or_table_create_kind(alpha, delta, rmax, tol_rel, 0);
+}
+
 void or_table_free(void *t)
 {
     or_table *T = (or_table *)t;
@@ -334,12 +360,48 @@ int or_direct_sum(const void *t, int64_t ns, const double *xs, const double *ys,
     return bad ? -1 : 0;
 }
 
+/* Direct pair sum of the double layer: u_i = sum_d F_D(|x_i - y_d|) (x_i - y_d) . s_d with
+ * s_d = (sx_d, sy_d) = mu_d w_d nu_d (t: a kind-1 table), Neumaier-compensated, sources in index
+ * order; s_abs_i = sum_d F_D(r) r |s_d| (the conditioning scale of u_i). */
+int or_direct_sum_dl(const void *t, int64_t nd, const double *xd, const double *yd,
+                     const double *sx, const double *sy, int64_t nt, const double *xt,
+                     const double *yt, double *u, double *s_abs)
+{
+    const or_table *T = (const or_table *)t;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+    for (int64_t i = 0; i < nt; ++i) {
+        double sum = 0.0, comp = 0.0, sa = 0.0, ca = 0.0;
+        for (int64_t j = 0; j < nd; ++j) {
+            double dx = xt[i] - xd[j], dy = yt[i] - yd[j];
+            double r = sqrt(dx * dx + dy * dy);
+            if (r > T->rmax * (1.0 + 1e-12)) { bad = 1; continue; }
+            double f = table_eval(T, r);
+            double v = f * (dx * sx[j] + dy * sy[j]), nsum = sum + v;
+            if (fabs(sum) >= fabs(v)) comp += (sum - nsum) + v;
+            else comp += (v - nsum) + sum;
+            sum = nsum;
+            double va = f * r * sqrt(sx[j] * sx[j] + sy[j] * sy[j]), na = sa + va;
+            if (fabs(sa) >= fabs(va)) ca += (sa - na) + va;
+            else ca += (va - na) + sa;
+            sa = na;
+        }
+        u[i] = sum + comp;
+        if (s_abs) s_abs[i] = sa + ca;
+    }
+    return bad ? -1 : 0;
+}
+
 /* ---------------------------------------------------------------------------------------- */
 /* Discrete formula of Section 5.2 on modes |m_x|,|m_y| <= M, Delta k = 2pi/P, coordinates     */
 /* taken relative to (cx, cy) (a common shift; the result does not depend on it).              */
-int or_discrete_sum(double alpha, double delta, double P, int64_t M, double cx, double cy,
-                    int64_t ns, const double *xs, const double *ys, const double *q,
-                    int64_t nt, const double *xt, const double *yt, double *u)
+/* Charges q at (xs, ys) and dipoles s = (sx, sy) at (xd, yd) (nd may be 0); a dipole's
+ * coefficient is -i (k . s) exp(-i k . y). */
+int or_discrete_sum_dl(double alpha, double delta, double P, int64_t M, double cx, double cy,
+                       int64_t ns, const double *xs, const double *ys, const double *q,
+                       int64_t nd, const double *xd, const double *yd, const double *sx,
+                       const double *sy, int64_t nt, const double *xt, const double *yt,
+                       double *u)
 {
     const int64_t nm = 2 * M + 1;
     const double dk = 2.0 * OR_PI / P;
@@ -360,6 +422,20 @@ int or_discrete_sum(double alpha, double delta, double P, int64_t M, double cx, 
             for (int64_t a = 0; a < nm; ++a) {
                 double complex qa = q[j] * ex[a];
                 for (int64_t b = 0; b < nm; ++b) cl[a * nm + b] += qa * ey[b];
+            }
+        }
+#pragma omp for schedule(static)
+        for (int64_t j = 0; j < nd; ++j) {
+            for (int64_t m = -M; m <= M; ++m) {
+                ex[m + M] = cexp(-I * dk * (double)m * (xd[j] - cx));
+                ey[m + M] = cexp(-I * dk * (double)m * (yd[j] - cy));
+            }
+            for (int64_t a = 0; a < nm; ++a) {
+                const double kx = dk * (double)(a - M);
+                for (int64_t b = 0; b < nm; ++b) {
+                    const double ky = dk * (double)(b - M);
+                    cl[a * nm + b] += -I * (kx * sx[j] + ky * sy[j]) * ex[a] * ey[b];
+                }
             }
         }
 #pragma omp critical
@@ -398,6 +474,14 @@ int or_discrete_sum(double alpha, double delta, double P, int64_t M, double cx, 
     }
     free(c);
     return 0;
+}
+
+int or_discrete_sum(double alpha, double delta, double P, int64_t M, double cx, double cy,
+                    int64_t ns, const double *xs, const double *ys, const double *q,
+                    int64_t nt, const double *xt, const double *yt, double *u)
+{
+    return or_discrete_sum_dl(alpha, delta, P, M, cx, cy, ns, xs, ys, q, 0, NULL, NULL, NULL,
+                              NULL, nt, xt, yt, u);
 }
 
 int or_num_threads(void)

@@ -14,6 +14,11 @@ rules separately in C++, and the tests compare the two.
                           reading of the Nyquist/periodicity condition of eq. nf used for the period.
 * ``modes``            — largest mode index M = ceil(k_max P / (2 pi)) for Delta k = 2 pi / P
                           (eq. delta_k with the symmetric mode set |m| <= M).
+* ``kmax_dlp_paper``   — eq. kmax_dlp as printed: k_max exp(-delta (alpha^2 + k_max^2)) <= eps (the
+                          extra factor of k from the normal derivative), 0 when it holds at every k.
+* ``kmax_dlp_relative``— the same reading relative to the kernel's size: the tail
+                          int_k^inf exp(-delta(alpha^2+s^2)) s^2/(alpha^2+s^2) ds is at most eps times
+                          the whole integral (from 0), the bound on |G_H'| of the radial form.
 """
 from __future__ import annotations
 
@@ -63,3 +68,29 @@ def r_tol(alpha: float, delta: float, eps: float) -> float:
 
 def modes(kmax: float, period: float) -> int:
     return int(math.ceil(kmax * period / (2.0 * math.pi)))
+
+
+def kmax_dlp_paper(alpha: float, delta: float, eps: float) -> float:
+    f = lambda k: k * math.exp(-delta * (alpha * alpha + k * k))
+    kpk = 1.0 / math.sqrt(2.0 * delta)          # maximiser of k exp(-delta k^2)
+    if f(kpk) <= eps:
+        return 0.0
+    lo, hi = kpk, 2.0 * kpk
+    while f(hi) > eps:
+        lo, hi = hi, 2.0 * hi
+    return so.brentq(lambda k: f(k) - eps, lo, hi, xtol=1e-13, rtol=1e-15)
+
+
+def _dlp_tail(alpha, delta, k):
+    import scipy.integrate as si
+    g = lambda s: math.exp(-delta * (alpha * alpha + s * s)) * s * s / (alpha * alpha + s * s)
+    return si.quad(g, k, np.inf, epsabs=0.0, epsrel=1e-13, limit=400)[0]
+
+
+def kmax_dlp_relative(alpha: float, delta: float, eps: float) -> float:
+    target = eps * _dlp_tail(alpha, delta, 0.0)
+    lo, hi = 0.0, 1.0 / math.sqrt(delta)
+    while _dlp_tail(alpha, delta, hi) > target:
+        lo, hi = hi, 2.0 * hi
+    return so.brentq(lambda k: _dlp_tail(alpha, delta, k) - target, lo, hi, xtol=1e-12,
+                     rtol=1e-14)

@@ -43,6 +43,13 @@ class Starfish:
     def speed(self, t):
         return np.hypot(self.radius(t), self.dradius(t))
 
+    def normal(self, t):
+        """Outward unit normal (the parametrisation runs counter-clockwise)."""
+        r, dr = self.radius(t), self.dradius(t)
+        tx, ty = dr * np.cos(t) - r * np.sin(t), dr * np.sin(t) + r * np.cos(t)
+        s = np.hypot(tx, ty)
+        return ty / s, -tx / s
+
     def inside(self, x, y):
         rho = np.hypot(x, y)
         return rho < self.radius(np.arctan2(y, x))
@@ -69,6 +76,14 @@ def boundary_nodes(curve: Starfish, n_panels: int, n_gl: int = 16):
     x, y = curve.point(t)
     w = (curve.speed(t).reshape(n_panels, n_gl) * half * om[None, :]).ravel()
     return x, y, w, t
+
+
+def double_layer_nodes(curve: Starfish, n_panels: int, n_gl: int = 16):
+    """Boundary nodes for a double layer: (x, y, w, nx, ny, mu) with the outward unit normal and
+    the smooth density mu(t) = sin(2t) + 0.3 cos(t)."""
+    x, y, w, t = boundary_nodes(curve, n_panels, n_gl)
+    nx, ny = curve.normal(t)
+    return x, y, w, nx, ny, np.sin(2.0 * t) + 0.3 * np.cos(t)
 
 
 def boundary_density(t):
