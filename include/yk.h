@@ -87,6 +87,11 @@ typedef struct {
     int fft_fp64;       /* FP64 path only: nonzero runs the FFT passes in FP64 arithmetic; the
                            default (0) runs them in double-float (FP32 pairs, ~48-bit mantissa,
                            error ~1e-14), which B300 executes much faster than FP64 */
+    int dlp;            /* nonzero: the plan also takes double-layer (dipole) sources through
+                           yk_set_points_dl / yk_eval_longrange_dl; k_max then also meets the
+                           double-layer cutoff (Section 5.1, eq. kmax_dlp, read as kmax_rule says:
+                           0: the tail of int exp(-delta(alpha^2+k^2)) k^2/(alpha^2+k^2) dk beyond
+                           k_max is at most eps times the whole integral; 1: as printed) */
 } yk_opts;
 
 /* Parameters the plan chose (all derived from alpha, tol, delta and the box). */
@@ -135,6 +140,36 @@ YK_API yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, con
  * values, written).  Returns YK_ERR_STATE before any yk_set_points.
  */
 YK_API yk_status yk_eval_longrange(yk_plan_t p, const double *density, double *u);
+
+/*
+ * Double layer (Section 2, eq. dlp; history part D_H of Section 2.1; Fourier form in Section 5.1).
+ * Dipole sources at boundary nodes y_d with quadrature weights wd_d and outward unit normals
+ * (nx_d, ny_d) add
+ *
+ *     D_H[mu](x_i) = sum_d mu_d wd_d nu_d . grad_y G_H(x_i - y_d)
+ *
+ * to u.  In Fourier space this is the factor -i k . nu of the paper's D_H formula (the derivative
+ * of exp(ik.(x - y)) with respect to the source point; the printed +i k has the sign of the
+ * derivative in x).  The library folds that factor into the spread: a dipole is spread with the
+ * gradient of the window, so charges and dipoles share one grid, one FFT pair and one
+ * interpolation.
+ *
+ * yk_set_points_dl: as yk_set_points, plus n_dip dipole nodes (xd, yd, wd, nx, ny; host or device,
+ * FP64; the caller's normals are used as given).  The plan must have been created with opts.dlp
+ * when n_dip > 0 (else YK_ERR_ARG).  yk_set_points is yk_set_points_dl with n_dip = 0.
+ *
+ * yk_eval_longrange_dl: u = S_H[sigma] + V_H[f] (density, n_src values) + D_H[mu] (mu: n_dip
+ * values at the dipole nodes); u (n_trg) is written.  yk_eval_longrange on a plan whose points
+ * include dipoles returns YK_ERR_ARG (mu is required).  Batches (yk_batch_*) and the
+ * allocation-free entry point take charges only: a plan with dipoles there is YK_ERR_UNSUPPORTED.
+ */
+YK_API yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const double *ys,
+                                  const double *w, int64_t n_dip, const double *xd,
+                                  const double *yd, const double *wd, const double *nx,
+                                  const double *ny, int64_t n_trg, const double *xt,
+                                  const double *yt);
+YK_API yk_status yk_eval_longrange_dl(yk_plan_t p, const double *density, const double *mu,
+                                      double *u);
 
 /*
  * yk_plan_params: the parameters yk_plan would choose for (alpha, o), and in info->device_bytes

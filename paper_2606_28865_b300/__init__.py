@@ -48,7 +48,7 @@ class Opts(ctypes.Structure):
                 ("period", ctypes.c_double), ("tile", ctypes.c_int),
                 ("profile", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", _ALLOC),
                 ("free", _FREE), ("alloc_ctx", ctypes.c_void_p), ("use_tuned", ctypes.c_int),
-                ("n_src_hint", ctypes.c_int64), ("fft_fp64", ctypes.c_int)]
+                ("n_src_hint", ctypes.c_int64), ("fft_fp64", ctypes.c_int), ("dlp", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -73,6 +73,9 @@ _lib.yk_plan.argtypes = [_d, ctypes.POINTER(Opts), ctypes.POINTER(_vp)]
 _lib.yk_plan_params.argtypes = [_d, ctypes.POINTER(Opts), _i64, _i64, ctypes.POINTER(Info)]
 _lib.yk_set_points.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp]
 _lib.yk_eval_longrange.argtypes = [_vp, _vp, _vp]
+_lib.yk_set_points_dl.argtypes = [_vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64,
+                                  _vp, _vp]
+_lib.yk_eval_longrange_dl.argtypes = [_vp, _vp, _vp, _vp]
 _lib.yk_sync.argtypes = [_vp]
 _lib.yk_stage_times.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
 _lib.yk_plan_info.argtypes = [_vp, ctypes.POINTER(Info)]
@@ -80,6 +83,7 @@ _lib.yk_destroy.argtypes = [_vp]
 _lib.yk_batch_eval.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                ctypes.c_int]
 for _f in ("yk_plan", "yk_plan_params", "yk_set_points", "yk_eval_longrange", "yk_sync",
+           "yk_set_points_dl", "yk_eval_longrange_dl",
            "yk_stage_times",
            "yk_plan_info", "yk_destroy", "yk_batch_eval"):
     getattr(_lib, _f).restype = ctypes.c_int
@@ -124,7 +128,7 @@ def _len(a) -> int:
 def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
               box=(-1.5, 1.5, -1.5, 1.5), kmax=0.0, kmax_rule=0, period=0.0, tile=0,
               profile=False, stream=None, use_tuned=False, n_src_hint=0,
-              fft_fp64=False) -> Opts:
+              fft_fp64=False, dlp=False) -> Opts:
     o = Opts()
     _lib.yk_opts_default(ctypes.byref(o))
     o.precision = int(precision)
@@ -143,6 +147,7 @@ def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
     o.use_tuned = 1 if use_tuned else 0
     o.n_src_hint = int(n_src_hint)
     o.fft_fp64 = 1 if fft_fp64 else 0
+    o.dlp = 1 if dlp else 0
     return o
 
 
@@ -175,6 +180,7 @@ class Plan:
         _check(_lib.yk_plan(float(alpha), ctypes.byref(self._opts), ctypes.byref(h)), "yk_plan")
         self._h = h
         self.n_src = 0
+        self.n_dip = 0
         self.n_trg = 0
 
     @property
@@ -187,29 +193,50 @@ class Plan:
         _check(_lib.yk_plan_info(self._h, ctypes.byref(info)), "yk_plan_info")
         return info.as_dict()
 
-    def set_points(self, xs, ys, w, xt, yt):
+    def set_points(self, xs, ys, w, xt, yt, dipoles=None):
+        """Charges (xs, ys, w), targets (xt, yt) and optionally double-layer nodes
+        dipoles = (xd, yd, wd, nx, ny) (plan created with dlp=True)."""
         keep = []
         ns, nt = _len(xs), _len(xt)
         if _len(ys) != ns or _len(w) != ns or _len(yt) != nt:
             raise ValueError("coordinate/weight lengths differ")
-        _check(_lib.yk_set_points(self._h, ns, _ptr(xs, keep), _ptr(ys, keep), _ptr(w, keep), nt,
-                                  _ptr(xt, keep), _ptr(yt, keep)), "yk_set_points")
+        if dipoles is None:
+            _check(_lib.yk_set_points(self._h, ns, _ptr(xs, keep), _ptr(ys, keep), _ptr(w, keep),
+                                      nt, _ptr(xt, keep), _ptr(yt, keep)), "yk_set_points")
+            nd = 0
+        else:
+            xd, yd, wd, nx, ny = dipoles
+            nd = _len(xd)
+            if any(_len(a) != nd for a in (yd, wd, nx, ny)):
+                raise ValueError("dipole array lengths differ")
+            _check(_lib.yk_set_points_dl(self._h, ns, _ptr(xs, keep), _ptr(ys, keep),
+                                         _ptr(w, keep), nd, _ptr(xd, keep), _ptr(yd, keep),
+                                         _ptr(wd, keep), _ptr(nx, keep), _ptr(ny, keep), nt,
+                                         _ptr(xt, keep), _ptr(yt, keep)), "yk_set_points_dl")
         self._keep_points = keep
-        self.n_src, self.n_trg = ns, nt
+        self.n_src, self.n_dip, self.n_trg = ns, nd, nt
 
-    def eval(self, density, out=None):
-        """u at the targets; `out` (same kind of array as `density` by default) is written."""
+    def eval(self, density, out=None, mu=None):
+        """u at the targets; `out` (same kind of array as `density` by default) is written.
+        mu: double-layer density at the dipole nodes (required when the points include them)."""
         if _len(density) != self.n_src:
             raise ValueError("density length differs from the number of sources")
+        if mu is not None and _len(mu) != self.n_dip:
+            raise ValueError("mu length differs from the number of dipoles")
         torch = _torch()
+        ref = density if self.n_src or mu is None else mu
         if out is None:
-            if torch is not None and isinstance(density, torch.Tensor):
-                out = torch.empty(self.n_trg, dtype=torch.float64, device=density.device)
+            if torch is not None and isinstance(ref, torch.Tensor):
+                out = torch.empty(self.n_trg, dtype=torch.float64, device=ref.device)
             else:
                 out = np.empty(self.n_trg, dtype=np.float64)
         keep = []
-        _check(_lib.yk_eval_longrange(self._h, _ptr(density, keep), _ptr(out, keep)),
-               "yk_eval_longrange")
+        if mu is None:
+            _check(_lib.yk_eval_longrange(self._h, _ptr(density, keep), _ptr(out, keep)),
+                   "yk_eval_longrange")
+        else:
+            _check(_lib.yk_eval_longrange_dl(self._h, _ptr(density, keep), _ptr(mu, keep),
+                                             _ptr(out, keep)), "yk_eval_longrange_dl")
         self._keep_eval = keep
         return out
 

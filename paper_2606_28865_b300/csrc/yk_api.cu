@@ -154,6 +154,67 @@ double kmax_paper(double alpha, double delta, double eps)
     return v > 0.0 ? std::sqrt(v) : 0.0;
 }
 
+/* eq. kmax_dlp as printed: k exp(-delta (alpha^2 + k^2)) <= eps beyond k (0 if it holds for all k) */
+double kmax_dlp_paper(double alpha, double delta, double eps)
+{
+    auto f = [&](double k) { return k * std::exp(-delta * (alpha * alpha + k * k)); };
+    const double kpk = 1.0 / std::sqrt(2.0 * delta); /* maximiser of k exp(-delta k^2) */
+    if (f(kpk) <= eps) return 0.0;
+    double lo = kpk, hi = 2.0 * kpk;
+    while (f(hi) > eps) {
+        lo = hi;
+        hi *= 2.0;
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-14 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (f(mid) > eps) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
+/* int_k^inf exp(-delta s^2) s^2 / (alpha^2 + s^2) ds (the common factor exp(-delta alpha^2)
+ * dropped): composite 16-point Gauss-Legendre on panels no wider than 1/(4 sqrt(delta)) and half
+ * the distance to the poles at +-i alpha, up to where exp(-delta s^2) has fallen by e^{-60} */
+double dlp_tail(double alpha, double delta, double k)
+{
+    struct Rule {
+        double x[16], w[16];
+        Rule() { gauss_legendre(16, x, w); }
+    };
+    static const Rule rule;
+    const double K = std::sqrt(k * k + 60.0 / delta), cap = 0.25 / std::sqrt(delta);
+    double sum = 0.0;
+    for (double a = k; a < K;) {
+        double L = std::min(cap, 0.5 * std::sqrt(a * a + alpha * alpha));
+        if (a + L > K) L = K - a;
+        for (int i = 0; i < 16; ++i) {
+            const double t = a + 0.5 * L * (rule.x[i] + 1.0), t2 = t * t;
+            sum += 0.5 * L * rule.w[i] * std::exp(-delta * t2) * t2 / (alpha * alpha + t2);
+        }
+        a += L;
+    }
+    return sum;
+}
+
+/* reading of eq. kmax_dlp relative to the kernel's size: the radial integrand of -G_H' carries
+ * one more factor of k than G_H's; its tail beyond k_max is at most eps times its whole integral */
+double kmax_dlp_relative(double alpha, double delta, double eps)
+{
+    const double target = eps * dlp_tail(alpha, delta, 0.0);
+    double lo = 0.0, hi = 1.0 / std::sqrt(delta);
+    while (dlp_tail(alpha, delta, hi) > target) {
+        lo = hi;
+        hi *= 2.0;
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-13 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (dlp_tail(alpha, delta, mid) > target) lo = mid;
+        else hi = mid;
+    }
+    return hi;
+}
+
 /* decay length: smallest r with G_H(r') <= eps G_H(0) for all r' >= r (G_H decreases in r) */
 double decay_length(double alpha, double delta, double eps)
 {
@@ -193,14 +254,15 @@ double window_ft(double xi, int w, double beta)
 
 /* per-tap window polynomials: tap a covers z = u - w/2 + a, u in [0, 1); with x = 2u - 1 the
  * window there is interpolated at deg+1 Chebyshev points and the series converted to powers of
- * x, all in long double; out[k * w + a] = coefficient of x^k for tap a */
-void window_polys(int w, double beta, int deg, std::vector<double> &out,
-                  std::vector<float2> &out_df)
+ * x, all in long double; mono[k * w + a] = coefficient of x^k for tap a.  With deriv, deg * w
+ * more coefficients follow: those of phi'(z) = 2 dP_a/dx (z in cells), and *dmax receives a bound
+ * on |phi'| sampled over every tap. */
+void window_polys(int w, double beta, int deg, bool deriv, std::vector<long double> &mono_all,
+                  double *dmax)
 {
     const int m = deg + 1;
     const long double pi = 3.14159265358979323846264338327950288L;
-    out.assign((size_t)m * w, 0.0);
-    out_df.assign((size_t)m * w, make_float2(0.0f, 0.0f));
+    mono_all.assign((size_t)m * w + (deriv ? (size_t)deg * w : 0), 0.0L);
     for (int a = 0; a < w; ++a) {
         std::vector<long double> f(m), c(m, 0.0L), mono(m, 0.0L), t0(m, 0.0L), t1(m, 0.0L), t2(m);
         for (int j = 0; j < m; ++j) {
@@ -225,10 +287,16 @@ void window_polys(int w, double beta, int deg, std::vector<double> &out,
             t0 = t1;
             t1 = t2;
         }
-        for (int k = 0; k < m; ++k) {
-            out[(size_t)k * w + a] = (double)mono[k];
-            const float hi = (float)mono[k];
-            out_df[(size_t)k * w + a] = make_float2(hi, (float)(mono[k] - (long double)hi));
+        for (int k = 0; k < m; ++k) mono_all[(size_t)k * w + a] = mono[k];
+        if (deriv) {
+            long double *dc = mono_all.data() + (size_t)m * w;
+            for (int k = 0; k < deg; ++k) dc[(size_t)k * w + a] = 2.0L * (k + 1) * mono[k + 1];
+            for (int sidx = 0; sidx <= 64; ++sidx) {
+                const long double x = -1.0L + sidx / 32.0L;
+                long double pd = dc[(size_t)(deg - 1) * w + a];
+                for (int k = deg - 2; k >= 0; --k) pd = pd * x + dc[(size_t)k * w + a];
+                if (fabsl(pd) > *dmax) *dmax = (double)fabsl(pd);
+            }
         }
     }
 }
@@ -333,7 +401,8 @@ void buf_free(yk_plan_t p, DevBuf &b)
 void free_all(yk_plan_t p)
 {
     DevBuf *all[] = {&p->grid, &p->spec, &p->mult, &p->tw, &p->perm_h, &p->iperm_f, &p->win,
-                     &p->win_df,
+                     &p->win_df, &p->win32, &p->wnu, &p->stage_d[0], &p->stage_d[1],
+                     &p->stage_d[2], &p->stage_d[3], &p->stage_d[4], &p->stage_d[5],
                      &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->tile_order, &p->trg_cnt,
                      &p->trg_ptr,
                      &p->trg_cur, &p->err, &p->w_src, &p->src_t, &p->ent_t, &p->ent_j,
@@ -488,20 +557,40 @@ yk_status plan_tables(yk_plan_t p)
         const double ph = window_ft(2.0 * kPi * (double)m / (double)n, p->w, p->beta);
         dfac[m] = 1.0 / (ph * ph);
     }
-    if (!f32) {
-        /* FP64 windows as per-tap polynomials of degree w + 1 */
+    if (!f32 || p->dlp) {
+        /* windows as per-tap polynomials of degree w + 1 (the FP64 path always; FP32C for its
+         * dipoles), followed by the derivative's coefficients when the plan takes dipoles */
         p->wdeg = p->w + 1;
-        std::vector<double> poly;
-        std::vector<float2> poly_df;
-        window_polys(p->w, p->beta, p->wdeg, poly, poly_df);
-        if ((s = buf_alloc(p, p->win, sizeof(double) * poly.size(), "window")) != YK_OK) return s;
-        if ((s = buf_alloc(p, p->win_df, sizeof(float2) * poly_df.size(), "window")) != YK_OK)
-            return s;
-        cudaError_t ew = cudaMemcpy(p->win.ptr, poly.data(), sizeof(double) * poly.size(),
-                                    cudaMemcpyHostToDevice);
-        if (ew == cudaSuccess)
-            ew = cudaMemcpy(p->win_df.ptr, poly_df.data(), sizeof(float2) * poly_df.size(),
+        std::vector<long double> mono;
+        p->dmax = 0.0;
+        window_polys(p->w, p->beta, p->wdeg, p->dlp != 0, mono, &p->dmax);
+        p->dmax *= 1.0 + 1e-6;
+        cudaError_t ew = cudaSuccess;
+        if (!f32) {
+            std::vector<double> poly(mono.size());
+            std::vector<float2> poly_df(mono.size());
+            for (size_t i = 0; i < mono.size(); ++i) {
+                poly[i] = (double)mono[i];
+                const float hi = (float)mono[i];
+                poly_df[i] = make_float2(hi, (float)(mono[i] - (long double)hi));
+            }
+            if ((s = buf_alloc(p, p->win, sizeof(double) * poly.size(), "window")) != YK_OK)
+                return s;
+            if ((s = buf_alloc(p, p->win_df, sizeof(float2) * poly_df.size(), "window")) != YK_OK)
+                return s;
+            ew = cudaMemcpy(p->win.ptr, poly.data(), sizeof(double) * poly.size(),
                             cudaMemcpyHostToDevice);
+            if (ew == cudaSuccess)
+                ew = cudaMemcpy(p->win_df.ptr, poly_df.data(), sizeof(float2) * poly_df.size(),
+                                cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> poly32(mono.size());
+            for (size_t i = 0; i < mono.size(); ++i) poly32[i] = (float)mono[i];
+            if ((s = buf_alloc(p, p->win32, sizeof(float) * poly32.size(), "window")) != YK_OK)
+                return s;
+            ew = cudaMemcpy(p->win32.ptr, poly32.data(), sizeof(float) * poly32.size(),
+                            cudaMemcpyHostToDevice);
+        }
         if (ew != cudaSuccess) return cuda_fail(ew, "window table");
     }
     DevBuf d_dfac = {nullptr, 0};
@@ -544,7 +633,7 @@ void yk_set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
 {
     yk_plan_s *p = const_cast<yk_plan_s *>(pc);
-    if (p->zero || p->n_src == 0 || p->n_trg == 0) return false;
+    if (p->zero || p->n_src + p->n_dip == 0 || p->n_trg == 0) return false;
     std::memset((void *)d, 0, sizeof *d);
     d->g = geom_of(p);
     d->sth = p->st_half;
@@ -571,6 +660,11 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->win = P<double>(p->win);
     d->win_df = P<float2>(p->win_df);
     d->wdeg = p->wdeg;
+    d->n_chg = (int)p->n_src;
+    d->dip = p->n_dip > 0 ? 1 : 0;
+    d->wnu = P<double2>(p->wnu);
+    d->win32 = P<float>(p->win32);
+    d->dmax = p->dmax;
     for (int s = 0; s < yk::ST_COUNT; ++s) {
         d->items[s] = yk::stage_items(*d, s);
         d->smem[s] = yk::stage_smem(*d, s);
@@ -632,9 +726,13 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
     p->alloc_ctx = o->alloc_ctx;
 
     /* Fourier cutoff (eq. kmax) and period (decay length of G_H beyond the box span) */
+    p->dlp = o->dlp ? 1 : 0;
     p->kmax = o->kmax > 0.0         ? o->kmax
               : o->kmax_rule == 1 ? kmax_paper(alpha, delta, p->eps)
                                   : kmax_relative(alpha, delta, p->eps);
+    if (p->dlp && !(o->kmax > 0.0)) /* the double layer's cutoff (eq. kmax_dlp) is stricter */
+        p->kmax = std::max(p->kmax, o->kmax_rule == 1 ? kmax_dlp_paper(alpha, delta, p->eps)
+                                                      : kmax_dlp_relative(alpha, delta, p->eps));
     const double span = std::max(o->box[1] - o->box[0], o->box[3] - o->box[2]);
     p->period = o->period > 0.0 ? o->period : span + decay_length(alpha, delta, p->eps);
     if (!(p->period > span))
@@ -648,6 +746,10 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
 
     /* window width (digits of eps), grid size (>= 2 (2M+1), 5-smooth, with a tile edge) */
     int w = (int)std::ceil(std::log10(1.0 / p->eps)) + 1;
+    /* a dipole is spread with the window's gradient: its aliasing error is the charges' times up
+     * to |k'| / |k| ~ 3 (alias k' of a kept mode k at two-fold oversampling), so a plan that takes
+     * dipoles uses one more digit of window */
+    if (p->dlp) ++w;
     w = std::min(16, std::max(2, w));
     p->w = w;
     p->beta = 2.30 * w;
@@ -693,7 +795,8 @@ static int64_t predicted_bytes(const yk_plan_s *p, int64_t n_src, int64_t n_trg)
     const int64_t r = p->precision == YK_FP32C ? 4 : 8; /* bytes of the real type */
     int64_t b = r * n * n + 2 * r * (M + 1) * n + r * (M + 1) * (2 * M + 1) + 2 * r * n +
                 4 * (n / 2) + 4 * n + 4 * (7 * nt2 + 2) + 4;
-    if (p->precision == YK_FP64) b += 8 * (int64_t)(p->w + 2) * p->w;
+    if (p->precision == YK_FP64) b += 8 * (int64_t)(p->w + 2) * p->w * (p->dlp ? 2 : 1);
+    else if (p->dlp) b += 4 * (int64_t)(2 * p->w + 3) * p->w;
     b += n_src * (8 + 16 + 4 * (16 + 4)) + n_trg * (16 + 4 + 16);
     return b;
 }
@@ -777,19 +880,25 @@ yk_status yk_plan_info(yk_plan_t p, yk_info *info)
     return YK_OK;
 }
 
-yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const double *ys,
-                        const double *w, int64_t n_trg, const double *xt, const double *yt)
+yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const double *ys,
+                           const double *w, int64_t n_dip, const double *xd, const double *yd,
+                           const double *wd, const double *nx, const double *ny, int64_t n_trg,
+                           const double *xt, const double *yt)
 {
     if (!p) return fail(YK_ERR_ARG, "plan is NULL");
-    if (n_src < 0 || n_trg < 0) return fail(YK_ERR_ARG, "negative point count");
-    if (n_src > (1ll << 28) || n_trg > (1ll << 30))
+    if (n_src < 0 || n_trg < 0 || n_dip < 0) return fail(YK_ERR_ARG, "negative point count");
+    if (n_src + n_dip > (1ll << 28) || n_trg > (1ll << 30))
         return fail(YK_ERR_UNSUPPORTED, "too many points for 32-bit entry indices");
-    if ((n_src > 0 && (!xs || !ys || !w)) || (n_trg > 0 && (!xt || !yt)))
-        return fail(YK_ERR_ARG, "NULL coordinate or weight array");
+    if ((n_src > 0 && (!xs || !ys || !w)) || (n_trg > 0 && (!xt || !yt)) ||
+        (n_dip > 0 && (!xd || !yd || !wd || !nx || !ny)))
+        return fail(YK_ERR_ARG, "NULL coordinate, weight or normal array");
+    if (n_dip > 0 && !p->dlp)
+        return fail(YK_ERR_ARG, "dipole sources need a plan created with opts.dlp");
     if (p->status != YK_OK) return fail((yk_status)p->status, "plan is in an error state");
     p->points_set = false;
     ++p->layout_version;
     p->n_src = n_src;
+    p->n_dip = n_dip;
     p->n_trg = n_trg;
     if (p->zero) {
         p->points_set = true;
@@ -800,28 +909,37 @@ yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const doub
     do {                                                                                        \
         if ((s = (x)) != YK_OK) return s;                                                       \
     } while (0)
-    const size_t ns = (size_t)n_src, nt = (size_t)n_trg;
+    const size_t ns = (size_t)n_src, nd = (size_t)n_dip, nt = (size_t)n_trg;
     YK_TRY(buf_alloc(p, p->w_src, sizeof(double) * ns, "weights"));
-    YK_TRY(buf_alloc(p, p->src_t, sizeof(double2) * ns, "source coordinates"));
-    YK_TRY(buf_alloc(p, p->ent_t, sizeof(double2) * 4 * ns, "entries"));
-    YK_TRY(buf_alloc(p, p->ent_j, sizeof(int) * 4 * ns, "entries"));
+    YK_TRY(buf_alloc(p, p->src_t, sizeof(double2) * (ns + nd), "source coordinates"));
+    YK_TRY(buf_alloc(p, p->ent_t, sizeof(double2) * 4 * (ns + nd), "entries"));
+    YK_TRY(buf_alloc(p, p->ent_j, sizeof(int) * 4 * (ns + nd), "entries"));
     YK_TRY(buf_alloc(p, p->trg_t, sizeof(double2) * nt, "targets"));
     YK_TRY(buf_alloc(p, p->trg_idx, sizeof(int) * nt, "targets"));
     YK_TRY(buf_alloc(p, p->trg_tmp, sizeof(double2) * nt, "targets"));
+    if (nd > 0) YK_TRY(buf_alloc(p, p->wnu, sizeof(double2) * nd, "dipole weights"));
     const yk::Geom g = geom_of(p);
     const double *dx = nullptr, *dy = nullptr, *dw = nullptr;
     YK_TRY(to_device(p, xs, n_src, p->stage_x, &dx, "source x"));
     YK_TRY(to_device(p, ys, n_src, p->stage_y, &dy, "source y"));
     YK_TRY(to_device(p, w, n_src, p->stage_w, &dw, "weights"));
+    const double *ddx = nullptr, *ddy = nullptr, *ddw = nullptr, *dnx = nullptr, *dny = nullptr;
+    YK_TRY(to_device(p, xd, n_dip, p->stage_d[0], &ddx, "dipole x"));
+    YK_TRY(to_device(p, yd, n_dip, p->stage_d[1], &ddy, "dipole y"));
+    YK_TRY(to_device(p, wd, n_dip, p->stage_d[2], &ddw, "dipole weights"));
+    YK_TRY(to_device(p, nx, n_dip, p->stage_d[3], &dnx, "dipole normals"));
+    YK_TRY(to_device(p, ny, n_dip, p->stage_d[4], &dny, "dipole normals"));
     if (n_src > 0)
         YK_CU(cudaMemcpyAsync(p->w_src.ptr, dw, sizeof(double) * ns, cudaMemcpyDeviceToDevice,
                               p->stream),
               "weights");
+    YK_CU(yk::launch_pack_wnu(n_dip, ddw, dnx, dny, P<double2>(p->wnu), p->stream),
+          "dipole weights");
     stage_begin(p, YK_STAGE_BIN_SRC);
-    YK_CU(yk::launch_bin_sources(g, n_src, dx, dy, P<double2>(p->src_t), P<int>(p->tile_cnt),
-                                 P<int>(p->tile_ptr), P<int>(p->tile_cur), P<double2>(p->ent_t),
-                                 P<int>(p->ent_j), P<int>(p->err), p->stream,
-                                 p->precision == YK_FP32C),
+    YK_CU(yk::launch_bin_sources(g, n_src, dx, dy, n_dip, ddx, ddy, P<double2>(p->src_t),
+                                 P<int>(p->tile_cnt), P<int>(p->tile_ptr), P<int>(p->tile_cur),
+                                 P<double2>(p->ent_t), P<int>(p->ent_j), P<int>(p->err),
+                                 p->stream, p->precision == YK_FP32C),
           "bin sources");
     /* the cursors are free after the fill: they serve as the ordering's scratch */
     YK_CU(yk::launch_tile_order(P<int>(p->tile_ptr), p->nt * p->nt, P<int>(p->tile_order),
@@ -841,7 +959,8 @@ yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const doub
     stage_end(p, YK_STAGE_BIN_TRG);
 #undef YK_TRY
     /* host inputs: return after the copies are consumed so the caller may reuse its arrays */
-    if (!is_device_ptr(xs) || !is_device_ptr(xt)) {
+    if ((n_src > 0 && !is_device_ptr(xs)) || (n_trg > 0 && !is_device_ptr(xt)) ||
+        (n_dip > 0 && !is_device_ptr(xd))) {
         s = sync_and_check(p);
         if (s != YK_OK) return s;
     }
@@ -849,13 +968,23 @@ yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const doub
     return YK_OK;
 }
 
-yk_status yk_eval_longrange(yk_plan_t p, const double *density, double *u)
+yk_status yk_set_points(yk_plan_t p, int64_t n_src, const double *xs, const double *ys,
+                        const double *w, int64_t n_trg, const double *xt, const double *yt)
+{
+    return yk_set_points_dl(p, n_src, xs, ys, w, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                            n_trg, xt, yt);
+}
+
+yk_status yk_eval_longrange_dl(yk_plan_t p, const double *density, const double *mu, double *u)
 {
     if (!p) return fail(YK_ERR_ARG, "plan is NULL");
     if (!p->points_set) return fail(YK_ERR_STATE, "yk_set_points has not been called");
     if (p->status != YK_OK) return fail((yk_status)p->status, "plan is in an error state");
     if ((p->n_src > 0 && !density) || (p->n_trg > 0 && !u))
         return fail(YK_ERR_ARG, "NULL density or output array");
+    if (p->n_dip > 0 && !mu)
+        return fail(YK_ERR_ARG, "the plan's points include dipoles: give their density mu "
+                                "(yk_eval_longrange_dl)");
     const bool host_u = p->n_trg > 0 && !is_device_ptr(u);
     yk_status s;
     double *du = u;
@@ -865,14 +994,17 @@ yk_status yk_eval_longrange(yk_plan_t p, const double *density, double *u)
         du = P<double>(p->stage_u);
     }
     if (p->n_trg > 0) {
-        if (p->zero || p->n_src == 0) {
+        if (p->zero || p->n_src + p->n_dip == 0) {
             YK_CU(cudaMemsetAsync(du, 0, sizeof(double) * (size_t)p->n_trg, p->stream), "zero output");
         } else {
-            const double *dd = nullptr;
+            const double *dd = nullptr, *dmu = nullptr;
             if ((s = to_device(p, density, p->n_src, p->stage_w, &dd, "density")) != YK_OK) return s;
+            if ((s = to_device(p, mu, p->n_dip, p->stage_d[5], &dmu, "dipole density")) != YK_OK)
+                return s;
             yk::Inst d;
             yk_fill_inst(p, &d);
             d.dens = dd;
+            d.mu = dmu;
             d.u = du;
             static const char *names[yk::ST_COUNT] = {"spread", "row FFT", "column FFT",
                                                       "row inverse FFT", "interpolation"};
@@ -889,8 +1021,16 @@ yk_status yk_eval_longrange(yk_plan_t p, const double *density, double *u)
               "output copy");
         return sync_and_check(p);
     }
-    if (p->n_src > 0 && !is_device_ptr(density)) return sync_and_check(p);
+    if ((p->n_src > 0 && !is_device_ptr(density)) || (p->n_dip > 0 && !is_device_ptr(mu)))
+        return sync_and_check(p);
     return YK_OK;
+}
+
+yk_status yk_eval_longrange(yk_plan_t p, const double *density, double *u)
+{
+    if (p && p->n_dip > 0)
+        return fail(YK_ERR_ARG, "the plan's points include dipoles: use yk_eval_longrange_dl");
+    return yk_eval_longrange_dl(p, density, nullptr, u);
 }
 
 yk_status yk_stage_times(yk_plan_t p, double *ms)

@@ -184,6 +184,10 @@ yk_status build(yk_batch_s *b)
         if (!p) return bfail(YK_ERR_ARG, "plan %d is NULL", i);
         if (!p->points_set) return bfail(YK_ERR_STATE, "plan %d has no points (yk_set_points)", i);
         if (p->status != YK_OK) return bfail((yk_status)p->status, "plan %d is in an error state", i);
+        if (p->n_dip > 0)
+            return bfail(YK_ERR_UNSUPPORTED,
+                         "plan %d has dipole sources: batches take charges only "
+                         "(use yk_eval_longrange_dl)", i);
         b->versions[i] = p->layout_version;
         Inst d;
         if (!yk_fill_inst(p, &d)) {

@@ -60,6 +60,16 @@ struct Inst {
                                  window formula is evaluated directly */
     int wdeg;                 /* polynomial degree */
     const float2 *win_df;     /* the same coefficients as FP32 pairs (hi, lo), double-float path */
+    /* double layer: entries with source index j >= n_chg are dipoles d = j - n_chg of vector
+     * strength mu[d] * wnu[d] (weight times unit normal), spread with the window's gradient.
+     * With dip set, win / win_df / win32 hold after the window's (wdeg+1) x w coefficients the
+     * wdeg x w coefficients of its derivative phi'(z) (z in cells) in the same variable x. */
+    int dip;                  /* nonzero: this evaluation has dipole sources */
+    int n_chg;                /* number of charge sources (dipoles follow in the index space) */
+    const double *mu;         /* double-layer density (n_dip, device) */
+    const double2 *wnu;       /* wd * (nx, ny) per dipole (device) */
+    const float *win32;       /* FP32C with dipoles: window and derivative polynomials in FP32 */
+    double dmax;              /* bound on |phi'| over the window (cells^-1), for the FP64 scale */
     int items[ST_COUNT];      /* work items of each stage */
     int smem[ST_COUNT];       /* dynamic shared memory of each stage (bytes) */
 };
@@ -74,9 +84,15 @@ int rows_per_item(int n, bool f32);
 
 /* kernel launchers (yk_kernels.cu); all enqueue on `st` and return the launch status.
  * f32 selects the FP32C entry layout (first tap + FP32 offset) for the binned points. */
+/* sources: ns charges (xs, ys) then nd dipoles (xd, yd); src_t holds ns + nd grid coordinates and
+ * a dipole's entries carry source index ns + d */
 cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
-                               double2 *src_t, int *tile_cnt, int *tile_ptr, int *tile_cur,
-                               double2 *ent_t, int *ent_j, int *err, cudaStream_t st, bool f32);
+                               int64_t nd, const double *xd, const double *yd, double2 *src_t,
+                               int *tile_cnt, int *tile_ptr, int *tile_cur, double2 *ent_t,
+                               int *ent_j, int *err, cudaStream_t st, bool f32);
+/* wnu[d] = wd[d] * (nx[d], ny[d]) */
+cudaError_t launch_pack_wnu(int64_t nd, const double *wd, const double *nx, const double *ny,
+                            double2 *wnu, cudaStream_t st);
 cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, const double *yt,
                                double2 *trg_tmp, int *cnt, int *ptr, int *cur, double2 *trg_t,
                                int *trg_idx, int *err, cudaStream_t st, bool f32);
@@ -157,7 +173,10 @@ struct yk_plan_s {
     DevBuf iperm_f;  /* int[n]: frequency held at DIF position i (full-length transform) */
     DevBuf win;      /* double[(wdeg+1) * w]: window polynomials of the FP64 path */
     DevBuf win_df;   /* float2[(wdeg+1) * w]: the same as FP32 pairs (double-float path) */
+    DevBuf win32;    /* float: FP32C window + derivative polynomials (plans with dlp) */
     int wdeg;
+    int dlp;         /* plan takes dipole sources */
+    double dmax;     /* bound on |phi'| (cells^-1) */
     DevBuf tile_cnt, tile_ptr, tile_cur; /* int[nt^2], int[nt^2+1], int[nt^2] (sources) */
     DevBuf tile_order; /* int[nt^2]: heavy-first processing order of the source tiles */
     DevBuf trg_cnt, trg_ptr, trg_cur;    /* same for targets */
@@ -166,8 +185,9 @@ struct yk_plan_s {
     /* resident point layout (grown on demand) */
     bool points_set;
     int64_t layout_version; /* incremented by every yk_set_points */
-    int64_t n_src, n_trg;
+    int64_t n_src, n_trg, n_dip;
     DevBuf w_src;    /* double[n_src]: quadrature weights, original order */
+    DevBuf wnu;      /* double2[n_dip]: dipole weight times unit normal */
     DevBuf src_t;    /* double2[n_src]: grid coordinates of the sources, original order */
     DevBuf ent_t;    /* 16 B x (<= 4 n_src): (source, tile) entries grouped by tile; FP64: grid
                         coordinate (double2); FP32C: first tap and FP32 offset (int2 + float2) */
@@ -177,6 +197,7 @@ struct yk_plan_s {
     DevBuf trg_tmp;  /* double2[n_trg]: grid coordinates in original order */
     /* staging copies of host arrays */
     DevBuf stage_x, stage_y, stage_w, stage_u;
+    DevBuf stage_d[6]; /* dipole inputs xd, yd, wd, nx, ny and the density mu */
     int status;      /* sticky yk_status */
 
     /* optional stage timing: a ring of kEventRing runs per stage; events[r][2 s] and

@@ -120,7 +120,7 @@ __global__ void k_bin_src_count(int64_t ns, const double *__restrict__ xs,
 template <int W, bool F32>
 __global__ void k_bin_src_fill(int64_t ns, const double2 *__restrict__ src_t, Geom g,
                                const int *__restrict__ ptr, int *__restrict__ cur,
-                               double2 *__restrict__ ent_t, int *__restrict__ ent_j)
+                               double2 *__restrict__ ent_t, int *__restrict__ ent_j, int joff)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int tiles[4] = {-1, -1, -1, -1};
@@ -135,7 +135,7 @@ __global__ void k_bin_src_fill(int64_t ns, const double2 *__restrict__ src_t, Ge
         if (v) {
             const int slot = ptr[tiles[r]] + off;
             ent_t[slot] = rec;
-            ent_j[slot] = (int)j;
+            ent_j[slot] = (int)j + joff;
         }
     }
 }
@@ -409,23 +409,30 @@ int stage_items(const Inst &d, int stage)
 int stage_smem(const Inst &d, int stage)
 {
     const int T = d.g.T, W = d.g.w;
-    const int win_bytes = d.win ? (int)sizeof(double) * (d.wdeg + 1) * W : 0;
-    const int c = d.f32 ? 8 : 16; /* bytes of a complex value */
+    /* window coefficients (and, with dipoles, the derivative's) staged by the FP64 kernels */
+    const int ncoef = (d.wdeg + 1) * W + (d.dip ? d.wdeg * W : 0);
+    const int win_bytes = d.win ? (int)sizeof(double) * ncoef : 0;
+    const int SW = d.dip ? 4 * W : 2 * W; /* window values kept per spread entry */
+    const int c = d.f32 ? 8 : 16;          /* bytes of a complex value */
     switch (stage) {
     case ST_SPREAD:
         if (d.fft_df)
             return (int)(sizeof(df32) * kSpreadWarps * T * (T + 1) +
-                         sizeof(df32) * kSpreadWarps * 32 * 2 * W + sizeof(int) * kSpreadWarps * 64 +
-                         sizeof(df32) * (d.wdeg + 1) * W);
+                         sizeof(df32) * kSpreadWarps * 32 * SW + sizeof(int) * kSpreadWarps * 64 +
+                         sizeof(df32) * ncoef);
         return d.f32 ? (int)(sizeof(float2) * kSpreadWarps * T * (T + 1) +
-                             sizeof(float) * kSpreadWarps * 32 * 2 * W + sizeof(int) * kSpreadWarps * 64)
+                             sizeof(float) * kSpreadWarps * 32 * SW +
+                             sizeof(int) * kSpreadWarps * 64 + (d.dip ? sizeof(float) * ncoef : 0))
                      : (int)(sizeof(unsigned long long) * T * T + win_bytes);
     case ST_ROW_FWD:
     case ST_ROW_INV: return c * d.rows * (d.n / 2);
     case ST_COLUMNS: return c * d.n;
-    default:
-        if (d.fft_df) return 8 * (T + W) * (T + W) + (int)sizeof(df32) * (d.wdeg + 1) * W;
-        return d.f32 ? 4 * (T + W) * (T + W) : 8 * (T + W) * (T + W) + win_bytes;
+    default: {
+        const int nw = (d.wdeg + 1) * W; /* interpolation stages the window only */
+        if (d.fft_df) return 8 * (T + W) * (T + W) + (int)sizeof(df32) * nw;
+        return d.f32 ? 4 * (T + W) * (T + W)
+                     : 8 * (T + W) * (T + W) + (d.win ? (int)sizeof(double) * nw : 0);
+    }
     }
 }
 
@@ -467,32 +474,57 @@ cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStrea
 }
 
 cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
-                               double2 *src_t, int *tile_cnt, int *tile_ptr, int *tile_cur,
-                               double2 *ent_t, int *ent_j, int *err, cudaStream_t st, bool f32)
+                               int64_t nd, const double *xd, const double *yd, double2 *src_t,
+                               int *tile_cnt, int *tile_ptr, int *tile_cur, double2 *ent_t,
+                               int *ent_j, int *err, cudaStream_t st, bool f32)
 {
     const int ntiles = g.nt * g.nt;
     cudaError_t e = cudaMemsetAsync(tile_cnt, 0, sizeof(int) * ntiles, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(tile_cur, 0, sizeof(int) * ntiles, st);
     if (e != cudaSuccess) return e;
-    const int blocks = (int)((ns + 255) / 256);
-    if (ns > 0) {
-#define YK_CALL(W) k_bin_src_count<W><<<blocks, 256, 0, st>>>(ns, xs, ys, g, src_t, tile_cnt, err)
+    /* the two point sets: charges, then dipoles (index offset ns) */
+    const int64_t cnt[2] = {ns, nd};
+    const double *px[2] = {xs, xd}, *py[2] = {ys, yd};
+    double2 *pt[2] = {src_t, src_t + ns};
+    for (int k = 0; k < 2; ++k) {
+        if (cnt[k] <= 0) continue;
+        const int blocks = (int)((cnt[k] + 255) / 256);
+#define YK_CALL(W)                                                                              \
+    k_bin_src_count<W><<<blocks, 256, 0, st>>>(cnt[k], px[k], py[k], g, pt[k], tile_cnt, err)
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     }
     if ((e = launch_scan(tile_cnt, tile_ptr, ntiles, tile_cur, st)) != cudaSuccess) return e;
-    if (ns > 0) {
+    for (int k = 0; k < 2; ++k) {
+        if (cnt[k] <= 0) continue;
+        const int blocks = (int)((cnt[k] + 255) / 256);
+        const int joff = k ? (int)ns : 0;
 #define YK_CALL(W)                                                                              \
     if (f32)                                                                                    \
-        k_bin_src_fill<W, true><<<blocks, 256, 0, st>>>(ns, src_t, g, tile_ptr, tile_cur, ent_t, \
-                                                        ent_j);                                 \
+        k_bin_src_fill<W, true><<<blocks, 256, 0, st>>>(cnt[k], pt[k], g, tile_ptr, tile_cur,   \
+                                                        ent_t, ent_j, joff);                    \
     else                                                                                        \
-        k_bin_src_fill<W, false><<<blocks, 256, 0, st>>>(ns, src_t, g, tile_ptr, tile_cur,      \
-                                                         ent_t, ent_j)
+        k_bin_src_fill<W, false><<<blocks, 256, 0, st>>>(cnt[k], pt[k], g, tile_ptr, tile_cur,  \
+                                                         ent_t, ent_j, joff)
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     }
+    return cudaGetLastError();
+}
+
+__global__ void k_pack_wnu(int64_t nd, const double *__restrict__ wd, const double *__restrict__ nx,
+                           const double *__restrict__ ny, double2 *__restrict__ wnu)
+{
+    const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < nd) wnu[d] = make_double2(wd[d] * nx[d], wd[d] * ny[d]);
+}
+
+cudaError_t launch_pack_wnu(int64_t nd, const double *wd, const double *nx, const double *ny,
+                            double2 *wnu, cudaStream_t st)
+{
+    if (nd <= 0) return cudaSuccess;
+    k_pack_wnu<<<(int)((nd + 255) / 256), 256, 0, st>>>(nd, wd, nx, ny, wnu);
     return cudaGetLastError();
 }
 

@@ -127,9 +127,16 @@ __device__ __forceinline__ df32 window_arg_df(int l0, double t, int W)
     return df32(2.0 * (((double)l0 - t) + 0.5 * W) - 1.0);
 }
 
-__device__ __forceinline__ df32 *stage_window_df(const Inst &d, df32 *dst)
+/* window coefficients, followed by the derivative's when the evaluation has dipoles */
+__device__ __forceinline__ int window_coeffs(const Inst &d)
 {
-    const int m = (d.wdeg + 1) * d.g.w;
+    return (d.wdeg + 1) * d.g.w + (d.dip ? d.wdeg * d.g.w : 0);
+}
+
+/* copy the first m double-float window coefficients into shared memory (the spread takes the
+ * derivative's too, the interpolation the window's only) */
+__device__ __forceinline__ df32 *stage_window_df(const Inst &d, df32 *dst, int m)
+{
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const float2 c = d.win_df[i];
         dst[i] = df32(c.x, c.y);
@@ -138,12 +145,19 @@ __device__ __forceinline__ df32 *stage_window_df(const Inst &d, df32 *dst)
 }
 
 /* copy the window polynomials into shared memory (NULL when the formula is used) */
-__device__ __forceinline__ const double *stage_window(const Inst &d, double *dst)
+__device__ __forceinline__ const double *stage_window(const Inst &d, double *dst, int m)
 {
     if (!d.win) return nullptr;
-    const int m = (d.wdeg + 1) * d.g.w;
     for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = d.win[i];
     return dst;
+}
+
+/* FP32 Horner on per-tap polynomials (FP32C dipoles): x = 2u - 1 as for windows64 */
+template <int W> __device__ __forceinline__ float window32(const float *cw, int deg, int a, float x)
+{
+    float p = cw[deg * W + a];
+    for (int k = deg - 1; k >= 0; --k) p = fmaf(p, x, cw[k * W + a]);
+    return p;
 }
 
 /* ----------------------------------------------------------------------------------------- */
@@ -165,12 +179,17 @@ template <int W> __device__ void st_spread64(const Inst &d, int item, unsigned c
     const double *__restrict__ dens = d.dens;
     double *__restrict__ grid = static_cast<double *>(d.grid);
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) acc[i] = 0ull;
-    const double *cw = stage_window(d, reinterpret_cast<double *>(acc + T * T));
+    const double *cw = stage_window(d, reinterpret_cast<double *>(acc + T * T), window_coeffs(d));
     const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
     double mq = 0.0;
     for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
         const int j = d.ent_j[e];
-        mq = fmax(mq, fabs(wq[j] * dens[j]));
+        if (!d.dip || j < d.n_chg) {
+            mq = fmax(mq, fabs(wq[j] * dens[j]));
+        } else { /* a dipole's taps are at most (|s_x| + |s_y|) max|phi'| */
+            const double2 wn = d.wnu[j - d.n_chg];
+            mq = fmax(mq, fabs(d.mu[j - d.n_chg] * g.inv_h) * (fabs(wn.x) + fabs(wn.y)) * d.dmax);
+        }
     }
     mq = block_max(mq, red);
     if (threadIdx.x == 0) {
@@ -186,7 +205,6 @@ template <int W> __device__ void st_spread64(const Inst &d, int item, unsigned c
         for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
             const double2 t = d.ent_t[e];
             const int j = d.ent_j[e];
-            const double qs = ldexp(wq[j] * dens[j], kexp);
             const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
             double fx[W], fy[W];
             windows64<W>(fx, lx, t.x, cw, d.wdeg, g);
@@ -195,6 +213,36 @@ template <int W> __device__ void st_spread64(const Inst &d, int item, unsigned c
             if (dx0 < 0) dx0 += g.n;
             int dy0 = (ly - Y0) % g.n;
             if (dy0 < 0) dy0 += g.n;
+            if (d.dip && j >= d.n_chg) {
+                /* dipole: taps s_x phi'(X - t_x) phi(Y - t_y) + s_y phi(X - t_x) phi'(Y - t_y),
+                 * s = -mu w nu / h (the gradient of the window in the source point) */
+                const double2 wn = d.wnu[j - d.n_chg];
+                const double m = ldexp(-d.mu[j - d.n_chg] * g.inv_h, kexp);
+                const double sx = m * wn.x, sy = m * wn.y;
+                double gx[W], gy[W];
+                windows64<W>(gx, lx, t.x, cw + (d.wdeg + 1) * W, d.wdeg - 1, g);
+                windows64<W>(gy, ly, t.y, cw + (d.wdeg + 1) * W, d.wdeg - 1, g);
+#pragma unroll
+                for (int c = 0; c < W; ++c) {
+                    int yy = dy0 + c;
+                    if (yy >= g.n) yy -= g.n;
+                    if (yy < T) {
+                        const double ay = sx * fy[c], cy = sy * gy[c];
+#pragma unroll
+                        for (int a = 0; a < W; ++a) {
+                            int xx = dx0 + a;
+                            if (xx >= g.n) xx -= g.n;
+                            if (xx < T) {
+                                const double v = fma(cy, fx[a], ay * gx[a]);
+                                const long long iv = __double_as_longlong(v + kMagic) - magic_bits;
+                                atomicAdd(&acc[yy * T + xx], (unsigned long long)iv);
+                            }
+                        }
+                    }
+                }
+                continue;
+            }
+            const double qs = ldexp(wq[j] * dens[j], kexp);
 #pragma unroll
             for (int c = 0; c < W; ++c) {
                 int yy = dy0 + c;
@@ -233,9 +281,11 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
 {
     const Geom &g = d.g;
     const int T = g.T, PT = T + 1; /* padded pitch (float2 units) */
+    const int SW = d.dip ? 4 * W : 2 * W; /* window values kept per entry */
     float2 *acc = reinterpret_cast<float2 *>(sm);                          /* [warps][T][PT] */
-    float *wbuf = reinterpret_cast<float *>(acc + kSpreadWarps * T * PT);  /* [warps][32][2W] */
-    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * 2 * W); /* [warps][32][2] */
+    float *wbuf = reinterpret_cast<float *>(acc + kSpreadWarps * T * PT);  /* [warps][32][SW] */
+    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * SW);    /* [warps][32][2] */
+    float *cw32 = reinterpret_cast<float *>(obuf + kSpreadWarps * 64);     /* dipole windows */
     const int tile = d.order ? d.order[item] : item;
     const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
     const int X0 = txi * T, Y0 = tyi * T;
@@ -247,38 +297,62 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
             grid[(size_t)(Y0 + i / T) * g.n + X0 + i % T] = 0.0f;
         return;
     }
+    if (d.dip)
+        for (int i = threadIdx.x; i < window_coeffs(d); i += blockDim.x) cw32[i] = d.win32[i];
     for (int i = threadIdx.x; i < kSpreadWarps * T * PT; i += blockDim.x)
         acc[i] = make_float2(0.0f, 0.0f);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2 *mine = acc + warp * T * PT;
-    float *wb = wbuf + warp * 32 * 2 * W;
+    float *wb = wbuf + warp * 32 * SW;
     int *ob = obuf + warp * 64;
     const float beta = (float)g.beta, cw = (float)g.c;
+    const int D = d.wdeg;
     for (int b0 = beg + warp * 32; b0 < end; b0 += kSpreadWarps * 32) {
         const int e = b0 + lane;
         if (e < end) {
             const int4 r = ent[e];
             const int j = d.ent_j[e];
-            const float q = (float)(d.wq[j] * d.dens[j]);
             const float sx = __int_as_float(r.z), sy = __int_as_float(r.w);
+            float *wl = wb + lane * SW;
+            int flag = 0;
+            if (!d.dip || j < d.n_chg) {
+                const float q = (float)(d.wq[j] * d.dens[j]);
 #pragma unroll
-            for (int a = 0; a < W; ++a) {
-                wb[lane * 2 * W + a] = q * es_window_stable<float>(sy + (float)a, beta, cw);
-                wb[lane * 2 * W + W + a] = es_window_stable<float>(sx + (float)a, beta, cw);
+                for (int a = 0; a < W; ++a) {
+                    wl[a] = q * es_window_stable<float>(sy + (float)a, beta, cw);
+                    wl[W + a] = es_window_stable<float>(sx + (float)a, beta, cw);
+                }
+            } else {
+                /* dipole: s = -mu w nu / h; window and derivative from the FP32 polynomials */
+                const double2 wn = d.wnu[j - d.n_chg];
+                const double m = -d.mu[j - d.n_chg] * g.inv_h;
+                const float gx = (float)(m * wn.x), gy = (float)(m * wn.y);
+                const float xx = 2.0f * sx + (float)(W - 1), xy = 2.0f * sy + (float)(W - 1);
+                const float *cwd = cw32 + (D + 1) * W;
+#pragma unroll
+                for (int a = 0; a < W; ++a) {
+                    wl[a] = gx * window32<W>(cw32, D, a, xy);
+                    wl[W + a] = window32<W>(cwd, D - 1, a, xx);
+                    wl[2 * W + a] = gy * window32<W>(cwd, D - 1, a, xy);
+                    wl[3 * W + a] = window32<W>(cw32, D, a, xx);
+                }
+                flag = 1 << 30;
             }
             int dx0 = (r.x - X0) % g.n;
             if (dx0 < 0) dx0 += g.n;
             int dy0 = (r.y - Y0) % g.n;
             if (dy0 < 0) dy0 += g.n;
             ob[2 * lane] = dx0;
-            ob[2 * lane + 1] = dy0;
+            ob[2 * lane + 1] = dy0 | flag;
         }
         __syncwarp();
         const int cnt = min(32, end - b0);
         for (int k = 0; k < cnt; ++k) {
-            const int dx0 = ob[2 * k], dy0 = ob[2 * k + 1];
-            const float *wk = wb + k * 2 * W;
+            const int dx0 = ob[2 * k], dyf = ob[2 * k + 1];
+            const int dy0 = dyf & 0x3fffffff;
+            const bool dipk = dyf >> 30; /* warp-uniform: one entry at a time */
+            const float *wk = wb + k * SW;
 #pragma unroll
             for (int t0 = 0; t0 < W * W; t0 += 32) {
                 const int t = t0 + lane;
@@ -289,7 +363,8 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
                     int xx = dx0 + a;
                     if (xx >= g.n) xx -= g.n;
                     if (yy < T && xx < T) {
-                        const float v = wk[c] * wk[W + a];
+                        float v = wk[c] * wk[W + a];
+                        if (dipk) v = fmaf(wk[2 * W + c], wk[3 * W + a], v);
                         float2 cell = mine[yy * PT + xx];
                         const float s = __fadd_rn(cell.x, v);
                         const float bp = __fsub_rn(s, cell.x);
@@ -333,9 +408,10 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
     const Geom &g = d.g;
     const int T = g.T, PT = T + 1, D = d.wdeg;
     const int NW = blockDim.x >> 5;
+    const int SW = d.dip ? 4 * W : 2 * W; /* window values kept per entry */
     df32 *acc = reinterpret_cast<df32 *>(sm);                        /* [warps][T][PT] */
-    df32 *wbuf = acc + kSpreadWarps * T * PT;                        /* [warps][32][2W] */
-    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * 2 * W); /* [warps][64] */
+    df32 *wbuf = acc + kSpreadWarps * T * PT;                        /* [warps][32][SW] */
+    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * SW); /* [warps][64] */
     const int tile = d.order ? d.order[item] : item;
     const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
     const int X0 = txi * T, Y0 = tyi * T;
@@ -346,37 +422,58 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
             grid[(size_t)(Y0 + i / T) * g.n + X0 + i % T] = df32(0.0f, 0.0f);
         return;
     }
-    df32 *cw = stage_window_df(d, reinterpret_cast<df32 *>(obuf + kSpreadWarps * 64));
+    df32 *cw = stage_window_df(d, reinterpret_cast<df32 *>(obuf + kSpreadWarps * 64),
+                               window_coeffs(d));
     for (int i = threadIdx.x; i < NW * T * PT; i += blockDim.x) acc[i] = df32(0.0f, 0.0f);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     df32 *mine = acc + warp * T * PT;
-    df32 *wb = wbuf + warp * 32 * 2 * W;
+    df32 *wb = wbuf + warp * 32 * SW;
     int *ob = obuf + warp * 64;
+    const df32 *cwd = cw + (D + 1) * W; /* derivative coefficients (dipoles) */
     for (int b0 = beg + warp * 32; b0 < end; b0 += NW * 32) {
         const int e = b0 + lane;
         if (e < end) {
             const double2 t = d.ent_t[e];
             const int j = d.ent_j[e];
-            const df32 q(d.wq[j] * d.dens[j]);
             const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
             const df32 ax = window_arg_df(lx, t.x, W), ay = window_arg_df(ly, t.y, W);
-            for (int a = 0; a < W; ++a) {
-                wb[lane * 2 * W + a] = q * window_df<W>(cw, D, a, ay);
-                wb[lane * 2 * W + W + a] = window_df<W>(cw, D, a, ax);
+            df32 *wl = wb + lane * SW;
+            int flag = 0;
+            if (!d.dip || j < d.n_chg) {
+                const df32 q(d.wq[j] * d.dens[j]);
+                for (int a = 0; a < W; ++a) {
+                    wl[a] = q * window_df<W>(cw, D, a, ay);
+                    wl[W + a] = window_df<W>(cw, D, a, ax);
+                }
+            } else {
+                /* dipole: taps s_x phi'(X - t_x) phi(Y - t_y) + s_y phi(X - t_x) phi'(Y - t_y),
+                 * s = -mu w nu / h (the gradient of the window in the source point) */
+                const double2 wn = d.wnu[j - d.n_chg];
+                const double m = -d.mu[j - d.n_chg] * g.inv_h;
+                const df32 sx(m * wn.x), sy(m * wn.y);
+                for (int a = 0; a < W; ++a) {
+                    wl[a] = sx * window_df<W>(cw, D, a, ay);
+                    wl[W + a] = window_df<W>(cwd, D - 1, a, ax);
+                    wl[2 * W + a] = sy * window_df<W>(cwd, D - 1, a, ay);
+                    wl[3 * W + a] = window_df<W>(cw, D, a, ax);
+                }
+                flag = 1 << 30;
             }
             int dx0 = (lx - X0) % g.n;
             if (dx0 < 0) dx0 += g.n;
             int dy0 = (ly - Y0) % g.n;
             if (dy0 < 0) dy0 += g.n;
             ob[2 * lane] = dx0;
-            ob[2 * lane + 1] = dy0;
+            ob[2 * lane + 1] = dy0 | flag;
         }
         __syncwarp();
         const int cnt = min(32, end - b0);
         for (int k = 0; k < cnt; ++k) {
-            const int dx0 = ob[2 * k], dy0 = ob[2 * k + 1];
-            const df32 *wk = wb + k * 2 * W;
+            const int dx0 = ob[2 * k], dyf = ob[2 * k + 1];
+            const int dy0 = dyf & 0x3fffffff;
+            const bool dipk = dyf >> 30; /* warp-uniform: one entry at a time */
+            const df32 *wk = wb + k * SW;
 #pragma unroll
             for (int t0 = 0; t0 < W * W; t0 += 32) {
                 const int t = t0 + lane;
@@ -386,7 +483,11 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
                     if (yy >= g.n) yy -= g.n;
                     int xx = dx0 + a;
                     if (xx >= g.n) xx -= g.n;
-                    if (yy < T && xx < T) mine[yy * PT + xx] = mine[yy * PT + xx] + wk[c] * wk[W + a];
+                    if (yy < T && xx < T) {
+                        df32 v = wk[c] * wk[W + a];
+                        if (dipk) v = v + wk[2 * W + c] * wk[3 * W + a];
+                        mine[yy * PT + xx] = mine[yy * PT + xx] + v;
+                    }
                 }
             }
             __syncwarp(); /* the next entry may touch the same cells through other lanes */
@@ -588,7 +689,7 @@ template <int W> __device__ void st_interp64(const Inst &d, int item, unsigned c
     if (beg == end) return; /* uniform across the CTA */
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;
     stage_halo<double>(sg, static_cast<const double *>(d.grid), g, X0, Y0, P);
-    const double *cw = stage_window(d, sg + P * P);
+    const double *cw = stage_window(d, sg + P * P, (d.wdeg + 1) * W);
     __syncthreads();
     for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
         const double2 t = d.trg_t[e];
@@ -659,7 +760,7 @@ template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned 
     if (beg == end) return;
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;
     stage_halo<df32>(sg, static_cast<const df32 *>(d.grid), g, X0, Y0, P);
-    const df32 *cw = stage_window_df(d, sg + P * P);
+    const df32 *cw = stage_window_df(d, sg + P * P, (d.wdeg + 1) * W);
     __syncthreads();
     const int D = d.wdeg;
     for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {

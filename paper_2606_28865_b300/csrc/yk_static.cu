@@ -292,7 +292,8 @@ extern "C" YK_API yk_status yk_eval_longrange_static(double alpha, const yk_opts
                                   info.delta, 2.0 * 3.14159265358979323846 / info.period,
                                   info.period, st);
     if (e == cudaSuccess)
-        e = yk::launch_bin_sources(g, n_src, xs, ys, (double2 *)at(o_srct), (int *)at(o_tcnt),
+        e = yk::launch_bin_sources(g, n_src, xs, ys, 0, nullptr, nullptr, (double2 *)at(o_srct),
+                                   (int *)at(o_tcnt),
                                    (int *)at(o_tptr), (int *)at(o_tcur), (double2 *)at(o_entt),
                                    (int *)at(o_entj), (int *)at(o_err), st, false);
     if (e == cudaSuccess)

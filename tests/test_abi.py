@@ -67,6 +67,22 @@ def test_paper_kmax_rule_and_zero_case():
     assert info["kmax"] == pytest.approx(OP.kmax_paper(10.0, 0.0167, eps), rel=1e-14)
 
 
+@pytest.mark.parametrize("alpha,delta", [(10.0, 0.0167), (10.0, 3.93e-5), (1.0, 3.93e-5),
+                                         (100.0, 3.82e-5)])
+def test_double_layer_cutoff_rules(alpha, delta):
+    # opts.dlp: k_max also meets eq. kmax_dlp (relative reading, or as printed with kmax_rule=1)
+    eps = 1e-10 / 4
+    info = yk.plan_params(alpha, delta=delta, tol=1e-10, dlp=True)
+    ref = max(OP.kmax_relative(alpha, delta, eps), OP.kmax_dlp_relative(alpha, delta, eps))
+    assert info["kmax"] == pytest.approx(ref, rel=1e-8)
+    info = yk.plan_params(alpha, delta=delta, tol=1e-10, dlp=True, kmax_rule=1)
+    ref = max(OP.kmax_paper(alpha, delta, eps), OP.kmax_dlp_paper(alpha, delta, eps))
+    assert info["kmax"] == pytest.approx(ref, rel=1e-12)
+    plain = yk.plan_params(alpha, delta=delta, tol=1e-10)
+    assert info["kmax"] >= plain["kmax"]
+    assert info["w"] == plain["w"] + 1   # one more digit of window for the gradient spread
+
+
 @pytest.mark.parametrize("kw,status", [
     (dict(alpha=0.0, delta=0.01), yk.YK_ERR_ARG),
     (dict(alpha=-1.0, delta=0.01), yk.YK_ERR_ARG),
