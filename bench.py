@@ -52,6 +52,7 @@ def parse():
                     help="targets per alpha in each reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32c", action="store_true", help="skip the FP32C measurement")
+    ap.add_argument("--no-dlp", action="store_true", help="skip the double-layer measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch section")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-requests", type=int, default=4000,
@@ -513,6 +514,45 @@ def main():
         for a in alphas:
             plans32[a].close()
 
+    # the same step with the double layer D_H added: 1e5 boundary dipoles (the boundary nodes with
+    # their normals and mu = sin 2t + 0.3 cos t) on top of the charges, one grid for both
+    dlp = None
+    if not args.no_dlp:
+        xd, yd, wd, nx, ny, mu = W.double_layer_nodes(W.Starfish(), 6250)
+        t = lambda v: torch.as_tensor(v, dtype=torch.float64, device=dev)
+        dl_dev = tuple(t(v) for v in (xd, yd, wd, nx, ny))
+        mu_dev = t(mu)
+        plans_dl = {a: yk.Plan(a, tol=TOL, h_vol=works[a].h_vol, box=works[a].box, profile=True,
+                               stream=stream, dlp=True) for a in alphas}
+
+        def step_dl():
+            for a in alphas:
+                xs, ys, w, xt, yt, d = dbufs[a]
+                plans_dl[a].set_points(xs, ys, w, xt, yt, dipoles=dl_dev)
+                plans_dl[a].eval(d, out=outs[a], mu=mu_dev)
+
+        for _ in range(max(3, args.warmup)):
+            step_dl()
+        torch.cuda.synchronize()
+        for a in alphas:
+            plans_dl[a].stage_times()
+        barrier(pg)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_dl()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_dl = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
+        pts_dl = pts_step + len(alphas) * len(mu)
+        dlp = {"value": pts_dl * world / (ms_dl * 1e-3), "unit": "points/s",
+               "ms_per_step": ms_dl, "n_dip": int(len(mu)), "tol": TOL,
+               "what": "S_H + V_H + D_H: set_points_dl + eval_longrange_dl per alpha per step",
+               "w": {str(a): plans_dl[a].info["w"] for a in alphas},
+               "grids": {str(a): plans_dl[a].info["n_grid"] for a in alphas},
+               "stage_ms": {str(a): plans_dl[a].stage_times() for a in alphas}}
+        for a in alphas:
+            plans_dl[a].close()
+
     batch = None if args.no_batch else batch_section(yk, torch, rank)
     serving = None if args.no_serving else serving_section(yk, args.serve_requests)
 
@@ -549,6 +589,7 @@ def main():
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "what": "one yk_eval_longrange on a resident layout, all alphas"},
         "fp32c": fp32c,
+        "double_layer": dlp,
         "batch": batch,
         "serving": serving,
     }

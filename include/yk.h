@@ -92,6 +92,14 @@ typedef struct {
                            double-layer cutoff (Section 5.1, eq. kmax_dlp, read as kmax_rule says:
                            0: the tail of int exp(-delta(alpha^2+k^2)) k^2/(alpha^2+k^2) dk beyond
                            k_max is at most eps times the whole integral; 1: as printed) */
+    int truncate;       /* small-alpha path (the paper points to Vico et al. for alpha -> 0, Section
+                           5.2): every source-target distance is at most the box diagonal D, so G_H
+                           may be replaced by G_H chi with chi = 1 on r <= D and a smooth step to 0
+                           on [D, D + 12 s], s = 20 / k_max; the period then only needs to exceed
+                           the span by D + 12 s instead of by the decay length of G_H, and the
+                           multiplier is that kernel's radial transform (computed on the device
+                           at plan time).  0: automatic (when it gives the shorter period and
+                           opts.period is 0), 1: never, 2: always */
 } yk_opts;
 
 /* Parameters the plan chose (all derived from alpha, tol, delta and the box). */
@@ -108,6 +116,8 @@ typedef struct {
     int tile;                      /* tile edge (grid cells) */
     int precision;                 /* yk_precision */
     int64_t device_bytes;          /* device memory held by the plan now */
+    int truncated;                 /* 1: the truncated kernel is used (opts.truncate) */
+    double r_support;              /* truncated kernel: radius beyond which it is zero */
 } yk_info;
 
 /* Fill *o with defaults: FP64, tol 1e-10, delta rule with eps_hist 1e-6, box [-1.5,1.5]^2. */

@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
                 ("period", ctypes.c_double), ("tile", ctypes.c_int),
                 ("profile", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", _ALLOC),
                 ("free", _FREE), ("alloc_ctx", ctypes.c_void_p), ("use_tuned", ctypes.c_int),
-                ("n_src_hint", ctypes.c_int64), ("fft_fp64", ctypes.c_int), ("dlp", ctypes.c_int)]
+                ("n_src_hint", ctypes.c_int64), ("fft_fp64", ctypes.c_int), ("dlp", ctypes.c_int),
+                ("truncate", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -57,7 +58,8 @@ class Info(ctypes.Structure):
                 ("origin", ctypes.c_double * 2), ("h", ctypes.c_double),
                 ("n_modes", ctypes.c_int64), ("n_grid", ctypes.c_int64), ("w", ctypes.c_int),
                 ("beta", ctypes.c_double), ("tile", ctypes.c_int), ("precision", ctypes.c_int),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("truncated", ctypes.c_int),
+                ("r_support", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -128,7 +130,7 @@ def _len(a) -> int:
 def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
               box=(-1.5, 1.5, -1.5, 1.5), kmax=0.0, kmax_rule=0, period=0.0, tile=0,
               profile=False, stream=None, use_tuned=False, n_src_hint=0,
-              fft_fp64=False, dlp=False) -> Opts:
+              fft_fp64=False, dlp=False, truncate=0) -> Opts:
     o = Opts()
     _lib.yk_opts_default(ctypes.byref(o))
     o.precision = int(precision)
@@ -148,6 +150,7 @@ def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
     o.n_src_hint = int(n_src_hint)
     o.fft_fp64 = 1 if fft_fp64 else 0
     o.dlp = 1 if dlp else 0
+    o.truncate = int(truncate)
     return o
 
 

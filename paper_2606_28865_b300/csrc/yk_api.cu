@@ -81,6 +81,21 @@ double expint_e1(double x)
     return h * std::exp(-x);
 }
 
+/* modified Bessel function K_nu(x), x > 0, from K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt
+ * by the trapezoidal rule (step 1/16; the integrand is analytic in the strip |Im t| < pi/2, so the
+ * error is of order exp(-pi^2 16)), in long double, up to where x cosh t exceeds 11000 */
+double bessel_k(int nu, double x)
+{
+    const long double h = 1.0L / 16.0L, xl = x;
+    long double sum = 0.5L * expl(-xl);
+    for (int i = 1;; ++i) {
+        const long double t = h * i, c = coshl(t);
+        if (xl * c > 11000.0L) break;
+        sum += expl(-xl * c) * coshl(nu * t);
+    }
+    return (double)(h * sum);
+}
+
 /* Gauss-Legendre nodes/weights on [-1, 1] (Newton on the Legendre recurrence) */
 void gauss_legendre(int n, double *x, double *w)
 {
@@ -606,19 +621,60 @@ yk_status plan_tables(yk_plan_t p)
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_dfac.ptr, dfac.data(), sizeof(double) * (M + 1),
                             cudaMemcpyHostToDevice, p->stream);
+    /* truncated kernel: its radial transform on a fine k table (spacing H with R1 H = 0.22, so
+     * 10-point interpolation errs by ~1e-13 of the peak), up to the corner of the mode square */
+    DevBuf d_tab = {nullptr, 0}, d_nodes = {nullptr, 0};
+    const double dk = 2.0 * kPi / p->period;
+    double H = 0.0;
+    int ntab = 0;
+    if (e == cudaSuccess && p->truncated) {
+        H = 0.22 / p->r1;
+        const double ktop = std::sqrt(2.0) * (double)M * dk;
+        ntab = (int)std::ceil(ktop / H) + 12;
+        /* transition quadrature: 16-point Gauss-Legendre panels no wider than 6 / ktop */
+        const double sw = (p->r1 - p->r0) / 12.0;
+        const int npan = (int)std::ceil((p->r1 - p->r0) * ktop / 6.0) + 2;
+        double gx[16], gw[16];
+        gauss_legendre(16, gx, gw);
+        std::vector<double2> nodes((size_t)npan * 16);
+        const double L = (p->r1 - p->r0) / npan;
+        for (int a = 0; a < npan; ++a)
+            for (int i = 0; i < 16; ++i) {
+                const double r = p->r0 + L * (a + 0.5 * (gx[i] + 1.0));
+                const double chi = 0.5 * std::erfc((r - p->r0 - 6.0 * sw) / sw);
+                nodes[(size_t)a * 16 + i] =
+                    make_double2(r, 0.5 * L * gw[i] * bessel_k(0, p->alpha * r) * chi * r);
+            }
+        if ((s = buf_alloc(p, d_tab, sizeof(double) * ntab, "kernel table")) != YK_OK ||
+            (s = buf_alloc(p, d_nodes, sizeof(double2) * nodes.size(), "kernel table")) != YK_OK) {
+            buf_free(p, d_dfac);
+            buf_free(p, d_tab);
+            return s;
+        }
+        e = cudaMemcpyAsync(d_nodes.ptr, nodes.data(), sizeof(double2) * nodes.size(),
+                            cudaMemcpyHostToDevice, p->stream);
+        if (e == cudaSuccess)
+            e = yk::launch_trunc_table(P<double>(d_tab), ntab, H, p->alpha, p->delta, p->r0,
+                                       bessel_k(0, p->alpha * p->r0),
+                                       bessel_k(1, p->alpha * p->r0), P<double2>(d_nodes),
+                                       (int)nodes.size(), p->stream);
+    }
+    const double *tab = p->truncated ? P<double>(d_tab) : nullptr;
     if (e == cudaSuccess) {
         if (f32)
             e = yk::launch_build_mult32(P<float>(p->mult), P<double>(d_dfac), (int)M, p->alpha,
-                                        p->delta, 2.0 * kPi / p->period, p->period, p->stream);
+                                        p->delta, dk, p->period, p->stream, tab, ntab, H);
         else if (p->fft_df)
             e = yk::launch_build_mult_df(p->mult.ptr, P<double>(d_dfac), (int)M, p->alpha,
-                                         p->delta, 2.0 * kPi / p->period, p->period, p->stream);
+                                         p->delta, dk, p->period, p->stream, tab, ntab, H);
         else
             e = yk::launch_build_mult(P<double>(p->mult), P<double>(d_dfac), (int)M, p->alpha,
-                                      p->delta, 2.0 * kPi / p->period, p->period, p->stream);
+                                      p->delta, dk, p->period, p->stream, tab, ntab, H);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     buf_free(p, d_dfac);
+    buf_free(p, d_tab);
+    buf_free(p, d_nodes);
     if (e != cudaSuccess) return cuda_fail(e, "plan tables");
     return YK_OK;
 }
@@ -734,7 +790,34 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
         p->kmax = std::max(p->kmax, o->kmax_rule == 1 ? kmax_dlp_paper(alpha, delta, p->eps)
                                                       : kmax_dlp_relative(alpha, delta, p->eps));
     const double span = std::max(o->box[1] - o->box[0], o->box[3] - o->box[2]);
-    p->period = o->period > 0.0 ? o->period : span + decay_length(alpha, delta, p->eps);
+    if (o->truncate < 0 || o->truncate > 2) return fail(YK_ERR_ARG, "truncate must be 0, 1 or 2");
+    p->truncated = 0;
+    if (p->kmax > 0.0 && o->truncate != 1) {
+        /* truncated kernel: chi = 1 up to the box diagonal D (no source-target pair is farther
+         * apart), then 1/2 erfc((r - D - 6 s)/s) down to ~1e-17 at D + 12 s.  s = 20 / k_max keeps
+         * the transform's tail beyond k_max at that of G_H.  Valid while G_H = K0(alpha r)/(2 pi)
+         * beyond D (the local part there is below E1(D^2 / (4 delta)) / (4 pi)). */
+        const double D = std::hypot(o->box[1] - o->box[0], o->box[3] - o->box[2]);
+        const double s = 20.0 / p->kmax, r1 = D + 12.0 * s;
+        const bool valid = D * D / (4.0 * delta) >= 50.0;
+        const double p_plain = o->period > 0.0 ? o->period
+                                               : span + decay_length(alpha, delta, p->eps);
+        if (o->truncate == 2 && !valid)
+            return fail(YK_ERR_ARG, "the truncated kernel needs box diagonal^2 / (4 delta) >= 50");
+        if (valid && (o->truncate == 2 || (o->period <= 0.0 && span + r1 < p_plain))) {
+            p->truncated = 1;
+            p->r0 = D;
+            p->r1 = r1;
+            p->period = o->period > 0.0 ? o->period : span + r1;
+            if (!(p->period >= span + r1))
+                return fail(YK_ERR_ARG, "period %.17g is below span + truncation radius %.17g",
+                            p->period, span + r1);
+        } else {
+            p->period = p_plain;
+        }
+    } else {
+        p->period = o->period > 0.0 ? o->period : span + decay_length(alpha, delta, p->eps);
+    }
     if (!(p->period > span))
         return fail(YK_ERR_ARG, "period %.17g must exceed the box span %.17g", p->period, span);
     for (int k = 0; k < 4; ++k) p->box[k] = o->box[k];
@@ -877,6 +960,8 @@ yk_status yk_plan_info(yk_plan_t p, yk_info *info)
     info->tile = p->T;
     info->precision = p->precision;
     info->device_bytes = p->bytes;
+    info->truncated = p->truncated;
+    info->r_support = p->truncated ? p->r1 : 0.0;
     return YK_OK;
 }
 

@@ -125,13 +125,23 @@ cudaError_t launch_interp(const Geom &g, const int *trg_ptr, const double2 *trg_
                           const int *trg_idx, const double *grid, double *u, cudaStream_t st);
 cudaError_t launch_interp32(const Geom &g, const int *trg_ptr, const double2 *trg_t,
                             const int *trg_idx, const float *grid, double *u, cudaStream_t st);
+/* multiplier tables; tab (ntab entries at spacing H) non-NULL: the truncated kernel's radial
+ * transform, interpolated, replaces exp(-delta(alpha^2+k^2))/(alpha^2+k^2) */
 cudaError_t launch_build_mult(double *mult, const double *dfac, int M, double alpha, double delta,
-                              double dk, double period, cudaStream_t st);
+                              double dk, double period, cudaStream_t st,
+                              const double *tab = nullptr, int ntab = 0, double H = 0.0);
 cudaError_t launch_build_mult32(float *mult, const double *dfac, int M, double alpha,
-                                double delta, double dk, double period, cudaStream_t st);
+                                double delta, double dk, double period, cudaStream_t st,
+                                const double *tab = nullptr, int ntab = 0, double H = 0.0);
 /* multiplier as double-float pairs (FP64 path with double-float FFT arithmetic) */
 cudaError_t launch_build_mult_df(void *mult, const double *dfac, int M, double alpha,
-                                 double delta, double dk, double period, cudaStream_t st);
+                                 double delta, double dk, double period, cudaStream_t st,
+                                 const double *tab = nullptr, int ntab = 0, double H = 0.0);
+/* radial transform of the truncated kernel at k_i = i H (see k_trunc_table); nodes[q] =
+ * (r_q, f_q) with f_q = K0(alpha r_q) chi(r_q) r_q times the quadrature weight */
+cudaError_t launch_trunc_table(double *tab, int ntab, double H, double alpha, double delta,
+                               double R0, double k0a, double k1a, const double2 *nodes, int nq,
+                               cudaStream_t st);
 
 /* largest grid the column pass supports (one column of n complex values in shared memory) */
 constexpr int kMaxGridF64 = 14400;
@@ -176,6 +186,8 @@ struct yk_plan_s {
     DevBuf win32;    /* float: FP32C window + derivative polynomials (plans with dlp) */
     int wdeg;
     int dlp;         /* plan takes dipole sources */
+    int truncated;   /* the kernel is truncated at the box diagonal (small-alpha path) */
+    double r0, r1;   /* truncation: chi = 1 on r <= r0, a smooth step to 0 on [r0, r1] */
     double dmax;     /* bound on |phi'| (cells^-1) */
     DevBuf tile_cnt, tile_ptr, tile_cur; /* int[nt^2], int[nt^2+1], int[nt^2] (sources) */
     DevBuf tile_order; /* int[nt^2]: heavy-first processing order of the source tiles */

@@ -354,9 +354,38 @@ template <int W> __global__ void __launch_bounds__(256) k_interp32(Inst d)
 /* (eq. sh_fourier with Delta k = 2 pi / P, so (Delta k)^2 / (2 pi)^2 = 1 / P^2; dfac is the   */
 /* squared inverse window transform that undoes spreading and interpolation).  Evaluated in    */
 /* FP64 and rounded once to the table's type.                                                  */
+/* radial multiplier at |k| from an equispaced table tab[i] = G(i H) by 10-point Lagrange
+ * interpolation on the nearest nodes (truncated kernel) */
+__device__ double table_interp(const double *__restrict__ tab, int ntab, double H, double k)
+{
+    constexpr int NP = 10;
+    int i0 = (int)floor(k / H) - NP / 2 + 1;
+    i0 = max(0, min(i0, ntab - NP));
+    const double x = k / H - (double)i0;
+    double pre[NP + 1], suf[NP + 1];
+    pre[0] = 1.0;
+    for (int j = 0; j < NP; ++j) pre[j + 1] = pre[j] * (x - (double)j);
+    suf[NP] = 1.0;
+    for (int j = NP - 1; j >= 0; --j) suf[j] = suf[j + 1] * (x - (double)j);
+    /* weights 1 / prod_{m != j} (j - m) = (-1)^(NP-1-j) / (j! (NP-1-j)!) */
+    double fact[NP];
+    fact[0] = 1.0;
+    for (int j = 1; j < NP; ++j) fact[j] = fact[j - 1] * (double)j;
+    double sum = 0.0;
+    for (int j = 0; j < NP; ++j) {
+        const double den = fact[j] * fact[NP - 1 - j] * (((NP - 1 - j) & 1) ? -1.0 : 1.0);
+        sum += tab[i0 + j] * pre[j] * suf[j + 1] / den;
+    }
+    return sum;
+}
+
+/* multiplier table (M+1) x (2M+1): Ghat(k)/P^2 times the window deconvolution of both axes, in
+ * FP64 and rounded once to the table's type.  Ghat is exp(-delta(alpha^2+k^2))/(alpha^2+k^2)
+ * (Section 5.1, eq. sh), or, for the truncated kernel, interpolated from tab. */
 template <typename R>
 __global__ void k_build_mult(R *__restrict__ mult, const double *__restrict__ dfac, int M,
-                             double alpha, double delta, double dk, double period)
+                             double alpha, double delta, double dk, double period,
+                             const double *__restrict__ tab, int ntab, double H)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t w = 2 * M + 1;
@@ -364,7 +393,37 @@ __global__ void k_build_mult(R *__restrict__ mult, const double *__restrict__ df
     const int kx = (int)(i / w), my = (int)(i - (int64_t)kx * w) - M;
     const double k2 = dk * dk * ((double)kx * kx + (double)my * my);
     const double s = alpha * alpha + k2;
-    mult[i] = (R)(exp(-delta * s) / s / (period * period) * dfac[kx] * dfac[my < 0 ? -my : my]);
+    const double gh = tab ? table_interp(tab, ntab, H, sqrt(k2)) : exp(-delta * s) / s;
+    mult[i] = (R)(gh / (period * period) * dfac[kx] * dfac[my < 0 ? -my : my]);
+}
+
+/* Fourier transform of the truncated history kernel G_T = G_H chi (chi = 1 for r <= R0, a smooth
+ * step to 0 on [R0, R1]) at k_i = i H, one warp per table entry:
+ *   Ghat_T(k) = [exp(-delta(alpha^2+k^2)) + R0 k J1(k R0) K0(alpha R0) - R0 alpha J0(k R0)
+ *                K1(alpha R0)] / (alpha^2 + k^2)  +  sum_q f_q J0(k r_q),
+ * the first term the exact transform of G_H on the disc r <= R0 (where G_H = K0(alpha r)/(2 pi)
+ * minus a local part supported well inside it), the sum a quadrature of the transition
+ * int_R0^R1 K0(alpha r) chi(r) J0(k r) r dr with weights folded into f_q. */
+__global__ void k_trunc_table(double *__restrict__ tab, int ntab, double H, double alpha,
+                              double delta, double R0, double k0a, double k1a,
+                              const double2 *__restrict__ nodes, int nq)
+{
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (warp >= ntab) return; /* whole warps exit together */
+    const double k = (double)warp * H;
+    double sum = 0.0;
+    for (int q = lane; q < nq; q += 32) {
+        const double2 nd = nodes[q];
+        sum += nd.y * j0(k * nd.x);
+    }
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) {
+        const double s = alpha * alpha + k * k;
+        const double disc = (exp(-delta * s) + R0 * k * j1(k * R0) * k0a -
+                             R0 * alpha * j0(k * R0) * k1a) / s;
+        tab[warp] = disc + sum;
+    }
 }
 
 template <typename K> cudaError_t set_smem(K kernel, size_t bytes)
@@ -794,30 +853,43 @@ cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st)
 }
 
 cudaError_t launch_build_mult_df(void *mult, const double *dfac, int M, double alpha,
-                                 double delta, double dk, double period, cudaStream_t st)
+                                 double delta, double dk, double period, cudaStream_t st,
+                                 const double *tab, int ntab, double H)
 {
     const int64_t total = (int64_t)(M + 1) * (2 * M + 1);
-    k_build_mult<df32><<<(int)((total + 255) / 256), 256, 0, st>>>(static_cast<df32 *>(mult),
-                                                                   dfac, M, alpha, delta, dk,
-                                                                   period);
+    k_build_mult<df32><<<(int)((total + 255) / 256), 256, 0, st>>>(
+        static_cast<df32 *>(mult), dfac, M, alpha, delta, dk, period, tab, ntab, H);
     return cudaGetLastError();
 }
 
 cudaError_t launch_build_mult(double *mult, const double *dfac, int M, double alpha, double delta,
-                              double dk, double period, cudaStream_t st)
+                              double dk, double period, cudaStream_t st, const double *tab,
+                              int ntab, double H)
 {
     const int64_t total = (int64_t)(M + 1) * (2 * M + 1);
     k_build_mult<double><<<(int)((total + 255) / 256), 256, 0, st>>>(mult, dfac, M, alpha, delta,
-                                                                     dk, period);
+                                                                     dk, period, tab, ntab, H);
     return cudaGetLastError();
 }
 
 cudaError_t launch_build_mult32(float *mult, const double *dfac, int M, double alpha,
-                                double delta, double dk, double period, cudaStream_t st)
+                                double delta, double dk, double period, cudaStream_t st,
+                                const double *tab, int ntab, double H)
 {
     const int64_t total = (int64_t)(M + 1) * (2 * M + 1);
     k_build_mult<float><<<(int)((total + 255) / 256), 256, 0, st>>>(mult, dfac, M, alpha, delta,
-                                                                    dk, period);
+                                                                    dk, period, tab, ntab, H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trunc_table(double *tab, int ntab, double H, double alpha, double delta,
+                               double R0, double k0a, double k1a, const double2 *nodes, int nq,
+                               cudaStream_t st)
+{
+    if (ntab <= 0) return cudaSuccess;
+    const int64_t threads = (int64_t)ntab * 32;
+    k_trunc_table<<<(int)((threads + 255) / 256), 256, 0, st>>>(tab, ntab, H, alpha, delta, R0,
+                                                                 k0a, k1a, nodes, nq);
     return cudaGetLastError();
 }
 
