@@ -263,7 +263,8 @@ YK_API yk_status yk_fma_peak(int precision, double *tflops);
  * example code embedded in a host application that owns every device allocation, or a process
  * that must not grow its device footprint after start-up.  The paper has no counterpart; this is
  * a deployment variant of the same kernels.
- *  - alpha, o: as for yk_plan (o->alloc/o->free must be NULL; o->stream is used).
+ *  - alpha, o: as for yk_plan (o->alloc/o->free must be NULL; o->stream is used; o->truncate is
+ *    ignored: this entry point always uses the untruncated kernel and its period).
  *  - xs, ys, w, density (n_src) and xt, yt (n_trg) are inputs, u (n_trg) is written; every array
  *    must be device memory, or YK_ERR_ARG.
  *  - All scratch lives in one static device array of 32 MiB that every GPU loading the library

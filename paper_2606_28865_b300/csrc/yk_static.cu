@@ -209,6 +209,10 @@ extern "C" YK_API yk_status yk_eval_longrange_static(double alpha, const yk_opts
     if ((n_src > 0 && (!is_device(xs) || !is_device(ys) || !is_device(w) || !is_device(density))) ||
         (n_trg > 0 && (!is_device(xt) || !is_device(yt) || !is_device(u))))
         return static_fail(YK_ERR_ARG, "every array must be device memory (no staging copies)");
+    /* this entry point builds the plain multiplier only: no truncated kernel */
+    yk_opts oc = *o;
+    oc.truncate = 1;
+    o = &oc;
     yk_info info;
     yk_status s = yk_plan_params(alpha, o, n_src, n_trg, &info);
     if (s != YK_OK) return static_fail(s, "parameters: ", yk_last_error());

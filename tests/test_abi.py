@@ -36,7 +36,8 @@ def test_library_exports_every_declared_symbol():
 @pytest.mark.parametrize("alpha", [10.0, 0.5, 200.0])
 def test_plan_parameters_follow_the_rules(alpha):
     w = W.config_small()
-    info = yk.plan_params(alpha, w.n_src, w.n_trg, h_vol=w.h_vol, tol=1e-10)
+    # the untruncated kernel's rules (the truncated kernel has its own test)
+    info = yk.plan_params(alpha, w.n_src, w.n_trg, h_vol=w.h_vol, tol=1e-10, truncate=1)
     eps = 1e-10 / 4
     delta = OP.delta_from_mesh(alpha, w.h_vol)
     assert info["delta"] == pytest.approx(delta, rel=1e-14)
@@ -81,6 +82,39 @@ def test_double_layer_cutoff_rules(alpha, delta):
     plain = yk.plan_params(alpha, delta=delta, tol=1e-10)
     assert info["kmax"] >= plain["kmax"]
     assert info["w"] == plain["w"] + 1   # one more digit of window for the gradient spread
+
+
+def test_truncated_kernel_parameters():
+    # small alpha: the kernel is cut at the box diagonal D with a smooth step of width 12 s,
+    # s = 20 / k_max, and the period only exceeds the span by D + 12 s
+    eps = 1e-10 / 4
+    for alpha in (1.0, 0.5, 3.0):
+        delta = 3.45e-5
+        info = yk.plan_params(alpha, delta=delta, tol=1e-10)
+        kmax = OP.kmax_relative(alpha, delta, eps)
+        r1 = math.hypot(3.0, 3.0) + 12 * 20 / kmax
+        assert info["truncated"] == 1
+        assert info["r_support"] == pytest.approx(r1, rel=1e-12)
+        assert info["period"] == pytest.approx(3.0 + r1, rel=1e-12)
+        # automatic mode truncates because the decay length is the longer margin
+        assert 3.0 + OP.r_tol(alpha, delta, eps) > info["period"]
+    plain = yk.plan_params(3.0, delta=3.45e-5, tol=1e-10, truncate=1)
+    trunc = yk.plan_params(3.0, delta=3.45e-5, tol=1e-10)
+    assert plain["truncated"] == 0 and plain["period"] > trunc["period"]
+    assert plain["kmax"] == trunc["kmax"]
+    # large alpha: the decay length is shorter, so automatic mode keeps the plain kernel
+    info = yk.plan_params(10.0, delta=3.45e-5, tol=1e-10)
+    assert info["truncated"] == 0
+    forced = yk.plan_params(10.0, delta=3.45e-5, tol=1e-10, truncate=2)
+    assert forced["truncated"] == 1 and forced["period"] > info["period"]
+    # an explicit period keeps the plain kernel unless truncation is forced
+    assert yk.plan_params(1.0, delta=3.45e-5, tol=1e-10, period=30.0)["truncated"] == 0
+    with pytest.raises(yk.YkError) as ei:
+        yk.plan_params(1.0, delta=3.45e-5, tol=1e-10, period=5.0, truncate=2)
+    assert ei.value.status == yk.YK_ERR_ARG
+    with pytest.raises(yk.YkError) as ei:
+        yk.plan_params(1.0, delta=3.45e-5, tol=1e-10, truncate=3)
+    assert ei.value.status == yk.YK_ERR_ARG
 
 
 @pytest.mark.parametrize("kw,status", [
