@@ -416,7 +416,7 @@ void buf_free(yk_plan_t p, DevBuf &b)
 void free_all(yk_plan_t p)
 {
     DevBuf *all[] = {&p->grid, &p->spec, &p->mult, &p->tw, &p->perm_h, &p->iperm_f, &p->win,
-                     &p->win_df, &p->win32, &p->wnu, &p->stage_d[0], &p->stage_d[1],
+                     &p->win_df, &p->win32, &p->wnu, &p->win_src, &p->win_dip, &p->win_trg, &p->stage_d[0], &p->stage_d[1],
                      &p->stage_d[2], &p->stage_d[3], &p->stage_d[4], &p->stage_d[5],
                      &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->tile_order, &p->trg_cnt,
                      &p->trg_ptr,
@@ -575,7 +575,9 @@ yk_status plan_tables(yk_plan_t p)
     if (!f32 || p->dlp) {
         /* windows as per-tap polynomials of degree w + 1 (the FP64 path always; FP32C for its
          * dipoles), followed by the derivative's coefficients when the plan takes dipoles */
-        p->wdeg = p->w + 1;
+        /* degree w - 1: interior taps to ~1e-13 of the peak at w = 12 (the two edge taps carry
+         * the window's square-root edge, ~5e-13 at any degree), well inside eps = 10^(1-w) */
+        p->wdeg = std::max(2, p->w - 1);
         std::vector<long double> mono;
         p->dmax = 0.0;
         window_polys(p->w, p->beta, p->wdeg, p->dlp != 0, mono, &p->dmax);
@@ -721,6 +723,9 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->wnu = P<double2>(p->wnu);
     d->win32 = P<float>(p->win32);
     d->dmax = p->dmax;
+    d->win_src = P<float2>(p->win_src);
+    d->win_dip = P<float2>(p->win_dip);
+    d->win_trg = P<float2>(p->win_trg);
     for (int s = 0; s < yk::ST_COUNT; ++s) {
         d->items[s] = yk::stage_items(*d, s);
         d->smem[s] = yk::stage_smem(*d, s);
@@ -881,6 +886,7 @@ static int64_t predicted_bytes(const yk_plan_s *p, int64_t n_src, int64_t n_trg)
     if (p->precision == YK_FP64) b += 8 * (int64_t)(p->w + 2) * p->w * (p->dlp ? 2 : 1);
     else if (p->dlp) b += 4 * (int64_t)(2 * p->w + 3) * p->w;
     b += n_src * (8 + 16 + 4 * (16 + 4)) + n_trg * (16 + 4 + 16);
+    if (p->fft_df) b += (n_src + n_trg) * 16 * (int64_t)p->w; /* per-point window values */
     return b;
 }
 
@@ -1030,6 +1036,22 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
     YK_CU(yk::launch_tile_order(P<int>(p->tile_ptr), p->nt * p->nt, P<int>(p->tile_order),
                                 P<int>(p->tile_cur), p->stream),
           "tile order");
+    if (p->fft_df) {
+        /* double-float path: window values once per source (they depend on positions only) */
+        const size_t w = (size_t)p->w;
+        YK_TRY(buf_alloc(p, p->win_src, sizeof(float2) * 2 * w * ns, "source windows"));
+        YK_CU(yk::launch_point_windows_df(g, n_src, P<double2>(p->src_t), nullptr,
+                                          P<float2>(p->win_df), p->wdeg, false,
+                                          P<float2>(p->win_src), p->stream),
+              "source windows");
+        if (nd > 0) {
+            YK_TRY(buf_alloc(p, p->win_dip, sizeof(float2) * 4 * w * nd, "dipole windows"));
+            YK_CU(yk::launch_point_windows_df(g, n_dip, P<double2>(p->src_t) + ns, nullptr,
+                                              P<float2>(p->win_df), p->wdeg, true,
+                                              P<float2>(p->win_dip), p->stream),
+                  "dipole windows");
+        }
+    }
     stage_end(p, YK_STAGE_BIN_SRC);
     /* the staging buffers are reused for the targets: order the copies after the source bins */
     const double *tx = nullptr, *ty = nullptr;
@@ -1041,6 +1063,14 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
                                  P<int>(p->trg_idx), P<int>(p->err), p->stream,
                                  p->precision == YK_FP32C),
           "bin targets");
+    if (p->fft_df) {
+        YK_TRY(buf_alloc(p, p->win_trg, sizeof(float2) * 2 * (size_t)p->w * nt, "target windows"));
+        YK_CU(yk::launch_point_windows_df(g, n_trg, P<double2>(p->trg_t),
+                                          P<int>(p->trg_ptr) + (size_t)p->nt * p->nt,
+                                          P<float2>(p->win_df), p->wdeg, false,
+                                          P<float2>(p->win_trg), p->stream),
+              "target windows");
+    }
     stage_end(p, YK_STAGE_BIN_TRG);
 #undef YK_TRY
     /* host inputs: return after the copies are consumed so the caller may reuse its arrays */

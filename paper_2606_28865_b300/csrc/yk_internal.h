@@ -70,6 +70,10 @@ struct Inst {
     const double2 *wnu;       /* wd * (nx, ny) per dipole (device) */
     const float *win32;       /* FP32C with dipoles: window and derivative polynomials in FP32 */
     double dmax;              /* bound on |phi'| over the window (cells^-1), for the FP64 scale */
+    /* double-float path: window values computed once per point at yk_set_points (they depend on
+     * positions only): per charge [phi(Y - t_y) taps | phi(X - t_x) taps] (2w double-floats, source
+     * order), per dipole [phi_y | phi_x | phi'_y | phi'_x] (4w), per target in tile order (2w) */
+    const float2 *win_src, *win_dip, *win_trg;
     int items[ST_COUNT];      /* work items of each stage */
     int smem[ST_COUNT];       /* dynamic shared memory of each stage (bytes) */
 };
@@ -90,6 +94,13 @@ cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, cons
                                int64_t nd, const double *xd, const double *yd, double2 *src_t,
                                int *tile_cnt, int *tile_ptr, int *tile_cur, double2 *ent_t,
                                int *ent_j, int *err, cudaStream_t st, bool f32);
+/* double-float window values of n points at grid coordinates pts (a point with t.x < 0 lies
+ * outside the box and gets none): out[i * 2w ...] as described for Inst::win_src; with deriv, 4w
+ * values per point including the derivative's.  count (device, may be NULL): only the first
+ * *count points are valid. */
+cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts,
+                                    const int *count, const float2 *coef, int deg, bool deriv,
+                                    float2 *out, cudaStream_t st);
 /* wnu[d] = wd[d] * (nx[d], ny[d]) */
 cudaError_t launch_pack_wnu(int64_t nd, const double *wd, const double *nx, const double *ny,
                             double2 *wnu, cudaStream_t st);
@@ -200,6 +211,7 @@ struct yk_plan_s {
     int64_t n_src, n_trg, n_dip;
     DevBuf w_src;    /* double[n_src]: quadrature weights, original order */
     DevBuf wnu;      /* double2[n_dip]: dipole weight times unit normal */
+    DevBuf win_src, win_dip, win_trg; /* double-float path: per-point window values */
     DevBuf src_t;    /* double2[n_src]: grid coordinates of the sources, original order */
     DevBuf ent_t;    /* 16 B x (<= 4 n_src): (source, tile) entries grouped by tile; FP64: grid
                         coordinate (double2); FP32C: first tap and FP32 offset (int2 + float2) */

@@ -299,6 +299,41 @@ __global__ void k_order_fill(const int *__restrict__ ptr, int ntiles, int *__res
     if (v) order[off] = t;
 }
 
+/* double-float window values per point (see launch_point_windows_df): one thread per point,
+ * Horner in double-float on the per-tap polynomials staged in shared memory */
+template <int W>
+__global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
+                                   const int *__restrict__ count, const float2 *__restrict__ coef,
+                                   int deg, int deriv, float2 *__restrict__ out)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    df32 *cw = reinterpret_cast<df32 *>(sm);
+    const int m = (deg + 1) * W + (deriv ? deg * W : 0);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) cw[i] = df32(coef[i].x, coef[i].y);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || (count && i >= (int64_t)*count)) return;
+    const double2 t = pts[i];
+    if (t.x < 0.0) return; /* outside the box: no entries */
+    const int stride = deriv ? 4 * W : 2 * W;
+    float2 *o = out + (size_t)i * stride;
+    const df32 ax = window_arg_df(first_tap<W>(t.x), t.x, W);
+    const df32 ay = window_arg_df(first_tap<W>(t.y), t.y, W);
+    for (int a = 0; a < W; ++a) {
+        const df32 py = window_df<W>(cw, deg, a, ay), px = window_df<W>(cw, deg, a, ax);
+        o[a] = make_float2(py.hi, py.lo);
+        o[W + a] = make_float2(px.hi, px.lo);
+    }
+    if (deriv) {
+        const df32 *cwd = cw + (deg + 1) * W;
+        for (int a = 0; a < W; ++a) {
+            const df32 qy = window_df<W>(cwd, deg - 1, a, ay), qx = window_df<W>(cwd, deg - 1, a, ax);
+            o[2 * W + a] = make_float2(qy.hi, qy.lo);
+            o[3 * W + a] = make_float2(qx.hi, qx.lo);
+        }
+    }
+}
+
 /* ----------------------------------------------------------------------------------------- */
 /* per-stage kernels: one CTA per work item                                                   */
 
@@ -312,7 +347,7 @@ template <int W> __global__ void __launch_bounds__(32 * kSpreadWarps) k_spread32
     extern __shared__ __align__(16) unsigned char sm[];
     st_spread32<W>(d, blockIdx.x, sm);
 }
-template <int W> __global__ void __launch_bounds__(32 * kSpreadWarps) k_spread_df(Inst d)
+template <int W> __global__ void __launch_bounds__(32 * kSpreadWarps, 2) k_spread_df(Inst d)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     st_spread_df<W>(d, blockIdx.x, sm);
@@ -477,8 +512,8 @@ int stage_smem(const Inst &d, int stage)
     case ST_SPREAD:
         if (d.fft_df)
             return (int)(sizeof(df32) * kSpreadWarps * T * (T + 1) +
-                         sizeof(df32) * kSpreadWarps * 32 * SW + sizeof(int) * kSpreadWarps * 64 +
-                         sizeof(df32) * ncoef);
+                         sizeof(df32) * kSpreadWarps * kSpreadBatch * SW +
+                         sizeof(int) * kSpreadWarps * 2 * kSpreadBatch);
         return d.f32 ? (int)(sizeof(float2) * kSpreadWarps * T * (T + 1) +
                              sizeof(float) * kSpreadWarps * 32 * SW +
                              sizeof(int) * kSpreadWarps * 64 + (d.dip ? sizeof(float) * ncoef : 0))
@@ -488,7 +523,7 @@ int stage_smem(const Inst &d, int stage)
     case ST_COLUMNS: return c * d.n;
     default: {
         const int nw = (d.wdeg + 1) * W; /* interpolation stages the window only */
-        if (d.fft_df) return 8 * (T + W) * (T + W) + (int)sizeof(df32) * nw;
+        if (d.fft_df) return 8 * (T + W) * (T + W);
         return d.f32 ? 4 * (T + W) * (T + W)
                      : 8 * (T + W) * (T + W) + (d.win ? (int)sizeof(double) * nw : 0);
     }
@@ -577,6 +612,20 @@ __global__ void k_pack_wnu(int64_t nd, const double *__restrict__ wd, const doub
 {
     const int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (d < nd) wnu[d] = make_double2(wd[d] * nx[d], wd[d] * ny[d]);
+}
+
+cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts,
+                                    const int *count, const float2 *coef, int deg, bool deriv,
+                                    float2 *out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = sizeof(df32) * ((deg + 1) * g.w + (deriv ? deg * g.w : 0));
+    const int blocks = (int)((n + 255) / 256);
+#define YK_CALL(W)                                                                              \
+    k_point_windows_df<W><<<blocks, 256, smem, st>>>(n, pts, count, coef, deg, deriv ? 1 : 0, out)
+    YK_W_DISPATCH(g.w, YK_CALL)
+#undef YK_CALL
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pack_wnu(int64_t nd, const double *wd, const double *nx, const double *ny,

@@ -74,6 +74,8 @@ template <> struct Tr<df32> {
 
 constexpr double kMagic = 6755399441055744.0; /* 1.5 * 2^52: fma(a, b, kMagic) rounds a*b to an integer */
 constexpr int kSpreadWarps = 8;               /* warps per CTA of the FP32C spread */
+constexpr int kSpreadBatch = 16;              /* entries a warp of the double-float spread takes
+                                                 at a time (two lanes each) */
 
 __device__ __forceinline__ double block_max(double v, double *red)
 {
@@ -353,9 +355,16 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
             const int dy0 = dyf & 0x3fffffff;
             const bool dipk = dyf >> 30; /* warp-uniform: one entry at a time */
             const float *wk = wb + k * SW;
+            /* all loads of a lane's taps before any store: the taps of one entry are distinct
+             * cells, so the shared-memory round trips overlap */
+            constexpr int NI = (W * W + 31) / 32;
+            int idx[NI];
+            float v[NI];
+            float2 cell[NI];
 #pragma unroll
-            for (int t0 = 0; t0 < W * W; t0 += 32) {
-                const int t = t0 + lane;
+            for (int i = 0; i < NI; ++i) {
+                const int t = i * 32 + lane;
+                idx[i] = -1;
                 if (t < W * W) {
                     const int c = t / W, a = t - c * W;
                     int yy = dy0 + c;
@@ -363,19 +372,24 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
                     int xx = dx0 + a;
                     if (xx >= g.n) xx -= g.n;
                     if (yy < T && xx < T) {
-                        float v = wk[c] * wk[W + a];
-                        if (dipk) v = fmaf(wk[2 * W + c], wk[3 * W + a], v);
-                        float2 cell = mine[yy * PT + xx];
-                        const float s = __fadd_rn(cell.x, v);
-                        const float bp = __fsub_rn(s, cell.x);
-                        const float err =
-                            __fadd_rn(__fsub_rn(cell.x, __fsub_rn(s, bp)), __fsub_rn(v, bp));
-                        cell.x = s;
-                        cell.y = __fadd_rn(cell.y, err);
-                        mine[yy * PT + xx] = cell;
+                        idx[i] = yy * PT + xx;
+                        v[i] = wk[c] * wk[W + a];
+                        if (dipk) v[i] = fmaf(wk[2 * W + c], wk[3 * W + a], v[i]);
                     }
                 }
             }
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+                if (idx[i] >= 0) cell[i] = mine[idx[i]];
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+                if (idx[i] >= 0) {
+                    const float s = __fadd_rn(cell[i].x, v[i]);
+                    const float bp = __fsub_rn(s, cell[i].x);
+                    const float err =
+                        __fadd_rn(__fsub_rn(cell[i].x, __fsub_rn(s, bp)), __fsub_rn(v[i], bp));
+                    mine[idx[i]] = make_float2(s, __fadd_rn(cell[i].y, err));
+                }
             __syncwarp(); /* the next entry may touch the same cells through other lanes */
         }
         __syncwarp(); /* window buffers are rewritten by the next batch of entries */
@@ -399,19 +413,24 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
 }
 
 /* FP64 path, double-float arithmetic: the FP32C scheme with FP32 pairs.  Each warp owns a
- * private double-float copy of the tile; it evaluates the windows of 32 entries (lane per entry,
- * Horner in double-float), then walks them one entry at a time with one lane per tap and adds the
- * double-float products into its copy; the copies are summed in warp order and the tile is
- * written as FP32 pairs.  Uses blockDim.x / 32 <= kSpreadWarps warps. */
+ * private double-float copy of the tile.  It takes its entries kSpreadBatch at a time: two lanes
+ * per entry fetch the entry's window values (computed once per source at yk_set_points) and
+ * scale the y-windows by the strength, then the warp walks the batch one entry at a time with one
+ * lane per tap, loading all of its taps' cells before adding and storing (the taps of one entry
+ * are distinct cells), so a lane's shared-memory round trips overlap.  The copies are summed in
+ * warp order and the tile is written as FP32 pairs.  Uses blockDim.x / 32 <= kSpreadWarps
+ * warps. */
 template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned char *sm)
 {
+    constexpr int EB = kSpreadBatch;
+    constexpr int NI = (W * W + 31) / 32; /* taps per lane per entry */
     const Geom &g = d.g;
-    const int T = g.T, PT = T + 1, D = d.wdeg;
+    const int T = g.T, PT = T + 1;
     const int NW = blockDim.x >> 5;
     const int SW = d.dip ? 4 * W : 2 * W; /* window values kept per entry */
     df32 *acc = reinterpret_cast<df32 *>(sm);                        /* [warps][T][PT] */
-    df32 *wbuf = acc + kSpreadWarps * T * PT;                        /* [warps][32][SW] */
-    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * SW); /* [warps][64] */
+    df32 *wbuf = acc + kSpreadWarps * T * PT;                        /* [warps][EB][SW] */
+    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * EB * SW); /* [warps][EB][2] */
     const int tile = d.order ? d.order[item] : item;
     const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
     const int X0 = txi * T, Y0 = tyi * T;
@@ -422,74 +441,92 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
             grid[(size_t)(Y0 + i / T) * g.n + X0 + i % T] = df32(0.0f, 0.0f);
         return;
     }
-    df32 *cw = stage_window_df(d, reinterpret_cast<df32 *>(obuf + kSpreadWarps * 64),
-                               window_coeffs(d));
     for (int i = threadIdx.x; i < NW * T * PT; i += blockDim.x) acc[i] = df32(0.0f, 0.0f);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = lane & (EB - 1), half = lane / EB;
     df32 *mine = acc + warp * T * PT;
-    df32 *wb = wbuf + warp * 32 * SW;
-    int *ob = obuf + warp * 64;
-    const df32 *cwd = cw + (D + 1) * W; /* derivative coefficients (dipoles) */
-    for (int b0 = beg + warp * 32; b0 < end; b0 += NW * 32) {
-        const int e = b0 + lane;
+    df32 *wb = wbuf + warp * EB * SW;
+    int *ob = obuf + warp * 2 * EB;
+    /* this lane's taps (c, a) = (t / W, t % W) for t = i * 32 + lane */
+    int tc[NI], ta[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+        const int t = i * 32 + lane;
+        tc[i] = t < W * W ? t / W : 1 << 20; /* out of every tile */
+        ta[i] = t < W * W ? t - (t / W) * W : 0;
+    }
+    const float2 *__restrict__ ws = d.win_src;
+    const float2 *__restrict__ wd = d.win_dip;
+    for (int b0 = beg + warp * EB; b0 < end; b0 += NW * EB) {
+        const int e = b0 + slot;
         if (e < end) {
-            const double2 t = d.ent_t[e];
             const int j = d.ent_j[e];
-            const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
-            const df32 ax = window_arg_df(lx, t.x, W), ay = window_arg_df(ly, t.y, W);
-            df32 *wl = wb + lane * SW;
-            int flag = 0;
+            df32 *wl = wb + slot * SW;
             if (!d.dip || j < d.n_chg) {
-                const df32 q(d.wq[j] * d.dens[j]);
+                /* half 0: q phi_y; half 1: phi_x (a factor of exactly 1) */
+                const df32 f = half ? df32(1.0f, 0.0f) : df32(d.wq[j] * d.dens[j]);
+                const float2 *src = ws + (size_t)j * 2 * W + half * W;
+#pragma unroll
                 for (int a = 0; a < W; ++a) {
-                    wl[a] = q * window_df<W>(cw, D, a, ay);
-                    wl[W + a] = window_df<W>(cw, D, a, ax);
+                    const float2 v = src[a];
+                    wl[half * W + a] = f * df32(v.x, v.y);
                 }
             } else {
                 /* dipole: taps s_x phi'(X - t_x) phi(Y - t_y) + s_y phi(X - t_x) phi'(Y - t_y),
-                 * s = -mu w nu / h (the gradient of the window in the source point) */
-                const double2 wn = d.wnu[j - d.n_chg];
-                const double m = -d.mu[j - d.n_chg] * g.inv_h;
-                const df32 sx(m * wn.x), sy(m * wn.y);
+                 * s = -mu w nu / h (the gradient of the window in the source point); half 0
+                 * stores s_x phi_y and s_y phi'_y, half 1 phi'_x and phi_x */
+                const int jd = j - d.n_chg;
+                const double2 wn = d.wnu[jd];
+                const double m = -d.mu[jd] * g.inv_h;
+                const df32 f1 = half ? df32(1.0f, 0.0f) : df32(m * wn.x);
+                const df32 f2 = half ? df32(1.0f, 0.0f) : df32(m * wn.y);
+                const float2 *src = wd + (size_t)jd * 4 * W;
+                const float2 *s1 = src + (half ? 3 * W : 0), *s2 = src + (half ? W : 2 * W);
+#pragma unroll
                 for (int a = 0; a < W; ++a) {
-                    wl[a] = sx * window_df<W>(cw, D, a, ay);
-                    wl[W + a] = window_df<W>(cwd, D - 1, a, ax);
-                    wl[2 * W + a] = sy * window_df<W>(cwd, D - 1, a, ay);
-                    wl[3 * W + a] = window_df<W>(cw, D, a, ax);
+                    const float2 v1 = s1[a], v2 = s2[a];
+                    wl[half * W + a] = f1 * df32(v1.x, v1.y);
+                    wl[(2 + half) * W + a] = f2 * df32(v2.x, v2.y);
                 }
-                flag = 1 << 30;
             }
-            int dx0 = (lx - X0) % g.n;
-            if (dx0 < 0) dx0 += g.n;
-            int dy0 = (ly - Y0) % g.n;
-            if (dy0 < 0) dy0 += g.n;
-            ob[2 * lane] = dx0;
-            ob[2 * lane + 1] = dy0 | flag;
+            if (half == 0) {
+                /* first tap relative to the tile, in [-(W - 1), T): the window overlaps it */
+                const double2 t = d.ent_t[e];
+                int dx0 = first_tap<W>(t.x) - X0, dy0 = first_tap<W>(t.y) - Y0;
+                if (dx0 >= T) dx0 -= g.n;
+                else if (dx0 <= -W) dx0 += g.n;
+                if (dy0 >= T) dy0 -= g.n;
+                else if (dy0 <= -W) dy0 += g.n;
+                ob[2 * slot] = dx0;
+                ob[2 * slot + 1] = (dy0 + W) | ((d.dip && j >= d.n_chg) ? 1 << 30 : 0);
+            }
         }
         __syncwarp();
-        const int cnt = min(32, end - b0);
+        const int cnt = min(EB, end - b0);
         for (int k = 0; k < cnt; ++k) {
             const int dx0 = ob[2 * k], dyf = ob[2 * k + 1];
-            const int dy0 = dyf & 0x3fffffff;
+            const int dy0 = (dyf & 0x3fffffff) - W;
             const bool dipk = dyf >> 30; /* warp-uniform: one entry at a time */
             const df32 *wk = wb + k * SW;
+            int idx[NI];
+            df32 v[NI], cur[NI];
 #pragma unroll
-            for (int t0 = 0; t0 < W * W; t0 += 32) {
-                const int t = t0 + lane;
-                if (t < W * W) {
-                    const int c = t / W, a = t - c * W;
-                    int yy = dy0 + c;
-                    if (yy >= g.n) yy -= g.n;
-                    int xx = dx0 + a;
-                    if (xx >= g.n) xx -= g.n;
-                    if (yy < T && xx < T) {
-                        df32 v = wk[c] * wk[W + a];
-                        if (dipk) v = v + wk[2 * W + c] * wk[3 * W + a];
-                        mine[yy * PT + xx] = mine[yy * PT + xx] + v;
-                    }
+            for (int i = 0; i < NI; ++i) {
+                const int yy = dy0 + tc[i], xx = dx0 + ta[i];
+                idx[i] = -1;
+                if ((unsigned)yy < (unsigned)T && (unsigned)xx < (unsigned)T) {
+                    idx[i] = yy * PT + xx;
+                    v[i] = wk[tc[i]] * wk[W + ta[i]];
+                    if (dipk) v[i] = v[i] + wk[2 * W + tc[i]] * wk[3 * W + ta[i]];
                 }
             }
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+                if (idx[i] >= 0) cur[i] = mine[idx[i]];
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+                if (idx[i] >= 0) mine[idx[i]] = cur[i] + v[i];
             __syncwarp(); /* the next entry may touch the same cells through other lanes */
         }
         __syncwarp();
@@ -760,16 +797,15 @@ template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned 
     if (beg == end) return;
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;
     stage_halo<df32>(sg, static_cast<const df32 *>(d.grid), g, X0, Y0, P);
-    const df32 *cw = stage_window_df(d, sg + P * P, (d.wdeg + 1) * W);
     __syncthreads();
-    const int D = d.wdeg;
     for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
         const double2 t = d.trg_t[e];
         const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
-        const df32 ax = window_arg_df(lx, t.x, W), ay = window_arg_df(ly, t.y, W);
+        /* window values of this target, computed at yk_set_points: [phi_y taps | phi_x taps] */
+        const float2 *wv = d.win_trg + (size_t)e * 2 * W;
         df32 fx[W];
 #pragma unroll
-        for (int a = 0; a < W; ++a) fx[a] = window_df<W>(cw, D, a, ax);
+        for (int a = 0; a < W; ++a) fx[a] = df32(wv[W + a].x, wv[W + a].y);
         const df32 *base = sg + (ly - Y0) * P + (lx - X0);
         df32 acc(0.0f, 0.0f);
 #pragma unroll
@@ -777,7 +813,7 @@ template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned 
             df32 row = fx[0] * base[c * P];
 #pragma unroll
             for (int a = 1; a < W; ++a) row = row + fx[a] * base[c * P + a];
-            acc = acc + window_df<W>(cw, D, c, ay) * row;
+            acc = acc + df32(wv[c].x, wv[c].y) * row;
         }
         d.u[d.trg_idx[e]] = acc.to_double();
     }
