@@ -137,24 +137,28 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------
 # algorithmic work per stage (per launch), used for the roofline of the dominant stage
 def stage_work(info, ns, nt):
-    """(bytes, fp64 flops) each stage must move / compute at minimum for one launch."""
+    """(bytes, fp64 flops) each stage must move / compute at minimum for one launch.
+
+    The double-float path computes every point's window values once, in the set-up stages
+    (bin_src: sources, bin_trg: targets), by Horner on per-tap polynomials of degree w - 1 (2 flops
+    per step); the spread and the interpolation read them (16 bytes per point and tap pair).
+    """
     n, M, w = info["n_grid"], info["n_modes"], info["w"]
     G = n * n
     L = n // 2
     entries = ns * (1 + (w - 1) / info["tile"]) ** 2  # windows spread into each tile they touch
-    # window value per tap and axis: a Horner polynomial of degree w + 1 (2 flops per step)
-    win = 2 * (w + 1)
+    win = 2 * (w - 1)                                 # flops per window value
     fft_row = 5 * L * math.log2(L) + 12 * L   # complex FFT of n/2 points + real post-processing
     fft_col = 5 * n * math.log2(n)
     return {
-        "bin_src": (ns * (16 + 16 + 4 * 3) + entries * 20, 20 * ns),
-        "bin_trg": (nt * (16 + 16 + 4 * 3) + nt * 20, 20 * nt),
-        "spread": (entries * 20 + ns * 16 + G * 8, entries * (2 * w * win + 2 * w * w)),
+        "bin_src": (ns * (16 + 16 + 4 * 3 + 16 * w) + entries * 20, ns * (20 + 2 * w * win)),
+        "bin_trg": (nt * (16 + 16 + 4 * 3 + 16 * w) + nt * 20, nt * (20 + 2 * w * win)),
+        "spread": (entries * (20 + 16 * w) + ns * 16 + G * 8, entries * (2 * w * w + 2 * w)),
         "row_fwd": (G * 8 + (M + 1) * n * 16, n * fft_row),
         "columns": (2 * (M + 1) * n * 16 + (M + 1) * (2 * M + 1) * 8,
                     (M + 1) * (2 * fft_col + 6 * n)),
         "row_inv": ((M + 1) * n * 16 + G * 8, n * fft_row),
-        "interp": (G * 8 + nt * 28, nt * (2 * w * win + 2 * w * w + 2 * w)),
+        "interp": (G * 8 + nt * (28 + 16 * w), nt * (2 * w * w + 2 * w)),
     }
 
 

@@ -95,6 +95,19 @@ YK_HD df32 operator*(df32 a, df32 b)
     e = YK_FFMA(a.lo, b.hi, e);
     return df_fast_two_sum(p, e);
 }
+/* acc + a * b with the product left unnormalised: its (p, e) pair goes straight into the sum */
+YK_HD df32 df_mul_add(df32 acc, df32 a, df32 b)
+{
+    const float p = YK_FMUL(a.hi, b.hi);
+    float e = YK_FFMA(a.hi, b.hi, -p);
+    e = YK_FFMA(a.hi, b.lo, e);
+    e = YK_FFMA(a.lo, b.hi, e);
+    const float s = YK_FADD(acc.hi, p);
+    const float bb = YK_FSUB(s, acc.hi);
+    float t = YK_FADD(YK_FSUB(acc.hi, YK_FSUB(s, bb)), YK_FSUB(p, bb));
+    t = YK_FADD(t, YK_FADD(acc.lo, e));
+    return df_fast_two_sum(s, t);
+}
 
 /* ---------------------------------------------------------------------------------------- */
 /* exponential-of-semicircle window phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)), |z| <= w/2    */

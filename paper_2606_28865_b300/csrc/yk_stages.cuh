@@ -448,13 +448,17 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
     df32 *mine = acc + warp * T * PT;
     df32 *wb = wbuf + warp * EB * SW;
     int *ob = obuf + warp * 2 * EB;
-    /* this lane's taps (c, a) = (t / W, t % W) for t = i * 32 + lane */
+    /* this lane's taps (c, a) = (t / W, t % W) for t = i * 32 + lane; lanes past the last tap
+     * (tv false) take tap (0, 0) and, like taps outside the tile, add into the padding cell T of
+     * row 0 (never read), so the walk has no divergent branch */
     int tc[NI], ta[NI];
+    bool tv[NI];
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
         const int t = i * 32 + lane;
-        tc[i] = t < W * W ? t / W : 1 << 20; /* out of every tile */
-        ta[i] = t < W * W ? t - (t / W) * W : 0;
+        tv[i] = t < W * W;
+        tc[i] = tv[i] ? t / W : 0;
+        ta[i] = tv[i] ? t - (t / W) * W : 0;
     }
     const float2 *__restrict__ ws = d.win_src;
     const float2 *__restrict__ wd = d.win_dip;
@@ -510,23 +514,22 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
             const bool dipk = dyf >> 30; /* warp-uniform: one entry at a time */
             const df32 *wk = wb + k * SW;
             int idx[NI];
-            df32 v[NI], cur[NI];
+            df32 cur[NI];
 #pragma unroll
             for (int i = 0; i < NI; ++i) {
                 const int yy = dy0 + tc[i], xx = dx0 + ta[i];
-                idx[i] = -1;
-                if ((unsigned)yy < (unsigned)T && (unsigned)xx < (unsigned)T) {
-                    idx[i] = yy * PT + xx;
-                    v[i] = wk[tc[i]] * wk[W + ta[i]];
-                    if (dipk) v[i] = v[i] + wk[2 * W + tc[i]] * wk[3 * W + ta[i]];
-                }
+                const bool in = tv[i] && (unsigned)yy < (unsigned)T && (unsigned)xx < (unsigned)T;
+                idx[i] = in ? yy * PT + xx : T;
             }
 #pragma unroll
-            for (int i = 0; i < NI; ++i)
-                if (idx[i] >= 0) cur[i] = mine[idx[i]];
+            for (int i = 0; i < NI; ++i) cur[i] = mine[idx[i]];
 #pragma unroll
-            for (int i = 0; i < NI; ++i)
-                if (idx[i] >= 0) mine[idx[i]] = cur[i] + v[i];
+            for (int i = 0; i < NI; ++i) {
+                cur[i] = df_mul_add(cur[i], wk[tc[i]], wk[W + ta[i]]);
+                if (dipk) cur[i] = df_mul_add(cur[i], wk[2 * W + tc[i]], wk[3 * W + ta[i]]);
+            }
+#pragma unroll
+            for (int i = 0; i < NI; ++i) mine[idx[i]] = cur[i];
             __syncwarp(); /* the next entry may touch the same cells through other lanes */
         }
         __syncwarp();
