@@ -8,10 +8,15 @@ alpha = 1, 10 and 100 in FP64 at relative accuracy 1e-10.  Per alpha the step ru
 path: bin/sort of sources and targets (yk_set_points) and spread, FFTs with the multiplier, and
 interpolation (yk_eval_longrange).  Inputs are synthetic and resident in HBM before timing.
 
-`value` = source+target points of all alphas and ranks per second of device time (CUDA events,
-max over ranks).  `e2e` = the same through the C ABI with pinned host buffers, host<->device
-copies inside the timed region.  `roofline` = the stage with the largest device time, against
-the measured FP64 FMA peak (ALU-bound) or the measured HBM copy bandwidth.  `cpu_baseline` = the
+The three evaluations of a step are independent: each alpha's plan has its own CUDA stream, so
+their kernels overlap and, end to end, one alpha's host copies overlap another's kernels.
+
+`value` = source+target points of all alphas and ranks per second of device time (CUDA events on
+the main stream around the fork to and join from the three streams, max over ranks).  `e2e` = the
+same through the C ABI with page-locked host buffers, host<->device copies inside the timed
+region.  `roofline` = the stage with the largest device time, against the measured ALU peak
+(double-float stages: FP32 FMA rate / DF_COST) or the measured HBM copy bandwidth; its durations
+come from the timed region (overlapping streams), `achieved_alone` from the kernels run alone.  `cpu_baseline` = the
 FP64 oracle (direct pair sum) on the host cores for a bounded sample of targets, scaled to a full
 evaluation.  `--impl reference` times that oracle alone as the reference arm.
 """
@@ -298,7 +303,7 @@ def batch_section(yk, torch, rank):
             for p, bf in zip(plans, bufs):
                 p.eval(bf[5], out=bf[6])
 
-        reps = 3
+        reps = 10
         per_call()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -359,11 +364,27 @@ def main():
     alphas = [float(a) for a in args.alphas.split(",")]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    # one stream per alpha: the three evaluations of a step are independent, so their kernels and
+    # (for e2e) their host copies overlap; a timed region forks from `stream` and joins back to it
+    lanes = {a: torch.cuda.Stream(device=dev) for a in alphas}
+
+    def fork():
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        for s_ in lanes.values():
+            s_.wait_event(ev)
+
+    def join():
+        for s_ in lanes.values():
+            ev = torch.cuda.Event()
+            ev.record(s_)
+            stream.wait_event(ev)
+
     works, plans, dbufs, outs = {}, {}, {}, {}
     for a in alphas:
         wk = W.config_large(a, seed=rank)
         works[a] = wk
-        plans[a] = yk.Plan(a, tol=TOL, h_vol=wk.h_vol, box=wk.box, profile=True, stream=stream)
+        plans[a] = yk.Plan(a, tol=TOL, h_vol=wk.h_vol, box=wk.box, profile=True, stream=lanes[a])
         t = lambda v: torch.as_tensor(v, dtype=torch.float64, device=dev)
         dbufs[a] = [t(wk.xs), t(wk.ys), t(wk.w), t(wk.xt), t(wk.yt), t(wk.density)]
         outs[a] = torch.empty(wk.n_trg, dtype=torch.float64, device=dev)
@@ -385,8 +406,10 @@ def main():
     clocks = ClockSampler(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    fork()
     for _ in range(args.steps):
         step()
+    join()
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -402,13 +425,11 @@ def main():
         xs, ys, w, xt, yt, d = dbufs[a]
         for _ in range(5):
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
+            s0.record(lanes[a])
             plans[a].eval(d, out=outs[a])
-            s1.record(stream)
+            s1.record(lanes[a])
             torch.cuda.synchronize()
             lat.append(s0.elapsed_time(s1))
-    eval_only_ms = sum(sum(v for k, v in stage_ms[a].items()
-                           if k not in ("bin_src", "bin_trg") and v) for a in alphas)
 
     # end to end through the C ABI with pinned host buffers
     hbufs = {}
@@ -438,28 +459,49 @@ def main():
     for a in alphas:
         plans[a].stage_times()
 
+    # the same step with one alpha at a time (no other stream running): stage durations of the
+    # kernels alone, reported beside the timed region's (where the three alphas overlap)
+    for a in alphas:
+        plans[a].stage_times()
+    for _ in range(3):
+        for a in alphas:
+            xs, ys, w, xt, yt, d = dbufs[a]
+            plans[a].set_points(xs, ys, w, xt, yt)
+            plans[a].eval(d, out=outs[a])
+            torch.cuda.synchronize()
+    stage_ms_alone = {a: plans[a].stage_times() for a in alphas}
+    # evaluation stages only (a resident layout), summed over the alphas, kernels alone
+    eval_only_ms = sum(sum(v for k, v in stage_ms_alone[a].items()
+                           if k not in ("bin_src", "bin_trg") and v) for a in alphas)
+
     # roofline of the dominant stage (largest device time per step)
     hbm_peak, peak_kind = load_peaks()
     fp64_peak = yk.fma_peak_tflops(yk.YK_FP64)
     fp32_peak = yk.fma_peak_tflops(yk.YK_FP32C)
-    tot = {}
-    work_b, work_f = {}, {}
-    for a in alphas:
-        info = plans[a].info
-        sw = stage_work(info, works[a].n_src, works[a].n_trg)
-        for k, v in stage_ms[a].items():
-            if v is None:
-                continue
-            tot[k] = tot.get(k, 0.0) + v
-            work_b[k] = work_b.get(k, 0.0) + sw[k][0]
-            work_f[k] = work_f.get(k, 0.0) + sw[k][1]
-    dom = max(tot, key=tot.get)
+
+    def stage_totals(sms):
+        tot, work_b, work_f = {}, {}, {}
+        for a in alphas:
+            sw = stage_work(plans[a].info, works[a].n_src, works[a].n_trg)
+            for k, v in sms[a].items():
+                if v is None:
+                    continue
+                tot[k] = tot.get(k, 0.0) + v
+                work_b[k] = work_b.get(k, 0.0) + sw[k][0]
+                work_f[k] = work_f.get(k, 0.0) + sw[k][1]
+        return tot, work_b, work_f
+
+    tot, work_b, work_f = stage_totals(stage_ms)
+    tot1, _, _ = stage_totals(stage_ms_alone)
+    dom = max(tot1, key=tot1.get)  # the costliest stage when each kernel runs alone
     t_dom = tot[dom] * 1e-3
     gbs = work_b[dom] / t_dom / 1e9
     tfl = work_f[dom] / t_dom / 1e12
+    t_dom1 = tot1[dom] * 1e-3
     traffic = load_traffic().get(dom)
     # the FP64 path computes spread, FFTs and interpolation in FP32 pairs (double-float)
-    df_stage = dom in ("spread", "row_fwd", "columns", "row_inv", "interp")
+    # (the set-up stages' arithmetic is the double-float window kernel)
+    df_stage = dom in ("bin_src", "bin_trg", "spread", "row_fwd", "columns", "row_inv", "interp")
     alu_peak = fp32_peak / DF_COST if df_stage else fp64_peak
     if tfl / alu_peak >= gbs / hbm_peak:
         roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",
@@ -472,14 +514,22 @@ def main():
         peak_note = f"HBM copy bandwidth, {peak_kind} (MEASURED_PEAKS.json)"
     roof.update({"kernel": dom, "launches_per_step": len(alphas), "peak_source": peak_note,
                  "hbm_achieved_gbs": gbs, "alu_achieved_tflops": tfl,
-                 "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak})
+                 "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak,
+                 "durations": "CUDA events around the stage on its stream in the timed region, "
+                              "where the three alphas' streams overlap (so the durations include "
+                              "other streams' kernels)",
+                 "achieved_alone": (work_f[dom] / t_dom1 / 1e12 if roof["unit"] == "TFLOP/s"
+                                    else work_b[dom] / t_dom1 / 1e9),
+                 "frac_alone": ((work_f[dom] / t_dom1 / 1e12 if roof["unit"] == "TFLOP/s"
+                                 else work_b[dom] / t_dom1 / 1e9) / roof["peak"]),
+                 "alone": "the same stage timed with one alpha at a time, no other stream running"})
 
     # the FP32C form of the same workload (FP32 spread/FFT/interp, two-sum grid sums, FP64
     # final sums at the targets; relative accuracy 1e-6)
     fp32c = None
     if not args.no_fp32c:
         plans32 = {a: yk.Plan(a, tol=1e-6, precision=yk.YK_FP32C, h_vol=works[a].h_vol,
-                              box=works[a].box, profile=True, stream=stream) for a in alphas}
+                              box=works[a].box, profile=True, stream=lanes[a]) for a in alphas}
 
         def step32():
             for a in alphas:
@@ -494,8 +544,10 @@ def main():
             plans32[a].stage_times()
         barrier(pg)
         e0.record(stream)
+        fork()
         for _ in range(args.steps):
             step32()
+        join()
         e1.record(stream)
         torch.cuda.synchronize()
         ms32 = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
@@ -504,9 +556,9 @@ def main():
         for a in alphas:
             for _ in range(5):
                 s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s0.record(stream)
+                s0.record(lanes[a])
                 plans32[a].eval(dbufs[a][5], out=outs[a])
-                s1.record(stream)
+                s1.record(lanes[a])
                 torch.cuda.synchronize()
                 lat32.append(s0.elapsed_time(s1))
         fp32c = {"value": pts_step * world / (ms32 * 1e-3), "unit": "points/s",
@@ -527,7 +579,7 @@ def main():
         dl_dev = tuple(t(v) for v in (xd, yd, wd, nx, ny))
         mu_dev = t(mu)
         plans_dl = {a: yk.Plan(a, tol=TOL, h_vol=works[a].h_vol, box=works[a].box, profile=True,
-                               stream=stream, dlp=True) for a in alphas}
+                               stream=lanes[a], dlp=True) for a in alphas}
 
         def step_dl():
             for a in alphas:
@@ -542,8 +594,10 @@ def main():
             plans_dl[a].stage_times()
         barrier(pg)
         e0.record(stream)
+        fork()
         for _ in range(args.steps):
             step_dl()
+        join()
         e1.record(stream)
         torch.cuda.synchronize()
         ms_dl = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
@@ -588,6 +642,7 @@ def main():
         "gpu_launches_what": "library kernels in the timed FP64 region (5 evaluation + 13 set-up per alpha)",
         "clocks": clk,
         "stage_ms": {str(a): stage_ms[a] for a in alphas},
+        "stage_ms_alone": {str(a): stage_ms_alone[a] for a in alphas},
         "eval_only": {"ms_per_step": eval_only_ms,
                       "value": pts_step * world / (eval_only_ms * 1e-3) if eval_only_ms else None},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

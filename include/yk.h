@@ -19,12 +19,16 @@
  *  - Arrays are FP64 at the ABI.  Each array pointer may be host or device memory (detected with
  *    cudaPointerGetAttributes); device pointers must be usable on the plan's stream.
  *  - The caller owns every array it passes; the library owns the plan and its device buffers.
- *  - Calls are ordered on the plan's stream.  A call whose outputs are all device memory returns
- *    once its work is enqueued; a call with a host output returns after the stream has finished.
+ *  - Calls are ordered on the plan's stream.  A call whose arrays are all device memory or
+ *    page-locked (pinned) host memory returns once its work and copies are enqueued: the caller
+ *    must not change such inputs or read such outputs before yk_sync (or another call that waits
+ *    for the stream).  A call with a pageable host input returns after the input has been copied,
+ *    and one with a pageable host output after the stream has finished.
  *  - No call aborts or throws across the ABI; every failure is a yk_status.  The message of the
  *    last failure on the calling thread is yk_last_error().
  *  - Errors detected by kernels (a point outside the box) are sticky in the plan and are
- *    returned by the next call that synchronises (yk_sync, or a call with host outputs).
+ *    returned by the next call that synchronises (yk_sync, or a call with pageable host
+ *    arrays).
  */
 #ifndef YK_H
 #define YK_H

@@ -221,7 +221,9 @@ class Plan:
 
     def eval(self, density, out=None, mu=None):
         """u at the targets; `out` (same kind of array as `density` by default) is written.
-        mu: double-layer density at the dipole nodes (required when the points include them)."""
+        mu: double-layer density at the dipole nodes (required when the points include them).
+        Device and page-locked (pinned) host arrays are used asynchronously: `out` is valid after
+        sync(); pageable host arrays (numpy) are complete on return."""
         if _len(density) != self.n_src:
             raise ValueError("density length differs from the number of sources")
         if mu is not None and _len(mu) != self.n_dip:

@@ -446,6 +446,19 @@ bool is_device_ptr(const void *ptr)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+/* pageable host memory (not device, managed or page-locked): a call that reads it must finish its
+ * copies before returning, and one that writes it must wait for the stream */
+bool is_pageable_ptr(const void *ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeUnregistered;
+}
+
 /* device view of n doubles: the pointer itself if it is device memory, else a staging copy */
 yk_status to_device(yk_plan_t p, const double *src, int64_t n, DevBuf &stage,
                     const double **out, const char *what)
@@ -1074,8 +1087,16 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
     stage_end(p, YK_STAGE_BIN_TRG);
 #undef YK_TRY
     /* host inputs: return after the copies are consumed so the caller may reuse its arrays */
-    if ((n_src > 0 && !is_device_ptr(xs)) || (n_trg > 0 && !is_device_ptr(xt)) ||
-        (n_dip > 0 && !is_device_ptr(xd))) {
+    /* pageable host inputs: return after the copies are consumed so the caller may reuse its
+     * arrays (page-locked inputs are copied asynchronously, like device memory) */
+    bool pageable = false;
+    for (const double *a : {xs, ys, w})
+        pageable = pageable || (n_src > 0 && is_pageable_ptr(a));
+    for (const double *a : {xd, yd, wd, nx, ny})
+        pageable = pageable || (n_dip > 0 && is_pageable_ptr(a));
+    for (const double *a : {xt, yt})
+        pageable = pageable || (n_trg > 0 && is_pageable_ptr(a));
+    if (pageable) {
         s = sync_and_check(p);
         if (s != YK_OK) return s;
     }
@@ -1134,9 +1155,10 @@ yk_status yk_eval_longrange_dl(yk_plan_t p, const double *density, const double 
         YK_CU(cudaMemcpyAsync(u, du, sizeof(double) * (size_t)p->n_trg, cudaMemcpyDeviceToHost,
                               p->stream),
               "output copy");
-        return sync_and_check(p);
+        /* a page-locked output is written asynchronously: valid after yk_sync */
+        if (is_pageable_ptr(u)) return sync_and_check(p);
     }
-    if ((p->n_src > 0 && !is_device_ptr(density)) || (p->n_dip > 0 && !is_device_ptr(mu)))
+    if ((p->n_src > 0 && is_pageable_ptr(density)) || (p->n_dip > 0 && is_pageable_ptr(mu)))
         return sync_and_check(p);
     return YK_OK;
 }

@@ -36,8 +36,8 @@ __device__ __forceinline__ int ld_acquire(const int *p)
     return v;
 }
 
-/* items[q] = (instance, stage << 24 | index) */
-template <typename R>
+/* items[q] = (instance, stage << 24 | index); one kernel per precision and window width */
+template <typename R, int W>
 __global__ void __launch_bounds__(256)
     k_batch(const Inst *__restrict__ insts, const int *__restrict__ need,
             const int2 *__restrict__ items, int total, int *head, int *done, int *status,
@@ -45,6 +45,10 @@ __global__ void __launch_bounds__(256)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_q, s_go;
+    /* the item's instance descriptor, copied into shared memory: the stage bodies index its
+     * tables (FFT stage lists) dynamically, which from global memory cost registers and spills */
+    __shared__ __align__(16) Inst s_inst;
+    static_assert(sizeof(Inst) % 16 == 0, "Inst is copied in 16-byte words");
     for (;;) {
         if (threadIdx.x == 0) {
             const int q = atomicAdd(head, 1);
@@ -80,7 +84,13 @@ __global__ void __launch_bounds__(256)
         if (q >= total) return;
         const int2 it = items[q];
         const int inst = it.x, stage = it.y >> 24, idx = it.y & 0xffffff;
-        if (s_go) yk::run_stage<R>(insts[inst], stage, idx, sm);
+        if (s_go) {
+            const int4 *src = reinterpret_cast<const int4 *>(insts + inst);
+            int4 *dst = reinterpret_cast<int4 *>(&s_inst);
+            for (int i = threadIdx.x; i < (int)(sizeof(Inst) / 16); i += blockDim.x) dst[i] = src[i];
+            __syncthreads();
+            yk::run_stage_w<R, W>(s_inst, stage, idx, sm);
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -122,9 +132,10 @@ struct Buf {
     }
 };
 
-/* the instances of one precision */
+/* the instances of one precision and window width */
 struct Group {
     bool f32 = false;
+    int w = 0;
     std::vector<int> members;     /* indices into the batch's plans */
     std::vector<Inst> h_inst;     /* host copies (density/output pointers refreshed per run) */
     Buf insts, need, items, done, head;
@@ -138,7 +149,7 @@ struct yk_batch_s {
     std::vector<int64_t> versions;
     std::vector<int> trivial;      /* plans whose output is zero (no kernels) */
     std::vector<int64_t> trivial_n;
-    Group grp[2];                  /* FP64, FP32C */
+    std::vector<Group> grp;        /* one per (precision, window width) */
     Buf status;
     cudaStream_t stream = nullptr;
     bool own_stream = false; /* created here: graphs cannot be captured on the legacy stream */
@@ -166,6 +177,42 @@ double inst_cost(const Inst &d)
     return n * n * (std::log2(n) + 4.0) + 50.0 * (d.tile_ptr ? 1.0 : 0.0);
 }
 
+/* shared-memory attribute and occupancy of the group's kernel */
+template <typename R, int W> cudaError_t setup_one(int smem, int *per_sm)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_batch<R, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_batch<R, W>,
+                                                                          256, smem);
+    return e;
+}
+
+cudaError_t kernel_setup(bool f32, int w, int smem, int *per_sm)
+{
+    cudaError_t e = cudaSuccess;
+#define YK_C(W) e = f32 ? setup_one<float, W>(smem, per_sm) : setup_one<double, W>(smem, per_sm)
+    YK_W_SWITCH(w, YK_C)
+#undef YK_C
+    return e;
+}
+
+void launch_group(const Group &g, const yk_batch_s *b)
+{
+    const Inst *insts = (const Inst *)g.insts.ptr;
+    const int *need = (const int *)g.need.ptr;
+    const int2 *items = (const int2 *)g.items.ptr;
+    int *head = (int *)g.head.ptr, *done = (int *)g.done.ptr, *status = (int *)b->status.ptr;
+#define YK_C(W)                                                                                 \
+    if (g.f32)                                                                                  \
+        k_batch<float, W><<<g.grid, 256, g.smem, b->stream>>>(insts, need, items, g.total, head, \
+                                                              done, status, b->spin_limit);     \
+    else                                                                                        \
+        k_batch<double, W><<<g.grid, 256, g.smem, b->stream>>>(insts, need, items, g.total,      \
+                                                               head, done, status, b->spin_limit)
+    YK_W_SWITCH(g.w, YK_C)
+#undef YK_C
+}
+
 yk_status build(yk_batch_s *b)
 {
     drop_graph(b);
@@ -175,8 +222,6 @@ yk_status build(yk_batch_s *b)
         g.members.clear();
         g.h_inst.clear();
     }
-    b->grp[0].f32 = false;
-    b->grp[1].f32 = true;
     const int n = (int)b->plans.size();
     b->versions.assign(n, 0);
     for (int i = 0; i < n; ++i) {
@@ -195,7 +240,16 @@ yk_status build(yk_batch_s *b)
             b->trivial_n.push_back(p->n_trg);
             continue;
         }
-        Group &g = b->grp[d.f32 ? 1 : 0];
+        Group *gp = nullptr;
+        for (Group &g : b->grp)
+            if (g.f32 == (d.f32 != 0) && g.w == d.g.w) gp = &g;
+        if (!gp) {
+            b->grp.emplace_back();
+            gp = &b->grp.back();
+            gp->f32 = d.f32 != 0;
+            gp->w = d.g.w;
+        }
+        Group &g = *gp;
         g.members.push_back(i);
         g.h_inst.push_back(d);
     }
@@ -235,15 +289,8 @@ yk_status build(yk_batch_s *b)
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(g.items.ptr, items.data(), sizeof(int2) * items.size(),
                                 cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) {
-            if (g.f32) e = cudaFuncSetAttribute(k_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
-            else e = cudaFuncSetAttribute(k_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, g.smem);
-        }
         int per_sm = 0;
-        if (e == cudaSuccess) {
-            if (g.f32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<float>, 256, g.smem);
-            else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<double>, 256, g.smem);
-        }
+        if (e == cudaSuccess) e = kernel_setup(g.f32, g.w, g.smem, &per_sm);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return bfail(e == cudaErrorMemoryAllocation ? YK_ERR_OOM : YK_ERR_CUDA,
@@ -266,14 +313,7 @@ cudaError_t enqueue(yk_batch_s *b)
         e = cudaMemsetAsync(g.done.ptr, 0, sizeof(int) * g.members.size() * yk::ST_COUNT, b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(g.head.ptr, 0, sizeof(int), b->stream);
         if (e != cudaSuccess) break;
-        if (g.f32)
-            k_batch<float><<<g.grid, 256, g.smem, b->stream>>>(
-                (const Inst *)g.insts.ptr, (const int *)g.need.ptr, (const int2 *)g.items.ptr,
-                g.total, (int *)g.head.ptr, (int *)g.done.ptr, (int *)b->status.ptr, b->spin_limit);
-        else
-            k_batch<double><<<g.grid, 256, g.smem, b->stream>>>(
-                (const Inst *)g.insts.ptr, (const int *)g.need.ptr, (const int2 *)g.items.ptr,
-                g.total, (int *)g.head.ptr, (int *)g.done.ptr, (int *)b->status.ptr, b->spin_limit);
+        launch_group(g, b);
         e = cudaGetLastError();
     }
     return e;

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "yk_internal.h"
 
 namespace yk {
@@ -907,6 +909,45 @@ __device__ __forceinline__ void run_stage<float>(const Inst &d, int stage, int i
         YK_W_SWITCH(d.g.w, YK_C)
 #undef YK_C
     } break;
+    }
+}
+
+/* the same dispatch for one compile-time window width (the batch kernel is instantiated per
+ * width, so its registers are those of that width's stage bodies, not of the widest) */
+template <typename R, int W>
+__device__ __forceinline__ void run_stage_w(const Inst &d, int stage, int item, unsigned char *sm)
+{
+    if constexpr (std::is_same<R, float>::value) {
+        switch (stage) {
+        case ST_SPREAD: st_spread32<W>(d, item, sm); break;
+        case ST_ROW_FWD: st_row_fwd<float>(d, item, sm); break;
+        case ST_COLUMNS: st_columns<float>(d, item, sm); break;
+        case ST_ROW_INV: st_row_inv<float>(d, item, sm); break;
+        default: st_interp32<W>(d, item, sm); break;
+        }
+    } else {
+        switch (stage) {
+        case ST_SPREAD:
+            if (d.fft_df) st_spread_df<W>(d, item, sm);
+            else st_spread64<W>(d, item, sm);
+            break;
+        case ST_ROW_FWD:
+            if (d.fft_df) st_row_fwd<df32>(d, item, sm);
+            else st_row_fwd<double>(d, item, sm);
+            break;
+        case ST_COLUMNS:
+            if (d.fft_df) st_columns<df32>(d, item, sm);
+            else st_columns<double>(d, item, sm);
+            break;
+        case ST_ROW_INV:
+            if (d.fft_df) st_row_inv<df32>(d, item, sm);
+            else st_row_inv<double>(d, item, sm);
+            break;
+        default:
+            if (d.fft_df) st_interp_df<W>(d, item, sm);
+            else st_interp64<W>(d, item, sm);
+            break;
+        }
     }
 }
 
