@@ -316,6 +316,68 @@ void window_polys(int w, double beta, int deg, bool deriv, std::vector<long doub
     }
 }
 
+/* window of width w at offset z (cells), long double */
+long double es_phi_ld(long double z, int w, double beta)
+{
+    const long double v = (2.0L * z / w) * (2.0L * z / w);
+    return v <= 1.0L ? expl(-(long double)beta * v / (1.0L + sqrtl(1.0L - v))) : 0.0L;
+}
+
+/* kWinPieces-piece window polynomials for the double-float window kernel: piece h of tap a covers
+ * u in [h/P, (h+1)/P) (u = l0 - t + w/2, P = kWinPieces) with x = 2P u - 2h - 1 in [-1, 1); the
+ * window there is interpolated at D+1 Chebyshev points and converted to powers of x in long double:
+ * out[(h (D+1) + k) w + a].  With deriv, the coefficients of phi'(z) = 2P dP_h/dx follow:
+ * out[P (D+1) w + (h D + k) w + a].  Returns the largest deviation from the window at 48 points of
+ * every piece of the interior taps (the two edge taps carry the window's square-root edge, a
+ * floor of ~5e-13 at w = 12 whatever the degree). */
+constexpr int kWinPieces = 4;
+long double window_pieces(int w, double beta, int D, bool deriv, std::vector<long double> &out)
+{
+    const int P = kWinPieces, m = D + 1;
+    const long double pi = 3.14159265358979323846264338327950288L;
+    out.assign((size_t)P * m * w + (deriv ? (size_t)P * D * w : 0), 0.0L);
+    long double worst = 0.0L;
+    for (int a = 0; a < w; ++a)
+        for (int h = 0; h < P; ++h) {
+            std::vector<long double> f(m), c(m, 0.0L), mono(m, 0.0L), t0(m, 0.0L), t1(m, 0.0L),
+                t2(m);
+            for (int j = 0; j < m; ++j) {
+                const long double x = cosl(pi * (j + 0.5L) / m);
+                const long double u = (x + 1.0L + 2.0L * h) / (2.0L * P);
+                f[j] = es_phi_ld(u - 0.5L * w + a, w, beta);
+            }
+            for (int k = 0; k < m; ++k) {
+                long double sum = 0.0L;
+                for (int j = 0; j < m; ++j) sum += f[j] * cosl(pi * k * (j + 0.5L) / m);
+                c[k] = 2.0L * sum / m;
+            }
+            c[0] *= 0.5L;
+            t0[0] = 1.0L;
+            if (m > 1) t1[1] = 1.0L;
+            for (int i = 0; i < m; ++i) mono[i] += c[0] * t0[i];
+            for (int k = 1; k < m; ++k) {
+                for (int i = 0; i < m; ++i) mono[i] += c[k] * t1[i];
+                for (int i = 0; i < m; ++i) t2[i] = -t0[i] + (i > 0 ? 2.0L * t1[i - 1] : 0.0L);
+                t0 = t1;
+                t1 = t2;
+            }
+            for (int k = 0; k < m; ++k) out[((size_t)h * m + k) * w + a] = mono[k];
+            if (deriv)
+                for (int k = 0; k < D; ++k)
+                    out[(size_t)P * m * w + ((size_t)h * D + k) * w + a] =
+                        2.0L * P * (k + 1) * mono[k + 1];
+            if (a > 0 && a < w - 1)
+                for (int sidx = 0; sidx < 48; ++sidx) {
+                    const long double x = -1.0L + (sidx + 0.5L) / 24.0L;
+                    long double pv = mono[D];
+                    for (int k = D - 1; k >= 0; --k) pv = pv * x + mono[k];
+                    const long double u = (x + 1.0L + 2.0L * h) / (2.0L * P);
+                    worst = std::max(worst, fabsl(pv - es_phi_ld(u - 0.5L * w + a, w, beta)));
+                }
+        }
+    return worst;
+}
+
 bool smooth5(int64_t n)
 {
     for (int p : {2, 3, 5})
@@ -416,7 +478,7 @@ void buf_free(yk_plan_t p, DevBuf &b)
 void free_all(yk_plan_t p)
 {
     DevBuf *all[] = {&p->grid, &p->spec, &p->mult, &p->tw, &p->perm_h, &p->iperm_f, &p->win,
-                     &p->win_df, &p->win32, &p->wnu, &p->win_src, &p->win_dip, &p->win_trg, &p->stage_d[0], &p->stage_d[1],
+                     &p->win_df, &p->win_pc, &p->win32, &p->wnu, &p->win_src, &p->win_dip, &p->win_trg, &p->stage_d[0], &p->stage_d[1],
                      &p->stage_d[2], &p->stage_d[3], &p->stage_d[4], &p->stage_d[5],
                      &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->tile_order, &p->trg_cnt,
                      &p->trg_ptr,
@@ -596,6 +658,23 @@ yk_status plan_tables(yk_plan_t p)
         window_polys(p->w, p->beta, p->wdeg, p->dlp != 0, mono, &p->dmax);
         p->dmax *= 1.0 + 1e-6;
         cudaError_t ew = cudaSuccess;
+        if (!f32 && p->fft_df) {
+            /* the double-float window kernel's 4-piece tables (degree kPieceDeg[w]) */
+            std::vector<long double> pc;
+            const int D = yk::kPieceDeg[p->w];
+            p->pdeg = D;
+            window_pieces(p->w, p->beta, D, p->dlp != 0, pc);
+            std::vector<float2> pc_df(pc.size());
+            for (size_t i = 0; i < pc.size(); ++i) {
+                const float hi = (float)pc[i];
+                pc_df[i] = make_float2(hi, (float)(pc[i] - (long double)hi));
+            }
+            if ((s = buf_alloc(p, p->win_pc, sizeof(float2) * pc_df.size(), "window")) != YK_OK)
+                return s;
+            ew = cudaMemcpy(p->win_pc.ptr, pc_df.data(), sizeof(float2) * pc_df.size(),
+                            cudaMemcpyHostToDevice);
+            if (ew != cudaSuccess) return cuda_fail(ew, "window table");
+        }
         if (!f32) {
             std::vector<double> poly(mono.size());
             std::vector<float2> poly_df(mono.size());
@@ -1054,13 +1133,13 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
         const size_t w = (size_t)p->w;
         YK_TRY(buf_alloc(p, p->win_src, sizeof(float2) * 2 * w * ns, "source windows"));
         YK_CU(yk::launch_point_windows_df(g, n_src, P<double2>(p->src_t), nullptr,
-                                          P<float2>(p->win_df), p->wdeg, false,
+                                          P<float2>(p->win_pc), p->pdeg, false,
                                           P<float2>(p->win_src), p->stream),
               "source windows");
         if (nd > 0) {
             YK_TRY(buf_alloc(p, p->win_dip, sizeof(float2) * 4 * w * nd, "dipole windows"));
             YK_CU(yk::launch_point_windows_df(g, n_dip, P<double2>(p->src_t) + ns, nullptr,
-                                              P<float2>(p->win_df), p->wdeg, true,
+                                              P<float2>(p->win_pc), p->pdeg, true,
                                               P<float2>(p->win_dip), p->stream),
                   "dipole windows");
         }
@@ -1080,7 +1159,7 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
         YK_TRY(buf_alloc(p, p->win_trg, sizeof(float2) * 2 * (size_t)p->w * nt, "target windows"));
         YK_CU(yk::launch_point_windows_df(g, n_trg, P<double2>(p->trg_t),
                                           P<int>(p->trg_ptr) + (size_t)p->nt * p->nt,
-                                          P<float2>(p->win_df), p->wdeg, false,
+                                          P<float2>(p->win_pc), p->pdeg, false,
                                           P<float2>(p->win_trg), p->stream),
               "target windows");
     }

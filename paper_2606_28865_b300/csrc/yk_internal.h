@@ -13,6 +13,11 @@
 
 namespace yk {
 
+/* degree of the 4-piece window polynomials for window width w (index w, 2..16): the lowest
+ * degree whose interior error is within 3% of eps = 10^(1-w) (or 1e-15), found by fitting in long
+ * double (at w = 12: 3.2e-13 at degree 7, 5.4e-15 at degree 8) */
+constexpr int kPieceDeg[17] = {3, 3, 3, 3, 3, 4, 4, 5, 6, 6, 7, 7, 8, 8, 8, 9, 9};
+
 /* grid geometry handed to kernels by value */
 struct Geom {
     double ox, oy;  /* lower-left corner of the periodic box */
@@ -195,6 +200,9 @@ struct yk_plan_s {
     DevBuf win;      /* double[(wdeg+1) * w]: window polynomials of the FP64 path */
     DevBuf win_df;   /* float2[(wdeg+1) * w]: the same as FP32 pairs (double-float path) */
     DevBuf win32;    /* float: FP32C window + derivative polynomials (plans with dlp) */
+    DevBuf win_pc;   /* float2: 4-piece window (+ derivative) polynomials of the double-float
+                        window kernel, degree pdeg */
+    int pdeg;
     int wdeg;
     int dlp;         /* plan takes dipole sources */
     int truncated;   /* the kernel is truncated at the box diagonal (small-alpha path) */

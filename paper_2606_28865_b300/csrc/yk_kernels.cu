@@ -299,16 +299,31 @@ __global__ void k_order_fill(const int *__restrict__ ptr, int ntiles, int *__res
     if (v) order[off] = t;
 }
 
+/* W window values of one coordinate by Horner in double-float on the piece's polynomials
+ * (compile-time degree D, taps interleaved: W independent chains) */
+template <int W, int D>
+__device__ __forceinline__ void windows_piece(const df32 *c, df32 x, df32 (&p)[W])
+{
+#pragma unroll
+    for (int a = 0; a < W; ++a) p[a] = c[D * W + a];
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k)
+#pragma unroll
+        for (int a = 0; a < W; ++a) p[a] = p[a] * x + c[k * W + a];
+}
+
 /* double-float window values per point (see launch_point_windows_df): one thread per point,
- * Horner in double-float on the per-tap polynomials staged in shared memory */
+ * Horner in double-float on the 4-piece per-tap polynomials staged in shared memory (piece h of
+ * u = l0 - t + w/2 in [0, 1) is [h/4, (h+1)/4), argument x = 8u - 2h - 1) */
 template <int W>
 __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
                                    const int *__restrict__ count, const float2 *__restrict__ coef,
-                                   int deg, int deriv, float2 *__restrict__ out)
+                                   int deriv, float2 *__restrict__ out)
 {
+    constexpr int NP = 4, D = kPieceDeg[W];
     extern __shared__ __align__(16) unsigned char sm[];
     df32 *cw = reinterpret_cast<df32 *>(sm);
-    const int m = (deg + 1) * W + (deriv ? deg * W : 0);
+    const int m = NP * (D + 1) * W + (deriv ? NP * D * W : 0);
     for (int i = threadIdx.x; i < m; i += blockDim.x) cw[i] = df32(coef[i].x, coef[i].y);
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -317,20 +332,25 @@ __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
     if (t.x < 0.0) return; /* outside the box: no entries */
     const int stride = deriv ? 4 * W : 2 * W;
     float2 *o = out + (size_t)i * stride;
-    const df32 ax = window_arg_df(first_tap<W>(t.x), t.x, W);
-    const df32 ay = window_arg_df(first_tap<W>(t.y), t.y, W);
-    for (int a = 0; a < W; ++a) {
-        const df32 py = window_df<W>(cw, deg, a, ay), px = window_df<W>(cw, deg, a, ax);
-        o[a] = make_float2(py.hi, py.lo);
-        o[W + a] = make_float2(px.hi, px.lo);
-    }
+    const double ux = ((double)first_tap<W>(t.x) - t.x) + 0.5 * W;
+    const double uy = ((double)first_tap<W>(t.y) - t.y) + 0.5 * W;
+    const int hx = min(NP - 1, (int)(ux * NP)), hy = min(NP - 1, (int)(uy * NP));
+    const df32 ax(2.0 * NP * ux - 2.0 * hx - 1.0), ay(2.0 * NP * uy - 2.0 * hy - 1.0);
+    df32 p[W];
+    windows_piece<W, D>(cw + hy * (D + 1) * W, ay, p);
+#pragma unroll
+    for (int a = 0; a < W; ++a) o[a] = make_float2(p[a].hi, p[a].lo);
+    windows_piece<W, D>(cw + hx * (D + 1) * W, ax, p);
+#pragma unroll
+    for (int a = 0; a < W; ++a) o[W + a] = make_float2(p[a].hi, p[a].lo);
     if (deriv) {
-        const df32 *cwd = cw + (deg + 1) * W;
-        for (int a = 0; a < W; ++a) {
-            const df32 qy = window_df<W>(cwd, deg - 1, a, ay), qx = window_df<W>(cwd, deg - 1, a, ax);
-            o[2 * W + a] = make_float2(qy.hi, qy.lo);
-            o[3 * W + a] = make_float2(qx.hi, qx.lo);
-        }
+        const df32 *cwd = cw + NP * (D + 1) * W;
+        windows_piece<W, D - 1>(cwd + hy * D * W, ay, p);
+#pragma unroll
+        for (int a = 0; a < W; ++a) o[2 * W + a] = make_float2(p[a].hi, p[a].lo);
+        windows_piece<W, D - 1>(cwd + hx * D * W, ax, p);
+#pragma unroll
+        for (int a = 0; a < W; ++a) o[3 * W + a] = make_float2(p[a].hi, p[a].lo);
     }
 }
 
@@ -619,10 +639,11 @@ cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts
                                     float2 *out, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
-    const size_t smem = sizeof(df32) * ((deg + 1) * g.w + (deriv ? deg * g.w : 0));
+    if (g.w < 2 || g.w > 16 || deg != kPieceDeg[g.w]) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(df32) * 4 * ((deg + 1) * g.w + (deriv ? deg * g.w : 0));
     const int blocks = (int)((n + 255) / 256);
 #define YK_CALL(W)                                                                              \
-    k_point_windows_df<W><<<blocks, 256, smem, st>>>(n, pts, count, coef, deg, deriv ? 1 : 0, out)
+    k_point_windows_df<W><<<blocks, 256, smem, st>>>(n, pts, count, coef, deriv ? 1 : 0, out)
     YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     return cudaGetLastError();
