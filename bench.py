@@ -431,6 +431,19 @@ def main():
             torch.cuda.synchronize()
             lat.append(s0.elapsed_time(s1))
 
+    # cold: plan creation (parameters, multiplier, FFT tables) + set_points + eval, host wall time
+    cold_ms = {}
+    for a in alphas:
+        xs, ys, w, xt, yt, d = dbufs[a]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pc = yk.Plan(a, tol=TOL, h_vol=works[a].h_vol, box=works[a].box, stream=lanes[a])
+        pc.set_points(xs, ys, w, xt, yt)
+        pc.eval(d, out=outs[a])
+        pc.sync()
+        cold_ms[str(a)] = (time.perf_counter() - t0) * 1e3
+        pc.close()
+
     # end to end through the C ABI with pinned host buffers
     hbufs = {}
     for a in alphas:
@@ -643,6 +656,7 @@ def main():
         "clocks": clk,
         "stage_ms": {str(a): stage_ms[a] for a in alphas},
         "stage_ms_alone": {str(a): stage_ms_alone[a] for a in alphas},
+        "cold_ms": cold_ms,
         "eval_only": {"ms_per_step": eval_only_ms,
                       "value": pts_step * world / (eval_only_ms * 1e-3) if eval_only_ms else None},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
