@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32c", action="store_true", help="skip the FP32C measurement")
     ap.add_argument("--no-dlp", action="store_true", help="skip the double-layer measurement")
+    ap.add_argument("--no-local", action="store_true", help="skip the local-part measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch section")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
     ap.add_argument("--serve-requests", type=int, default=4000,
@@ -624,6 +625,32 @@ def main():
         for a in alphas:
             plans_dl[a].close()
 
+    # single-layer local asymptotic part S_{L,A} (closest point + lemma) at the 1e6 targets for
+    # the 1e5-node boundary, delta* = delta of the alpha = 10 plan (one call, host wall time: the
+    # call bins the panels, evaluates and returns after its stream finished)
+    local = None
+    if not args.no_local:
+        a_loc = 10.0 if 10.0 in alphas else alphas[0]
+        xb, yb, _, tb = W.boundary_nodes(W.Starfish(), 6250, 16)
+        t = lambda v: torch.as_tensor(v, dtype=torch.float64, device=dev)
+        lb = (t(xb), t(yb), t(W.boundary_density(tb)))
+        dstar = plans[a_loc].info["delta"]
+        xt_l, yt_l = dbufs[a_loc][3], dbufs[a_loc][4]
+        ul = torch.empty_like(xt_l)
+        for _ in range(2):
+            yk.slp_local(a_loc, dstar, *lb, xt_l, yt_l, q=16, out=ul, stream=lanes[a_loc])
+        reps = 5
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            yk.slp_local(a_loc, dstar, *lb, xt_l, yt_l, q=16, out=ul, stream=lanes[a_loc])
+        ms_loc = (time.perf_counter() - t0) / reps * 1e3
+        near = int((ul != 0).sum().item())
+        local = {"value": (len(xb) + xt_l.numel()) / (ms_loc * 1e-3), "unit": "points/s",
+                 "ms": ms_loc, "alpha": a_loc, "delta_star": dstar, "n_boundary": len(xb),
+                 "n_targets": int(xt_l.numel()), "targets_within_locality": near,
+                 "what": "yk_slp_local: panel series, cell lists, closest point, lemma terms"}
+
     batch = None if args.no_batch else batch_section(yk, torch, rank)
     serving = None if args.no_serving else serving_section(yk, args.serve_requests)
 
@@ -663,6 +690,7 @@ def main():
                        "what": "one yk_eval_longrange on a resident layout, all alphas"},
         "fp32c": fp32c,
         "double_layer": dlp,
+        "slp_local": local,
         "batch": batch,
         "serving": serving,
     }

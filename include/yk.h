@@ -186,6 +186,35 @@ YK_API yk_status yk_eval_longrange_dl(yk_plan_t p, const double *density, const 
                                       double *u);
 
 /*
+ * yk_slp_local: the single-layer local asymptotic part S_{L,A}[sigma](x_i) = int_0^{delta_star}
+ * int_boundary H(t, x_i - x') sigma(x') ds dt (Section 2.1, eq. sla) by the expansion of Section
+ * 4.1 (Lemma, eq. slp_local1) through its delta_star^{3/2} term, at the closest boundary point
+ * found by Newton on the panel polynomial (Section 3.2).  With the history part at the same
+ * delta (yk_eval_longrange with opts.delta = delta_star) it gives the single layer potential
+ * S = S_{L,A} + S_H up to O(delta_star^2) near the boundary (no dyadic levels).
+ *  - alpha > 0, delta_star > 0.
+ *  - xb, yb, sigma: n_panels * q values, panel by panel, at the q Gauss-Legendre nodes of each
+ *    panel's parameter t in [-1, 1] in ascending order; panels in counter-clockwise order around
+ *    the closed boundary (panel p + 1 follows panel p, the last is followed by the first);
+ *    2 <= q <= 32.
+ *  - xt, yt (n_trg) in, u (n_trg) written: u_i = S_{L,A} at target i, 0 beyond the locality radius
+ *    sqrt(delta_star)(12 + 2 alpha sqrt(delta_star)) from the boundary (remark on locality).
+ *  - Every array is device memory (else YK_ERR_ARG); the call allocates and frees its scratch
+ *    (Legendre series, cell lists of the panels and the targets) stream-ordered, from the
+ *    device's default memory pool, and returns after its work on `stream`
+ *    (cudaStream_t, NULL = legacy default stream) has finished.  YK_ERR_OOM if the scratch
+ *    cannot be allocated, YK_ERR_UNSUPPORTED beyond 2^30 nodes or 2^31 - 1 targets, YK_ERR_CUDA
+ *    if a CUDA call fails.
+ *  - Readings of the printed lemma: Z = 4 c2 exp(-c1^2/4 - c2^2)/sqrt(pi) (the printed Z lacks the
+ *    factor c2); kappa0 is the boundary's curvature in the (tangent, outward normal) frame, i.e.
+ *    negative on a convex piece; rho = sign((x - x0) . nu0).
+ */
+YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_t n_panels, int q,
+                              const double *xb, const double *yb, const double *sigma,
+                              int64_t n_trg, const double *xt, const double *yt, double *u,
+                              void *stream);
+
+/*
  * yk_plan_params: the parameters yk_plan would choose for (alpha, o), and in info->device_bytes
  * the device memory such a plan would hold after yk_set_points with n_src sources and n_trg
  * targets.  Makes no CUDA call (usable for memory-based admission before any allocation).

@@ -354,6 +354,29 @@ def batch_eval(plans, densities, outs):
     return outs
 
 
+_lib.yk_slp_local.argtypes = [_d, _d, _i64, ctypes.c_int, _vp, _vp, _vp, _i64, _vp, _vp, _vp,
+                              _vp]
+_lib.yk_slp_local.restype = ctypes.c_int
+
+
+def slp_local(alpha, delta_star, xb, yb, sigma, xt, yt, q=16, out=None, stream=None):
+    """Single-layer local asymptotic part at the targets (device float64 tensors); the boundary
+    as panels of q Gauss-Legendre nodes, counter-clockwise (see yk_slp_local)."""
+    torch = _torch()
+    nb, nt = _len(xb), _len(xt)
+    if nb % q or _len(yb) != nb or _len(sigma) != nb or _len(yt) != nt:
+        raise ValueError("boundary arrays must hold n_panels * q values; target lengths differ")
+    if out is None:
+        out = torch.empty(nt, dtype=torch.float64, device=xt.device)
+    if stream is None:
+        stream = _current_stream()
+    keep = []
+    _check(_lib.yk_slp_local(float(alpha), float(delta_star), nb // q, int(q), _ptr(xb, keep),
+                             _ptr(yb, keep), _ptr(sigma, keep), nt, _ptr(xt, keep),
+                             _ptr(yt, keep), _ptr(out, keep), stream), "yk_slp_local")
+    return out
+
+
 _lib.yk_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
 _lib.yk_fma_peak.restype = ctypes.c_int
 

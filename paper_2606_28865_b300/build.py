@@ -6,7 +6,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libyk.so")
-SOURCES = ["yk_api.cu", "yk_kernels.cu", "yk_batch.cu", "yk_peak.cu", "yk_static.cu", "yk_tune.cu"]
+SOURCES = ["yk_api.cu", "yk_kernels.cu", "yk_batch.cu", "yk_peak.cu", "yk_static.cu", "yk_tune.cu",
+           "yk_local.cu"]
 HEADERS = ["yk_core.h", "yk_internal.h", "yk_stages.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -23,17 +24,22 @@ def _stale() -> bool:
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
-    objs = []
     build_dir = os.path.join(HERE, "_build")
     os.makedirs(build_dir, exist_ok=True)
-    for src in SOURCES:
+
+    def compile_one(src):
         obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         cmd = ["nvcc", "-std=c++17", "-O3", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
                "-Xcompiler", "-fvisibility=hidden", "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         subprocess.check_call(cmd)
-        objs.append(obj)
+        return obj
+
+    # the translation units are independent: compile them concurrently
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     subprocess.check_call(["nvcc", "-shared", *ARCH, *objs, "-o", tmp, "-lcudart_static", "-lrt",
                            "-lpthread", "-ldl"])

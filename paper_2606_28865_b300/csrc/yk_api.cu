@@ -780,6 +780,8 @@ yk_status plan_tables(yk_plan_t p)
 
 void yk_set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 
+void yk_gauss_legendre(int n, double *x, double *w) { gauss_legendre(n, x, w); }
+
 bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
 {
     yk_plan_s *p = const_cast<yk_plan_s *>(pc);

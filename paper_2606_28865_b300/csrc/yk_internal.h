@@ -106,6 +106,9 @@ cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, cons
 cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts,
                                     const int *count, const float2 *coef, int deg, bool deriv,
                                     float2 *out, cudaStream_t st);
+/* exclusive scan of cnt[0..count) into ptr[0..count]; cur (>= ceil(count / 4096) ints) is scratch
+ * and is left zeroed */
+cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStream_t st);
 /* wnu[d] = wd[d] * (nx[d], ny[d]) */
 cudaError_t launch_pack_wnu(int64_t nd, const double *wd, const double *nx, const double *ny,
                             double2 *wnu, cudaStream_t st);
@@ -247,6 +250,9 @@ bool yk_fill_inst(const yk_plan_s *p, yk::Inst *d);
 
 /* tile edge recorded by the autotuner for this key (0: none) */
 int yk_tuned_tile(int precision, int w, int64_t n, int64_t n_src_hint);
+
+/* Gauss-Legendre nodes (ascending) and weights on [-1, 1] */
+void yk_gauss_legendre(int n, double *x, double *w);
 
 /* set the calling thread's message returned by yk_last_error */
 void yk_set_last_error(const char *msg);

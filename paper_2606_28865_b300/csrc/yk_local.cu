@@ -1,0 +1,565 @@
+/*
+ * yk_local.cu — the single-layer local asymptotic part S_{L,A}[sigma] (Section 2.1, eq. sla;
+ * Section 4.1, Lemma, eq. slp_local1, through its delta*^{3/2} term) at targets near the boundary.
+ *
+ * The boundary arrives as panels of q Gauss-Legendre nodes in the panel parameter t in [-1, 1]
+ * (Section 3.2): per panel the node coordinates and the density are turned into Legendre series,
+ * so gamma(t), sigma(t) and their first two derivatives are available anywhere on the panel.  Per
+ * target (one thread each): the panels within the locality radius r_loc = sqrt(d*)(12 + 2 alpha
+ * sqrt(d*)) (remark on locality, Section 4.1) are listed by a cell grid; the panel with the nearest
+ * node is refined by Newton on d/dt |x - gamma(t)|^2 = 0 (Section 3.2, closest point), moving to a
+ * neighbouring panel when the root leaves [-1, 1]; at the closest point x0 the lemma's terms are
+ * evaluated in FP64 with
+ *   c1 = r / sqrt(d*), c2 = alpha sqrt(d*), rho = sign((x - x0) . nu0),
+ *   kappa0 = curvature of the boundary graph in the (tangent, outward normal) frame,
+ *   Z = 4 c2 exp(-c1^2/4 - c2^2) / sqrt(pi)  (the printed Z lacks the factor c2),
+ *   sigma0'' = second arclength derivative of sigma at x0.
+ * Targets farther than r_loc from the boundary get 0.
+ */
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "yk_internal.h"
+
+namespace {
+
+constexpr int kMaxQ = 32;      /* nodes per panel this build accepts */
+constexpr int kMaxCells = 1 << 22;
+
+/* (2n+1)/(n+1) and n/(n+1): the Legendre recurrence without divisions */
+__constant__ double c_la[kMaxQ], c_lb[kMaxQ];
+__constant__ float c_laf[kMaxQ], c_lbf[kMaxQ];
+
+struct LocalGrid {
+    double x0, y0, h; /* cell (i, j) covers [x0 + i h, x0 + (i+1) h) x [y0 + j h, ...) */
+    int nx, ny;
+};
+
+/* Legendre series of the panel's x, y and sigma relative to their values at the panel's middle
+ * node (ref), from the values at the Gauss-Legendre nodes: c_n = sum_k L[n][k] (f_k - f_ref) with
+ * L[n][k] = (2n+1)/2 w_k P_n(t_k) (exact for the degree q-1 interpolant).  Relative to the panel,
+ * the coefficients' rounding scales with the panel's extent, not with |x| ~ 1: on short panels the
+ * t-derivatives (curvature) would otherwise lose most of their digits.  Also writes FP32 copies
+ * (coordinates, the middle nodes, the x and y series) for the FP32 search phase. */
+__global__ void k_panel_series(int64_t npan, int q, const double *__restrict__ xb,
+                               const double *__restrict__ yb, const double *__restrict__ sg,
+                               const double *__restrict__ L, double *__restrict__ cx,
+                               double *__restrict__ cy, double *__restrict__ cs,
+                               float *__restrict__ cxf, float *__restrict__ cyf,
+                               float *__restrict__ xbf, float *__restrict__ ybf,
+                               float *__restrict__ xmf, float *__restrict__ ymf)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npan * q) return;
+    const int64_t p = i / q;
+    const int n = (int)(i - p * q);
+    const int64_t m = p * q + q / 2; /* the reference node */
+    const double xr = xb[m], yr = yb[m], sr = sg[m];
+    double ax = 0.0, ay = 0.0, as = 0.0, mx = 0.0, my = 0.0, ms = 0.0;
+    for (int k = 0; k < q; ++k) {
+        const double lk = L[n * q + k];
+        const double fx = xb[p * q + k] - xr, fy = yb[p * q + k] - yr, fs = sg[p * q + k] - sr;
+        ax += lk * fx;
+        ay += lk * fy;
+        as += lk * fs;
+        mx = fmax(mx, fabs(fx));
+        my = fmax(my, fabs(fy));
+        ms = fmax(ms, fabs(fs));
+    }
+    /* a coefficient below the sums' rounding (a few ulp of the values times q) is noise: on a
+     * short panel the high coefficients are, and P_n'' (up to n^4/8) would amplify them into the
+     * curvature; they are set to zero */
+    const double noise = 8.0 * q * 1.1102230246251565e-16;
+    cx[i] = (n >= 2 && fabs(ax) < noise * mx) ? 0.0 : ax;
+    cy[i] = (n >= 2 && fabs(ay) < noise * my) ? 0.0 : ay;
+    cs[i] = (n >= 2 && fabs(as) < noise * ms) ? 0.0 : as;
+    cxf[i] = (float)cx[i];
+    cyf[i] = (float)cy[i];
+    xbf[i] = (float)xb[i];
+    ybf[i] = (float)yb[i];
+    if (n == q / 2) {
+        xmf[p] = (float)xr;
+        ymf[p] = (float)yr;
+    }
+}
+
+/* the boundary's bounding box and longest panel chord, per CTA (grid-strided):
+ * out[5 b + 0..4] = {xmin, xmax, ymin, ymax, hmax} over CTA b's share (reduced on the host) */
+__global__ void __launch_bounds__(1024) k_extent(int64_t npan, int q, const double *__restrict__ xb,
+                                                 const double *__restrict__ yb,
+                                                 double *__restrict__ out)
+{
+    __shared__ double red[5][32];
+    double v[5] = {1e300, -1e300, 1e300, -1e300, 0.0};
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                  stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = t0; k < npan * q; k += stride) {
+        v[0] = fmin(v[0], xb[k]);
+        v[1] = fmax(v[1], xb[k]);
+        v[2] = fmin(v[2], yb[k]);
+        v[3] = fmax(v[3], yb[k]);
+    }
+    for (int64_t p = t0; p < npan; p += stride)
+        v[4] = fmax(v[4], hypot(xb[p * q + q - 1] - xb[p * q], yb[p * q + q - 1] - yb[p * q]));
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] = fmin(v[0], __shfl_xor_sync(0xffffffffu, v[0], o));
+        v[1] = fmax(v[1], __shfl_xor_sync(0xffffffffu, v[1], o));
+        v[2] = fmin(v[2], __shfl_xor_sync(0xffffffffu, v[2], o));
+        v[3] = fmax(v[3], __shfl_xor_sync(0xffffffffu, v[3], o));
+        v[4] = fmax(v[4], __shfl_xor_sync(0xffffffffu, v[4], o));
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0)
+        for (int j = 0; j < 5; ++j) red[j][w] = v[j];
+    __syncthreads();
+    if (threadIdx.x < 5) {
+        const int j = threadIdx.x;
+        double a = red[j][0];
+        for (int k = 1; k < nw; ++k) a = (j == 0 || j == 2) ? fmin(a, red[j][k]) : fmax(a, red[j][k]);
+        out[5 * blockIdx.x + j] = a;
+    }
+}
+
+/* the cells a panel's nodes, widened by r_loc, overlap (count, then fill) */
+__device__ void panel_cells(const double *xb, const double *yb, int64_t p, int q, double rl,
+                            const LocalGrid &G, int &i0, int &i1, int &j0, int &j1)
+{
+    double xmin = xb[p * q], xmax = xmin, ymin = yb[p * q], ymax = ymin;
+    for (int k = 1; k < q; ++k) {
+        xmin = fmin(xmin, xb[p * q + k]);
+        xmax = fmax(xmax, xb[p * q + k]);
+        ymin = fmin(ymin, yb[p * q + k]);
+        ymax = fmax(ymax, yb[p * q + k]);
+    }
+    i0 = max(0, (int)floor((xmin - rl - G.x0) / G.h));
+    i1 = min(G.nx - 1, (int)floor((xmax + rl - G.x0) / G.h));
+    j0 = max(0, (int)floor((ymin - rl - G.y0) / G.h));
+    j1 = min(G.ny - 1, (int)floor((ymax + rl - G.y0) / G.h));
+}
+
+__global__ void k_cell_count(int64_t npan, int q, const double *__restrict__ xb,
+                             const double *__restrict__ yb, double rl, LocalGrid G,
+                             int *__restrict__ cnt)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npan) return;
+    int i0, i1, j0, j1;
+    panel_cells(xb, yb, p, q, rl, G, i0, i1, j0, j1);
+    for (int j = j0; j <= j1; ++j)
+        for (int i = i0; i <= i1; ++i) atomicAdd(&cnt[j * G.nx + i], 1);
+}
+
+__global__ void k_cell_fill(int64_t npan, int q, const double *__restrict__ xb,
+                            const double *__restrict__ yb, double rl, LocalGrid G,
+                            const int *__restrict__ ptr, int *__restrict__ cur,
+                            int *__restrict__ list)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npan) return;
+    int i0, i1, j0, j1;
+    panel_cells(xb, yb, p, q, rl, G, i0, i1, j0, j1);
+    for (int j = j0; j <= j1; ++j)
+        for (int i = i0; i <= i1; ++i) {
+            const int c = j * G.nx + i;
+            list[ptr[c] + atomicAdd(&cur[c], 1)] = (int)p;
+        }
+}
+
+/* value and first two t-derivatives of NS Legendre series (coefficients c[s][0..q)) at t, sharing
+ * the recurrences P_{n+1} = ((2n+1) t P_n - n P_{n-1}) / (n+1), P'_{n+1} = P'_{n-1} + (2n+1) P_n,
+ * P''_{n+1} = P''_{n-1} + (2n+1) P'_n */
+template <typename T, int NS>
+__device__ __forceinline__ void legendre_eval(const T *const (&c)[NS], int q, T t, T (&f)[NS],
+                                              T (&f1)[NS], T (&f2)[NS], const T *la, const T *lb)
+{
+    T p0 = 1, p1 = t, d0 = 0, d1 = 1, e0 = 0, e1 = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        f[s] = c[s][0] + c[s][1] * t;
+        f1[s] = c[s][1];
+        f2[s] = 0;
+    }
+    for (int n = 1; n + 1 < q; ++n) {
+        const T k = (T)(2 * n + 1);
+        const T p2 = la[n] * t * p1 - lb[n] * p0;
+        const T d2 = d0 + k * p1;
+        const T e2 = e0 + k * d1;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const T cn = c[s][n + 1];
+            f[s] += cn * p2;
+            f1[s] += cn * d2;
+            f2[s] += cn * e2;
+        }
+        p0 = p1;
+        p1 = p2;
+        d0 = d1;
+        d1 = d2;
+        e0 = e1;
+        e1 = e2;
+    }
+}
+
+/* the lemma's expansion through the delta*^{3/2} term */
+__device__ double lemma_terms(double alpha, double dstar, double r, double rho, double kappa0,
+                              double s0, double s0pp)
+{
+    const double sd = sqrt(dstar), c1 = r / sd, c2 = alpha * sd;
+    const double em = exp(-c1 * c2) * erfc(0.5 * c1 - c2);
+    const double ep = exp(c1 * c2) * erfc(0.5 * c1 + c2);
+    const double phm = em - ep, php = em + ep;
+    const double Z = 4.0 * c2 * exp(-0.25 * c1 * c1 - c2 * c2) * 0.56418958354775628695; /* 1/sqrt(pi) */
+    const double P0 = phm / c2, P1 = c1 * P0, P2 = c1 * P1;
+    const double Q0 = (phm - Z) / (c2 * c2 * c2) + c1 * php / (c2 * c2);
+    return sd * s0 * 0.25 * P0 + dstar * rho * kappa0 * s0 * 0.125 * P1 +
+           dstar * sd * (kappa0 * kappa0 * s0 / 32.0 * (Q0 + 3.0 * P2) + s0pp * 0.125 * Q0);
+}
+
+/* cell of each target (-1 outside the grid) and the targets per cell */
+__global__ void k_target_cells(int64_t nt, const double *__restrict__ xt,
+                               const double *__restrict__ yt, LocalGrid G,
+                               const int *__restrict__ pan_ptr, int *__restrict__ tcell,
+                               int *__restrict__ tcnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const int ci = (int)floor((xt[i] - G.x0) / G.h), cj = (int)floor((yt[i] - G.y0) / G.h);
+    int c = -1;
+    if (ci >= 0 && ci < G.nx && cj >= 0 && cj < G.ny) {
+        c = cj * G.nx + ci;
+        if (pan_ptr[c + 1] == pan_ptr[c]) c = -1; /* no panel within r_loc: u = 0 */
+    }
+    tcell[i] = c;
+    if (c >= 0) atomicAdd(&tcnt[c], 1);
+}
+
+__global__ void k_target_fill(int64_t nt, const int *__restrict__ tcell,
+                              const int *__restrict__ tptr, int *__restrict__ tcur,
+                              int *__restrict__ order)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const int c = tcell[i];
+    if (c >= 0) order[tptr[c] + atomicAdd(&tcur[c], 1)] = (int)i;
+}
+
+/* one thread per near target, the targets grouped by cell (so a warp scans one cell's panels).
+ * The search runs in FP32 (nearest middle node, nearest node, Newton to ~1e-5 in t, panel moves);
+ * Newton then polishes t in FP64, where f = (gamma - x) . gamma' is evaluated relative to the
+ * panel's reference node; x0's quantities are FP64. */
+__global__ void __launch_bounds__(128) k_slp_local(
+    int n_near, const int *__restrict__ order, const int *__restrict__ tcell,
+    const double *__restrict__ xt, const double *__restrict__ yt, int64_t npan, int q,
+    const double *__restrict__ xb, const double *__restrict__ yb, const double *__restrict__ cx,
+    const double *__restrict__ cy, const double *__restrict__ cs,
+    const double *__restrict__ sigma_ref, const float *__restrict__ cxf,
+    const float *__restrict__ cyf, const float *__restrict__ xbf, const float *__restrict__ ybf,
+    const float *__restrict__ xmf, const float *__restrict__ ymf, const double *__restrict__ tq,
+    const int *__restrict__ ptr, const int *__restrict__ list, double alpha, double dstar,
+    double rl, double *__restrict__ u)
+{
+    const int e0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e0 >= n_near) return;
+    const int i = order[e0];
+    const double x = xt[i], y = yt[i];
+    const float xf = (float)x, yf = (float)y;
+    const int c = tcell[i];
+    const int h = q / 2; /* each panel's middle (reference) node */
+    /* the panel whose middle node is nearest */
+    float best = 3.0e38f;
+    int64_t p = -1;
+    for (int e = ptr[c]; e < ptr[c + 1]; ++e) {
+        const int pp = list[e];
+        const float dx = xmf[pp] - xf, dy = ymf[pp] - yf;
+        const float d2 = dx * dx + dy * dy;
+        if (d2 < best) {
+            best = d2;
+            p = pp;
+        }
+    }
+    if (p < 0) { /* no panel listed (k_target_cells keeps such targets out) */
+        u[i] = 0.0;
+        return;
+    }
+    /* start at the nearest node of that panel and its two neighbours */
+    float t = 0.0f;
+    {
+        const int64_t p0 = p;
+        best = 3.0e38f;
+        for (int dp = -1; dp <= 1; ++dp) {
+            int64_t pp = p0 + dp;
+            pp = pp < 0 ? npan - 1 : (pp >= npan ? 0 : pp);
+            for (int k = 0; k < q; ++k) {
+                const float dx = xbf[pp * q + k] - xf, dy = ybf[pp * q + k] - yf;
+                const float d2 = dx * dx + dy * dy;
+                if (d2 < best) {
+                    best = d2;
+                    p = pp;
+                    t = (float)tq[k];
+                }
+            }
+        }
+    }
+    /* FP32 Newton on f(t) = (gamma(t) - x) . gamma'(t), moving to a neighbour panel when the
+     * root leaves [-1, 1] (at most two moves) */
+    for (int hop = 0; hop < 3; ++hop) {
+        const float ox = (float)(xb[p * q + h] - x), oy = (float)(yb[p * q + h] - y);
+        const float *const cf[2] = {cxf + p * q, cyf + p * q};
+        for (int it = 0; it < 10; ++it) {
+            float g[2], g1[2], g2[2];
+            legendre_eval<float, 2>(cf, q, t, g, g1, g2, c_laf, c_lbf);
+            const float ex = g[0] + ox, ey = g[1] + oy;
+            const float f = ex * g1[0] + ey * g1[1];
+            const float fp = g1[0] * g1[0] + g1[1] * g1[1] + ex * g2[0] + ey * g2[1];
+            float dt = f / fp;
+            if (!(fabsf(dt) < 4.0f)) dt = dt > 0.0f ? 4.0f : -4.0f;
+            t = fminf(fmaxf(t - dt, -3.0f), 3.0f);
+            if (fabsf(dt) < 2e-5f) break;
+        }
+        if (t > 1.0f && hop < 2) {
+            p = p + 1 < npan ? p + 1 : 0;
+            t = -1.0f;
+        } else if (t < -1.0f && hop < 2) {
+            p = p > 0 ? p - 1 : npan - 1;
+            t = 1.0f;
+        } else {
+            break;
+        }
+    }
+    /* FP64 polish (quadratic: from ~1e-5 two steps reach the rounding level) */
+    const double xr = xb[p * q + h], yr = yb[p * q + h];
+    const double ox = xr - x, oy = yr - y;
+    const double *const c2[2] = {cx + p * q, cy + p * q};
+    double td = t;
+    for (int it = 0; it < 8; ++it) {
+        double g[2], g1[2], g2[2];
+        legendre_eval<double, 2>(c2, q, td, g, g1, g2, c_la, c_lb);
+        const double ex = g[0] + ox, ey = g[1] + oy;
+        const double f = ex * g1[0] + ey * g1[1];
+        const double fp = g1[0] * g1[0] + g1[1] * g1[1] + ex * g2[0] + ey * g2[1];
+        double dt = f / fp;
+        if (!(fabs(dt) < 4.0)) dt = dt > 0.0 ? 4.0 : -4.0;
+        td = fmin(fmax(td - dt, -3.0), 3.0);
+        if (fabs(dt) < 1e-9) break;
+    }
+    const double *const c3[3] = {cx + p * q, cy + p * q, cs + p * q};
+    double g[3], g1[3], g2[3];
+    legendre_eval<double, 3>(c3, q, td, g, g1, g2, c_la, c_lb);
+    const double s = g[2] + sigma_ref[p * q + h], s1 = g1[2], s2 = g2[2];
+    const double st = sqrt(g1[0] * g1[0] + g1[1] * g1[1]);
+    const double nux = g1[1] / st, nuy = -g1[0] / st; /* outward (counter-clockwise) */
+    const double dx = -ox - g[0], dy = -oy - g[1];     /* x - gamma(t) */
+    const double r = sqrt(dx * dx + dy * dy);
+    double val = 0.0;
+    if (r < rl) {
+        const double rho = dx * nux + dy * nuy >= 0.0 ? 1.0 : -1.0;
+        const double kappa0 = -(g1[0] * g2[1] - g1[1] * g2[0]) / (st * st * st);
+        const double stt = (g1[0] * g2[0] + g1[1] * g2[1]) / st;
+        const double s0pp = (s2 - s1 * stt / st) / (st * st);
+        val = lemma_terms(alpha, dstar, r, rho, kappa0, s, s0pp);
+    }
+    u[i] = val;
+}
+
+bool is_dev(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+yk_status lfail(yk_status s, const char *msg)
+{
+    yk_set_last_error(msg);
+    return s;
+}
+
+} /* namespace */
+
+extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_t n_panels, int q,
+                                         const double *xb, const double *yb, const double *sigma,
+                                         int64_t n_trg, const double *xt, const double *yt,
+                                         double *u, void *stream)
+{
+    if (!(alpha > 0.0) || !(delta_star > 0.0) || !std::isfinite(alpha) || !std::isfinite(delta_star))
+        return lfail(YK_ERR_ARG, "yk_slp_local: alpha and delta_star must be > 0");
+    if (n_panels < 1 || q < 2 || q > kMaxQ || n_trg < 0)
+        return lfail(YK_ERR_ARG, "yk_slp_local: need n_panels >= 1, 2 <= q <= 32, n_trg >= 0");
+    if (n_panels * q > (1ll << 30) || n_trg > (1ll << 31) - 1)
+        return lfail(YK_ERR_UNSUPPORTED, "yk_slp_local: too many nodes or targets");
+    if (!is_dev(xb) || !is_dev(yb) || !is_dev(sigma) ||
+        (n_trg > 0 && (!is_dev(xt) || !is_dev(yt) || !is_dev(u))))
+        return lfail(YK_ERR_ARG, "yk_slp_local: every array must be device memory");
+    if (n_trg == 0) return YK_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double sd = std::sqrt(delta_star), rl = sd * (12.0 + 2.0 * alpha * sd);
+
+    /* host: Gauss-Legendre nodes; the boundary's extent comes from one device-to-host copy */
+    /* host tables: the nodes t_k, then L[n][k] = (2n+1)/2 w_k P_n(t_k) (the projection onto the
+     * Legendre series), and the recurrence ratios */
+    std::vector<double> tq(q), wq(q), tab(q + q * q);
+    yk_gauss_legendre(q, tq.data(), wq.data());
+    for (int k = 0; k < q; ++k) {
+        tab[k] = tq[k];
+        double p0 = 1.0, p1 = tq[k];
+        for (int n = 0; n < q; ++n) {
+            const double pn = n == 0 ? 1.0 : (n == 1 ? tq[k] : 0.0);
+            double v = pn;
+            if (n >= 2) {
+                const double p2 = ((2.0 * n - 1.0) * tq[k] * p1 - (n - 1.0) * p0) / n;
+                p0 = p1;
+                p1 = p2;
+                v = p2;
+            }
+            tab[q + n * q + k] = 0.5 * (2.0 * n + 1.0) * wq[k] * v;
+        }
+    }
+    {
+        double la[kMaxQ], lb[kMaxQ];
+        float laf[kMaxQ], lbf[kMaxQ];
+        for (int n = 0; n < kMaxQ; ++n) {
+            la[n] = (2.0 * n + 1.0) / (n + 1.0);
+            lb[n] = (double)n / (n + 1.0);
+            laf[n] = (float)la[n];
+            lbf[n] = (float)lb[n];
+        }
+        cudaError_t ec = cudaMemcpyToSymbolAsync(c_la, la, sizeof la, 0, cudaMemcpyHostToDevice, st);
+        if (ec == cudaSuccess)
+            ec = cudaMemcpyToSymbolAsync(c_lb, lb, sizeof lb, 0, cudaMemcpyHostToDevice, st);
+        if (ec == cudaSuccess)
+            ec = cudaMemcpyToSymbolAsync(c_laf, laf, sizeof laf, 0, cudaMemcpyHostToDevice, st);
+        if (ec == cudaSuccess)
+            ec = cudaMemcpyToSymbolAsync(c_lbf, lbf, sizeof lbf, 0, cudaMemcpyHostToDevice, st);
+        if (ec != cudaSuccess) return lfail(YK_ERR_CUDA, "yk_slp_local: constant table copy failed");
+    }
+    const int64_t nb = n_panels * q;
+    const int nblk = (int)std::min<int64_t>(148, (nb + 1023) / 1024);
+    double *d_ext = nullptr;
+    std::vector<double> part(5 * nblk);
+    cudaError_t e = cudaMallocAsync(&d_ext, sizeof(double) * part.size(), st);
+    if (e == cudaSuccess) {
+        k_extent<<<nblk, 1024, 0, st>>>(n_panels, q, xb, yb, d_ext);
+        e = cudaMemcpyAsync(part.data(), d_ext, sizeof(double) * part.size(),
+                            cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(d_ext, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return lfail(YK_ERR_CUDA, "yk_slp_local: boundary extent failed");
+    double ext[5] = {part[0], part[1], part[2], part[3], part[4]};
+    for (int b = 1; b < nblk; ++b) {
+        ext[0] = std::fmin(ext[0], part[5 * b]);
+        ext[1] = std::fmax(ext[1], part[5 * b + 1]);
+        ext[2] = std::fmin(ext[2], part[5 * b + 2]);
+        ext[3] = std::fmax(ext[3], part[5 * b + 3]);
+        ext[4] = std::fmax(ext[4], part[5 * b + 4]);
+    }
+    const double xmin = ext[0], xmax = ext[1], ymin = ext[2], ymax = ext[3], hmax = ext[4];
+    if (!std::isfinite(xmin + xmax + ymin + ymax + hmax))
+        return lfail(YK_ERR_ARG, "yk_slp_local: non-finite boundary node");
+    /* cells of edge >= r_loc + panel size, so every panel within r_loc of a target is listed in
+     * the target's cell */
+    LocalGrid G;
+    G.h = rl + hmax;
+    G.x0 = xmin - rl;
+    G.y0 = ymin - rl;
+    G.nx = (int)std::ceil((xmax + rl - G.x0) / G.h) + 1;
+    G.ny = (int)std::ceil((ymax + rl - G.y0) / G.h) + 1;
+    while ((int64_t)G.nx * G.ny > kMaxCells) {
+        G.h *= 2.0;
+        G.nx = (int)std::ceil((xmax + rl - G.x0) / G.h) + 1;
+        G.ny = (int)std::ceil((ymax + rl - G.y0) / G.h) + 1;
+    }
+    const int ncell = G.nx * G.ny;
+
+    /* scratch: Legendre series, cell lists */
+    double *d_tq = nullptr, *d_c = nullptr;
+    float *d_cf = nullptr;
+    int *d_cnt = nullptr, *d_ptr = nullptr, *d_cur = nullptr, *d_list = nullptr;
+    int *d_tcell = nullptr, *d_tcnt = nullptr, *d_tptr = nullptr, *d_order = nullptr;
+    /* scratch is stream-ordered (no device-wide synchronisation on free) */
+    auto cleanup = [&]() {
+        for (void *b : {(void *)d_tq, (void *)d_c, (void *)d_cf, (void *)d_cnt, (void *)d_ptr,
+                        (void *)d_cur, (void *)d_list, (void *)d_tcell, (void *)d_tcnt,
+                        (void *)d_tptr, (void *)d_order})
+            if (b) cudaFreeAsync(b, st);
+        cudaStreamSynchronize(st);
+    };
+    e = cudaMallocAsync(&d_tq, sizeof(double) * tab.size(), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_c, sizeof(double) * 3 * nb, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_cf, sizeof(float) * (4 * nb + 2 * n_panels), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_cnt, sizeof(int) * ncell, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_ptr, sizeof(int) * (ncell + 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_cur, sizeof(int) * ncell, st);
+    if (e != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return lfail(YK_ERR_OOM, "yk_slp_local: scratch allocation failed");
+    }
+    e = cudaMemcpyAsync(d_tq, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st);
+    double *cx = d_c, *cy = d_c + nb, *cs = d_c + 2 * nb;
+    float *cxf = d_cf, *cyf = d_cf + nb, *xbf = d_cf + 2 * nb, *ybf = d_cf + 3 * nb;
+    float *xmf = d_cf + 4 * nb, *ymf = d_cf + 4 * nb + n_panels;
+    if (e == cudaSuccess) {
+        k_panel_series<<<(int)((nb + 255) / 256), 256, 0, st>>>(
+            n_panels, q, xb, yb, sigma, d_tq + q, cx, cy, cs, cxf, cyf, xbf, ybf, xmf, ymf);
+        e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * ncell, st);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cur, 0, sizeof(int) * ncell, st);
+    const int pb = (int)((n_panels + 255) / 256);
+    if (e == cudaSuccess) {
+        k_cell_count<<<pb, 256, 0, st>>>(n_panels, q, xb, yb, rl, G, d_cnt);
+        e = yk::launch_scan(d_cnt, d_ptr, ncell, d_cur, st);
+    }
+    int total = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&total, d_ptr + ncell, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_list, sizeof(int) * (total > 0 ? total : 1), st);
+    if (e == cudaSuccess) {
+        k_cell_fill<<<pb, 256, 0, st>>>(n_panels, q, xb, yb, rl, G, d_ptr, d_cur, d_list);
+        e = cudaGetLastError();
+    }
+    /* the targets in cells that list panels, grouped by cell */
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_tcell, sizeof(int) * n_trg, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_tcnt, sizeof(int) * ncell, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_tptr, sizeof(int) * (ncell + 1), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_order, sizeof(int) * n_trg, st);
+    const int tb = (int)((n_trg + 255) / 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u, 0, sizeof(double) * n_trg, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_tcnt, 0, sizeof(int) * ncell, st);
+    if (e == cudaSuccess) {
+        k_target_cells<<<tb, 256, 0, st>>>(n_trg, xt, yt, G, d_ptr, d_tcell, d_tcnt);
+        e = yk::launch_scan(d_tcnt, d_tptr, ncell, d_cur, st);
+    }
+    /* d_cur still holds the panel cursors: zero it for the target cursors */
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_cur, 0, sizeof(int) * ncell, st);
+    int n_near = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&n_near, d_tptr + ncell, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) {
+        k_target_fill<<<tb, 256, 0, st>>>(n_trg, d_tcell, d_tptr, d_cur, d_order);
+        e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess && n_near > 0) {
+        k_slp_local<<<(n_near + 127) / 128, 128, 0, st>>>(
+            n_near, d_order, d_tcell, xt, yt, n_panels, q, xb, yb, cx, cy, cs, sigma, cxf, cyf,
+            xbf, ybf, xmf, ymf, d_tq, d_ptr, d_list, alpha, delta_star, rl, u);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return lfail(YK_ERR_CUDA, "yk_slp_local: a CUDA call failed");
+    }
+    return YK_OK;
+}
