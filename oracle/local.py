@@ -108,3 +108,94 @@ def starfish_density(t):
     """sigma = cos 3t + 0.5 sin t (the workloads' boundary density) and its t-derivatives."""
     return (np.cos(3 * t) + 0.5 * np.sin(t), -3 * np.sin(3 * t) + 0.5 * np.cos(t),
             -9 * np.cos(3 * t) - 0.5 * np.sin(t))
+
+
+# ------------------------------------------------------------------------------------------------
+# Volume local part V_L[f](x) = int_0^{delta*} int_Omega H_t(x - x') f(x') dx' dt (Section 2.1,
+# eq. vl), by the expansion of the Lemma for V_L (Section 4.1, eq. vp_local1) through its
+# delta*^2 term, for targets in Omega.
+#
+# Readings:
+# * Q0, Q1 as in the single-layer lemma, with Z = 4 c2 exp(-c1^2/4 - c2^2)/sqrt(pi) (the printed
+#   corollary for boundary targets, eq. vp_local2, has exactly that factor).
+# * kappa0 is the second derivative of the boundary graph in the lemma's local frame, here
+#   (tangent, inward normal eta) with the target at the origin: positive where the domain is
+#   convex, kappa0 = (x'y'' - y'x'') / |gamma'|^3 for a counter-clockwise boundary.
+# * f^(0,1) = grad f . eta, f^(0,2) = eta^T (Hess f) eta, f^(2,0) = xi^T (Hess f) xi at the target,
+#   eta the inward normal at the closest boundary point and xi the tangent there.
+# tests/test_oracle_pins_vl.py fixes these against eq. vl (half-plane, disk, interior).
+# ------------------------------------------------------------------------------------------------
+
+def vl_lemma_terms(alpha, dstar, r, kappa0, f, f_eta, f_etaeta, f_xixi):
+    """The expansion of the lemma (eq. vp_local1) through the delta*^2 term, vectorised."""
+    r, kappa0, f, f_eta, f_etaeta, f_xixi = map(np.asarray, (r, kappa0, f, f_eta, f_etaeta,
+                                                             f_xixi))
+    sd = math.sqrt(dstar)
+    c1 = r / sd
+    c2 = alpha * sd
+    em = np.exp(-c1 * c2) * sp.erfc(c1 / 2 - c2)
+    ep = np.exp(c1 * c2) * sp.erfc(c1 / 2 + c2)
+    phi_m, phi_p = em - ep, em + ep
+    Z = 4.0 * c2 * np.exp(-c1 * c1 / 4 - c2 * c2) / math.sqrt(math.pi)
+    P1 = c1 * phi_m / c2
+    Q0 = (phi_m - Z) / c2 ** 3 + c1 * phi_p / c2 ** 2
+    Q1 = c1 * Q0
+    e2 = math.exp(-c2 * c2)
+    lam = e2 * sp.erfc(c1 / 2)
+    W0 = (4.0 - 4.0 * e2 + 2.0 * lam - phi_p) / c2 ** 2
+    W1 = (2.0 * W0 - P1 + 4.0 * (lam - 2.0 * e2)) / c2 ** 2
+    return (dstar * f / 4 * W0 + dstar * sd * (2 * f_eta - f * kappa0) / 8 * Q0
+            + dstar ** 2 * ((f_eta * kappa0 / 8 - 3 * f * kappa0 ** 2 / 32 - f_etaeta / 8) * Q1
+                            + (f_etaeta + f_xixi) / 8 * W1))
+
+
+def vl_interior(alpha, dstar, f, lap_f):
+    """Targets at least the locality radius from the boundary (corollary, eq. vp_local3)."""
+    c2s = alpha * alpha * dstar
+    e2 = math.exp(-c2s)
+    return (dstar * np.asarray(f) / c2s * (1.0 - e2)
+            + dstar ** 2 * np.asarray(lap_f) / c2s ** 2 * (1.0 - (1.0 + c2s) * e2))
+
+
+def vl_boundary(alpha, dstar, kappa0, f, f_eta, f_etaeta, f_xixi):
+    """Targets on the boundary (corollary, eq. vp_local2)."""
+    c2 = alpha * math.sqrt(dstar)
+    e2 = math.exp(-c2 * c2)
+    q = (2.0 * math.erf(c2) - 4.0 * c2 / math.sqrt(math.pi) * e2) / c2 ** 3
+    return (dstar * f / (2 * c2 * c2) * (1 - e2)
+            + dstar ** 1.5 * (2 * f_eta - f * kappa0) / 8 * q
+            + dstar ** 2 * (f_etaeta + f_xixi) / (2 * c2 ** 4) * (1 - (1 + c2 * c2) * e2))
+
+
+def vp_local_starfish(alpha, dstar, geom: StarfishGeom, fderiv, xt, yt):
+    """V_L[f] at targets in the starfish domain; fderiv(x, y) -> (f, f_x, f_y, f_xx, f_xy, f_yy)
+    at the targets.  Within the locality radius the lemma at the closest boundary point of the
+    analytic curve, beyond it eq. vp_local3; targets outside the domain get NaN."""
+    xt, yt = np.atleast_1d(xt).astype(float), np.atleast_1d(yt).astype(float)
+    f, fx, fy, fxx, fxy, fyy = (np.asarray(a, dtype=float) for a in fderiv(xt, yt))
+    t = geom.closest(xt, yt)
+    g, g1, g2 = geom.derivs(t)
+    sp_ = np.hypot(g1[0], g1[1])
+    tx, ty = g1[0] / sp_, g1[1] / sp_                 # tangent xi
+    ex, ey = -ty, tx                                   # inward normal eta (counter-clockwise)
+    dx, dy = xt - g[0], yt - g[1]
+    r = np.hypot(dx, dy)
+    outside = (dx * ex + dy * ey < 0.0) & (r > 1e-8 * math.sqrt(dstar))
+    kappa0 = (g1[0] * g2[1] - g1[1] * g2[0]) / sp_ ** 3
+    f_eta = fx * ex + fy * ey
+    f_etaeta = fxx * ex * ex + 2 * fxy * ex * ey + fyy * ey * ey
+    f_xixi = fxx * tx * tx + 2 * fxy * tx * ty + fyy * ty * ty
+    near = vl_lemma_terms(alpha, dstar, r, kappa0, f, f_eta, f_etaeta, f_xixi)
+    far = vl_interior(alpha, dstar, f, fxx + fyy)
+    u = np.where(r < locality_radius(alpha, dstar), near, far)
+    return np.where(outside, np.nan, u)
+
+
+def sincos_field(kx=2.0, ky=3.0):
+    """f = sin(kx x) cos(ky y) and its derivatives (the workloads' manufactured volume field)."""
+    def fd(x, y):
+        s, c = np.sin(kx * x), np.cos(kx * x)
+        sy, cy = np.sin(ky * y), np.cos(ky * y)
+        return (s * cy, kx * c * cy, -ky * s * sy, -kx * kx * s * cy, -kx * ky * c * sy,
+                -ky * ky * s * cy)
+    return fd
