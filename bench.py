@@ -651,6 +651,31 @@ def main():
                  "n_targets": int(xt_l.numel()), "targets_within_locality": near,
                  "what": "yk_slp_local: panel series, cell lists, closest point, lemma terms"}
 
+    # volume local part V_L at the volume nodes strictly inside the curve (the cut-cell nodes by
+    # concave chords may lie just outside it), delta* = the plan's delta, same boundary
+    vlocal = None
+    if not args.no_local:
+        wk = works[a_loc]
+        vx, vy = wk.xs[wk.n_bdry:], wk.ys[wk.n_bdry:]
+        keep = W.inside_starfish(W.Starfish(), vx, vy)
+        vx, vy = vx[keep], vy[keep]
+        xv, yv = t(vx), t(vy)
+        fdv = t(W.manufactured_source_derivs(vx, vy, a_loc))
+        uv = torch.empty_like(xv)
+        for _ in range(2):
+            yk.vp_local(a_loc, dstar, lb[0], lb[1], xv, yv, fdv, q=16, out=uv, stream=lanes[a_loc])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            yk.vp_local(a_loc, dstar, lb[0], lb[1], xv, yv, fdv, q=16, out=uv, stream=lanes[a_loc])
+        ms_v = (time.perf_counter() - t0) / reps * 1e3
+        rl_v = math.sqrt(dstar) * (12 + 2 * a_loc * math.sqrt(dstar))
+        vlocal = {"value": (len(xb) + len(vx)) / (ms_v * 1e-3), "unit": "points/s", "ms": ms_v,
+                  "alpha": a_loc, "delta_star": dstar, "n_boundary": len(xb),
+                  "n_targets": int(len(vx)), "locality_radius": rl_v,
+                  "what": "yk_vp_local at the volume nodes: interior form everywhere, closest point "
+                          "+ lemma within the locality radius"}
+
     batch = None if args.no_batch else batch_section(yk, torch, rank)
     serving = None if args.no_serving else serving_section(yk, args.serve_requests)
 
@@ -691,6 +716,7 @@ def main():
         "fp32c": fp32c,
         "double_layer": dlp,
         "slp_local": local,
+        "vp_local": vlocal,
         "batch": batch,
         "serving": serving,
     }

@@ -215,6 +215,26 @@ YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_t n_panels,
                               void *stream);
 
 /*
+ * yk_vp_local: the volume local part V_L[f](x_i) = int_0^{delta_star} int_Omega H_t(x_i - x') f(x')
+ * dx' dt (Section 2.1, eq. vl) by the expansion of the Lemma for V_L (Section 4.1, eq. vp_local1)
+ * through its delta_star^2 term at targets within the locality radius of the boundary (closest
+ * point as in yk_slp_local), and by its interior form (eq. vp_local3) elsewhere.  With the history
+ * part V_H at delta = delta_star it gives the volume potential V = V_L + V_H.
+ *  - alpha > 0, delta_star > 0; boundary panels xb, yb (n_panels * q) as for yk_slp_local.
+ *  - xt, yt (n_trg): targets in the closure of the domain; fd (6 * n_trg, plane after plane): f,
+ *    f_x, f_y, f_xx, f_xy, f_yy at the targets; u (n_trg) written.
+ *  - Reading: kappa0 is the second derivative of the boundary graph in the lemma's frame
+ *    (tangent, inward normal), positive where the domain is convex; f^(0,1), f^(0,2), f^(2,0) are
+ *    f's derivatives along the inward normal and the tangent at the closest point.
+ *  - Targets within the locality radius that lie outside the domain get NaN and the call returns
+ *    YK_ERR_ARG after finishing the others; targets farther away are taken to be inside.
+ *  - Device memory only, scratch and stream semantics as yk_slp_local; the same error codes.
+ */
+YK_API yk_status yk_vp_local(double alpha, double delta_star, int64_t n_panels, int q,
+                             const double *xb, const double *yb, int64_t n_trg, const double *xt,
+                             const double *yt, const double *fd, double *u, void *stream);
+
+/*
  * yk_plan_params: the parameters yk_plan would choose for (alpha, o), and in info->device_bytes
  * the device memory such a plan would hold after yk_set_points with n_src sources and n_trg
  * targets.  Makes no CUDA call (usable for memory-based admission before any allocation).

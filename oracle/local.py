@@ -149,12 +149,51 @@ def vl_lemma_terms(alpha, dstar, r, kappa0, f, f_eta, f_etaeta, f_xixi):
                             + (f_etaeta + f_xixi) / 8 * W1))
 
 
+def vl_lemma_terms_mp(alpha, dstar, r, kappa0, f, f_eta, f_etaeta, f_xixi, dps=40):
+    """eq. vp_local1 as printed, evaluated in 40-digit arithmetic (mpmath), elementwise.  W0's
+    numerator 4 - 4 e^{-c2^2} + 2 lambda - Phi_+ is O(c2^2) while its terms are O(1), so in FP64
+    the printed form loses ~1e-16 / c2^2 (3e-11 of W0 at c2 = 3e-3); 40 digits keep the oracle
+    exact to FP64 for any c2 the tests use."""
+    import mpmath as mp
+    mp.mp.dps = dps
+    sd = mp.sqrt(mp.mpf(dstar))
+    c2 = mp.mpf(alpha) * sd
+
+    def one(r_, k_, f_, fe, fee, fxx):
+        c1 = mp.mpf(r_) / sd
+        em = mp.exp(-c1 * c2) * mp.erfc(c1 / 2 - c2)
+        ep = mp.exp(c1 * c2) * mp.erfc(c1 / 2 + c2)
+        phi_m, phi_p = em - ep, em + ep
+        Z = 4 * c2 * mp.exp(-c1 * c1 / 4 - c2 * c2) / mp.sqrt(mp.pi)
+        P1 = c1 * phi_m / c2
+        Q0 = (phi_m - Z) / c2 ** 3 + c1 * phi_p / c2 ** 2
+        Q1 = c1 * Q0
+        e2 = mp.exp(-c2 * c2)
+        lam = e2 * mp.erfc(c1 / 2)
+        W0 = (4 - 4 * e2 + 2 * lam - phi_p) / c2 ** 2
+        W1 = (2 * W0 - P1 + 4 * (lam - 2 * e2)) / c2 ** 2
+        k_, f_, fe, fee, fxx = (mp.mpf(float(v)) for v in (k_, f_, fe, fee, fxx))
+        ds = sd * sd
+        v = (ds * f_ / 4 * W0 + ds * sd * (2 * fe - f_ * k_) / 8 * Q0
+             + ds ** 2 * ((fe * k_ / 8 - 3 * f_ * k_ ** 2 / 32 - fee / 8) * Q1
+                          + (fee + fxx) / 8 * W1))
+        return float(v)
+    args = np.broadcast_arrays(*(np.asarray(a, dtype=float) for a in
+                                 (r, kappa0, f, f_eta, f_etaeta, f_xixi)))
+    out = np.array([one(*vals) for vals in zip(*(a.ravel() for a in args))])
+    return out.reshape(args[0].shape)
+
+
 def vl_interior(alpha, dstar, f, lap_f):
-    """Targets at least the locality radius from the boundary (corollary, eq. vp_local3)."""
-    c2s = alpha * alpha * dstar
-    e2 = math.exp(-c2s)
-    return (dstar * np.asarray(f) / c2s * (1.0 - e2)
-            + dstar ** 2 * np.asarray(lap_f) / c2s ** 2 * (1.0 - (1.0 + c2s) * e2))
+    """Targets at least the locality radius from the boundary (corollary, eq. vp_local3).  Its
+    two coefficients (1 - e^{-c})/c and (1 - (1 + c) e^{-c})/c^2, c = alpha^2 delta*, are taken in
+    40-digit arithmetic: in FP64 the second loses ~1e-16 / c^2 of itself for small c."""
+    import mpmath as mp
+    mp.mp.dps = 40
+    c = mp.mpf(alpha) ** 2 * mp.mpf(dstar)
+    a1 = float((1 - mp.exp(-c)) / c)
+    a2 = float((1 - (1 + c) * mp.exp(-c)) / c ** 2)
+    return dstar * np.asarray(f) * a1 + dstar ** 2 * np.asarray(lap_f) * a2
 
 
 def vl_boundary(alpha, dstar, kappa0, f, f_eta, f_etaeta, f_xixi):
@@ -169,8 +208,9 @@ def vl_boundary(alpha, dstar, kappa0, f, f_eta, f_etaeta, f_xixi):
 
 def vp_local_starfish(alpha, dstar, geom: StarfishGeom, fderiv, xt, yt):
     """V_L[f] at targets in the starfish domain; fderiv(x, y) -> (f, f_x, f_y, f_xx, f_xy, f_yy)
-    at the targets.  Within the locality radius the lemma at the closest boundary point of the
-    analytic curve, beyond it eq. vp_local3; targets outside the domain get NaN."""
+    at the targets.  Within the locality radius the lemma (40-digit evaluation) at the closest
+    boundary point of the analytic curve, beyond it eq. vp_local3; targets outside the domain get
+    NaN."""
     xt, yt = np.atleast_1d(xt).astype(float), np.atleast_1d(yt).astype(float)
     f, fx, fy, fxx, fxy, fyy = (np.asarray(a, dtype=float) for a in fderiv(xt, yt))
     t = geom.closest(xt, yt)
@@ -185,9 +225,13 @@ def vp_local_starfish(alpha, dstar, geom: StarfishGeom, fderiv, xt, yt):
     f_eta = fx * ex + fy * ey
     f_etaeta = fxx * ex * ex + 2 * fxy * ex * ey + fyy * ey * ey
     f_xixi = fxx * tx * tx + 2 * fxy * tx * ty + fyy * ty * ty
-    near = vl_lemma_terms(alpha, dstar, r, kappa0, f, f_eta, f_etaeta, f_xixi)
-    far = vl_interior(alpha, dstar, f, fxx + fyy)
-    u = np.where(r < locality_radius(alpha, dstar), near, far)
+    rl = locality_radius(alpha, dstar)
+    u = vl_interior(alpha, dstar, f, fxx + fyy)
+    m = r < rl
+    if np.any(m):
+        u = np.array(u, dtype=float)
+        u[m] = vl_lemma_terms_mp(alpha, dstar, r[m], kappa0[m], f[m], f_eta[m], f_etaeta[m],
+                                 f_xixi[m])
     return np.where(outside, np.nan, u)
 
 

@@ -377,6 +377,33 @@ def slp_local(alpha, delta_star, xb, yb, sigma, xt, yt, q=16, out=None, stream=N
     return out
 
 
+_lib.yk_vp_local.argtypes = [_d, _d, _i64, ctypes.c_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
+                             _vp]
+_lib.yk_vp_local.restype = ctypes.c_int
+
+
+def vp_local(alpha, delta_star, xb, yb, xt, yt, fd, q=16, out=None, stream=None):
+    """Volume local part at targets in the domain (device float64 tensors).  fd: the six planes
+    f, f_x, f_y, f_xx, f_xy, f_yy at the targets, as a (6, n_trg) tensor or a sequence of six
+    (see yk_vp_local)."""
+    torch = _torch()
+    nb, nt = _len(xb), _len(xt)
+    if not isinstance(fd, torch.Tensor):
+        fd = torch.stack([torch.as_tensor(a, dtype=torch.float64, device=xt.device) for a in fd])
+    fd = fd.contiguous()
+    if nb % q or _len(yb) != nb or _len(yt) != nt or fd.numel() != 6 * nt:
+        raise ValueError("boundary arrays must hold n_panels * q values; fd must hold 6 * n_trg")
+    if out is None:
+        out = torch.empty(nt, dtype=torch.float64, device=xt.device)
+    if stream is None:
+        stream = _current_stream()
+    keep = []
+    _check(_lib.yk_vp_local(float(alpha), float(delta_star), nb // q, int(q), _ptr(xb, keep),
+                            _ptr(yb, keep), nt, _ptr(xt, keep), _ptr(yt, keep), _ptr(fd, keep),
+                            _ptr(out, keep), stream), "yk_vp_local")
+    return out
+
+
 _lib.yk_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
 _lib.yk_fma_peak.restype = ctypes.c_int
 

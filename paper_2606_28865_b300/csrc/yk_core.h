@@ -63,7 +63,7 @@ template <int SIGN, typename R> YK_HD cpx<R> mul_i(cpx<R> a)
 #define YK_FFMA(a, b, c) fmaf(a, b, c)
 #endif
 
-struct df32 {
+struct alignas(8) df32 { /* 8-byte aligned: one 64-bit shared-memory access per value */
     float hi, lo;
     df32() = default;
     YK_HD df32(float h, float l) : hi(h), lo(l) {}

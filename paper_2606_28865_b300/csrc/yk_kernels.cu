@@ -531,10 +531,10 @@ int stage_smem(const Inst &d, int stage)
     switch (stage) {
     case ST_SPREAD:
         if (d.fft_df)
-            return (int)(sizeof(df32) * kSpreadWarps * T * (T + 1) +
+            return (int)(sizeof(df32) * kSpreadWarps * spread_tile_cells(T) +
                          sizeof(df32) * kSpreadWarps * kSpreadBatch * SW +
                          sizeof(int) * kSpreadWarps * 2 * kSpreadBatch);
-        return d.f32 ? (int)(sizeof(float2) * kSpreadWarps * T * (T + 1) +
+        return d.f32 ? (int)(sizeof(float2) * kSpreadWarps * spread_tile_cells(T) +
                              sizeof(float) * kSpreadWarps * 32 * SW +
                              sizeof(int) * kSpreadWarps * 64 + (d.dip ? sizeof(float) * ncoef : 0))
                      : (int)(sizeof(unsigned long long) * T * T + win_bytes);

@@ -15,6 +15,12 @@
  *   Z = 4 c2 exp(-c1^2/4 - c2^2) / sqrt(pi)  (the printed Z lacks the factor c2),
  *   sigma0'' = second arclength derivative of sigma at x0.
  * Targets farther than r_loc from the boundary get 0.
+ *
+ * The volume local part V_L[f] (Section 2.1, eq. vl; Lemma for V_L, eq. vp_local1, through its
+ * delta*^2 term) reuses the same closest-point search: at the near targets the lemma in the frame
+ * (tangent xi, inward normal eta) at x0, with f's derivatives at the target rotated into that
+ * frame and kappa0 the boundary graph's second derivative there (positive where the domain is
+ * convex); elsewhere the interior form (eq. vp_local3).
  */
 #include <cuda_runtime.h>
 
@@ -248,68 +254,62 @@ __global__ void k_target_fill(int64_t nt, const int *__restrict__ tcell,
     if (c >= 0) order[tptr[c] + atomicAdd(&tcur[c], 1)] = (int)i;
 }
 
-/* one thread per near target, the targets grouped by cell (so a warp scans one cell's panels).
- * The search runs in FP32 (nearest middle node, nearest node, Newton to ~1e-5 in t, panel moves);
- * Newton then polishes t in FP64, where f = (gamma - x) . gamma' is evaluated relative to the
- * panel's reference node; x0's quantities are FP64. */
-__global__ void __launch_bounds__(128) k_slp_local(
-    int n_near, const int *__restrict__ order, const int *__restrict__ tcell,
-    const double *__restrict__ xt, const double *__restrict__ yt, int64_t npan, int q,
-    const double *__restrict__ xb, const double *__restrict__ yb, const double *__restrict__ cx,
-    const double *__restrict__ cy, const double *__restrict__ cs,
-    const double *__restrict__ sigma_ref, const float *__restrict__ cxf,
-    const float *__restrict__ cyf, const float *__restrict__ xbf, const float *__restrict__ ybf,
-    const float *__restrict__ xmf, const float *__restrict__ ymf, const double *__restrict__ tq,
-    const int *__restrict__ ptr, const int *__restrict__ list, double alpha, double dstar,
-    double rl, double *__restrict__ u)
+/* the boundary as the target kernels see it */
+struct PanelSet {
+    int64_t npan;
+    int q;
+    const double *xb, *yb;            /* nodes (FP64) */
+    const double *cx, *cy, *cs;       /* Legendre series relative to the middle nodes */
+    const double *sref;               /* sigma at the nodes (its middle node is cs's reference) */
+    const float *cxf, *cyf, *xbf, *ybf, *xmf, *ymf; /* FP32 copies for the search */
+    const double *tq;                 /* Gauss-Legendre nodes */
+    const int *ptr, *list;            /* panels listed per cell */
+};
+
+/* Closest boundary point of (x, y), the target's cell c listing at least one panel: panel p and
+ * parameter t.  The search runs in FP32 (nearest middle node, nearest node of that panel and its
+ * neighbours, Newton on f(t) = (gamma(t) - x) . gamma'(t) to ~1e-5 in t, moving to a neighbour
+ * panel when the root leaves [-1, 1], at most twice); Newton then polishes t in FP64, with f
+ * evaluated relative to the panel's reference node (quadratic: from ~1e-5 two steps reach the
+ * rounding level).  Returns false if the cell lists no panel. */
+__device__ bool closest_point(const PanelSet &P, double x, double y, int c, int64_t &pout,
+                              double &tout)
 {
-    const int e0 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e0 >= n_near) return;
-    const int i = order[e0];
-    const double x = xt[i], y = yt[i];
+    const int q = P.q, h = q / 2;
     const float xf = (float)x, yf = (float)y;
-    const int c = tcell[i];
-    const int h = q / 2; /* each panel's middle (reference) node */
-    /* the panel whose middle node is nearest */
     float best = 3.0e38f;
     int64_t p = -1;
-    for (int e = ptr[c]; e < ptr[c + 1]; ++e) {
-        const int pp = list[e];
-        const float dx = xmf[pp] - xf, dy = ymf[pp] - yf;
+    for (int e = P.ptr[c]; e < P.ptr[c + 1]; ++e) {
+        const int pp = P.list[e];
+        const float dx = P.xmf[pp] - xf, dy = P.ymf[pp] - yf;
         const float d2 = dx * dx + dy * dy;
         if (d2 < best) {
             best = d2;
             p = pp;
         }
     }
-    if (p < 0) { /* no panel listed (k_target_cells keeps such targets out) */
-        u[i] = 0.0;
-        return;
-    }
-    /* start at the nearest node of that panel and its two neighbours */
+    if (p < 0) return false;
     float t = 0.0f;
     {
         const int64_t p0 = p;
         best = 3.0e38f;
         for (int dp = -1; dp <= 1; ++dp) {
             int64_t pp = p0 + dp;
-            pp = pp < 0 ? npan - 1 : (pp >= npan ? 0 : pp);
+            pp = pp < 0 ? P.npan - 1 : (pp >= P.npan ? 0 : pp);
             for (int k = 0; k < q; ++k) {
-                const float dx = xbf[pp * q + k] - xf, dy = ybf[pp * q + k] - yf;
+                const float dx = P.xbf[pp * q + k] - xf, dy = P.ybf[pp * q + k] - yf;
                 const float d2 = dx * dx + dy * dy;
                 if (d2 < best) {
                     best = d2;
                     p = pp;
-                    t = (float)tq[k];
+                    t = (float)P.tq[k];
                 }
             }
         }
     }
-    /* FP32 Newton on f(t) = (gamma(t) - x) . gamma'(t), moving to a neighbour panel when the
-     * root leaves [-1, 1] (at most two moves) */
     for (int hop = 0; hop < 3; ++hop) {
-        const float ox = (float)(xb[p * q + h] - x), oy = (float)(yb[p * q + h] - y);
-        const float *const cf[2] = {cxf + p * q, cyf + p * q};
+        const float ox = (float)(P.xb[p * q + h] - x), oy = (float)(P.yb[p * q + h] - y);
+        const float *const cf[2] = {P.cxf + p * q, P.cyf + p * q};
         for (int it = 0; it < 10; ++it) {
             float g[2], g1[2], g2[2];
             legendre_eval<float, 2>(cf, q, t, g, g1, g2, c_laf, c_lbf);
@@ -322,19 +322,17 @@ __global__ void __launch_bounds__(128) k_slp_local(
             if (fabsf(dt) < 2e-5f) break;
         }
         if (t > 1.0f && hop < 2) {
-            p = p + 1 < npan ? p + 1 : 0;
+            p = p + 1 < P.npan ? p + 1 : 0;
             t = -1.0f;
         } else if (t < -1.0f && hop < 2) {
-            p = p > 0 ? p - 1 : npan - 1;
+            p = p > 0 ? p - 1 : P.npan - 1;
             t = 1.0f;
         } else {
             break;
         }
     }
-    /* FP64 polish (quadratic: from ~1e-5 two steps reach the rounding level) */
-    const double xr = xb[p * q + h], yr = yb[p * q + h];
-    const double ox = xr - x, oy = yr - y;
-    const double *const c2[2] = {cx + p * q, cy + p * q};
+    const double ox = P.xb[p * q + h] - x, oy = P.yb[p * q + h] - y;
+    const double *const c2[2] = {P.cx + p * q, P.cy + p * q};
     double td = t;
     for (int it = 0; it < 8; ++it) {
         double g[2], g1[2], g2[2];
@@ -347,13 +345,38 @@ __global__ void __launch_bounds__(128) k_slp_local(
         td = fmin(fmax(td - dt, -3.0), 3.0);
         if (fabs(dt) < 1e-9) break;
     }
-    const double *const c3[3] = {cx + p * q, cy + p * q, cs + p * q};
+    pout = p;
+    tout = td;
+    return true;
+}
+
+/* S_{L,A}: one thread per near target, the targets grouped by cell (a warp scans one cell's
+ * panel list) */
+__global__ void __launch_bounds__(128) k_slp_local(int n_near, const int *__restrict__ order,
+                                                   const int *__restrict__ tcell,
+                                                   const double *__restrict__ xt,
+                                                   const double *__restrict__ yt, PanelSet P,
+                                                   double alpha, double dstar, double rl,
+                                                   double *__restrict__ u)
+{
+    const int e0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e0 >= n_near) return;
+    const int i = order[e0];
+    const double x = xt[i], y = yt[i];
+    int64_t p;
+    double td;
+    if (!closest_point(P, x, y, tcell[i], p, td)) {
+        u[i] = 0.0;
+        return;
+    }
+    const int q = P.q, h = q / 2;
+    const double *const c3[3] = {P.cx + p * q, P.cy + p * q, P.cs + p * q};
     double g[3], g1[3], g2[3];
     legendre_eval<double, 3>(c3, q, td, g, g1, g2, c_la, c_lb);
-    const double s = g[2] + sigma_ref[p * q + h], s1 = g1[2], s2 = g2[2];
+    const double s = g[2] + P.sref[p * q + h], s1 = g1[2], s2 = g2[2];
     const double st = sqrt(g1[0] * g1[0] + g1[1] * g1[1]);
     const double nux = g1[1] / st, nuy = -g1[0] / st; /* outward (counter-clockwise) */
-    const double dx = -ox - g[0], dy = -oy - g[1];     /* x - gamma(t) */
+    const double dx = (x - P.xb[p * q + h]) - g[0], dy = (y - P.yb[p * q + h]) - g[1];
     const double r = sqrt(dx * dx + dy * dy);
     double val = 0.0;
     if (r < rl) {
@@ -364,6 +387,139 @@ __global__ void __launch_bounds__(128) k_slp_local(
         val = lemma_terms(alpha, dstar, r, rho, kappa0, s, s0pp);
     }
     u[i] = val;
+}
+
+/* V_L beyond the locality radius (corollary, eq. vp_local3): f and its Laplacian only */
+__device__ __forceinline__ double vl_interior(double alpha, double dstar, double f, double lap)
+{
+    const double c2s = alpha * alpha * dstar, e2 = exp(-c2s);
+    /* 1 - e^{-c} and 1 - (1 + c) e^{-c} without cancellation for small c */
+    const double a1 = -expm1(-c2s);
+    const double a2 = a1 - c2s * e2;
+    return dstar * f / c2s * a1 + dstar * dstar * lap / (c2s * c2s) * a2;
+}
+
+/* The lemma's P1, Q0, W0, W1 for small c2.  The printed W0 = (4 - 4 e^{-c2^2} + 2 lambda -
+ * Phi_+) / c2^2 has an O(c2^2) numerator made of O(1) terms, so in FP64 it loses ~1e-16 / c2^2.
+ * Instead: g = e^{-c1 c2} erfc(c1/2 - c2) and h = e^{c1 c2} erfc(c1/2 + c2) satisfy
+ * g' = -c1 g + G e^{-c2^2}, h' = c1 h - G e^{-c2^2} (d/dc2, G = 2 e^{-c1^2/4} / sqrt(pi)), so
+ * Phi_+ = g + h and Phi_- = g - h have the Taylor coefficients p_n, m_n in c2 of
+ *   (n+1) p_{n+1} = -c1 m_n,  (n+1) m_{n+1} = -c1 p_n + 2 G e_n,  p_0 = 2 erfc(c1/2), m_0 = 0,
+ * e_n those of e^{-c2^2}.  Dividing the series by the powers of c2 term by term leaves sums with
+ * no cancellation (the leading term of W0 is the remark's 4 - (2 + c1^2) E + c1 G). */
+__device__ void lemma_small_c2(double c1, double c2, double &P1, double &Q0, double &W0,
+                               double &W1)
+{
+    const double E = erfc(0.5 * c1), G = 1.1283791670955126 * exp(-0.25 * c1 * c1);
+    double p = 2.0 * E, m = 0.0;   /* p_n, m_n */
+    double en = 1.0;               /* e_n for even n */
+    double c2n = 1.0;              /* c2^n */
+    const double ic2 = 1.0 / c2, ic2s = ic2 * ic2;
+    P1 = Q0 = W0 = W1 = 0.0;
+    for (int n = 0; n < 90; ++n) {
+        const bool even = (n & 1) == 0;
+        const double e_n = even ? en : 0.0;
+        if (even && n >= 2) {
+            const double w0n = (2.0 * E - 4.0) * e_n - p; /* W0's coefficient of c2^{n-2} */
+            W0 += w0n * c2n * ic2s;
+            Q0 += (c1 * p - G * 2.0 * e_n) * c2n * ic2s;
+            W1 += (4.0 * E - 8.0) * e_n * c2n * ic2s;
+            if (n >= 4) W1 += 2.0 * w0n * c2n * ic2s * ic2s;
+        }
+        if (!even) {
+            P1 += c1 * m * c2n * ic2;
+            if (n >= 3) {
+                Q0 += m * c2n * ic2s * ic2;
+                W1 -= c1 * m * c2n * ic2s * ic2;
+            }
+        }
+        /* next coefficients */
+        const double pn1 = -c1 * m / (n + 1), mn1 = (-c1 * p + 2.0 * G * e_n) / (n + 1);
+        p = pn1;
+        m = mn1;
+        if (even) en = -en / (n / 2 + 1); /* e_{n+2} = -e_n / (n/2 + 1) */
+        c2n *= c2;
+        if (n >= 12 && fabs(p) * c2n < 1e-19 * c2 * c2 && fabs(m) * c2n < 1e-19 * c2 * c2 &&
+            fabs(en) * c2n < 1e-19 * c2 * c2)
+            break;
+    }
+}
+
+/* V_L by the lemma (eq. vp_local1) through the delta*^2 term */
+__device__ double vl_lemma_terms(double alpha, double dstar, double r, double kappa0, double f,
+                                 double f_eta, double f_etaeta, double f_xixi)
+{
+    const double sd = sqrt(dstar), c1 = r / sd, c2 = alpha * sd;
+    double P1, Q0, W0, W1;
+    if (c2 < 0.5) {
+        lemma_small_c2(c1, c2, P1, Q0, W0, W1);
+    } else {
+        const double em = exp(-c1 * c2) * erfc(0.5 * c1 - c2);
+        const double ep = exp(c1 * c2) * erfc(0.5 * c1 + c2);
+        const double phm = em - ep, php = em + ep;
+        const double Z = 4.0 * c2 * exp(-0.25 * c1 * c1 - c2 * c2) * 0.56418958354775628695;
+        P1 = c1 * phm / c2;
+        Q0 = (phm - Z) / (c2 * c2 * c2) + c1 * php / (c2 * c2);
+        const double e2 = exp(-c2 * c2), lam = e2 * erfc(0.5 * c1);
+        W0 = (4.0 - 4.0 * e2 + 2.0 * lam - php) / (c2 * c2);
+        W1 = (2.0 * W0 - P1 + 4.0 * (lam - 2.0 * e2)) / (c2 * c2);
+    }
+    const double Q1 = c1 * Q0;
+    return dstar * f * 0.25 * W0 + dstar * sd * (2.0 * f_eta - f * kappa0) * 0.125 * Q0 +
+           dstar * dstar *
+               ((f_eta * kappa0 * 0.125 - 3.0 * f * kappa0 * kappa0 / 32.0 - f_etaeta * 0.125) * Q1 +
+                (f_etaeta + f_xixi) * 0.125 * W1);
+}
+
+/* every target: eq. vp_local3 (the near targets are overwritten by k_vp_local) */
+__global__ void k_vp_interior(int64_t nt, const double *__restrict__ fd, double alpha, double dstar,
+                              double *__restrict__ u)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    u[i] = vl_interior(alpha, dstar, fd[i], fd[3 * nt + i] + fd[5 * nt + i]);
+}
+
+/* V_L at the near targets: closest point, then the lemma in the frame (tangent xi, inward normal
+ * eta) at x0; a target found outside the domain (on the outward side, beyond rounding) gets NaN
+ * and is counted */
+__global__ void __launch_bounds__(128) k_vp_local(int n_near, const int *__restrict__ order,
+                                                  const int *__restrict__ tcell,
+                                                  const double *__restrict__ xt,
+                                                  const double *__restrict__ yt, int64_t nt,
+                                                  const double *__restrict__ fd, PanelSet P,
+                                                  double alpha, double dstar, double rl,
+                                                  double *__restrict__ u, int *__restrict__ nout)
+{
+    const int e0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e0 >= n_near) return;
+    const int i = order[e0];
+    const double x = xt[i], y = yt[i];
+    int64_t p;
+    double td;
+    if (!closest_point(P, x, y, tcell[i], p, td)) return; /* keeps the interior value */
+    const int q = P.q, h = q / 2;
+    const double *const c2[2] = {P.cx + p * q, P.cy + p * q};
+    double g[2], g1[2], g2[2];
+    legendre_eval<double, 2>(c2, q, td, g, g1, g2, c_la, c_lb);
+    const double st = sqrt(g1[0] * g1[0] + g1[1] * g1[1]);
+    const double tx = g1[0] / st, ty = g1[1] / st; /* tangent xi */
+    const double ex = -ty, ey = tx;                 /* inward normal eta (counter-clockwise) */
+    const double dx = (x - P.xb[p * q + h]) - g[0], dy = (y - P.yb[p * q + h]) - g[1];
+    const double r = sqrt(dx * dx + dy * dy);
+    if (!(r < rl)) return;                          /* keeps the interior value */
+    if (dx * ex + dy * ey < 0.0 && r > 1e-8 * sqrt(dstar)) {
+        u[i] = nan("");
+        atomicAdd(nout, 1);
+        return;
+    }
+    const double kappa0 = (g1[0] * g2[1] - g1[1] * g2[0]) / (st * st * st);
+    const double f = fd[i], fx = fd[nt + i], fy = fd[2 * nt + i];
+    const double fxx = fd[3 * nt + i], fxy = fd[4 * nt + i], fyy = fd[5 * nt + i];
+    const double f_eta = fx * ex + fy * ey;
+    const double f_etaeta = fxx * ex * ex + 2.0 * fxy * ex * ey + fyy * ey * ey;
+    const double f_xixi = fxx * tx * tx + 2.0 * fxy * tx * ty + fyy * ty * ty;
+    u[i] = vl_lemma_terms(alpha, dstar, r, kappa0, f, f_eta, f_etaeta, f_xixi);
 }
 
 bool is_dev(const void *p)
@@ -383,23 +539,28 @@ yk_status lfail(yk_status s, const char *msg)
     return s;
 }
 
-} /* namespace */
-
-extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_t n_panels, int q,
-                                         const double *xb, const double *yb, const double *sigma,
-                                         int64_t n_trg, const double *xt, const double *yt,
-                                         double *u, void *stream)
+/* S_{L,A} (vol false: sigma) or V_L (vol true: fd): shared set-up (extent, panel
+ * series, cell lists, near targets grouped by cell), then the part's kernels */
+yk_status run_local(const char *name, bool vol, double alpha, double delta_star, int64_t n_panels, int q,
+                    const double *xb, const double *yb, const double *sigma, int64_t n_trg,
+                    const double *xt, const double *yt, const double *fd, double *u, void *stream)
 {
+    char msg[160];
+    auto fail = [&](yk_status code, const char *what) {
+        std::snprintf(msg, sizeof msg, "%s: %s", name, what);
+        return lfail(code, msg);
+    };
     if (!(alpha > 0.0) || !(delta_star > 0.0) || !std::isfinite(alpha) || !std::isfinite(delta_star))
-        return lfail(YK_ERR_ARG, "yk_slp_local: alpha and delta_star must be > 0");
+        return fail(YK_ERR_ARG, "alpha and delta_star must be > 0");
     if (n_panels < 1 || q < 2 || q > kMaxQ || n_trg < 0)
-        return lfail(YK_ERR_ARG, "yk_slp_local: need n_panels >= 1, 2 <= q <= 32, n_trg >= 0");
+        return fail(YK_ERR_ARG, "need n_panels >= 1, 2 <= q <= 32, n_trg >= 0");
     if (n_panels * q > (1ll << 30) || n_trg > (1ll << 31) - 1)
-        return lfail(YK_ERR_UNSUPPORTED, "yk_slp_local: too many nodes or targets");
-    if (!is_dev(xb) || !is_dev(yb) || !is_dev(sigma) ||
-        (n_trg > 0 && (!is_dev(xt) || !is_dev(yt) || !is_dev(u))))
-        return lfail(YK_ERR_ARG, "yk_slp_local: every array must be device memory");
+        return fail(YK_ERR_UNSUPPORTED, "too many nodes or targets");
+    if (!is_dev(xb) || !is_dev(yb) || (!vol && !is_dev(sigma)) ||
+        (n_trg > 0 && (!is_dev(xt) || !is_dev(yt) || !is_dev(u) || (vol && !is_dev(fd)))))
+        return fail(YK_ERR_ARG, "every array must be device memory");
     if (n_trg == 0) return YK_OK;
+    if (vol) sigma = xb; /* the density series is not used; any node array serves */
     cudaStream_t st = (cudaStream_t)stream;
     const double sd = std::sqrt(delta_star), rl = sd * (12.0 + 2.0 * alpha * sd);
 
@@ -439,7 +600,7 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
             ec = cudaMemcpyToSymbolAsync(c_laf, laf, sizeof laf, 0, cudaMemcpyHostToDevice, st);
         if (ec == cudaSuccess)
             ec = cudaMemcpyToSymbolAsync(c_lbf, lbf, sizeof lbf, 0, cudaMemcpyHostToDevice, st);
-        if (ec != cudaSuccess) return lfail(YK_ERR_CUDA, "yk_slp_local: constant table copy failed");
+        if (ec != cudaSuccess) return fail(YK_ERR_CUDA, "constant table copy failed");
     }
     const int64_t nb = n_panels * q;
     const int nblk = (int)std::min<int64_t>(148, (nb + 1023) / 1024);
@@ -453,7 +614,7 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
         cudaFreeAsync(d_ext, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return lfail(YK_ERR_CUDA, "yk_slp_local: boundary extent failed");
+    if (e != cudaSuccess) return fail(YK_ERR_CUDA, "boundary extent failed");
     double ext[5] = {part[0], part[1], part[2], part[3], part[4]};
     for (int b = 1; b < nblk; ++b) {
         ext[0] = std::fmin(ext[0], part[5 * b]);
@@ -464,7 +625,7 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
     }
     const double xmin = ext[0], xmax = ext[1], ymin = ext[2], ymax = ext[3], hmax = ext[4];
     if (!std::isfinite(xmin + xmax + ymin + ymax + hmax))
-        return lfail(YK_ERR_ARG, "yk_slp_local: non-finite boundary node");
+        return fail(YK_ERR_ARG, "non-finite boundary node");
     /* cells of edge >= r_loc + panel size, so every panel within r_loc of a target is listed in
      * the target's cell */
     LocalGrid G;
@@ -485,11 +646,12 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
     float *d_cf = nullptr;
     int *d_cnt = nullptr, *d_ptr = nullptr, *d_cur = nullptr, *d_list = nullptr;
     int *d_tcell = nullptr, *d_tcnt = nullptr, *d_tptr = nullptr, *d_order = nullptr;
+    int *d_nout = nullptr;
     /* scratch is stream-ordered (no device-wide synchronisation on free) */
     auto cleanup = [&]() {
         for (void *b : {(void *)d_tq, (void *)d_c, (void *)d_cf, (void *)d_cnt, (void *)d_ptr,
                         (void *)d_cur, (void *)d_list, (void *)d_tcell, (void *)d_tcnt,
-                        (void *)d_tptr, (void *)d_order})
+                        (void *)d_tptr, (void *)d_order, (void *)d_nout})
             if (b) cudaFreeAsync(b, st);
         cudaStreamSynchronize(st);
     };
@@ -499,10 +661,12 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
     if (e == cudaSuccess) e = cudaMallocAsync(&d_cnt, sizeof(int) * ncell, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_ptr, sizeof(int) * (ncell + 1), st);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_cur, sizeof(int) * ncell, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_nout, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_nout, 0, sizeof(int), st);
     if (e != cudaSuccess) {
         cleanup();
         cudaGetLastError();
-        return lfail(YK_ERR_OOM, "yk_slp_local: scratch allocation failed");
+        return fail(YK_ERR_OOM, "scratch allocation failed");
     }
     e = cudaMemcpyAsync(d_tq, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st);
     double *cx = d_c, *cy = d_c + nb, *cs = d_c + 2 * nb;
@@ -534,7 +698,14 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
     if (e == cudaSuccess) e = cudaMallocAsync(&d_tptr, sizeof(int) * (ncell + 1), st);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_order, sizeof(int) * n_trg, st);
     const int tb = (int)((n_trg + 255) / 256);
-    if (e == cudaSuccess) e = cudaMemsetAsync(u, 0, sizeof(double) * n_trg, st);
+    if (e == cudaSuccess) {
+        if (vol) {
+            k_vp_interior<<<tb, 256, 0, st>>>(n_trg, fd, alpha, delta_star, u);
+            e = cudaGetLastError();
+        } else {
+            e = cudaMemsetAsync(u, 0, sizeof(double) * n_trg, st);
+        }
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_tcnt, 0, sizeof(int) * ncell, st);
     if (e == cudaSuccess) {
         k_target_cells<<<tb, 256, 0, st>>>(n_trg, xt, yt, G, d_ptr, d_tcell, d_tcnt);
@@ -549,17 +720,69 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
         k_target_fill<<<tb, 256, 0, st>>>(n_trg, d_tcell, d_tptr, d_cur, d_order);
         e = cudaStreamSynchronize(st);
     }
+    PanelSet P;
+    P.npan = n_panels;
+    P.q = q;
+    P.xb = xb;
+    P.yb = yb;
+    P.cx = cx;
+    P.cy = cy;
+    P.cs = cs;
+    P.sref = sigma;
+    P.cxf = cxf;
+    P.cyf = cyf;
+    P.xbf = xbf;
+    P.ybf = ybf;
+    P.xmf = xmf;
+    P.ymf = ymf;
+    P.tq = d_tq;
+    P.ptr = d_ptr;
+    P.list = d_list;
     if (e == cudaSuccess && n_near > 0) {
-        k_slp_local<<<(n_near + 127) / 128, 128, 0, st>>>(
-            n_near, d_order, d_tcell, xt, yt, n_panels, q, xb, yb, cx, cy, cs, sigma, cxf, cyf,
-            xbf, ybf, xmf, ymf, d_tq, d_ptr, d_list, alpha, delta_star, rl, u);
+        const int nb2 = (n_near + 127) / 128;
+        if (vol)
+            k_vp_local<<<nb2, 128, 0, st>>>(n_near, d_order, d_tcell, xt, yt, n_trg, fd, P, alpha,
+                                            delta_star, rl, u, d_nout);
+        else
+            k_slp_local<<<nb2, 128, 0, st>>>(n_near, d_order, d_tcell, xt, yt, P, alpha,
+                                             delta_star, rl, u);
         e = cudaGetLastError();
     }
+    int n_out = 0;
+    if (e == cudaSuccess && vol)
+        e = cudaMemcpyAsync(&n_out, d_nout, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cleanup();
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return lfail(YK_ERR_CUDA, "yk_slp_local: a CUDA call failed");
+        return fail(YK_ERR_CUDA, "a CUDA call failed");
+    }
+    if (n_out > 0) {
+        std::snprintf(msg, sizeof msg, "%s: %d targets within the locality radius lie outside the "
+                      "domain (u = NaN there)", name, n_out);
+        return lfail(YK_ERR_ARG, msg);
     }
     return YK_OK;
+}
+
+} /* namespace */
+
+extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_t n_panels, int q,
+                                         const double *xb, const double *yb, const double *sigma,
+                                         int64_t n_trg, const double *xt, const double *yt,
+                                         double *u, void *stream)
+{
+    if (!sigma) return lfail(YK_ERR_ARG, "yk_slp_local: sigma is NULL");
+    return run_local("yk_slp_local", false, alpha, delta_star, n_panels, q, xb, yb, sigma, n_trg, xt, yt,
+                     nullptr, u, stream);
+}
+
+extern "C" YK_API yk_status yk_vp_local(double alpha, double delta_star, int64_t n_panels, int q,
+                                        const double *xb, const double *yb, int64_t n_trg,
+                                        const double *xt, const double *yt, const double *fd,
+                                        double *u, void *stream)
+{
+    if (n_trg > 0 && !fd) return lfail(YK_ERR_ARG, "yk_vp_local: fd is NULL");
+    return run_local("yk_vp_local", true, alpha, delta_star, n_panels, q, xb, yb, nullptr, n_trg,
+                     xt, yt, fd, u, stream);
 }

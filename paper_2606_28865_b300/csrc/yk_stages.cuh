@@ -79,6 +79,20 @@ constexpr int kSpreadWarps = 8;               /* warps per CTA of the FP32C spre
 constexpr int kSpreadBatch = 16;              /* entries a warp of the double-float spread takes
                                                  at a time (two lanes each) */
 
+/* Layout of a warp's private spread tile (8-byte cells): cell (y, x) of the T x T tile sits at
+ * y * PT + (x & ~15) + ((x + y * S) & 15) with PT = T rounded up to 16 and S = W mod 16 (a
+ * rotation of each 16-cell group of a row by y S).  Tap t = c W + a of a window at (x0, y0) then
+ * lands in 8-byte bank slot (x0 + y0 S + t) mod 16, so any 16 consecutive taps (a half-warp of
+ * 64-bit accesses) hit 16 distinct slots: no bank conflicts, where a pitch of T + 1 put the rows a
+ * warp covers on top of each other.  A 16-cell row after the tile takes the taps that fall
+ * outside it, each in its own slot. */
+__host__ __device__ constexpr int spread_pitch(int T) { return (T + 15) & ~15; }
+__host__ __device__ constexpr int spread_tile_cells(int T) { return T * spread_pitch(T) + 16; }
+__device__ __forceinline__ int spread_cell(int y, int x, int PT, int S)
+{
+    return y * PT + (x & ~15) + ((x + y * S) & 15);
+}
+
 __device__ __forceinline__ double block_max(double v, double *red)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -284,10 +298,11 @@ template <int W> __device__ void st_spread64(const Inst &d, int item, unsigned c
 template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned char *sm)
 {
     const Geom &g = d.g;
-    const int T = g.T, PT = T + 1; /* padded pitch (float2 units) */
+    constexpr int S = W & 15;
+    const int T = g.T, PT = spread_pitch(T), TS = spread_tile_cells(T);
     const int SW = d.dip ? 4 * W : 2 * W; /* window values kept per entry */
-    float2 *acc = reinterpret_cast<float2 *>(sm);                          /* [warps][T][PT] */
-    float *wbuf = reinterpret_cast<float *>(acc + kSpreadWarps * T * PT);  /* [warps][32][SW] */
+    float2 *acc = reinterpret_cast<float2 *>(sm);                          /* [warps][TS] */
+    float *wbuf = reinterpret_cast<float *>(acc + kSpreadWarps * TS);      /* [warps][32][SW] */
     int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * SW);    /* [warps][32][2] */
     float *cw32 = reinterpret_cast<float *>(obuf + kSpreadWarps * 64);     /* dipole windows */
     const int tile = d.order ? d.order[item] : item;
@@ -303,11 +318,11 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
     }
     if (d.dip)
         for (int i = threadIdx.x; i < window_coeffs(d); i += blockDim.x) cw32[i] = d.win32[i];
-    for (int i = threadIdx.x; i < kSpreadWarps * T * PT; i += blockDim.x)
+    for (int i = threadIdx.x; i < kSpreadWarps * TS; i += blockDim.x)
         acc[i] = make_float2(0.0f, 0.0f);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *mine = acc + warp * T * PT;
+    float2 *mine = acc + warp * TS;
     float *wb = wbuf + warp * 32 * SW;
     int *ob = obuf + warp * 64;
     const float beta = (float)g.beta, cw = (float)g.c;
@@ -374,7 +389,7 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
                     int xx = dx0 + a;
                     if (xx >= g.n) xx -= g.n;
                     if (yy < T && xx < T) {
-                        idx[i] = yy * PT + xx;
+                        idx[i] = spread_cell(yy, xx, PT, S);
                         v[i] = wk[c] * wk[W + a];
                         if (dipk) v[i] = fmaf(wk[2 * W + c], wk[3 * W + a], v[i]);
                     }
@@ -401,7 +416,7 @@ template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned c
         const int rr = i / T, cc = i - rr * T;
         float hi = 0.0f, lo = 0.0f;
         for (int w = 0; w < kSpreadWarps; ++w) {
-            const float2 p = acc[w * T * PT + rr * PT + cc];
+            const float2 p = acc[w * TS + spread_cell(rr, cc, PT, S)];
             const float s = __fadd_rn(hi, p.x);
             const float bp = __fsub_rn(s, hi);
             lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)),
@@ -427,11 +442,12 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
     constexpr int EB = kSpreadBatch;
     constexpr int NI = (W * W + 31) / 32; /* taps per lane per entry */
     const Geom &g = d.g;
-    const int T = g.T, PT = T + 1;
+    constexpr int S = W & 15;
+    const int T = g.T, PT = spread_pitch(T), TS = spread_tile_cells(T);
     const int NW = blockDim.x >> 5;
     const int SW = d.dip ? 4 * W : 2 * W; /* window values kept per entry */
-    df32 *acc = reinterpret_cast<df32 *>(sm);                        /* [warps][T][PT] */
-    df32 *wbuf = acc + kSpreadWarps * T * PT;                        /* [warps][EB][SW] */
+    df32 *acc = reinterpret_cast<df32 *>(sm);                        /* [warps][TS] */
+    df32 *wbuf = acc + kSpreadWarps * TS;                            /* [warps][EB][SW] */
     int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * EB * SW); /* [warps][EB][2] */
     const int tile = d.order ? d.order[item] : item;
     const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
@@ -443,16 +459,16 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
             grid[(size_t)(Y0 + i / T) * g.n + X0 + i % T] = df32(0.0f, 0.0f);
         return;
     }
-    for (int i = threadIdx.x; i < NW * T * PT; i += blockDim.x) acc[i] = df32(0.0f, 0.0f);
+    for (int i = threadIdx.x; i < NW * TS; i += blockDim.x) acc[i] = df32(0.0f, 0.0f);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = lane & (EB - 1), half = lane / EB;
-    df32 *mine = acc + warp * T * PT;
+    df32 *mine = acc + warp * TS;
     df32 *wb = wbuf + warp * EB * SW;
     int *ob = obuf + warp * 2 * EB;
     /* this lane's taps (c, a) = (t / W, t % W) for t = i * 32 + lane; lanes past the last tap
-     * (tv false) take tap (0, 0) and, like taps outside the tile, add into the padding cell T of
-     * row 0 (never read), so the walk has no divergent branch */
+     * (tv false) take tap (0, 0) and, like taps outside the tile, add into the dummy row (never
+     * read), so the walk has no divergent branch */
     int tc[NI], ta[NI];
     bool tv[NI];
 #pragma unroll
@@ -517,11 +533,13 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
             const df32 *wk = wb + k * SW;
             int idx[NI];
             df32 cur[NI];
+            const int base = dx0 + dy0 * S; /* + t is the tap's bank slot (mod 16) */
 #pragma unroll
             for (int i = 0; i < NI; ++i) {
                 const int yy = dy0 + tc[i], xx = dx0 + ta[i];
                 const bool in = tv[i] && (unsigned)yy < (unsigned)T && (unsigned)xx < (unsigned)T;
-                idx[i] = in ? yy * PT + xx : T;
+                const int sl = (base + i * 32 + lane) & 15;
+                idx[i] = in ? yy * PT + (xx & ~15) + sl : T * PT + sl;
             }
 #pragma unroll
             for (int i = 0; i < NI; ++i) cur[i] = mine[idx[i]];
@@ -539,8 +557,9 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
     __syncthreads();
     for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
         const int rr = i / T, cc = i - rr * T;
-        df32 sum = acc[rr * PT + cc];
-        for (int w = 1; w < NW; ++w) sum = sum + acc[w * T * PT + rr * PT + cc];
+        const int ci = spread_cell(rr, cc, PT, S);
+        df32 sum = acc[ci];
+        for (int w = 1; w < NW; ++w) sum = sum + acc[w * TS + ci];
         grid[(size_t)(Y0 + rr) * g.n + X0 + cc] = sum;
     }
     __syncthreads();

@@ -105,3 +105,102 @@ def test_slp_local_arguments():
     assert ei.value.status == yk.YK_ERR_ARG
     with pytest.raises(ValueError):
         yk.slp_local(1.0, 1e-4, x, x, x, dev(np.zeros(3)), dev(np.zeros(3)), q=5)
+
+
+# ------------------------------------------------------------------------------------------------
+# volume local part V_L (Lemma for V_L, eq. vp_local1; eq. vp_local3 away from the boundary)
+
+def inside_targets(n, rl, seed):
+    """near targets moved inward by up to 0.95 r_loc (a tenth on the boundary) and interior
+    targets (polar radius < 0.5, the starfish radius is >= 0.7)"""
+    g = OL.StarfishGeom()
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(0, 2 * np.pi, n)
+    p, d1, _ = g.derivs(t)
+    nrm = np.hypot(d1[0], d1[1])
+    off = rng.uniform(0, 0.95 * rl, n)
+    off[: n // 10] = 0.0
+    xn, yn = p[0] - off * d1[1] / nrm, p[1] + off * d1[0] / nrm      # inward normal
+    rad, th = 0.5 * np.sqrt(rng.uniform(0, 1, n // 3)), rng.uniform(0, 2 * np.pi, n // 3)
+    return np.r_[xn, rad * np.cos(th)], np.r_[yn, rad * np.sin(th)]
+
+
+def run_vp(n_panels, alpha, dstar, xt, yt, fd=None):
+    yk = _yk()
+    xb, yb, _, _ = W.boundary_nodes(W.Starfish(), n_panels, 16)
+    fd = fd or OL.sincos_field()
+    planes = np.stack(fd(xt, yt))
+    u = yk.vp_local(alpha, dstar, dev(xb), dev(yb), dev(xt), dev(yt), dev(planes), q=16)
+    torch.cuda.synchronize()
+    return u.cpu().numpy()
+
+
+@pytest.mark.parametrize("n_panels,alpha,dstar", [(32, 10.0, 1e-4), (32, 1.0, 1e-5),
+                                                  (32, 0.1, 1e-5), (32, 100.0, 1e-5),
+                                                  (128, 10.0, 1e-5)])
+def test_vp_local_matches_oracle(n_panels, alpha, dstar):
+    rl = OL.locality_radius(alpha, dstar)
+    xt, yt = inside_targets(3000, min(rl, 0.03), seed=6)
+    u = run_vp(n_panels, alpha, dstar, xt, yt)
+    ref = OL.vp_local_starfish(alpha, dstar, OL.StarfishGeom(), OL.sincos_field(), xt, yt)
+    assert np.all(np.isfinite(ref))
+    err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+    assert err <= TOL, f"err={err:.3e}"
+
+
+def test_vp_local_interior_is_the_semigroup_expansion():
+    # away from the boundary every target takes eq. vp_local3, here against the oracle's form
+    alpha, dstar = 10.0, 1e-5
+    rng = np.random.default_rng(2)
+    rad, th = 0.5 * np.sqrt(rng.uniform(0, 1, 1000)), rng.uniform(0, 2 * np.pi, 1000)
+    xt, yt = rad * np.cos(th), rad * np.sin(th)
+    u = run_vp(32, alpha, dstar, xt, yt)
+    f, _, _, fxx, _, fyy = OL.sincos_field()(xt, yt)
+    ref = OL.vl_interior(alpha, dstar, f, fxx + fyy)
+    assert np.max(np.abs(u - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_vp_local_outside_targets_are_reported():
+    yk = _yk()
+    alpha, dstar = 10.0, 1e-5
+    rl = OL.locality_radius(alpha, dstar)
+    g = OL.StarfishGeom()
+    t = np.array([0.4, 2.2, 4.0])
+    p, d1, _ = g.derivs(t)
+    nrm = np.hypot(d1[0], d1[1])
+    xo, yo = p[0] + 0.5 * rl * d1[1] / nrm, p[1] - 0.5 * rl * d1[0] / nrm   # outward
+    xt, yt = np.r_[0.1, xo, 0.0], np.r_[0.2, yo, -0.3]
+    xb, yb, _, _ = W.boundary_nodes(W.Starfish(), 32, 16)
+    planes = np.stack(OL.sincos_field()(xt, yt))
+    out = dev(np.zeros(len(xt)))
+    with pytest.raises(yk.YkError) as ei:
+        yk.vp_local(alpha, dstar, dev(xb), dev(yb), dev(xt), dev(yt), dev(planes), q=16, out=out)
+    assert ei.value.status == yk.YK_ERR_ARG
+    u = out.cpu().numpy()
+    assert np.all(np.isnan(u[1:4])) and np.isfinite(u[0]) and np.isfinite(u[4])
+
+
+@pytest.mark.slow
+def test_vp_local_config_two_boundary():
+    alpha = 10.0
+    import oracle.params as OP
+    dstar = OP.delta_from_mesh(alpha, 0.004467)
+    rl = OL.locality_radius(alpha, dstar)
+    xt, yt = inside_targets(20000, rl, seed=10)
+    u = run_vp(6250, alpha, dstar, xt, yt)
+    ref = OL.vp_local_starfish(alpha, dstar, OL.StarfishGeom(), OL.sincos_field(), xt, yt)
+    assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) <= TOL_SHORT_PANELS
+
+
+def test_vp_local_arguments():
+    yk = _yk()
+    x = dev(np.zeros(32))
+    t3 = dev(np.zeros(3))
+    with pytest.raises(yk.YkError) as ei:
+        yk.vp_local(0.0, 1e-4, x, x, t3, t3, dev(np.zeros(18)), q=16)
+    assert ei.value.status == yk.YK_ERR_ARG
+    with pytest.raises(ValueError):
+        yk.vp_local(1.0, 1e-4, x, x, t3, t3, dev(np.zeros(12)), q=16)
+    # no targets: nothing to do
+    e = dev(np.zeros(0))
+    assert yk.vp_local(1.0, 1e-4, x, x, e, e, dev(np.zeros(0)), q=16).numel() == 0

@@ -159,3 +159,20 @@ def test_starfish_targets_inside_and_outside():
     yout = p[1] - 0.002 * d1[0] / nrm
     u = OL.vp_local_starfish(10.0, ds, g, fd, np.r_[0.0, xin, xout], np.r_[0.0, yin, yout])
     assert np.all(np.isfinite(u[:3])) and np.all(np.isnan(u[3:]))
+
+
+def test_high_precision_lemma_agrees_with_fp64_where_conditioned():
+    # where c2 is not small the FP64 and the 40-digit evaluations of the printed lemma agree; at
+    # c2 = 3e-3 the FP64 form is off by ~1e-16 / c2^2 relative
+    rng = np.random.default_rng(1)
+    for alpha, ds in [(10.0, 1e-4), (100.0, 1e-5), (30.0, 1e-3)]:
+        sd = math.sqrt(ds)
+        r = rng.uniform(0, 10 * sd, 20)
+        args = (r, 0.8, 1.1, -0.3, 0.7, 2.0)
+        a = OL.vl_lemma_terms(alpha, ds, *args)
+        b = OL.vl_lemma_terms_mp(alpha, ds, *args)
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+    ds = 1e-5
+    ex = halfplane_exact(1.0, ds, 0.3 * math.sqrt(ds), 1.3, 0.7, -0.4, 2.1, 0.9, -1.6)
+    v = OL.vl_lemma_terms_mp(1.0, ds, 0.3 * math.sqrt(ds), 0.0, 1.3, 0.7, -1.6, 2.1)
+    assert abs(v - ex) <= 1e-14 * abs(ex)

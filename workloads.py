@@ -252,6 +252,21 @@ def manufactured_source(x, y, alpha):
     return (13.0 + alpha * alpha) * np.sin(2.0 * x) * np.cos(3.0 * y)
 
 
+def manufactured_source_derivs(x, y, alpha):
+    """The six planes f, f_x, f_y, f_xx, f_xy, f_yy of manufactured_source (input data for the
+    volume local part at the volume nodes)."""
+    c = 13.0 + alpha * alpha
+    s2, c2 = np.sin(2.0 * x), np.cos(2.0 * x)
+    s3, c3 = np.sin(3.0 * y), np.cos(3.0 * y)
+    return np.stack([c * s2 * c3, 2 * c * c2 * c3, -3 * c * s2 * s3, -4 * c * s2 * c3,
+                     -6 * c * c2 * s3, -9 * c * s2 * c3])
+
+
+def inside_starfish(curve, x, y):
+    """Points strictly inside the star-shaped curve (polar test |x| < r(theta))."""
+    return np.hypot(x, y) < curve.radius(np.arctan2(y, x))
+
+
 def config_small(alpha=10.0, seed=0, n_panels=32, n_vol=2048, n_trg=2048):
     """512 boundary nodes (32 panels x 16 GL) on r = 1 + 0.3 cos 5t, ~2048 volume nodes with
     f = exp(-|x|^2/0.1), 2048 uniform targets in [-1.5, 1.5]^2."""
