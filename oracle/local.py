@@ -243,3 +243,63 @@ def sincos_field(kx=2.0, ky=3.0):
         return (s * cy, kx * c * cy, -ky * s * sy, -kx * kx * s * cy, -kx * ky * c * sy,
                 -ky * ky * s * cy)
     return fd
+
+
+# ------------------------------------------------------------------------------------------------
+# Dyadic corrections of the single-layer local part (Section 2.1, eqs. slp_dyad, sld; difference
+# kernel eq. diffker_s through the identity eq. equiv_split): with delta_j = delta / 4^j,
+#   S_{L,D}^{(j)}[sigma](x) = int_boundary K_j(|x - x'|) sigma(x') ds,
+#   K_j(r) = int_{delta_j}^{delta_{j-1}} e^{-r^2/4t - alpha^2 t} / (4 pi t) dt
+#          = G^R(r, delta_{j-1}) - G^R(r, delta_j).
+# The oracle takes K_j from its t-integral (composite Gauss-Legendre in log t), not from
+# incomplete Bessel functions.
+# ------------------------------------------------------------------------------------------------
+
+_GL32 = np.polynomial.legendre.leggauss(32)
+
+
+def dyadic_kernel(alpha, delta, j, r):
+    """K_j(r) by 4 panels x 32 Gauss-Legendre nodes in u = log t over [log delta_j,
+    log delta_{j-1}] (the integrand is smooth in u)."""
+    r = np.asarray(r, dtype=float)
+    lo, hi = math.log(delta / 4.0 ** j), math.log(delta / 4.0 ** (j - 1))
+    x, w = _GL32
+    acc = np.zeros_like(r)
+    npan = 4
+    for p in range(npan):
+        a = lo + (hi - lo) * p / npan
+        b = lo + (hi - lo) * (p + 1) / npan
+        u = 0.5 * (b - a) * x + 0.5 * (a + b)
+        t = np.exp(u)
+        ww = 0.5 * (b - a) * w
+        acc = acc + np.sum(ww * np.exp(-(r[..., None] ** 2) / (4 * t) - alpha * alpha * t), axis=-1)
+    return acc / (4 * math.pi)
+
+
+def slp_dyadic_starfish(alpha, delta, J, geom: StarfishGeom, sigma, xt, yt, n_scan=8192):
+    """sum_{j=1}^J S_{L,D}^{(j)}[sigma] at the targets, on the analytic curve: composite
+    16-point Gauss-Legendre over the scan intervals of the curve parameter that come within the
+    level-1 locality radius sqrt(delta)(12 + 2 alpha sqrt(delta)) of the target (beyond it every
+    K_j is below 1e-16 of its peak)."""
+    xt, yt = np.atleast_1d(xt).astype(float), np.atleast_1d(yt).astype(float)
+    R = locality_radius(alpha, delta)
+    ts = np.linspace(0.0, 2 * math.pi, n_scan + 1)
+    g, g1, _ = geom.derivs(ts)
+    seg = np.hypot(np.diff(g[0]), np.diff(g[1]))        # chord of each scan interval
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    out = np.zeros(len(xt))
+    for i in range(len(xt)):
+        d = np.hypot(g[0] - xt[i], g[1] - yt[i])
+        near = np.nonzero(np.minimum(d[:-1], d[1:]) < R + seg)[0]
+        if len(near) == 0:
+            continue
+        a, b = ts[near], ts[near + 1]
+        t = (0.5 * (b - a))[:, None] * xg[None, :] + (0.5 * (a + b))[:, None]
+        w = (0.5 * (b - a))[:, None] * wg[None, :]
+        p, p1, _ = geom.derivs(t)
+        s0, _, _ = sigma(t)
+        r = np.hypot(p[0] - xt[i], p[1] - yt[i])
+        q = s0 * np.hypot(p1[0], p1[1]) * w
+        for j in range(1, J + 1):
+            out[i] += np.sum(q * dyadic_kernel(alpha, delta, j, r))
+    return out
