@@ -177,6 +177,10 @@ def load_peaks():
     return 6400.0, "fallback"
 
 
+# the sources that define the stage kernels whose DRAM bytes profiles/ncu_traffic.json records
+TRAFFIC_SOURCES = ("yk_core.h", "yk_internal.h", "yk_kernels.cu", "yk_stages.cuh")
+
+
 def load_traffic():
     """ncu DRAM bytes per launch per stage recorded under profiles/, valid for the current source."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -186,7 +190,7 @@ def load_traffic():
     with open(path) as f:
         d = json.load(f)
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_2606_28865_b300", "csrc"))):
+    for fn in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_2606_28865_b300", "csrc", fn), "rb") as fh:
             h.update(fh.read())
     if d.get("csrc_sha256") != h.hexdigest():
@@ -676,6 +680,26 @@ def main():
                   "what": "yk_vp_local at the volume nodes: interior form everywhere, closest point "
                           "+ lemma within the locality radius"}
 
+    # dyadic corrections of the single-layer local part (J = 3 levels below the plan's delta) at
+    # the same 1e6 targets and boundary
+    dyadic = None
+    if not args.no_local:
+        J = 3
+        ud = torch.empty_like(xt_l)
+        for _ in range(2):
+            yk.slp_dyadic(a_loc, dstar, J, *lb, xt_l, yt_l, q=16, out=ud, stream=lanes[a_loc])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            yk.slp_dyadic(a_loc, dstar, J, *lb, xt_l, yt_l, q=16, out=ud, stream=lanes[a_loc])
+        ms_d = (time.perf_counter() - t0) / reps * 1e3
+        dyadic = {"value": (len(xb) + xt_l.numel()) / (ms_d * 1e-3), "unit": "points/s",
+                  "ms": ms_d, "alpha": a_loc, "delta": dstar, "levels": J,
+                  "n_boundary": len(xb), "n_targets": int(xt_l.numel()),
+                  "targets_reached": int((ud != 0).sum().item()),
+                  "what": "yk_slp_dyadic: per level resampled panel nodes binned in cells, "
+                          "difference kernel from a table, summed over nodes within R_j"}
+
     batch = None if args.no_batch else batch_section(yk, torch, rank)
     serving = None if args.no_serving else serving_section(yk, args.serve_requests)
 
@@ -717,6 +741,7 @@ def main():
         "double_layer": dlp,
         "slp_local": local,
         "vp_local": vlocal,
+        "slp_dyadic": dyadic,
         "batch": batch,
         "serving": serving,
     }

@@ -215,6 +215,26 @@ YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_t n_panels,
                               void *stream);
 
 /*
+ * yk_slp_dyadic: the dyadic corrections of the single-layer local part (Section 2.1, eqs. slp_dyad
+ * and sld): u_i = sum_{j=1}^{J} S_{L,D}^{(j)}[sigma](x_i), S_{L,D}^{(j)} = int_boundary
+ * K_j(|x_i - x'|) sigma(x') ds with the difference kernel K_j(r) = int_{delta/4^j}^{delta/4^(j-1)}
+ * e^{-r^2/4t - alpha^2 t} / (4 pi t) dt (eq. diffker_s through eq. equiv_split).  With
+ * yk_slp_local at delta_star = delta / 4^J and the history part at delta this gives the single
+ * layer potential S = S_{L,A} + sum_j S_{L,D}^{(j)} + S_H.
+ *  - alpha > 0, delta > 0, 1 <= J <= 10; panels, sigma, targets and u as for yk_slp_local.
+ *  - Level j resamples every panel on m_j sub-panels of the same q-point rule (no longer than
+ *    3 sqrt(delta_j), from the panel's polynomial: the paper's bisection by interpolation) and
+ *    sums over the nodes within R_j = sqrt(delta_{j-1})(12 + 2 alpha sqrt(delta_{j-1})), K_j from
+ *    a piecewise polynomial table accurate to ~1e-16 of its peak.
+ *  - Device memory only; YK_ERR_OOM if a level's scratch cannot be allocated; other errors as
+ *    yk_slp_local.
+ */
+YK_API yk_status yk_slp_dyadic(double alpha, double delta, int J, int64_t n_panels, int q,
+                               const double *xb, const double *yb, const double *sigma,
+                               int64_t n_trg, const double *xt, const double *yt, double *u,
+                               void *stream);
+
+/*
  * yk_vp_local: the volume local part V_L[f](x_i) = int_0^{delta_star} int_Omega H_t(x_i - x') f(x')
  * dx' dt (Section 2.1, eq. vl) by the expansion of the Lemma for V_L (Section 4.1, eq. vp_local1)
  * through its delta_star^2 term at targets within the locality radius of the boundary (closest

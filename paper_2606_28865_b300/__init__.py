@@ -377,6 +377,30 @@ def slp_local(alpha, delta_star, xb, yb, sigma, xt, yt, q=16, out=None, stream=N
     return out
 
 
+_lib.yk_slp_dyadic.argtypes = [_d, _d, ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp, _i64,
+                               _vp, _vp, _vp, _vp]
+_lib.yk_slp_dyadic.restype = ctypes.c_int
+
+
+def slp_dyadic(alpha, delta, J, xb, yb, sigma, xt, yt, q=16, out=None, stream=None):
+    """Sum of the J dyadic corrections of the single-layer local part at the targets (device
+    float64 tensors; see yk_slp_dyadic)."""
+    torch = _torch()
+    nb, nt = _len(xb), _len(xt)
+    if nb % q or _len(yb) != nb or _len(sigma) != nb or _len(yt) != nt:
+        raise ValueError("boundary arrays must hold n_panels * q values; target lengths differ")
+    if out is None:
+        out = torch.empty(nt, dtype=torch.float64, device=xt.device)
+    if stream is None:
+        stream = _current_stream()
+    keep = []
+    _check(_lib.yk_slp_dyadic(float(alpha), float(delta), int(J), nb // q, int(q),
+                              _ptr(xb, keep), _ptr(yb, keep), _ptr(sigma, keep), nt,
+                              _ptr(xt, keep), _ptr(yt, keep), _ptr(out, keep), stream),
+           "yk_slp_dyadic")
+    return out
+
+
 _lib.yk_vp_local.argtypes = [_d, _d, _i64, ctypes.c_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                              _vp]
 _lib.yk_vp_local.restype = ctypes.c_int

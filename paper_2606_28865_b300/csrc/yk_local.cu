@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -522,6 +523,181 @@ __global__ void __launch_bounds__(128) k_vp_local(int n_near, const int *__restr
     u[i] = vl_lemma_terms(alpha, dstar, r, kappa0, f, f_eta, f_etaeta, f_xixi);
 }
 
+/* ----------------------------------------------------------------------------------------- */
+/* dyadic corrections S_{L,D}^{(j)} (eqs. slp_dyad, sld): per level j the panels are resampled on
+ * m_j sub-panels of the same Gauss-Legendre rule (from the panel's Legendre series, i.e. the
+ * interpolation of the paper's bisection), the nodes binned in cells of edge R_j, and every near
+ * target sums K_j(|x - x'|) sigma ds over the nodes within R_j, K_j from a table */
+
+constexpr int kDyDeg = 12; /* degree of the table's pieces (width 1 in rho = r^2 / (4 delta_j)) */
+
+struct DyLevel {
+    double inv4d;      /* 1 / (4 delta_j) */
+    double R2;         /* R_j^2: K_j is below 1e-16 of its peak beyond R_j */
+    int npc;           /* table pieces */
+    const double *tab; /* npc x (kDyDeg + 1) monomial coefficients in z = 2 (rho - k) - 1 */
+    LocalGrid G;       /* cells of edge >= R_j */
+    const int *ptr;    /* nodes per cell */
+    const double *X, *Y, *Q; /* nodes sorted by cell; Q = sigma |gamma'| w */
+};
+
+/* node (p, s, k): parameter -1 + (2 s + 1 + t_k) / m of panel p */
+__global__ void k_dy_nodes(int64_t npan, int q, int m, PanelSet P, const double *__restrict__ wq,
+                           double *__restrict__ X, double *__restrict__ Y, double *__restrict__ Q)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)m * q;
+    if (i >= npan * per) return;
+    const int64_t p = i / per;
+    const int rem = (int)(i - p * per), sb = rem / q, k = rem - sb * q;
+    const double t = -1.0 + (2.0 * sb + 1.0 + P.tq[k]) / m;
+    const double *const c3[3] = {P.cx + p * q, P.cy + p * q, P.cs + p * q};
+    double g[3], g1[3], g2[3];
+    legendre_eval<double, 3>(c3, q, t, g, g1, g2, c_la, c_lb);
+    const int h = q / 2;
+    X[i] = P.xb[p * q + h] + g[0];
+    Y[i] = P.yb[p * q + h] + g[1];
+    Q[i] = (P.sref[p * q + h] + g[2]) * sqrt(g1[0] * g1[0] + g1[1] * g1[1]) * wq[k] / m;
+}
+
+__device__ __forceinline__ int pt_cell(double x, double y, const LocalGrid &G)
+{
+    int ci = (int)floor((x - G.x0) / G.h), cj = (int)floor((y - G.y0) / G.h);
+    ci = min(max(ci, 0), G.nx - 1);
+    cj = min(max(cj, 0), G.ny - 1);
+    return cj * G.nx + ci;
+}
+
+__global__ void k_pt_count(int64_t n, const double *__restrict__ X, const double *__restrict__ Y,
+                           LocalGrid G, int *__restrict__ cnt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[pt_cell(X[i], Y[i], G)], 1);
+}
+
+__global__ void k_pt_fill(int64_t n, const double *__restrict__ X, const double *__restrict__ Y,
+                          const double *__restrict__ Q, LocalGrid G, const int *__restrict__ ptr,
+                          int *__restrict__ cur, double *__restrict__ Xs, double *__restrict__ Ys,
+                          double *__restrict__ Qs)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = pt_cell(X[i], Y[i], G);
+    const int e = ptr[c] + atomicAdd(&cur[c], 1);
+    Xs[e] = X[i];
+    Ys[e] = Y[i];
+    Qs[e] = Q[i];
+}
+
+/* u_i += S_{L,D}^{(j)} at the near targets: one warp per target (the targets grouped by cell),
+ * the lanes striding over the nodes of the 3 x 3 cells around it (sorted by cell, so the loads are
+ * contiguous), partial sums combined by shuffles in a fixed order */
+__global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__restrict__ order,
+                                                      const double *__restrict__ xt,
+                                                      const double *__restrict__ yt, DyLevel L,
+                                                      double *__restrict__ u)
+{
+    const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= n_near) return; /* whole warps leave together */
+    const int i = order[w];
+    const double x = xt[i], y = yt[i];
+    const LocalGrid &G = L.G;
+    const double fx = floor((x - G.x0) / G.h), fy = floor((y - G.y0) / G.h);
+    if (!(fx >= -1.0 && fx <= G.nx && fy >= -1.0 && fy <= G.ny)) return; /* no node within R_j */
+    const int ci = (int)fx, cj = (int)fy;
+    double acc = 0.0;
+    for (int dj = -1; dj <= 1; ++dj) {
+        const int cy = cj + dj;
+        if (cy < 0 || cy >= G.ny) continue;
+        /* the three cells of a row are contiguous in the sorted order */
+        const int c0 = cy * G.nx + max(ci - 1, 0), c1 = cy * G.nx + min(ci + 1, G.nx - 1);
+        if (ci + 1 < 0 || ci - 1 >= G.nx) continue;
+        for (int e = L.ptr[c0] + lane; e < L.ptr[c1 + 1]; e += 32) {
+            const double dx = L.X[e] - x, dy = L.Y[e] - y;
+            const double r2 = dx * dx + dy * dy;
+            if (r2 < L.R2) {
+                const double rho = r2 * L.inv4d;
+                const int k = min((int)rho, L.npc - 1);
+                const double z = 2.0 * (rho - k) - 1.0;
+                const double *a = L.tab + k * (kDyDeg + 1);
+                double f = a[kDyDeg];
+#pragma unroll
+                for (int n = kDyDeg - 1; n >= 0; --n) f = fma(f, z, a[n]);
+                acc = fma(L.Q[e], f, acc);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) u[i] += acc;
+}
+
+/* K_j on the pieces [k, k + 1] of rho = r^2 / (4 delta_j):
+ * K_j = (1/4 pi) int_0^{ln 4} exp(-rho e^{-u} - alpha^2 delta_j e^u) du (t = delta_j e^u), by
+ * 3 x 48 Gauss-Legendre nodes in u; each piece interpolated at its 13 Chebyshev points and
+ * written as a polynomial in z = 2 (rho - k) - 1 */
+void dyadic_table_build(double c, int npc, std::vector<double> &tab)
+{
+    constexpr int NG = 48, NP = 3, D = kDyDeg;
+    static const struct Rule {
+        double x[NG], w[NG];
+        Rule() { yk_gauss_legendre(NG, x, w); }
+    } rule; /* initialised once, thread-safely */
+    const double *gx = rule.x, *gw = rule.w;
+    const double L4 = std::log(4.0);
+    auto K = [&](double rho) {
+        double acc = 0.0;
+        for (int p = 0; p < NP; ++p) {
+            const double a = L4 * p / NP, b = L4 * (p + 1) / NP;
+            for (int n = 0; n < NG; ++n) {
+                const double uu = 0.5 * (b - a) * gx[n] + 0.5 * (a + b);
+                acc += 0.5 * (b - a) * gw[n] * std::exp(-rho * std::exp(-uu) - c * std::exp(uu));
+            }
+        }
+        return acc / (4.0 * M_PI);
+    };
+    /* Chebyshev T_n as monomials in z */
+    double T[D + 1][D + 1] = {};
+    T[0][0] = 1.0;
+    T[1][1] = 1.0;
+    for (int n = 2; n <= D; ++n)
+        for (int k = 0; k <= n; ++k)
+            T[n][k] = (k > 0 ? 2.0 * T[n - 1][k - 1] : 0.0) - T[n - 2][k];
+    tab.assign((size_t)npc * (D + 1), 0.0);
+    double f[D + 1], zc[D + 1];
+    for (int i = 0; i <= D; ++i) zc[i] = std::cos(M_PI * (i + 0.5) / (D + 1));
+    for (int k = 0; k < npc; ++k) {
+        for (int i = 0; i <= D; ++i) f[i] = K(k + 0.5 * (zc[i] + 1.0));
+        for (int n = 0; n <= D; ++n) {
+            double an = 0.0;
+            for (int i = 0; i <= D; ++i) an += f[i] * std::cos(n * M_PI * (i + 0.5) / (D + 1));
+            an *= 2.0 / (D + 1);
+            if (n == 0) an *= 0.5;
+            for (int m = 0; m <= n; ++m) tab[(size_t)k * (D + 1) + m] += an * T[n][m];
+        }
+    }
+}
+
+/* tables are reused across calls with the same (alpha^2 delta_j, pieces) (a Rothe march or a
+ * bench repeats them); a small mutex-guarded cache, oldest entry dropped beyond 32 */
+void dyadic_table(double c, int npc, std::vector<double> &tab)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<double, int>, std::vector<double>>> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (auto &kv : cache)
+            if (kv.first.first == c && kv.first.second == npc) {
+                tab = kv.second;
+                return;
+            }
+    }
+    dyadic_table_build(c, npc, tab);
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() >= 32) cache.erase(cache.begin());
+    cache.push_back({{c, npc}, tab});
+}
+
 bool is_dev(const void *p)
 {
     if (!p) return false;
@@ -541,7 +717,7 @@ yk_status lfail(yk_status s, const char *msg)
 
 /* S_{L,A} (vol false: sigma) or V_L (vol true: fd): shared set-up (extent, panel
  * series, cell lists, near targets grouped by cell), then the part's kernels */
-yk_status run_local(const char *name, bool vol, double alpha, double delta_star, int64_t n_panels, int q,
+yk_status run_local(const char *name, bool vol, int J, double alpha, double delta_star, int64_t n_panels, int q,
                     const double *xb, const double *yb, const double *sigma, int64_t n_trg,
                     const double *xt, const double *yt, const double *fd, double *u, void *stream)
 {
@@ -743,10 +919,82 @@ yk_status run_local(const char *name, bool vol, double alpha, double delta_star,
         if (vol)
             k_vp_local<<<nb2, 128, 0, st>>>(n_near, d_order, d_tcell, xt, yt, n_trg, fd, P, alpha,
                                             delta_star, rl, u, d_nout);
-        else
+        else if (J == 0)
             k_slp_local<<<nb2, 128, 0, st>>>(n_near, d_order, d_tcell, xt, yt, P, alpha,
                                              delta_star, rl, u);
         e = cudaGetLastError();
+    }
+    /* dyadic levels: delta_star is delta here, so the set-up's near targets are those within the
+     * level-1 radius */
+    bool dy_oom = false;
+    for (int j = 1; j <= J && e == cudaSuccess && n_near > 0; ++j) {
+        const double dj = delta_star / std::pow(4.0, j), dj1 = 4.0 * dj;
+        const double R = std::sqrt(dj1) * (12.0 + 2.0 * alpha * std::sqrt(dj1));
+        const int npc = (int)std::ceil(R * R / (4.0 * dj)) + 1;
+        std::vector<double> tab;
+        dyadic_table(alpha * alpha * dj, npc, tab);
+        /* sub-panels no longer than 3 sqrt(delta_j) (chords at most 1.5 x shorter than arcs) */
+        const int m = std::max(1, (int)std::ceil(1.5 * hmax / (3.0 * std::sqrt(dj))));
+        const int64_t nn = n_panels * m * q;
+        if (nn > (1ll << 31) - 1) {
+            e = cudaErrorMemoryAllocation;
+            dy_oom = true;
+            break;
+        }
+        DyLevel L;
+        L.inv4d = 1.0 / (4.0 * dj);
+        L.R2 = R * R;
+        L.npc = npc;
+        L.G.h = R;
+        L.G.x0 = xmin - 2.0 * R;
+        L.G.y0 = ymin - 2.0 * R;
+        L.G.nx = (int)std::ceil((xmax + 2.0 * R - L.G.x0) / L.G.h) + 1;
+        L.G.ny = (int)std::ceil((ymax + 2.0 * R - L.G.y0) / L.G.h) + 1;
+        while ((int64_t)L.G.nx * L.G.ny > kMaxCells) {
+            L.G.h *= 2.0;
+            L.G.nx = (int)std::ceil((xmax + 2.0 * R - L.G.x0) / L.G.h) + 1;
+            L.G.ny = (int)std::ceil((ymax + 2.0 * R - L.G.y0) / L.G.h) + 1;
+        }
+        const int nc = L.G.nx * L.G.ny;
+        double *d_tab = nullptr, *d_nodes = nullptr, *d_wq = nullptr;
+        int *d_c = nullptr; /* cnt | ptr | cur */
+        e = cudaMallocAsync(&d_tab, sizeof(double) * tab.size(), st);
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_nodes, sizeof(double) * 6 * nn, st);
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_wq, sizeof(double) * q, st);
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_c, sizeof(int) * (3 * (size_t)nc + 1), st);
+        if (e != cudaSuccess) dy_oom = true;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_tab, tab.data(), sizeof(double) * tab.size(),
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_wq, wq.data(), sizeof(double) * q, cudaMemcpyHostToDevice, st);
+        int *cnt = d_c, *cptr = d_c + nc, *ccur = d_c + 2 * nc + 1;
+        double *X = d_nodes, *Y = d_nodes + nn, *Qn = d_nodes + 2 * nn;
+        double *Xs = d_nodes + 3 * nn, *Ys = d_nodes + 4 * nn, *Qs = d_nodes + 5 * nn;
+        const int gb = (int)((nn + 255) / 256);
+        if (e == cudaSuccess) {
+            k_dy_nodes<<<gb, 256, 0, st>>>(n_panels, q, m, P, d_wq, X, Y, Qn);
+            e = cudaMemsetAsync(cnt, 0, sizeof(int) * nc, st);
+        }
+        if (e == cudaSuccess) {
+            k_pt_count<<<gb, 256, 0, st>>>(nn, X, Y, L.G, cnt);
+            e = yk::launch_scan(cnt, cptr, nc, ccur, st);
+        }
+        /* the scan used the cursors as scratch: zero them for the fill */
+        if (e == cudaSuccess) e = cudaMemsetAsync(ccur, 0, sizeof(int) * nc, st);
+        if (e == cudaSuccess) {
+            k_pt_fill<<<gb, 256, 0, st>>>(nn, X, Y, Qn, L.G, cptr, ccur, Xs, Ys, Qs);
+            L.tab = d_tab;
+            L.ptr = cptr;
+            L.X = Xs;
+            L.Y = Ys;
+            L.Q = Qs;
+            k_dyadic_level<<<(int)(((int64_t)n_near * 32 + 255) / 256), 256, 0, st>>>(
+                n_near, d_order, xt, yt, L, u);
+            e = cudaGetLastError();
+        }
+        for (void *b : {(void *)d_tab, (void *)d_nodes, (void *)d_wq, (void *)d_c})
+            if (b) cudaFreeAsync(b, st);
     }
     int n_out = 0;
     if (e == cudaSuccess && vol)
@@ -755,7 +1003,8 @@ yk_status run_local(const char *name, bool vol, double alpha, double delta_star,
     cleanup();
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(YK_ERR_CUDA, "a CUDA call failed");
+        return dy_oom ? fail(YK_ERR_OOM, "dyadic level scratch allocation failed")
+                      : fail(YK_ERR_CUDA, "a CUDA call failed");
     }
     if (n_out > 0) {
         std::snprintf(msg, sizeof msg, "%s: %d targets within the locality radius lie outside the "
@@ -773,7 +1022,7 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
                                          double *u, void *stream)
 {
     if (!sigma) return lfail(YK_ERR_ARG, "yk_slp_local: sigma is NULL");
-    return run_local("yk_slp_local", false, alpha, delta_star, n_panels, q, xb, yb, sigma, n_trg, xt, yt,
+    return run_local("yk_slp_local", false, 0, alpha, delta_star, n_panels, q, xb, yb, sigma, n_trg, xt, yt,
                      nullptr, u, stream);
 }
 
@@ -783,6 +1032,17 @@ extern "C" YK_API yk_status yk_vp_local(double alpha, double delta_star, int64_t
                                         double *u, void *stream)
 {
     if (n_trg > 0 && !fd) return lfail(YK_ERR_ARG, "yk_vp_local: fd is NULL");
-    return run_local("yk_vp_local", true, alpha, delta_star, n_panels, q, xb, yb, nullptr, n_trg,
+    return run_local("yk_vp_local", true, 0, alpha, delta_star, n_panels, q, xb, yb, nullptr, n_trg,
                      xt, yt, fd, u, stream);
+}
+
+extern "C" YK_API yk_status yk_slp_dyadic(double alpha, double delta, int J, int64_t n_panels,
+                                          int q, const double *xb, const double *yb,
+                                          const double *sigma, int64_t n_trg, const double *xt,
+                                          const double *yt, double *u, void *stream)
+{
+    if (!sigma) return lfail(YK_ERR_ARG, "yk_slp_dyadic: sigma is NULL");
+    if (J < 1 || J > 10) return lfail(YK_ERR_ARG, "yk_slp_dyadic: need 1 <= J <= 10");
+    return run_local("yk_slp_dyadic", false, J, alpha, delta, n_panels, q, xb, yb, sigma, n_trg,
+                     xt, yt, nullptr, u, stream);
 }

@@ -204,3 +204,48 @@ def test_vp_local_arguments():
     # no targets: nothing to do
     e = dev(np.zeros(0))
     assert yk.vp_local(1.0, 1e-4, x, x, e, e, dev(np.zeros(0)), q=16).numel() == 0
+
+
+# ------------------------------------------------------------------------------------------------
+# dyadic corrections of the single-layer local part (eqs. slp_dyad, sld, diffker_s)
+
+def run_dy(n_panels, alpha, delta, J, xt, yt):
+    yk = _yk()
+    xb, yb, _, tb = W.boundary_nodes(W.Starfish(), n_panels, 16)
+    sig = W.boundary_density(tb)
+    u = yk.slp_dyadic(alpha, delta, J, dev(xb), dev(yb), dev(sig), dev(xt), dev(yt), q=16)
+    torch.cuda.synchronize()
+    return u.cpu().numpy()
+
+
+@pytest.mark.parametrize("n_panels,alpha,delta,J", [(32, 10.0, 1e-4, 3), (32, 1.0, 3e-5, 2),
+                                                    (128, 100.0, 1e-4, 3), (32, 10.0, 4e-4, 1)])
+def test_slp_dyadic_matches_oracle(n_panels, alpha, delta, J):
+    R1 = OL.locality_radius(alpha, delta)
+    xt, yt = near_targets(300, min(0.9 * R1, 0.05), seed=12)
+    u = run_dy(n_panels, alpha, delta, J, xt, yt)
+    ref = OL.slp_dyadic_starfish(alpha, delta, J, OL.StarfishGeom(), OL.starfish_density, xt, yt)
+    err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+    assert err <= TOL, f"err={err:.3e}"
+
+
+def test_slp_dyadic_far_targets_and_arguments():
+    yk = _yk()
+    u = run_dy(32, 10.0, 1e-4, 3, np.array([0.0, 2.5, -3.0]), np.array([0.0, 0.0, 1.0]))
+    assert np.all(u == 0.0)
+    x = dev(np.zeros(32))
+    with pytest.raises(yk.YkError) as ei:
+        yk.slp_dyadic(10.0, 1e-4, 0, x, x, x, dev(np.zeros(3)), dev(np.zeros(3)), q=16)
+    assert ei.value.status == yk.YK_ERR_ARG
+
+
+@pytest.mark.slow
+def test_slp_dyadic_config_two_boundary():
+    alpha, J = 10.0, 3
+    import oracle.params as OP
+    delta = OP.delta_from_mesh(alpha, 0.004467)
+    R1 = OL.locality_radius(alpha, delta)
+    xt, yt = near_targets(200, 0.9 * R1, seed=13)
+    u = run_dy(6250, alpha, delta, J, xt, yt)
+    ref = OL.slp_dyadic_starfish(alpha, delta, J, OL.StarfishGeom(), OL.starfish_density, xt, yt)
+    assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) <= TOL
