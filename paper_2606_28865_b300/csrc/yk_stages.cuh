@@ -545,8 +545,8 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
             for (int i = 0; i < NI; ++i) cur[i] = mine[idx[i]];
 #pragma unroll
             for (int i = 0; i < NI; ++i) {
-                cur[i] = df_mul_add(cur[i], wk[tc[i]], wk[W + ta[i]]);
-                if (dipk) cur[i] = df_mul_add(cur[i], wk[2 * W + tc[i]], wk[3 * W + ta[i]]);
+                cur[i] = df_mul_add_lazy(cur[i], wk[tc[i]], wk[W + ta[i]]);
+                if (dipk) cur[i] = df_mul_add_lazy(cur[i], wk[2 * W + tc[i]], wk[3 * W + ta[i]]);
             }
 #pragma unroll
             for (int i = 0; i < NI; ++i) mine[idx[i]] = cur[i];
@@ -560,7 +560,8 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
         const int ci = spread_cell(rr, cc, PT, S);
         df32 sum = acc[ci];
         for (int w = 1; w < NW; ++w) sum = sum + acc[w * TS + ci];
-        grid[(size_t)(Y0 + rr) * g.n + X0 + cc] = sum;
+        /* the cells were accumulated unnormalised (df_mul_add_lazy): normalise before the FFT */
+        grid[(size_t)(Y0 + rr) * g.n + X0 + cc] = df_fast_two_sum(sum.hi, sum.lo);
     }
     __syncthreads();
 }
