@@ -303,3 +303,55 @@ def slp_dyadic_starfish(alpha, delta, J, geom: StarfishGeom, sigma, xt, yt, n_sc
         for j in range(1, J + 1):
             out[i] += np.sum(q * dyadic_kernel(alpha, delta, j, r))
     return out
+
+
+# Double layer (Section 2.1, eqs. dld, diffker_dlp): the normal derivative in the source point of
+# the heat kernel is nu' . (x - x') H / (2t), so
+#   D_{L,D}^{(j)}[mu](x) = int_boundary nu(x') . (x - x') K^D_j(|x - x'|) mu(x') ds,
+#   K^D_j(r) = int_{delta_j}^{delta_{j-1}} e^{-r^2/4t - alpha^2 t} / (8 pi t^2) dt
+# (eq. diffker_dlp with K_nu(x, y) = int_1^inf s^{nu-1} e^{-x s - y/s} ds).
+
+def dyadic_kernel_dl(alpha, delta, j, r):
+    """K^D_j(r) by 4 panels x 32 Gauss-Legendre nodes in u = log t (dt / t^2 = du / t)."""
+    r = np.asarray(r, dtype=float)
+    lo, hi = math.log(delta / 4.0 ** j), math.log(delta / 4.0 ** (j - 1))
+    x, w = _GL32
+    acc = np.zeros_like(r)
+    for p in range(4):
+        a = lo + (hi - lo) * p / 4
+        b = lo + (hi - lo) * (p + 1) / 4
+        t = np.exp(0.5 * (b - a) * x + 0.5 * (a + b))
+        ww = 0.5 * (b - a) * w
+        acc = acc + np.sum(ww * np.exp(-(r[..., None] ** 2) / (4 * t) - alpha * alpha * t) / t,
+                           axis=-1)
+    return acc / (8 * math.pi)
+
+
+def dlp_dyadic_starfish(alpha, delta, J, geom: StarfishGeom, mu, xt, yt, n_scan=8192):
+    """sum_{j=1}^J D_{L,D}^{(j)}[mu] at the targets on the analytic curve (outward normal of the
+    counter-clockwise parametrisation), quadrature as slp_dyadic_starfish."""
+    xt, yt = np.atleast_1d(xt).astype(float), np.atleast_1d(yt).astype(float)
+    R = locality_radius(alpha, delta)
+    ts = np.linspace(0.0, 2 * math.pi, n_scan + 1)
+    g, _, _ = geom.derivs(ts)
+    seg = np.hypot(np.diff(g[0]), np.diff(g[1]))
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    out = np.zeros(len(xt))
+    for i in range(len(xt)):
+        d = np.hypot(g[0] - xt[i], g[1] - yt[i])
+        near = np.nonzero(np.minimum(d[:-1], d[1:]) < R + seg)[0]
+        if len(near) == 0:
+            continue
+        a, b = ts[near], ts[near + 1]
+        t = (0.5 * (b - a))[:, None] * xg[None, :] + (0.5 * (a + b))[:, None]
+        w = (0.5 * (b - a))[:, None] * wg[None, :]
+        p, p1, _ = geom.derivs(t)
+        sp_ = np.hypot(p1[0], p1[1])
+        nux, nuy = p1[1] / sp_, -p1[0] / sp_
+        m0, _, _ = mu(t)
+        dx, dy = xt[i] - p[0], yt[i] - p[1]
+        r = np.hypot(dx, dy)
+        q = m0 * sp_ * w * (nux * dx + nuy * dy)
+        for j in range(1, J + 1):
+            out[i] += np.sum(q * dyadic_kernel_dl(alpha, delta, j, r))
+    return out
