@@ -693,7 +693,16 @@ def main():
         for _ in range(reps):
             yk.slp_dyadic(a_loc, dstar, J, *lb, xt_l, yt_l, q=16, out=ud, stream=lanes[a_loc])
         ms_d = (time.perf_counter() - t0) / reps * 1e3
+        udl = torch.empty_like(xt_l)
+        for _ in range(2):
+            yk.dlp_dyadic(a_loc, dstar, J, *lb, xt_l, yt_l, q=16, out=udl, stream=lanes[a_loc])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            yk.dlp_dyadic(a_loc, dstar, J, *lb, xt_l, yt_l, q=16, out=udl, stream=lanes[a_loc])
+        ms_dl = (time.perf_counter() - t0) / reps * 1e3
         dyadic = {"value": (len(xb) + xt_l.numel()) / (ms_d * 1e-3), "unit": "points/s",
+                  "double_layer_ms": ms_dl,
                   "ms": ms_d, "alpha": a_loc, "delta": dstar, "levels": J,
                   "n_boundary": len(xb), "n_targets": int(xt_l.numel()),
                   "targets_reached": int((ud != 0).sum().item()),

@@ -235,6 +235,20 @@ YK_API yk_status yk_slp_dyadic(double alpha, double delta, int J, int64_t n_pane
                                void *stream);
 
 /*
+ * yk_dlp_dyadic: the dyadic corrections of the double-layer local part (Section 2.1, eqs. dld and
+ * diffker_dlp): u_i = sum_{j=1}^{J} int_boundary nu(x') . (x_i - x') K^D_j(|x_i - x'|) mu(x') ds,
+ * K^D_j(r) = int_{delta/4^j}^{delta/4^(j-1)} e^{-r^2/4t - alpha^2 t} / (8 pi t^2) dt (the
+ * source-point normal derivative of the heat kernel integrated over the level; eq. diffker_dlp
+ * with K_nu(x, y) = int_1^inf s^(nu-1) e^(-x s - y/s) ds), nu the outward normal of the
+ * counter-clockwise boundary.  Arguments, resampling and errors as yk_slp_dyadic (mu in place of
+ * sigma).
+ */
+YK_API yk_status yk_dlp_dyadic(double alpha, double delta, int J, int64_t n_panels, int q,
+                               const double *xb, const double *yb, const double *mu,
+                               int64_t n_trg, const double *xt, const double *yt, double *u,
+                               void *stream);
+
+/*
  * yk_vp_local: the volume local part V_L[f](x_i) = int_0^{delta_star} int_Omega H_t(x_i - x') f(x')
  * dx' dt (Section 2.1, eq. vl) by the expansion of the Lemma for V_L (Section 4.1, eq. vp_local1)
  * through its delta_star^2 term at targets within the locality radius of the boundary (closest

@@ -401,6 +401,29 @@ def slp_dyadic(alpha, delta, J, xb, yb, sigma, xt, yt, q=16, out=None, stream=No
     return out
 
 
+_lib.yk_dlp_dyadic.argtypes = list(_lib.yk_slp_dyadic.argtypes)
+_lib.yk_dlp_dyadic.restype = ctypes.c_int
+
+
+def dlp_dyadic(alpha, delta, J, xb, yb, mu, xt, yt, q=16, out=None, stream=None):
+    """Sum of the J dyadic corrections of the double-layer local part at the targets (device
+    float64 tensors; see yk_dlp_dyadic)."""
+    torch = _torch()
+    nb, nt = _len(xb), _len(xt)
+    if nb % q or _len(yb) != nb or _len(mu) != nb or _len(yt) != nt:
+        raise ValueError("boundary arrays must hold n_panels * q values; target lengths differ")
+    if out is None:
+        out = torch.empty(nt, dtype=torch.float64, device=xt.device)
+    if stream is None:
+        stream = _current_stream()
+    keep = []
+    _check(_lib.yk_dlp_dyadic(float(alpha), float(delta), int(J), nb // q, int(q),
+                              _ptr(xb, keep), _ptr(yb, keep), _ptr(mu, keep), nt,
+                              _ptr(xt, keep), _ptr(yt, keep), _ptr(out, keep), stream),
+           "yk_dlp_dyadic")
+    return out
+
+
 _lib.yk_vp_local.argtypes = [_d, _d, _i64, ctypes.c_int, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
                              _vp]
 _lib.yk_vp_local.restype = ctypes.c_int

@@ -538,12 +538,14 @@ struct DyLevel {
     const double *tab; /* npc x (kDyDeg + 1) monomial coefficients in z = 2 (rho - k) - 1 */
     LocalGrid G;       /* cells of edge >= R_j */
     const int *ptr;    /* nodes per cell */
-    const double *X, *Y, *Q; /* nodes sorted by cell; Q = sigma |gamma'| w */
+    const double *X, *Y, *Q; /* nodes sorted by cell; Q = density |gamma'| w */
+    const double *NX, *NY;   /* outward unit normals at the nodes (double layer), else NULL */
 };
 
 /* node (p, s, k): parameter -1 + (2 s + 1 + t_k) / m of panel p */
 __global__ void k_dy_nodes(int64_t npan, int q, int m, PanelSet P, const double *__restrict__ wq,
-                           double *__restrict__ X, double *__restrict__ Y, double *__restrict__ Q)
+                           double *__restrict__ X, double *__restrict__ Y, double *__restrict__ Q,
+                           double *__restrict__ NX, double *__restrict__ NY)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t per = (int64_t)m * q;
@@ -557,7 +559,12 @@ __global__ void k_dy_nodes(int64_t npan, int q, int m, PanelSet P, const double 
     const int h = q / 2;
     X[i] = P.xb[p * q + h] + g[0];
     Y[i] = P.yb[p * q + h] + g[1];
-    Q[i] = (P.sref[p * q + h] + g[2]) * sqrt(g1[0] * g1[0] + g1[1] * g1[1]) * wq[k] / m;
+    const double sp = sqrt(g1[0] * g1[0] + g1[1] * g1[1]);
+    Q[i] = (P.sref[p * q + h] + g[2]) * sp * wq[k] / m;
+    if (NX) { /* outward normal of the counter-clockwise boundary */
+        NX[i] = g1[1] / sp;
+        NY[i] = -g1[0] / sp;
+    }
 }
 
 __device__ __forceinline__ int pt_cell(double x, double y, const LocalGrid &G)
@@ -576,9 +583,11 @@ __global__ void k_pt_count(int64_t n, const double *__restrict__ X, const double
 }
 
 __global__ void k_pt_fill(int64_t n, const double *__restrict__ X, const double *__restrict__ Y,
-                          const double *__restrict__ Q, LocalGrid G, const int *__restrict__ ptr,
+                          const double *__restrict__ Q, const double *__restrict__ NX,
+                          const double *__restrict__ NY, LocalGrid G, const int *__restrict__ ptr,
                           int *__restrict__ cur, double *__restrict__ Xs, double *__restrict__ Ys,
-                          double *__restrict__ Qs)
+                          double *__restrict__ Qs, double *__restrict__ NXs,
+                          double *__restrict__ NYs)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -587,6 +596,10 @@ __global__ void k_pt_fill(int64_t n, const double *__restrict__ X, const double 
     Xs[e] = X[i];
     Ys[e] = Y[i];
     Qs[e] = Q[i];
+    if (NX) {
+        NXs[e] = NX[i];
+        NYs[e] = NY[i];
+    }
 }
 
 /* u_i += S_{L,D}^{(j)} at the near targets: one warp per target (the targets grouped by cell),
@@ -624,7 +637,9 @@ __global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__r
                 double f = a[kDyDeg];
 #pragma unroll
                 for (int n = kDyDeg - 1; n >= 0; --n) f = fma(f, z, a[n]);
-                acc = fma(L.Q[e], f, acc);
+                /* double layer: nu' . (x - x') = -(nu'_x dx + nu'_y dy) */
+                const double qe = L.NX ? -L.Q[e] * (L.NX[e] * dx + L.NY[e] * dy) : L.Q[e];
+                acc = fma(qe, f, acc);
             }
         }
     }
@@ -636,7 +651,7 @@ __global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__r
  * K_j = (1/4 pi) int_0^{ln 4} exp(-rho e^{-u} - alpha^2 delta_j e^u) du (t = delta_j e^u), by
  * 3 x 48 Gauss-Legendre nodes in u; each piece interpolated at its 13 Chebyshev points and
  * written as a polynomial in z = 2 (rho - k) - 1 */
-void dyadic_table_build(double c, int npc, std::vector<double> &tab)
+void dyadic_table_build(double c, int npc, double dj, bool dl, std::vector<double> &tab)
 {
     constexpr int NG = 48, NP = 3, D = kDyDeg;
     static const struct Rule {
@@ -651,10 +666,12 @@ void dyadic_table_build(double c, int npc, std::vector<double> &tab)
             const double a = L4 * p / NP, b = L4 * (p + 1) / NP;
             for (int n = 0; n < NG; ++n) {
                 const double uu = 0.5 * (b - a) * gx[n] + 0.5 * (a + b);
-                acc += 0.5 * (b - a) * gw[n] * std::exp(-rho * std::exp(-uu) - c * std::exp(uu));
+                const double wgt = dl ? std::exp(-uu) : 1.0; /* dt / t^2 = e^{-u} du / delta_j */
+                acc += 0.5 * (b - a) * gw[n] * wgt *
+                       std::exp(-rho * std::exp(-uu) - c * std::exp(uu));
             }
         }
-        return acc / (4.0 * M_PI);
+        return dl ? acc / (8.0 * M_PI * dj) : acc / (4.0 * M_PI);
     };
     /* Chebyshev T_n as monomials in z */
     double T[D + 1][D + 1] = {};
@@ -680,22 +697,28 @@ void dyadic_table_build(double c, int npc, std::vector<double> &tab)
 
 /* tables are reused across calls with the same (alpha^2 delta_j, pieces) (a Rothe march or a
  * bench repeats them); a small mutex-guarded cache, oldest entry dropped beyond 32 */
-void dyadic_table(double c, int npc, std::vector<double> &tab)
+void dyadic_table(double c, int npc, double dj, bool dl, std::vector<double> &tab)
 {
+    struct Entry {
+        double c, dj;
+        int npc;
+        bool dl;
+        std::vector<double> tab;
+    };
     static std::mutex mu;
-    static std::vector<std::pair<std::pair<double, int>, std::vector<double>>> cache;
+    static std::vector<Entry> cache;
     {
         std::lock_guard<std::mutex> lk(mu);
-        for (auto &kv : cache)
-            if (kv.first.first == c && kv.first.second == npc) {
-                tab = kv.second;
+        for (auto &en : cache)
+            if (en.c == c && en.npc == npc && en.dl == dl && (!dl || en.dj == dj)) {
+                tab = en.tab;
                 return;
             }
     }
-    dyadic_table_build(c, npc, tab);
+    dyadic_table_build(c, npc, dj, dl, tab);
     std::lock_guard<std::mutex> lk(mu);
     if (cache.size() >= 32) cache.erase(cache.begin());
-    cache.push_back({{c, npc}, tab});
+    cache.push_back({c, dj, npc, dl, tab});
 }
 
 bool is_dev(const void *p)
@@ -717,7 +740,7 @@ yk_status lfail(yk_status s, const char *msg)
 
 /* S_{L,A} (vol false: sigma) or V_L (vol true: fd): shared set-up (extent, panel
  * series, cell lists, near targets grouped by cell), then the part's kernels */
-yk_status run_local(const char *name, bool vol, int J, double alpha, double delta_star, int64_t n_panels, int q,
+yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, double delta_star, int64_t n_panels, int q,
                     const double *xb, const double *yb, const double *sigma, int64_t n_trg,
                     const double *xt, const double *yt, const double *fd, double *u, void *stream)
 {
@@ -932,7 +955,7 @@ yk_status run_local(const char *name, bool vol, int J, double alpha, double delt
         const double R = std::sqrt(dj1) * (12.0 + 2.0 * alpha * std::sqrt(dj1));
         const int npc = (int)std::ceil(R * R / (4.0 * dj)) + 1;
         std::vector<double> tab;
-        dyadic_table(alpha * alpha * dj, npc, tab);
+        dyadic_table(alpha * alpha * dj, npc, dj, dl, tab);
         /* sub-panels no longer than 3 sqrt(delta_j) (chords at most 1.5 x shorter than arcs) */
         const int m = std::max(1, (int)std::ceil(1.5 * hmax / (3.0 * std::sqrt(dj))));
         const int64_t nn = n_panels * m * q;
@@ -959,7 +982,8 @@ yk_status run_local(const char *name, bool vol, int J, double alpha, double delt
         double *d_tab = nullptr, *d_nodes = nullptr, *d_wq = nullptr;
         int *d_c = nullptr; /* cnt | ptr | cur */
         e = cudaMallocAsync(&d_tab, sizeof(double) * tab.size(), st);
-        if (e == cudaSuccess) e = cudaMallocAsync(&d_nodes, sizeof(double) * 6 * nn, st);
+        const int na = dl ? 10 : 6; /* X Y Q (NX NY), then the sorted copies */
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_nodes, sizeof(double) * na * nn, st);
         if (e == cudaSuccess) e = cudaMallocAsync(&d_wq, sizeof(double) * q, st);
         if (e == cudaSuccess) e = cudaMallocAsync(&d_c, sizeof(int) * (3 * (size_t)nc + 1), st);
         if (e != cudaSuccess) dy_oom = true;
@@ -969,11 +993,16 @@ yk_status run_local(const char *name, bool vol, int J, double alpha, double delt
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_wq, wq.data(), sizeof(double) * q, cudaMemcpyHostToDevice, st);
         int *cnt = d_c, *cptr = d_c + nc, *ccur = d_c + 2 * nc + 1;
+        const int half = na / 2;
         double *X = d_nodes, *Y = d_nodes + nn, *Qn = d_nodes + 2 * nn;
-        double *Xs = d_nodes + 3 * nn, *Ys = d_nodes + 4 * nn, *Qs = d_nodes + 5 * nn;
+        double *NX = dl ? d_nodes + 3 * nn : nullptr, *NY = dl ? d_nodes + 4 * nn : nullptr;
+        double *Xs = d_nodes + half * nn, *Ys = d_nodes + (half + 1) * nn;
+        double *Qs = d_nodes + (half + 2) * nn;
+        double *NXs = dl ? d_nodes + (half + 3) * nn : nullptr;
+        double *NYs = dl ? d_nodes + (half + 4) * nn : nullptr;
         const int gb = (int)((nn + 255) / 256);
         if (e == cudaSuccess) {
-            k_dy_nodes<<<gb, 256, 0, st>>>(n_panels, q, m, P, d_wq, X, Y, Qn);
+            k_dy_nodes<<<gb, 256, 0, st>>>(n_panels, q, m, P, d_wq, X, Y, Qn, NX, NY);
             e = cudaMemsetAsync(cnt, 0, sizeof(int) * nc, st);
         }
         if (e == cudaSuccess) {
@@ -983,12 +1012,15 @@ yk_status run_local(const char *name, bool vol, int J, double alpha, double delt
         /* the scan used the cursors as scratch: zero them for the fill */
         if (e == cudaSuccess) e = cudaMemsetAsync(ccur, 0, sizeof(int) * nc, st);
         if (e == cudaSuccess) {
-            k_pt_fill<<<gb, 256, 0, st>>>(nn, X, Y, Qn, L.G, cptr, ccur, Xs, Ys, Qs);
+            k_pt_fill<<<gb, 256, 0, st>>>(nn, X, Y, Qn, NX, NY, L.G, cptr, ccur, Xs, Ys, Qs, NXs,
+                                          NYs);
             L.tab = d_tab;
             L.ptr = cptr;
             L.X = Xs;
             L.Y = Ys;
             L.Q = Qs;
+            L.NX = NXs;
+            L.NY = NYs;
             k_dyadic_level<<<(int)(((int64_t)n_near * 32 + 255) / 256), 256, 0, st>>>(
                 n_near, d_order, xt, yt, L, u);
             e = cudaGetLastError();
@@ -1022,7 +1054,7 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
                                          double *u, void *stream)
 {
     if (!sigma) return lfail(YK_ERR_ARG, "yk_slp_local: sigma is NULL");
-    return run_local("yk_slp_local", false, 0, alpha, delta_star, n_panels, q, xb, yb, sigma, n_trg, xt, yt,
+    return run_local("yk_slp_local", false, 0, false, alpha, delta_star, n_panels, q, xb, yb, sigma, n_trg, xt, yt,
                      nullptr, u, stream);
 }
 
@@ -1032,7 +1064,7 @@ extern "C" YK_API yk_status yk_vp_local(double alpha, double delta_star, int64_t
                                         double *u, void *stream)
 {
     if (n_trg > 0 && !fd) return lfail(YK_ERR_ARG, "yk_vp_local: fd is NULL");
-    return run_local("yk_vp_local", true, 0, alpha, delta_star, n_panels, q, xb, yb, nullptr, n_trg,
+    return run_local("yk_vp_local", true, 0, false, alpha, delta_star, n_panels, q, xb, yb, nullptr, n_trg,
                      xt, yt, fd, u, stream);
 }
 
@@ -1043,6 +1075,17 @@ extern "C" YK_API yk_status yk_slp_dyadic(double alpha, double delta, int J, int
 {
     if (!sigma) return lfail(YK_ERR_ARG, "yk_slp_dyadic: sigma is NULL");
     if (J < 1 || J > 10) return lfail(YK_ERR_ARG, "yk_slp_dyadic: need 1 <= J <= 10");
-    return run_local("yk_slp_dyadic", false, J, alpha, delta, n_panels, q, xb, yb, sigma, n_trg,
+    return run_local("yk_slp_dyadic", false, J, false, alpha, delta, n_panels, q, xb, yb, sigma, n_trg,
+                     xt, yt, nullptr, u, stream);
+}
+
+extern "C" YK_API yk_status yk_dlp_dyadic(double alpha, double delta, int J, int64_t n_panels,
+                                          int q, const double *xb, const double *yb,
+                                          const double *mu, int64_t n_trg, const double *xt,
+                                          const double *yt, double *u, void *stream)
+{
+    if (!mu) return lfail(YK_ERR_ARG, "yk_dlp_dyadic: mu is NULL");
+    if (J < 1 || J > 10) return lfail(YK_ERR_ARG, "yk_dlp_dyadic: need 1 <= J <= 10");
+    return run_local("yk_dlp_dyadic", false, J, true, alpha, delta, n_panels, q, xb, yb, mu, n_trg,
                      xt, yt, nullptr, u, stream);
 }

@@ -249,3 +249,35 @@ def test_slp_dyadic_config_two_boundary():
     u = run_dy(6250, alpha, delta, J, xt, yt)
     ref = OL.slp_dyadic_starfish(alpha, delta, J, OL.StarfishGeom(), OL.starfish_density, xt, yt)
     assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) <= TOL
+
+
+def run_dl_dy(n_panels, alpha, delta, J, xt, yt):
+    yk = _yk()
+    xb, yb, _, tb = W.boundary_nodes(W.Starfish(), n_panels, 16)
+    mu = W.boundary_density(tb)
+    u = yk.dlp_dyadic(alpha, delta, J, dev(xb), dev(yb), dev(mu), dev(xt), dev(yt), q=16)
+    torch.cuda.synchronize()
+    return u.cpu().numpy()
+
+
+@pytest.mark.parametrize("n_panels,alpha,delta,J", [(32, 10.0, 1e-4, 3), (32, 1.0, 3e-5, 2),
+                                                    (128, 100.0, 1e-4, 3)])
+def test_dlp_dyadic_matches_oracle(n_panels, alpha, delta, J):
+    R1 = OL.locality_radius(alpha, delta)
+    xt, yt = near_targets(300, min(0.9 * R1, 0.05), seed=14)
+    u = run_dl_dy(n_panels, alpha, delta, J, xt, yt)
+    ref = OL.dlp_dyadic_starfish(alpha, delta, J, OL.StarfishGeom(), OL.starfish_density, xt, yt)
+    err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+    assert err <= TOL, f"err={err:.3e}"
+
+
+@pytest.mark.slow
+def test_dlp_dyadic_config_two_boundary():
+    alpha, J = 10.0, 3
+    import oracle.params as OP
+    delta = OP.delta_from_mesh(alpha, 0.004467)
+    R1 = OL.locality_radius(alpha, delta)
+    xt, yt = near_targets(200, 0.9 * R1, seed=15)
+    u = run_dl_dy(6250, alpha, delta, J, xt, yt)
+    ref = OL.dlp_dyadic_starfish(alpha, delta, J, OL.StarfishGeom(), OL.starfish_density, xt, yt)
+    assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) <= TOL
