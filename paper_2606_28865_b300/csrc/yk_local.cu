@@ -529,13 +529,16 @@ __global__ void __launch_bounds__(128) k_vp_local(int n_near, const int *__restr
  * interpolation of the paper's bisection), the nodes binned in cells of edge R_j, and every near
  * target sums K_j(|x - x'|) sigma ds over the nodes within R_j, K_j from a table */
 
-constexpr int kDyDeg = 12; /* degree of the table's pieces (width 1 in rho = r^2 / (4 delta_j)) */
+constexpr int kDyDeg = 8;          /* degree of the table's pieces */
+constexpr double kDyPiece = 0.5;   /* their width in rho = r^2 / (4 delta_j) */
 
 struct DyLevel {
-    double inv4d;      /* 1 / (4 delta_j) */
+    double inv4d;      /* 1 / (kDyPiece 4 delta_j): the piece coordinate */
     double R2;         /* R_j^2: K_j is below 1e-16 of its peak beyond R_j */
+    float R2f;         /* FP32 screen radius^2: R_j widened past the FP32 distance error */
     int npc;           /* table pieces */
-    const double *tab; /* npc x (kDyDeg + 1) monomial coefficients in z = 2 (rho - k) - 1 */
+    const double *tab; /* npc x (kDyDeg + 1) monomial coefficients in z = 2 (rho' - k) - 1 */
+    const float *Xf, *Yf; /* FP32 copies of the sorted nodes (the screen) */
     LocalGrid G;       /* cells of edge >= R_j */
     const int *ptr;    /* nodes per cell */
     const double *X, *Y, *Q; /* nodes sorted by cell; Q = density |gamma'| w */
@@ -587,7 +590,8 @@ __global__ void k_pt_fill(int64_t n, const double *__restrict__ X, const double 
                           const double *__restrict__ NY, LocalGrid G, const int *__restrict__ ptr,
                           int *__restrict__ cur, double *__restrict__ Xs, double *__restrict__ Ys,
                           double *__restrict__ Qs, double *__restrict__ NXs,
-                          double *__restrict__ NYs)
+                          double *__restrict__ NYs, float *__restrict__ Xfs,
+                          float *__restrict__ Yfs)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -596,6 +600,8 @@ __global__ void k_pt_fill(int64_t n, const double *__restrict__ X, const double 
     Xs[e] = X[i];
     Ys[e] = Y[i];
     Qs[e] = Q[i];
+    Xfs[e] = (float)X[i];
+    Yfs[e] = (float)Y[i];
     if (NX) {
         NXs[e] = NX[i];
         NYs[e] = NY[i];
@@ -615,6 +621,7 @@ __global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__r
     if (w >= n_near) return; /* whole warps leave together */
     const int i = order[w];
     const double x = xt[i], y = yt[i];
+    const float xf = (float)x, yf = (float)y;
     const LocalGrid &G = L.G;
     const double fx = floor((x - G.x0) / G.h), fy = floor((y - G.y0) / G.h);
     if (!(fx >= -1.0 && fx <= G.nx && fy >= -1.0 && fy <= G.ny)) return; /* no node within R_j */
@@ -627,6 +634,8 @@ __global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__r
         const int c0 = cy * G.nx + max(ci - 1, 0), c1 = cy * G.nx + min(ci + 1, G.nx - 1);
         if (ci + 1 < 0 || ci - 1 >= G.nx) continue;
         for (int e = L.ptr[c0] + lane; e < L.ptr[c1 + 1]; e += 32) {
+            const float dxf = L.Xf[e] - xf, dyf = L.Yf[e] - yf;
+            if (!(dxf * dxf + dyf * dyf < L.R2f)) continue; /* FP32 screen */
             const double dx = L.X[e] - x, dy = L.Y[e] - y;
             const double r2 = dx * dx + dy * dy;
             if (r2 < L.R2) {
@@ -647,10 +656,11 @@ __global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__r
     if (lane == 0) u[i] += acc;
 }
 
-/* K_j on the pieces [k, k + 1] of rho = r^2 / (4 delta_j):
+/* K_j on the pieces [k, k + 1] kDyPiece of rho = r^2 / (4 delta_j):
  * K_j = (1/4 pi) int_0^{ln 4} exp(-rho e^{-u} - alpha^2 delta_j e^u) du (t = delta_j e^u), by
- * 3 x 48 Gauss-Legendre nodes in u; each piece interpolated at its 13 Chebyshev points and
- * written as a polynomial in z = 2 (rho - k) - 1 */
+ * 3 x 48 Gauss-Legendre nodes in u; each piece interpolated at its kDyDeg + 1 Chebyshev points
+ * and written as a polynomial in z = 2 (rho / kDyPiece - k) - 1 (degree 8 on width 0.5: within
+ * ~1e-16 of the piece's values, the fastest component being e^{-rho}) */
 void dyadic_table_build(double c, int npc, double dj, bool dl, std::vector<double> &tab)
 {
     constexpr int NG = 48, NP = 3, D = kDyDeg;
@@ -684,7 +694,7 @@ void dyadic_table_build(double c, int npc, double dj, bool dl, std::vector<doubl
     double f[D + 1], zc[D + 1];
     for (int i = 0; i <= D; ++i) zc[i] = std::cos(M_PI * (i + 0.5) / (D + 1));
     for (int k = 0; k < npc; ++k) {
-        for (int i = 0; i <= D; ++i) f[i] = K(k + 0.5 * (zc[i] + 1.0));
+        for (int i = 0; i <= D; ++i) f[i] = K(kDyPiece * (k + 0.5 * (zc[i] + 1.0)));
         for (int n = 0; n <= D; ++n) {
             double an = 0.0;
             for (int i = 0; i <= D; ++i) an += f[i] * std::cos(n * M_PI * (i + 0.5) / (D + 1));
@@ -953,7 +963,7 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
     for (int j = 1; j <= J && e == cudaSuccess && n_near > 0; ++j) {
         const double dj = delta_star / std::pow(4.0, j), dj1 = 4.0 * dj;
         const double R = std::sqrt(dj1) * (12.0 + 2.0 * alpha * std::sqrt(dj1));
-        const int npc = (int)std::ceil(R * R / (4.0 * dj)) + 1;
+        const int npc = (int)std::ceil(R * R / (4.0 * dj) / kDyPiece) + 1;
         std::vector<double> tab;
         dyadic_table(alpha * alpha * dj, npc, dj, dl, tab);
         /* sub-panels no longer than 3 sqrt(delta_j) (chords at most 1.5 x shorter than arcs) */
@@ -965,8 +975,16 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
             break;
         }
         DyLevel L;
-        L.inv4d = 1.0 / (4.0 * dj);
+        L.inv4d = 1.0 / (kDyPiece * 4.0 * dj);
         L.R2 = R * R;
+        {
+            /* screen radius: R plus the FP32 rounding of the coordinates (< 2^-24 |x| each, three
+             * roundings per difference) with room to spare */
+            const double amax = std::max(std::max(std::fabs(xmin), std::fabs(xmax)),
+                                         std::max(std::fabs(ymin), std::fabs(ymax))) + 2.0 * R;
+            const double Rs = R * 1.0005 + 5e-7 * amax;
+            L.R2f = (float)(Rs * Rs);
+        }
         L.npc = npc;
         L.G.h = R;
         L.G.x0 = xmin - 2.0 * R;
@@ -983,7 +1001,9 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
         int *d_c = nullptr; /* cnt | ptr | cur */
         e = cudaMallocAsync(&d_tab, sizeof(double) * tab.size(), st);
         const int na = dl ? 10 : 6; /* X Y Q (NX NY), then the sorted copies */
+        float *d_f = nullptr;       /* FP32 copies of the sorted X, Y */
         if (e == cudaSuccess) e = cudaMallocAsync(&d_nodes, sizeof(double) * na * nn, st);
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_f, sizeof(float) * 2 * nn, st);
         if (e == cudaSuccess) e = cudaMallocAsync(&d_wq, sizeof(double) * q, st);
         if (e == cudaSuccess) e = cudaMallocAsync(&d_c, sizeof(int) * (3 * (size_t)nc + 1), st);
         if (e != cudaSuccess) dy_oom = true;
@@ -1013,7 +1033,9 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
         if (e == cudaSuccess) e = cudaMemsetAsync(ccur, 0, sizeof(int) * nc, st);
         if (e == cudaSuccess) {
             k_pt_fill<<<gb, 256, 0, st>>>(nn, X, Y, Qn, NX, NY, L.G, cptr, ccur, Xs, Ys, Qs, NXs,
-                                          NYs);
+                                          NYs, d_f, d_f + nn);
+            L.Xf = d_f;
+            L.Yf = d_f + nn;
             L.tab = d_tab;
             L.ptr = cptr;
             L.X = Xs;
@@ -1025,7 +1047,7 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
                 n_near, d_order, xt, yt, L, u);
             e = cudaGetLastError();
         }
-        for (void *b : {(void *)d_tab, (void *)d_nodes, (void *)d_wq, (void *)d_c})
+        for (void *b : {(void *)d_tab, (void *)d_nodes, (void *)d_wq, (void *)d_c, (void *)d_f})
             if (b) cudaFreeAsync(b, st);
     }
     int n_out = 0;
