@@ -820,6 +820,7 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->win_src = P<float2>(p->win_src);
     d->win_dip = P<float2>(p->win_dip);
     d->win_trg = P<float2>(p->win_trg);
+    d->win_trg_pitch = p->n_trg;
     for (int s = 0; s < yk::ST_COUNT; ++s) {
         d->items[s] = yk::stage_items(*d, s);
         d->smem[s] = yk::stage_smem(*d, s);
@@ -1162,7 +1163,7 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
         YK_CU(yk::launch_point_windows_df(g, n_trg, P<double2>(p->trg_t),
                                           P<int>(p->trg_ptr) + (size_t)p->nt * p->nt,
                                           P<float2>(p->win_pc), p->pdeg, false,
-                                          P<float2>(p->win_trg), p->stream),
+                                          P<float2>(p->win_trg), p->stream, n_trg),
               "target windows");
     }
     stage_end(p, YK_STAGE_BIN_TRG);

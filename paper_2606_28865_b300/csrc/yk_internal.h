@@ -77,8 +77,12 @@ struct Inst {
     double dmax;              /* bound on |phi'| over the window (cells^-1), for the FP64 scale */
     /* double-float path: window values computed once per point at yk_set_points (they depend on
      * positions only): per charge [phi(Y - t_y) taps | phi(X - t_x) taps] (2w double-floats, source
-     * order), per dipole [phi_y | phi_x | phi'_y | phi'_x] (4w), per target in tile order (2w) */
+     * order), per dipole [phi_y | phi_x | phi'_y | phi'_x] (4w), per target in tile order (2w planes
+     * of n_trg values) */
     const float2 *win_src, *win_dip, *win_trg;
+    int64_t win_trg_pitch;    /* the target windows are value-major: value k of target e at
+                                 k * win_trg_pitch + e (coalesced reads in the interpolation) */
+    int64_t pad16_;           /* keeps sizeof(Inst) a multiple of 16 (copied in 16-byte words) */
     int items[ST_COUNT];      /* work items of each stage */
     int smem[ST_COUNT];       /* dynamic shared memory of each stage (bytes) */
 };
@@ -105,7 +109,7 @@ cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, cons
  * *count points are valid. */
 cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts,
                                     const int *count, const float2 *coef, int deg, bool deriv,
-                                    float2 *out, cudaStream_t st);
+                                    float2 *out, cudaStream_t st, int64_t pitch = 0);
 /* exclusive scan of cnt[0..count) into ptr[0..count]; cur (>= ceil(count / 4096) ints) is scratch
  * and is left zeroed */
 cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStream_t st);

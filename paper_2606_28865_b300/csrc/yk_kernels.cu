@@ -318,7 +318,7 @@ __device__ __forceinline__ void windows_piece(const df32 *c, df32 x, df32 (&p)[W
 template <int W>
 __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
                                    const int *__restrict__ count, const float2 *__restrict__ coef,
-                                   int deriv, float2 *__restrict__ out)
+                                   int deriv, int64_t pitch, float2 *__restrict__ out)
 {
     constexpr int NP = 4, D = kPieceDeg[W];
     extern __shared__ __align__(16) unsigned char sm[];
@@ -330,8 +330,12 @@ __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
     if (i >= n || (count && i >= (int64_t)*count)) return;
     const double2 t = pts[i];
     if (t.x < 0.0) return; /* outside the box: no entries */
+    /* point-major records (pitch 0: values k of point i at i * stride + k) or value-major planes
+     * (value k of point i at k * pitch + i: the interpolation's lanes then read consecutive
+     * points) */
     const int stride = deriv ? 4 * W : 2 * W;
-    float2 *o = out + (size_t)i * stride;
+    float2 *o = pitch ? out + i : out + (size_t)i * stride;
+    const int64_t ks = pitch ? pitch : 1;
     const double ux = ((double)first_tap<W>(t.x) - t.x) + 0.5 * W;
     const double uy = ((double)first_tap<W>(t.y) - t.y) + 0.5 * W;
     const int hx = min(NP - 1, (int)(ux * NP)), hy = min(NP - 1, (int)(uy * NP));
@@ -339,18 +343,18 @@ __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
     df32 p[W];
     windows_piece<W, D>(cw + hy * (D + 1) * W, ay, p);
 #pragma unroll
-    for (int a = 0; a < W; ++a) o[a] = make_float2(p[a].hi, p[a].lo);
+    for (int a = 0; a < W; ++a) o[(a) * ks] = make_float2(p[a].hi, p[a].lo);
     windows_piece<W, D>(cw + hx * (D + 1) * W, ax, p);
 #pragma unroll
-    for (int a = 0; a < W; ++a) o[W + a] = make_float2(p[a].hi, p[a].lo);
+    for (int a = 0; a < W; ++a) o[(W + a) * ks] = make_float2(p[a].hi, p[a].lo);
     if (deriv) {
         const df32 *cwd = cw + NP * (D + 1) * W;
         windows_piece<W, D - 1>(cwd + hy * D * W, ay, p);
 #pragma unroll
-        for (int a = 0; a < W; ++a) o[2 * W + a] = make_float2(p[a].hi, p[a].lo);
+        for (int a = 0; a < W; ++a) o[(2 * W + a) * ks] = make_float2(p[a].hi, p[a].lo);
         windows_piece<W, D - 1>(cwd + hx * D * W, ax, p);
 #pragma unroll
-        for (int a = 0; a < W; ++a) o[3 * W + a] = make_float2(p[a].hi, p[a].lo);
+        for (int a = 0; a < W; ++a) o[(3 * W + a) * ks] = make_float2(p[a].hi, p[a].lo);
     }
 }
 
@@ -636,14 +640,15 @@ __global__ void k_pack_wnu(int64_t nd, const double *__restrict__ wd, const doub
 
 cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts,
                                     const int *count, const float2 *coef, int deg, bool deriv,
-                                    float2 *out, cudaStream_t st)
+                                    float2 *out, cudaStream_t st, int64_t pitch)
 {
     if (n <= 0) return cudaSuccess;
     if (g.w < 2 || g.w > 16 || deg != kPieceDeg[g.w]) return cudaErrorInvalidValue;
     const size_t smem = sizeof(df32) * 4 * ((deg + 1) * g.w + (deriv ? deg * g.w : 0));
     const int blocks = (int)((n + 255) / 256);
 #define YK_CALL(W)                                                                              \
-    k_point_windows_df<W><<<blocks, 256, smem, st>>>(n, pts, count, coef, deriv ? 1 : 0, out)
+    k_point_windows_df<W><<<blocks, 256, smem, st>>>(n, pts, count, coef, deriv ? 1 : 0, pitch, \
+                                                     out)
     YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     return cudaGetLastError();

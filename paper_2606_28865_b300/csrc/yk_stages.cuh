@@ -731,13 +731,29 @@ template <typename R>
 __device__ __forceinline__ void stage_halo(R *sg, const R *__restrict__ grid, const Geom &g,
                                            int X0, int Y0, int P)
 {
-    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
-        const int r = i / P, c = i - r * P;
-        int gy = (Y0 + r) % g.n;
-        if (gy < 0) gy += g.n;
-        int gx = (X0 + c) % g.n;
-        if (gx < 0) gx += g.n;
-        sg[i] = grid[(size_t)gy * g.n + gx];
+    /* rows by warp, columns by lane (coalesced row reads, no division).  The halo reaches at most
+     * W past the tile and n >= 2T >= 2W, so X0 + c and Y0 + r lie in (-n, 2n): one conditional
+     * add or subtract wraps them onto the periodic grid.  Needs blockDim.x % 32 == 0. */
+    if (P > g.n) { /* a halo wider than the grid: plain modulo (not reached with n >= 2T) */
+        for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+            const int r = i / P, c = i - r * P;
+            int gy = (Y0 + r) % g.n, gx = (X0 + c) % g.n;
+            gy += gy < 0 ? g.n : 0;
+            gx += gx < 0 ? g.n : 0;
+            sg[i] = grid[(size_t)gy * g.n + gx];
+        }
+        return;
+    }
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < P; r += nw) {
+        int gy = Y0 + r;
+        gy += gy < 0 ? g.n : (gy >= g.n ? -g.n : 0);
+        const R *__restrict__ row = grid + (size_t)gy * g.n;
+        for (int c = lane; c < P; c += 32) {
+            int gx = X0 + c;
+            gx += gx < 0 ? g.n : (gx >= g.n ? -g.n : 0);
+            sg[r * P + c] = row[gx];
+        }
     }
 }
 
@@ -826,11 +842,16 @@ template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned 
     for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
         const double2 t = d.trg_t[e];
         const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
-        /* window values of this target, computed at yk_set_points: [phi_y taps | phi_x taps] */
-        const float2 *wv = d.win_trg + (size_t)e * 2 * W;
+        /* window values of this target, computed at yk_set_points: planes [phi_y taps | phi_x
+         * taps], value k at k * pitch + e (consecutive threads read consecutive targets) */
+        const float2 *wv = d.win_trg + e;
+        const int64_t pw = d.win_trg_pitch;
         df32 fx[W];
 #pragma unroll
-        for (int a = 0; a < W; ++a) fx[a] = df32(wv[W + a].x, wv[W + a].y);
+        for (int a = 0; a < W; ++a) {
+            const float2 v = wv[(W + a) * pw];
+            fx[a] = df32(v.x, v.y);
+        }
         const df32 *base = sg + (ly - Y0) * P + (lx - X0);
         df32 acc(0.0f, 0.0f);
 #pragma unroll
@@ -838,7 +859,8 @@ template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned 
             df32 row = fx[0] * base[c * P];
 #pragma unroll
             for (int a = 1; a < W; ++a) row = row + fx[a] * base[c * P + a];
-            acc = acc + df32(wv[c].x, wv[c].y) * row;
+            const float2 wy = wv[c * pw];
+            acc = acc + df32(wy.x, wy.y) * row;
         }
         d.u[d.trg_idx[e]] = acc.to_double();
     }
