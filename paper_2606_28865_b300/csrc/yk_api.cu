@@ -330,7 +330,7 @@ long double es_phi_ld(long double z, int w, double beta)
  * out[P (D+1) w + (h D + k) w + a].  Returns the largest deviation from the window at 48 points of
  * every piece of the interior taps (the two edge taps carry the window's square-root edge, a
  * floor of ~5e-13 at w = 12 whatever the degree). */
-constexpr int kWinPieces = 4;
+using yk::kWinPieces;
 long double window_pieces(int w, double beta, int D, bool deriv, std::vector<long double> &out)
 {
     const int P = kWinPieces, m = D + 1;
@@ -659,7 +659,7 @@ yk_status plan_tables(yk_plan_t p)
         p->dmax *= 1.0 + 1e-6;
         cudaError_t ew = cudaSuccess;
         if (!f32 && p->fft_df) {
-            /* the double-float window kernel's 4-piece tables (degree kPieceDeg[w]) */
+            /* the double-float window kernel's kWinPieces-piece tables (degree kPieceDeg[w]) */
             std::vector<long double> pc;
             const int D = yk::kPieceDeg[p->w];
             p->pdeg = D;

@@ -13,10 +13,12 @@
 
 namespace yk {
 
-/* degree of the 4-piece window polynomials for window width w (index w, 2..16): the lowest
- * degree whose interior error is within 3% of eps = 10^(1-w) (or 1e-15), found by fitting in long
- * double (at w = 12: 3.2e-13 at degree 7, 5.4e-15 at degree 8) */
-constexpr int kPieceDeg[17] = {3, 3, 3, 3, 3, 4, 4, 5, 6, 6, 7, 7, 8, 8, 8, 9, 9};
+/* pieces per tap of the double-float window polynomials, and their degree for window width w
+ * (index w, 2..16): the lowest degree whose interior error is within 3% of eps = 10^(1-w), found by
+ * fitting in long double (at w = 12: 1.4e-13 at degree 6; w = 15, 16 take the degree whose error
+ * matches 4 pieces of degree 9, ~3.6e-16) */
+constexpr int kWinPieces = 8;
+constexpr int kPieceDeg[17] = {3, 3, 3, 3, 3, 3, 4, 4, 5, 5, 5, 6, 6, 7, 7, 8, 8};
 
 /* grid geometry handed to kernels by value */
 struct Geom {
@@ -207,7 +209,7 @@ struct yk_plan_s {
     DevBuf win;      /* double[(wdeg+1) * w]: window polynomials of the FP64 path */
     DevBuf win_df;   /* float2[(wdeg+1) * w]: the same as FP32 pairs (double-float path) */
     DevBuf win32;    /* float: FP32C window + derivative polynomials (plans with dlp) */
-    DevBuf win_pc;   /* float2: 4-piece window (+ derivative) polynomials of the double-float
+    DevBuf win_pc;   /* float2: kWinPieces-piece window (+ derivative) polynomials of the double-float
                         window kernel, degree pdeg */
     int pdeg;
     int wdeg;

@@ -313,14 +313,14 @@ __device__ __forceinline__ void windows_piece(const df32 *c, df32 x, df32 (&p)[W
 }
 
 /* double-float window values per point (see launch_point_windows_df): one thread per point,
- * Horner in double-float on the 4-piece per-tap polynomials staged in shared memory (piece h of
- * u = l0 - t + w/2 in [0, 1) is [h/4, (h+1)/4), argument x = 8u - 2h - 1) */
+ * Horner in double-float on the kWinPieces-piece per-tap polynomials staged in shared memory
+ * (piece h of u = l0 - t + w/2 in [0, 1) is [h/P, (h+1)/P), argument x = 2P u - 2h - 1) */
 template <int W>
 __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
                                    const int *__restrict__ count, const float2 *__restrict__ coef,
                                    int deriv, int64_t pitch, float2 *__restrict__ out)
 {
-    constexpr int NP = 4, D = kPieceDeg[W];
+    constexpr int NP = kWinPieces, D = kPieceDeg[W];
     extern __shared__ __align__(16) unsigned char sm[];
     df32 *cw = reinterpret_cast<df32 *>(sm);
     const int m = NP * (D + 1) * W + (deriv ? NP * D * W : 0);
@@ -644,7 +644,7 @@ cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts
 {
     if (n <= 0) return cudaSuccess;
     if (g.w < 2 || g.w > 16 || deg != kPieceDeg[g.w]) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(df32) * 4 * ((deg + 1) * g.w + (deriv ? deg * g.w : 0));
+    const size_t smem = sizeof(df32) * kWinPieces * ((deg + 1) * g.w + (deriv ? deg * g.w : 0));
     const int blocks = (int)((n + 255) / 256);
 #define YK_CALL(W)                                                                              \
     k_point_windows_df<W><<<blocks, 256, smem, st>>>(n, pts, count, coef, deriv ? 1 : 0, pitch, \
