@@ -326,35 +326,59 @@ __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
     const int m = NP * (D + 1) * W + (deriv ? NP * D * W : 0);
     for (int i = threadIdx.x; i < m; i += blockDim.x) cw[i] = df32(coef[i].x, coef[i].y);
     __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || (count && i >= (int64_t)*count)) return;
-    const double2 t = pts[i];
-    if (t.x < 0.0) return; /* outside the box: no entries */
-    /* point-major records (pitch 0: values k of point i at i * stride + k) or value-major planes
-     * (value k of point i at k * pitch + i: the interpolation's lanes then read consecutive
-     * points) */
+    const int64_t wbase = i - lane; /* the warp's first point */
+    /* every lane stays to the end (the point-major stores are warp-cooperative); lanes past the
+     * valid points or outside the box compute a dummy point and store nothing */
+    const int64_t nv = count ? min(n, (int64_t)*count) : n;
+    double2 t = make_double2(0.0, 0.0);
+    bool ok = i < nv;
+    if (ok) {
+        t = pts[i];
+        ok = t.x >= 0.0; /* outside the box: no entries */
+        if (!ok) t = make_double2(0.0, 0.0);
+    }
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
     const int stride = deriv ? 4 * W : 2 * W;
-    float2 *o = pitch ? out + i : out + (size_t)i * stride;
-    const int64_t ks = pitch ? pitch : 1;
+    /* part q (W values) of every point: value-major planes (value k of point i at k * pitch + i,
+     * the interpolation's lanes then read consecutive points) or point-major records (values
+     * i * stride + q W + a), the latter staged per warp in shared memory and written as
+     * consecutive addresses */
+    float2 *stg = reinterpret_cast<float2 *>(cw + m) + (size_t)warp * 32 * (W + 1);
+    auto emit = [&](int q, const df32 (&v)[W]) {
+        if (pitch) {
+            if (ok)
+#pragma unroll
+                for (int a = 0; a < W; ++a)
+                    out[(int64_t)(q * W + a) * pitch + i] = make_float2(v[a].hi, v[a].lo);
+            return;
+        }
+#pragma unroll
+        for (int a = 0; a < W; ++a) stg[lane * (W + 1) + a] = make_float2(v[a].hi, v[a].lo);
+        __syncwarp();
+        for (int e = lane; e < 32 * W; e += 32) {
+            const int pt = e / W, a = e - pt * W;
+            if ((okm >> pt) & 1u)
+                out[(size_t)(wbase + pt) * stride + q * W + a] = stg[pt * (W + 1) + a];
+        }
+        __syncwarp(); /* the buffer is refilled by the next part */
+    };
     const double ux = ((double)first_tap<W>(t.x) - t.x) + 0.5 * W;
     const double uy = ((double)first_tap<W>(t.y) - t.y) + 0.5 * W;
-    const int hx = min(NP - 1, (int)(ux * NP)), hy = min(NP - 1, (int)(uy * NP));
+    const int hx = max(0, min(NP - 1, (int)(ux * NP))), hy = max(0, min(NP - 1, (int)(uy * NP)));
     const df32 ax(2.0 * NP * ux - 2.0 * hx - 1.0), ay(2.0 * NP * uy - 2.0 * hy - 1.0);
     df32 p[W];
     windows_piece<W, D>(cw + hy * (D + 1) * W, ay, p);
-#pragma unroll
-    for (int a = 0; a < W; ++a) o[(a) * ks] = make_float2(p[a].hi, p[a].lo);
+    emit(0, p);
     windows_piece<W, D>(cw + hx * (D + 1) * W, ax, p);
-#pragma unroll
-    for (int a = 0; a < W; ++a) o[(W + a) * ks] = make_float2(p[a].hi, p[a].lo);
+    emit(1, p);
     if (deriv) {
         const df32 *cwd = cw + NP * (D + 1) * W;
         windows_piece<W, D - 1>(cwd + hy * D * W, ay, p);
-#pragma unroll
-        for (int a = 0; a < W; ++a) o[(2 * W + a) * ks] = make_float2(p[a].hi, p[a].lo);
+        emit(2, p);
         windows_piece<W, D - 1>(cwd + hx * D * W, ax, p);
-#pragma unroll
-        for (int a = 0; a < W; ++a) o[(3 * W + a) * ks] = make_float2(p[a].hi, p[a].lo);
+        emit(3, p);
     }
 }
 
@@ -644,9 +668,13 @@ cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts
 {
     if (n <= 0) return cudaSuccess;
     if (g.w < 2 || g.w > 16 || deg != kPieceDeg[g.w]) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(df32) * kWinPieces * ((deg + 1) * g.w + (deriv ? deg * g.w : 0));
+    /* coefficient tables, then a 32 x (w + 1) staging buffer per warp of 256 threads */
+    const size_t smem = sizeof(df32) * kWinPieces * ((deg + 1) * g.w + (deriv ? deg * g.w : 0)) +
+                        sizeof(float2) * 8 * 32 * (g.w + 1);
     const int blocks = (int)((n + 255) / 256);
+    cudaError_t e = cudaSuccess;
 #define YK_CALL(W)                                                                              \
+    if ((e = set_smem(k_point_windows_df<W>, smem)) != cudaSuccess) return e;                  \
     k_point_windows_df<W><<<blocks, 256, smem, st>>>(n, pts, count, coef, deriv ? 1 : 0, pitch, \
                                                      out)
     YK_W_DISPATCH(g.w, YK_CALL)
