@@ -168,6 +168,15 @@ def stage_work(info, ns, nt):
     }
 
 
+def workload_config(alphas, works):
+    """The workload both arms report (the reference arm samples its targets)."""
+    w = works[alphas[0]]
+    return {"workload": "starfish 1e5 boundary + ~1e6 volume sources, 1e6 targets, alpha in "
+                        + str(alphas) + ", FP64, rel tol 1e-10; set_points + eval per alpha "
+                        "per step",
+            "alphas": alphas, "n_src": int(w.n_src), "n_trg": int(w.n_trg), "tol": TOL}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -260,8 +269,7 @@ def run_reference(args, rank, world, pg):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * scale * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "starfish 1.1e6 sources + 1e6 targets, alpha in "
-                                   + str(alphas) + ", FP64 tol 1e-10", "alphas": alphas},
+            "config": workload_config(alphas, works),
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": oracle.num_threads(),
                              "kind": "oracle",
                              "sample": f"all sources x {args.ref_targets} targets per alpha per "
@@ -724,11 +732,7 @@ def main():
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "starfish 1e5 boundary + ~1e6 volume sources, 1e6 targets, "
-                               "alpha in " + str(alphas) + ", FP64, rel tol 1e-10; "
-                               "set_points + eval per alpha per step",
-                   "alphas": alphas, "n_src": works[alphas[0]].n_src,
-                   "n_trg": works[alphas[0]].n_trg, "tol": TOL,
+        "config": {**workload_config(alphas, works),
                    "grids": {str(a): plans[a].info["n_grid"] for a in alphas},
                    "l2": "inputs and grids larger than L2 (126 MB) per step; no flush",
                    "parallelism": f"replicas x{world}"},
