@@ -281,3 +281,49 @@ def test_dlp_dyadic_config_two_boundary():
     u = run_dl_dy(6250, alpha, delta, J, xt, yt)
     ref = OL.dlp_dyadic_starfish(alpha, delta, J, OL.StarfishGeom(), OL.starfish_density, xt, yt)
     assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) <= TOL
+
+
+# ------------------------------------------------------------------------------------------------
+# edge cases: the closed-form branch of V_L (c2 >= 0.5), another panel order, targets at panel
+# junctions (Newton moves across panel ends), no targets
+
+def test_vp_local_closed_form_branch():
+    # alpha sqrt(delta*) = 0.95: the lemma's printed closed forms, not the small-c2 series
+    alpha, dstar = 300.0, 1e-5
+    rl = OL.locality_radius(alpha, dstar)
+    xt, yt = inside_targets(2000, rl, seed=21)
+    u = run_vp(32, alpha, dstar, xt, yt)
+    ref = OL.vp_local_starfish(alpha, dstar, OL.StarfishGeom(), OL.sincos_field(), xt, yt)
+    assert np.max(np.abs(u - ref)) <= TOL * np.max(np.abs(ref))
+
+
+def test_slp_local_ten_point_panels_and_junctions():
+    yk = _yk()
+    alpha, dstar, n_panels, q = 10.0, 1e-5, 128, 10
+    rl = OL.locality_radius(alpha, dstar)
+    xb, yb, _, tb = W.boundary_nodes(W.Starfish(), n_panels, q)
+    sig = W.boundary_density(tb)
+    # targets off the panel junctions (parameters 2 pi p / n_panels) and at random parameters
+    g = OL.StarfishGeom()
+    tj = 2 * np.pi * np.arange(n_panels) / n_panels
+    p, d1, _ = g.derivs(tj)
+    nrm = np.hypot(d1[0], d1[1])
+    off = np.linspace(-0.9, 0.9, n_panels) * rl
+    xj, yj = p[0] + off * d1[1] / nrm, p[1] - off * d1[0] / nrm
+    xr, yr = near_targets(1000, 0.9 * rl, seed=22)
+    xt, yt = np.r_[xj, xr], np.r_[yj, yr]
+    u = yk.slp_local(alpha, dstar, dev(xb), dev(yb), dev(sig), dev(xt), dev(yt), q=q)
+    torch.cuda.synchronize()
+    ref = OL.slp_local_starfish(alpha, dstar, g, OL.starfish_density, xt, yt)
+    assert np.max(np.abs(u.cpu().numpy() - ref)) <= TOL * np.max(np.abs(ref))
+
+
+def test_local_parts_without_targets():
+    yk = _yk()
+    xb, yb, _, tb = W.boundary_nodes(W.Starfish(), 32, 16)
+    b = (dev(xb), dev(yb), dev(W.boundary_density(tb)))
+    e = dev(np.zeros(0))
+    assert yk.slp_local(10.0, 1e-5, *b, e, e, q=16).numel() == 0
+    assert yk.slp_dyadic(10.0, 1e-4, 2, *b, e, e, q=16).numel() == 0
+    assert yk.dlp_dyadic(10.0, 1e-4, 2, *b, e, e, q=16).numel() == 0
+    assert yk.vp_local(10.0, 1e-5, b[0], b[1], e, e, dev(np.zeros(0)), q=16).numel() == 0
