@@ -14,11 +14,14 @@ their kernels overlap and, end to end, one alpha's host copies overlap another's
 `value` = source+target points of all alphas and ranks per second of device time (CUDA events on
 the main stream around the fork to and join from the three streams, max over ranks).  `e2e` = the
 same through the C ABI with page-locked host buffers, host<->device copies inside the timed
-region.  `roofline` = the stage with the largest device time, against the measured ALU peak
-(double-float stages: FP32 FMA rate / DF_COST) or the measured HBM copy bandwidth; its durations
-come from the timed region (overlapping streams), `achieved_alone` from the kernels run alone.  `cpu_baseline` = the
-FP64 oracle (direct pair sum) on the host cores for a bounded sample of targets, scaled to a full
-evaluation.  `--impl reference` times that oracle alone as the reference arm.
+region.  `roofline` = the stage with the largest device time (each alpha run alone), its
+algorithmic flops (the method's: N_s (2w^2 + 2w) for the spread) against the measured rate of the
+arithmetic it is built from (double-float multiply-add chains, yk_fma_peak) and its algorithmic
+bytes against the measured HBM copy bandwidth; durations from the timed region (overlapping
+streams), `alone` from the kernels run one alpha at a time.  `fp32c.roofline` is the same for the
+FP32C step.  `cpu_baseline` = the FP64 oracle (direct pair sum) on the host cores for a bounded
+sample of targets, scaled to a full evaluation; `error_vs_oracle` = the timed step's results on
+that sample.  `--impl reference` times that oracle alone as the reference arm.
 """
 import argparse
 import json
@@ -41,7 +44,6 @@ METRIC = "source+target points/s at rel err 1e-10 (FP64) & 1e-6 (FP32); p50/p99 
 ALPHAS = (1.0, 10.0, 100.0)
 TOL = 1e-10
 L2_BYTES = 126 * 1024 * 1024
-DF_COST = 10  # FP32 operations per double-float add or multiply (two-sum / two-product)
 
 
 def parse():
@@ -142,30 +144,51 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------------------------
 # algorithmic work per stage (per launch), used for the roofline of the dominant stage
-def stage_work(info, ns, nt):
-    """(bytes, fp64 flops) each stage must move / compute at minimum for one launch.
+def stage_work(info, ns, nt, b=8):
+    """(bytes, flops) each stage must move / compute for one launch, counting the method's work
+    only: b bytes per real (8 FP64, 4 FP32C), G = n^2 grid cells.
 
-    The double-float path computes every point's window values once, in the set-up stages
-    (bin_src: sources, bin_trg: targets), by Horner on per-tap polynomials of degree w - 1 (2 flops
-    per step); the spread and the interpolation read them (16 bytes per point and tap pair).
+    * spread: 3 b N_s in (two coordinates and a strength per source) and b G out; N_s (2w^2 + 2w)
+      flops (w^2 taps of one multiply and one add, plus the strength times the w y-windows and
+      the w x-windows).
+    * interp: b G in, 3 b N_t (two coordinates in, one value out); N_t (2w^2 + 2w) flops.
+    * FFT passes: the pruned passes' own reads and writes of the grid and the half spectrum,
+      5 L log2 L flops per complex L-point transform.
+    * bin_src / bin_trg (set-up): 2 b per point in and the sorted layout (a grid coordinate pair
+      and an index) out; the window values per point: 2w values by Horner of degree w - 1.
+    What the resident layout adds on top (per-point window records read by the spread and the
+    interpolation) is reported apart as `layout_bytes`, not counted as the method's work.
     """
     n, M, w = info["n_grid"], info["n_modes"], info["w"]
     G = n * n
     L = n // 2
-    entries = ns * (1 + (w - 1) / info["tile"]) ** 2  # windows spread into each tile they touch
-    win = 2 * (w - 1)                                 # flops per window value
+    win = 2 * (w - 1)                                 # flops per window value (Horner, deg w-1)
     fft_row = 5 * L * math.log2(L) + 12 * L   # complex FFT of n/2 points + real post-processing
     fft_col = 5 * n * math.log2(n)
+    c = 2 * b                                          # bytes of a complex value
     return {
-        "bin_src": (ns * (16 + 16 + 4 * 3 + 16 * w) + entries * 20, ns * (20 + 2 * w * win)),
-        "bin_trg": (nt * (16 + 16 + 4 * 3 + 16 * w) + nt * 20, nt * (20 + 2 * w * win)),
-        "spread": (entries * (20 + 16 * w) + ns * 16 + G * 8, entries * (2 * w * w + 2 * w)),
-        "row_fwd": (G * 8 + (M + 1) * n * 16, n * fft_row),
-        "columns": (2 * (M + 1) * n * 16 + (M + 1) * (2 * M + 1) * 8,
+        "bin_src": (ns * (2 * b + 2 * b + 4), ns * 2 * w * win),
+        "bin_trg": (nt * (2 * b + 2 * b + 4), nt * 2 * w * win),
+        "spread": (3 * b * ns + b * G, ns * (2 * w * w + 2 * w)),
+        "row_fwd": (b * G + (M + 1) * n * c, n * fft_row),
+        "columns": (2 * (M + 1) * n * c + (M + 1) * (2 * M + 1) * b,
                     (M + 1) * (2 * fft_col + 6 * n)),
-        "row_inv": ((M + 1) * n * 16 + G * 8, n * fft_row),
-        "interp": (G * 8 + nt * (28 + 16 * w), nt * (2 * w * w + 2 * w)),
+        "row_inv": ((M + 1) * n * c + b * G, n * fft_row),
+        "interp": (b * G + 3 * b * nt, nt * (2 * w * w + 2 * w)),
     }
+
+
+def layout_bytes(info, ns, nt):
+    """Bytes per launch the FP64 path's resident layout adds: per-point window records (2w
+    double-float values of 8 bytes) read by the spread and the interpolation."""
+    w = info["w"]
+    return {"spread": ns * 16 * w, "interp": nt * 16 * w}
+
+
+def algorithmic_bytes_eval(info, ns, nt, b):
+    """Section 8(d) bytes of one evaluation: points b (3 N_s + 3 N_t) plus ten grid sweeps."""
+    G = info["n_grid"] ** 2
+    return b * (3 * ns + 3 * nt) + 10 * G * b
 
 
 def workload_config(alphas, works):
@@ -207,12 +230,95 @@ def load_traffic():
     return d.get("bytes_per_launch", {})
 
 
+LAT_SAMPLES = 200  # evaluations per alpha behind each p50/p99
+
+
+def latency_samples(torch, plans, dbufs, outs, lanes, alphas, n=LAT_SAMPLES):
+    """Device time of single yk_eval_longrange calls on a resident layout (events around each
+    call on the plan's stream, synchronised per call): n samples per alpha."""
+    lat = []
+    for a in alphas:
+        d = dbufs[a][5]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n)]
+        for s0, s1 in ev:
+            s0.record(lanes[a])
+            plans[a].eval(d, out=outs[a])
+            s1.record(lanes[a])
+            s1.synchronize()
+        lat.extend(s0.elapsed_time(s1) for s0, s1 in ev)
+    return lat
+
+
+def roofline(stage_ms, stage_ms_alone, plans, works, alphas, peaks, hbm_peak, peak_kind, b, df):
+    """Roofline block of the dominant stage (largest summed device time over the alphas when
+    each kernel runs alone): algorithmic flops against the measured rate of the arithmetic the
+    stage is built from, and algorithmic bytes against the measured HBM copy bandwidth."""
+    def totals(sms):
+        tot, wb, wf, lb = {}, {}, {}, {}
+        for a in alphas:
+            info = plans[a].info
+            sw = stage_work(info, works[a].n_src, works[a].n_trg, b)
+            lay = layout_bytes(info, works[a].n_src, works[a].n_trg) if df else {}
+            for k, v in sms[a].items():
+                if v is None:
+                    continue
+                tot[k] = tot.get(k, 0.0) + v
+                wb[k] = wb.get(k, 0.0) + sw[k][0]
+                wf[k] = wf.get(k, 0.0) + sw[k][1]
+                lb[k] = lb.get(k, 0.0) + lay.get(k, 0)
+        return tot, wb, wf, lb
+
+    tot, wb, wf, lb = totals(stage_ms)
+    tot1, _, _, _ = totals(stage_ms_alone)
+    dom = max(tot1, key=tot1.get)
+    if df:
+        # the FP64 path's spread accumulates with the unnormalised double-float multiply-add, the
+        # other stages with the renormalised one (both measured by yk_fma_peak)
+        key = "df_lazy" if dom == "spread" else "df"
+        note = ("double-float multiply-add chains measured by yk_fma_peak (%s form), 2 "
+                "FP64-equivalent flops each" % ("unnormalised" if key == "df_lazy" else
+                                                "renormalised"))
+    else:
+        key = "fp32"
+        note = "FP32 FMA chains measured by yk_fma_peak"
+    alu_peak = peaks[key]
+    t_in, t_al = tot[dom] * 1e-3, tot1[dom] * 1e-3
+    alu_in, alu_al = wf[dom] / t_in / 1e12, wf[dom] / t_al / 1e12
+    hbm_in, hbm_al = wb[dom] / t_in / 1e9, wb[dom] / t_al / 1e9
+    fa, fh = alu_in / alu_peak, hbm_in / hbm_peak
+    alu = fa >= fh
+    traffic = load_traffic().get(dom) if df else None
+    return {"bound": "alu" if alu else "hbm",
+            "achieved": alu_in if alu else hbm_in, "peak": alu_peak if alu else hbm_peak,
+            "unit": "TFLOP/s" if alu else "GB/s", "frac": fa if alu else fh,
+            "traffic": traffic, "kernel": dom, "launches_per_step": len(alphas),
+            "peak_source": note if alu else f"HBM copy bandwidth, {peak_kind} "
+                                              "(MEASURED_PEAKS.json)",
+            "frac_alu": fa, "frac_hbm": fh, "alu_peak_tflops": alu_peak,
+            "hbm_peak_gbs": hbm_peak, "alu_achieved_tflops": alu_in, "hbm_achieved_gbs": hbm_in,
+            "algorithmic_flops_per_step": wf[dom], "algorithmic_bytes_per_step": wb[dom],
+            "layout_bytes_per_step": lb.get(dom, 0),
+            "durations": "CUDA events around the stage on its stream in the timed region, where "
+                         "the alphas' streams overlap (so the durations include other streams' "
+                         "kernels), summed over the alphas",
+            "alone": {"alu_achieved_tflops": alu_al, "hbm_achieved_gbs": hbm_al,
+                      "frac_alu": alu_al / alu_peak, "frac_hbm": hbm_al / hbm_peak,
+                      "what": "the same stage with each alpha run alone (no other stream "
+                              "running)"},
+            "measured_peaks_tflops": peaks}
+
+
 # ---------------------------------------------------------------------------------------------
-def cpu_baseline(alphas, n_targets):
-    """FP64 oracle, all sources x a bounded sample of targets, scaled to full evaluations."""
+def cpu_baseline(alphas, n_targets, results=None):
+    """FP64 oracle, all sources x a bounded sample of targets, scaled to full evaluations.
+
+    results: {name: {alpha: u at all targets}} from the GPU runs; each gets its relative L-inf
+    error against the oracle on the sampled targets, max |u - u_oracle| / max |u_oracle|."""
     import oracle
     total_pts = 0.0
     total_t = 0.0
+    errors = {name: {} for name in (results or {})}
     for a in alphas:
         work = W.config_large(a)
         rng = np.random.default_rng(1)
@@ -220,16 +326,21 @@ def cpu_baseline(alphas, n_targets):
         table = oracle.GHTable(a, _delta(work, a), oracle.pair_rmax(work.xs, work.ys, work.xt,
                                                                       work.yt))
         t0 = time.perf_counter()
-        oracle.direct_sum(a, _delta(work, a), work.xs, work.ys, work.q, work.xt[idx],
-                          work.yt[idx], table=table)
+        ref = oracle.direct_sum(a, _delta(work, a), work.xs, work.ys, work.q, work.xt[idx],
+                                work.yt[idx], table=table)
         dt = time.perf_counter() - t0
         total_t += dt * work.n_trg / n_targets           # time of the full evaluation
         total_pts += work.n_src + work.n_trg
-    return {"value": total_pts / total_t, "unit": "points/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": (f"FP64 direct pair sum over all {int(W.config_large(alphas[0]).n_src)} "
-                       f"sources for {n_targets} of the 1e6 targets at each alpha in "
-                       f"{list(alphas)}; time scaled by 1e6/{n_targets} to a full evaluation")}
+        for name, res in (results or {}).items():
+            if res is not None and a in res:
+                errors[name][str(a)] = float(np.max(np.abs(res[a][idx] - ref)) /
+                                             np.max(np.abs(ref)))
+    out = {"value": total_pts / total_t, "unit": "points/s", "cores": oracle.num_threads(),
+           "kind": "oracle",
+           "sample": (f"FP64 direct pair sum over all {int(W.config_large(alphas[0]).n_src)} "
+                      f"sources for {n_targets} of the 1e6 targets at each alpha in "
+                      f"{list(alphas)}; time scaled by 1e6/{n_targets} to a full evaluation")}
+    return out, errors
 
 
 def _delta(work, alpha):
@@ -432,17 +543,11 @@ def main():
     pts_step = sum(works[a].n_src + works[a].n_trg for a in alphas)
     value = pts_step * world / (ms_step * 1e-3)
 
-    # per-eval latency distribution (device events per call)
-    lat = []
-    for a in alphas:
-        xs, ys, w, xt, yt, d = dbufs[a]
-        for _ in range(5):
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s0.record(lanes[a])
-            plans[a].eval(d, out=outs[a])
-            s1.record(lanes[a])
-            torch.cuda.synchronize()
-            lat.append(s0.elapsed_time(s1))
+    # the step's results, kept for the per-alpha error against the oracle sample
+    u_fp64 = {a: outs[a].cpu().numpy().copy() for a in alphas}
+
+    # per-eval latency distribution (device events per call, LAT_SAMPLES calls per alpha)
+    lat = latency_samples(torch, plans, dbufs, outs, lanes, alphas)
 
     # cold: plan creation (parameters, multiplier, FFT tables) + set_points + eval, host wall time
     cold_ms = {}
@@ -502,57 +607,15 @@ def main():
 
     # roofline of the dominant stage (largest device time per step)
     hbm_peak, peak_kind = load_peaks()
-    fp64_peak = yk.fma_peak_tflops(yk.YK_FP64)
-    fp32_peak = yk.fma_peak_tflops(yk.YK_FP32C)
-
-    def stage_totals(sms):
-        tot, work_b, work_f = {}, {}, {}
-        for a in alphas:
-            sw = stage_work(plans[a].info, works[a].n_src, works[a].n_trg)
-            for k, v in sms[a].items():
-                if v is None:
-                    continue
-                tot[k] = tot.get(k, 0.0) + v
-                work_b[k] = work_b.get(k, 0.0) + sw[k][0]
-                work_f[k] = work_f.get(k, 0.0) + sw[k][1]
-        return tot, work_b, work_f
-
-    tot, work_b, work_f = stage_totals(stage_ms)
-    tot1, _, _ = stage_totals(stage_ms_alone)
-    dom = max(tot1, key=tot1.get)  # the costliest stage when each kernel runs alone
-    t_dom = tot[dom] * 1e-3
-    gbs = work_b[dom] / t_dom / 1e9
-    tfl = work_f[dom] / t_dom / 1e12
-    t_dom1 = tot1[dom] * 1e-3
-    traffic = load_traffic().get(dom)
-    # the FP64 path computes spread, FFTs and interpolation in FP32 pairs (double-float)
-    # (the set-up stages' arithmetic is the double-float window kernel)
-    df_stage = dom in ("bin_src", "bin_trg", "spread", "row_fwd", "columns", "row_inv", "interp")
-    alu_peak = fp32_peak / DF_COST if df_stage else fp64_peak
-    if tfl / alu_peak >= gbs / hbm_peak:
-        roof = {"bound": "alu", "achieved": tfl, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": tfl / alu_peak, "traffic": traffic}
-        peak_note = ("FP32 FMA rate measured by yk_fma_peak / %d FP32 ops per double-float "
-                     "flop" % DF_COST) if df_stage else "FP64 FMA rate measured by yk_fma_peak"
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": gbs / hbm_peak, "traffic": traffic}
-        peak_note = f"HBM copy bandwidth, {peak_kind} (MEASURED_PEAKS.json)"
-    roof.update({"kernel": dom, "launches_per_step": len(alphas), "peak_source": peak_note,
-                 "hbm_achieved_gbs": gbs, "alu_achieved_tflops": tfl,
-                 "fp64_peak_tflops": fp64_peak, "fp32_peak_tflops": fp32_peak,
-                 "durations": "CUDA events around the stage on its stream in the timed region, "
-                              "where the three alphas' streams overlap (so the durations include "
-                              "other streams' kernels)",
-                 "achieved_alone": (work_f[dom] / t_dom1 / 1e12 if roof["unit"] == "TFLOP/s"
-                                    else work_b[dom] / t_dom1 / 1e9),
-                 "frac_alone": ((work_f[dom] / t_dom1 / 1e12 if roof["unit"] == "TFLOP/s"
-                                 else work_b[dom] / t_dom1 / 1e9) / roof["peak"]),
-                 "alone": "the same stage timed with one alpha at a time, no other stream running"})
+    peaks = {"fp64": yk.fma_peak_tflops(yk.YK_FP64), "fp32": yk.fma_peak_tflops(yk.YK_FP32C),
+             "df": yk.fma_peak_tflops(yk.YK_PEAK_DF),
+             "df_lazy": yk.fma_peak_tflops(yk.YK_PEAK_DF_LAZY)}
+    roof = roofline(stage_ms, stage_ms_alone, plans, works, alphas, peaks, hbm_peak, peak_kind,
+                    b=8, df=True)
 
     # the FP32C form of the same workload (FP32 spread/FFT/interp, two-sum grid sums, FP64
     # final sums at the targets; relative accuracy 1e-6)
-    fp32c = None
+    fp32c, u_fp32c = None, None
     if not args.no_fp32c:
         plans32 = {a: yk.Plan(a, tol=1e-6, precision=yk.YK_FP32C, h_vol=works[a].h_vol,
                               box=works[a].box, profile=True, stream=lanes[a]) for a in alphas}
@@ -577,22 +640,38 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms32 = max_over_ranks(pg, e0.elapsed_time(e1) / args.steps)
-        st32 = {str(a): plans32[a].stage_times() for a in alphas}
-        lat32 = []
-        for a in alphas:
-            for _ in range(5):
-                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s0.record(lanes[a])
-                plans32[a].eval(dbufs[a][5], out=outs[a])
-                s1.record(lanes[a])
+        st32 = {a: plans32[a].stage_times() for a in alphas}
+        u_fp32c = {a: outs[a].cpu().numpy().copy() for a in alphas}
+        lat32 = latency_samples(torch, plans32, dbufs, outs, lanes, alphas)
+        # each alpha alone: stage durations without the other streams, and the evaluation
+        # stages' Section 8(d) bytes per second against the HBM copy bandwidth
+        for _ in range(3):
+            for a in alphas:
+                xs, ys, w, xt, yt, d = dbufs[a]
+                plans32[a].set_points(xs, ys, w, xt, yt)
+                plans32[a].eval(d, out=outs[a])
                 torch.cuda.synchronize()
-                lat32.append(s0.elapsed_time(s1))
+        st32_alone = {a: plans32[a].stage_times() for a in alphas}
+        eval_hbm = {}
+        for a in alphas:
+            ms_e = sum(v for k, v in st32_alone[a].items()
+                       if k not in ("bin_src", "bin_trg") and v)
+            by = algorithmic_bytes_eval(plans32[a].info, works[a].n_src, works[a].n_trg, 4)
+            eval_hbm[str(a)] = {"eval_ms": ms_e, "algorithmic_bytes": by,
+                                "gbs": by / (ms_e * 1e-3) / 1e9,
+                                "frac_hbm": by / (ms_e * 1e-3) / 1e9 / hbm_peak}
+        roof32 = roofline(st32, st32_alone, plans32, works, alphas, peaks, hbm_peak, peak_kind,
+                          b=4, df=False)
         fp32c = {"value": pts_step * world / (ms32 * 1e-3), "unit": "points/s",
                  "ms_per_step": ms32, "tol": 1e-6, "dtype": "f32 (two-sum grid, f64 final sums)",
                  "grids": {str(a): plans32[a].info["n_grid"] for a in alphas},
-                 "stage_ms": st32,
+                 "stage_ms": {str(a): v for a, v in st32.items()},
+                 "stage_ms_alone": {str(a): v for a, v in st32_alone.items()},
+                 "roofline": roof32,
+                 "eval_only_hbm": eval_hbm,
                  "latency_ms": {"p50": float(np.percentile(lat32, 50)),
-                                "p99": float(np.percentile(lat32, 99))}}
+                                "p99": float(np.percentile(lat32, 99)),
+                                "samples": len(lat32)}}
         for a in alphas:
             plans32[a].close()
 
@@ -720,9 +799,13 @@ def main():
     batch = None if args.no_batch else batch_section(yk, torch, rank)
     serving = None if args.no_serving else serving_section(yk, args.serve_requests)
 
-    cpu = None
+    cpu, errors = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(alphas, args.cpu_targets)
+        cpu, errors = cpu_baseline(alphas, args.cpu_targets,
+                                   {"fp64": u_fp64, "fp32c": u_fp32c})
+        errors["what"] = (f"relative L-inf error max|u - u_oracle| / max|u_oracle| on the "
+                          f"{args.cpu_targets} sampled targets per alpha of the timed step's "
+                          f"results; bars 1e-10 (fp64) and 1e-6 (fp32c)")
 
     launches_per_eval = 5
     # count, three scan passes, fill for sources and for targets; three for the tile order
@@ -749,7 +832,10 @@ def main():
         "eval_only": {"ms_per_step": eval_only_ms,
                       "value": pts_step * world / (eval_only_ms * 1e-3) if eval_only_ms else None},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "what": "one yk_eval_longrange on a resident layout, all alphas"},
+                       "samples": len(lat),
+                       "what": f"one yk_eval_longrange on a resident layout, {LAT_SAMPLES} calls "
+                               f"per alpha"},
+        "error_vs_oracle": errors,
         "fp32c": fp32c,
         "double_layer": dlp,
         "slp_local": local,

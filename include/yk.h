@@ -338,10 +338,15 @@ YK_API yk_status yk_tune_cache_load(const char *path);
 YK_API void yk_tune_cache_clear(void);
 
 /*
- * yk_fma_peak: measured FMA throughput of the current device in TFLOP/s (2 flops per FMA) for
- * precision YK_FP64 or YK_FP32C (FP32), from independent FMA chains on every SM.  A diagnostic
- * used to report ALU-bound kernels against a measured peak; the paper has no counterpart.
+ * yk_fma_peak: measured FMA throughput of the current device in TFLOP/s (2 flops per FMA) from
+ * independent chains on every SM, for `precision` = YK_FP64 (FP64 FMA), YK_FP32C (FP32 FMA),
+ * YK_PEAK_DF (the double-float multiply-add acc + a*b with a renormalised result, the building
+ * block of the FP64 path's FFT passes and interpolation) or YK_PEAK_DF_LAZY (its unnormalised
+ * form, the spread's per-tap operation); a double-float multiply-add counts as 2 FP64-equivalent
+ * flops.  Other values: YK_ERR_ARG.  A diagnostic used to report ALU-bound kernels against a
+ * measured peak; the paper has no counterpart.
  */
+enum { YK_PEAK_DF = 2, YK_PEAK_DF_LAZY = 3 };
 YK_API yk_status yk_fma_peak(int precision, double *tflops);
 
 /*

@@ -24,6 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 YK_OK, YK_ERR_ARG, YK_ERR_OOM, YK_ERR_CUDA, YK_ERR_TIMEOUT, YK_ERR_STATE, YK_ERR_INTERNAL, \
     YK_ERR_UNSUPPORTED = range(8)
 YK_FP64, YK_FP32C = 0, 1
+YK_PEAK_DF, YK_PEAK_DF_LAZY = 2, 3  # yk_fma_peak: double-float multiply-add chains
 _STATUS = {0: "YK_OK", 1: "YK_ERR_ARG", 2: "YK_ERR_OOM", 3: "YK_ERR_CUDA", 4: "YK_ERR_TIMEOUT",
            5: "YK_ERR_STATE", 6: "YK_ERR_INTERNAL", 7: "YK_ERR_UNSUPPORTED"}
 
@@ -121,6 +122,39 @@ def _ptr(a, keep: list):
     return a.ctypes.data if a.size else None
 
 
+def _out_ptr(a, keep: list):
+    """Pointer of an output array, which the library writes in place: a copy would leave the
+    caller's array unchanged, so a non-contiguous or non-float64 output is refused, not copied."""
+    if a is None:
+        return None
+    torch = _torch()
+    if torch is not None and isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("outputs must be contiguous float64 tensors (written in place)")
+        keep.append(a)
+        return a.data_ptr() if a.numel() else None
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+            and a.flags.writeable):
+        raise TypeError("outputs must be writable C-contiguous float64 numpy arrays")
+    keep.append(a)
+    return a.ctypes.data if a.size else None
+
+
+def _dev_ptr(a, keep: list):
+    """Pointer of a contiguous float64 tensor on the current CUDA device, with no conversion or
+    copy (a copy would be a device allocation, and for an output a silent wrong result)."""
+    torch = _torch()
+    if torch is None or not isinstance(a, torch.Tensor) or not a.is_cuda:
+        raise TypeError("every array must be a CUDA tensor")
+    if a.dtype != torch.float64 or not a.is_contiguous():
+        raise TypeError("every array must be a contiguous float64 tensor")
+    if a.device.index != torch.cuda.current_device():
+        raise TypeError(f"tensor on {a.device}, but the current device is "
+                        f"cuda:{torch.cuda.current_device()}")
+    keep.append(a)
+    return a.data_ptr() if a.numel() else None
+
+
 def _len(a) -> int:
     if a is None:
         return 0
@@ -130,7 +164,10 @@ def _len(a) -> int:
 def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
               box=(-1.5, 1.5, -1.5, 1.5), kmax=0.0, kmax_rule=0, period=0.0, tile=0,
               profile=False, stream=None, use_tuned=False, n_src_hint=0,
-              fft_fp64=False, dlp=False, truncate=0) -> Opts:
+              fft_fp64=False, dlp=False, truncate=0, allocator=None) -> Opts:
+    """Plan options.  allocator (optional): an object with alloc(nbytes, stream) -> device
+    address (0 when it cannot allocate: the library then returns YK_ERR_OOM) and
+    free(address, stream), used for every device buffer of the plan instead of cudaMalloc."""
     o = Opts()
     _lib.yk_opts_default(ctypes.byref(o))
     o.precision = int(precision)
@@ -151,6 +188,11 @@ def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
     o.fft_fp64 = 1 if fft_fp64 else 0
     o.dlp = 1 if dlp else 0
     o.truncate = int(truncate)
+    if allocator is not None:
+        a_cb = _ALLOC(lambda nbytes, stream, ctx: allocator.alloc(int(nbytes), stream) or None)
+        f_cb = _FREE(lambda ptr, stream, ctx: allocator.free(int(ptr), stream))
+        o.alloc, o.free = a_cb, f_cb
+        o._callbacks = (a_cb, f_cb)  # the plan holds its options: the callbacks stay alive
     return o
 
 
@@ -237,11 +279,11 @@ class Plan:
                 out = np.empty(self.n_trg, dtype=np.float64)
         keep = []
         if mu is None:
-            _check(_lib.yk_eval_longrange(self._h, _ptr(density, keep), _ptr(out, keep)),
+            _check(_lib.yk_eval_longrange(self._h, _ptr(density, keep), _out_ptr(out, keep)),
                    "yk_eval_longrange")
         else:
             _check(_lib.yk_eval_longrange_dl(self._h, _ptr(density, keep), _ptr(mu, keep),
-                                             _ptr(out, keep)), "yk_eval_longrange_dl")
+                                             _out_ptr(out, keep)), "yk_eval_longrange_dl")
         self._keep_eval = keep
         return out
 
@@ -323,7 +365,7 @@ class Batch:
         n = len(self.plans)
         keep = []
         dp = (_vp * n)(*[_ptr(d, keep) for d in densities])
-        up = (_vp * n)(*[_ptr(u, keep) for u in outs])
+        up = (_vp * n)(*[_out_ptr(u, keep) for u in outs])
         _check(_lib.yk_batch_run(self._h, dp, up), "yk_batch_run")
         self._keep = keep
         return outs
@@ -349,7 +391,7 @@ def batch_eval(plans, densities, outs):
     keep = []
     hp = (_vp * n)(*[p.handle for p in plans])
     dp = (_vp * n)(*[_ptr(d, keep) for d in densities])
-    up = (_vp * n)(*[_ptr(u, keep) for u in outs])
+    up = (_vp * n)(*[_out_ptr(u, keep) for u in outs])
     _check(_lib.yk_batch_eval(hp, dp, up, n), "yk_batch_eval")
     return outs
 
@@ -373,7 +415,7 @@ def slp_local(alpha, delta_star, xb, yb, sigma, xt, yt, q=16, out=None, stream=N
     keep = []
     _check(_lib.yk_slp_local(float(alpha), float(delta_star), nb // q, int(q), _ptr(xb, keep),
                              _ptr(yb, keep), _ptr(sigma, keep), nt, _ptr(xt, keep),
-                             _ptr(yt, keep), _ptr(out, keep), stream), "yk_slp_local")
+                             _ptr(yt, keep), _out_ptr(out, keep), stream), "yk_slp_local")
     return out
 
 
@@ -396,7 +438,7 @@ def slp_dyadic(alpha, delta, J, xb, yb, sigma, xt, yt, q=16, out=None, stream=No
     keep = []
     _check(_lib.yk_slp_dyadic(float(alpha), float(delta), int(J), nb // q, int(q),
                               _ptr(xb, keep), _ptr(yb, keep), _ptr(sigma, keep), nt,
-                              _ptr(xt, keep), _ptr(yt, keep), _ptr(out, keep), stream),
+                              _ptr(xt, keep), _ptr(yt, keep), _out_ptr(out, keep), stream),
            "yk_slp_dyadic")
     return out
 
@@ -419,7 +461,7 @@ def dlp_dyadic(alpha, delta, J, xb, yb, mu, xt, yt, q=16, out=None, stream=None)
     keep = []
     _check(_lib.yk_dlp_dyadic(float(alpha), float(delta), int(J), nb // q, int(q),
                               _ptr(xb, keep), _ptr(yb, keep), _ptr(mu, keep), nt,
-                              _ptr(xt, keep), _ptr(yt, keep), _ptr(out, keep), stream),
+                              _ptr(xt, keep), _ptr(yt, keep), _out_ptr(out, keep), stream),
            "yk_dlp_dyadic")
     return out
 
@@ -447,7 +489,7 @@ def vp_local(alpha, delta_star, xb, yb, xt, yt, fd, q=16, out=None, stream=None)
     keep = []
     _check(_lib.yk_vp_local(float(alpha), float(delta_star), nb // q, int(q), _ptr(xb, keep),
                             _ptr(yb, keep), nt, _ptr(xt, keep), _ptr(yt, keep), _ptr(fd, keep),
-                            _ptr(out, keep), stream), "yk_vp_local")
+                            _out_ptr(out, keep), stream), "yk_vp_local")
     return out
 
 
@@ -456,7 +498,8 @@ _lib.yk_fma_peak.restype = ctypes.c_int
 
 
 def fma_peak_tflops(precision=YK_FP64) -> float:
-    """Measured FMA throughput of the current CUDA device (TFLOP/s)."""
+    """Measured FMA throughput of the current CUDA device (TFLOP/s): YK_FP64, YK_FP32C (FP32),
+    YK_PEAK_DF / YK_PEAK_DF_LAZY (double-float multiply-add, 2 FP64-equivalent flops each)."""
     v = ctypes.c_double()
     _check(_lib.yk_fma_peak(int(precision), ctypes.byref(v)), "yk_fma_peak")
     return v.value
@@ -469,15 +512,16 @@ _lib.yk_eval_longrange_static.restype = ctypes.c_int
 
 def eval_longrange_static(alpha, xs, ys, w, density, xt, yt, out, stream=None, **opts):
     """One evaluation with no device allocation: all scratch is the library's static 32 MiB
-    device array.  Every array (including `out`) must already be on the device."""
+    device array.  Every array (including `out`) must be a contiguous float64 CUDA tensor on the
+    current device: anything else raises TypeError (converting it would allocate)."""
     if stream is None:
         stream = _current_stream()
     o = make_opts(stream=stream, **opts)
     keep = []
+    ptrs = [_dev_ptr(a, keep) for a in (xs, ys, w, density, xt, yt, out)]
     msg = ctypes.create_string_buffer(512)
-    st = _lib.yk_eval_longrange_static(float(alpha), ctypes.byref(o), _len(xs), _ptr(xs, keep),
-                                       _ptr(ys, keep), _ptr(w, keep), _ptr(density, keep),
-                                       _len(xt), _ptr(xt, keep), _ptr(yt, keep), _ptr(out, keep),
+    st = _lib.yk_eval_longrange_static(float(alpha), ctypes.byref(o), _len(xs), ptrs[0], ptrs[1],
+                                       ptrs[2], ptrs[3], _len(xt), ptrs[4], ptrs[5], ptrs[6],
                                        msg, len(msg))
     if st != YK_OK:
         raise YkError(st, "yk_eval_longrange_static", msg.value.decode(errors="replace"))

@@ -9,7 +9,10 @@
  * device array of kStaticScratchBytes.  Every GPU that loads the library holds that array until
  * the process exits.  Host code cannot use the array's name as a device address, so the first
  * call on each device looks the address up with cudaGetSymbolAddress (with that device current)
- * and keeps it; that first call should come before any stream capture.  Every call shares the
+ * and keeps it for that device's current CUDA context; that first call should come before any
+ * stream capture.  The kept address is tied to the context's unique id: after cudaDeviceReset,
+ * or under another context on the same device, the module is loaded anew and the next call
+ * repeats the look-up instead of using an address of the old context.  Every call shares the
  * array: the contents left by the previous call are overwritten, everything that must start at
  * zero is cleared by the call itself, and calls whose work overlaps on the GPU (different
  * streams, or different host threads) race on the array.  The call waits for its stream.
@@ -31,7 +34,9 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
 std::mutex g_setup_mutex;
+/* per device: the scratch address and the unique id of the context it was looked up in */
 void *g_scratch_addr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];
 
 /* failure message into the caller's buffer (if any) */
 struct Msg {
@@ -46,7 +51,38 @@ yk_status static_fail(yk_status s, const char *msg, const char *detail = "")
     return s;
 }
 
-/* device address of g_scratch for the current device, looked up once per device */
+/* unique id of the calling thread's current CUDA context (driver entry points fetched through the
+ * runtime, so the library needs no link against the driver library); the runtime has made its
+ * primary context current by the time this runs (the pointer checks come first) */
+typedef int (*ctx_current_fn)(void **);
+typedef int (*ctx_id_fn)(void *, unsigned long long *);
+
+yk_status current_context_id(unsigned long long *id)
+{
+    static ctx_current_fn get_current = nullptr;
+    static ctx_id_fn get_id = nullptr;
+    if (!get_current || !get_id) { /* under g_setup_mutex */
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                         cudaEnableDefault, &q1);
+        if (e == cudaSuccess)
+            e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess || !f1 || !f2 || q1 != cudaDriverEntryPointSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            return static_fail(YK_ERR_CUDA, "driver entry points cuCtxGetCurrent/cuCtxGetId: ",
+                               e != cudaSuccess ? cudaGetErrorString(e) : "not found");
+        get_current = (ctx_current_fn)f1;
+        get_id = (ctx_id_fn)f2;
+    }
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx)
+        return static_fail(YK_ERR_CUDA, "no current CUDA context");
+    if (get_id(ctx, id) != 0) return static_fail(YK_ERR_CUDA, "cuCtxGetId failed");
+    return YK_OK;
+}
+
+/* device address of g_scratch for the current device: looked up once per device and context */
 yk_status scratch_base(void **out)
 {
     int dev = 0;
@@ -54,12 +90,16 @@ yk_status scratch_base(void **out)
     if (e != cudaSuccess) return static_fail(YK_ERR_CUDA, "cudaGetDevice: ", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return static_fail(YK_ERR_UNSUPPORTED, "device ordinal >= 64");
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long ctx = 0;
+    yk_status s = current_context_id(&ctx);
+    if (s != YK_OK) return s;
+    if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_scratch);
         if (e != cudaSuccess || !ptr)
             return static_fail(YK_ERR_CUDA, "cudaGetSymbolAddress: ", cudaGetErrorString(e));
         g_scratch_addr[dev] = ptr;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return YK_OK;
@@ -164,6 +204,8 @@ bool stages_for(int L, int n_tab, yk::FftStages &st)
     return true;
 }
 
+/* device (or managed) memory of the current device: a pointer into another GPU's memory is
+ * refused, since the kernels run on the current device */
 bool is_device(const void *p)
 {
     if (!p) return false;
@@ -172,7 +214,13 @@ bool is_device(const void *p)
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 /* bump allocator over the static array (offsets only; nothing is allocated) */
@@ -208,7 +256,8 @@ extern "C" YK_API yk_status yk_eval_longrange_static(double alpha, const yk_opts
         return static_fail(YK_ERR_UNSUPPORTED, "too many points for 32-bit entry indices");
     if ((n_src > 0 && (!is_device(xs) || !is_device(ys) || !is_device(w) || !is_device(density))) ||
         (n_trg > 0 && (!is_device(xt) || !is_device(yt) || !is_device(u))))
-        return static_fail(YK_ERR_ARG, "every array must be device memory (no staging copies)");
+        return static_fail(YK_ERR_ARG, "every array must be device memory of the current device (no "
+                                       "staging copies)");
     /* this entry point builds the plain multiplier only: no truncated kernel */
     yk_opts oc = *o;
     oc.truncate = 1;

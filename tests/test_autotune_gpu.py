@@ -2,6 +2,8 @@
 import numpy as np
 import pytest
 
+import oracle
+import oracle.params as OP
 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -29,4 +31,36 @@ def test_autotune_records_the_fastest_tile():
     ut = plan_t.eval(args[3]).cpu().numpy()
     ud = plan_d.eval(args[3]).cpu().numpy()
     assert np.max(np.abs(ut - ud)) <= 1e-6 * np.max(np.abs(ud))
+    yk.tune_cache_clear()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+def test_every_admissible_tile_and_the_tuned_plan_match_the_oracle(prec, tol):
+    """Each tile edge a plan may take (the autotuner's candidates), and the plan built from the
+    tuned cache, against the FP64 oracle at the stated tolerance (config-1 workload, alpha = 10,
+    and a larger grid at alpha = 0.5)."""
+    import paper_2606_28865_b300 as yk
+    wk = W.config_small()
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    args = [t(wk.xs), t(wk.ys), t(wk.w), t(wk.density), t(wk.xt), t(wk.yt)]
+    for alpha in (wk.alpha, 0.5):
+        ref = oracle.direct_sum(alpha, OP.delta_from_mesh(alpha, wk.h_vol), wk.xs, wk.ys, wk.q,
+                                wk.xt, wk.yt)
+        scale = np.max(np.abs(ref))
+        yk.tune_cache_clear()
+        res = yk.autotune(alpha, *args, tol=tol, precision=prec, h_vol=wk.h_vol, box=wk.box)
+        assert len(res["tried"]) >= 1
+        for tile in sorted(res["tried"]):
+            with yk.Plan(alpha, tol=tol, precision=prec, h_vol=wk.h_vol, box=wk.box,
+                         tile=int(tile)) as p:
+                assert p.info["tile"] == int(tile)
+                p.set_points(args[0], args[1], args[2], args[4], args[5])
+                u = p.eval(args[3]).cpu().numpy()
+            assert np.max(np.abs(u - ref)) <= tol * scale, (alpha, tile)
+        with yk.Plan(alpha, tol=tol, precision=prec, h_vol=wk.h_vol, box=wk.box, use_tuned=True,
+                     n_src_hint=wk.n_src) as p:
+            assert p.info["tile"] == res["best_tile"]
+            p.set_points(args[0], args[1], args[2], args[4], args[5])
+            u = p.eval(args[3]).cpu().numpy()
+        assert np.max(np.abs(u - ref)) <= tol * scale, alpha
     yk.tune_cache_clear()
