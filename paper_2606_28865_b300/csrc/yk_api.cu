@@ -480,7 +480,7 @@ void free_all(yk_plan_t p)
     DevBuf *all[] = {&p->grid, &p->spec, &p->mult, &p->tw, &p->perm_h, &p->iperm_f, &p->win,
                      &p->win_df, &p->win_pc, &p->win32, &p->wnu, &p->win_src, &p->win_dip, &p->win_trg, &p->stage_d[0], &p->stage_d[1],
                      &p->stage_d[2], &p->stage_d[3], &p->stage_d[4], &p->stage_d[5],
-                     &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->tile_order, &p->trg_cnt,
+                     &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->tile_order, &p->part, &p->trg_cnt,
                      &p->trg_ptr,
                      &p->trg_cur, &p->err, &p->w_src, &p->src_t, &p->ent_t, &p->ent_j,
                      &p->trg_t, &p->trg_idx, &p->trg_tmp, &p->stage_x, &p->stage_y,
@@ -614,6 +614,10 @@ yk_status plan_tables(yk_plan_t p)
     YK_TRY(buf_alloc(p, p->trg_cnt, sizeof(int) * nt2, "tile counts"));
     YK_TRY(buf_alloc(p, p->trg_ptr, sizeof(int) * (nt2 + 1), "tile offsets"));
     YK_TRY(buf_alloc(p, p->trg_cur, sizeof(int) * nt2, "tile cursors"));
+    if (p->fft_df) { /* owner-tile spread: one padded tile of partial sums per tile */
+        const size_t span = (size_t)p->T + p->w - 1;
+        YK_TRY(buf_alloc(p, p->part, sizeof(double) * nt2 * span * span, "padded tiles"));
+    }
 #undef YK_TRY
     if (!make_stages((int)(n / 2), (int)n, p->st_half) || !make_stages((int)n, (int)n, p->st_full))
         return fail(YK_ERR_INTERNAL, "FFT stage plan failed for n = %lld", (long long)n);
@@ -799,6 +803,7 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->order = P<int>(p->tile_order);
     d->ent_t = P<double2>(p->ent_t);
     d->ent_j = P<int>(p->ent_j);
+    d->part = p->fft_df ? p->part.ptr : nullptr;
     d->wq = P<double>(p->w_src);
     d->trg_ptr = P<int>(p->trg_ptr);
     d->trg_t = P<double2>(p->trg_t);
@@ -980,7 +985,9 @@ static int64_t predicted_bytes(const yk_plan_s *p, int64_t n_src, int64_t n_trg)
                 4 * (n / 2) + 4 * n + 4 * (7 * nt2 + 2) + 4;
     if (p->precision == YK_FP64) b += 8 * (int64_t)(p->w + 2) * p->w * (p->dlp ? 2 : 1);
     else if (p->dlp) b += 4 * (int64_t)(2 * p->w + 3) * p->w;
-    b += n_src * (8 + 16 + 4 * (16 + 4)) + n_trg * (16 + 4 + 16);
+    const int64_t epp = p->fft_df ? 1 : 4; /* entries per source */
+    b += n_src * (8 + 16 + epp * (16 + 4)) + n_trg * (16 + 4 + 16);
+    if (p->fft_df) b += 8 * nt2 * (int64_t)(p->T + p->w - 1) * (p->T + p->w - 1);
     if (p->fft_df) b += (n_src + n_trg) * 16 * (int64_t)p->w; /* per-point window values */
     return b;
 }
@@ -1098,8 +1105,10 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
     const size_t ns = (size_t)n_src, nd = (size_t)n_dip, nt = (size_t)n_trg;
     YK_TRY(buf_alloc(p, p->w_src, sizeof(double) * ns, "weights"));
     YK_TRY(buf_alloc(p, p->src_t, sizeof(double2) * (ns + nd), "source coordinates"));
-    YK_TRY(buf_alloc(p, p->ent_t, sizeof(double2) * 4 * (ns + nd), "entries"));
-    YK_TRY(buf_alloc(p, p->ent_j, sizeof(int) * 4 * (ns + nd), "entries"));
+    /* entries: one per source for the owner-tile spread, else one per tile a window touches */
+    const size_t epp = p->fft_df ? 1 : 4;
+    YK_TRY(buf_alloc(p, p->ent_t, sizeof(double2) * epp * (ns + nd), "entries"));
+    YK_TRY(buf_alloc(p, p->ent_j, sizeof(int) * epp * (ns + nd), "entries"));
     YK_TRY(buf_alloc(p, p->trg_t, sizeof(double2) * nt, "targets"));
     YK_TRY(buf_alloc(p, p->trg_idx, sizeof(int) * nt, "targets"));
     YK_TRY(buf_alloc(p, p->trg_tmp, sizeof(double2) * nt, "targets"));
@@ -1125,19 +1134,23 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
     YK_CU(yk::launch_bin_sources(g, n_src, dx, dy, n_dip, ddx, ddy, P<double2>(p->src_t),
                                  P<int>(p->tile_cnt), P<int>(p->tile_ptr), P<int>(p->tile_cur),
                                  P<double2>(p->ent_t), P<int>(p->ent_j), P<int>(p->err),
-                                 p->stream, p->precision == YK_FP32C),
+                                 p->stream, p->precision == YK_FP32C, p->fft_df != 0),
           "bin sources");
     /* the cursors are free after the fill: they serve as the ordering's scratch */
     YK_CU(yk::launch_tile_order(P<int>(p->tile_ptr), p->nt * p->nt, P<int>(p->tile_order),
                                 P<int>(p->tile_cur), p->stream),
           "tile order");
     if (p->fft_df) {
-        /* double-float path: window values once per source (they depend on positions only) */
+        /* double-float path: window values once per source (they depend on positions only),
+         * in the order of the owner-tile entries (a dipole's entry slot stays unused: dipoles
+         * keep their own records) */
         const size_t w = (size_t)p->w;
-        YK_TRY(buf_alloc(p, p->win_src, sizeof(float2) * 2 * w * ns, "source windows"));
-        YK_CU(yk::launch_point_windows_df(g, n_src, P<double2>(p->src_t), nullptr,
+        YK_TRY(buf_alloc(p, p->win_src, sizeof(float2) * 2 * w * (ns + nd), "source windows"));
+        YK_CU(yk::launch_point_windows_df(g, n_src + n_dip, P<double2>(p->src_t),
+                                          P<int>(p->tile_ptr) + (size_t)p->nt * p->nt,
                                           P<float2>(p->win_pc), p->pdeg, false,
-                                          P<float2>(p->win_src), p->stream),
+                                          P<float2>(p->win_src), p->stream, 0, P<int>(p->ent_j),
+                                          n_src),
               "source windows");
         if (nd > 0) {
             YK_TRY(buf_alloc(p, p->win_dip, sizeof(float2) * 4 * w * nd, "dipole windows"));

@@ -78,13 +78,17 @@ struct Inst {
     const float *win32;       /* FP32C with dipoles: window and derivative polynomials in FP32 */
     double dmax;              /* bound on |phi'| over the window (cells^-1), for the FP64 scale */
     /* double-float path: window values computed once per point at yk_set_points (they depend on
-     * positions only): per charge [phi(Y - t_y) taps | phi(X - t_x) taps] (2w double-floats, source
-     * order), per dipole [phi_y | phi_x | phi'_y | phi'_x] (4w), per target in tile order (2w planes
-     * of n_trg values) */
+     * positions only): per charge [phi(Y - t_y) taps | phi(X - t_x) taps] (2w double-floats, in
+     * the order of the owner-tile entries, so a batch of a tile's sources is one contiguous block),
+     * per dipole [phi_y | phi_x | phi'_y | phi'_x] (4w, source order), per target in tile order
+     * (2w planes of n_trg values) */
     const float2 *win_src, *win_dip, *win_trg;
     int64_t win_trg_pitch;    /* the target windows are value-major: value k of target e at
                                  k * win_trg_pitch + e (coalesced reads in the interpolation) */
-    int64_t pad16_;           /* keeps sizeof(Inst) a multiple of 16 (copied in 16-byte words) */
+    void *part;               /* owner-tile spread (double-float and FP32C paths): padded tile
+                                 partials, tile t's (T + w - 1)^2 cells at t (T + w - 1)^2 (FP32
+                                 pairs), folded into the grid by the row FFT's load; NULL: the
+                                 spread writes the grid itself (fixed-point FP64 path) */
     int items[ST_COUNT];      /* work items of each stage */
     int smem[ST_COUNT];       /* dynamic shared memory of each stage (bytes) */
 };
@@ -101,17 +105,22 @@ int rows_per_item(int n, bool f32);
  * f32 selects the FP32C entry layout (first tap + FP32 offset) for the binned points. */
 /* sources: ns charges (xs, ys) then nd dipoles (xd, yd); src_t holds ns + nd grid coordinates and
  * a dipole's entries carry source index ns + d */
+/* owner == false: one entry per tile a source's window touches (<= 4); owner == true: one entry
+ * per source, in the tile of its first tap (the owner-tile spread) */
 cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
                                int64_t nd, const double *xd, const double *yd, double2 *src_t,
                                int *tile_cnt, int *tile_ptr, int *tile_cur, double2 *ent_t,
-                               int *ent_j, int *err, cudaStream_t st, bool f32);
+                               int *ent_j, int *err, cudaStream_t st, bool f32,
+                               bool owner = false);
 /* double-float window values of n points at grid coordinates pts (a point with t.x < 0 lies
  * outside the box and gets none): out[i * 2w ...] as described for Inst::win_src; with deriv, 4w
  * values per point including the derivative's.  count (device, may be NULL): only the first
- * *count points are valid. */
+ * *count points are valid.  idx (device, may be NULL): point i is pts[idx[i]], and points with
+ * idx[i] >= idx_lim get no values (the owner-tile entries, whose dipoles keep their own records). */
 cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts,
                                     const int *count, const float2 *coef, int deg, bool deriv,
-                                    float2 *out, cudaStream_t st, int64_t pitch = 0);
+                                    float2 *out, cudaStream_t st, int64_t pitch = 0,
+                                    const int *idx = nullptr, int64_t idx_lim = 0);
 /* exclusive scan of cnt[0..count) into ptr[0..count]; cur (>= ceil(count / 4096) ints) is scratch
  * and is left zeroed */
 cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStream_t st);
@@ -219,6 +228,7 @@ struct yk_plan_s {
     double dmax;     /* bound on |phi'| (cells^-1) */
     DevBuf tile_cnt, tile_ptr, tile_cur; /* int[nt^2], int[nt^2+1], int[nt^2] (sources) */
     DevBuf tile_order; /* int[nt^2]: heavy-first processing order of the source tiles */
+    DevBuf part;     /* owner-tile spread: nt^2 padded tiles of (T + w - 1)^2 FP32 pairs */
     DevBuf trg_cnt, trg_ptr, trg_cur;    /* same for targets */
     DevBuf err;      /* int: device error bits */
 

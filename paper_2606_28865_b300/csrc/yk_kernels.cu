@@ -38,6 +38,18 @@ __device__ __forceinline__ bool in_box(const Geom &g, double x, double y)
  * the offset s = l0 - t in FP32, both computed from t in FP64 at set-up, so the FP32 kernels
  * never see absolute coordinates (k h |x| eps_32 would otherwise dominate the error) */
 template <int W> __device__ __forceinline__ double2 pack_f64(double2 t) { return t; }
+/* owner-tile entry: (offset of the first tap in the tile's padded copy, source index, FP32
+ * offsets s = l0 - t of both axes as for FP32C), so the spread does no FP64 rounding */
+template <int W> __device__ __forceinline__ double2 pack_owner(double2 t, const Geom &g, int j)
+{
+    const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
+    const int wx = wrap(lx, g.n), wy = wrap(ly, g.n);
+    const int off = (wy % g.T) * owner_pitch(g.T, W) + wx % g.T;
+    const float sx = (float)((double)lx - t.x), sy = (float)((double)ly - t.y);
+    double2 r;
+    *reinterpret_cast<int4 *>(&r) = make_int4(off, j, __float_as_int(sx), __float_as_int(sy));
+    return r;
+}
 template <int W> __device__ __forceinline__ double2 pack_f32c(double2 t)
 {
     const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
@@ -85,6 +97,15 @@ template <int W> __device__ __forceinline__ void src_tiles(double2 t, const Geom
     tiles[3] = (ay1 != ay0 && ax1 != ax0) ? ay1 * g.nt + ax1 : -1;
 }
 
+/* the owner tile of a source: the tile of its first tap (wrapped), whose padded (T + w - 1)^2
+ * region holds the whole w x w window; the other slots are -1 */
+template <int W> __device__ __forceinline__ void owner_tile(double2 t, const Geom &g, int tiles[4])
+{
+    const int lx = wrap(first_tap<W>(t.x), g.n), ly = wrap(first_tap<W>(t.y), g.n);
+    tiles[0] = (ly / g.T) * g.nt + lx / g.T;
+    tiles[1] = tiles[2] = tiles[3] = -1;
+}
+
 /* grid coordinates of a point and whether it lies in the plan's box (and so in the grid) */
 __device__ __forceinline__ bool grid_coords(const Geom &g, double x, double y, double2 &t)
 {
@@ -94,7 +115,7 @@ __device__ __forceinline__ bool grid_coords(const Geom &g, double x, double y, d
 
 /* the block size of the binning kernels is a multiple of 32 and every lane reaches the warp
  * collectives (no early return) */
-template <int W>
+template <int W, bool OWNER>
 __global__ void k_bin_src_count(int64_t ns, const double *__restrict__ xs,
                                 const double *__restrict__ ys, Geom g, double2 *__restrict__ src_t,
                                 int *__restrict__ cnt, int *__restrict__ err)
@@ -108,16 +129,18 @@ __global__ void k_bin_src_count(int64_t ns, const double *__restrict__ xs,
         if (!ok) {
             atomicOr(err, ERR_POINT_OUTSIDE);
             t = make_double2(-1.0, -1.0);
+        } else if (OWNER) {
+            owner_tile<W>(t, g, tiles);
         } else {
             src_tiles<W>(t, g, tiles);
         }
         src_t[j] = t;
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) agg_count(cnt, tiles[r], tiles[r] >= 0);
+    for (int r = 0; r < (OWNER ? 1 : 4); ++r) agg_count(cnt, tiles[r], tiles[r] >= 0);
 }
 
-template <int W, bool F32>
+template <int W, bool F32, bool OWNER>
 __global__ void k_bin_src_fill(int64_t ns, const double2 *__restrict__ src_t, Geom g,
                                const int *__restrict__ ptr, int *__restrict__ cur,
                                double2 *__restrict__ ent_t, int *__restrict__ ent_j, int joff)
@@ -126,10 +149,14 @@ __global__ void k_bin_src_fill(int64_t ns, const double2 *__restrict__ src_t, Ge
     int tiles[4] = {-1, -1, -1, -1};
     double2 t = make_double2(-1.0, -1.0);
     if (j < ns) t = src_t[j];
-    if (t.x >= 0.0) src_tiles<W>(t, g, tiles);
-    const double2 rec = F32 ? pack_f32c<W>(t) : pack_f64<W>(t);
+    if (t.x >= 0.0) {
+        if (OWNER) owner_tile<W>(t, g, tiles);
+        else src_tiles<W>(t, g, tiles);
+    }
+    const double2 rec = OWNER ? pack_owner<W>(t, g, (int)j + joff)
+                              : (F32 ? pack_f32c<W>(t) : pack_f64<W>(t));
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < (OWNER ? 1 : 4); ++r) {
         const bool v = tiles[r] >= 0;
         const int off = agg_reserve(cur, tiles[r], v);
         if (v) {
@@ -318,7 +345,8 @@ __device__ __forceinline__ void windows_piece(const df32 *c, df32 x, df32 (&p)[W
 template <int W>
 __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
                                    const int *__restrict__ count, const float2 *__restrict__ coef,
-                                   int deriv, int64_t pitch, float2 *__restrict__ out)
+                                   int deriv, int64_t pitch, float2 *__restrict__ out,
+                                   const int *__restrict__ idx, int64_t idx_lim)
 {
     constexpr int NP = kWinPieces, D = kPieceDeg[W];
     extern __shared__ __align__(16) unsigned char sm[];
@@ -334,8 +362,14 @@ __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
     const int64_t nv = count ? min(n, (int64_t)*count) : n;
     double2 t = make_double2(0.0, 0.0);
     bool ok = i < nv;
-    if (ok) {
+    if (ok && idx) { /* point i is pts[idx[i]]; indices >= idx_lim get no values */
+        const int k = idx[i];
+        ok = k < idx_lim;
+        if (ok) t = pts[k];
+    } else if (ok) {
         t = pts[i];
+    }
+    if (ok) {
         ok = t.x >= 0.0; /* outside the box: no entries */
         if (!ok) t = make_double2(0.0, 0.0);
     }
@@ -399,6 +433,18 @@ template <int W> __global__ void __launch_bounds__(32 * kSpreadWarps, 2) k_sprea
 {
     extern __shared__ __align__(16) unsigned char sm[];
     st_spread_df<W>(d, blockIdx.x, sm);
+}
+template <int W> __global__ void __launch_bounds__(32 * kOwnerCopies, 3) k_spread_owner_df(Inst d)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_spread_owner_df<W, false>(d, blockIdx.x, sm);
+}
+/* with dipole sources: twice the window values per source (2 CTAs per SM by shared memory) */
+template <int W>
+__global__ void __launch_bounds__(32 * kOwnerCopies, 2) k_spread_owner_df_dip(Inst d)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    st_spread_owner_df<W, true>(d, blockIdx.x, sm);
 }
 template <int W> __global__ void __launch_bounds__(256) k_interp_df(Inst d)
 {
@@ -558,6 +604,11 @@ int stage_smem(const Inst &d, int stage)
     const int c = d.f32 ? 8 : 16;          /* bytes of a complex value */
     switch (stage) {
     case ST_SPREAD:
+        if (d.fft_df && d.part) /* owner-tile spread: kOwnerCopies padded copies */
+            return (int)(sizeof(df32) * kOwnerCopies *
+                             (owner_copy_cells(T, W) +
+                              kSpreadBatch * (owner_batch_stride(W, d.dip != 0) + 1)) +
+                         sizeof(int) * kOwnerCopies * kSpreadBatch);
         if (d.fft_df)
             return (int)(sizeof(df32) * kSpreadWarps * spread_tile_cells(T) +
                          sizeof(df32) * kSpreadWarps * kSpreadBatch * SW +
@@ -618,7 +669,7 @@ cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStrea
 cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
                                int64_t nd, const double *xd, const double *yd, double2 *src_t,
                                int *tile_cnt, int *tile_ptr, int *tile_cur, double2 *ent_t,
-                               int *ent_j, int *err, cudaStream_t st, bool f32)
+                               int *ent_j, int *err, cudaStream_t st, bool f32, bool owner)
 {
     const int ntiles = g.nt * g.nt;
     cudaError_t e = cudaMemsetAsync(tile_cnt, 0, sizeof(int) * ntiles, st);
@@ -633,7 +684,12 @@ cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, cons
         if (cnt[k] <= 0) continue;
         const int blocks = (int)((cnt[k] + 255) / 256);
 #define YK_CALL(W)                                                                              \
-    k_bin_src_count<W><<<blocks, 256, 0, st>>>(cnt[k], px[k], py[k], g, pt[k], tile_cnt, err)
+    if (owner)                                                                                  \
+        k_bin_src_count<W, true><<<blocks, 256, 0, st>>>(cnt[k], px[k], py[k], g, pt[k],        \
+                                                         tile_cnt, err);                        \
+    else                                                                                        \
+        k_bin_src_count<W, false><<<blocks, 256, 0, st>>>(cnt[k], px[k], py[k], g, pt[k],       \
+                                                          tile_cnt, err)
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     }
@@ -642,15 +698,20 @@ cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, cons
         if (cnt[k] <= 0) continue;
         const int blocks = (int)((cnt[k] + 255) / 256);
         const int joff = k ? (int)ns : 0;
+#define YK_FILL(W, F, O)                                                                        \
+    k_bin_src_fill<W, F, O><<<blocks, 256, 0, st>>>(cnt[k], pt[k], g, tile_ptr, tile_cur, ent_t, \
+                                                    ent_j, joff)
 #define YK_CALL(W)                                                                              \
-    if (f32)                                                                                    \
-        k_bin_src_fill<W, true><<<blocks, 256, 0, st>>>(cnt[k], pt[k], g, tile_ptr, tile_cur,   \
-                                                        ent_t, ent_j, joff);                    \
-    else                                                                                        \
-        k_bin_src_fill<W, false><<<blocks, 256, 0, st>>>(cnt[k], pt[k], g, tile_ptr, tile_cur,  \
-                                                         ent_t, ent_j, joff)
+    if (f32) {                                                                                  \
+        if (owner) YK_FILL(W, true, true);                                                      \
+        else YK_FILL(W, true, false);                                                           \
+    } else {                                                                                    \
+        if (owner) YK_FILL(W, false, true);                                                     \
+        else YK_FILL(W, false, false);                                                          \
+    }
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
+#undef YK_FILL
     }
     return cudaGetLastError();
 }
@@ -664,7 +725,8 @@ __global__ void k_pack_wnu(int64_t nd, const double *__restrict__ wd, const doub
 
 cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts,
                                     const int *count, const float2 *coef, int deg, bool deriv,
-                                    float2 *out, cudaStream_t st, int64_t pitch)
+                                    float2 *out, cudaStream_t st, int64_t pitch, const int *idx,
+                                    int64_t idx_lim)
 {
     if (n <= 0) return cudaSuccess;
     if (g.w < 2 || g.w > 16 || deg != kPieceDeg[g.w]) return cudaErrorInvalidValue;
@@ -676,7 +738,7 @@ cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts
 #define YK_CALL(W)                                                                              \
     if ((e = set_smem(k_point_windows_df<W>, smem)) != cudaSuccess) return e;                  \
     k_point_windows_df<W><<<blocks, 256, smem, st>>>(n, pts, count, coef, deriv ? 1 : 0, pitch, \
-                                                     out)
+                                                     out, idx, idx_lim)
     YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     return cudaGetLastError();
@@ -908,6 +970,14 @@ cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st)
     case ST_SPREAD:
         if (d.f32) {
 #define YK_CALL(W) YK_LAUNCH(k_spread32<W>, 32 * kSpreadWarps)
+            YK_W_DISPATCH(d.g.w, YK_CALL)
+#undef YK_CALL
+        } else if (d.fft_df && d.part && d.dip) {
+#define YK_CALL(W) YK_LAUNCH(k_spread_owner_df_dip<W>, 32 * kOwnerCopies)
+            YK_W_DISPATCH(d.g.w, YK_CALL)
+#undef YK_CALL
+        } else if (d.fft_df && d.part) {
+#define YK_CALL(W) YK_LAUNCH(k_spread_owner_df<W>, 32 * kOwnerCopies)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
         } else if (d.fft_df) {

@@ -566,6 +566,282 @@ template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned 
     __syncthreads();
 }
 
+/* Owner-tile spread (double-float and FP32C paths).  Every source was binned once, to the tile
+ * of its first tap (lx, ly); its w x w window then lies in that tile's padded region of
+ * P = T + w - 1 cells per axis, so a tile accumulates whole windows with no in-tile test and writes
+ * a padded tile of P^2 partial sums.  A grid cell is covered by the padded regions of at most four
+ * tiles (its own and the tiles one step down and to the left, since P < 2T); the row FFT adds them
+ * in a fixed order when it loads the grid (fold_cell), so the result stays deterministic and no
+ * global atomics are used.
+ *
+ * A CTA takes one tile.  Each of its first kOwnerCopies warps owns a private padded copy of the
+ * tile in shared memory and walks every kOwnerCopies-th batch of the tile's sources one source at a
+ * time, one lane per tap, so the cells a warp updates together are distinct.  The copy's pitch is
+ * P rounded up to a value congruent to w mod 16: tap t = c w + a of a window then lands in 8-byte
+ * bank slot (base + t) mod 16, so 16 consecutive taps (a half-warp of 64-bit accesses) hit 16
+ * distinct slots.  The copies are summed in warp order when the padded tile is written. */
+constexpr int kOwnerCopies = 4;
+
+__host__ __device__ constexpr int owner_span(int T, int W) { return T + W - 1; }
+__host__ __device__ constexpr int owner_pitch(int T, int W)
+{
+    return owner_span(T, W) + ((((W - owner_span(T, W)) % 16) + 16) % 16);
+}
+__host__ __device__ constexpr int owner_copy_cells(int T, int W)
+{
+    return owner_span(T, W) * owner_pitch(T, W);
+}
+
+/* the copies of the walk, and the dynamic shared memory of an owner-tile spread CTA of nthreads */
+__host__ __device__ inline int owner_copies(int nthreads)
+{
+    return nthreads / 32 < kOwnerCopies ? nthreads / 32 : kOwnerCopies;
+}
+
+/* window values kept per source in the owner-tile spread's batch buffer: charges only, 2w values
+ * stored by the coalesced commit (consecutive 16-byte chunks, no bank conflicts); with dipoles,
+ * 4w values plus one (an odd stride: the per-source commit of 16 sources hits 16 distinct 8-byte
+ * bank slots) */
+__host__ __device__ constexpr int owner_batch_stride(int W, bool dip) { return dip ? 4 * W + 1 : 2 * W; }
+
+template <int W, bool DIP>
+__device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
+{
+    constexpr int EB = kSpreadBatch;
+    constexpr int NI = (W * W + 31) / 32; /* taps per lane per source */
+    constexpr int SW = owner_batch_stride(W, DIP);
+    const Geom &g = d.g;
+    const int T = g.T, P = owner_span(T, W), PP = owner_pitch(T, W), TS = P * PP;
+    const int NC = owner_copies(blockDim.x);
+    df32 *acc = reinterpret_cast<df32 *>(sm);                        /* [NC][TS] */
+    df32 *wbuf = acc + NC * TS;                                      /* [NC][EB][SW] */
+    df32 *qbuf = wbuf + NC * EB * SW;                                /* [NC][EB] */
+    int *obuf = reinterpret_cast<int *>(qbuf + NC * EB);             /* [NC][EB] */
+    const int tile = d.order ? d.order[item] : item;
+    const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
+    if (beg == end) return; /* nothing to write: the fold skips empty tiles */
+    for (int i = threadIdx.x; i < NC * TS; i += blockDim.x) acc[i] = df32(0.0f, 0.0f);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < NC) {
+        df32 *mine = acc + warp * TS;
+        df32 *wb = wbuf + warp * EB * SW;
+        df32 *qb = qbuf + warp * EB;
+        int *ob = obuf + warp * EB;
+        /* this lane's taps (c, a) = (t / W, t % W), t = i * 32 + lane; tv false past the last
+         * tap (the last round's idle lanes load and store nothing) */
+        int toff[NI], tc[NI], ta[NI];
+        bool tv[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int t = i * 32 + lane;
+            tv[i] = t < W * W;
+            tc[i] = tv[i] ? t / W : 0;
+            ta[i] = tv[i] ? t - (t / W) * W : 0;
+            toff[i] = tc[i] * PP + ta[i];
+        }
+        const float2 *__restrict__ ws = d.win_src;
+        const float2 *__restrict__ wd = d.win_dip;
+        const int4 *__restrict__ ent = reinterpret_cast<const int4 *>(d.ent_t);
+        const int stride = NC * EB;
+        /* Software pipeline over batches of EB sources: the inputs of the next batch (window
+         * values, weight and density) are loaded into registers before the current batch is
+         * walked and stored to shared memory after it, so the walk hides their latency; the entry
+         * records (tap offset, source index) are loaded one batch earlier still, since the weight
+         * and density loads depend on the source index.
+         * Charges only: the batch's window records are one contiguous block (entry order), read
+         * as 16-byte chunks, chunk g = r * 32 + lane of the block in round r; lane s < EB holds
+         * source s's record, weight and density.  With dipoles: two lanes per source (half 0 the
+         * y-parts, half 1 the x-parts), since a dipole's record lies elsewhere. */
+        constexpr int NCH = DIP ? 1 : (EB * W + 31) / 32;  /* chunks per lane (charges only) */
+        constexpr int NV = DIP ? W : 1;                     /* float2 per lane (with dipoles) */
+        float4 ch[NCH];
+        float2 v1[NV], v2[NV];
+        double pa = 0.0, pb = 0.0;
+        double2 pw = make_double2(0.0, 0.0);
+        const int slot = DIP ? (lane & (EB - 1)) : lane, half = DIP ? lane / EB : 0;
+        auto record = [&](int e) {
+            return (slot < EB && e < end) ? ent[e] : make_int4(0, -1, 0, 0);
+        };
+        auto fetch = [&](int bb, int4 r) {
+            if (!DIP) {
+                const float4 *src = reinterpret_cast<const float4 *>(ws + (size_t)bb * 2 * W);
+                const int nch = min(EB, end - bb) * W;
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    const int gi = k * 32 + lane;
+                    if (gi < nch) ch[k] = src[gi];
+                }
+                if (r.y >= 0) {
+                    pa = d.wq[r.y];
+                    pb = d.dens[r.y];
+                }
+                return;
+            }
+            if (r.y < 0) return;
+            const int j = r.y;
+            if (j < d.n_chg) {
+                /* half 0: phi_y (times q = w sigma at commit); half 1: phi_x */
+                const float2 *src = ws + (size_t)(bb + slot) * 2 * W + half * W;
+#pragma unroll
+                for (int a = 0; a < NV; ++a) v1[a] = src[a];
+                if (half == 0) {
+                    pa = d.wq[j];
+                    pb = d.dens[j];
+                }
+            } else {
+                /* dipole: half 0 phi_y, phi'_y (times s_x, s_y at commit); half 1 phi'_x, phi_x */
+                const int jd = j - d.n_chg;
+                const float2 *src = wd + (size_t)jd * 4 * W;
+                const float2 *s1 = src + (half ? 3 * W : 0), *s2 = src + (half ? W : 2 * W);
+#pragma unroll
+                for (int a = 0; a < NV; ++a) {
+                    v1[a] = s1[a];
+                    v2[a] = s2[a];
+                }
+                if (half == 0) {
+                    pa = d.mu[jd];
+                    pw = d.wnu[jd];
+                }
+            }
+        };
+        auto commit = [&](int bb, int4 r) {
+            if (!DIP) {
+                if (r.y >= 0) {
+                    qb[slot] = df32(pa * pb);
+                    ob[slot] = r.x;
+                }
+                __syncwarp();
+                const int nch = min(EB, end - bb) * W;
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    const int gi = k * 32 + lane;
+                    if (gi < nch) {
+                        /* values 2p, 2p + 1 of source s; the first W are phi_y, scaled by q */
+                        const int s = gi / W, p2 = 2 * (gi - s * W);
+                        const df32 q = qb[s];
+                        df32 x0(ch[k].x, ch[k].y), x1(ch[k].z, ch[k].w);
+                        if (p2 < W) x0 = q * x0;
+                        if (p2 + 1 < W) x1 = q * x1;
+                        wb[s * SW + p2] = x0;
+                        wb[s * SW + p2 + 1] = x1;
+                    }
+                }
+                return;
+            }
+            if (r.y < 0) return;
+            df32 *wl = wb + slot * SW;
+            const bool dipole = r.y >= d.n_chg;
+            if (!dipole) {
+                const df32 f = half ? df32(1.0f, 0.0f) : df32(pa * pb);
+#pragma unroll
+                for (int a = 0; a < NV; ++a) wl[half * W + a] = f * df32(v1[a].x, v1[a].y);
+            } else {
+                /* taps s_x phi'(X - t_x) phi(Y - t_y) + s_y phi(X - t_x) phi'(Y - t_y),
+                 * s = -mu w nu / h (the gradient of the window in the source point) */
+                const double m = -pa * g.inv_h;
+                const df32 f1 = half ? df32(1.0f, 0.0f) : df32(m * pw.x);
+                const df32 f2 = half ? df32(1.0f, 0.0f) : df32(m * pw.y);
+#pragma unroll
+                for (int a = 0; a < NV; ++a) {
+                    wl[half * W + a] = f1 * df32(v1[a].x, v1[a].y);
+                    wl[(2 + half) * W + a] = f2 * df32(v2[a].x, v2[a].y);
+                }
+            }
+            if (half == 0) ob[slot] = r.x | (dipole ? 1 << 30 : 0);
+        };
+        int b0 = beg + warp * EB;
+        int4 rc = record(b0 + slot);
+        int4 rn = record(b0 + stride + slot);
+        fetch(b0, rc);
+        for (; b0 < end; b0 += stride) {
+            commit(b0, rc);
+            __syncwarp();
+            rc = rn;
+            if (b0 + stride < end) fetch(b0 + stride, rc);
+            rn = record(b0 + 2 * stride + slot);
+            const int cnt = min(EB, end - b0);
+            for (int k = 0; k < cnt; ++k) {
+                const int v = ob[k];
+                const int base = v & 0x3fffffff;
+                const df32 *wk = wb + k * SW;
+                df32 cur[NI];
+#pragma unroll
+                for (int i = 0; i < NI; ++i)
+                    if (tv[i]) cur[i] = mine[base + toff[i]];
+                if (!DIP || !(v >> 30)) {
+#pragma unroll
+                    for (int i = 0; i < NI; ++i)
+                        cur[i] = df_mul_add_lazy(cur[i], wk[tc[i]], wk[W + ta[i]]);
+                } else { /* warp-uniform: one source at a time */
+#pragma unroll
+                    for (int i = 0; i < NI; ++i) {
+                        cur[i] = df_mul_add_lazy(cur[i], wk[tc[i]], wk[W + ta[i]]);
+                        cur[i] = df_mul_add_lazy(cur[i], wk[2 * W + tc[i]], wk[3 * W + ta[i]]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < NI; ++i)
+                    if (tv[i]) mine[base + toff[i]] = cur[i];
+                __syncwarp(); /* the next source may touch the same cells through other lanes */
+            }
+            __syncwarp(); /* the window buffers are refilled by the next batch */
+        }
+    }
+    __syncthreads();
+    /* padded tile = sum of the copies in warp order, normalised (the cells were accumulated
+     * unnormalised by df_mul_add_lazy) */
+    df32 *__restrict__ out = static_cast<df32 *>(d.part) + (size_t)tile * P * P;
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int r = i / P, c = i - r * P;
+        const int ci = r * PP + c;
+        df32 sum = acc[ci];
+        for (int w = 1; w < NC; ++w) sum = sum + acc[w * TS + ci];
+        out[i] = df_fast_two_sum(sum.hi, sum.lo);
+    }
+    __syncthreads(); /* shared memory is reused by the next item */
+}
+
+/* one grid cell (x, y) of the owner-tile spread's output: the padded partials of the tiles whose
+ * padded region covers it, added in a fixed order (far neighbours first); empty tiles were not
+ * written and are skipped.  ty, ly = y / T, y % T of the cell's row. */
+template <typename P2>
+__device__ __forceinline__ void fold_terms(const Inst &d, int ty, int ly, int x, float invT,
+                                           const P2 *__restrict__ part, P2 *v, int &nv)
+{
+    const Geom &g = d.g;
+    const int T = g.T, nt = g.nt, P = owner_span(T, g.w), PPc = P * P;
+    const int tx = min(nt - 1, (int)(((float)x + 0.5f) * invT)), lx = x - tx * T;
+    const int *__restrict__ tp = d.tile_ptr;
+    const int tyb = ty == 0 ? nt - 1 : ty - 1, txb = tx == 0 ? nt - 1 : tx - 1;
+    const bool hy = ly < g.w - 1, hx = lx < g.w - 1; /* also in the padded region below / left */
+    nv = 0;
+    if (hy && hx) {
+        const int t = tyb * nt + txb;
+        if (tp[t + 1] > tp[t]) v[nv++] = part[(size_t)t * PPc + (ly + T) * P + lx + T];
+    }
+    if (hy) {
+        const int t = tyb * nt + tx;
+        if (tp[t + 1] > tp[t]) v[nv++] = part[(size_t)t * PPc + (ly + T) * P + lx];
+    }
+    if (hx) {
+        const int t = ty * nt + txb;
+        if (tp[t + 1] > tp[t]) v[nv++] = part[(size_t)t * PPc + ly * P + lx + T];
+    }
+    const int t = ty * nt + tx;
+    if (tp[t + 1] > tp[t]) v[nv++] = part[(size_t)t * PPc + ly * P + lx];
+}
+
+__device__ __forceinline__ df32 fold_cell_df(const Inst &d, int ty, int ly, int x, float invT)
+{
+    df32 v[4];
+    int nv;
+    fold_terms<df32>(d, ty, ly, x, invT, static_cast<const df32 *>(d.part), v, nv);
+    df32 s(0.0f, 0.0f);
+    for (int k = 0; k < nv; ++k) s = k ? s + v[k] : v[k];
+    return s;
+}
+
 /* ----------------------------------------------------------------------------------------- */
 /* FFT passes (mixed-radix DIF in shared memory, see yk_core.h)                               */
 
@@ -641,6 +917,25 @@ __device__ __forceinline__ void fft_inv(cpx<R> *x, const FftStages &st, const TW
     for (int s = st.n - 1; s >= 0; --s) fft_stage_any<true, R>(x, st, s, tw, nrows, rowlen);
 }
 
+/* rows y0 .. y0 + nr - 1 of the grid from the owner-tile spread's padded partials, as packed
+ * complex values x[r L + l] = grid[y][2l] + i grid[y][2l + 1] */
+template <typename R> __device__ void load_folded_rows(const Inst &d, cpx<R> *x, int y0, int nr);
+
+template <>
+__device__ __forceinline__ void load_folded_rows<df32>(const Inst &d, cpx<df32> *x, int y0, int nr)
+{
+    const int L = d.n >> 1, T = d.g.T;
+    const float invT = 1.0f / (float)T;
+    for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
+        const int r = i / L, l = i - r * L, y = y0 + r;
+        const int ty = y / T, ly = y - ty * T;
+        x[i] = mk<df32>(fold_cell_df(d, ty, ly, 2 * l, invT), fold_cell_df(d, ty, ly, 2 * l + 1, invT));
+    }
+}
+
+template <> __device__ __forceinline__ void load_folded_rows<float>(const Inst &, cpx<float> *, int, int) {}
+template <> __device__ __forceinline__ void load_folded_rows<double>(const Inst &, cpx<double> *, int, int) {}
+
 /* rows [item*rows, ...): real-to-complex FFT, keep m_x <= M, store transposed spec[m_x*n + y] */
 template <typename R> __device__ void st_row_fwd(const Inst &d, int item, unsigned char *sm)
 {
@@ -654,9 +949,14 @@ template <typename R> __device__ void st_row_fwd(const Inst &d, int item, unsign
     const C2 *__restrict__ tw = static_cast<const C2 *>(d.tw);
     const int y0 = item * d.rows;
     const int nr = min(d.rows, n - y0);
-    for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
-        const int r = i / L, l = i - r * L;
-        x[i] = T::from_g2(reinterpret_cast<const G2 *>(grid + (size_t)(y0 + r) * n)[l]);
+    if (d.part) {
+        /* owner-tile spread: fold the padded tile partials into the rows as they are loaded */
+        load_folded_rows<R>(d, x, y0, nr);
+    } else {
+        for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
+            const int r = i / L, l = i - r * L;
+            x[i] = T::from_g2(reinterpret_cast<const G2 *>(grid + (size_t)(y0 + r) * n)[l]);
+        }
     }
     __syncthreads();
     fft_fwd<R>(x, d.sth, tw, nr, L);
@@ -897,7 +1197,13 @@ __device__ __forceinline__ void run_stage<double>(const Inst &d, int stage, int 
 {
     switch (stage) {
     case ST_SPREAD:
-        if (d.fft_df) {
+        if (d.fft_df && d.part) {
+#define YK_C(W)                                                                                  \
+    if (d.dip) st_spread_owner_df<W, true>(d, item, sm);                                         \
+    else st_spread_owner_df<W, false>(d, item, sm)
+            YK_W_SWITCH(d.g.w, YK_C)
+#undef YK_C
+        } else if (d.fft_df) {
 #define YK_C(W) st_spread_df<W>(d, item, sm)
             YK_W_SWITCH(d.g.w, YK_C)
 #undef YK_C
@@ -970,7 +1276,9 @@ __device__ __forceinline__ void run_stage_w(const Inst &d, int stage, int item, 
     } else {
         switch (stage) {
         case ST_SPREAD:
-            if (d.fft_df) st_spread_df<W>(d, item, sm);
+            if (d.fft_df && d.part && d.dip) st_spread_owner_df<W, true>(d, item, sm);
+            else if (d.fft_df && d.part) st_spread_owner_df<W, false>(d, item, sm);
+            else if (d.fft_df) st_spread_df<W>(d, item, sm);
             else st_spread64<W>(d, item, sm);
             break;
         case ST_ROW_FWD:

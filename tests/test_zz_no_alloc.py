@@ -45,7 +45,8 @@ def test_static_entry_two_calls_match_oracle_and_plan_path():
     args = [dev(a) for a in (w.xs, w.ys, w.w, w.density, w.xt, w.yt)]
     cases = [(0.5, oracle_u(w, 0.5), plan_u(w, 0.5, args)),
              (w.alpha, oracle_u(w, w.alpha), plan_u(w, w.alpha, args))]
-    outs = [torch.full((w.n_trg,), np.nan, dtype=torch.float64, device="cuda") for _ in cases]
+    outs = [torch.full((w.n_trg,), np.nan, dtype=torch.float64, device="cuda")
+            for _ in range(len(cases) + 1)]
     torch.cuda.synchronize()
     before = torch.cuda.memory_allocated()
     for (alpha, ref, via_plan), out in zip(cases, outs):
@@ -57,7 +58,7 @@ def test_static_entry_two_calls_match_oracle_and_plan_path():
         assert np.max(np.abs(u - ref)) <= TOL64 * scale, alpha
         assert np.max(np.abs(u - via_plan)) <= TOL64 * scale, alpha
     # and once more in the first order, after the small grid
-    out = torch.full((w.n_trg,), np.nan, dtype=torch.float64, device="cuda")
+    out = outs[-1]
     yk.eval_longrange_static(0.5, *args, out, tol=TOL64, h_vol=w.h_vol, box=w.box)
     assert torch.cuda.memory_allocated() == before
     ref = cases[0][1]
