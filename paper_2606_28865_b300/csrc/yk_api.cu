@@ -483,7 +483,8 @@ void free_all(yk_plan_t p)
                      &p->tile_cnt, &p->tile_ptr, &p->tile_cur, &p->tile_order, &p->part, &p->trg_cnt,
                      &p->trg_ptr,
                      &p->trg_cur, &p->err, &p->w_src, &p->src_t, &p->ent_t, &p->ent_j,
-                     &p->trg_t, &p->trg_idx, &p->trg_tmp, &p->stage_x, &p->stage_y,
+                     &p->trg_t, &p->trg_idx, &p->trg_tmp, &p->src_tap, &p->trg_tap,
+                     &p->trg_frac, &p->stage_x, &p->stage_y,
                      &p->stage_w, &p->stage_u};
     for (DevBuf *b : all) buf_free(p, *b);
     for (int r = 0; r < yk_plan_s::kEventRing; ++r)
@@ -549,6 +550,10 @@ yk::Geom geom_of(const yk_plan_s *p)
     g.nt = p->nt;
     g.w = p->w;
     for (int k = 0; k < 4; ++k) g.box[k] = p->box[k];
+    g.A = std::ldexp(g.inv_h, yk::kFixBits);
+    g.Bx = -p->ox * g.A;
+    g.By = -p->oy * g.A;
+    g.n44 = (long long)p->n << yk::kFixBits;
     return g;
 }
 
@@ -1130,12 +1135,28 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
               "weights");
     YK_CU(yk::launch_pack_wnu(n_dip, ddw, dnx, dny, P<double2>(p->wnu), p->stream),
           "dipole weights");
+    /* the double-float and FP32C paths prepare points in fixed point (no FP64 rounding past
+     * the grid coordinate); the all-FP64 path keeps FP64 grid coordinates */
+    const bool prep = p->fft_df || p->precision == YK_FP32C;
+    if (prep) {
+        YK_TRY(buf_alloc(p, p->src_tap, sizeof(int2) * (ns + nd), "source taps"));
+        YK_TRY(buf_alloc(p, p->trg_tap, sizeof(int4) * nt, "target taps"));
+        if (p->fft_df) YK_TRY(buf_alloc(p, p->trg_frac, sizeof(float4) * nt, "target windows"));
+    }
     stage_begin(p, YK_STAGE_BIN_SRC);
-    YK_CU(yk::launch_bin_sources(g, n_src, dx, dy, n_dip, ddx, ddy, P<double2>(p->src_t),
-                                 P<int>(p->tile_cnt), P<int>(p->tile_ptr), P<int>(p->tile_cur),
-                                 P<double2>(p->ent_t), P<int>(p->ent_j), P<int>(p->err),
-                                 p->stream, p->precision == YK_FP32C, p->fft_df != 0),
-          "bin sources");
+    if (prep)
+        YK_CU(yk::launch_prep_sources(g, n_src, dx, dy, n_dip, ddx, ddy, P<int2>(p->src_tap),
+                                      P<float4>(p->src_t), P<int>(p->tile_cnt),
+                                      P<int>(p->tile_ptr), P<int>(p->tile_cur),
+                                      P<double2>(p->ent_t), P<int>(p->ent_j), P<int>(p->err),
+                                      p->stream, p->fft_df != 0),
+              "bin sources");
+    else
+        YK_CU(yk::launch_bin_sources(g, n_src, dx, dy, n_dip, ddx, ddy, P<double2>(p->src_t),
+                                     P<int>(p->tile_cnt), P<int>(p->tile_ptr),
+                                     P<int>(p->tile_cur), P<double2>(p->ent_t), P<int>(p->ent_j),
+                                     P<int>(p->err), p->stream, false, false),
+              "bin sources");
     /* the cursors are free after the fill: they serve as the ordering's scratch */
     YK_CU(yk::launch_tile_order(P<int>(p->tile_ptr), p->nt * p->nt, P<int>(p->tile_order),
                                 P<int>(p->tile_cur), p->stream),
@@ -1146,17 +1167,19 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
          * keep their own records) */
         const size_t w = (size_t)p->w;
         YK_TRY(buf_alloc(p, p->win_src, sizeof(float2) * 2 * w * (ns + nd), "source windows"));
-        YK_CU(yk::launch_point_windows_df(g, n_src + n_dip, P<double2>(p->src_t),
-                                          P<int>(p->tile_ptr) + (size_t)p->nt * p->nt,
-                                          P<float2>(p->win_pc), p->pdeg, false,
-                                          P<float2>(p->win_src), p->stream, 0, P<int>(p->ent_j),
-                                          n_src),
+        YK_CU(yk::launch_frac_windows_df(g, n_src + n_dip, P<float4>(p->src_t),
+                                         P<int>(p->tile_ptr) + (size_t)p->nt * p->nt,
+                                         P<float2>(p->win_pc), p->pdeg, false,
+                                         P<float2>(p->win_src), p->stream, 0, P<int>(p->ent_j),
+                                         n_src),
               "source windows");
         if (nd > 0) {
+            /* dipoles in their own order (a dipole outside the box has no entries, and its
+             * record is never read) */
             YK_TRY(buf_alloc(p, p->win_dip, sizeof(float2) * 4 * w * nd, "dipole windows"));
-            YK_CU(yk::launch_point_windows_df(g, n_dip, P<double2>(p->src_t) + ns, nullptr,
-                                              P<float2>(p->win_pc), p->pdeg, true,
-                                              P<float2>(p->win_dip), p->stream),
+            YK_CU(yk::launch_frac_windows_df(g, n_dip, P<float4>(p->src_t) + ns, nullptr,
+                                             P<float2>(p->win_pc), p->pdeg, true,
+                                             P<float2>(p->win_dip), p->stream),
                   "dipole windows");
         }
     }
@@ -1166,17 +1189,25 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
     YK_TRY(to_device(p, xt, n_trg, p->stage_x, &tx, "target x"));
     YK_TRY(to_device(p, yt, n_trg, p->stage_y, &ty, "target y"));
     stage_begin(p, YK_STAGE_BIN_TRG);
-    YK_CU(yk::launch_bin_targets(g, n_trg, tx, ty, P<double2>(p->trg_tmp), P<int>(p->trg_cnt),
-                                 P<int>(p->trg_ptr), P<int>(p->trg_cur), P<double2>(p->trg_t),
-                                 P<int>(p->trg_idx), P<int>(p->err), p->stream,
-                                 p->precision == YK_FP32C),
-          "bin targets");
+    if (prep)
+        YK_CU(yk::launch_prep_targets(g, n_trg, tx, ty, P<int4>(p->trg_tap), P<float4>(p->trg_tmp),
+                                      P<int>(p->trg_cnt), P<int>(p->trg_ptr), P<int>(p->trg_cur),
+                                      P<double2>(p->trg_t),
+                                      p->fft_df ? P<float4>(p->trg_frac) : nullptr,
+                                      P<int>(p->trg_idx), P<int>(p->err), p->stream),
+              "bin targets");
+    else
+        YK_CU(yk::launch_bin_targets(g, n_trg, tx, ty, P<double2>(p->trg_tmp),
+                                     P<int>(p->trg_cnt), P<int>(p->trg_ptr), P<int>(p->trg_cur),
+                                     P<double2>(p->trg_t), P<int>(p->trg_idx), P<int>(p->err),
+                                     p->stream, false),
+              "bin targets");
     if (p->fft_df) {
         YK_TRY(buf_alloc(p, p->win_trg, sizeof(float2) * 2 * (size_t)p->w * nt, "target windows"));
-        YK_CU(yk::launch_point_windows_df(g, n_trg, P<double2>(p->trg_t),
-                                          P<int>(p->trg_ptr) + (size_t)p->nt * p->nt,
-                                          P<float2>(p->win_pc), p->pdeg, false,
-                                          P<float2>(p->win_trg), p->stream, n_trg),
+        YK_CU(yk::launch_frac_windows_df(g, n_trg, P<float4>(p->trg_frac),
+                                         P<int>(p->trg_ptr) + (size_t)p->nt * p->nt,
+                                         P<float2>(p->win_pc), p->pdeg, false,
+                                         P<float2>(p->win_trg), p->stream, n_trg),
               "target windows");
     }
     stage_end(p, YK_STAGE_BIN_TRG);

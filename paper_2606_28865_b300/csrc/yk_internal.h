@@ -14,11 +14,13 @@
 namespace yk {
 
 /* pieces per tap of the double-float window polynomials, and their degree for window width w
- * (index w, 2..16): the lowest degree whose interior error is within 3% of eps = 10^(1-w), found by
- * fitting in long double (at w = 12: 1.4e-13 at degree 6; w = 15, 16 take the degree whose error
- * matches 4 pieces of degree 9, ~3.6e-16) */
-constexpr int kWinPieces = 8;
-constexpr int kPieceDeg[17] = {3, 3, 3, 3, 3, 3, 4, 4, 5, 5, 5, 6, 6, 7, 7, 8, 8};
+ * (index w, 2..16): the lowest degree whose error at the interior taps is within 3% of
+ * eps = 10^(1-w) (w <= 14; w = 15, 16 take the degree at which the fit reaches FP64 rounding),
+ * found by interpolating at Chebyshev points in long double (at w = 12: 4.3e-14 at degree 4 with
+ * 64 pieces, against 1.4e-13 at degree 6 with 8; the two edge taps carry the window's
+ * square-root edge, ~1.1e-13 at w = 12 either way) */
+constexpr int kWinPieces = 64;
+constexpr int kPieceDeg[17] = {1, 1, 1, 1, 2, 2, 2, 3, 3, 3, 4, 4, 4, 5, 5, 5, 5};
 
 /* grid geometry handed to kernels by value */
 struct Geom {
@@ -31,7 +33,15 @@ struct Geom {
     int nt;         /* tiles per axis = n / T */
     int w;          /* window width */
     double box[4];  /* xmin, xmax, ymin, ymax: points outside are rejected */
+    /* fixed-point grid coordinates of the double-float and FP32C paths: T = rint(x A + B) is
+     * t 2^44 (t = (x - origin) / h in cells), A = 2^44 / h, B = -origin 2^44 / h per axis; a
+     * coordinate in [0, n) has T in [0, n44), n44 = n 2^44 */
+    double A, Bx, By;
+    long long n44;
 };
+
+/* fraction bits of the fixed-point grid coordinate */
+constexpr int kFixBits = 44;
 
 /* device error bits (sticky in the plan / batch) */
 enum { ERR_POINT_OUTSIDE = 1, ERR_WAIT_TIMEOUT = 2 };
@@ -112,15 +122,32 @@ cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, cons
                                int *tile_cnt, int *tile_ptr, int *tile_cur, double2 *ent_t,
                                int *ent_j, int *err, cudaStream_t st, bool f32,
                                bool owner = false);
-/* double-float window values of n points at grid coordinates pts (a point with t.x < 0 lies
- * outside the box and gets none): out[i * 2w ...] as described for Inst::win_src; with deriv, 4w
- * values per point including the derivative's.  count (device, may be NULL): only the first
- * *count points are valid.  idx (device, may be NULL): point i is pts[idx[i]], and points with
- * idx[i] >= idx_lim get no values (the owner-tile entries, whose dipoles keep their own records). */
-cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts,
-                                    const int *count, const float2 *coef, int deg, bool deriv,
-                                    float2 *out, cudaStream_t st, int64_t pitch = 0,
-                                    const int *idx = nullptr, int64_t idx_lim = 0);
+/* Point preparation of the double-float and FP32C paths (no FP64 arithmetic past the
+ * fixed-point coordinate): per point its first taps tap = (l0x, l0y) (INT_MIN: outside the box)
+ * and the window arguments u = l0 - t + w/2 in [0, 1) of both axes as exact FP32 pairs,
+ * frac = (ux.hi, ux.lo, uy.hi, uy.lo), in the original order (targets: tap_tmp also holds the
+ * tile of the target's cell, -1 outside).  Sources: ns charges then nd
+ * dipoles (index offset ns); one entry per source in its owner tile (owner) or one per tile its
+ * window touches; entry records int4 (owner: padded-copy offset, source index, sx, sy; else lx,
+ * ly, sx, sy) with s = l0 - t in FP32.  Targets: records int4 (lx, ly, sx, sy) grouped by the
+ * tile of their cell, and (trg_frac non-NULL) their frac in the same order. */
+cudaError_t launch_prep_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
+                                int64_t nd, const double *xd, const double *yd, int2 *tap,
+                                float4 *frac, int *tile_cnt, int *tile_ptr, int *tile_cur,
+                                double2 *ent_t, int *ent_j, int *err, cudaStream_t st, bool owner);
+cudaError_t launch_prep_targets(const Geom &g, int64_t nt, const double *xt, const double *yt,
+                                int4 *tap_tmp, float4 *frac_tmp, int *cnt, int *ptr, int *cur,
+                                double2 *trg_t, float4 *trg_frac, int *trg_idx, int *err,
+                                cudaStream_t st);
+/* double-float window values of points given by their window arguments frac (as above):
+ * out[i * 2w ...] as described for Inst::win_src; with deriv, 4w values per point including the
+ * derivative's; a point whose frac is never written gets none (tap.x == INT_MIN is not read
+ * here: invalid points are those past *count or, through idx, with idx[i] >= idx_lim).
+ * pitch > 0: value-major planes (value k of point i at k * pitch + i). */
+cudaError_t launch_frac_windows_df(const Geom &g, int64_t n, const float4 *frac, const int *count,
+                                   const float2 *coef, int deg, bool deriv, float2 *out,
+                                   cudaStream_t st, int64_t pitch = 0, const int *idx = nullptr,
+                                   int64_t idx_lim = 0);
 /* exclusive scan of cnt[0..count) into ptr[0..count]; cur (>= ceil(count / 4096) ints) is scratch
  * and is left zeroed */
 cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStream_t st);
@@ -245,7 +272,12 @@ struct yk_plan_s {
     DevBuf ent_j;    /* int[<= 4 n_src]: source index of each entry */
     DevBuf trg_t;    /* 16 B x n_trg: targets grouped by tile (same two layouts as ent_t) */
     DevBuf trg_idx;  /* int[n_trg]: original index of each grouped target */
-    DevBuf trg_tmp;  /* double2[n_trg]: grid coordinates in original order */
+    DevBuf trg_tmp;  /* double2[n_trg]: grid coordinates in original order (fixed-point
+                        preparation: the targets' window arguments, float4) */
+    /* fixed-point preparation (double-float and FP32C paths): src_t holds the sources' window
+     * arguments (float4) and src_tap their first taps (int2); trg_tap the targets' first taps and
+     * cell tiles (int4, original order); trg_frac the targets' window arguments in tile order */
+    DevBuf src_tap, trg_tap, trg_frac;
     /* staging copies of host arrays */
     DevBuf stage_x, stage_y, stage_w, stage_u;
     DevBuf stage_d[6]; /* dipole inputs xd, yd, wd, nx, ny and the density mu */

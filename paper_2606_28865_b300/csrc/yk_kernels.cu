@@ -22,6 +22,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <climits>
+
 #include "yk_stages.cuh"
 
 namespace yk {
@@ -204,6 +207,173 @@ __global__ void k_bin_trg_fill(int64_t nt, const double2 *__restrict__ tmp, Geom
     }
 }
 
+/* ----------------------------------------------------------------------------------------- */
+/* point preparation in fixed point (double-float and FP32C paths)                            */
+
+/* T = t 2^44 rounded (one FMA and one conversion: the only FP64 work per coordinate) */
+__device__ __forceinline__ long long fixed_coord(double x, double A, double B)
+{
+    return __double2ll_rn(fma(x, A, B));
+}
+
+/* first tap l0 = ceil(t - w/2) and u = l0 - t + w/2 in [0, 1) from T = t 2^44, with u as an exact
+ * FP32 pair: its 44 fraction bits split into 24 + 20 (both conversions exact), then renormalised */
+template <int W> __device__ __forceinline__ void tap_frac(long long T, int &l0, float &uh, float &ul)
+{
+    const long long v = T - ((long long)W << (kFixBits - 1));            /* (t - w/2) 2^44 */
+    const long long l = (v + ((1ll << kFixBits) - 1)) >> kFixBits;         /* ceil */
+    const long long uf = (l << kFixBits) - v;                              /* u 2^44 */
+    l0 = (int)l;
+    const float hi = __int2float_rn((int)(uf >> 20)) * 5.9604644775390625e-8f;         /* 2^-24 */
+    const float lo = __int2float_rn((int)(uf & 0xfffff)) * 5.684341886080801487e-14f;  /* 2^-44 */
+    const df32 u = df_fast_two_sum(hi, lo); /* hi >= lo unless hi == 0 */
+    uh = u.hi;
+    ul = u.lo;
+}
+
+/* s = l0 - t = u - w/2 rounded to FP32 (the FP32C kernels' window offset) */
+template <int W> __device__ __forceinline__ float frac_offset(float uh, float ul)
+{
+    const df32 s = df32(uh, 0.0f) + df32(-0.5f * W, 0.0f);
+    return YK_FADD(s.hi, YK_FADD(s.lo, ul));
+}
+
+/* the tiles (up to four) a window with first taps (lx, ly) touches; -1 where there is none */
+__device__ __forceinline__ void tap_tiles(int lx, int ly, int W, const Geom &g, int tiles[4])
+{
+    const int ax0 = wrap(lx, g.n) / g.T, ax1 = wrap(lx + W - 1, g.n) / g.T;
+    const int ay0 = wrap(ly, g.n) / g.T, ay1 = wrap(ly + W - 1, g.n) / g.T;
+    tiles[0] = ay0 * g.nt + ax0;
+    tiles[1] = ax1 != ax0 ? ay0 * g.nt + ax1 : -1;
+    tiles[2] = ay1 != ay0 ? ay1 * g.nt + ax0 : -1;
+    tiles[3] = (ay1 != ay0 && ax1 != ax0) ? ay1 * g.nt + ax1 : -1;
+}
+
+/* prepare one point: false when it lies outside the box or the grid */
+template <int W>
+__device__ __forceinline__ bool prep_point(const Geom &g, double x, double y, int2 &tap,
+                                           float4 &fr, long long &Tx, long long &Ty)
+{
+    Tx = fixed_coord(x, g.A, g.Bx);
+    Ty = fixed_coord(y, g.A, g.By);
+    if (!(in_box(g, x, y) && Tx >= 0 && Tx < g.n44 && Ty >= 0 && Ty < g.n44)) return false;
+    tap_frac<W>(Tx, tap.x, fr.x, fr.y);
+    tap_frac<W>(Ty, tap.y, fr.z, fr.w);
+    return true;
+}
+
+template <int W, bool OWNER>
+__global__ void k_prep_src_count(int64_t ns, const double *__restrict__ xs,
+                                 const double *__restrict__ ys, Geom g, int2 *__restrict__ tap,
+                                 float4 *__restrict__ frac, int *__restrict__ cnt,
+                                 int *__restrict__ err)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int tiles[4] = {-1, -1, -1, -1};
+    if (j < ns) {
+        int2 tp;
+        float4 fr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        long long Tx, Ty;
+        if (!prep_point<W>(g, xs[j], ys[j], tp, fr, Tx, Ty)) {
+            atomicOr(err, ERR_POINT_OUTSIDE);
+            tp = make_int2(INT_MIN, 0);
+        } else if (OWNER) {
+            tiles[0] = (wrap(tp.y, g.n) / g.T) * g.nt + wrap(tp.x, g.n) / g.T;
+        } else {
+            tap_tiles(tp.x, tp.y, W, g, tiles);
+        }
+        tap[j] = tp;
+        frac[j] = fr;
+    }
+#pragma unroll
+    for (int r = 0; r < (OWNER ? 1 : 4); ++r) agg_count(cnt, tiles[r], tiles[r] >= 0);
+}
+
+template <int W, bool OWNER>
+__global__ void k_prep_src_fill(int64_t ns, const int2 *__restrict__ tap,
+                                const float4 *__restrict__ frac, Geom g,
+                                const int *__restrict__ ptr, int *__restrict__ cur,
+                                double2 *__restrict__ ent_t, int *__restrict__ ent_j, int joff)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int tiles[4] = {-1, -1, -1, -1};
+    int2 tp = make_int2(INT_MIN, 0);
+    if (j < ns) tp = tap[j];
+    int4 rec = make_int4(0, 0, 0, 0);
+    if (tp.x != INT_MIN) {
+        const float4 fr = frac[j];
+        const float sx = frac_offset<W>(fr.x, fr.y), sy = frac_offset<W>(fr.z, fr.w);
+        if (OWNER) {
+            const int wx = wrap(tp.x, g.n), wy = wrap(tp.y, g.n);
+            tiles[0] = (wy / g.T) * g.nt + wx / g.T;
+            rec = make_int4((wy % g.T) * owner_pitch(g.T, W) + wx % g.T, (int)j + joff,
+                            __float_as_int(sx), __float_as_int(sy));
+        } else {
+            tap_tiles(tp.x, tp.y, W, g, tiles);
+            rec = make_int4(tp.x, tp.y, __float_as_int(sx), __float_as_int(sy));
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < (OWNER ? 1 : 4); ++r) {
+        const bool v = tiles[r] >= 0;
+        const int off = agg_reserve(cur, tiles[r], v);
+        if (v) {
+            const int slot = ptr[tiles[r]] + off;
+            *reinterpret_cast<int4 *>(ent_t + slot) = rec;
+            ent_j[slot] = (int)j + joff;
+        }
+    }
+}
+
+/* targets: tap4 = (l0x, l0y, tile of the cell floor(t), 0), tile -1 outside the box */
+template <int W>
+__global__ void k_prep_trg_count(int64_t nt, const double *__restrict__ xt,
+                                 const double *__restrict__ yt, Geom g, int4 *__restrict__ tap4,
+                                 float4 *__restrict__ frac, int *__restrict__ cnt,
+                                 int *__restrict__ err)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int tile = -1;
+    if (i < nt) {
+        int2 tp = make_int2(0, 0);
+        float4 fr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        long long Tx, Ty;
+        if (!prep_point<W>(g, xt[i], yt[i], tp, fr, Tx, Ty)) {
+            atomicOr(err, ERR_POINT_OUTSIDE);
+        } else {
+            tile = ((int)(Ty >> kFixBits) / g.T) * g.nt + (int)(Tx >> kFixBits) / g.T;
+        }
+        tap4[i] = make_int4(tp.x, tp.y, tile, 0);
+        frac[i] = fr;
+    }
+    agg_count(cnt, tile, tile >= 0);
+}
+
+/* targets grouped by the tile of their cell: records (lx, ly, sx, sy) and, when trg_frac is
+ * given, the window arguments in the same order */
+template <int W>
+__global__ void k_prep_trg_fill(int64_t nt, const int4 *__restrict__ tap4,
+                                const float4 *__restrict__ frac, const int *__restrict__ ptr,
+                                int *__restrict__ cur, double2 *__restrict__ trg_t,
+                                float4 *__restrict__ trg_frac, int *__restrict__ trg_idx)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int4 tp = make_int4(0, 0, -1, 0);
+    if (i < nt) tp = tap4[i];
+    const int tile = tp.z;
+    const bool v = tile >= 0;
+    const int off = agg_reserve(cur, tile, v);
+    if (v) {
+        const float4 fr = frac[i];
+        const int slot = ptr[tile] + off;
+        *reinterpret_cast<int4 *>(trg_t + slot) =
+            make_int4(tp.x, tp.y, __float_as_int(frac_offset<W>(fr.x, fr.y)),
+                      __float_as_int(frac_offset<W>(fr.z, fr.w)));
+        if (trg_frac) trg_frac[slot] = fr;
+        trg_idx[slot] = (int)i;
+    }
+}
+
 /* exclusive scan of cnt[0..count) into ptr[0..count] in three passes over blocks of kScanBlock
  * elements: block sums into bsum, a scan of the block sums (one CTA), then each block adds its
  * offset.  bsum holds ceil(count / kScanBlock) ints. */
@@ -327,7 +497,8 @@ __global__ void k_order_fill(const int *__restrict__ ptr, int ntiles, int *__res
 }
 
 /* W window values of one coordinate by Horner in double-float on the piece's polynomials
- * (compile-time degree D, taps interleaved: W independent chains) */
+ * (compile-time degree D, taps interleaved: W independent chains); each step c_k + p x is one
+ * fused double-float multiply-add (exact product terms added to c_k by two-sum) */
 template <int W, int D>
 __device__ __forceinline__ void windows_piece(const df32 *c, df32 x, df32 (&p)[W])
 {
@@ -336,17 +507,18 @@ __device__ __forceinline__ void windows_piece(const df32 *c, df32 x, df32 (&p)[W
 #pragma unroll
     for (int k = D - 1; k >= 0; --k)
 #pragma unroll
-        for (int a = 0; a < W; ++a) p[a] = p[a] * x + c[k * W + a];
+        for (int a = 0; a < W; ++a) p[a] = df_mul_add(c[k * W + a], p[a], x);
 }
 
-/* double-float window values per point (see launch_point_windows_df): one thread per point,
+/* double-float window values per point (see launch_frac_windows_df): one thread per point,
  * Horner in double-float on the kWinPieces-piece per-tap polynomials staged in shared memory
- * (piece h of u = l0 - t + w/2 in [0, 1) is [h/P, (h+1)/P), argument x = 2P u - 2h - 1) */
+ * (piece h of u = l0 - t + w/2 in [0, 1) is [h/P, (h+1)/P), argument x = 2P u - 2h - 1); the
+ * argument comes from the point's exact FP32 pair u, so no FP64 arithmetic is involved */
 template <int W>
-__global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
-                                   const int *__restrict__ count, const float2 *__restrict__ coef,
-                                   int deriv, int64_t pitch, float2 *__restrict__ out,
-                                   const int *__restrict__ idx, int64_t idx_lim)
+__global__ void k_frac_windows_df(int64_t n, const float4 *__restrict__ frac,
+                                  const int *__restrict__ count, const float2 *__restrict__ coef,
+                                  int deriv, int64_t pitch, float2 *__restrict__ out,
+                                  const int *__restrict__ idx, int64_t idx_lim)
 {
     constexpr int NP = kWinPieces, D = kPieceDeg[W];
     extern __shared__ __align__(16) unsigned char sm[];
@@ -355,64 +527,69 @@ __global__ void k_point_windows_df(int64_t n, const double2 *__restrict__ pts,
     for (int i = threadIdx.x; i < m; i += blockDim.x) cw[i] = df32(coef[i].x, coef[i].y);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t wbase = i - lane; /* the warp's first point */
     /* every lane stays to the end (the point-major stores are warp-cooperative); lanes past the
-     * valid points or outside the box compute a dummy point and store nothing */
+     * valid points compute a dummy point and store nothing */
     const int64_t nv = count ? min(n, (int64_t)*count) : n;
-    double2 t = make_double2(0.0, 0.0);
-    bool ok = i < nv;
-    if (ok && idx) { /* point i is pts[idx[i]]; indices >= idx_lim get no values */
-        const int k = idx[i];
-        ok = k < idx_lim;
-        if (ok) t = pts[k];
-    } else if (ok) {
-        t = pts[i];
-    }
-    if (ok) {
-        ok = t.x >= 0.0; /* outside the box: no entries */
-        if (!ok) t = make_double2(0.0, 0.0);
-    }
-    const unsigned okm = __ballot_sync(0xffffffffu, ok);
     const int stride = deriv ? 4 * W : 2 * W;
-    /* part q (W values) of every point: value-major planes (value k of point i at k * pitch + i,
-     * the interpolation's lanes then read consecutive points) or point-major records (values
-     * i * stride + q W + a), the latter staged per warp in shared memory and written as
-     * consecutive addresses */
     float2 *stg = reinterpret_cast<float2 *>(cw + m) + (size_t)warp * 32 * (W + 1);
-    auto emit = [&](int q, const df32 (&v)[W]) {
-        if (pitch) {
-            if (ok)
-#pragma unroll
-                for (int a = 0; a < W; ++a)
-                    out[(int64_t)(q * W + a) * pitch + i] = make_float2(v[a].hi, v[a].lo);
-            return;
-        }
-#pragma unroll
-        for (int a = 0; a < W; ++a) stg[lane * (W + 1) + a] = make_float2(v[a].hi, v[a].lo);
-        __syncwarp();
-        for (int e = lane; e < 32 * W; e += 32) {
-            const int pt = e / W, a = e - pt * W;
-            if ((okm >> pt) & 1u)
-                out[(size_t)(wbase + pt) * stride + q * W + a] = stg[pt * (W + 1) + a];
-        }
-        __syncwarp(); /* the buffer is refilled by the next part */
+    /* the argument x = 2P u - (2h + 1) of u = (uh, ul): 2P uh and the integer are exact in FP32,
+     * so one two-sum gives their difference exactly; 2P ul is added to its low word */
+    auto piece_arg = [&](float uh, float ul, int &h) {
+        h = max(0, min(NP - 1, __float2int_rz(uh * (float)NP)));
+        const df32 s = df32(YK_FMUL(2.0f * NP, uh), 0.0f) + df32(-(float)(2 * h + 1), 0.0f);
+        return df_fast_two_sum(s.hi, YK_FADD(s.lo, YK_FMUL(2.0f * NP, ul)));
     };
-    const double ux = ((double)first_tap<W>(t.x) - t.x) + 0.5 * W;
-    const double uy = ((double)first_tap<W>(t.y) - t.y) + 0.5 * W;
-    const int hx = max(0, min(NP - 1, (int)(ux * NP))), hy = max(0, min(NP - 1, (int)(uy * NP)));
-    const df32 ax(2.0 * NP * ux - 2.0 * hx - 1.0), ay(2.0 * NP * uy - 2.0 * hy - 1.0);
-    df32 p[W];
-    windows_piece<W, D>(cw + hy * (D + 1) * W, ay, p);
-    emit(0, p);
-    windows_piece<W, D>(cw + hx * (D + 1) * W, ax, p);
-    emit(1, p);
-    if (deriv) {
-        const df32 *cwd = cw + NP * (D + 1) * W;
-        windows_piece<W, D - 1>(cwd + hy * D * W, ay, p);
-        emit(2, p);
-        windows_piece<W, D - 1>(cwd + hx * D * W, ax, p);
-        emit(3, p);
+    /* grid-stride over blocks of points, so the coefficient tables are staged once per CTA */
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nv;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t wbase = i - lane; /* the warp's first point */
+        float4 fr = make_float4(0.5f, 0.0f, 0.5f, 0.0f);
+        bool ok = i < nv;
+        if (ok && idx) { /* point i is frac[idx[i]]; indices >= idx_lim get no values */
+            const int k = idx[i];
+            ok = k < idx_lim;
+            if (ok) fr = frac[k];
+        } else if (ok) {
+            fr = frac[i];
+        }
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+        /* part q (W values) of every point: value-major planes (value k of point i at
+         * k * pitch + i, the interpolation's lanes then read consecutive points) or point-major
+         * records (values i * stride + q W + a), the latter staged per warp in shared memory and
+         * written as consecutive addresses */
+        auto emit = [&](int q, const df32 (&v)[W]) {
+            if (pitch) {
+                if (ok)
+#pragma unroll
+                    for (int a = 0; a < W; ++a)
+                        out[(int64_t)(q * W + a) * pitch + i] = make_float2(v[a].hi, v[a].lo);
+                return;
+            }
+#pragma unroll
+            for (int a = 0; a < W; ++a) stg[lane * (W + 1) + a] = make_float2(v[a].hi, v[a].lo);
+            __syncwarp();
+            for (int e = lane; e < 32 * W; e += 32) {
+                const int pt = e / W, a = e - pt * W;
+                if ((okm >> pt) & 1u)
+                    out[(size_t)(wbase + pt) * stride + q * W + a] = stg[pt * (W + 1) + a];
+            }
+            __syncwarp(); /* the buffer is refilled by the next part */
+        };
+        int hx, hy;
+        const df32 ax = piece_arg(fr.x, fr.y, hx), ay = piece_arg(fr.z, fr.w, hy);
+        df32 p[W];
+        windows_piece<W, D>(cw + hy * (D + 1) * W, ay, p);
+        emit(0, p);
+        windows_piece<W, D>(cw + hx * (D + 1) * W, ax, p);
+        emit(1, p);
+        if (deriv) {
+            const df32 *cwd = cw + NP * (D + 1) * W;
+            windows_piece<W, D - 1>(cwd + hy * D * W, ay, p);
+            emit(2, p);
+            windows_piece<W, D - 1>(cwd + hx * D * W, ax, p);
+            emit(3, p);
+        }
     }
 }
 
@@ -723,24 +900,98 @@ __global__ void k_pack_wnu(int64_t nd, const double *__restrict__ wd, const doub
     if (d < nd) wnu[d] = make_double2(wd[d] * nx[d], wd[d] * ny[d]);
 }
 
-cudaError_t launch_point_windows_df(const Geom &g, int64_t n, const double2 *pts,
-                                    const int *count, const float2 *coef, int deg, bool deriv,
-                                    float2 *out, cudaStream_t st, int64_t pitch, const int *idx,
-                                    int64_t idx_lim)
+cudaError_t launch_frac_windows_df(const Geom &g, int64_t n, const float4 *frac, const int *count,
+                                   const float2 *coef, int deg, bool deriv, float2 *out,
+                                   cudaStream_t st, int64_t pitch, const int *idx, int64_t idx_lim)
 {
     if (n <= 0) return cudaSuccess;
     if (g.w < 2 || g.w > 16 || deg != kPieceDeg[g.w]) return cudaErrorInvalidValue;
     /* coefficient tables, then a 32 x (w + 1) staging buffer per warp of 256 threads */
     const size_t smem = sizeof(df32) * kWinPieces * ((deg + 1) * g.w + (deriv ? deg * g.w : 0)) +
                         sizeof(float2) * 8 * 32 * (g.w + 1);
-    const int blocks = (int)((n + 255) / 256);
+    /* grid-stride: at most 8 CTAs of 256 points per SM of a 148-SM part, looping over the rest */
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
     cudaError_t e = cudaSuccess;
 #define YK_CALL(W)                                                                              \
-    if ((e = set_smem(k_point_windows_df<W>, smem)) != cudaSuccess) return e;                  \
-    k_point_windows_df<W><<<blocks, 256, smem, st>>>(n, pts, count, coef, deriv ? 1 : 0, pitch, \
-                                                     out, idx, idx_lim)
+    if ((e = set_smem(k_frac_windows_df<W>, smem)) != cudaSuccess) return e;                   \
+    k_frac_windows_df<W><<<blocks, 256, smem, st>>>(n, frac, count, coef, deriv ? 1 : 0, pitch,  \
+                                                    out, idx, idx_lim)
     YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
+                                int64_t nd, const double *xd, const double *yd, int2 *tap,
+                                float4 *frac, int *tile_cnt, int *tile_ptr, int *tile_cur,
+                                double2 *ent_t, int *ent_j, int *err, cudaStream_t st, bool owner)
+{
+    const int ntiles = g.nt * g.nt;
+    cudaError_t e = cudaMemsetAsync(tile_cnt, 0, sizeof(int) * ntiles, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(tile_cur, 0, sizeof(int) * ntiles, st);
+    if (e != cudaSuccess) return e;
+    /* the two point sets: charges, then dipoles (index offset ns) */
+    const int64_t cnt[2] = {ns, nd};
+    const double *px[2] = {xs, xd}, *py[2] = {ys, yd};
+    for (int k = 0; k < 2; ++k) {
+        if (cnt[k] <= 0) continue;
+        const int blocks = (int)((cnt[k] + 255) / 256);
+        const int64_t o = k ? ns : 0;
+#define YK_CALL(W)                                                                              \
+    if (owner)                                                                                  \
+        k_prep_src_count<W, true><<<blocks, 256, 0, st>>>(cnt[k], px[k], py[k], g, tap + o,     \
+                                                          frac + o, tile_cnt, err);             \
+    else                                                                                        \
+        k_prep_src_count<W, false><<<blocks, 256, 0, st>>>(cnt[k], px[k], py[k], g, tap + o,    \
+                                                           frac + o, tile_cnt, err)
+        YK_W_DISPATCH(g.w, YK_CALL)
+#undef YK_CALL
+    }
+    if ((e = launch_scan(tile_cnt, tile_ptr, ntiles, tile_cur, st)) != cudaSuccess) return e;
+    for (int k = 0; k < 2; ++k) {
+        if (cnt[k] <= 0) continue;
+        const int blocks = (int)((cnt[k] + 255) / 256);
+        const int64_t o = k ? ns : 0;
+#define YK_CALL(W)                                                                              \
+    if (owner)                                                                                  \
+        k_prep_src_fill<W, true><<<blocks, 256, 0, st>>>(cnt[k], tap + o, frac + o, g, tile_ptr, \
+                                                         tile_cur, ent_t, ent_j, (int)o);       \
+    else                                                                                        \
+        k_prep_src_fill<W, false><<<blocks, 256, 0, st>>>(cnt[k], tap + o, frac + o, g,         \
+                                                          tile_ptr, tile_cur, ent_t, ent_j,     \
+                                                          (int)o)
+        YK_W_DISPATCH(g.w, YK_CALL)
+#undef YK_CALL
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_targets(const Geom &g, int64_t nt, const double *xt, const double *yt,
+                                int4 *tap_tmp, float4 *frac_tmp, int *cnt, int *ptr, int *cur,
+                                double2 *trg_t, float4 *trg_frac, int *trg_idx, int *err,
+                                cudaStream_t st)
+{
+    const int ntiles = g.nt * g.nt;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ntiles, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(cur, 0, sizeof(int) * ntiles, st);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)((nt + 255) / 256);
+    if (nt > 0) {
+#define YK_CALL(W)                                                                              \
+    k_prep_trg_count<W><<<blocks, 256, 0, st>>>(nt, xt, yt, g, tap_tmp, frac_tmp, cnt, err)
+        YK_W_DISPATCH(g.w, YK_CALL)
+#undef YK_CALL
+    }
+    if ((e = launch_scan(cnt, ptr, ntiles, cur, st)) != cudaSuccess) return e;
+    if (nt > 0) {
+#define YK_CALL(W)                                                                              \
+    k_prep_trg_fill<W><<<blocks, 256, 0, st>>>(nt, tap_tmp, frac_tmp, ptr, cur, trg_t, trg_frac, \
+                                               trg_idx)
+        YK_W_DISPATCH(g.w, YK_CALL)
+#undef YK_CALL
+    }
     return cudaGetLastError();
 }
 

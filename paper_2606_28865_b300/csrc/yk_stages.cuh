@@ -1139,9 +1139,10 @@ template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned 
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;
     stage_halo<df32>(sg, static_cast<const df32 *>(d.grid), g, X0, Y0, P);
     __syncthreads();
+    const int4 *__restrict__ trg = reinterpret_cast<const int4 *>(d.trg_t);
     for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
-        const double2 t = d.trg_t[e];
-        const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
+        const int4 r = trg[e]; /* first taps (lx, ly), from the fixed-point preparation */
+        const int lx = r.x, ly = r.y;
         /* window values of this target, computed at yk_set_points: planes [phi_y taps | phi_x
          * taps], value k at k * pitch + e (consecutive threads read consecutive targets) */
         const float2 *wv = d.win_trg + e;
