@@ -554,6 +554,11 @@ yk::Geom geom_of(const yk_plan_s *p)
     g.Bx = -p->ox * g.A;
     g.By = -p->oy * g.A;
     g.n44 = (long long)p->n << yk::kFixBits;
+    /* the same FMA and rounding as the device's fixed_coord (both IEEE, round to nearest even) */
+    g.tbox[0] = std::llrint(std::fma(p->box[0], g.A, g.Bx));
+    g.tbox[1] = std::llrint(std::fma(p->box[1], g.A, g.Bx));
+    g.tbox[2] = std::llrint(std::fma(p->box[2], g.A, g.By));
+    g.tbox[3] = std::llrint(std::fma(p->box[3], g.A, g.By));
     return g;
 }
 

@@ -77,6 +77,13 @@ YK_HD df32 df_fast_two_sum(float a, float b)
     const float s = YK_FADD(a, b);
     return df32(s, YK_FSUB(b, YK_FSUB(s, a)));
 }
+/* a + b exactly as a normalised pair, whatever their magnitudes (Knuth's two-sum) */
+YK_HD df32 df_two_sum(float a, float b)
+{
+    const float s = YK_FADD(a, b);
+    const float bb = YK_FSUB(s, a);
+    return df32(s, YK_FADD(YK_FSUB(a, YK_FSUB(s, bb)), YK_FSUB(b, bb)));
+}
 YK_HD df32 operator+(df32 a, df32 b)
 {
     const float s = YK_FADD(a.hi, b.hi);

@@ -38,6 +38,8 @@ struct Geom {
      * coordinate in [0, n) has T in [0, n44), n44 = n 2^44 */
     double A, Bx, By;
     long long n44;
+    long long tbox[4]; /* the box edges in the same fixed point (rounding is monotonic, so a
+                          point in the box has tbox[0] <= T_x <= tbox[1], tbox[2] <= T_y <= tbox[3]) */
 };
 
 /* fraction bits of the fixed-point grid coordinate */

@@ -249,14 +249,23 @@ __device__ __forceinline__ void tap_tiles(int lx, int ly, int W, const Geom &g, 
     tiles[3] = (ay1 != ay0 && ax1 != ax0) ? ay1 * g.nt + ax1 : -1;
 }
 
-/* prepare one point: false when it lies outside the box or the grid */
+/* a finite double (exponent field not all ones), tested on its bits */
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
+/* prepare one point: false when it lies outside the box or the grid (the box test in the fixed
+ * point of the coordinates, so no FP64 comparison is needed) */
 template <int W>
 __device__ __forceinline__ bool prep_point(const Geom &g, double x, double y, int2 &tap,
                                            float4 &fr, long long &Tx, long long &Ty)
 {
     Tx = fixed_coord(x, g.A, g.Bx);
     Ty = fixed_coord(y, g.A, g.By);
-    if (!(in_box(g, x, y) && Tx >= 0 && Tx < g.n44 && Ty >= 0 && Ty < g.n44)) return false;
+    if (!(finite_bits(x) && finite_bits(y) && Tx >= g.tbox[0] && Tx <= g.tbox[1] &&
+          Ty >= g.tbox[2] && Ty <= g.tbox[3] && Tx >= 0 && Tx < g.n44 && Ty >= 0 && Ty < g.n44))
+        return false;
     tap_frac<W>(Tx, tap.x, fr.x, fr.y);
     tap_frac<W>(Ty, tap.y, fr.z, fr.w);
     return true;
@@ -350,26 +359,50 @@ __global__ void k_prep_trg_count(int64_t nt, const double *__restrict__ xt,
 }
 
 /* targets grouped by the tile of their cell: records (lx, ly, sx, sy) and, when trg_frac is
- * given, the window arguments in the same order */
+ * given, the window arguments in the same order.  Each thread takes kFillPer targets (a block's
+ * targets strided by the block size) and issues their slot reservations back to back, so the
+ * atomics' latencies overlap (uniformly spread targets rarely share a tile within a warp). */
+constexpr int kFillPer = 4;
+
 template <int W>
 __global__ void k_prep_trg_fill(int64_t nt, const int4 *__restrict__ tap4,
                                 const float4 *__restrict__ frac, const int *__restrict__ ptr,
                                 int *__restrict__ cur, double2 *__restrict__ trg_t,
                                 float4 *__restrict__ trg_frac, int *__restrict__ trg_idx)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int4 tp = make_int4(0, 0, -1, 0);
-    if (i < nt) tp = tap4[i];
-    const int tile = tp.z;
-    const bool v = tile >= 0;
-    const int off = agg_reserve(cur, tile, v);
-    if (v) {
-        const float4 fr = frac[i];
-        const int slot = ptr[tile] + off;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x * kFillPer + threadIdx.x;
+    int4 tp[kFillPer];
+    float4 fr[kFillPer];
+#pragma unroll
+    for (int k = 0; k < kFillPer; ++k) {
+        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        tp[k] = i < nt ? tap4[i] : make_int4(0, 0, -1, 0);
+        if (tp[k].z >= 0) fr[k] = frac[i];
+    }
+    /* agg_reserve split in two passes: all groups' atomics first, then the broadcasts */
+    const int lane = threadIdx.x & 31;
+    unsigned grp[kFillPer];
+    int base[kFillPer], off[kFillPer];
+#pragma unroll
+    for (int k = 0; k < kFillPer; ++k) {
+        const bool v = tp[k].z >= 0;
+        grp[k] = __match_any_sync(0xffffffffu, v ? tp[k].z : -1 - lane);
+        base[k] = 0;
+        if (v && lane == __ffs(grp[k]) - 1) base[k] = atomicAdd(&cur[tp[k].z], __popc(grp[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < kFillPer; ++k)
+        off[k] = __shfl_sync(grp[k], base[k], __ffs(grp[k]) - 1) +
+                 __popc(grp[k] & ((1u << lane) - 1u));
+#pragma unroll
+    for (int k = 0; k < kFillPer; ++k) {
+        if (tp[k].z < 0) continue;
+        const int64_t i = i0 + (int64_t)k * blockDim.x;
+        const int slot = ptr[tp[k].z] + off[k];
         *reinterpret_cast<int4 *>(trg_t + slot) =
-            make_int4(tp.x, tp.y, __float_as_int(frac_offset<W>(fr.x, fr.y)),
-                      __float_as_int(frac_offset<W>(fr.z, fr.w)));
-        if (trg_frac) trg_frac[slot] = fr;
+            make_int4(tp[k].x, tp[k].y, __float_as_int(frac_offset<W>(fr[k].x, fr[k].y)),
+                      __float_as_int(frac_offset<W>(fr[k].z, fr[k].w)));
+        if (trg_frac) trg_frac[slot] = fr[k];
         trg_idx[slot] = (int)i;
     }
 }
@@ -496,18 +529,43 @@ __global__ void k_order_fill(const int *__restrict__ ptr, int ntiles, int *__res
     if (v) order[off] = t;
 }
 
+/* Shared-memory layout of the window tables in the window kernel: piece h's coefficient k of tap
+ * a at h S + k WE + a, with WE = W rounded up to even (so a tap pair is one aligned 16-byte
+ * load) and the piece stride S = (deg + 1) WE padded to an odd number of 16-byte slots: the lanes
+ * of a warp read random pieces, and an odd stride spreads them over all bank groups instead of a
+ * few. */
+__host__ __device__ constexpr int win_even(int W) { return W + (W & 1); }
+__host__ __device__ constexpr int win_piece_stride(int W, int D)
+{
+    return ((D + 1) * win_even(W) / 2) % 2 ? (D + 1) * win_even(W) : (D + 1) * win_even(W) + 2;
+}
+
 /* W window values of one coordinate by Horner in double-float on the piece's polynomials
  * (compile-time degree D, taps interleaved: W independent chains); each step c_k + p x is one
  * fused double-float multiply-add (exact product terms added to c_k by two-sum) */
 template <int W, int D>
 __device__ __forceinline__ void windows_piece(const df32 *c, df32 x, df32 (&p)[W])
 {
+    constexpr int WE = win_even(W);
+    df32 ck[WE];
+    auto row = [&](int k) {
+        const float4 *r = reinterpret_cast<const float4 *>(c + k * WE);
 #pragma unroll
-    for (int a = 0; a < W; ++a) p[a] = c[D * W + a];
+        for (int m = 0; m < WE / 2; ++m) {
+            const float4 v = r[m];
+            ck[2 * m] = df32(v.x, v.y);
+            ck[2 * m + 1] = df32(v.z, v.w);
+        }
+    };
+    row(D);
 #pragma unroll
-    for (int k = D - 1; k >= 0; --k)
+    for (int a = 0; a < W; ++a) p[a] = ck[a];
 #pragma unroll
-        for (int a = 0; a < W; ++a) p[a] = df_mul_add(c[k * W + a], p[a], x);
+    for (int k = D - 1; k >= 0; --k) {
+        row(k);
+#pragma unroll
+        for (int a = 0; a < W; ++a) p[a] = df_mul_add(ck[a], p[a], x);
+    }
 }
 
 /* double-float window values per point (see launch_frac_windows_df): one thread per point,
@@ -520,11 +578,21 @@ __global__ void k_frac_windows_df(int64_t n, const float4 *__restrict__ frac,
                                   int deriv, int64_t pitch, float2 *__restrict__ out,
                                   const int *__restrict__ idx, int64_t idx_lim)
 {
-    constexpr int NP = kWinPieces, D = kPieceDeg[W];
+    constexpr int NP = kWinPieces, D = kPieceDeg[W], WE = win_even(W);
+    constexpr int S0 = win_piece_stride(W, D), S1 = win_piece_stride(W, D - 1);
     extern __shared__ __align__(16) unsigned char sm[];
     df32 *cw = reinterpret_cast<df32 *>(sm);
-    const int m = NP * (D + 1) * W + (deriv ? NP * D * W : 0);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) cw[i] = df32(coef[i].x, coef[i].y);
+    /* the tables (window, then derivative) in the padded layout; the pad cells are zero */
+    const int m = NP * S0 + (deriv ? NP * S1 : 0);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) cw[i] = df32(0.0f, 0.0f);
+    __syncthreads();
+    const int n0 = NP * (D + 1) * W, n1 = deriv ? NP * D * W : 0;
+    for (int i = threadIdx.x; i < n0 + n1; i += blockDim.x) {
+        const bool dv = i >= n0;
+        const int j = dv ? i - n0 : i, rows = dv ? D : D + 1;
+        const int a = j % W, hk = j / W, h = hk / rows, k = hk - h * rows;
+        cw[(dv ? NP * S0 : 0) + h * (dv ? S1 : S0) + k * WE + a] = df32(coef[i].x, coef[i].y);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     /* every lane stays to the end (the point-major stores are warp-cooperative); lanes past the
@@ -579,15 +647,15 @@ __global__ void k_frac_windows_df(int64_t n, const float4 *__restrict__ frac,
         int hx, hy;
         const df32 ax = piece_arg(fr.x, fr.y, hx), ay = piece_arg(fr.z, fr.w, hy);
         df32 p[W];
-        windows_piece<W, D>(cw + hy * (D + 1) * W, ay, p);
+        windows_piece<W, D>(cw + hy * S0, ay, p);
         emit(0, p);
-        windows_piece<W, D>(cw + hx * (D + 1) * W, ax, p);
+        windows_piece<W, D>(cw + hx * S0, ax, p);
         emit(1, p);
         if (deriv) {
-            const df32 *cwd = cw + NP * (D + 1) * W;
-            windows_piece<W, D - 1>(cwd + hy * D * W, ay, p);
+            const df32 *cwd = cw + NP * S0;
+            windows_piece<W, D - 1>(cwd + hy * S1, ay, p);
             emit(2, p);
-            windows_piece<W, D - 1>(cwd + hx * D * W, ax, p);
+            windows_piece<W, D - 1>(cwd + hx * S1, ax, p);
             emit(3, p);
         }
     }
@@ -906,8 +974,9 @@ cudaError_t launch_frac_windows_df(const Geom &g, int64_t n, const float4 *frac,
 {
     if (n <= 0) return cudaSuccess;
     if (g.w < 2 || g.w > 16 || deg != kPieceDeg[g.w]) return cudaErrorInvalidValue;
-    /* coefficient tables, then a 32 x (w + 1) staging buffer per warp of 256 threads */
-    const size_t smem = sizeof(df32) * kWinPieces * ((deg + 1) * g.w + (deriv ? deg * g.w : 0)) +
+    /* coefficient tables (padded layout), then a 32 x (w + 1) staging buffer per warp */
+    const size_t smem = sizeof(df32) * kWinPieces *
+                            (win_piece_stride(g.w, deg) + (deriv ? win_piece_stride(g.w, deg - 1) : 0)) +
                         sizeof(float2) * 8 * 32 * (g.w + 1);
     /* grid-stride: at most 8 CTAs of 256 points per SM of a 148-SM part, looping over the rest */
     const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
@@ -986,9 +1055,10 @@ cudaError_t launch_prep_targets(const Geom &g, int64_t nt, const double *xt, con
     }
     if ((e = launch_scan(cnt, ptr, ntiles, cur, st)) != cudaSuccess) return e;
     if (nt > 0) {
+        const int fblocks = (int)((nt + 256 * kFillPer - 1) / (256 * kFillPer));
 #define YK_CALL(W)                                                                              \
-    k_prep_trg_fill<W><<<blocks, 256, 0, st>>>(nt, tap_tmp, frac_tmp, ptr, cur, trg_t, trg_frac, \
-                                               trg_idx)
+    k_prep_trg_fill<W><<<fblocks, 256, 0, st>>>(nt, tap_tmp, frac_tmp, ptr, cur, trg_t, trg_frac, \
+                                                trg_idx)
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     }

@@ -1157,11 +1157,14 @@ template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned 
         df32 acc(0.0f, 0.0f);
 #pragma unroll
         for (int c = 0; c < W; ++c) {
-            df32 row = fx[0] * base[c * P];
+            /* row sum of W products with the unnormalised multiply-add (exact two-sum of the
+             * high words, low words gathered), renormalised once by a full two-sum */
+            df32 row(0.0f, 0.0f);
 #pragma unroll
-            for (int a = 1; a < W; ++a) row = row + fx[a] * base[c * P + a];
+            for (int a = 0; a < W; ++a) row = df_mul_add_lazy(row, fx[a], base[c * P + a]);
+            row = df_two_sum(row.hi, row.lo);
             const float2 wy = wv[c * pw];
-            acc = acc + df32(wy.x, wy.y) * row;
+            acc = df_mul_add(acc, df32(wy.x, wy.y), row);
         }
         d.u[d.trg_idx[e]] = acc.to_double();
     }
