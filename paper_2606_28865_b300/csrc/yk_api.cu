@@ -624,7 +624,7 @@ yk_status plan_tables(yk_plan_t p)
     YK_TRY(buf_alloc(p, p->trg_cnt, sizeof(int) * nt2, "tile counts"));
     YK_TRY(buf_alloc(p, p->trg_ptr, sizeof(int) * (nt2 + 1), "tile offsets"));
     YK_TRY(buf_alloc(p, p->trg_cur, sizeof(int) * nt2, "tile cursors"));
-    if (p->fft_df) { /* owner-tile spread: one padded tile of partial sums per tile */
+    if (p->fft_df || f32) { /* owner-tile spread: one padded tile of partial sums per tile */
         const size_t span = (size_t)p->T + p->w - 1;
         YK_TRY(buf_alloc(p, p->part, sizeof(double) * nt2 * span * span, "padded tiles"));
     }
@@ -813,7 +813,7 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->order = P<int>(p->tile_order);
     d->ent_t = P<double2>(p->ent_t);
     d->ent_j = P<int>(p->ent_j);
-    d->part = p->fft_df ? p->part.ptr : nullptr;
+    d->part = (p->fft_df || d->f32) ? p->part.ptr : nullptr;
     d->wq = P<double>(p->w_src);
     d->trg_ptr = P<int>(p->trg_ptr);
     d->trg_t = P<double2>(p->trg_t);
@@ -966,7 +966,7 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
         if (o->tile > 0) {
             if (n % o->tile == 0 && o->tile >= w && n >= 2 * o->tile) T = o->tile;
         } else {
-            /* per-warp private tiles (FP32C and the double-float FP64 spread) need T <= 32 */
+            /* the owner-tile spreads (FP32C, double-float FP64) keep per-warp padded copies: T <= 32 */
             const int tmax = (o->precision == YK_FP32C || !o->fft_fp64) ? 32 : 64;
             const int pref = o->use_tuned ? yk_tuned_tile(o->precision, w, n, o->n_src_hint) : 0;
             for (int t = tmax; t >= w; --t)
@@ -995,9 +995,10 @@ static int64_t predicted_bytes(const yk_plan_s *p, int64_t n_src, int64_t n_trg)
                 4 * (n / 2) + 4 * n + 4 * (7 * nt2 + 2) + 4;
     if (p->precision == YK_FP64) b += 8 * (int64_t)(p->w + 2) * p->w * (p->dlp ? 2 : 1);
     else if (p->dlp) b += 4 * (int64_t)(2 * p->w + 3) * p->w;
-    const int64_t epp = p->fft_df ? 1 : 4; /* entries per source */
+    const bool owner = p->fft_df || p->precision == YK_FP32C;
+    const int64_t epp = owner ? 1 : 4; /* entries per source */
     b += n_src * (8 + 16 + epp * (16 + 4)) + n_trg * (16 + 4 + 16);
-    if (p->fft_df) b += 8 * nt2 * (int64_t)(p->T + p->w - 1) * (p->T + p->w - 1);
+    if (owner) b += 8 * nt2 * (int64_t)(p->T + p->w - 1) * (p->T + p->w - 1);
     if (p->fft_df) b += (n_src + n_trg) * 16 * (int64_t)p->w; /* per-point window values */
     return b;
 }
@@ -1116,7 +1117,7 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
     YK_TRY(buf_alloc(p, p->w_src, sizeof(double) * ns, "weights"));
     YK_TRY(buf_alloc(p, p->src_t, sizeof(double2) * (ns + nd), "source coordinates"));
     /* entries: one per source for the owner-tile spread, else one per tile a window touches */
-    const size_t epp = p->fft_df ? 1 : 4;
+    const size_t epp = (p->fft_df || p->precision == YK_FP32C) ? 1 : 4;
     YK_TRY(buf_alloc(p, p->ent_t, sizeof(double2) * epp * (ns + nd), "entries"));
     YK_TRY(buf_alloc(p, p->ent_j, sizeof(int) * epp * (ns + nd), "entries"));
     YK_TRY(buf_alloc(p, p->trg_t, sizeof(double2) * nt, "targets"));
@@ -1154,7 +1155,7 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
                                       P<float4>(p->src_t), P<int>(p->tile_cnt),
                                       P<int>(p->tile_ptr), P<int>(p->tile_cur),
                                       P<double2>(p->ent_t), P<int>(p->ent_j), P<int>(p->err),
-                                      p->stream, p->fft_df != 0),
+                                      p->stream, true),
               "bin sources");
     else
         YK_CU(yk::launch_bin_sources(g, n_src, dx, dy, n_dip, ddx, ddy, P<double2>(p->src_t),

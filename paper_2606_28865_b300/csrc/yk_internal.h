@@ -166,9 +166,6 @@ cudaError_t launch_tile_order(const int *tile_ptr, int ntiles, int *order, int *
 cudaError_t launch_spread(const Geom &g, const int *tile_ptr, const int *order,
                           const double2 *ent_t, const int *ent_j, const double *wq,
                           const double *dens, double *grid, cudaStream_t st);
-cudaError_t launch_spread32(const Geom &g, const int *tile_ptr, const int *order,
-                            const double2 *ent_t, const int *ent_j, const double *wq,
-                            const double *dens, float *grid, cudaStream_t st);
 cudaError_t launch_row_fwd(const double *grid, double2 *spec, const double2 *tw, const int *perm_h,
                            const FftStages &sth, int n, int M, cudaStream_t st);
 cudaError_t launch_columns(double2 *spec, const double *mult, const double2 *tw,

@@ -669,15 +669,16 @@ template <int W> __global__ void __launch_bounds__(256) k_spread(Inst d)
     extern __shared__ __align__(16) unsigned char sm[];
     st_spread64<W>(d, blockIdx.x, sm);
 }
-template <int W> __global__ void __launch_bounds__(32 * kSpreadWarps) k_spread32(Inst d)
+template <int W> __global__ void __launch_bounds__(32 * kOwnerCopies, 3) k_spread_owner32(Inst d)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    st_spread32<W>(d, blockIdx.x, sm);
+    st_spread_owner32<W, false>(d, blockIdx.x, sm);
 }
-template <int W> __global__ void __launch_bounds__(32 * kSpreadWarps, 2) k_spread_df(Inst d)
+template <int W>
+__global__ void __launch_bounds__(32 * kOwnerCopies, 2) k_spread_owner32_dip(Inst d)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    st_spread_df<W>(d, blockIdx.x, sm);
+    st_spread_owner32<W, true>(d, blockIdx.x, sm);
 }
 template <int W> __global__ void __launch_bounds__(32 * kOwnerCopies, 3) k_spread_owner_df(Inst d)
 {
@@ -849,19 +850,17 @@ int stage_smem(const Inst &d, int stage)
     const int c = d.f32 ? 8 : 16;          /* bytes of a complex value */
     switch (stage) {
     case ST_SPREAD:
-        if (d.fft_df && d.part) /* owner-tile spread: kOwnerCopies padded copies */
+        if (d.f32) /* FP32C owner-tile spread: kOwnerCopies padded copies of (hi, lo) pairs */
+            return (int)(sizeof(float2) * kOwnerCopies * owner_copy_cells(T, W) +
+                         sizeof(float) * kOwnerCopies * kOwnerBatch32 * (SW + 1) +
+                         sizeof(int) * kOwnerCopies * kOwnerBatch32 +
+                         (d.dip ? sizeof(float) * ncoef : 0));
+        if (d.fft_df) /* double-float owner-tile spread */
             return (int)(sizeof(df32) * kOwnerCopies *
                              (owner_copy_cells(T, W) +
                               kSpreadBatch * (owner_batch_stride(W, d.dip != 0) + 1)) +
                          sizeof(int) * kOwnerCopies * kSpreadBatch);
-        if (d.fft_df)
-            return (int)(sizeof(df32) * kSpreadWarps * spread_tile_cells(T) +
-                         sizeof(df32) * kSpreadWarps * kSpreadBatch * SW +
-                         sizeof(int) * kSpreadWarps * 2 * kSpreadBatch);
-        return d.f32 ? (int)(sizeof(float2) * kSpreadWarps * spread_tile_cells(T) +
-                             sizeof(float) * kSpreadWarps * 32 * SW +
-                             sizeof(int) * kSpreadWarps * 64 + (d.dip ? sizeof(float) * ncoef : 0))
-                     : (int)(sizeof(unsigned long long) * T * T + win_bytes);
+        return (int)(sizeof(unsigned long long) * T * T + win_bytes);
     case ST_ROW_FWD:
     case ST_ROW_INV: return c * d.rows * (d.n / 2);
     case ST_COLUMNS: return c * d.n;
@@ -1134,31 +1133,6 @@ cudaError_t launch_spread(const Geom &g, const int *tile_ptr, const int *order,
     return cudaGetLastError();
 }
 
-cudaError_t launch_spread32(const Geom &g, const int *tile_ptr, const int *order,
-                            const double2 *ent_t, const int *ent_j, const double *wq,
-                            const double *dens, float *grid, cudaStream_t st)
-{
-    Inst d = blank_inst(g.n, 0);
-    d.g = g;
-    d.f32 = 1;
-    d.tile_ptr = tile_ptr;
-    d.order = order;
-    d.ent_t = ent_t;
-    d.ent_j = ent_j;
-    d.wq = wq;
-    d.dens = dens;
-    d.grid = grid;
-    const size_t smem = stage_smem(d, ST_SPREAD);
-    cudaError_t e = cudaSuccess;
-#define YK_CALL(W)                                                                              \
-    e = set_smem(k_spread32<W>, smem);                                                          \
-    if (e != cudaSuccess) return e;                                                             \
-    k_spread32<W><<<g.nt * g.nt, 32 * kSpreadWarps, smem, st>>>(d)
-    YK_W_DISPATCH(g.w, YK_CALL)
-#undef YK_CALL
-    return cudaGetLastError();
-}
-
 template <typename R>
 cudaError_t launch_fft_t(int stage, const void *grid_in, void *grid_out, void *spec,
                          const void *mult, const void *tw, const int *perm_h, const int *iperm_f,
@@ -1289,20 +1263,20 @@ cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st)
     } while (0)
     switch (stage) {
     case ST_SPREAD:
-        if (d.f32) {
-#define YK_CALL(W) YK_LAUNCH(k_spread32<W>, 32 * kSpreadWarps)
+        if (d.f32 && d.dip) {
+#define YK_CALL(W) YK_LAUNCH(k_spread_owner32_dip<W>, 32 * kOwnerCopies)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
-        } else if (d.fft_df && d.part && d.dip) {
+        } else if (d.f32) {
+#define YK_CALL(W) YK_LAUNCH(k_spread_owner32<W>, 32 * kOwnerCopies)
+            YK_W_DISPATCH(d.g.w, YK_CALL)
+#undef YK_CALL
+        } else if (d.fft_df && d.dip) {
 #define YK_CALL(W) YK_LAUNCH(k_spread_owner_df_dip<W>, 32 * kOwnerCopies)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
-        } else if (d.fft_df && d.part) {
-#define YK_CALL(W) YK_LAUNCH(k_spread_owner_df<W>, 32 * kOwnerCopies)
-            YK_W_DISPATCH(d.g.w, YK_CALL)
-#undef YK_CALL
         } else if (d.fft_df) {
-#define YK_CALL(W) YK_LAUNCH(k_spread_df<W>, 32 * kSpreadWarps)
+#define YK_CALL(W) YK_LAUNCH(k_spread_owner_df<W>, 32 * kOwnerCopies)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
         } else {

@@ -75,23 +75,8 @@ template <> struct Tr<df32> {
 };
 
 constexpr double kMagic = 6755399441055744.0; /* 1.5 * 2^52: fma(a, b, kMagic) rounds a*b to an integer */
-constexpr int kSpreadWarps = 8;               /* warps per CTA of the FP32C spread */
-constexpr int kSpreadBatch = 16;              /* entries a warp of the double-float spread takes
-                                                 at a time (two lanes each) */
-
-/* Layout of a warp's private spread tile (8-byte cells): cell (y, x) of the T x T tile sits at
- * y * PT + (x & ~15) + ((x + y * S) & 15) with PT = T rounded up to 16 and S = W mod 16 (a
- * rotation of each 16-cell group of a row by y S).  Tap t = c W + a of a window at (x0, y0) then
- * lands in 8-byte bank slot (x0 + y0 S + t) mod 16, so any 16 consecutive taps (a half-warp of
- * 64-bit accesses) hit 16 distinct slots: no bank conflicts, where a pitch of T + 1 put the rows a
- * warp covers on top of each other.  A 16-cell row after the tile takes the taps that fall
- * outside it, each in its own slot. */
-__host__ __device__ constexpr int spread_pitch(int T) { return (T + 15) & ~15; }
-__host__ __device__ constexpr int spread_tile_cells(int T) { return T * spread_pitch(T) + 16; }
-__device__ __forceinline__ int spread_cell(int y, int x, int PT, int S)
-{
-    return y * PT + (x & ~15) + ((x + y * S) & 15);
-}
+constexpr int kSpreadBatch = 16;              /* sources a warp of the double-float owner-tile
+                                                 spread takes at a time */
 
 __device__ __forceinline__ double block_max(double v, double *red)
 {
@@ -288,282 +273,6 @@ template <int W> __device__ void st_spread64(const Inst &d, int item, unsigned c
             mq > 0.0 ? ldexp((double)(long long)acc[i], -kexp) : 0.0;
     }
     __syncthreads(); /* shared memory is reused by the next item */
-}
-
-/* FP32C: FP32 window values and products, compensated (two-sum) accumulation.  Each warp owns a
- * private hi + lo copy of the tile; it evaluates the windows of 32 entries (one per lane), then
- * walks them one entry at a time with one lane per tap, so the taps a warp updates together are
- * distinct cells and no atomics are needed.  The copies are combined in a fixed order at the end.
- * Needs blockDim.x == 32 * kSpreadWarps. */
-template <int W> __device__ void st_spread32(const Inst &d, int item, unsigned char *sm)
-{
-    const Geom &g = d.g;
-    constexpr int S = W & 15;
-    const int T = g.T, PT = spread_pitch(T), TS = spread_tile_cells(T);
-    const int SW = d.dip ? 4 * W : 2 * W; /* window values kept per entry */
-    float2 *acc = reinterpret_cast<float2 *>(sm);                          /* [warps][TS] */
-    float *wbuf = reinterpret_cast<float *>(acc + kSpreadWarps * TS);      /* [warps][32][SW] */
-    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * 32 * SW);    /* [warps][32][2] */
-    float *cw32 = reinterpret_cast<float *>(obuf + kSpreadWarps * 64);     /* dipole windows */
-    const int tile = d.order ? d.order[item] : item;
-    const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
-    const int X0 = txi * T, Y0 = tyi * T;
-    const int4 *__restrict__ ent = reinterpret_cast<const int4 *>(d.ent_t);
-    float *__restrict__ grid = static_cast<float *>(d.grid);
-    const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
-    if (beg == end) { /* no window reaches this tile */
-        for (int i = threadIdx.x; i < T * T; i += blockDim.x)
-            grid[(size_t)(Y0 + i / T) * g.n + X0 + i % T] = 0.0f;
-        return;
-    }
-    if (d.dip)
-        for (int i = threadIdx.x; i < window_coeffs(d); i += blockDim.x) cw32[i] = d.win32[i];
-    for (int i = threadIdx.x; i < kSpreadWarps * TS; i += blockDim.x)
-        acc[i] = make_float2(0.0f, 0.0f);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2 *mine = acc + warp * TS;
-    float *wb = wbuf + warp * 32 * SW;
-    int *ob = obuf + warp * 64;
-    const float beta = (float)g.beta, cw = (float)g.c;
-    const int D = d.wdeg;
-    for (int b0 = beg + warp * 32; b0 < end; b0 += kSpreadWarps * 32) {
-        const int e = b0 + lane;
-        if (e < end) {
-            const int4 r = ent[e];
-            const int j = d.ent_j[e];
-            const float sx = __int_as_float(r.z), sy = __int_as_float(r.w);
-            float *wl = wb + lane * SW;
-            int flag = 0;
-            if (!d.dip || j < d.n_chg) {
-                const float q = (float)(d.wq[j] * d.dens[j]);
-#pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    wl[a] = q * es_window_stable<float>(sy + (float)a, beta, cw);
-                    wl[W + a] = es_window_stable<float>(sx + (float)a, beta, cw);
-                }
-            } else {
-                /* dipole: s = -mu w nu / h; window and derivative from the FP32 polynomials */
-                const double2 wn = d.wnu[j - d.n_chg];
-                const double m = -d.mu[j - d.n_chg] * g.inv_h;
-                const float gx = (float)(m * wn.x), gy = (float)(m * wn.y);
-                const float xx = 2.0f * sx + (float)(W - 1), xy = 2.0f * sy + (float)(W - 1);
-                const float *cwd = cw32 + (D + 1) * W;
-#pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    wl[a] = gx * window32<W>(cw32, D, a, xy);
-                    wl[W + a] = window32<W>(cwd, D - 1, a, xx);
-                    wl[2 * W + a] = gy * window32<W>(cwd, D - 1, a, xy);
-                    wl[3 * W + a] = window32<W>(cw32, D, a, xx);
-                }
-                flag = 1 << 30;
-            }
-            int dx0 = (r.x - X0) % g.n;
-            if (dx0 < 0) dx0 += g.n;
-            int dy0 = (r.y - Y0) % g.n;
-            if (dy0 < 0) dy0 += g.n;
-            ob[2 * lane] = dx0;
-            ob[2 * lane + 1] = dy0 | flag;
-        }
-        __syncwarp();
-        const int cnt = min(32, end - b0);
-        for (int k = 0; k < cnt; ++k) {
-            const int dx0 = ob[2 * k], dyf = ob[2 * k + 1];
-            const int dy0 = dyf & 0x3fffffff;
-            const bool dipk = dyf >> 30; /* warp-uniform: one entry at a time */
-            const float *wk = wb + k * SW;
-            /* all loads of a lane's taps before any store: the taps of one entry are distinct
-             * cells, so the shared-memory round trips overlap */
-            constexpr int NI = (W * W + 31) / 32;
-            int idx[NI];
-            float v[NI];
-            float2 cell[NI];
-#pragma unroll
-            for (int i = 0; i < NI; ++i) {
-                const int t = i * 32 + lane;
-                idx[i] = -1;
-                if (t < W * W) {
-                    const int c = t / W, a = t - c * W;
-                    int yy = dy0 + c;
-                    if (yy >= g.n) yy -= g.n;
-                    int xx = dx0 + a;
-                    if (xx >= g.n) xx -= g.n;
-                    if (yy < T && xx < T) {
-                        idx[i] = spread_cell(yy, xx, PT, S);
-                        v[i] = wk[c] * wk[W + a];
-                        if (dipk) v[i] = fmaf(wk[2 * W + c], wk[3 * W + a], v[i]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < NI; ++i)
-                if (idx[i] >= 0) cell[i] = mine[idx[i]];
-#pragma unroll
-            for (int i = 0; i < NI; ++i)
-                if (idx[i] >= 0) {
-                    const float s = __fadd_rn(cell[i].x, v[i]);
-                    const float bp = __fsub_rn(s, cell[i].x);
-                    const float err =
-                        __fadd_rn(__fsub_rn(cell[i].x, __fsub_rn(s, bp)), __fsub_rn(v[i], bp));
-                    mine[idx[i]] = make_float2(s, __fadd_rn(cell[i].y, err));
-                }
-            __syncwarp(); /* the next entry may touch the same cells through other lanes */
-        }
-        __syncwarp(); /* window buffers are rewritten by the next batch of entries */
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-        const int rr = i / T, cc = i - rr * T;
-        float hi = 0.0f, lo = 0.0f;
-        for (int w = 0; w < kSpreadWarps; ++w) {
-            const float2 p = acc[w * TS + spread_cell(rr, cc, PT, S)];
-            const float s = __fadd_rn(hi, p.x);
-            const float bp = __fsub_rn(s, hi);
-            lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)),
-                                                   __fsub_rn(p.x, bp)),
-                                         p.y));
-            hi = s;
-        }
-        grid[(size_t)(Y0 + rr) * g.n + X0 + cc] = hi + lo;
-    }
-    __syncthreads();
-}
-
-/* FP64 path, double-float arithmetic: the FP32C scheme with FP32 pairs.  Each warp owns a
- * private double-float copy of the tile.  It takes its entries kSpreadBatch at a time: two lanes
- * per entry fetch the entry's window values (computed once per source at yk_set_points) and
- * scale the y-windows by the strength, then the warp walks the batch one entry at a time with one
- * lane per tap, loading all of its taps' cells before adding and storing (the taps of one entry
- * are distinct cells), so a lane's shared-memory round trips overlap.  The copies are summed in
- * warp order and the tile is written as FP32 pairs.  Uses blockDim.x / 32 <= kSpreadWarps
- * warps. */
-template <int W> __device__ void st_spread_df(const Inst &d, int item, unsigned char *sm)
-{
-    constexpr int EB = kSpreadBatch;
-    constexpr int NI = (W * W + 31) / 32; /* taps per lane per entry */
-    const Geom &g = d.g;
-    constexpr int S = W & 15;
-    const int T = g.T, PT = spread_pitch(T), TS = spread_tile_cells(T);
-    const int NW = blockDim.x >> 5;
-    const int SW = d.dip ? 4 * W : 2 * W; /* window values kept per entry */
-    df32 *acc = reinterpret_cast<df32 *>(sm);                        /* [warps][TS] */
-    df32 *wbuf = acc + kSpreadWarps * TS;                            /* [warps][EB][SW] */
-    int *obuf = reinterpret_cast<int *>(wbuf + kSpreadWarps * EB * SW); /* [warps][EB][2] */
-    const int tile = d.order ? d.order[item] : item;
-    const int tyi = tile / g.nt, txi = tile - tyi * g.nt;
-    const int X0 = txi * T, Y0 = tyi * T;
-    df32 *__restrict__ grid = static_cast<df32 *>(d.grid);
-    const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
-    if (beg == end) { /* no window reaches this tile */
-        for (int i = threadIdx.x; i < T * T; i += blockDim.x)
-            grid[(size_t)(Y0 + i / T) * g.n + X0 + i % T] = df32(0.0f, 0.0f);
-        return;
-    }
-    for (int i = threadIdx.x; i < NW * TS; i += blockDim.x) acc[i] = df32(0.0f, 0.0f);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slot = lane & (EB - 1), half = lane / EB;
-    df32 *mine = acc + warp * TS;
-    df32 *wb = wbuf + warp * EB * SW;
-    int *ob = obuf + warp * 2 * EB;
-    /* this lane's taps (c, a) = (t / W, t % W) for t = i * 32 + lane; lanes past the last tap
-     * (tv false) take tap (0, 0) and, like taps outside the tile, add into the dummy row (never
-     * read), so the walk has no divergent branch */
-    int tc[NI], ta[NI];
-    bool tv[NI];
-#pragma unroll
-    for (int i = 0; i < NI; ++i) {
-        const int t = i * 32 + lane;
-        tv[i] = t < W * W;
-        tc[i] = tv[i] ? t / W : 0;
-        ta[i] = tv[i] ? t - (t / W) * W : 0;
-    }
-    const float2 *__restrict__ ws = d.win_src;
-    const float2 *__restrict__ wd = d.win_dip;
-    for (int b0 = beg + warp * EB; b0 < end; b0 += NW * EB) {
-        const int e = b0 + slot;
-        if (e < end) {
-            const int j = d.ent_j[e];
-            df32 *wl = wb + slot * SW;
-            if (!d.dip || j < d.n_chg) {
-                /* half 0: q phi_y; half 1: phi_x (a factor of exactly 1) */
-                const df32 f = half ? df32(1.0f, 0.0f) : df32(d.wq[j] * d.dens[j]);
-                const float2 *src = ws + (size_t)j * 2 * W + half * W;
-#pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    const float2 v = src[a];
-                    wl[half * W + a] = f * df32(v.x, v.y);
-                }
-            } else {
-                /* dipole: taps s_x phi'(X - t_x) phi(Y - t_y) + s_y phi(X - t_x) phi'(Y - t_y),
-                 * s = -mu w nu / h (the gradient of the window in the source point); half 0
-                 * stores s_x phi_y and s_y phi'_y, half 1 phi'_x and phi_x */
-                const int jd = j - d.n_chg;
-                const double2 wn = d.wnu[jd];
-                const double m = -d.mu[jd] * g.inv_h;
-                const df32 f1 = half ? df32(1.0f, 0.0f) : df32(m * wn.x);
-                const df32 f2 = half ? df32(1.0f, 0.0f) : df32(m * wn.y);
-                const float2 *src = wd + (size_t)jd * 4 * W;
-                const float2 *s1 = src + (half ? 3 * W : 0), *s2 = src + (half ? W : 2 * W);
-#pragma unroll
-                for (int a = 0; a < W; ++a) {
-                    const float2 v1 = s1[a], v2 = s2[a];
-                    wl[half * W + a] = f1 * df32(v1.x, v1.y);
-                    wl[(2 + half) * W + a] = f2 * df32(v2.x, v2.y);
-                }
-            }
-            if (half == 0) {
-                /* first tap relative to the tile, in [-(W - 1), T): the window overlaps it */
-                const double2 t = d.ent_t[e];
-                int dx0 = first_tap<W>(t.x) - X0, dy0 = first_tap<W>(t.y) - Y0;
-                if (dx0 >= T) dx0 -= g.n;
-                else if (dx0 <= -W) dx0 += g.n;
-                if (dy0 >= T) dy0 -= g.n;
-                else if (dy0 <= -W) dy0 += g.n;
-                ob[2 * slot] = dx0;
-                ob[2 * slot + 1] = (dy0 + W) | ((d.dip && j >= d.n_chg) ? 1 << 30 : 0);
-            }
-        }
-        __syncwarp();
-        const int cnt = min(EB, end - b0);
-        for (int k = 0; k < cnt; ++k) {
-            const int dx0 = ob[2 * k], dyf = ob[2 * k + 1];
-            const int dy0 = (dyf & 0x3fffffff) - W;
-            const bool dipk = dyf >> 30; /* warp-uniform: one entry at a time */
-            const df32 *wk = wb + k * SW;
-            int idx[NI];
-            df32 cur[NI];
-            const int base = dx0 + dy0 * S; /* + t is the tap's bank slot (mod 16) */
-#pragma unroll
-            for (int i = 0; i < NI; ++i) {
-                const int yy = dy0 + tc[i], xx = dx0 + ta[i];
-                const bool in = tv[i] && (unsigned)yy < (unsigned)T && (unsigned)xx < (unsigned)T;
-                const int sl = (base + i * 32 + lane) & 15;
-                idx[i] = in ? yy * PT + (xx & ~15) + sl : T * PT + sl;
-            }
-#pragma unroll
-            for (int i = 0; i < NI; ++i) cur[i] = mine[idx[i]];
-#pragma unroll
-            for (int i = 0; i < NI; ++i) {
-                cur[i] = df_mul_add_lazy(cur[i], wk[tc[i]], wk[W + ta[i]]);
-                if (dipk) cur[i] = df_mul_add_lazy(cur[i], wk[2 * W + tc[i]], wk[3 * W + ta[i]]);
-            }
-#pragma unroll
-            for (int i = 0; i < NI; ++i) mine[idx[i]] = cur[i];
-            __syncwarp(); /* the next entry may touch the same cells through other lanes */
-        }
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < T * T; i += blockDim.x) {
-        const int rr = i / T, cc = i - rr * T;
-        const int ci = spread_cell(rr, cc, PT, S);
-        df32 sum = acc[ci];
-        for (int w = 1; w < NW; ++w) sum = sum + acc[w * TS + ci];
-        /* the cells were accumulated unnormalised (df_mul_add_lazy): normalise before the FFT */
-        grid[(size_t)(Y0 + rr) * g.n + X0 + cc] = df_fast_two_sum(sum.hi, sum.lo);
-    }
-    __syncthreads();
 }
 
 /* Owner-tile spread (double-float and FP32C paths).  Every source was binned once, to the tile
@@ -802,12 +511,140 @@ __device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
     __syncthreads(); /* shared memory is reused by the next item */
 }
 
+/* FP32C owner-tile spread: FP32 window values (computed here from the source's FP32 offsets) and
+ * products, each cell a compensated pair (hi, lo) updated by two-sum; one lane per source
+ * evaluates its windows, then the warp walks the batch one source at a time with one lane per
+ * tap as above.  The copies are summed in warp order into a normalised pair per cell. */
+constexpr int kOwnerBatch32 = 32; /* sources per batch of the FP32C owner spread */
+
+template <int W, bool DIP>
+__device__ void st_spread_owner32(const Inst &d, int item, unsigned char *sm)
+{
+    constexpr int EB = kOwnerBatch32;
+    constexpr int NI = (W * W + 31) / 32;
+    constexpr int SW = (DIP ? 4 * W : 2 * W) + 1; /* odd stride: the lanes' stores hit distinct banks */
+    const Geom &g = d.g;
+    const int T = g.T, P = owner_span(T, W), PP = owner_pitch(T, W), TS = P * PP;
+    const int NC = owner_copies(blockDim.x);
+    float2 *acc = reinterpret_cast<float2 *>(sm);                        /* [NC][TS] */
+    float *wbuf = reinterpret_cast<float *>(acc + NC * TS);              /* [NC][EB][SW] */
+    int *obuf = reinterpret_cast<int *>(wbuf + NC * EB * SW);            /* [NC][EB] */
+    float *cw32 = reinterpret_cast<float *>(obuf + NC * EB);             /* dipole polynomials */
+    const int tile = d.order ? d.order[item] : item;
+    const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
+    if (beg == end) return; /* nothing to write: the fold skips empty tiles */
+    if (DIP)
+        for (int i = threadIdx.x; i < window_coeffs(d); i += blockDim.x) cw32[i] = d.win32[i];
+    for (int i = threadIdx.x; i < NC * TS; i += blockDim.x) acc[i] = make_float2(0.0f, 0.0f);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < NC) {
+        float2 *mine = acc + warp * TS;
+        float *wb = wbuf + warp * EB * SW;
+        int *ob = obuf + warp * EB;
+        int toff[NI], tc[NI], ta[NI];
+        bool tv[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int t = i * 32 + lane;
+            tv[i] = t < W * W;
+            tc[i] = tv[i] ? t / W : 0;
+            ta[i] = tv[i] ? t - (t / W) * W : 0;
+            toff[i] = tc[i] * PP + ta[i];
+        }
+        const int4 *__restrict__ ent = reinterpret_cast<const int4 *>(d.ent_t);
+        const float beta = (float)g.beta, cwin = (float)g.c;
+        const int D = d.wdeg;
+        for (int b0 = beg + warp * EB; b0 < end; b0 += NC * EB) {
+            const int e = b0 + lane;
+            if (e < end) {
+                const int4 r = ent[e];
+                const int j = r.y;
+                const float sx = __int_as_float(r.z), sy = __int_as_float(r.w);
+                float *wl = wb + lane * SW;
+                int flag = 0;
+                if (!DIP || j < d.n_chg) {
+                    const float q = (float)(d.wq[j] * d.dens[j]);
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        wl[a] = q * es_window_stable<float>(sy + (float)a, beta, cwin);
+                        wl[W + a] = es_window_stable<float>(sx + (float)a, beta, cwin);
+                    }
+                } else {
+                    /* dipole: s = -mu w nu / h; window and derivative from the FP32 polynomials */
+                    const double2 wn = d.wnu[j - d.n_chg];
+                    const double m = -d.mu[j - d.n_chg] * g.inv_h;
+                    const float gx = (float)(m * wn.x), gy = (float)(m * wn.y);
+                    const float xx = 2.0f * sx + (float)(W - 1), xy = 2.0f * sy + (float)(W - 1);
+                    const float *cwd = cw32 + (D + 1) * W;
+#pragma unroll
+                    for (int a = 0; a < W; ++a) {
+                        wl[a] = gx * window32<W>(cw32, D, a, xy);
+                        wl[W + a] = window32<W>(cwd, D - 1, a, xx);
+                        if (DIP) {
+                            wl[2 * W + a] = gy * window32<W>(cwd, D - 1, a, xy);
+                            wl[3 * W + a] = window32<W>(cw32, D, a, xx);
+                        }
+                    }
+                    flag = 1 << 30;
+                }
+                ob[lane] = r.x | flag;
+            }
+            __syncwarp();
+            const int cnt = min(EB, end - b0);
+            for (int k = 0; k < cnt; ++k) {
+                const int v = ob[k];
+                const int base = v & 0x3fffffff;
+                const bool dipk = DIP && (v >> 30); /* warp-uniform: one source at a time */
+                const float *wk = wb + k * SW;
+                float2 cell[NI];
+#pragma unroll
+                for (int i = 0; i < NI; ++i)
+                    if (tv[i]) cell[i] = mine[base + toff[i]];
+#pragma unroll
+                for (int i = 0; i < NI; ++i) {
+                    float val = wk[tc[i]] * wk[W + ta[i]];
+                    if (dipk) val = fmaf(wk[2 * W + tc[i]], wk[3 * W + ta[i]], val);
+                    const float s2 = __fadd_rn(cell[i].x, val);
+                    const float bp = __fsub_rn(s2, cell[i].x);
+                    const float err =
+                        __fadd_rn(__fsub_rn(cell[i].x, __fsub_rn(s2, bp)), __fsub_rn(val, bp));
+                    cell[i] = make_float2(s2, __fadd_rn(cell[i].y, err));
+                }
+#pragma unroll
+                for (int i = 0; i < NI; ++i)
+                    if (tv[i]) mine[base + toff[i]] = cell[i];
+                __syncwarp(); /* the next source may touch the same cells through other lanes */
+            }
+            __syncwarp(); /* the window buffers are refilled by the next batch */
+        }
+    }
+    __syncthreads();
+    /* padded tile = the copies' pairs summed in warp order (two-sum of the high words, low words
+     * added), written as a normalised pair */
+    float2 *__restrict__ out = static_cast<float2 *>(d.part) + (size_t)tile * P * P;
+    for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+        const int r = i / P, c = i - r * P;
+        const int ci = r * PP + c;
+        float hi = acc[ci].x, lo = acc[ci].y;
+        for (int w = 1; w < NC; ++w) {
+            const float2 q = acc[w * TS + ci];
+            const df32 t = df_two_sum(hi, q.x);
+            hi = t.hi;
+            lo = __fadd_rn(lo, __fadd_rn(t.lo, q.y));
+        }
+        const df32 n2 = df_two_sum(hi, lo);
+        out[i] = make_float2(n2.hi, n2.lo);
+    }
+    __syncthreads(); /* shared memory is reused by the next item */
+}
+
 /* one grid cell (x, y) of the owner-tile spread's output: the padded partials of the tiles whose
  * padded region covers it, added in a fixed order (far neighbours first); empty tiles were not
  * written and are skipped.  ty, ly = y / T, y % T of the cell's row. */
-template <typename P2>
+template <typename P2, typename ADD>
 __device__ __forceinline__ void fold_terms(const Inst &d, int ty, int ly, int x, float invT,
-                                           const P2 *__restrict__ part, P2 *v, int &nv)
+                                           const P2 *__restrict__ part, ADD add)
 {
     const Geom &g = d.g;
     const int T = g.T, nt = g.nt, P = owner_span(T, g.w), PPc = P * P;
@@ -815,30 +652,27 @@ __device__ __forceinline__ void fold_terms(const Inst &d, int ty, int ly, int x,
     const int *__restrict__ tp = d.tile_ptr;
     const int tyb = ty == 0 ? nt - 1 : ty - 1, txb = tx == 0 ? nt - 1 : tx - 1;
     const bool hy = ly < g.w - 1, hx = lx < g.w - 1; /* also in the padded region below / left */
-    nv = 0;
     if (hy && hx) {
         const int t = tyb * nt + txb;
-        if (tp[t + 1] > tp[t]) v[nv++] = part[(size_t)t * PPc + (ly + T) * P + lx + T];
+        if (tp[t + 1] > tp[t]) add(part[(size_t)t * PPc + (ly + T) * P + lx + T]);
     }
     if (hy) {
         const int t = tyb * nt + tx;
-        if (tp[t + 1] > tp[t]) v[nv++] = part[(size_t)t * PPc + (ly + T) * P + lx];
+        if (tp[t + 1] > tp[t]) add(part[(size_t)t * PPc + (ly + T) * P + lx]);
     }
     if (hx) {
         const int t = ty * nt + txb;
-        if (tp[t + 1] > tp[t]) v[nv++] = part[(size_t)t * PPc + ly * P + lx + T];
+        if (tp[t + 1] > tp[t]) add(part[(size_t)t * PPc + ly * P + lx + T]);
     }
     const int t = ty * nt + tx;
-    if (tp[t + 1] > tp[t]) v[nv++] = part[(size_t)t * PPc + ly * P + lx];
+    if (tp[t + 1] > tp[t]) add(part[(size_t)t * PPc + ly * P + lx]);
 }
 
 __device__ __forceinline__ df32 fold_cell_df(const Inst &d, int ty, int ly, int x, float invT)
 {
-    df32 v[4];
-    int nv;
-    fold_terms<df32>(d, ty, ly, x, invT, static_cast<const df32 *>(d.part), v, nv);
     df32 s(0.0f, 0.0f);
-    for (int k = 0; k < nv; ++k) s = k ? s + v[k] : v[k];
+    fold_terms<df32>(d, ty, ly, x, invT, static_cast<const df32 *>(d.part),
+                     [&](df32 v) { s = s + v; });
     return s;
 }
 
@@ -933,7 +767,30 @@ __device__ __forceinline__ void load_folded_rows<df32>(const Inst &d, cpx<df32> 
     }
 }
 
-template <> __device__ __forceinline__ void load_folded_rows<float>(const Inst &, cpx<float> *, int, int) {}
+/* FP32C: the partials are compensated pairs; a cell's (up to four) pairs are summed by two-sum
+ * of the high words with the low words added, then rounded to one FP32 value */
+__device__ __forceinline__ float fold_cell32(const Inst &d, int ty, int ly, int x, float invT)
+{
+    float hi = 0.0f, lo = 0.0f;
+    fold_terms<float2>(d, ty, ly, x, invT, static_cast<const float2 *>(d.part), [&](float2 v) {
+        const df32 t = df_two_sum(hi, v.x);
+        hi = t.hi;
+        lo = __fadd_rn(lo, __fadd_rn(t.lo, v.y));
+    });
+    return __fadd_rn(hi, lo);
+}
+
+template <>
+__device__ __forceinline__ void load_folded_rows<float>(const Inst &d, cpx<float> *x, int y0, int nr)
+{
+    const int L = d.n >> 1, T = d.g.T;
+    const float invT = 1.0f / (float)T;
+    for (int i = threadIdx.x; i < nr * L; i += blockDim.x) {
+        const int r = i / L, l = i - r * L, y = y0 + r;
+        const int ty = y / T, ly = y - ty * T;
+        x[i] = mk<float>(fold_cell32(d, ty, ly, 2 * l, invT), fold_cell32(d, ty, ly, 2 * l + 1, invT));
+    }
+}
 template <> __device__ __forceinline__ void load_folded_rows<double>(const Inst &, cpx<double> *, int, int) {}
 
 /* rows [item*rows, ...): real-to-complex FFT, keep m_x <= M, store transposed spec[m_x*n + y] */
@@ -1207,10 +1064,6 @@ __device__ __forceinline__ void run_stage<double>(const Inst &d, int stage, int 
     else st_spread_owner_df<W, false>(d, item, sm)
             YK_W_SWITCH(d.g.w, YK_C)
 #undef YK_C
-        } else if (d.fft_df) {
-#define YK_C(W) st_spread_df<W>(d, item, sm)
-            YK_W_SWITCH(d.g.w, YK_C)
-#undef YK_C
         } else {
 #define YK_C(W) st_spread64<W>(d, item, sm)
             YK_W_SWITCH(d.g.w, YK_C)
@@ -1249,7 +1102,9 @@ __device__ __forceinline__ void run_stage<float>(const Inst &d, int stage, int i
 {
     switch (stage) {
     case ST_SPREAD: {
-#define YK_C(W) st_spread32<W>(d, item, sm)
+#define YK_C(W)                                                                                  \
+    if (d.dip) st_spread_owner32<W, true>(d, item, sm);                                          \
+    else st_spread_owner32<W, false>(d, item, sm)
         YK_W_SWITCH(d.g.w, YK_C)
 #undef YK_C
     } break;
@@ -1271,7 +1126,10 @@ __device__ __forceinline__ void run_stage_w(const Inst &d, int stage, int item, 
 {
     if constexpr (std::is_same<R, float>::value) {
         switch (stage) {
-        case ST_SPREAD: st_spread32<W>(d, item, sm); break;
+        case ST_SPREAD:
+            if (d.dip) st_spread_owner32<W, true>(d, item, sm);
+            else st_spread_owner32<W, false>(d, item, sm);
+            break;
         case ST_ROW_FWD: st_row_fwd<float>(d, item, sm); break;
         case ST_COLUMNS: st_columns<float>(d, item, sm); break;
         case ST_ROW_INV: st_row_inv<float>(d, item, sm); break;
@@ -1282,7 +1140,6 @@ __device__ __forceinline__ void run_stage_w(const Inst &d, int stage, int item, 
         case ST_SPREAD:
             if (d.fft_df && d.part && d.dip) st_spread_owner_df<W, true>(d, item, sm);
             else if (d.fft_df && d.part) st_spread_owner_df<W, false>(d, item, sm);
-            else if (d.fft_df) st_spread_df<W>(d, item, sm);
             else st_spread64<W>(d, item, sm);
             break;
         case ST_ROW_FWD:
