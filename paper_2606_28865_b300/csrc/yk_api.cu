@@ -874,6 +874,10 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
         !std::isfinite(o->box[1]) || !std::isfinite(o->box[2]) || !std::isfinite(o->box[3]))
         return fail(YK_ERR_ARG, "box must satisfy xmin < xmax and ymin < ymax");
     if (o->tile < 0) return fail(YK_ERR_ARG, "tile must be >= 0");
+    /* the owner-tile spreads (FP32C, double-float FP64) keep per-warp padded copies of a tile in
+     * shared memory and pack in-tile positions in 6 bits: their tile edge is at most 32 */
+    if (o->tile > 32 && (o->precision == YK_FP32C || !o->fft_fp64))
+        return fail(YK_ERR_ARG, "tile must be <= 32 (64 with fft_fp64)");
     if (o->kmax_rule != 0 && o->kmax_rule != 1) return fail(YK_ERR_ARG, "kmax_rule must be 0 or 1");
     if ((o->alloc == nullptr) != (o->free == nullptr))
         return fail(YK_ERR_ARG, "give both alloc and free callbacks, or neither");
@@ -966,7 +970,6 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
         if (o->tile > 0) {
             if (n % o->tile == 0 && o->tile >= w && n >= 2 * o->tile) T = o->tile;
         } else {
-            /* the owner-tile spreads (FP32C, double-float FP64) keep per-warp padded copies: T <= 32 */
             const int tmax = (o->precision == YK_FP32C || !o->fft_fp64) ? 32 : 64;
             const int pref = o->use_tuned ? yk_tuned_tile(o->precision, w, n, o->n_src_hint) : 0;
             for (int t = tmax; t >= w; --t)
@@ -1161,7 +1164,7 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
         YK_CU(yk::launch_bin_sources(g, n_src, dx, dy, n_dip, ddx, ddy, P<double2>(p->src_t),
                                      P<int>(p->tile_cnt), P<int>(p->tile_ptr),
                                      P<int>(p->tile_cur), P<double2>(p->ent_t), P<int>(p->ent_j),
-                                     P<int>(p->err), p->stream, false, false),
+                                     P<int>(p->err), p->stream),
               "bin sources");
     /* the cursors are free after the fill: they serve as the ordering's scratch */
     YK_CU(yk::launch_tile_order(P<int>(p->tile_ptr), p->nt * p->nt, P<int>(p->tile_order),
@@ -1206,7 +1209,7 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
         YK_CU(yk::launch_bin_targets(g, n_trg, tx, ty, P<double2>(p->trg_tmp),
                                      P<int>(p->trg_cnt), P<int>(p->trg_ptr), P<int>(p->trg_cur),
                                      P<double2>(p->trg_t), P<int>(p->trg_idx), P<int>(p->err),
-                                     p->stream, false),
+                                     p->stream),
               "bin targets");
     if (p->fft_df) {
         YK_TRY(buf_alloc(p, p->win_trg, sizeof(float2) * 2 * (size_t)p->w * nt, "target windows"));

@@ -113,17 +113,15 @@ int stage_smem(const Inst &d, int stage);
 int stage_items(const Inst &d, int stage);
 int rows_per_item(int n, bool f32);
 
-/* kernel launchers (yk_kernels.cu); all enqueue on `st` and return the launch status.
- * f32 selects the FP32C entry layout (first tap + FP32 offset) for the binned points. */
-/* sources: ns charges (xs, ys) then nd dipoles (xd, yd); src_t holds ns + nd grid coordinates and
- * a dipole's entries carry source index ns + d */
-/* owner == false: one entry per tile a source's window touches (<= 4); owner == true: one entry
- * per source, in the tile of its first tap (the owner-tile spread) */
+/* kernel launchers (yk_kernels.cu); all enqueue on `st` and return the launch status. */
+/* The all-FP64 path's binning (FP64 grid coordinates): sources ns charges (xs, ys) then nd dipoles
+ * (xd, yd), one entry per tile a source's window touches (<= 4), entries holding the grid
+ * coordinate (double2) and the source index (a dipole's carries ns + d); src_t holds the ns + nd
+ * grid coordinates */
 cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
                                int64_t nd, const double *xd, const double *yd, double2 *src_t,
                                int *tile_cnt, int *tile_ptr, int *tile_cur, double2 *ent_t,
-                               int *ent_j, int *err, cudaStream_t st, bool f32,
-                               bool owner = false);
+                               int *ent_j, int *err, cudaStream_t st);
 /* Point preparation of the double-float and FP32C paths (no FP64 arithmetic past the
  * fixed-point coordinate): per point its first taps tap = (l0x, l0y) (INT_MIN: outside the box)
  * and the window arguments u = l0 - t + w/2 in [0, 1) of both axes as exact FP32 pairs,
@@ -158,7 +156,7 @@ cudaError_t launch_pack_wnu(int64_t nd, const double *wd, const double *nx, cons
                             double2 *wnu, cudaStream_t st);
 cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, const double *yt,
                                double2 *trg_tmp, int *cnt, int *ptr, int *cur, double2 *trg_t,
-                               int *trg_idx, int *err, cudaStream_t st, bool f32);
+                               int *trg_idx, int *err, cudaStream_t st);
 /* heavy-first tile order (order[i] = tile the i-th spread CTA takes); order may be NULL in the
  * spread launchers, meaning tile i for CTA i */
 cudaError_t launch_tile_order(const int *tile_ptr, int ntiles, int *order, int *scratch,

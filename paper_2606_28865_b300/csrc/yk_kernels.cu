@@ -37,32 +37,8 @@ __device__ __forceinline__ bool in_box(const Geom &g, double x, double y)
     return x >= g.box[0] && x <= g.box[1] && y >= g.box[2] && y <= g.box[3];
 }
 
-/* entry layouts: FP64 keeps the grid coordinate t (double2); FP32C keeps the first tap l0 and
- * the offset s = l0 - t in FP32, both computed from t in FP64 at set-up, so the FP32 kernels
- * never see absolute coordinates (k h |x| eps_32 would otherwise dominate the error) */
+/* legacy entry layout of the all-FP64 path: the grid coordinate t (double2) */
 template <int W> __device__ __forceinline__ double2 pack_f64(double2 t) { return t; }
-/* owner-tile entry: (offset of the first tap in the tile's padded copy, source index, FP32
- * offsets s = l0 - t of both axes as for FP32C), so the spread does no FP64 rounding */
-template <int W> __device__ __forceinline__ double2 pack_owner(double2 t, const Geom &g, int j)
-{
-    const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
-    const int wx = wrap(lx, g.n), wy = wrap(ly, g.n);
-    const int off = (wy % g.T) * owner_pitch(g.T, W) + wx % g.T;
-    const float sx = (float)((double)lx - t.x), sy = (float)((double)ly - t.y);
-    double2 r;
-    *reinterpret_cast<int4 *>(&r) = make_int4(off, j, __float_as_int(sx), __float_as_int(sy));
-    return r;
-}
-template <int W> __device__ __forceinline__ double2 pack_f32c(double2 t)
-{
-    const int lx = first_tap<W>(t.x), ly = first_tap<W>(t.y);
-    const float sx = (float)((double)lx - t.x), sy = (float)((double)ly - t.y);
-    double2 r;
-    int4 *q = reinterpret_cast<int4 *>(&r);
-    *q = make_int4(lx, ly, __float_as_int(sx), __float_as_int(sy));
-    return r;
-}
-
 /* ----------------------------------------------------------------------------------------- */
 /* binning                                                                                    */
 
@@ -100,15 +76,6 @@ template <int W> __device__ __forceinline__ void src_tiles(double2 t, const Geom
     tiles[3] = (ay1 != ay0 && ax1 != ax0) ? ay1 * g.nt + ax1 : -1;
 }
 
-/* the owner tile of a source: the tile of its first tap (wrapped), whose padded (T + w - 1)^2
- * region holds the whole w x w window; the other slots are -1 */
-template <int W> __device__ __forceinline__ void owner_tile(double2 t, const Geom &g, int tiles[4])
-{
-    const int lx = wrap(first_tap<W>(t.x), g.n), ly = wrap(first_tap<W>(t.y), g.n);
-    tiles[0] = (ly / g.T) * g.nt + lx / g.T;
-    tiles[1] = tiles[2] = tiles[3] = -1;
-}
-
 /* grid coordinates of a point and whether it lies in the plan's box (and so in the grid) */
 __device__ __forceinline__ bool grid_coords(const Geom &g, double x, double y, double2 &t)
 {
@@ -118,7 +85,7 @@ __device__ __forceinline__ bool grid_coords(const Geom &g, double x, double y, d
 
 /* the block size of the binning kernels is a multiple of 32 and every lane reaches the warp
  * collectives (no early return) */
-template <int W, bool OWNER>
+template <int W>
 __global__ void k_bin_src_count(int64_t ns, const double *__restrict__ xs,
                                 const double *__restrict__ ys, Geom g, double2 *__restrict__ src_t,
                                 int *__restrict__ cnt, int *__restrict__ err)
@@ -132,18 +99,16 @@ __global__ void k_bin_src_count(int64_t ns, const double *__restrict__ xs,
         if (!ok) {
             atomicOr(err, ERR_POINT_OUTSIDE);
             t = make_double2(-1.0, -1.0);
-        } else if (OWNER) {
-            owner_tile<W>(t, g, tiles);
         } else {
             src_tiles<W>(t, g, tiles);
         }
         src_t[j] = t;
     }
 #pragma unroll
-    for (int r = 0; r < (OWNER ? 1 : 4); ++r) agg_count(cnt, tiles[r], tiles[r] >= 0);
+    for (int r = 0; r < 4; ++r) agg_count(cnt, tiles[r], tiles[r] >= 0);
 }
 
-template <int W, bool F32, bool OWNER>
+template <int W>
 __global__ void k_bin_src_fill(int64_t ns, const double2 *__restrict__ src_t, Geom g,
                                const int *__restrict__ ptr, int *__restrict__ cur,
                                double2 *__restrict__ ent_t, int *__restrict__ ent_j, int joff)
@@ -152,14 +117,10 @@ __global__ void k_bin_src_fill(int64_t ns, const double2 *__restrict__ src_t, Ge
     int tiles[4] = {-1, -1, -1, -1};
     double2 t = make_double2(-1.0, -1.0);
     if (j < ns) t = src_t[j];
-    if (t.x >= 0.0) {
-        if (OWNER) owner_tile<W>(t, g, tiles);
-        else src_tiles<W>(t, g, tiles);
-    }
-    const double2 rec = OWNER ? pack_owner<W>(t, g, (int)j + joff)
-                              : (F32 ? pack_f32c<W>(t) : pack_f64<W>(t));
+    if (t.x >= 0.0) src_tiles<W>(t, g, tiles);
+    const double2 rec = pack_f64<W>(t);
 #pragma unroll
-    for (int r = 0; r < (OWNER ? 1 : 4); ++r) {
+    for (int r = 0; r < 4; ++r) {
         const bool v = tiles[r] >= 0;
         const int off = agg_reserve(cur, tiles[r], v);
         if (v) {
@@ -189,7 +150,7 @@ __global__ void k_bin_trg_count(int64_t nt, const double *__restrict__ xt,
     agg_count(cnt, tile, tile >= 0);
 }
 
-template <int W, bool F32>
+template <int W>
 __global__ void k_bin_trg_fill(int64_t nt, const double2 *__restrict__ tmp, Geom g,
                                const int *__restrict__ ptr, int *__restrict__ cur,
                                double2 *__restrict__ trg_t, int *__restrict__ trg_idx)
@@ -202,7 +163,7 @@ __global__ void k_bin_trg_fill(int64_t nt, const double2 *__restrict__ tmp, Geom
     const int off = agg_reserve(cur, tile, v);
     if (v) {
         const int slot = ptr[tile] + off;
-        trg_t[slot] = F32 ? pack_f32c<W>(t) : pack_f64<W>(t);
+        trg_t[slot] = pack_f64<W>(t);
         trg_idx[slot] = (int)i;
     }
 }
@@ -913,7 +874,7 @@ cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStrea
 cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, const double *ys,
                                int64_t nd, const double *xd, const double *yd, double2 *src_t,
                                int *tile_cnt, int *tile_ptr, int *tile_cur, double2 *ent_t,
-                               int *ent_j, int *err, cudaStream_t st, bool f32, bool owner)
+                               int *ent_j, int *err, cudaStream_t st)
 {
     const int ntiles = g.nt * g.nt;
     cudaError_t e = cudaMemsetAsync(tile_cnt, 0, sizeof(int) * ntiles, st);
@@ -928,12 +889,7 @@ cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, cons
         if (cnt[k] <= 0) continue;
         const int blocks = (int)((cnt[k] + 255) / 256);
 #define YK_CALL(W)                                                                              \
-    if (owner)                                                                                  \
-        k_bin_src_count<W, true><<<blocks, 256, 0, st>>>(cnt[k], px[k], py[k], g, pt[k],        \
-                                                         tile_cnt, err);                        \
-    else                                                                                        \
-        k_bin_src_count<W, false><<<blocks, 256, 0, st>>>(cnt[k], px[k], py[k], g, pt[k],       \
-                                                          tile_cnt, err)
+    k_bin_src_count<W><<<blocks, 256, 0, st>>>(cnt[k], px[k], py[k], g, pt[k], tile_cnt, err)
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     }
@@ -942,20 +898,11 @@ cudaError_t launch_bin_sources(const Geom &g, int64_t ns, const double *xs, cons
         if (cnt[k] <= 0) continue;
         const int blocks = (int)((cnt[k] + 255) / 256);
         const int joff = k ? (int)ns : 0;
-#define YK_FILL(W, F, O)                                                                        \
-    k_bin_src_fill<W, F, O><<<blocks, 256, 0, st>>>(cnt[k], pt[k], g, tile_ptr, tile_cur, ent_t, \
-                                                    ent_j, joff)
 #define YK_CALL(W)                                                                              \
-    if (f32) {                                                                                  \
-        if (owner) YK_FILL(W, true, true);                                                      \
-        else YK_FILL(W, true, false);                                                           \
-    } else {                                                                                    \
-        if (owner) YK_FILL(W, false, true);                                                     \
-        else YK_FILL(W, false, false);                                                          \
-    }
+    k_bin_src_fill<W><<<blocks, 256, 0, st>>>(cnt[k], pt[k], g, tile_ptr, tile_cur, ent_t, ent_j, \
+                                              joff)
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
-#undef YK_FILL
     }
     return cudaGetLastError();
 }
@@ -1074,7 +1021,7 @@ cudaError_t launch_pack_wnu(int64_t nd, const double *wd, const double *nx, cons
 
 cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, const double *yt,
                                double2 *trg_tmp, int *cnt, int *ptr, int *cur, double2 *trg_t,
-                               int *trg_idx, int *err, cudaStream_t st, bool f32)
+                               int *trg_idx, int *err, cudaStream_t st)
 {
     const int ntiles = g.nt * g.nt;
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ntiles, st);
@@ -1086,10 +1033,7 @@ cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, cons
     if ((e = launch_scan(cnt, ptr, ntiles, cur, st)) != cudaSuccess) return e;
     if (nt > 0) {
 #define YK_CALL(W)                                                                              \
-    if (f32)                                                                                    \
-        k_bin_trg_fill<W, true><<<blocks, 256, 0, st>>>(nt, trg_tmp, g, ptr, cur, trg_t, trg_idx); \
-    else                                                                                        \
-        k_bin_trg_fill<W, false><<<blocks, 256, 0, st>>>(nt, trg_tmp, g, ptr, cur, trg_t, trg_idx)
+    k_bin_trg_fill<W><<<blocks, 256, 0, st>>>(nt, trg_tmp, g, ptr, cur, trg_t, trg_idx)
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     }

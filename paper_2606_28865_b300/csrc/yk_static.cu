@@ -348,11 +348,11 @@ extern "C" YK_API yk_status yk_eval_longrange_static(double alpha, const yk_opts
         e = yk::launch_bin_sources(g, n_src, xs, ys, 0, nullptr, nullptr, (double2 *)at(o_srct),
                                    (int *)at(o_tcnt),
                                    (int *)at(o_tptr), (int *)at(o_tcur), (double2 *)at(o_entt),
-                                   (int *)at(o_entj), (int *)at(o_err), st, false);
+                                   (int *)at(o_entj), (int *)at(o_err), st);
     if (e == cudaSuccess)
         e = yk::launch_bin_targets(g, n_trg, xt, yt, (double2 *)at(o_tmp), (int *)at(o_gcnt),
                                    (int *)at(o_gptr), (int *)at(o_gcur), (double2 *)at(o_trgt),
-                                   (int *)at(o_trgi), (int *)at(o_err), st, false);
+                                   (int *)at(o_trgi), (int *)at(o_err), st);
     if (e == cudaSuccess)
         e = yk::launch_spread(g, (const int *)at(o_tptr), nullptr, (const double2 *)at(o_entt),
                               (const int *)at(o_entj), w, density, (double *)at(o_grid), st);
