@@ -63,8 +63,8 @@ def parse():
     ap.add_argument("--no-local", action="store_true", help="skip the local-part measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch section")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving section")
-    ap.add_argument("--serve-requests", type=int, default=4000,
-                    help="requests of the Rothe stream (Poisson, 2000 req/s)")
+    ap.add_argument("--serve-requests", type=int, default=20000,
+                    help="requests of the Rothe stream per arrival rate")
     return ap.parse_args()
 
 
@@ -456,22 +456,40 @@ def batch_section(yk, torch, rank):
     return out
 
 
+SERVE_RATES = (2000.0, 8000.0, 32000.0, 128000.0)
+
+
 def serving_section(yk, n_req):
-    """Rothe stream: 64 simulations (points log-uniform in [1e3, 1e6], dt log-uniform in
-    [1e-4, 1e-1]), Poisson arrivals at 2000 req/s: FP32C continuous batching vs the plain FP64
-    per-call form on the same arrivals."""
+    """Rothe stream (config 5): 64 simulations (points log-uniform in [1e3, 1e6], dt log-uniform
+    in [1e-4, 1e-1]), n_req Poisson arrivals, swept over arrival rates up to saturation: the FP32C
+    continuous-batching server against the plain FP64 per-call form (one stream, each call waited
+    for) on the same requests and the same GPU.  The same geometries and requests at every rate
+    (only the arrival times scale)."""
     from paper_2606_28865_b300.serving import RotheServer
-    geoms, reqs = W.rothe_stream(n_req=n_req, rate=2000.0, n_geom=64, seed=0)
-    out = {"workload": f"{n_req} requests, Poisson 2000 req/s, 64 resident geometries",
-           "points_total": int(sum(geoms[r["geom"]].n_src + geoms[r["geom"]].n_trg
-                                   for r in reqs))}
-    for key, prec, batch in (("fp32c_batched", yk.YK_FP32C, True),
-                             ("fp64_per_call", yk.YK_FP64, False)):
-        srv = RotheServer(geoms, precision=prec, max_inflight=64, n_streams=4, batch=batch)
+    geoms, _ = W.rothe_stream(n_req=1, rate=SERVE_RATES[0], n_geom=64, seed=0)
+    out = {"workload": f"{n_req} requests per rate, Poisson arrivals, 64 resident geometries "
+                       f"(points log-uniform in [1e3, 1e6])",
+           "rates_req_per_s": list(SERVE_RATES)}
+    forms = (("fp32c_batched", yk.YK_FP32C, dict(max_inflight=64, n_streams=4), "serve"),
+             ("fp64_plain", yk.YK_FP64, dict(n_streams=1), "serve_plain"))
+    for key, prec, kw, how in forms:
+        srv = RotheServer(geoms, precision=prec, **kw)
         srv.warm(range(len(geoms)))
-        st = srv.serve(reqs)
-        st.pop("results", None)
-        out[key] = st
+        per_rate = []
+        for rate in SERVE_RATES:
+            _, reqs = W.rothe_stream(n_req=n_req, rate=rate, n_geom=64, seed=0)
+            st = getattr(srv, how)(reqs)
+            st.pop("results", None)
+            st["rate_req_per_s"] = rate
+            st["offered_points_per_s"] = (sum(geoms[r["geom"]].n_src + geoms[r["geom"]].n_trg
+                                              for r in reqs) / reqs[-1]["t_arrive"])
+            per_rate.append(st)
+        out[key] = per_rate
+        out[key + "_saturated"] = {"points_per_s": per_rate[-1]["points_per_s"],
+                                   "p50_ms": per_rate[-1]["latency_ms"]["p50"],
+                                   "p99_ms": per_rate[-1]["latency_ms"]["p99"],
+                                   "mean_batch": per_rate[-1]["mean_batch"],
+                                   "rate_req_per_s": SERVE_RATES[-1]}
         srv.close()
     return out
 

@@ -220,6 +220,51 @@ class RotheServer:
             "results": kept,
         }
 
+    def serve_plain(self, requests, keep_results=()):
+        """The plain per-call form, for comparison: no admission loop and no batching;
+        requests are taken in arrival order, each evaluated as soon as it has arrived and the
+        previous call has returned, and each call waits for its result (a caller that calls the
+        evaluator and uses the potential).  Meant for a server built with n_streams=1, so every
+        call runs on one stream.  Same statistics as serve()."""
+        order = sorted(range(len(requests)), key=lambda i: requests[i]["t_arrive"])
+        lat = np.full(len(requests), np.nan)
+        kept, keep = {}, set(keep_results)
+        done_points = 0
+        for g in {requests[r]["geom"] for r in order}:
+            self._ensure_plan(g)
+        t0 = time.perf_counter()
+        t_last = None
+        for r in order:
+            while time.perf_counter() - t0 < requests[r]["t_arrive"]:
+                pass
+            g = requests[r]["geom"]
+            geo = self.geoms[g]
+            p = self.plans[g]
+            p.eval(geo.dens[requests[r]["seed"] % len(geo.dens)], out=geo.out)
+            p.stream_obj.synchronize()
+            tc = time.perf_counter() - t0
+            lat[r] = tc - requests[r]["t_arrive"]
+            done_points += geo.points
+            if r in keep:
+                kept[r] = geo.out.cpu().numpy()
+            t_last = tc
+        wall = (t_last or 0.0) - float(requests[order[0]]["t_arrive"] if requests else 0.0)
+        return {
+            "requests": int(np.sum(~np.isnan(lat))),
+            "points": int(done_points),
+            "points_per_s": done_points / wall if wall > 0 else None,
+            "wall_s": wall,
+            "latency_ms": {"p50": float(np.nanpercentile(lat, 50) * 1e3),
+                           "p99": float(np.nanpercentile(lat, 99) * 1e3),
+                           "max": float(np.nanmax(lat) * 1e3)},
+            "batches": len(order),
+            "mean_batch": 1.0,
+            "plans_created": self.n_created,
+            "plans_evicted": self.n_evicted,
+            "resident_bytes": int(self.resident),
+            "results": kept,
+        }
+
     def eval_alone(self, req):
         """The same request evaluated alone on an idle GPU (for the mix-invariance check)."""
         g = req["geom"]

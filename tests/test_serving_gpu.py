@@ -51,3 +51,29 @@ def test_memory_budget_evicts_idle_plans(stream_small):
         alone = srv.eval_alone(reqs[r])
         assert np.max(np.abs(st["results"][r] - alone)) <= 1e-6 * np.max(np.abs(alone))
     srv.close()
+
+
+def test_saturated_stream_batches_and_matches_alone():
+    """Requests arriving faster than the GPU serves them (all 400 within ~1 ms): the server must
+    batch (mean batch > 1) and each result must still equal the request evaluated alone; the plain
+    per-call form on one stream gives the same potentials."""
+    from paper_2606_28865_b300.serving import RotheServer
+    import paper_2606_28865_b300 as yk
+    geoms, reqs = W.rothe_stream(n_req=400, rate=4e5, n_geom=8, seed=5, n_lo=1e3, n_hi=4e4)
+    sample = list(range(0, len(reqs), 41))
+    srv = RotheServer(geoms, precision=yk.YK_FP32C, max_inflight=32, n_streams=3)
+    srv.warm(range(len(geoms)))
+    st = srv.serve(reqs, keep_results=sample)
+    assert st["requests"] == len(reqs)
+    assert st["mean_batch"] > 1.0
+    for r in sample:
+        alone = srv.eval_alone(reqs[r])
+        assert np.max(np.abs(st["results"][r] - alone)) <= srv.tol * np.max(np.abs(alone)), r
+    srv.close()
+    plain = RotheServer(geoms, precision=yk.YK_FP64, n_streams=1)
+    sp = plain.serve_plain(reqs, keep_results=sample)
+    assert sp["requests"] == len(reqs) and sp["mean_batch"] == 1.0
+    for r in sample:
+        alone = plain.eval_alone(reqs[r])
+        assert np.max(np.abs(sp["results"][r] - alone)) <= 1e-10 * np.max(np.abs(alone)), r
+    plain.close()
