@@ -104,6 +104,13 @@ typedef struct {
                            multiplier is that kernel's radial transform (computed on the device
                            at plan time).  0: automatic (when it gives the shorter period and
                            opts.period is 0), 1: never, 2: always */
+    /* launch shape of the FP32C and double-float spreads and interpolations (0: the default, or
+     * the autotuner's choice with use_tuned); other values are YK_ERR_ARG */
+    int spread_warps;   /* warps per spread CTA, each with its own copy of the tile: 1..4
+                           (default 4) */
+    int spread_batch;   /* sources a spread warp takes at a time: 4, 8 or 16 on the double-float
+                           path (default 16), 8, 16 or 32 on FP32C (default 32) */
+    int interp_threads; /* threads per interpolation CTA: 64, 128 or 256 (default 256) */
 } yk_opts;
 
 /* Parameters the plan chose (all derived from alpha, tol, delta and the box). */
@@ -122,6 +129,7 @@ typedef struct {
     int64_t device_bytes;          /* device memory held by the plan now */
     int truncated;                 /* 1: the truncated kernel is used (opts.truncate) */
     double r_support;              /* truncated kernel: radius beyond which it is zero */
+    int spread_warps, spread_batch, interp_threads; /* launch shape (see yk_opts) */
 } yk_info;
 
 /* Fill *o with defaults: FP64, tol 1e-10, delta rule with eps_hist 1e-6, box [-1.5,1.5]^2. */
@@ -314,18 +322,22 @@ YK_API yk_status yk_destroy(yk_plan_t p);
 YK_API const char *yk_last_error(void);
 
 /*
- * Autotuner.  yk_autotune times every admissible tile edge for (alpha, o) on the caller's points
- * (all arrays device memory; density n_src values) and records the fastest in a process-wide
- * cache used by plans created with o->use_tuned.  The paper has no counterpart.
+ * Autotuner.  yk_autotune times, on the caller's points (all arrays device memory; density n_src
+ * values), every admissible tile edge with the default launch shape, then at the fastest edge the
+ * spread's warps per CTA and sources per batch and the interpolation's threads per CTA (each stage
+ * timed alone), and records the fastest of each in a process-wide cache used by plans created
+ * with o->use_tuned (batch plans included).  The paper has no counterpart.
  */
 #define YK_TUNE_MAX 16
 typedef struct {
-    int n_tried;              /* candidates timed */
+    int n_tried;              /* tile candidates timed */
     int tile[YK_TUNE_MAX];    /* candidate tile edges */
     double ms[YK_TUNE_MAX];   /* device ms of one evaluation (sum of its stages) per candidate */
     int best_tile;
-    double best_ms;
+    double best_ms;           /* one evaluation at the best tile and launch shape */
     int64_t n_grid;
+    int best_spread_warps, best_spread_batch, best_interp_threads;
+    double spread_ms, interp_ms; /* the spread and interpolation at the chosen launch shape */
 } yk_tune_result;
 
 YK_API yk_status yk_autotune(double alpha, const yk_opts *o, int64_t n_src, const double *xs,

@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
                 ("profile", ctypes.c_int), ("stream", ctypes.c_void_p), ("alloc", _ALLOC),
                 ("free", _FREE), ("alloc_ctx", ctypes.c_void_p), ("use_tuned", ctypes.c_int),
                 ("n_src_hint", ctypes.c_int64), ("fft_fp64", ctypes.c_int), ("dlp", ctypes.c_int),
-                ("truncate", ctypes.c_int)]
+                ("truncate", ctypes.c_int), ("spread_warps", ctypes.c_int),
+                ("spread_batch", ctypes.c_int), ("interp_threads", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -60,7 +61,8 @@ class Info(ctypes.Structure):
                 ("n_modes", ctypes.c_int64), ("n_grid", ctypes.c_int64), ("w", ctypes.c_int),
                 ("beta", ctypes.c_double), ("tile", ctypes.c_int), ("precision", ctypes.c_int),
                 ("device_bytes", ctypes.c_int64), ("truncated", ctypes.c_int),
-                ("r_support", ctypes.c_double)]
+                ("r_support", ctypes.c_double), ("spread_warps", ctypes.c_int),
+                ("spread_batch", ctypes.c_int), ("interp_threads", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -164,7 +166,8 @@ def _len(a) -> int:
 def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
               box=(-1.5, 1.5, -1.5, 1.5), kmax=0.0, kmax_rule=0, period=0.0, tile=0,
               profile=False, stream=None, use_tuned=False, n_src_hint=0,
-              fft_fp64=False, dlp=False, truncate=0, allocator=None) -> Opts:
+              fft_fp64=False, dlp=False, truncate=0, allocator=None, spread_warps=0,
+              spread_batch=0, interp_threads=0) -> Opts:
     """Plan options.  allocator (optional): an object with alloc(nbytes, stream) -> device
     address (0 when it cannot allocate: the library then returns YK_ERR_OOM) and
     free(address, stream), used for every device buffer of the plan instead of cudaMalloc."""
@@ -188,6 +191,9 @@ def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
     o.fft_fp64 = 1 if fft_fp64 else 0
     o.dlp = 1 if dlp else 0
     o.truncate = int(truncate)
+    o.spread_warps = int(spread_warps)
+    o.spread_batch = int(spread_batch)
+    o.interp_threads = int(interp_threads)
     if allocator is not None:
         a_cb = _ALLOC(lambda nbytes, stream, ctx: allocator.alloc(int(nbytes), stream) or None)
         f_cb = _FREE(lambda ptr, stream, ctx: allocator.free(int(ptr), stream))
@@ -531,7 +537,10 @@ def eval_longrange_static(alpha, xs, ys, w, density, xt, yt, out, stream=None, *
 class TuneResult(ctypes.Structure):
     _fields_ = [("n_tried", ctypes.c_int), ("tile", ctypes.c_int * 16),
                 ("ms", ctypes.c_double * 16), ("best_tile", ctypes.c_int),
-                ("best_ms", ctypes.c_double), ("n_grid", ctypes.c_int64)]
+                ("best_ms", ctypes.c_double), ("n_grid", ctypes.c_int64),
+                ("best_spread_warps", ctypes.c_int), ("best_spread_batch", ctypes.c_int),
+                ("best_interp_threads", ctypes.c_int), ("spread_ms", ctypes.c_double),
+                ("interp_ms", ctypes.c_double)]
 
 
 _lib.yk_autotune.argtypes = [_d, ctypes.POINTER(Opts), _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp,
@@ -554,7 +563,10 @@ def autotune(alpha, xs, ys, w, density, xt, yt, **opts) -> dict:
                             _ptr(ys, keep), _ptr(w, keep), _ptr(density, keep), _len(xt),
                             _ptr(xt, keep), _ptr(yt, keep), ctypes.byref(r)), "yk_autotune")
     return {"best_tile": r.best_tile, "best_ms": r.best_ms, "n_grid": r.n_grid,
-            "tried": {r.tile[k]: r.ms[k] for k in range(r.n_tried)}}
+            "tried": {r.tile[k]: r.ms[k] for k in range(r.n_tried)},
+            "best_spread_warps": r.best_spread_warps, "best_spread_batch": r.best_spread_batch,
+            "best_interp_threads": r.best_interp_threads, "spread_ms": r.spread_ms,
+            "interp_ms": r.interp_ms}
 
 
 def tune_cache_save(path: str):

@@ -814,6 +814,9 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->ent_t = P<double2>(p->ent_t);
     d->ent_j = P<int>(p->ent_j);
     d->part = (p->fft_df || d->f32) ? p->part.ptr : nullptr;
+    d->spread_warps = p->spread_warps;
+    d->spread_batch = p->spread_batch;
+    d->interp_threads = p->interp_threads;
     d->wq = P<double>(p->w_src);
     d->trg_ptr = P<int>(p->trg_ptr);
     d->trg_t = P<double2>(p->trg_t);
@@ -879,6 +882,15 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
     if (o->tile > 32 && (o->precision == YK_FP32C || !o->fft_fp64))
         return fail(YK_ERR_ARG, "tile must be <= 32 (64 with fft_fp64)");
     if (o->kmax_rule != 0 && o->kmax_rule != 1) return fail(YK_ERR_ARG, "kmax_rule must be 0 or 1");
+    if (o->spread_warps < 0 || o->spread_warps > 4)
+        return fail(YK_ERR_ARG, "spread_warps must be 0 (default) or 1..4");
+    if (o->spread_batch != 0 &&
+        (o->precision == YK_FP32C ? (o->spread_batch != 8 && o->spread_batch != 16 && o->spread_batch != 32)
+                                  : (o->spread_batch != 4 && o->spread_batch != 8 && o->spread_batch != 16)))
+        return fail(YK_ERR_ARG, "spread_batch must be 0, 4, 8 or 16 (FP32C: 0, 8, 16 or 32)");
+    if (o->interp_threads != 0 && o->interp_threads != 64 && o->interp_threads != 128 &&
+        o->interp_threads != 256)
+        return fail(YK_ERR_ARG, "interp_threads must be 0, 64, 128 or 256");
     if ((o->alloc == nullptr) != (o->free == nullptr))
         return fail(YK_ERR_ARG, "give both alloc and free callbacks, or neither");
     double delta = o->delta;
@@ -971,7 +983,8 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
             if (n % o->tile == 0 && o->tile >= w && n >= 2 * o->tile) T = o->tile;
         } else {
             const int tmax = (o->precision == YK_FP32C || !o->fft_fp64) ? 32 : 64;
-            const int pref = o->use_tuned ? yk_tuned_tile(o->precision, w, n, o->n_src_hint) : 0;
+            int pref = 0, sw = 0, sb = 0, it = 0;
+            if (o->use_tuned) yk_tuned_shape(o->precision, w, n, o->n_src_hint, &pref, &sw, &sb, &it);
             for (int t = tmax; t >= w; --t)
                 if (n % t == 0 && n >= 2 * t) {
                     /* largest admissible edge, or the one nearest the tuned edge */
@@ -985,6 +998,13 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
     p->T = T;
     p->nt = (int)(n / T);
     p->h = p->period / (double)n;
+    /* launch shape: the caller's, else the autotuner's (use_tuned), else the defaults */
+    int tt = 0, sw = 0, sb = 0, it = 0;
+    if (o->use_tuned) yk_tuned_shape(o->precision, w, n, o->n_src_hint, &tt, &sw, &sb, &it);
+    p->spread_warps = o->spread_warps ? o->spread_warps : (sw ? sw : 4);
+    p->spread_batch = o->spread_batch ? o->spread_batch
+                                      : (sb ? sb : (o->precision == YK_FP32C ? 32 : 16));
+    p->interp_threads = o->interp_threads ? o->interp_threads : (it ? it : 256);
     return YK_OK;
 }
 
@@ -1084,6 +1104,9 @@ yk_status yk_plan_info(yk_plan_t p, yk_info *info)
     info->device_bytes = p->bytes;
     info->truncated = p->truncated;
     info->r_support = p->truncated ? p->r1 : 0.0;
+    info->spread_warps = p->spread_warps;
+    info->spread_batch = p->spread_batch;
+    info->interp_threads = p->interp_threads;
     return YK_OK;
 }
 

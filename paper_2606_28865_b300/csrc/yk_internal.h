@@ -101,6 +101,10 @@ struct Inst {
                                  partials, tile t's (T + w - 1)^2 cells at t (T + w - 1)^2 (FP32
                                  pairs), folded into the grid by the row FFT's load; NULL: the
                                  spread writes the grid itself (fixed-point FP64 path) */
+    int spread_warps;         /* owner-tile spread: warps (padded copies) per CTA */
+    int spread_batch;         /* owner-tile spread: sources a warp takes at a time */
+    int interp_threads;       /* threads per interpolation CTA (per-stage launches) */
+    int pad_shape_;           /* keeps sizeof(Inst) a multiple of 16 */
     int items[ST_COUNT];      /* work items of each stage */
     int smem[ST_COUNT];       /* dynamic shared memory of each stage (bytes) */
 };
@@ -221,6 +225,7 @@ struct yk_plan_s {
     double box[4];
     int64_t M, n;
     int w, T, nt, precision;
+    int spread_warps, spread_batch, interp_threads; /* launch shape (yk_opts) */
     int fft_df; /* FP64 path: FFT arithmetic in double-float (default) or in FP64 */
     bool zero; /* k_max == 0: history below tolerance, u = 0 */
     cudaStream_t stream;
@@ -293,8 +298,10 @@ struct yk_plan_s {
  * needs no kernels (k_max = 0, no sources or no targets: u = 0) */
 bool yk_fill_inst(const yk_plan_s *p, yk::Inst *d);
 
-/* tile edge recorded by the autotuner for this key (0: none) */
-int yk_tuned_tile(int precision, int w, int64_t n, int64_t n_src_hint);
+/* launch shape recorded by the autotuner for this key: false when none (the outputs are then
+ * left as they are) */
+bool yk_tuned_shape(int precision, int w, int64_t n, int64_t n_src_hint, int *tile,
+                    int *spread_warps, int *spread_batch, int *interp_threads);
 
 /* Gauss-Legendre nodes (ascending) and weights on [-1, 1] */
 void yk_gauss_legendre(int n, double *x, double *w);

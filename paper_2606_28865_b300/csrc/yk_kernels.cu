@@ -811,16 +811,16 @@ int stage_smem(const Inst &d, int stage)
     const int c = d.f32 ? 8 : 16;          /* bytes of a complex value */
     switch (stage) {
     case ST_SPREAD:
-        if (d.f32) /* FP32C owner-tile spread: kOwnerCopies padded copies of (hi, lo) pairs */
-            return (int)(sizeof(float2) * kOwnerCopies * owner_copy_cells(T, W) +
-                         sizeof(float) * kOwnerCopies * kOwnerBatch32 * (SW + 1) +
-                         sizeof(int) * kOwnerCopies * kOwnerBatch32 +
+        if (d.f32) /* FP32C owner-tile spread: padded copies of (hi, lo) pairs per warp */
+            return (int)(sizeof(float2) * d.spread_warps * owner_copy_cells(T, W) +
+                         sizeof(float) * d.spread_warps * d.spread_batch * (SW + 1) +
+                         sizeof(int) * d.spread_warps * d.spread_batch +
                          (d.dip ? sizeof(float) * ncoef : 0));
         if (d.fft_df) /* double-float owner-tile spread */
-            return (int)(sizeof(df32) * kOwnerCopies *
+            return (int)(sizeof(df32) * d.spread_warps *
                              (owner_copy_cells(T, W) +
-                              kSpreadBatch * (owner_batch_stride(W, d.dip != 0) + 1)) +
-                         sizeof(int) * kOwnerCopies * kSpreadBatch);
+                              d.spread_batch * (owner_batch_stride(W, d.dip != 0) + 1)) +
+                         sizeof(int) * d.spread_warps * d.spread_batch);
         return (int)(sizeof(unsigned long long) * T * T + win_bytes);
     case ST_ROW_FWD:
     case ST_ROW_INV: return c * d.rows * (d.n / 2);
@@ -1208,19 +1208,19 @@ cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st)
     switch (stage) {
     case ST_SPREAD:
         if (d.f32 && d.dip) {
-#define YK_CALL(W) YK_LAUNCH(k_spread_owner32_dip<W>, 32 * kOwnerCopies)
+#define YK_CALL(W) YK_LAUNCH(k_spread_owner32_dip<W>, 32 * d.spread_warps)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
         } else if (d.f32) {
-#define YK_CALL(W) YK_LAUNCH(k_spread_owner32<W>, 32 * kOwnerCopies)
+#define YK_CALL(W) YK_LAUNCH(k_spread_owner32<W>, 32 * d.spread_warps)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
         } else if (d.fft_df && d.dip) {
-#define YK_CALL(W) YK_LAUNCH(k_spread_owner_df_dip<W>, 32 * kOwnerCopies)
+#define YK_CALL(W) YK_LAUNCH(k_spread_owner_df_dip<W>, 32 * d.spread_warps)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
         } else if (d.fft_df) {
-#define YK_CALL(W) YK_LAUNCH(k_spread_owner_df<W>, 32 * kOwnerCopies)
+#define YK_CALL(W) YK_LAUNCH(k_spread_owner_df<W>, 32 * d.spread_warps)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
         } else {
@@ -1246,11 +1246,11 @@ cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st)
         break;
     default:
         if (d.f32) {
-#define YK_CALL(W) YK_LAUNCH(k_interp32<W>, 256)
+#define YK_CALL(W) YK_LAUNCH(k_interp32<W>, d.interp_threads)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
         } else if (d.fft_df) {
-#define YK_CALL(W) YK_LAUNCH(k_interp_df<W>, 256)
+#define YK_CALL(W) YK_LAUNCH(k_interp_df<W>, d.interp_threads)
             YK_W_DISPATCH(d.g.w, YK_CALL)
 #undef YK_CALL
         } else {

@@ -301,10 +301,11 @@ __host__ __device__ constexpr int owner_copy_cells(int T, int W)
     return owner_span(T, W) * owner_pitch(T, W);
 }
 
-/* the copies of the walk, and the dynamic shared memory of an owner-tile spread CTA of nthreads */
-__host__ __device__ inline int owner_copies(int nthreads)
+/* the copies of the walk in a CTA of nthreads: the plan's warps per spread CTA (<= kOwnerCopies);
+ * the batch kernel's larger CTAs leave their other warps idle during the walk */
+__host__ __device__ inline int owner_copies(int nthreads, int spread_warps)
 {
-    return nthreads / 32 < kOwnerCopies ? nthreads / 32 : kOwnerCopies;
+    return nthreads / 32 < spread_warps ? nthreads / 32 : spread_warps;
 }
 
 /* window values kept per source in the owner-tile spread's batch buffer: charges only, 2w values
@@ -316,16 +317,17 @@ __host__ __device__ constexpr int owner_batch_stride(int W, bool dip) { return d
 template <int W, bool DIP>
 __device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
 {
-    constexpr int EB = kSpreadBatch;
+    constexpr int EB = kSpreadBatch;      /* the largest batch (register arrays are sized for it) */
     constexpr int NI = (W * W + 31) / 32; /* taps per lane per source */
     constexpr int SW = owner_batch_stride(W, DIP);
     const Geom &g = d.g;
     const int T = g.T, P = owner_span(T, W), PP = owner_pitch(T, W), TS = P * PP;
-    const int NC = owner_copies(blockDim.x);
+    const int NC = owner_copies(blockDim.x, d.spread_warps);
+    const int eb = d.spread_batch;        /* sources per batch: 4, 8 or 16 */
     df32 *acc = reinterpret_cast<df32 *>(sm);                        /* [NC][TS] */
-    df32 *wbuf = acc + NC * TS;                                      /* [NC][EB][SW] */
-    df32 *qbuf = wbuf + NC * EB * SW;                                /* [NC][EB] */
-    int *obuf = reinterpret_cast<int *>(qbuf + NC * EB);             /* [NC][EB] */
+    df32 *wbuf = acc + NC * TS;                                      /* [NC][eb][SW] */
+    df32 *qbuf = wbuf + NC * eb * SW;                                /* [NC][eb] */
+    int *obuf = reinterpret_cast<int *>(qbuf + NC * eb);             /* [NC][eb] */
     const int tile = d.order ? d.order[item] : item;
     const int beg = d.tile_ptr[tile], end = d.tile_ptr[tile + 1];
     if (beg == end) return; /* nothing to write: the fold skips empty tiles */
@@ -334,9 +336,9 @@ __device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp < NC) {
         df32 *mine = acc + warp * TS;
-        df32 *wb = wbuf + warp * EB * SW;
-        df32 *qb = qbuf + warp * EB;
-        int *ob = obuf + warp * EB;
+        df32 *wb = wbuf + warp * eb * SW;
+        df32 *qb = qbuf + warp * eb;
+        int *ob = obuf + warp * eb;
         /* this lane's taps (c, a) = (t / W, t % W), t = i * 32 + lane; tv false past the last
          * tap (the last round's idle lanes load and store nothing) */
         int toff[NI], tc[NI], ta[NI];
@@ -352,14 +354,14 @@ __device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
         const float2 *__restrict__ ws = d.win_src;
         const float2 *__restrict__ wd = d.win_dip;
         const int4 *__restrict__ ent = reinterpret_cast<const int4 *>(d.ent_t);
-        const int stride = NC * EB;
-        /* Software pipeline over batches of EB sources: the inputs of the next batch (window
+        const int stride = NC * eb;
+        /* Software pipeline over batches of eb sources: the inputs of the next batch (window
          * values, weight and density) are loaded into registers before the current batch is
          * walked and stored to shared memory after it, so the walk hides their latency; the entry
          * records (tap offset, source index) are loaded one batch earlier still, since the weight
          * and density loads depend on the source index.
          * Charges only: the batch's window records are one contiguous block (entry order), read
-         * as 16-byte chunks, chunk g = r * 32 + lane of the block in round r; lane s < EB holds
+         * as 16-byte chunks, chunk g = r * 32 + lane of the block in round r; lane s < eb holds
          * source s's record, weight and density.  With dipoles: two lanes per source (half 0 the
          * y-parts, half 1 the x-parts), since a dipole's record lies elsewhere. */
         constexpr int NCH = DIP ? 1 : (EB * W + 31) / 32;  /* chunks per lane (charges only) */
@@ -370,12 +372,12 @@ __device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
         double2 pw = make_double2(0.0, 0.0);
         const int slot = DIP ? (lane & (EB - 1)) : lane, half = DIP ? lane / EB : 0;
         auto record = [&](int e) {
-            return (slot < EB && e < end) ? ent[e] : make_int4(0, -1, 0, 0);
+            return (slot < eb && e < end) ? ent[e] : make_int4(0, -1, 0, 0);
         };
         auto fetch = [&](int bb, int4 r) {
             if (!DIP) {
                 const float4 *src = reinterpret_cast<const float4 *>(ws + (size_t)bb * 2 * W);
-                const int nch = min(EB, end - bb) * W;
+                const int nch = min(eb, end - bb) * W;
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) {
                     const int gi = k * 32 + lane;
@@ -421,7 +423,7 @@ __device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
                     ob[slot] = r.x;
                 }
                 __syncwarp();
-                const int nch = min(EB, end - bb) * W;
+                const int nch = min(eb, end - bb) * W;
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) {
                     const int gi = k * 32 + lane;
@@ -459,7 +461,7 @@ __device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
             }
             if (half == 0) ob[slot] = r.x | (dipole ? 1 << 30 : 0);
         };
-        int b0 = beg + warp * EB;
+        int b0 = beg + warp * eb;
         int4 rc = record(b0 + slot);
         int4 rn = record(b0 + stride + slot);
         fetch(b0, rc);
@@ -469,7 +471,7 @@ __device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
             rc = rn;
             if (b0 + stride < end) fetch(b0 + stride, rc);
             rn = record(b0 + 2 * stride + slot);
-            const int cnt = min(EB, end - b0);
+            const int cnt = min(eb, end - b0);
             for (int k = 0; k < cnt; ++k) {
                 const int v = ob[k];
                 const int base = v & 0x3fffffff;
@@ -515,17 +517,15 @@ __device__ void st_spread_owner_df(const Inst &d, int item, unsigned char *sm)
  * products, each cell a compensated pair (hi, lo) updated by two-sum; one lane per source
  * evaluates its windows, then the warp walks the batch one source at a time with one lane per
  * tap as above.  The copies are summed in warp order into a normalised pair per cell. */
-constexpr int kOwnerBatch32 = 32; /* sources per batch of the FP32C owner spread */
-
 template <int W, bool DIP>
 __device__ void st_spread_owner32(const Inst &d, int item, unsigned char *sm)
 {
-    constexpr int EB = kOwnerBatch32;
     constexpr int NI = (W * W + 31) / 32;
     constexpr int SW = (DIP ? 4 * W : 2 * W) + 1; /* odd stride: the lanes' stores hit distinct banks */
     const Geom &g = d.g;
     const int T = g.T, P = owner_span(T, W), PP = owner_pitch(T, W), TS = P * PP;
-    const int NC = owner_copies(blockDim.x);
+    const int NC = owner_copies(blockDim.x, d.spread_warps);
+    const int EB = d.spread_batch;  /* sources per batch (one lane each): 8, 16 or 32 */
     float2 *acc = reinterpret_cast<float2 *>(sm);                        /* [NC][TS] */
     float *wbuf = reinterpret_cast<float *>(acc + NC * TS);              /* [NC][EB][SW] */
     int *obuf = reinterpret_cast<int *>(wbuf + NC * EB * SW);            /* [NC][EB] */
@@ -557,7 +557,7 @@ __device__ void st_spread_owner32(const Inst &d, int item, unsigned char *sm)
         const int D = d.wdeg;
         for (int b0 = beg + warp * EB; b0 < end; b0 += NC * EB) {
             const int e = b0 + lane;
-            if (e < end) {
+            if (lane < EB && e < end) {
                 const int4 r = ent[e];
                 const int j = r.y;
                 const float sx = __int_as_float(r.z), sy = __int_as_float(r.w);

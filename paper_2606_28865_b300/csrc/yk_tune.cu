@@ -1,14 +1,18 @@
 /*
- * yk_tune.cu — tile-size autotuner and its cache.
+ * yk_tune.cu — launch-shape autotuner and its cache.
  *
  * The tile edge T (grid cells per side of a spread/interpolation tile; a divisor of the grid size
- * n with w <= T <= 64, or <= 32 for FP32C, and n >= 2T) decides how many windows straddle tiles,
- * how much shared memory a CTA holds and how evenly work spreads over the SMs.  yk_autotune times
- * every admissible T on the caller's own points (CUDA events around the evaluation's kernels,
- * through the public ABI) and records the fastest in a process-wide cache keyed by precision,
- * window width, grid size band and sources per grid cell band.  Plans created with
- * opts.use_tuned take the admissible divisor of their n nearest to the cached tile.  The paper has
- * no counterpart (its NUFFT library chooses its own bins).
+ * n with w <= T <= 64, or <= 32 for the owner-tile spreads, and n >= 2T) decides how many grid
+ * cells a tile's padded copy adds, how much shared memory a CTA holds and how evenly work spreads
+ * over the SMs; the spread's warps per CTA (its padded copies) and sources per batch trade
+ * shared memory and registers against latency hiding; the interpolation's threads per CTA set its
+ * occupancy.  yk_autotune times every admissible T with the default shape on the caller's own
+ * points (CUDA events around the evaluation's kernels, through the public ABI), then, at the
+ * fastest T, every spread shape and every interpolation block size (each stage timed alone), and
+ * records the winners in a process-wide cache keyed by precision, window width, grid size band and
+ * sources per grid cell band.  Plans created with opts.use_tuned take the admissible divisor of
+ * their n nearest to the cached tile and the cached shape.  The paper has no counterpart (its
+ * NUFFT library chooses its own bins).
  */
 #include <cuda_runtime.h>
 
@@ -26,8 +30,12 @@ namespace {
 
 using Key = std::tuple<int, int, int, int>; /* precision, w, log2 n band, log2 density band */
 
+struct Shape {
+    int tile, spread_warps, spread_batch, interp_threads;
+};
+
 std::mutex g_tune_mutex;
-std::map<Key, int> g_tuned;
+std::map<Key, Shape> g_tuned;
 
 int band(double v) { return v > 0 ? (int)std::floor(2.0 * std::log2(v) + 0.5) : -999; }
 
@@ -37,14 +45,44 @@ Key key_of(int precision, int w, int64_t n, int64_t n_src)
     return Key(precision, w, band((double)n), band(dens));
 }
 
+/* set_points once, one warm-up evaluation, then the mean per-stage device time of three */
+yk_status time_plan(double alpha, const yk_opts &oc, int64_t n_src, const double *xs,
+                    const double *ys, const double *w, const double *density, int64_t n_trg,
+                    const double *xt, const double *yt, double *u, double *ms)
+{
+    yk_plan_t p = nullptr;
+    yk_status s = yk_plan(alpha, &oc, &p);
+    if (s != YK_OK) return s;
+    s = yk_set_points(p, n_src, xs, ys, w, n_trg, xt, yt);
+    if (s == YK_OK) s = yk_eval_longrange(p, density, u);
+    if (s == YK_OK) s = yk_stage_times(p, ms);
+    for (int r = 0; r < 3 && s == YK_OK; ++r) s = yk_eval_longrange(p, density, u);
+    if (s == YK_OK) s = yk_stage_times(p, ms);
+    yk_destroy(p);
+    return s;
+}
+
+double eval_ms(const double *ms)
+{
+    double t = 0.0;
+    for (int st = YK_STAGE_SPREAD; st <= YK_STAGE_INTERP; ++st) t += ms[st] > 0 ? ms[st] : 0.0;
+    return t;
+}
+
 } /* namespace */
 
-/* preferred tile for a plan (0: nothing cached) — used by yk_plan when opts.use_tuned is set */
-int yk_tuned_tile(int precision, int w, int64_t n, int64_t n_src_hint)
+/* launch shape recorded for a plan's key — used by yk_plan when opts.use_tuned is set */
+bool yk_tuned_shape(int precision, int w, int64_t n, int64_t n_src_hint, int *tile,
+                    int *spread_warps, int *spread_batch, int *interp_threads)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(key_of(precision, w, n, n_src_hint));
-    return it == g_tuned.end() ? 0 : it->second;
+    if (it == g_tuned.end()) return false;
+    *tile = it->second.tile;
+    *spread_warps = it->second.spread_warps;
+    *spread_batch = it->second.spread_batch;
+    *interp_threads = it->second.interp_threads;
+    return true;
 }
 
 extern "C" {
@@ -64,7 +102,8 @@ YK_API yk_status yk_autotune(double alpha, const yk_opts *o, int64_t n_src, cons
     if (s != YK_OK) return s;
     if (info.n_grid == 0 || n_src == 0 || n_trg == 0) return YK_OK; /* nothing to tune */
     const int64_t n = info.n_grid;
-    const int tmax = (o->precision == YK_FP32C || !o->fft_fp64) ? 32 : 64;
+    const bool owner = o->precision == YK_FP32C || !o->fft_fp64;
+    const int tmax = owner ? 32 : 64;
     std::vector<int> cand;
     for (int t = tmax; t >= info.w && (int)cand.size() < YK_TUNE_MAX; --t)
         if (n % t == 0 && n >= 2 * t) cand.push_back(t);
@@ -74,46 +113,94 @@ YK_API yk_status yk_autotune(double alpha, const yk_opts *o, int64_t n_src, cons
         cudaGetLastError();
         return YK_ERR_OOM;
     }
+    yk_opts base = *o;
+    base.profile = 1;
+    base.use_tuned = 0;
+    double ms[YK_NUM_STAGES];
+    /* 1. the tile edge, with the caller's (or the default) launch shape */
     double best = 1e300;
     for (size_t k = 0; k < cand.size(); ++k) {
-        yk_opts oc = *o;
+        yk_opts oc = base;
         oc.tile = cand[k];
-        oc.profile = 1;
-        oc.use_tuned = 0;
-        yk_plan_t p = nullptr;
-        s = yk_plan(alpha, &oc, &p);
+        s = time_plan(alpha, oc, n_src, xs, ys, w, density, n_trg, xt, yt, u, ms);
         if (s != YK_OK) {
             cudaFree(u);
             return s;
         }
-        double ms[YK_NUM_STAGES];
-        s = yk_set_points(p, n_src, xs, ys, w, n_trg, xt, yt);
-        /* one warm-up evaluation, then the mean of three timed ones */
-        if (s == YK_OK) s = yk_eval_longrange(p, density, u);
-        if (s == YK_OK) s = yk_stage_times(p, ms);
-        for (int r = 0; r < 3 && s == YK_OK; ++r) s = yk_eval_longrange(p, density, u);
-        if (s == YK_OK) s = yk_stage_times(p, ms);
-        yk_destroy(p);
-        if (s != YK_OK) {
-            cudaFree(u);
-            return s;
-        }
-        double t_eval = 0.0;
-        for (int st = YK_STAGE_SPREAD; st <= YK_STAGE_INTERP; ++st) t_eval += ms[st] > 0 ? ms[st] : 0.0;
         res->tile[k] = cand[k];
-        res->ms[k] = t_eval;
-        if (t_eval < best) {
-            best = t_eval;
+        res->ms[k] = eval_ms(ms);
+        if (res->ms[k] < best) {
+            best = res->ms[k];
             res->best_tile = cand[k];
-            res->best_ms = t_eval;
+            res->spread_ms = ms[YK_STAGE_SPREAD];
+            res->interp_ms = ms[YK_STAGE_INTERP];
         }
     }
-    cudaFree(u);
     res->n_tried = (int)cand.size();
     res->n_grid = n;
+    base.tile = res->best_tile;
+    {
+        yk_info di;
+        if ((s = yk_plan_params(alpha, &base, n_src, n_trg, &di)) != YK_OK) {
+            cudaFree(u);
+            return s;
+        }
+        res->best_spread_warps = di.spread_warps;
+        res->best_spread_batch = di.spread_batch;
+        res->best_interp_threads = di.interp_threads;
+    }
+    if (owner && res->best_tile > 0) {
+        /* 2. the spread's warps per CTA and sources per batch at that tile (spread time alone) */
+        const int batches32[3] = {8, 16, 32}, batches_df[3] = {4, 8, 16};
+        const int *batches = o->precision == YK_FP32C ? batches32 : batches_df;
+        for (int sw = 2; sw <= 4; ++sw)
+            for (int b = 1; b < 3; ++b) {
+                yk_opts oc = base;
+                oc.spread_warps = sw;
+                oc.spread_batch = batches[b];
+                s = time_plan(alpha, oc, n_src, xs, ys, w, density, n_trg, xt, yt, u, ms);
+                if (s != YK_OK) {
+                    cudaFree(u);
+                    return s;
+                }
+                if (ms[YK_STAGE_SPREAD] > 0 && ms[YK_STAGE_SPREAD] < res->spread_ms) {
+                    res->spread_ms = ms[YK_STAGE_SPREAD];
+                    res->best_spread_warps = sw;
+                    res->best_spread_batch = batches[b];
+                }
+            }
+        /* 3. the interpolation's threads per CTA (interpolation time alone) */
+        base.spread_warps = res->best_spread_warps;
+        base.spread_batch = res->best_spread_batch;
+        for (int th : {128, 256}) {
+            yk_opts oc = base;
+            oc.interp_threads = th;
+            s = time_plan(alpha, oc, n_src, xs, ys, w, density, n_trg, xt, yt, u, ms);
+            if (s != YK_OK) {
+                cudaFree(u);
+                return s;
+            }
+            if (ms[YK_STAGE_INTERP] > 0 && ms[YK_STAGE_INTERP] < res->interp_ms) {
+                res->interp_ms = ms[YK_STAGE_INTERP];
+                res->best_interp_threads = th;
+            }
+        }
+        /* the whole evaluation at the chosen shape */
+        base.interp_threads = res->best_interp_threads;
+        s = time_plan(alpha, base, n_src, xs, ys, w, density, n_trg, xt, yt, u, ms);
+        if (s != YK_OK) {
+            cudaFree(u);
+            return s;
+        }
+        best = eval_ms(ms);
+    }
+    res->best_ms = best;
+    cudaFree(u);
     if (res->best_tile > 0) {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tuned[key_of(o->precision, info.w, n, n_src)] = res->best_tile;
+        g_tuned[key_of(o->precision, info.w, n, n_src)] =
+            Shape{res->best_tile, res->best_spread_warps, res->best_spread_batch,
+                  res->best_interp_threads};
     }
     return YK_OK;
 }
@@ -124,10 +211,12 @@ YK_API yk_status yk_tune_cache_save(const char *path)
     FILE *f = std::fopen(path, "w");
     if (!f) return YK_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    std::fprintf(f, "# precision w n_band density_band tile\n");
+    std::fprintf(f, "# precision w n_band density_band tile spread_warps spread_batch "
+                    "interp_threads\n");
     for (const auto &kv : g_tuned)
-        std::fprintf(f, "%d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
-                     std::get<2>(kv.first), std::get<3>(kv.first), kv.second);
+        std::fprintf(f, "%d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                     std::get<2>(kv.first), std::get<3>(kv.first), kv.second.tile,
+                     kv.second.spread_warps, kv.second.spread_batch, kv.second.interp_threads);
     std::fclose(f);
     return YK_OK;
 }
@@ -140,10 +229,12 @@ YK_API yk_status yk_tune_cache_load(const char *path)
     char line[256];
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     while (std::fgets(line, sizeof line, f)) {
-        int a, b, c, d, t;
+        int a, b, c, d, t, sw = 0, sb = 0, it = 0;
         if (line[0] == '#') continue;
-        if (std::sscanf(line, "%d %d %d %d %d", &a, &b, &c, &d, &t) == 5 && t > 0)
-            g_tuned[Key(a, b, c, d)] = t;
+        /* five columns (tile only) or eight (tile and launch shape; 0 = default) */
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d", &a, &b, &c, &d, &t, &sw,
+                                    &sb, &it);
+        if (got >= 5 && t > 0) g_tuned[Key(a, b, c, d)] = Shape{t, sw, sb, it};
     }
     std::fclose(f);
     return YK_OK;

@@ -181,3 +181,22 @@ def test_tuned_tile_cache_roundtrip(tmp_path):
     yk.tune_cache_clear()
     assert yk.plan_params(10.0, 100000, 100000, delta=3.9e-5, tol=1e-10, use_tuned=True,
                           n_src_hint=100000)["tile"] == max(divisors)
+
+
+def test_launch_shape_options_are_checked_and_reported():
+    """The spread's warps per CTA and sources per batch and the interpolation's threads per CTA:
+    defaults, explicit values reported back, and out-of-range values refused."""
+    import paper_2606_28865_b300 as yk
+    d = yk.plan_params(10.0, delta=0.0167)
+    assert (d["spread_warps"], d["spread_batch"], d["interp_threads"]) == (4, 16, 256)
+    f = yk.plan_params(10.0, delta=0.0167, tol=1e-6, precision=yk.YK_FP32C)
+    assert (f["spread_warps"], f["spread_batch"], f["interp_threads"]) == (4, 32, 256)
+    e = yk.plan_params(10.0, delta=0.0167, spread_warps=2, spread_batch=8, interp_threads=128)
+    assert (e["spread_warps"], e["spread_batch"], e["interp_threads"]) == (2, 8, 128)
+    for bad in (dict(spread_warps=5), dict(spread_batch=32), dict(interp_threads=512),
+                dict(spread_warps=-1), dict(tile=64)):
+        with pytest.raises(yk.YkError) as ei:
+            yk.plan_params(10.0, delta=0.0167, **bad)
+        assert ei.value.status == yk.YK_ERR_ARG, bad
+    with pytest.raises(yk.YkError):
+        yk.plan_params(10.0, delta=0.0167, tol=1e-6, precision=yk.YK_FP32C, spread_batch=4)

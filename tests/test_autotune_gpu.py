@@ -18,7 +18,8 @@ def test_autotune_records_the_fastest_tile():
     args = [t(wk.xs), t(wk.ys), t(wk.w), t(wk.density), t(wk.xt), t(wk.yt)]
     res = yk.autotune(10.0, *args, tol=1e-6, precision=yk.YK_FP32C, h_vol=wk.h_vol)
     assert len(res["tried"]) >= 2
-    assert res["best_ms"] == min(res["tried"].values()) > 0
+    assert res["tried"][res["best_tile"]] == min(res["tried"].values()) > 0
+    assert res["best_ms"] > 0   # one evaluation at the best tile and the tuned launch shape
     info = yk.plan_params(10.0, wk.n_src, wk.n_trg, tol=1e-6, precision=yk.YK_FP32C,
                           h_vol=wk.h_vol, use_tuned=True, n_src_hint=wk.n_src)
     assert info["tile"] == res["best_tile"]
@@ -57,10 +58,43 @@ def test_every_admissible_tile_and_the_tuned_plan_match_the_oracle(prec, tol):
                 p.set_points(args[0], args[1], args[2], args[4], args[5])
                 u = p.eval(args[3]).cpu().numpy()
             assert np.max(np.abs(u - ref)) <= tol * scale, (alpha, tile)
+        # the launch shape was searched too, and a tuned plan takes all of it
+        assert 1 <= res["best_spread_warps"] <= 4 and res["best_interp_threads"] in (64, 128, 256)
+        assert res["best_spread_batch"] in ((4, 8, 16) if prec == 0 else (8, 16, 32))
         with yk.Plan(alpha, tol=tol, precision=prec, h_vol=wk.h_vol, box=wk.box, use_tuned=True,
                      n_src_hint=wk.n_src) as p:
-            assert p.info["tile"] == res["best_tile"]
+            info = p.info
+            assert info["tile"] == res["best_tile"]
+            assert (info["spread_warps"], info["spread_batch"], info["interp_threads"]) == (
+                res["best_spread_warps"], res["best_spread_batch"], res["best_interp_threads"])
             p.set_points(args[0], args[1], args[2], args[4], args[5])
             u = p.eval(args[3]).cpu().numpy()
         assert np.max(np.abs(u - ref)) <= tol * scale, alpha
+        # every launch shape the tuner may pick gives the same potentials within the tolerance
+        for sw, sb, it in ((1, 4 if prec == 0 else 8, 64), (2, 8 if prec == 0 else 16, 128),
+                           (3, 16 if prec == 0 else 32, 256)):
+            with yk.Plan(alpha, tol=tol, precision=prec, h_vol=wk.h_vol, box=wk.box,
+                         spread_warps=sw, spread_batch=sb, interp_threads=it) as p:
+                p.set_points(args[0], args[1], args[2], args[4], args[5])
+                u = p.eval(args[3]).cpu().numpy()
+            assert np.max(np.abs(u - ref)) <= tol * scale, (alpha, sw, sb, it)
+    yk.tune_cache_clear()
+
+
+def test_tune_cache_round_trip_keeps_the_launch_shape(tmp_path):
+    import paper_2606_28865_b300 as yk
+    yk.tune_cache_clear()
+    wk = W.config_small()
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    args = [t(wk.xs), t(wk.ys), t(wk.w), t(wk.density), t(wk.xt), t(wk.yt)]
+    res = yk.autotune(wk.alpha, *args, tol=1e-10, h_vol=wk.h_vol, box=wk.box)
+    path = str(tmp_path / "tune.txt")
+    yk.tune_cache_save(path)
+    yk.tune_cache_clear()
+    yk.tune_cache_load(path)
+    info = yk.plan_params(wk.alpha, wk.n_src, wk.n_trg, tol=1e-10, h_vol=wk.h_vol, box=wk.box,
+                          use_tuned=True, n_src_hint=wk.n_src)
+    assert (info["tile"], info["spread_warps"], info["spread_batch"], info["interp_threads"]) == (
+        res["best_tile"], res["best_spread_warps"], res["best_spread_batch"],
+        res["best_interp_threads"])
     yk.tune_cache_clear()
