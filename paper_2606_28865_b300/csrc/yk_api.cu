@@ -484,7 +484,7 @@ void free_all(yk_plan_t p)
                      &p->trg_ptr,
                      &p->trg_cur, &p->err, &p->w_src, &p->src_t, &p->ent_t, &p->ent_j,
                      &p->trg_t, &p->trg_idx, &p->trg_tmp, &p->src_tap, &p->trg_tap,
-                     &p->trg_frac, &p->stage_x, &p->stage_y,
+                     &p->trg_frac, &p->trg_hist, &p->stage_x, &p->stage_y,
                      &p->stage_w, &p->stage_u};
     for (DevBuf *b : all) buf_free(p, *b);
     for (int r = 0; r < yk_plan_s::kEventRing; ++r)
@@ -1174,6 +1174,10 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
         YK_TRY(buf_alloc(p, p->src_tap, sizeof(int2) * (ns + nd), "source taps"));
         YK_TRY(buf_alloc(p, p->trg_tap, sizeof(int4) * nt, "target taps"));
         if (p->fft_df) YK_TRY(buf_alloc(p, p->trg_frac, sizeof(float4) * nt, "target windows"));
+        const int64_t nch = yk::hist_chunks(n_trg, p->nt * p->nt);
+        if (nch > 0)
+            YK_TRY(buf_alloc(p, p->trg_hist, sizeof(int) * (size_t)nch * p->nt * p->nt,
+                             "target histograms"));
     }
     stage_begin(p, YK_STAGE_BIN_SRC);
     if (prep)
@@ -1226,7 +1230,8 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
                                       P<int>(p->trg_cnt), P<int>(p->trg_ptr), P<int>(p->trg_cur),
                                       P<double2>(p->trg_t),
                                       p->fft_df ? P<float4>(p->trg_frac) : nullptr,
-                                      P<int>(p->trg_idx), P<int>(p->err), p->stream),
+                                      P<int>(p->trg_idx), P<int>(p->err), p->stream,
+                                      P<int>(p->trg_hist)),
               "bin targets");
     else
         YK_CU(yk::launch_bin_targets(g, n_trg, tx, ty, P<double2>(p->trg_tmp),

@@ -139,10 +139,14 @@ cudaError_t launch_prep_sources(const Geom &g, int64_t ns, const double *xs, con
                                 int64_t nd, const double *xd, const double *yd, int2 *tap,
                                 float4 *frac, int *tile_cnt, int *tile_ptr, int *tile_cur,
                                 double2 *ent_t, int *ent_j, int *err, cudaStream_t st, bool owner);
+/* hist (may be NULL): hist_chunks(nt, tiles) x tiles ints of scratch for the histogram binning
+ * (no global atomics); without it, or when the tiles' counters do not fit in shared memory, the
+ * targets are binned with warp-aggregated global atomics */
 cudaError_t launch_prep_targets(const Geom &g, int64_t nt, const double *xt, const double *yt,
                                 int4 *tap_tmp, float4 *frac_tmp, int *cnt, int *ptr, int *cur,
                                 double2 *trg_t, float4 *trg_frac, int *trg_idx, int *err,
-                                cudaStream_t st);
+                                cudaStream_t st, int *hist = nullptr);
+int64_t hist_chunks(int64_t nt, int ntiles);
 /* double-float window values of points given by their window arguments frac (as above):
  * out[i * 2w ...] as described for Inst::win_src; with deriv, 4w values per point including the
  * derivative's; a point whose frac is never written gets none (tap.x == INT_MIN is not read
@@ -280,6 +284,7 @@ struct yk_plan_s {
      * arguments (float4) and src_tap their first taps (int2); trg_tap the targets' first taps and
      * cell tiles (int4, original order); trg_frac the targets' window arguments in tile order */
     DevBuf src_tap, trg_tap, trg_frac;
+    DevBuf trg_hist; /* int[chunks * tiles]: the targets' histogram binning */
     /* staging copies of host arrays */
     DevBuf stage_x, stage_y, stage_w, stage_u;
     DevBuf stage_d[6]; /* dipole inputs xd, yd, wd, nx, ny and the density mu */

@@ -368,6 +368,103 @@ __global__ void k_prep_trg_fill(int64_t nt, const int4 *__restrict__ tap4,
     }
 }
 
+/* Target binning by chunk histograms (no global atomics): CTA c prepares the targets of its chunk
+ * and counts them per tile in shared memory, its row of counts goes to hist[c][.]; a column pass
+ * turns each tile's counts into exclusive offsets over the chunks (and the tile totals); after the
+ * scan of the totals, CTA c scatters its targets from per-tile cursors ptr[t] + hist[c][t] held in
+ * shared memory.  Uniformly spread targets make per-target global atomics contend on few
+ * addresses; shared-memory counters do not.  Used while the tiles' counters fit in shared memory
+ * (kHistTiles). */
+constexpr int kHistTiles = 16384;
+constexpr int kHistThreads = 1024;
+
+template <int W>
+__global__ void __launch_bounds__(kHistThreads)
+    k_trg_hist(int64_t nt, int64_t chunk, const double *__restrict__ xt,
+               const double *__restrict__ yt, Geom g, int4 *__restrict__ tap4,
+               float4 *__restrict__ frac, int *__restrict__ hist, int *__restrict__ err)
+{
+    extern __shared__ int sh_cnt[];
+    const int ntiles = g.nt * g.nt;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) sh_cnt[t] = 0;
+    __syncthreads();
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(nt, i0 + chunk);
+    bool bad = false;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        int2 tp = make_int2(0, 0);
+        float4 fr = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        long long Tx, Ty;
+        int tile = -1;
+        if (prep_point<W>(g, xt[i], yt[i], tp, fr, Tx, Ty)) {
+            tile = ((int)(Ty >> kFixBits) / g.T) * g.nt + (int)(Tx >> kFixBits) / g.T;
+            atomicAdd(&sh_cnt[tile], 1);
+        } else {
+            bad = true;
+        }
+        tap4[i] = make_int4(tp.x, tp.y, tile, 0);
+        frac[i] = fr;
+    }
+    if (bad) atomicOr(err, ERR_POINT_OUTSIDE);
+    __syncthreads();
+    int *row = hist + (int64_t)blockIdx.x * ntiles;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) row[t] = sh_cnt[t];
+}
+
+/* per tile t: hist[c][t] <- sum of hist[c'][t] over c' < c (in place), cnt[t] <- the total.  A
+ * CTA takes 32 consecutive tiles: their counts of every chunk are read row by row (coalesced)
+ * into shared memory, one thread per tile scans its column there, and the offsets are written
+ * back the same way.  Needs nchunks * 33 ints of shared memory. */
+__global__ void __launch_bounds__(256)
+    k_hist_columns(int *__restrict__ hist, int nchunks, int ntiles, int *__restrict__ cnt)
+{
+    extern __shared__ int sh_col[]; /* [nchunks][33] */
+    const int t0 = blockIdx.x * 32;
+    for (int idx = threadIdx.x; idx < nchunks * 32; idx += blockDim.x) {
+        const int c = idx >> 5, j = idx & 31;
+        sh_col[c * 33 + j] = t0 + j < ntiles ? hist[(int64_t)c * ntiles + t0 + j] : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int run = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            const int v = sh_col[c * 33 + threadIdx.x];
+            sh_col[c * 33 + threadIdx.x] = run;
+            run += v;
+        }
+        if (t0 + threadIdx.x < ntiles) cnt[t0 + threadIdx.x] = run;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nchunks * 32; idx += blockDim.x) {
+        const int c = idx >> 5, j = idx & 31;
+        if (t0 + j < ntiles) hist[(int64_t)c * ntiles + t0 + j] = sh_col[c * 33 + j];
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kHistThreads)
+    k_trg_scatter(int64_t nt, int64_t chunk, const int4 *__restrict__ tap4,
+                  const float4 *__restrict__ frac, const int *__restrict__ hist, int ntiles,
+                  const int *__restrict__ ptr, double2 *__restrict__ trg_t,
+                  float4 *__restrict__ trg_frac, int *__restrict__ trg_idx)
+{
+    extern __shared__ int sh_cur[];
+    const int *row = hist + (int64_t)blockIdx.x * ntiles;
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) sh_cur[t] = ptr[t] + row[t];
+    __syncthreads();
+    const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(nt, i0 + chunk);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const int4 tp = tap4[i];
+        if (tp.z < 0) continue;
+        const float4 fr = frac[i];
+        const int slot = atomicAdd(&sh_cur[tp.z], 1);
+        *reinterpret_cast<int4 *>(trg_t + slot) =
+            make_int4(tp.x, tp.y, __float_as_int(frac_offset<W>(fr.x, fr.y)),
+                      __float_as_int(frac_offset<W>(fr.z, fr.w)));
+        if (trg_frac) trg_frac[slot] = fr;
+        trg_idx[slot] = (int)i;
+    }
+}
+
 /* exclusive scan of cnt[0..count) into ptr[0..count] in three passes over blocks of kScanBlock
  * elements: block sums into bsum, a scan of the block sums (one CTA), then each block adds its
  * offset.  bsum holds ceil(count / kScanBlock) ints. */
@@ -982,13 +1079,49 @@ cudaError_t launch_prep_sources(const Geom &g, int64_t ns, const double *xs, con
     return cudaGetLastError();
 }
 
+/* chunks of the histogram binning for nt targets over ntiles tiles: about 4096 targets each, at
+ * most enough that the histogram matrix stays below 8M counters; 0 when the tiles' counters do
+ * not fit in shared memory (the global-atomic binning is used then) */
+int64_t hist_chunks(int64_t nt, int ntiles)
+{
+    if (ntiles > kHistTiles || nt <= 0) return 0;
+    /* at least 4096 targets a chunk and one chunk (a CTA of kHistThreads) per SM of a 148-SM
+     * part at most: a chunk zeroes, fills and writes a whole row of tile counters, so its
+     * targets should outnumber its counters */
+    return std::max<int64_t>(1, std::min<int64_t>((nt + 4095) / 4096, 148));
+}
+
 cudaError_t launch_prep_targets(const Geom &g, int64_t nt, const double *xt, const double *yt,
                                 int4 *tap_tmp, float4 *frac_tmp, int *cnt, int *ptr, int *cur,
                                 double2 *trg_t, float4 *trg_frac, int *trg_idx, int *err,
-                                cudaStream_t st)
+                                cudaStream_t st, int *hist)
 {
     const int ntiles = g.nt * g.nt;
-    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ntiles, st);
+    const int64_t nch = hist ? hist_chunks(nt, ntiles) : 0;
+    cudaError_t e = cudaSuccess;
+    if (nch > 0) {
+        const int64_t chunk = (nt + nch - 1) / nch;
+        const size_t smem = sizeof(int) * (size_t)ntiles;
+#define YK_CALL(W)                                                                              \
+    if ((e = set_smem(k_trg_hist<W>, smem)) != cudaSuccess) return e;                          \
+    if ((e = set_smem(k_trg_scatter<W>, smem)) != cudaSuccess) return e;                       \
+    k_trg_hist<W><<<(int)nch, kHistThreads, smem, st>>>(nt, chunk, xt, yt, g, tap_tmp, frac_tmp,  \
+                                                        hist, err)
+        YK_W_DISPATCH(g.w, YK_CALL)
+#undef YK_CALL
+        const size_t csm = sizeof(int) * 33 * (size_t)nch;
+        if ((e = set_smem(k_hist_columns, csm)) != cudaSuccess) return e;
+        k_hist_columns<<<(ntiles + 31) / 32, 256, csm, st>>>(hist, (int)nch, ntiles, cnt);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = launch_scan(cnt, ptr, ntiles, cur, st)) != cudaSuccess) return e;
+#define YK_CALL(W)                                                                              \
+    k_trg_scatter<W><<<(int)nch, kHistThreads, smem, st>>>(nt, chunk, tap_tmp, frac_tmp, hist,     \
+                                                           ntiles, ptr, trg_t, trg_frac, trg_idx)
+        YK_W_DISPATCH(g.w, YK_CALL)
+#undef YK_CALL
+        return cudaGetLastError();
+    }
+    e = cudaMemsetAsync(cnt, 0, sizeof(int) * ntiles, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(cur, 0, sizeof(int) * ntiles, st);
     if (e != cudaSuccess) return e;
