@@ -592,51 +592,41 @@ __global__ void k_order_fill(const int *__restrict__ ptr, int ntiles, int *__res
  * load) and the piece stride S = (deg + 1) WE padded to an odd number of 16-byte slots: the lanes
  * of a warp read random pieces, and an odd stride spreads them over all bank groups instead of a
  * few. */
-__host__ __device__ constexpr int win_even(int W) { return W + (W & 1); }
-__host__ __device__ constexpr int win_piece_stride(int W, int D)
+/* a row holds the W taps padded with zeros to 4 ceil(W / 4) (the window kernel's four lanes per
+ * point read ceil(W / 4) taps each); the piece stride is made odd in 8-byte words so the pieces
+ * that lanes read spread over the banks */
+__host__ __device__ constexpr int win_row(int W) { return 4 * ((W + 3) / 4); }
+__host__ __device__ constexpr int win_piece_stride(int W, int D) { return (D + 1) * win_row(W) + 1; }
+
+/* TPL window values (taps a0 .. a0 + TPL - 1) of one coordinate by Horner in double-float on the
+ * piece's polynomials (compile-time degree D; the lane's taps interleaved: TPL independent
+ * chains); each step c_k + p x is one fused double-float multiply-add (exact product terms added
+ * to c_k by two-sum).  Taps past the window (a >= W) read the zero pad of the row. */
+template <int TPL, int D, int WE>
+__device__ __forceinline__ void windows_taps(const df32 *c, int a0, df32 x, df32 (&p)[TPL])
 {
-    return ((D + 1) * win_even(W) / 2) % 2 ? (D + 1) * win_even(W) : (D + 1) * win_even(W) + 2;
+#pragma unroll
+    for (int j = 0; j < TPL; ++j) p[j] = c[D * WE + a0 + j];
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k)
+#pragma unroll
+        for (int j = 0; j < TPL; ++j) p[j] = df_mul_add(c[k * WE + a0 + j], p[j], x);
 }
 
-/* W window values of one coordinate by Horner in double-float on the piece's polynomials
- * (compile-time degree D, taps interleaved: W independent chains); each step c_k + p x is one
- * fused double-float multiply-add (exact product terms added to c_k by two-sum) */
-template <int W, int D>
-__device__ __forceinline__ void windows_piece(const df32 *c, df32 x, df32 (&p)[W])
-{
-    constexpr int WE = win_even(W);
-    df32 ck[WE];
-    auto row = [&](int k) {
-        const float4 *r = reinterpret_cast<const float4 *>(c + k * WE);
-#pragma unroll
-        for (int m = 0; m < WE / 2; ++m) {
-            const float4 v = r[m];
-            ck[2 * m] = df32(v.x, v.y);
-            ck[2 * m + 1] = df32(v.z, v.w);
-        }
-    };
-    row(D);
-#pragma unroll
-    for (int a = 0; a < W; ++a) p[a] = ck[a];
-#pragma unroll
-    for (int k = D - 1; k >= 0; --k) {
-        row(k);
-#pragma unroll
-        for (int a = 0; a < W; ++a) p[a] = df_mul_add(ck[a], p[a], x);
-    }
-}
-
-/* double-float window values per point (see launch_frac_windows_df): one thread per point,
- * Horner in double-float on the kWinPieces-piece per-tap polynomials staged in shared memory
- * (piece h of u = l0 - t + w/2 in [0, 1) is [h/P, (h+1)/P), argument x = 2P u - 2h - 1); the
- * argument comes from the point's exact FP32 pair u, so no FP64 arithmetic is involved */
+/* double-float window values per point (see launch_frac_windows_df): four lanes per point, each
+ * evaluating TPL = ceil(W / 4) consecutive taps of both coordinates by Horner in double-float on
+ * the kWinPieces-piece per-tap polynomials staged in shared memory (piece h of
+ * u = l0 - t + w/2 in [0, 1) is [h/P, (h+1)/P), argument x = 2P u - 2h - 1).  The four lanes of
+ * a point read one piece's coefficients at consecutive taps, so a half-warp reads only four
+ * pieces; the argument comes from the point's exact FP32 pair u (no FP64 arithmetic). */
 template <int W>
-__global__ void k_frac_windows_df(int64_t n, const float4 *__restrict__ frac,
-                                  const int *__restrict__ count, const float2 *__restrict__ coef,
-                                  int deriv, int64_t pitch, float2 *__restrict__ out,
-                                  const int *__restrict__ idx, int64_t idx_lim)
+__global__ void __launch_bounds__(256)
+    k_frac_windows_df(int64_t n, const float4 *__restrict__ frac, const int *__restrict__ count,
+                      const float2 *__restrict__ coef, int deriv, int64_t pitch,
+                      float2 *__restrict__ out, const int *__restrict__ idx, int64_t idx_lim)
 {
-    constexpr int NP = kWinPieces, D = kPieceDeg[W], WE = win_even(W);
+    constexpr int NP = kWinPieces, D = kPieceDeg[W], WE = win_row(W);
+    constexpr int TPL = (W + 3) / 4;
     constexpr int S0 = win_piece_stride(W, D), S1 = win_piece_stride(W, D - 1);
     extern __shared__ __align__(16) unsigned char sm[];
     df32 *cw = reinterpret_cast<df32 *>(sm);
@@ -652,12 +642,9 @@ __global__ void k_frac_windows_df(int64_t n, const float4 *__restrict__ frac,
         cw[(dv ? NP * S0 : 0) + h * (dv ? S1 : S0) + k * WE + a] = df32(coef[i].x, coef[i].y);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    /* every lane stays to the end (the point-major stores are warp-cooperative); lanes past the
-     * valid points compute a dummy point and store nothing */
     const int64_t nv = count ? min(n, (int64_t)*count) : n;
     const int stride = deriv ? 4 * W : 2 * W;
-    float2 *stg = reinterpret_cast<float2 *>(cw + m) + (size_t)warp * 32 * (W + 1);
+    const int q = threadIdx.x & 3, a0 = q * TPL; /* this lane's first tap */
     /* the argument x = 2P u - (2h + 1) of u = (uh, ul): 2P uh and the integer are exact in FP32,
      * so one two-sum gives their difference exactly; 2P ul is added to its low word */
     auto piece_arg = [&](float uh, float ul, int &h) {
@@ -665,13 +652,12 @@ __global__ void k_frac_windows_df(int64_t n, const float4 *__restrict__ frac,
         const df32 s = df32(YK_FMUL(2.0f * NP, uh), 0.0f) + df32(-(float)(2 * h + 1), 0.0f);
         return df_fast_two_sum(s.hi, YK_FADD(s.lo, YK_FMUL(2.0f * NP, ul)));
     };
-    /* grid-stride over blocks of points, so the coefficient tables are staged once per CTA */
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nv;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        const int64_t wbase = i - lane; /* the warp's first point */
-        float4 fr = make_float4(0.5f, 0.0f, 0.5f, 0.0f);
+    /* grid-stride over groups of points (blockDim / 4 per CTA), tables staged once per CTA */
+    for (int64_t base = (int64_t)blockIdx.x * (blockDim.x >> 2); base < nv;
+         base += (int64_t)gridDim.x * (blockDim.x >> 2)) {
+        const int64_t i = base + (threadIdx.x >> 2);
         bool ok = i < nv;
+        float4 fr = make_float4(0.5f, 0.0f, 0.5f, 0.0f);
         if (ok && idx) { /* point i is frac[idx[i]]; indices >= idx_lim get no values */
             const int k = idx[i];
             ok = k < idx_lim;
@@ -679,41 +665,32 @@ __global__ void k_frac_windows_df(int64_t n, const float4 *__restrict__ frac,
         } else if (ok) {
             fr = frac[i];
         }
-        const unsigned okm = __ballot_sync(0xffffffffu, ok);
-        /* part q (W values) of every point: value-major planes (value k of point i at
-         * k * pitch + i, the interpolation's lanes then read consecutive points) or point-major
-         * records (values i * stride + q W + a), the latter staged per warp in shared memory and
-         * written as consecutive addresses */
-        auto emit = [&](int q, const df32 (&v)[W]) {
-            if (pitch) {
-                if (ok)
+        if (!ok) continue; /* no warp-wide operation follows */
+        /* part pq (W values) of point i: value-major planes (value k at k * pitch + i) or the
+         * point-major record (values i * stride + pq W + a) */
+        auto emit = [&](int pq, const df32 (&v)[TPL]) {
 #pragma unroll
-                    for (int a = 0; a < W; ++a)
-                        out[(int64_t)(q * W + a) * pitch + i] = make_float2(v[a].hi, v[a].lo);
-                return;
+            for (int j = 0; j < TPL; ++j) {
+                const int a = a0 + j;
+                if (a < W) {
+                    const float2 val = make_float2(v[j].hi, v[j].lo);
+                    if (pitch) out[(int64_t)(pq * W + a) * pitch + i] = val;
+                    else out[(size_t)i * stride + pq * W + a] = val;
+                }
             }
-#pragma unroll
-            for (int a = 0; a < W; ++a) stg[lane * (W + 1) + a] = make_float2(v[a].hi, v[a].lo);
-            __syncwarp();
-            for (int e = lane; e < 32 * W; e += 32) {
-                const int pt = e / W, a = e - pt * W;
-                if ((okm >> pt) & 1u)
-                    out[(size_t)(wbase + pt) * stride + q * W + a] = stg[pt * (W + 1) + a];
-            }
-            __syncwarp(); /* the buffer is refilled by the next part */
         };
         int hx, hy;
         const df32 ax = piece_arg(fr.x, fr.y, hx), ay = piece_arg(fr.z, fr.w, hy);
-        df32 p[W];
-        windows_piece<W, D>(cw + hy * S0, ay, p);
+        df32 p[TPL];
+        windows_taps<TPL, D, WE>(cw + hy * S0, a0, ay, p);
         emit(0, p);
-        windows_piece<W, D>(cw + hx * S0, ax, p);
+        windows_taps<TPL, D, WE>(cw + hx * S0, a0, ax, p);
         emit(1, p);
         if (deriv) {
             const df32 *cwd = cw + NP * S0;
-            windows_piece<W, D - 1>(cwd + hy * S1, ay, p);
+            windows_taps<TPL, D - 1, WE>(cwd + hy * S1, a0, ay, p);
             emit(2, p);
-            windows_piece<W, D - 1>(cwd + hx * S1, ax, p);
+            windows_taps<TPL, D - 1, WE>(cwd + hx * S1, a0, ax, p);
             emit(3, p);
         }
     }
@@ -1017,12 +994,11 @@ cudaError_t launch_frac_windows_df(const Geom &g, int64_t n, const float4 *frac,
 {
     if (n <= 0) return cudaSuccess;
     if (g.w < 2 || g.w > 16 || deg != kPieceDeg[g.w]) return cudaErrorInvalidValue;
-    /* coefficient tables (padded layout), then a 32 x (w + 1) staging buffer per warp */
+    /* coefficient tables in the padded layout */
     const size_t smem = sizeof(df32) * kWinPieces *
-                            (win_piece_stride(g.w, deg) + (deriv ? win_piece_stride(g.w, deg - 1) : 0)) +
-                        sizeof(float2) * 8 * 32 * (g.w + 1);
-    /* grid-stride: at most 8 CTAs of 256 points per SM of a 148-SM part, looping over the rest */
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 8);
+                        (win_piece_stride(g.w, deg) + (deriv ? win_piece_stride(g.w, deg - 1) : 0));
+    /* grid-stride: at most 8 CTAs of 64 points per SM of a 148-SM part, looping over the rest */
+    const int blocks = (int)std::min<int64_t>((n + 63) / 64, 148 * 8);
     cudaError_t e = cudaSuccess;
 #define YK_CALL(W)                                                                              \
     if ((e = set_smem(k_frac_windows_df<W>, smem)) != cudaSuccess) return e;                   \
