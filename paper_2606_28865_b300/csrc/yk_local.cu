@@ -35,6 +35,14 @@
 
 namespace {
 
+using yk::df32;
+using yk::df_fast_two_sum;
+using yk::df_mul_add;
+using yk::df_two_sum;
+using yk::operator+;
+using yk::operator-;
+using yk::operator*;
+
 constexpr int kMaxQ = 32;      /* nodes per panel this build accepts */
 constexpr int kMaxCells = 1 << 22;
 
@@ -537,16 +545,18 @@ constexpr int kDyDeg = 8;          /* degree of the table's pieces */
 constexpr double kDyPiece = 0.5;   /* their width in rho = r^2 / (4 delta_j) */
 
 struct DyLevel {
-    double inv4d;      /* 1 / (kDyPiece 4 delta_j): the piece coordinate */
-    double R2;         /* R_j^2: K_j is below 1e-16 of its peak beyond R_j */
+    df32 inv4d;        /* 1 / (kDyPiece 4 delta_j): the piece coordinate */
     float R2f;         /* FP32 screen radius^2: R_j widened past the FP32 distance error */
+    float R2;          /* R_j^2 (K_j is below 1e-16 of its peak beyond R_j) */
     int npc;           /* table pieces */
-    const double *tab; /* npc x (kDyDeg + 1) monomial coefficients in z = 2 (rho' - k) - 1 */
-    const float *Xf, *Yf; /* FP32 copies of the sorted nodes (the screen) */
+    const float2 *tab; /* npc x (kDyDeg + 1) monomial coefficients in z = 2 (rho' - k) - 1, as
+                          double-float pairs */
+    const float *Xf, *Yf; /* the sorted nodes' coordinates: high words (also the FP32 screen) */
+    const float *Xl, *Yl; /* and low words */
     LocalGrid G;       /* cells of edge >= R_j */
     const int *ptr;    /* nodes per cell */
-    const double *X, *Y, *Q; /* nodes sorted by cell; Q = density |gamma'| w */
-    const double *NX, *NY;   /* outward unit normals at the nodes (double layer), else NULL */
+    const float2 *Q;   /* density |gamma'| w of the sorted nodes, double-float */
+    const float2 *NX, *NY; /* outward unit normals (double layer, double-float), else NULL */
 };
 
 /* node (p, s, k): parameter -1 + (2 s + 1 + t_k) / m of panel p */
@@ -589,32 +599,42 @@ __global__ void k_pt_count(int64_t n, const double *__restrict__ X, const double
     if (i < n) atomicAdd(&cnt[pt_cell(X[i], Y[i], G)], 1);
 }
 
+/* the nodes sorted by cell, as double-float pairs (the high words of the coordinates double as
+ * the FP32 screen) */
+__device__ __forceinline__ float2 df_pair(double v)
+{
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
 __global__ void k_pt_fill(int64_t n, const double *__restrict__ X, const double *__restrict__ Y,
                           const double *__restrict__ Q, const double *__restrict__ NX,
                           const double *__restrict__ NY, LocalGrid G, const int *__restrict__ ptr,
-                          int *__restrict__ cur, double *__restrict__ Xs, double *__restrict__ Ys,
-                          double *__restrict__ Qs, double *__restrict__ NXs,
-                          double *__restrict__ NYs, float *__restrict__ Xfs,
-                          float *__restrict__ Yfs)
+                          int *__restrict__ cur, float *__restrict__ Xf, float *__restrict__ Xl,
+                          float *__restrict__ Yf, float *__restrict__ Yl, float2 *__restrict__ Qs,
+                          float2 *__restrict__ NXs, float2 *__restrict__ NYs)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int c = pt_cell(X[i], Y[i], G);
     const int e = ptr[c] + atomicAdd(&cur[c], 1);
-    Xs[e] = X[i];
-    Ys[e] = Y[i];
-    Qs[e] = Q[i];
-    Xfs[e] = (float)X[i];
-    Yfs[e] = (float)Y[i];
+    const float2 x = df_pair(X[i]), y = df_pair(Y[i]);
+    Xf[e] = x.x;
+    Xl[e] = x.y;
+    Yf[e] = y.x;
+    Yl[e] = y.y;
+    Qs[e] = df_pair(Q[i]);
     if (NX) {
-        NXs[e] = NX[i];
-        NYs[e] = NY[i];
+        NXs[e] = df_pair(NX[i]);
+        NYs[e] = df_pair(NY[i]);
     }
 }
 
 /* u_i += S_{L,D}^{(j)} at the near targets: one warp per target (the targets grouped by cell),
  * the lanes striding over the nodes of the 3 x 3 cells around it (sorted by cell, so the loads are
- * contiguous), partial sums combined by shuffles in a fixed order */
+ * contiguous), each node screened in FP32 and, within R_j, its term q K_j(r) evaluated in
+ * double-float arithmetic (distance, table piece, Horner, accumulation: B300 runs FP32 pairs much
+ * faster than FP64); lane sums combined by shuffles in a fixed order */
 __global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__restrict__ order,
                                                       const double *__restrict__ xt,
                                                       const double *__restrict__ yt, DyLevel L,
@@ -625,12 +645,13 @@ __global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__r
     if (w >= n_near) return; /* whole warps leave together */
     const int i = order[w];
     const double x = xt[i], y = yt[i];
-    const float xf = (float)x, yf = (float)y;
+    const df32 xd(x), yd(y);
+    const float xf = xd.hi, yf = yd.hi;
     const LocalGrid &G = L.G;
     const double fx = floor((x - G.x0) / G.h), fy = floor((y - G.y0) / G.h);
     if (!(fx >= -1.0 && fx <= G.nx && fy >= -1.0 && fy <= G.ny)) return; /* no node within R_j */
     const int ci = (int)fx, cj = (int)fy;
-    double acc = 0.0;
+    df32 acc(0.0f, 0.0f);
     for (int dj = -1; dj <= 1; ++dj) {
         const int cy = cj + dj;
         if (cy < 0 || cy >= G.ny) continue;
@@ -638,26 +659,36 @@ __global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__r
         const int c0 = cy * G.nx + max(ci - 1, 0), c1 = cy * G.nx + min(ci + 1, G.nx - 1);
         if (ci + 1 < 0 || ci - 1 >= G.nx) continue;
         for (int e = L.ptr[c0] + lane; e < L.ptr[c1 + 1]; e += 32) {
-            const float dxf = L.Xf[e] - xf, dyf = L.Yf[e] - yf;
+            const float xh = L.Xf[e], yh = L.Yf[e];
+            const float dxf = xh - xf, dyf = yh - yf;
             if (!(dxf * dxf + dyf * dyf < L.R2f)) continue; /* FP32 screen */
-            const double dx = L.X[e] - x, dy = L.Y[e] - y;
-            const double r2 = dx * dx + dy * dy;
-            if (r2 < L.R2) {
-                const double rho = r2 * L.inv4d;
-                const int k = min((int)rho, L.npc - 1);
-                const double z = 2.0 * (rho - k) - 1.0;
-                const double *a = L.tab + k * (kDyDeg + 1);
-                double f = a[kDyDeg];
+            const df32 dx = df32(xh, L.Xl[e]) - xd, dy = df32(yh, L.Yl[e]) - yd;
+            const df32 r2 = df_mul_add(dx * dx, dy, dy);
+            if (!(r2.hi < L.R2)) continue;
+            const df32 rho = r2 * L.inv4d;
+            const int k = max(0, min((int)rho.hi, L.npc - 1));
+            /* z = 2 (rho - k) - 1: rho.hi - k is exact, the rest by one two-sum */
+            const df32 zs = df_two_sum(YK_FMUL(2.0f, YK_FSUB(rho.hi, (float)k)), -1.0f);
+            const df32 z = df_fast_two_sum(zs.hi, YK_FADD(zs.lo, YK_FMUL(2.0f, rho.lo)));
+            const float2 *a = L.tab + k * (kDyDeg + 1);
+            df32 f(a[kDyDeg].x, a[kDyDeg].y);
 #pragma unroll
-                for (int n = kDyDeg - 1; n >= 0; --n) f = fma(f, z, a[n]);
-                /* double layer: nu' . (x - x') = -(nu'_x dx + nu'_y dy) */
-                const double qe = L.NX ? -L.Q[e] * (L.NX[e] * dx + L.NY[e] * dy) : L.Q[e];
-                acc = fma(qe, f, acc);
+            for (int n = kDyDeg - 1; n >= 0; --n) f = df_mul_add(df32(a[n].x, a[n].y), f, z);
+            const float2 qv = L.Q[e];
+            df32 qe(qv.x, qv.y);
+            if (L.NX) { /* double layer: nu' . (x - x') = -(nu'_x dx + nu'_y dy) */
+                const float2 nx = L.NX[e], ny = L.NY[e];
+                qe = -(qe * df_mul_add(df32(nx.x, nx.y) * dx, df32(ny.x, ny.y), dy));
             }
+            acc = df_mul_add(acc, qe, f);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) u[i] += acc;
+    for (int o = 16; o > 0; o >>= 1) {
+        const df32 v(__shfl_xor_sync(0xffffffffu, acc.hi, o),
+                     __shfl_xor_sync(0xffffffffu, acc.lo, o));
+        acc = acc + v;
+    }
+    if (lane == 0) u[i] += acc.to_double();
 }
 
 /* K_j on the pieces [k, k + 1] kDyPiece of rho = r^2 / (4 delta_j):
@@ -979,8 +1010,8 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
             break;
         }
         DyLevel L;
-        L.inv4d = 1.0 / (kDyPiece * 4.0 * dj);
-        L.R2 = R * R;
+        L.inv4d = df32(1.0 / (kDyPiece * 4.0 * dj));
+        L.R2 = (float)(R * R);
         {
             /* screen radius: R plus the FP32 rounding of the coordinates (< 2^-24 |x| each, three
              * roundings per difference) with room to spare */
@@ -1001,29 +1032,34 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
             L.G.ny = (int)std::ceil((ymax + 2.0 * R - L.G.y0) / L.G.h) + 1;
         }
         const int nc = L.G.nx * L.G.ny;
-        double *d_tab = nullptr, *d_nodes = nullptr, *d_wq = nullptr;
+        /* the table as double-float pairs */
+        std::vector<float2> tab2(tab.size());
+        for (size_t k = 0; k < tab.size(); ++k) {
+            const float h = (float)tab[k];
+            tab2[k] = make_float2(h, (float)(tab[k] - (double)h));
+        }
+        float2 *d_tab = nullptr;
+        double *d_nodes = nullptr, *d_wq = nullptr;
         int *d_c = nullptr; /* cnt | ptr | cur */
-        e = cudaMallocAsync(&d_tab, sizeof(double) * tab.size(), st);
-        const int na = dl ? 10 : 6; /* X Y Q (NX NY), then the sorted copies */
-        float *d_f = nullptr;       /* FP32 copies of the sorted X, Y */
-        if (e == cudaSuccess) e = cudaMallocAsync(&d_nodes, sizeof(double) * na * nn, st);
-        if (e == cudaSuccess) e = cudaMallocAsync(&d_f, sizeof(float) * 2 * nn, st);
+        e = cudaMallocAsync(&d_tab, sizeof(float2) * tab2.size(), st);
+        /* X Y Q (NX NY) per node in FP64, then the sorted Q (NX NY) as FP32 pairs */
+        const int nu = dl ? 5 : 3, nsrt = dl ? 3 : 1;
+        float *d_f = nullptr; /* the sorted X, Y: high words, low words */
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_nodes, sizeof(double) * (nu + nsrt) * nn, st);
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_f, sizeof(float) * 4 * nn, st);
         if (e == cudaSuccess) e = cudaMallocAsync(&d_wq, sizeof(double) * q, st);
         if (e == cudaSuccess) e = cudaMallocAsync(&d_c, sizeof(int) * (3 * (size_t)nc + 1), st);
         if (e != cudaSuccess) dy_oom = true;
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_tab, tab.data(), sizeof(double) * tab.size(),
+            e = cudaMemcpyAsync(d_tab, tab2.data(), sizeof(float2) * tab2.size(),
                                 cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(d_wq, wq.data(), sizeof(double) * q, cudaMemcpyHostToDevice, st);
         int *cnt = d_c, *cptr = d_c + nc, *ccur = d_c + 2 * nc + 1;
-        const int half = na / 2;
         double *X = d_nodes, *Y = d_nodes + nn, *Qn = d_nodes + 2 * nn;
         double *NX = dl ? d_nodes + 3 * nn : nullptr, *NY = dl ? d_nodes + 4 * nn : nullptr;
-        double *Xs = d_nodes + half * nn, *Ys = d_nodes + (half + 1) * nn;
-        double *Qs = d_nodes + (half + 2) * nn;
-        double *NXs = dl ? d_nodes + (half + 3) * nn : nullptr;
-        double *NYs = dl ? d_nodes + (half + 4) * nn : nullptr;
+        float2 *Qs = reinterpret_cast<float2 *>(d_nodes + nu * nn);
+        float2 *NXs = dl ? Qs + nn : nullptr, *NYs = dl ? Qs + 2 * nn : nullptr;
         const int gb = (int)((nn + 255) / 256);
         if (e == cudaSuccess) {
             k_dy_nodes<<<gb, 256, 0, st>>>(n_panels, q, m, P, d_wq, X, Y, Qn, NX, NY);
@@ -1036,14 +1072,14 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
         /* the scan used the cursors as scratch: zero them for the fill */
         if (e == cudaSuccess) e = cudaMemsetAsync(ccur, 0, sizeof(int) * nc, st);
         if (e == cudaSuccess) {
-            k_pt_fill<<<gb, 256, 0, st>>>(nn, X, Y, Qn, NX, NY, L.G, cptr, ccur, Xs, Ys, Qs, NXs,
-                                          NYs, d_f, d_f + nn);
+            k_pt_fill<<<gb, 256, 0, st>>>(nn, X, Y, Qn, NX, NY, L.G, cptr, ccur, d_f, d_f + nn,
+                                          d_f + 2 * nn, d_f + 3 * nn, Qs, NXs, NYs);
             L.Xf = d_f;
-            L.Yf = d_f + nn;
+            L.Xl = d_f + nn;
+            L.Yf = d_f + 2 * nn;
+            L.Yl = d_f + 3 * nn;
             L.tab = d_tab;
             L.ptr = cptr;
-            L.X = Xs;
-            L.Y = Ys;
             L.Q = Qs;
             L.NX = NXs;
             L.NY = NYs;
