@@ -630,27 +630,45 @@ __global__ void k_pt_fill(int64_t n, const double *__restrict__ X, const double 
     }
 }
 
+/* per near target of a level: its cell in the level's grid and its coordinates as FP32 pairs,
+ * computed once (one thread per target) instead of by every lane of the target's warp */
+__global__ void k_dy_targets(int n_near, const int *__restrict__ order,
+                             const double *__restrict__ xt, const double *__restrict__ yt,
+                             LocalGrid G, int2 *__restrict__ cell, float4 *__restrict__ xy)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n_near) return;
+    const int i = order[w];
+    const double x = xt[i], y = yt[i];
+    const double fx = floor((x - G.x0) / G.h), fy = floor((y - G.y0) / G.h);
+    /* outside the cells' reach: no node lies within R_j (marked by an x cell below -1) */
+    const bool in = fx >= -1.0 && fx <= G.nx && fy >= -1.0 && fy <= G.ny;
+    cell[w] = in ? make_int2((int)fx, (int)fy) : make_int2(-2, -2);
+    const float2 px = df_pair(x), py = df_pair(y);
+    xy[w] = make_float4(px.x, px.y, py.x, py.y);
+}
+
 /* u_i += S_{L,D}^{(j)} at the near targets: one warp per target (the targets grouped by cell),
  * the lanes striding over the nodes of the 3 x 3 cells around it (sorted by cell, so the loads are
  * contiguous), each node screened in FP32 and, within R_j, its term q K_j(r) evaluated in
  * double-float arithmetic (distance, table piece, Horner, accumulation: B300 runs FP32 pairs much
  * faster than FP64); lane sums combined by shuffles in a fixed order */
 __global__ void __launch_bounds__(256) k_dyadic_level(int n_near, const int *__restrict__ order,
-                                                      const double *__restrict__ xt,
-                                                      const double *__restrict__ yt, DyLevel L,
+                                                      const int2 *__restrict__ tcell,
+                                                      const float4 *__restrict__ txy, DyLevel L,
                                                       double *__restrict__ u)
 {
     const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (w >= n_near) return; /* whole warps leave together */
+    const int2 tc = tcell[w];
+    if (tc.x < -1) return; /* no node within R_j */
     const int i = order[w];
-    const double x = xt[i], y = yt[i];
-    const df32 xd(x), yd(y);
+    const float4 p4 = txy[w];
+    const df32 xd(p4.x, p4.y), yd(p4.z, p4.w);
     const float xf = xd.hi, yf = yd.hi;
     const LocalGrid &G = L.G;
-    const double fx = floor((x - G.x0) / G.h), fy = floor((y - G.y0) / G.h);
-    if (!(fx >= -1.0 && fx <= G.nx && fy >= -1.0 && fy <= G.ny)) return; /* no node within R_j */
-    const int ci = (int)fx, cj = (int)fy;
+    const int ci = tc.x, cj = tc.y;
     df32 acc(0.0f, 0.0f);
     for (int dj = -1; dj <= 1; ++dj) {
         const int cy = cj + dj;
@@ -1041,7 +1059,11 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
         float2 *d_tab = nullptr;
         double *d_nodes = nullptr, *d_wq = nullptr;
         int *d_c = nullptr; /* cnt | ptr | cur */
+        int2 *d_tcell = nullptr;
+        float4 *d_txy = nullptr;
         e = cudaMallocAsync(&d_tab, sizeof(float2) * tab2.size(), st);
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_tcell, sizeof(int2) * (size_t)n_near, st);
+        if (e == cudaSuccess) e = cudaMallocAsync(&d_txy, sizeof(float4) * (size_t)n_near, st);
         /* X Y Q (NX NY) per node in FP64, then the sorted Q (NX NY) as FP32 pairs */
         const int nu = dl ? 5 : 3, nsrt = dl ? 3 : 1;
         float *d_f = nullptr; /* the sorted X, Y: high words, low words */
@@ -1083,10 +1105,14 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
             L.Q = Qs;
             L.NX = NXs;
             L.NY = NYs;
+            k_dy_targets<<<(n_near + 255) / 256, 256, 0, st>>>(n_near, d_order, xt, yt, L.G,
+                                                                d_tcell, d_txy);
             k_dyadic_level<<<(int)(((int64_t)n_near * 32 + 255) / 256), 256, 0, st>>>(
-                n_near, d_order, xt, yt, L, u);
+                n_near, d_order, d_tcell, d_txy, L, u);
             e = cudaGetLastError();
         }
+        for (void *b : {(void *)d_tcell, (void *)d_txy})
+            if (b) cudaFreeAsync(b, st);
         for (void *b : {(void *)d_tab, (void *)d_nodes, (void *)d_wq, (void *)d_c, (void *)d_f})
             if (b) cudaFreeAsync(b, st);
     }

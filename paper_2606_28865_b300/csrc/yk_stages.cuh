@@ -970,15 +970,17 @@ template <int W> __device__ void st_interp32(const Inst &d, int item, unsigned c
             fy[a] = es_window_stable<float>(sy + (float)a, beta, cw);
         }
         const float *base = sg + (r.y - Y0) * P + (r.x - X0);
-        double acc = 0.0;
+        /* FP32 row sums combined in double-float (the exact product of the FP32 weight and row
+         * sum added by two-sum): the final accumulation keeps ~48 bits, on the FP32 pipe */
+        df32 acc(0.0f, 0.0f);
 #pragma unroll
         for (int cc = 0; cc < W; ++cc) {
             float row = 0.0f;
 #pragma unroll
             for (int a = 0; a < W; ++a) row = fmaf(fx[a], base[cc * P + a], row);
-            acc = fma((double)fy[cc], (double)row, acc);
+            acc = df_mul_add(acc, df32(fy[cc], 0.0f), df32(row, 0.0f));
         }
-        d.u[d.trg_idx[e]] = acc;
+        d.u[d.trg_idx[e]] = acc.to_double();
     }
     __syncthreads();
 }
