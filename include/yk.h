@@ -111,6 +111,11 @@ typedef struct {
     int spread_batch;   /* sources a spread warp takes at a time: 4, 8 or 16 on the double-float
                            path (default 16), 8, 16 or 32 on FP32C (default 32) */
     int interp_threads; /* threads per interpolation CTA: 64, 128 or 256 (default 256) */
+    int interp_tile;    /* FP32C and double-float paths: > 0 sets the edge of the targets' tiles
+                           (the target binning and the interpolation, which read one halo per
+                           tile): a divisor of n_grid, >= w, <= 32, else YK_ERR_ARG; 0: the
+                           autotuner's (use_tuned), else the largest admissible divisor up to 32.
+                           The all-FP64 path (fft_fp64) uses the tile edge for both and takes 0 */
 } yk_opts;
 
 /* Parameters the plan chose (all derived from alpha, tol, delta and the box). */
@@ -130,6 +135,7 @@ typedef struct {
     int truncated;                 /* 1: the truncated kernel is used (opts.truncate) */
     double r_support;              /* truncated kernel: radius beyond which it is zero */
     int spread_warps, spread_batch, interp_threads; /* launch shape (see yk_opts) */
+    int interp_tile;               /* edge of the targets' tiles (the tile edge on fft_fp64) */
 } yk_info;
 
 /* Fill *o with defaults: FP64, tol 1e-10, delta rule with eps_hist 1e-6, box [-1.5,1.5]^2. */
@@ -324,8 +330,8 @@ YK_API const char *yk_last_error(void);
 /*
  * Autotuner.  yk_autotune times, on the caller's points (all arrays device memory; density n_src
  * values), every admissible tile edge with the default launch shape, then at the fastest edge the
- * spread's warps per CTA and sources per batch and the interpolation's threads per CTA (each stage
- * timed alone), and records the fastest of each in a process-wide cache used by plans created
+ * spread's warps per CTA and sources per batch, the targets' tile edge and the interpolation's
+ * threads per CTA (each stage timed alone), and records the fastest of each in a process-wide cache used by plans created
  * with o->use_tuned (batch plans included).  The paper has no counterpart.
  */
 #define YK_TUNE_MAX 16
@@ -338,6 +344,7 @@ typedef struct {
     int64_t n_grid;
     int best_spread_warps, best_spread_batch, best_interp_threads;
     double spread_ms, interp_ms; /* the spread and interpolation at the chosen launch shape */
+    int best_interp_tile;        /* the targets' tile edge (FP32C and double-float paths) */
 } yk_tune_result;
 
 YK_API yk_status yk_autotune(double alpha, const yk_opts *o, int64_t n_src, const double *xs,

@@ -51,7 +51,8 @@ class Opts(ctypes.Structure):
                 ("free", _FREE), ("alloc_ctx", ctypes.c_void_p), ("use_tuned", ctypes.c_int),
                 ("n_src_hint", ctypes.c_int64), ("fft_fp64", ctypes.c_int), ("dlp", ctypes.c_int),
                 ("truncate", ctypes.c_int), ("spread_warps", ctypes.c_int),
-                ("spread_batch", ctypes.c_int), ("interp_threads", ctypes.c_int)]
+                ("spread_batch", ctypes.c_int), ("interp_threads", ctypes.c_int),
+                ("interp_tile", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -62,7 +63,8 @@ class Info(ctypes.Structure):
                 ("beta", ctypes.c_double), ("tile", ctypes.c_int), ("precision", ctypes.c_int),
                 ("device_bytes", ctypes.c_int64), ("truncated", ctypes.c_int),
                 ("r_support", ctypes.c_double), ("spread_warps", ctypes.c_int),
-                ("spread_batch", ctypes.c_int), ("interp_threads", ctypes.c_int)]
+                ("spread_batch", ctypes.c_int), ("interp_threads", ctypes.c_int),
+                ("interp_tile", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -167,7 +169,7 @@ def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
               box=(-1.5, 1.5, -1.5, 1.5), kmax=0.0, kmax_rule=0, period=0.0, tile=0,
               profile=False, stream=None, use_tuned=False, n_src_hint=0,
               fft_fp64=False, dlp=False, truncate=0, allocator=None, spread_warps=0,
-              spread_batch=0, interp_threads=0) -> Opts:
+              spread_batch=0, interp_threads=0, interp_tile=0) -> Opts:
     """Plan options.  allocator (optional): an object with alloc(nbytes, stream) -> device
     address (0 when it cannot allocate: the library then returns YK_ERR_OOM) and
     free(address, stream), used for every device buffer of the plan instead of cudaMalloc."""
@@ -194,6 +196,7 @@ def make_opts(tol=1e-10, precision=YK_FP64, delta=0.0, h_vol=0.0, eps_hist=1e-6,
     o.spread_warps = int(spread_warps)
     o.spread_batch = int(spread_batch)
     o.interp_threads = int(interp_threads)
+    o.interp_tile = int(interp_tile)
     if allocator is not None:
         a_cb = _ALLOC(lambda nbytes, stream, ctx: allocator.alloc(int(nbytes), stream) or None)
         f_cb = _FREE(lambda ptr, stream, ctx: allocator.free(int(ptr), stream))
@@ -540,7 +543,7 @@ class TuneResult(ctypes.Structure):
                 ("best_ms", ctypes.c_double), ("n_grid", ctypes.c_int64),
                 ("best_spread_warps", ctypes.c_int), ("best_spread_batch", ctypes.c_int),
                 ("best_interp_threads", ctypes.c_int), ("spread_ms", ctypes.c_double),
-                ("interp_ms", ctypes.c_double)]
+                ("interp_ms", ctypes.c_double), ("best_interp_tile", ctypes.c_int)]
 
 
 _lib.yk_autotune.argtypes = [_d, ctypes.POINTER(Opts), _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp,
@@ -566,7 +569,7 @@ def autotune(alpha, xs, ys, w, density, xt, yt, **opts) -> dict:
             "tried": {r.tile[k]: r.ms[k] for k in range(r.n_tried)},
             "best_spread_warps": r.best_spread_warps, "best_spread_batch": r.best_spread_batch,
             "best_interp_threads": r.best_interp_threads, "spread_ms": r.spread_ms,
-            "interp_ms": r.interp_ms}
+            "interp_ms": r.interp_ms, "best_interp_tile": r.best_interp_tile}
 
 
 def tune_cache_save(path: str):

@@ -548,6 +548,8 @@ yk::Geom geom_of(const yk_plan_s *p)
     g.n = (int)p->n;
     g.T = p->T;
     g.nt = p->nt;
+    g.Ti = p->Ti;
+    g.nti = p->nti;
     g.w = p->w;
     for (int k = 0; k < 4; ++k) g.box[k] = p->box[k];
     g.A = std::ldexp(g.inv_h, yk::kFixBits);
@@ -621,9 +623,10 @@ yk_status plan_tables(yk_plan_t p)
     /* the source cursors double as the heavy-first ordering's 80-int scratch */
     YK_TRY(buf_alloc(p, p->tile_cur, sizeof(int) * (nt2 > 80 ? nt2 : 80), "tile cursors"));
     YK_TRY(buf_alloc(p, p->tile_order, sizeof(int) * nt2, "tile order"));
-    YK_TRY(buf_alloc(p, p->trg_cnt, sizeof(int) * nt2, "tile counts"));
-    YK_TRY(buf_alloc(p, p->trg_ptr, sizeof(int) * (nt2 + 1), "tile offsets"));
-    YK_TRY(buf_alloc(p, p->trg_cur, sizeof(int) * nt2, "tile cursors"));
+    const size_t nti2 = (size_t)p->nti * p->nti;
+    YK_TRY(buf_alloc(p, p->trg_cnt, sizeof(int) * nti2, "tile counts"));
+    YK_TRY(buf_alloc(p, p->trg_ptr, sizeof(int) * (nti2 + 1), "tile offsets"));
+    YK_TRY(buf_alloc(p, p->trg_cur, sizeof(int) * nti2, "tile cursors"));
     if (p->fft_df || f32) { /* owner-tile spread: one padded tile of partial sums per tile */
         const size_t span = (size_t)p->T + p->w - 1;
         YK_TRY(buf_alloc(p, p->part, sizeof(double) * nt2 * span * span, "padded tiles"));
@@ -891,6 +894,10 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
     if (o->interp_threads != 0 && o->interp_threads != 64 && o->interp_threads != 128 &&
         o->interp_threads != 256)
         return fail(YK_ERR_ARG, "interp_threads must be 0, 64, 128 or 256");
+    if (o->interp_tile < 0 || o->interp_tile > 32 || (o->interp_tile > 0 && o->fft_fp64 &&
+                                                       o->precision == YK_FP64))
+        return fail(YK_ERR_ARG, "interp_tile must be 0 (default) or at most 32, and 0 with "
+                                "fft_fp64");
     if ((o->alloc == nullptr) != (o->free == nullptr))
         return fail(YK_ERR_ARG, "give both alloc and free callbacks, or neither");
     double delta = o->delta;
@@ -982,15 +989,24 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
         if (o->tile > 0) {
             if (n % o->tile == 0 && o->tile >= w && n >= 2 * o->tile) T = o->tile;
         } else {
-            const int tmax = (o->precision == YK_FP32C || !o->fft_fp64) ? 32 : 64;
-            int pref = 0, sw = 0, sb = 0, it = 0;
-            if (o->use_tuned) yk_tuned_shape(o->precision, w, n, o->n_src_hint, &pref, &sw, &sb, &it);
-            for (int t = tmax; t >= w; --t)
+            /* default edge: the largest admissible divisor up to 20 (FP32C) or 24 (double-float
+             * FP64), where the owner-tile spreads measured fastest on B300 (smaller padded copies:
+             * more CTAs, and so more warps, per SM); the all-FP64 path up to 64; the autotuner
+             * searches every edge up to 32 (64) */
+            const int tmax = o->precision == YK_FP32C ? 20 : (!o->fft_fp64 ? 24 : 64);
+            int pref = 0, sw = 0, sb = 0, it = 0, ti = 0;
+            if (o->use_tuned)
+                yk_tuned_shape(o->precision, w, n, o->n_src_hint, &pref, &sw, &sb, &it, &ti);
+            const int tlim = pref > 0 ? (o->precision == YK_FP32C || !o->fft_fp64 ? 32 : 64) : tmax;
+            for (int t = tlim; t >= w; --t)
                 if (n % t == 0 && n >= 2 * t) {
                     /* largest admissible edge, or the one nearest the tuned edge */
                     if (!T || (pref > 0 && std::abs(t - pref) < std::abs(T - pref))) T = t;
                     if (!pref) break;
                 }
+            /* no admissible edge up to tmax (w close to it): the smallest one above */
+            for (int t = tmax + 1; !T && t <= (o->precision == YK_FP32C || !o->fft_fp64 ? 32 : 64); ++t)
+                if (n % t == 0 && n >= 2 * t) T = t;
         }
         if (T) break;
     }
@@ -999,8 +1015,27 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
     p->nt = (int)(n / T);
     p->h = p->period / (double)n;
     /* launch shape: the caller's, else the autotuner's (use_tuned), else the defaults */
-    int tt = 0, sw = 0, sb = 0, it = 0;
-    if (o->use_tuned) yk_tuned_shape(o->precision, w, n, o->n_src_hint, &tt, &sw, &sb, &it);
+    int tt = 0, sw = 0, sb = 0, it = 0, ti = 0;
+    if (o->use_tuned) yk_tuned_shape(o->precision, w, n, o->n_src_hint, &tt, &sw, &sb, &it, &ti);
+    /* the targets' tile: the interpolation reads a tile's halo once for all its targets, so it
+     * gains from larger tiles where the owner-tile spread gains from smaller ones.  On those
+     * paths it is chosen apart from T: the caller's edge, else the admissible divisor nearest
+     * the tuned one, else the largest admissible divisor up to 32 (T itself when none is) */
+    p->Ti = T;
+    if (o->precision == YK_FP32C || !o->fft_fp64) {
+        const int want = o->interp_tile > 0 ? o->interp_tile : ti;
+        if (o->interp_tile > 0 && !(n % want == 0 && want >= w && n >= 2 * want))
+            return fail(YK_ERR_ARG, "interp_tile %d does not divide the grid size %lld or is "
+                                    "below the window width %d", want, (long long)n, w);
+        int best = 0;
+        for (int t = 32; t >= w; --t)
+            if (n % t == 0 && n >= 2 * t) {
+                if (!best || (want > 0 && std::abs(t - want) < std::abs(best - want))) best = t;
+                if (!want) break;
+            }
+        if (best) p->Ti = best;
+    }
+    p->nti = (int)(n / p->Ti);
     p->spread_warps = o->spread_warps ? o->spread_warps : (sw ? sw : 4);
     p->spread_batch = o->spread_batch ? o->spread_batch
                                       : (sb ? sb : (o->precision == YK_FP32C ? 32 : 16));
@@ -1012,10 +1047,11 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
 static int64_t predicted_bytes(const yk_plan_s *p, int64_t n_src, int64_t n_trg)
 {
     if (p->zero) return (int64_t)sizeof(int);
-    const int64_t n = p->n, M = p->M, nt2 = (int64_t)p->nt * p->nt;
+    const int64_t n = p->n, M = p->M, nt2 = (int64_t)p->nt * p->nt,
+                  nti2 = (int64_t)p->nti * p->nti;
     const int64_t r = p->precision == YK_FP32C ? 4 : 8; /* bytes of the real type */
     int64_t b = r * n * n + 2 * r * (M + 1) * n + r * (M + 1) * (2 * M + 1) + 2 * r * n +
-                4 * (n / 2) + 4 * n + 4 * (7 * nt2 + 2) + 4;
+                4 * (n / 2) + 4 * n + 4 * (4 * nt2 + 3 * nti2 + 2) + 4;
     if (p->precision == YK_FP64) b += 8 * (int64_t)(p->w + 2) * p->w * (p->dlp ? 2 : 1);
     else if (p->dlp) b += 4 * (int64_t)(2 * p->w + 3) * p->w;
     const bool owner = p->fft_df || p->precision == YK_FP32C;
@@ -1100,6 +1136,7 @@ yk_status yk_plan_info(yk_plan_t p, yk_info *info)
     info->w = p->w;
     info->beta = p->beta;
     info->tile = p->T;
+    info->interp_tile = p->Ti;
     info->precision = p->precision;
     info->device_bytes = p->bytes;
     info->truncated = p->truncated;
@@ -1174,9 +1211,9 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
         YK_TRY(buf_alloc(p, p->src_tap, sizeof(int2) * (ns + nd), "source taps"));
         YK_TRY(buf_alloc(p, p->trg_tap, sizeof(int4) * nt, "target taps"));
         if (p->fft_df) YK_TRY(buf_alloc(p, p->trg_frac, sizeof(float4) * nt, "target windows"));
-        const int64_t nch = yk::hist_chunks(n_trg, p->nt * p->nt);
+        const int64_t nch = yk::hist_chunks(n_trg, p->nti * p->nti);
         if (nch > 0)
-            YK_TRY(buf_alloc(p, p->trg_hist, sizeof(int) * (size_t)nch * p->nt * p->nt,
+            YK_TRY(buf_alloc(p, p->trg_hist, sizeof(int) * (size_t)nch * p->nti * p->nti,
                              "target histograms"));
     }
     stage_begin(p, YK_STAGE_BIN_SRC);
@@ -1242,7 +1279,7 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
     if (p->fft_df) {
         YK_TRY(buf_alloc(p, p->win_trg, sizeof(float2) * 2 * (size_t)p->w * nt, "target windows"));
         YK_CU(yk::launch_frac_windows_df(g, n_trg, P<float4>(p->trg_frac),
-                                         P<int>(p->trg_ptr) + (size_t)p->nt * p->nt,
+                                         P<int>(p->trg_ptr) + (size_t)p->nti * p->nti,
                                          P<float2>(p->win_pc), p->pdeg, false,
                                          P<float2>(p->win_trg), p->stream, n_trg),
               "target windows");

@@ -31,6 +31,9 @@ struct Geom {
     int n;          /* grid points per axis */
     int T;          /* tile edge (cells); divides n, T >= w, n >= 2T */
     int nt;         /* tiles per axis = n / T */
+    int Ti;         /* tile edge of the target binning and the interpolation (divides n, Ti >= w,
+                       n >= 2 Ti): T, or the plan's separate choice on the owner-tile paths */
+    int nti;        /* target tiles per axis = n / Ti */
     int w;          /* window width */
     double box[4];  /* xmin, xmax, ymin, ymax: points outside are rejected */
     /* fixed-point grid coordinates of the double-float and FP32C paths: T = rint(x A + B) is
@@ -104,7 +107,7 @@ struct Inst {
     int spread_warps;         /* owner-tile spread: warps (padded copies) per CTA */
     int spread_batch;         /* owner-tile spread: sources a warp takes at a time */
     int interp_threads;       /* threads per interpolation CTA (per-stage launches) */
-    int pad_shape_;           /* keeps sizeof(Inst) a multiple of 16 */
+    int pad_shape_[3];        /* keeps sizeof(Inst) a multiple of 16 */
     int items[ST_COUNT];      /* work items of each stage */
     int smem[ST_COUNT];       /* dynamic shared memory of each stage (bytes) */
 };
@@ -228,7 +231,7 @@ struct yk_plan_s {
     double ox, oy;
     double box[4];
     int64_t M, n;
-    int w, T, nt, precision;
+    int w, T, nt, Ti, nti, precision;
     int spread_warps, spread_batch, interp_threads; /* launch shape (yk_opts) */
     int fft_df; /* FP64 path: FFT arithmetic in double-float (default) or in FP64 */
     bool zero; /* k_max == 0: history below tolerance, u = 0 */
@@ -306,7 +309,7 @@ bool yk_fill_inst(const yk_plan_s *p, yk::Inst *d);
 /* launch shape recorded by the autotuner for this key: false when none (the outputs are then
  * left as they are) */
 bool yk_tuned_shape(int precision, int w, int64_t n, int64_t n_src_hint, int *tile,
-                    int *spread_warps, int *spread_batch, int *interp_threads);
+                    int *spread_warps, int *spread_batch, int *interp_threads, int *interp_tile);
 
 /* Gauss-Legendre nodes (ascending) and weights on [-1, 1] */
 void yk_gauss_legendre(int n, double *x, double *w);

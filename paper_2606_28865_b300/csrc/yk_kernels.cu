@@ -143,7 +143,7 @@ __global__ void k_bin_trg_count(int64_t nt, const double *__restrict__ xt,
             atomicOr(err, ERR_POINT_OUTSIDE);
             t = make_double2(-1.0, -1.0);
         } else {
-            tile = ((int)t.y / g.T) * g.nt + (int)t.x / g.T;
+            tile = ((int)t.y / g.Ti) * g.nti + (int)t.x / g.Ti;
         }
         tmp[i] = t;
     }
@@ -159,7 +159,7 @@ __global__ void k_bin_trg_fill(int64_t nt, const double2 *__restrict__ tmp, Geom
     double2 t = make_double2(-1.0, -1.0);
     if (i < nt) t = tmp[i];
     const bool v = t.x >= 0.0;
-    const int tile = v ? ((int)t.y / g.T) * g.nt + (int)t.x / g.T : -1;
+    const int tile = v ? ((int)t.y / g.Ti) * g.nti + (int)t.x / g.Ti : -1;
     const int off = agg_reserve(cur, tile, v);
     if (v) {
         const int slot = ptr[tile] + off;
@@ -311,7 +311,7 @@ __global__ void k_prep_trg_count(int64_t nt, const double *__restrict__ xt,
         if (!prep_point<W>(g, xt[i], yt[i], tp, fr, Tx, Ty)) {
             atomicOr(err, ERR_POINT_OUTSIDE);
         } else {
-            tile = ((int)(Ty >> kFixBits) / g.T) * g.nt + (int)(Tx >> kFixBits) / g.T;
+            tile = ((int)(Ty >> kFixBits) / g.Ti) * g.nti + (int)(Tx >> kFixBits) / g.Ti;
         }
         tap4[i] = make_int4(tp.x, tp.y, tile, 0);
         frac[i] = fr;
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kHistThreads)
                float4 *__restrict__ frac, int *__restrict__ hist, int *__restrict__ err)
 {
     extern __shared__ int sh_cnt[];
-    const int ntiles = g.nt * g.nt;
+    const int ntiles = g.nti * g.nti;
     for (int t = threadIdx.x; t < ntiles; t += blockDim.x) sh_cnt[t] = 0;
     __syncthreads();
     const int64_t i0 = (int64_t)blockIdx.x * chunk, i1 = min(nt, i0 + chunk);
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kHistThreads)
         long long Tx, Ty;
         int tile = -1;
         if (prep_point<W>(g, xt[i], yt[i], tp, fr, Tx, Ty)) {
-            tile = ((int)(Ty >> kFixBits) / g.T) * g.nt + (int)(Tx >> kFixBits) / g.T;
+            tile = ((int)(Ty >> kFixBits) / g.Ti) * g.nti + (int)(Tx >> kFixBits) / g.Ti;
             atomicAdd(&sh_cnt[tile], 1);
         } else {
             bad = true;
@@ -867,8 +867,8 @@ int rows_per_item(int n, bool f32)
 int stage_items(const Inst &d, int stage)
 {
     switch (stage) {
-    case ST_SPREAD:
-    case ST_INTERP: return d.g.nt * d.g.nt;
+    case ST_SPREAD: return d.g.nt * d.g.nt;
+    case ST_INTERP: return d.g.nti * d.g.nti;
     case ST_ROW_FWD:
     case ST_ROW_INV: return (d.n + d.rows - 1) / d.rows;
     default: return d.M + 1;
@@ -901,9 +901,10 @@ int stage_smem(const Inst &d, int stage)
     case ST_COLUMNS: return c * d.n;
     default: {
         const int nw = (d.wdeg + 1) * W; /* interpolation stages the window only */
-        if (d.fft_df) return 8 * (T + W) * (T + W);
-        return d.f32 ? 4 * (T + W) * (T + W)
-                     : 8 * (T + W) * (T + W) + (d.win ? (int)sizeof(double) * nw : 0);
+        const int Ti = d.g.Ti;
+        if (d.fft_df) return 8 * (Ti + W) * (Ti + W);
+        return d.f32 ? 4 * (Ti + W) * (Ti + W)
+                     : 8 * (Ti + W) * (Ti + W) + (d.win ? (int)sizeof(double) * nw : 0);
     }
     }
 }
@@ -1072,7 +1073,7 @@ cudaError_t launch_prep_targets(const Geom &g, int64_t nt, const double *xt, con
                                 double2 *trg_t, float4 *trg_frac, int *trg_idx, int *err,
                                 cudaStream_t st, int *hist)
 {
-    const int ntiles = g.nt * g.nt;
+    const int ntiles = g.nti * g.nti;
     const int64_t nch = hist ? hist_chunks(nt, ntiles) : 0;
     cudaError_t e = cudaSuccess;
     if (nch > 0) {
@@ -1132,7 +1133,7 @@ cudaError_t launch_bin_targets(const Geom &g, int64_t nt, const double *xt, cons
                                double2 *trg_tmp, int *cnt, int *ptr, int *cur, double2 *trg_t,
                                int *trg_idx, int *err, cudaStream_t st)
 {
-    const int ntiles = g.nt * g.nt;
+    const int ntiles = g.nti * g.nti;
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ntiles, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(cur, 0, sizeof(int) * ntiles, st);
@@ -1277,14 +1278,14 @@ cudaError_t launch_interp_t(const Geom &g, const int *trg_ptr, const double2 *tr
 #define YK_CALL(W)                                                                              \
     e = set_smem(k_interp32<W>, smem);                                                          \
     if (e != cudaSuccess) return e;                                                             \
-    k_interp32<W><<<g.nt * g.nt, 256, smem, st>>>(d)
+    k_interp32<W><<<g.nti * g.nti, 256, smem, st>>>(d)
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     } else {
 #define YK_CALL(W)                                                                              \
     e = set_smem(k_interp<W>, smem);                                                            \
     if (e != cudaSuccess) return e;                                                             \
-    k_interp<W><<<g.nt * g.nt, 256, smem, st>>>(d)
+    k_interp<W><<<g.nti * g.nti, 256, smem, st>>>(d)
         YK_W_DISPATCH(g.w, YK_CALL)
 #undef YK_CALL
     }

@@ -918,8 +918,8 @@ template <int W> __device__ void st_interp64(const Inst &d, int item, unsigned c
 {
     double *sg = reinterpret_cast<double *>(sm);
     const Geom &g = d.g;
-    const int T = g.T, P = T + W, lo = W / 2;
-    const int tyi = item / g.nt, txi = item - tyi * g.nt;
+    const int T = g.Ti, P = T + W, lo = W / 2;
+    const int tyi = item / g.nti, txi = item - tyi * g.nti;
     const int beg = d.trg_ptr[item], end = d.trg_ptr[item + 1];
     if (beg == end) return; /* uniform across the CTA */
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;
@@ -951,8 +951,8 @@ template <int W> __device__ void st_interp32(const Inst &d, int item, unsigned c
 {
     float *sg = reinterpret_cast<float *>(sm);
     const Geom &g = d.g;
-    const int T = g.T, P = T + W, lo = W / 2;
-    const int tyi = item / g.nt, txi = item - tyi * g.nt;
+    const int T = g.Ti, P = T + W, lo = W / 2;
+    const int tyi = item / g.nti, txi = item - tyi * g.nti;
     const int beg = d.trg_ptr[item], end = d.trg_ptr[item + 1];
     if (beg == end) return;
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;
@@ -990,9 +990,9 @@ template <int W> __device__ void st_interp32(const Inst &d, int item, unsigned c
 template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned char *sm)
 {
     const Geom &g = d.g;
-    const int T = g.T, P = T + W, lo = W / 2;
+    const int T = g.Ti, P = T + W, lo = W / 2;
     df32 *sg = reinterpret_cast<df32 *>(sm);
-    const int tyi = item / g.nt, txi = item - tyi * g.nt;
+    const int tyi = item / g.nti, txi = item - tyi * g.nti;
     const int beg = d.trg_ptr[item], end = d.trg_ptr[item + 1];
     if (beg == end) return;
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;

@@ -315,6 +315,8 @@ extern "C" YK_API yk_status yk_eval_longrange_static(double alpha, const yk_opts
     g.n = (int)n;
     g.T = T;
     g.nt = nt;
+    g.Ti = T;
+    g.nti = nt;
     g.w = info.w;
     for (int k = 0; k < 4; ++k) g.box[k] = o->box[k];
 

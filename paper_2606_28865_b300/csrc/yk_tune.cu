@@ -6,9 +6,11 @@
  * cells a tile's padded copy adds, how much shared memory a CTA holds and how evenly work spreads
  * over the SMs; the spread's warps per CTA (its padded copies) and sources per batch trade
  * shared memory and registers against latency hiding; the interpolation's threads per CTA set its
- * occupancy.  yk_autotune times every admissible T with the default shape on the caller's own
- * points (CUDA events around the evaluation's kernels, through the public ABI), then, at the
- * fastest T, every spread shape and every interpolation block size (each stage timed alone), and
+ * occupancy, and the targets' tile edge (apart from T on the owner-tile paths) how often the
+ * interpolation reads a halo.  yk_autotune times every admissible T with the default shape on the
+ * caller's own points (CUDA events around the evaluation's kernels, through the public ABI), then,
+ * at the fastest T, every spread shape, every targets' tile edge and every interpolation block
+ * size (each stage timed alone), and
  * records the winners in a process-wide cache keyed by precision, window width, grid size band and
  * sources per grid cell band.  Plans created with opts.use_tuned take the admissible divisor of
  * their n nearest to the cached tile and the cached shape.  The paper has no counterpart (its
@@ -31,7 +33,7 @@ namespace {
 using Key = std::tuple<int, int, int, int>; /* precision, w, log2 n band, log2 density band */
 
 struct Shape {
-    int tile, spread_warps, spread_batch, interp_threads;
+    int tile, spread_warps, spread_batch, interp_threads, interp_tile;
 };
 
 std::mutex g_tune_mutex;
@@ -73,7 +75,7 @@ double eval_ms(const double *ms)
 
 /* launch shape recorded for a plan's key — used by yk_plan when opts.use_tuned is set */
 bool yk_tuned_shape(int precision, int w, int64_t n, int64_t n_src_hint, int *tile,
-                    int *spread_warps, int *spread_batch, int *interp_threads)
+                    int *spread_warps, int *spread_batch, int *interp_threads, int *interp_tile)
 {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tuned.find(key_of(precision, w, n, n_src_hint));
@@ -82,6 +84,7 @@ bool yk_tuned_shape(int precision, int w, int64_t n, int64_t n_src_hint, int *ti
     *spread_warps = it->second.spread_warps;
     *spread_batch = it->second.spread_batch;
     *interp_threads = it->second.interp_threads;
+    *interp_tile = it->second.interp_tile;
     return true;
 }
 
@@ -148,6 +151,7 @@ YK_API yk_status yk_autotune(double alpha, const yk_opts *o, int64_t n_src, cons
         res->best_spread_warps = di.spread_warps;
         res->best_spread_batch = di.spread_batch;
         res->best_interp_threads = di.interp_threads;
+        res->best_interp_tile = di.interp_tile;
     }
     if (owner && res->best_tile > 0) {
         /* 2. the spread's warps per CTA and sources per batch at that tile (spread time alone) */
@@ -169,9 +173,25 @@ YK_API yk_status yk_autotune(double alpha, const yk_opts *o, int64_t n_src, cons
                     res->best_spread_batch = batches[b];
                 }
             }
-        /* 3. the interpolation's threads per CTA (interpolation time alone) */
+        /* 3. the targets' tile edge, then the interpolation's threads per CTA (interpolation
+         * time alone) */
         base.spread_warps = res->best_spread_warps;
         base.spread_batch = res->best_spread_batch;
+        for (int ti = 32; ti >= info.w; --ti) {
+            if (!(n % ti == 0 && n >= 2 * ti) || ti == res->best_interp_tile) continue;
+            yk_opts oc = base;
+            oc.interp_tile = ti;
+            s = time_plan(alpha, oc, n_src, xs, ys, w, density, n_trg, xt, yt, u, ms);
+            if (s != YK_OK) {
+                cudaFree(u);
+                return s;
+            }
+            if (ms[YK_STAGE_INTERP] > 0 && ms[YK_STAGE_INTERP] < res->interp_ms) {
+                res->interp_ms = ms[YK_STAGE_INTERP];
+                res->best_interp_tile = ti;
+            }
+        }
+        base.interp_tile = res->best_interp_tile;
         for (int th : {128, 256}) {
             yk_opts oc = base;
             oc.interp_threads = th;
@@ -200,7 +220,7 @@ YK_API yk_status yk_autotune(double alpha, const yk_opts *o, int64_t n_src, cons
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         g_tuned[key_of(o->precision, info.w, n, n_src)] =
             Shape{res->best_tile, res->best_spread_warps, res->best_spread_batch,
-                  res->best_interp_threads};
+                  res->best_interp_threads, res->best_interp_tile};
     }
     return YK_OK;
 }
@@ -212,11 +232,12 @@ YK_API yk_status yk_tune_cache_save(const char *path)
     if (!f) return YK_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     std::fprintf(f, "# precision w n_band density_band tile spread_warps spread_batch "
-                    "interp_threads\n");
+                    "interp_threads interp_tile\n");
     for (const auto &kv : g_tuned)
-        std::fprintf(f, "%d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
-                     std::get<2>(kv.first), std::get<3>(kv.first), kv.second.tile,
-                     kv.second.spread_warps, kv.second.spread_batch, kv.second.interp_threads);
+        std::fprintf(f, "%d %d %d %d %d %d %d %d %d\n", std::get<0>(kv.first),
+                     std::get<1>(kv.first), std::get<2>(kv.first), std::get<3>(kv.first),
+                     kv.second.tile, kv.second.spread_warps, kv.second.spread_batch,
+                     kv.second.interp_threads, kv.second.interp_tile);
     std::fclose(f);
     return YK_OK;
 }
@@ -229,12 +250,13 @@ YK_API yk_status yk_tune_cache_load(const char *path)
     char line[256];
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     while (std::fgets(line, sizeof line, f)) {
-        int a, b, c, d, t, sw = 0, sb = 0, it = 0;
+        int a, b, c, d, t, sw = 0, sb = 0, it = 0, ti = 0;
         if (line[0] == '#') continue;
-        /* five columns (tile only) or eight (tile and launch shape; 0 = default) */
-        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d", &a, &b, &c, &d, &t, &sw,
-                                    &sb, &it);
-        if (got >= 5 && t > 0) g_tuned[Key(a, b, c, d)] = Shape{t, sw, sb, it};
+        /* five columns (tile only), eight (and the launch shape) or nine (and the targets' tile);
+         * 0 = default */
+        const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &a, &b, &c, &d, &t, &sw,
+                                    &sb, &it, &ti);
+        if (got >= 5 && t > 0) g_tuned[Key(a, b, c, d)] = Shape{t, sw, sb, it, ti};
     }
     std::fclose(f);
     return YK_OK;

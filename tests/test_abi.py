@@ -160,10 +160,12 @@ def test_tuned_tile_cache_roundtrip(tmp_path):
     yk.tune_cache_clear()
     base = yk.plan_params(10.0, 100000, 100000, delta=3.9e-5, tol=1e-10)
     n, w = base["n_grid"], base["w"]
-    # FP64 plans with double-float arithmetic use tiles of at most 32 cells
+    # FP64 plans with double-float arithmetic take tiles of at most 32 cells, by default the
+    # largest admissible one up to 24
     divisors = [t for t in range(w, 33) if n % t == 0 and n >= 2 * t]
-    assert base["tile"] == max(divisors)
-    want = min(divisors)
+    default = max(t for t in divisors if t <= 24)
+    assert base["tile"] == default
+    want = max(divisors) if max(divisors) != default else min(divisors)
     import math as _m
     dens = 100000 / (n * n)
     band = lambda v: int(_m.floor(2 * _m.log2(v) + 0.5))
@@ -174,13 +176,13 @@ def test_tuned_tile_cache_roundtrip(tmp_path):
                            n_src_hint=100000)
     assert tuned["tile"] == want and tuned["n_grid"] == n
     untuned = yk.plan_params(10.0, 100000, 100000, delta=3.9e-5, tol=1e-10)
-    assert untuned["tile"] == max(divisors)
+    assert untuned["tile"] == default
     g = tmp_path / "saved.txt"
     yk.tune_cache_save(str(g))
     assert f"{want}" in g.read_text().split("\n")[1]
     yk.tune_cache_clear()
     assert yk.plan_params(10.0, 100000, 100000, delta=3.9e-5, tol=1e-10, use_tuned=True,
-                          n_src_hint=100000)["tile"] == max(divisors)
+                          n_src_hint=100000)["tile"] == default
 
 
 def test_launch_shape_options_are_checked_and_reported():
@@ -200,3 +202,32 @@ def test_launch_shape_options_are_checked_and_reported():
         assert ei.value.status == yk.YK_ERR_ARG, bad
     with pytest.raises(yk.YkError):
         yk.plan_params(10.0, delta=0.0167, tol=1e-6, precision=yk.YK_FP32C, spread_batch=4)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+def test_targets_tile_edge_apart_from_the_spread_tile(prec, tol):
+    """The targets' tiles (binning and interpolation) take their own edge: by default the
+    largest admissible divisor of n up to 32, else the caller's; the all-FP64 path keeps one edge."""
+    import paper_2606_28865_b300 as yk
+    d = yk.plan_params(10.0, 100000, 100000, delta=3.9e-5, tol=tol, precision=prec)
+    n, w = d["n_grid"], d["w"]
+    edges = [t for t in range(w, 33) if n % t == 0 and n >= 2 * t]
+    assert d["interp_tile"] == max(edges)
+    for ti in edges:
+        e = yk.plan_params(10.0, delta=3.9e-5, tol=tol, precision=prec, interp_tile=ti)
+        assert e["interp_tile"] == ti and e["tile"] == d["tile"]
+    # the targets' tile counters are part of the predicted footprint
+    small = yk.plan_params(10.0, 0, 0, delta=3.9e-5, tol=tol, precision=prec,
+                           interp_tile=min(edges))["device_bytes"]
+    large = yk.plan_params(10.0, 0, 0, delta=3.9e-5, tol=tol, precision=prec,
+                           interp_tile=max(edges))["device_bytes"]
+    assert small > large or len(edges) == 1
+    bad = [t for t in range(w, 33) if n % t] + [33, -1]
+    for ti in bad[:3] + bad[-2:]:
+        with pytest.raises(yk.YkError) as ei:
+            yk.plan_params(10.0, delta=3.9e-5, tol=tol, precision=prec, interp_tile=ti)
+        assert ei.value.status == yk.YK_ERR_ARG, ti
+    f = yk.plan_params(10.0, delta=3.9e-5, tol=tol, fft_fp64=True)
+    assert f["interp_tile"] == f["tile"]
+    with pytest.raises(yk.YkError):
+        yk.plan_params(10.0, delta=3.9e-5, tol=tol, fft_fp64=True, interp_tile=edges[0])

@@ -58,6 +58,17 @@ def test_every_admissible_tile_and_the_tuned_plan_match_the_oracle(prec, tol):
                 p.set_points(args[0], args[1], args[2], args[4], args[5])
                 u = p.eval(args[3]).cpu().numpy()
             assert np.max(np.abs(u - ref)) <= tol * scale, (alpha, tile)
+        # every edge of the targets' tiles (apart from the spread's tile edge)
+        n, w = res["n_grid"], yk.plan_params(alpha, tol=tol, precision=prec, h_vol=wk.h_vol)["w"]
+        edges = [e for e in range(w, 33) if n % e == 0 and n >= 2 * e]
+        assert res["best_interp_tile"] in edges
+        for ti in edges:
+            with yk.Plan(alpha, tol=tol, precision=prec, h_vol=wk.h_vol, box=wk.box,
+                         interp_tile=ti) as p:
+                assert p.info["interp_tile"] == ti
+                p.set_points(args[0], args[1], args[2], args[4], args[5])
+                u = p.eval(args[3]).cpu().numpy()
+            assert np.max(np.abs(u - ref)) <= tol * scale, (alpha, ti)
         # the launch shape was searched too, and a tuned plan takes all of it
         assert 1 <= res["best_spread_warps"] <= 4 and res["best_interp_threads"] in (64, 128, 256)
         assert res["best_spread_batch"] in ((4, 8, 16) if prec == 0 else (8, 16, 32))
@@ -65,8 +76,9 @@ def test_every_admissible_tile_and_the_tuned_plan_match_the_oracle(prec, tol):
                      n_src_hint=wk.n_src) as p:
             info = p.info
             assert info["tile"] == res["best_tile"]
-            assert (info["spread_warps"], info["spread_batch"], info["interp_threads"]) == (
-                res["best_spread_warps"], res["best_spread_batch"], res["best_interp_threads"])
+            assert (info["spread_warps"], info["spread_batch"], info["interp_threads"],
+                    info["interp_tile"]) == (res["best_spread_warps"], res["best_spread_batch"],
+                                             res["best_interp_threads"], res["best_interp_tile"])
             p.set_points(args[0], args[1], args[2], args[4], args[5])
             u = p.eval(args[3]).cpu().numpy()
         assert np.max(np.abs(u - ref)) <= tol * scale, alpha
@@ -94,7 +106,8 @@ def test_tune_cache_round_trip_keeps_the_launch_shape(tmp_path):
     yk.tune_cache_load(path)
     info = yk.plan_params(wk.alpha, wk.n_src, wk.n_trg, tol=1e-10, h_vol=wk.h_vol, box=wk.box,
                           use_tuned=True, n_src_hint=wk.n_src)
-    assert (info["tile"], info["spread_warps"], info["spread_batch"], info["interp_threads"]) == (
-        res["best_tile"], res["best_spread_warps"], res["best_spread_batch"],
-        res["best_interp_threads"])
+    assert (info["tile"], info["spread_warps"], info["spread_batch"], info["interp_threads"],
+            info["interp_tile"]) == (res["best_tile"], res["best_spread_warps"],
+                                     res["best_spread_batch"], res["best_interp_threads"],
+                                     res["best_interp_tile"])
     yk.tune_cache_clear()
