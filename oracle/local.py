@@ -1,4 +1,5 @@
-"""Oracle for the single-layer local asymptotic part S_{L,A} — TEST INFRASTRUCTURE ONLY.
+"""Oracle for the local asymptotic parts S_{L,A}, D_{L,A} and V_L and the dyadic corrections —
+TEST INFRASTRUCTURE ONLY.
 
 S_{L,A}[sigma](x) = int_0^{delta*} int_{boundary} H(t, x - x') sigma(x') ds dt, H the heat kernel of
 (-Lap + alpha^2) (Section 2.1, eq. sla), evaluated by the asymptotic expansion of Section 4.1
@@ -68,6 +69,18 @@ class StarfishGeom:
         g2 = np.array([r2 * c - 2 * r1 * s - r * c, r2 * s + 2 * r1 * c - r * s])
         return g, g1, g2
 
+    def derivs4(self, t):
+        """gamma and its first four derivatives at parameter t (Leibniz on r(t) e(t), e = (cos t,
+        sin t), whose derivatives cycle e, e_perp, -e, -e_perp)."""
+        a, m, ph = self.a, self.m, self.ph
+        ph_t = m * t + ph
+        rk = [self.r0 + a * np.cos(ph_t), -a * m * np.sin(ph_t), -a * m ** 2 * np.cos(ph_t),
+              a * m ** 3 * np.sin(ph_t), a * m ** 4 * np.cos(ph_t)]
+        c, s = np.cos(t), np.sin(t)
+        ek = [np.array([c, s]), np.array([-s, c]), np.array([-c, -s]), np.array([s, -c]),
+              np.array([c, s])]
+        return [sum(math.comb(k, j) * rk[j] * ek[k - j] for j in range(k + 1)) for k in range(5)]
+
     def closest(self, x, y, n_scan=4096, iters=60):
         """Parameter of the closest boundary point: best of a dense scan, then Newton on
         f(t) = (gamma(t) - x) . gamma'(t) = 0 with f' = |gamma'|^2 + (gamma - x) . gamma''."""
@@ -108,6 +121,115 @@ def starfish_density(t):
     """sigma = cos 3t + 0.5 sin t (the workloads' boundary density) and its t-derivatives."""
     return (np.cos(3 * t) + 0.5 * np.sin(t), -3 * np.sin(3 * t) + 0.5 * np.cos(t),
             -9 * np.cos(3 * t) - 0.5 * np.sin(t))
+
+
+def starfish_density4(t):
+    """the same density and its first four t-derivatives"""
+    return (np.cos(3 * t) + 0.5 * np.sin(t), -3 * np.sin(3 * t) + 0.5 * np.cos(t),
+            -9 * np.cos(3 * t) - 0.5 * np.sin(t), 27 * np.sin(3 * t) - 0.5 * np.cos(t),
+            81 * np.cos(3 * t) + 0.5 * np.sin(t))
+
+
+# ------------------------------------------------------------------------------------------------
+# Double-layer local part D_{L,A}[mu](x) = int_0^{delta*} int_boundary dH_t(x - x')/dnu' mu(x')
+# ds dt (Section 2.1, eq. dla), by the expansion of the double-layer lemma (Section 4.1,
+# eq. dlp_local1) through its delta*^2 term, at the closest boundary point x0.
+#
+# Readings:
+# * the normal derivative is taken in the source point, as for the history part D_H:
+#   dH_t(x - x')/dnu' = nu' . (x - x') H_t(x - x') / (2t), positive along nu'.  The printed
+#   expansion has the opposite overall sign: its leading term -rho mu0 U0 / 4 is, for a straight
+#   boundary and constant mu, the value of a derivative in the target.  Every term is taken with
+#   its sign reversed.
+# * P_m, Q_m, Z (with its factor c2), rho and kappa0 as in the single-layer lemma; U_m = c1^m Phi_+.
+# * the delta*^{3/2} bracket prints (5 kappa0^3 mu0/64 - mu0 gamma0''''/32)(3 Q0 - U_3).  Expanding
+#   eq. dla as the lemma's proof describes (z = sqrt(4t), xi = u z, Gaussian moments in u) gives
+#   every printed term but this one: the kappa0^3 part multiplies (3 Q0 - U_3), the gamma0''''
+#   part (3 Q0 + P_2).  The two agree at c1 = 0, so the corollary (eq. dlp_local2) is unchanged;
+#   the circle and starfish pins converge at the lemma's order only with (3 Q0 + P_2).
+# * mu0', mu0'', mu0^(4) and gamma0^(3), gamma0^(4) are derivatives in the tangent-line parameter
+#   xi at x0, gamma the boundary graph in the frame (tangent, outward normal nu0); they follow
+#   from the curve-parameter derivatives through the inverse of xi(t) = (gamma(t) - x0) . tangent.
+# * a target within 1e-10 sqrt(delta*) of the boundary is on it: rho = 0, and the value is the
+#   corollary's (eq. dlp_local2), the integral at the boundary point itself; any other target
+#   carries the layer's jump through the U_0 term (+-mu0/2 as r -> 0).
+# tests/test_oracle_pins_dla.py fixes these against eq. dla (straight boundary, circle, starfish).
+# ------------------------------------------------------------------------------------------------
+
+def dla_lemma_terms(alpha, dstar, r, rho, kappa0, mu0, mu1, mu2, mu4, g3, g4):
+    """The expansion of the double-layer lemma (eq. dlp_local1) through the delta*^2 term, with
+    the overall sign of the source-point normal derivative, vectorised."""
+    r, rho, kappa0, mu0, mu1, mu2, mu4, g3, g4 = map(
+        np.asarray, (r, rho, kappa0, mu0, mu1, mu2, mu4, g3, g4))
+    sd = math.sqrt(dstar)
+    c1 = r / sd
+    c2 = alpha * sd
+    em = np.exp(-c1 * c2) * sp.erfc(c1 / 2 - c2)
+    ep = np.exp(c1 * c2) * sp.erfc(c1 / 2 + c2)
+    phi_m, phi_p = em - ep, em + ep
+    Z = 4.0 * c2 * np.exp(-c1 * c1 / 4 - c2 * c2) / math.sqrt(math.pi)
+    P = [phi_m / c2]
+    for _ in range(3):
+        P.append(c1 * P[-1])
+    Q0 = (phi_m - Z) / c2 ** 3 + c1 * phi_p / c2 ** 2
+    Q1 = c1 * Q0
+    U = [phi_p]
+    for _ in range(4):
+        U.append(c1 * U[-1])
+    k = kappa0
+    printed = (-rho * mu0 / 4 * U[0]
+               - sd * k * mu0 / 8 * (P[0] + U[1])
+               - dstar * (rho * mu2 / 8 * P[1] + 3 * rho * k ** 2 * mu0 / 32 * (P[1] + U[2]))
+               + dstar * sd * (5 * k ** 3 * mu0 / 64 * (3 * Q0 - U[3])
+                               - mu0 * g4 / 32 * (3 * Q0 + P[2])
+                               + 3 * k * mu2 / 16 * (-Q0 - P[2])
+                               + mu1 * g3 / 8 * (-2 * Q0 - P[2]))
+               + dstar ** 2 * (35 * rho * k ** 4 * mu0 / 512 * (9 * Q1 + 2 * P[3] - U[4])
+                               - rho * mu4 / 32 * Q1
+                               - 15 * rho * k ** 2 * mu2 / 64 * (Q1 + P[3]))
+               - dstar ** 2 * (5 * rho * k * mu1 * g3 / 16 * (2 * Q1 + P[3])
+                               + (5 * rho * k * mu0 * g4 / 64 + 5 * rho * mu0 * g3 ** 2 / 96)
+                               * (3 * Q1 + P[3])))
+    return -printed
+
+
+def tangent_line_derivs(xi, f):
+    """Derivatives of F(xi) = f(t(xi)) at x0 from xi_k = d^k xi / dt^k (k = 1..4) and f_k = d^k f
+    / dt^k (k = 1..4), xi(t) = (gamma(t) - x0) . tangent (chain rule with the inverse function
+    t(xi): t' = 1/xi1, t'' = -xi2/xi1^3, ...).  Returns [F', F'', F''', F'''']."""
+    x1, x2, x3, x4 = xi
+    f1, f2, f3, f4 = f
+    t1 = 1.0 / x1
+    t2 = -x2 / x1 ** 3
+    t3 = (3 * x2 ** 2 - x1 * x3) / x1 ** 5
+    t4 = (-15 * x2 ** 3 + 10 * x1 * x2 * x3 - x1 ** 2 * x4) / x1 ** 7
+    return [f1 * t1,
+            f2 * t1 ** 2 + f1 * t2,
+            f3 * t1 ** 3 + 3 * f2 * t1 * t2 + f1 * t3,
+            f4 * t1 ** 4 + 6 * f3 * t1 ** 2 * t2 + f2 * (3 * t2 ** 2 + 4 * t1 * t3) + f1 * t4]
+
+
+def dla_local_starfish(alpha, dstar, geom: StarfishGeom, mu4, xt, yt):
+    """D_{L,A}[mu] at the targets for the analytic starfish; mu4(t) -> mu and its first four
+    t-derivatives.  Targets beyond the locality radius get 0."""
+    xt, yt = np.atleast_1d(xt).astype(float), np.atleast_1d(yt).astype(float)
+    t = geom.closest(xt, yt)
+    g = geom.derivs4(t)
+    sp_ = np.hypot(g[1][0], g[1][1])
+    tx, ty = g[1][0] / sp_, g[1][1] / sp_              # tangent
+    nux, nuy = ty, -tx                                  # outward normal (counter-clockwise)
+    xi = [g[k][0] * tx + g[k][1] * ty for k in range(1, 5)]
+    eta = [g[k][0] * nux + g[k][1] * nuy for k in range(1, 5)]
+    G = tangent_line_derivs(xi, eta)                    # G[0] = 0 at x0
+    kappa0, g3, g4 = G[1], G[2], G[3]
+    m = mu4(t)
+    M = tangent_line_derivs(xi, m[1:])
+    dx, dy = xt - g[0][0], yt - g[0][1]
+    r = np.hypot(dx, dy)
+    side = dx * nux + dy * nuy
+    rho = np.where(r <= 1e-10 * math.sqrt(dstar), 0.0, np.where(side >= 0.0, 1.0, -1.0))
+    u = dla_lemma_terms(alpha, dstar, r, rho, kappa0, m[0], M[0], M[1], M[3], g3, g4)
+    return np.where(r < locality_radius(alpha, dstar), u, 0.0)
 
 
 # ------------------------------------------------------------------------------------------------
