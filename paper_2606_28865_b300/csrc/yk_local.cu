@@ -343,6 +343,7 @@ __device__ bool closest_point(const PanelSet &P, double x, double y, int c, int6
     const double ox = P.xb[p * q + h] - x, oy = P.yb[p * q + h] - y;
     const double *const c2[2] = {P.cx + p * q, P.cy + p * q};
     double td = t;
+    bool last = false;
     for (int it = 0; it < 8; ++it) {
         double g[2], g1[2], g2[2];
         legendre_eval<double, 2>(c2, q, td, g, g1, g2, c_la, c_lb);
@@ -353,10 +354,12 @@ __device__ bool closest_point(const PanelSet &P, double x, double y, int c, int6
         if (!(fabs(dt) < 4.0)) dt = dt > 0.0 ? 4.0 : -4.0;
         td = fmin(fmax(td - dt, -3.0), 3.0);
         /* quadratic convergence: after a step of size dt the error is ~ C dt^2 with
-         * C = f'' / (2 f') well below 1e2 within the locality radius, so |dt| < 1e-6 leaves t
-         * within ~1e-10 of the root; r is stationary in t, and sigma0, kappa0 move by that
-         * fraction of their panel-parameter derivatives (the parity tests hold at 1e-10) */
-        if (fabs(dt) < 1e-6) break;
+         * C = f'' / (2 f').  f' = |gamma'|^2 (1 - d kappa) shrinks for targets at distance d
+         * near a concave stretch's radius of curvature 1 / |kappa|, which the locality radius
+         * may approach, so C has no useful bound there: once |dt| < 1e-6, one more step is
+         * taken, after which the error is ~ C (C 1e-12)^2, below 1e-16 for C up to 1e4 */
+        if (last) break;
+        last = fabs(dt) < 1e-6;
     }
     pout = p;
     tout = td;

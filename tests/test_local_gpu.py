@@ -61,6 +61,33 @@ def test_slp_local_matches_oracle(n_panels, alpha, dstar, off):
     assert err <= TOL, f"err={err:.3e}"
 
 
+def test_slp_local_outside_concave_tips_at_the_locality_radius():
+    """Targets outside the starfish opposite its concave stretches (radius of curvature ~0.072),
+    at 0.3 .. 0.97 of a locality radius of ~0.071: there f' of the closest-point Newton,
+    |gamma'|^2 (1 - d kappa), nearly vanishes and its quadratic constant is large, so the
+    stopping rule must not leave t short of the root (Section 3.2, closest point; Section 4.1,
+    Lemma)."""
+    alpha, dstar = 10.0, 3.45e-5
+    rl = OL.locality_radius(alpha, dstar)
+    g = OL.StarfishGeom()
+    rng = np.random.default_rng(17)
+    n = 2000
+    t = np.pi / 5 + 2 * np.pi * rng.integers(0, 5, n) / 5 + rng.uniform(-0.02, 0.02, n)
+    p, d1, _ = g.derivs(t)
+    nrm = np.hypot(d1[0], d1[1])
+    d = rng.uniform(0.3, 0.97, n) * rl
+    xt, yt = p[0] + d * d1[1] / nrm, p[1] - d * d1[0] / nrm      # outward
+    # the stretch is concave (the lemma's kappa0 > 0: the boundary bends towards the outward
+    # normal), its centre of curvature outside, within 10% of the locality radius
+    _, d1v, d2v = g.derivs(np.array([np.pi / 5]))
+    kappa = -(d1v[0] * d2v[1] - d1v[1] * d2v[0]) / np.hypot(d1v[0], d1v[1]) ** 3
+    assert kappa[0] > 0 and 0.9 * rl < 1 / kappa[0] < 1.1 * rl
+    u = run(128, alpha, dstar, xt, yt)
+    ref = OL.slp_local_starfish(alpha, dstar, g, OL.starfish_density, xt, yt)
+    err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+    assert err <= TOL, f"err={err:.3e}"
+
+
 def test_slp_local_far_targets_are_zero():
     alpha, dstar = 10.0, 1e-5
     rl = OL.locality_radius(alpha, dstar)
