@@ -760,6 +760,24 @@ def main():
                  "n_targets": int(xt_l.numel()), "targets_within_locality": near,
                  "what": "yk_slp_local: panel series, cell lists, closest point, lemma terms"}
 
+    # double-layer local asymptotic part D_{L,A} at the same targets, boundary and delta*
+    dlocal = None
+    if not args.no_local:
+        udla = torch.empty_like(xt_l)
+        for _ in range(2):
+            yk.dlp_local(a_loc, dstar, *lb, xt_l, yt_l, q=16, out=udla, stream=lanes[a_loc])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            yk.dlp_local(a_loc, dstar, *lb, xt_l, yt_l, q=16, out=udla, stream=lanes[a_loc])
+        ms_dla = (time.perf_counter() - t0) / reps * 1e3
+        dlocal = {"value": (len(xb) + xt_l.numel()) / (ms_dla * 1e-3), "unit": "points/s",
+                  "ms": ms_dla, "alpha": a_loc, "delta_star": dstar, "n_boundary": len(xb),
+                  "n_targets": int(xt_l.numel()),
+                  "targets_within_locality": int((udla != 0).sum().item()),
+                  "what": "yk_dlp_local: as yk_slp_local, with the curve's and the density's "
+                          "first four derivatives at the closest point"}
+
     # volume local part V_L at the volume nodes strictly inside the curve (the cut-cell nodes by
     # concave chords may lie just outside it), delta* = the plan's delta, same boundary
     vlocal = None
@@ -857,6 +875,7 @@ def main():
         "fp32c": fp32c,
         "double_layer": dlp,
         "slp_local": local,
+        "dlp_local": dlocal,
         "vp_local": vlocal,
         "slp_dyadic": dyadic,
         "batch": batch,

@@ -222,9 +222,38 @@ YK_API yk_status yk_eval_longrange_dl(yk_plan_t p, const double *density, const 
  *  - Readings of the printed lemma: Z = 4 c2 exp(-c1^2/4 - c2^2)/sqrt(pi) (the printed Z lacks the
  *    factor c2); kappa0 is the boundary's curvature in the (tangent, outward normal) frame, i.e.
  *    negative on a convex piece; rho = sign((x - x0) . nu0).
+ *  - The boundary's derivatives at x0 come from the panel's polynomial; on a panel shorter than
+ *    0.01 of the boundary's extent (where differentiating the rounded nodes would amplify their
+ *    rounding) those of order >= 2 come from a least-squares polynomial fit over the nodes of
+ *    the neighbouring panels within about that length, in the frame of the panel's middle node.
  */
 YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_t n_panels, int q,
                               const double *xb, const double *yb, const double *sigma,
+                              int64_t n_trg, const double *xt, const double *yt, double *u,
+                              void *stream);
+
+/*
+ * yk_dlp_local: the double-layer local asymptotic part D_{L,A}[mu](x_i) = int_0^{delta_star}
+ * int_boundary dH(t, x_i - x')/dnu' mu(x') ds dt (Section 2.1, eq. dla) by the expansion of
+ * Section 4.1 (the double-layer lemma, eq. dlp_local1) through its delta_star^2 term, at the
+ * closest boundary point found as for yk_slp_local.  The normal derivative is taken in the source
+ * point, nu' the outward normal (the convention of yk_eval_longrange_dl's dipoles), so that with
+ * the history part at the same delta it gives D = D_{L,A} + D_H up to O(delta_star^{5/2}).
+ *  - Arguments, memory, scratch, stream and errors as yk_slp_local, with mu (n_panels * q, at
+ *    the nodes) in place of sigma.
+ *  - u_i = D_{L,A} at target i, 0 beyond the locality radius.  A target within
+ *    1e-10 sqrt(delta_star) of the boundary is on it: u_i is the integral at that boundary point
+ *    (the corollary, eq. dlp_local2); any other target within the radius carries the double
+ *    layer's jump (u -> +-mu0/2 plus the corollary's value as the target approaches the boundary
+ *    from outside / inside).
+ *  - Readings of the printed lemma: its overall sign is that of a derivative in the target and is
+ *    reversed here; the gamma'''' part of the delta_star^{3/2} bracket multiplies 3 Q0 + P2 (the
+ *    expansion of eq. dla; the printed 3 Q0 - U3 holds for the kappa0^3 part, and both agree on the
+ *    boundary); mu', mu'', mu'''' and gamma''', gamma'''' are derivatives in the tangent-line
+ *    parameter at x0, taken from the panel's polynomial; Z, kappa0 and rho as for yk_slp_local.
+ */
+YK_API yk_status yk_dlp_local(double alpha, double delta_star, int64_t n_panels, int q,
+                              const double *xb, const double *yb, const double *mu,
                               int64_t n_trg, const double *xt, const double *yt, double *u,
                               void *stream);
 

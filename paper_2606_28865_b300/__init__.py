@@ -428,6 +428,28 @@ def slp_local(alpha, delta_star, xb, yb, sigma, xt, yt, q=16, out=None, stream=N
     return out
 
 
+_lib.yk_dlp_local.argtypes = list(_lib.yk_slp_local.argtypes)
+_lib.yk_dlp_local.restype = ctypes.c_int
+
+
+def dlp_local(alpha, delta_star, xb, yb, mu, xt, yt, q=16, out=None, stream=None):
+    """Double-layer local asymptotic part at the targets (device float64 tensors); the boundary
+    as panels of q Gauss-Legendre nodes, counter-clockwise (see yk_dlp_local)."""
+    torch = _torch()
+    nb, nt = _len(xb), _len(xt)
+    if nb % q or _len(yb) != nb or _len(mu) != nb or _len(yt) != nt:
+        raise ValueError("boundary arrays must hold n_panels * q values; target lengths differ")
+    if out is None:
+        out = torch.empty(nt, dtype=torch.float64, device=xt.device)
+    if stream is None:
+        stream = _current_stream()
+    keep = []
+    _check(_lib.yk_dlp_local(float(alpha), float(delta_star), nb // q, int(q), _ptr(xb, keep),
+                             _ptr(yb, keep), _ptr(mu, keep), nt, _ptr(xt, keep),
+                             _ptr(yt, keep), _out_ptr(out, keep), stream), "yk_dlp_local")
+    return out
+
+
 _lib.yk_slp_dyadic.argtypes = [_d, _d, ctypes.c_int, _i64, ctypes.c_int, _vp, _vp, _vp, _i64,
                                _vp, _vp, _vp, _vp]
 _lib.yk_slp_dyadic.restype = ctypes.c_int

@@ -273,6 +273,7 @@ struct PanelSet {
     const float *cxf, *cyf, *xbf, *ybf, *xmf, *ymf; /* FP32 copies for the search */
     const double *tq;                 /* Gauss-Legendre nodes */
     const int *ptr, *list;            /* panels listed per cell */
+    const double *wide;               /* window fits of short panels (k_panel_wide), or NULL */
 };
 
 /* Closest boundary point of (x, y), the target's cell c listing at least one panel: panel p and
@@ -366,6 +367,202 @@ __device__ bool closest_point(const PanelSet &P, double x, double y, int c, int6
     return true;
 }
 
+/* ----------------------------------------------------------------------------------------- */
+/* the boundary's derivatives at the closest point on short panels                            */
+
+/* Orders 2 to 4 of the curve's and the density's derivatives come from the panel's own
+ * degree-(q-1) series, whose coefficients carry the node rounding (~1e-16 of |x|, not of the
+ * panel's span): its k-th derivative amplifies that by ~(2/h)^k q^(2k) on a panel of length h,
+ * ~1e-6 of the curvature and nothing usable of the fourth derivative on 1e-3-long panels.  A
+ * panel shorter than the window W (0.01 of the boundary's extent) therefore also gets a
+ * least-squares fit over the nodes of its 2k + 1 neighbouring panels (covering ~W) in the frame
+ * of its middle node: the boundary graph eta(xi) and the density mu(xi), Legendre series of
+ * degree kWideDeg in xi / S (S the largest |xi| of the window's nodes).  The kernels take the
+ * derivatives of order >= 2 from it where it exists.  Layout per panel: k (0: no fit), S,
+ * tangent (2), eta's coefficients, mu's coefficients. */
+constexpr int kWideDeg = 10;
+constexpr int kWideN = kWideDeg + 1;
+constexpr int kWideStride = 4 + 2 * kWideN;
+
+/* value and first four derivatives of NS Legendre series (coefficients c[s][0..n)) at t, with
+ * P'''_{m+1} = P'''_{m-1} + (2m+1) P''_m and P''''_{m+1} = P''''_{m-1} + (2m+1) P'''_m as in
+ * legendre_eval */
+template <int NS>
+__device__ __forceinline__ void legendre_eval4(const double *const (&c)[NS], int n, double t,
+                                               double (&f)[5][NS])
+{
+    double p[5][2] = {{1.0, t}, {0.0, 1.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        f[0][s] = c[s][0] + c[s][1] * t;
+        f[1][s] = c[s][1];
+        f[2][s] = f[3][s] = f[4][s] = 0.0;
+    }
+    for (int m = 1; m + 1 < n; ++m) {
+        const double k = (double)(2 * m + 1);
+        double nx[5];
+        nx[0] = c_la[m] * t * p[0][1] - c_lb[m] * p[0][0];
+#pragma unroll
+        for (int d = 1; d < 5; ++d) nx[d] = p[d][0] + k * p[d - 1][1];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const double cn = c[s][m + 1];
+#pragma unroll
+            for (int d = 0; d < 5; ++d) f[d][s] += cn * nx[d];
+        }
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+            p[d][0] = p[d][1];
+            p[d][1] = nx[d];
+        }
+    }
+}
+
+/* derivatives in the tangent-line parameter xi of F(xi) = f(t(xi)) from the parameter
+ * derivatives of f and of xi(t) = (gamma(t) - x0) . tangent (inverse-function chain rule):
+ * out[k] = d^(k+1) F / dxi^(k+1), k = 0..3 */
+__device__ __forceinline__ void tangent_line(const double (&xi)[4], const double (&f)[4],
+                                             double (&out)[4])
+{
+    const double x1 = xi[0], x2 = xi[1], x3 = xi[2], x4 = xi[3];
+    const double i1 = 1.0 / x1, i2 = i1 * i1;
+    const double t1 = i1, t2 = -x2 * i2 * i1;
+    const double t3 = (3.0 * x2 * x2 - x1 * x3) * i2 * i2 * i1;
+    const double t4 = (-15.0 * x2 * x2 * x2 + 10.0 * x1 * x2 * x3 - x1 * x1 * x4) * i2 * i2 * i2 * i1;
+    out[0] = f[0] * t1;
+    out[1] = f[1] * t1 * t1 + f[0] * t2;
+    out[2] = f[2] * t1 * t1 * t1 + 3.0 * f[1] * t1 * t2 + f[0] * t3;
+    out[3] = f[3] * t1 * t1 * t1 * t1 + 6.0 * f[2] * t1 * t1 * t2 +
+             f[1] * (3.0 * t2 * t2 + 4.0 * t1 * t3) + f[0] * t4;
+}
+
+/* one thread per panel: the window fit described above (k = 0 for panels at least W long) */
+__global__ void k_panel_wide(int64_t npan, int q, const double *__restrict__ xb,
+                             const double *__restrict__ yb, const double *__restrict__ sg,
+                             const double *__restrict__ cx, const double *__restrict__ cy,
+                             const double *__restrict__ tq, double W, double *__restrict__ wide)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npan) return;
+    double *o = wide + p * kWideStride;
+    /* panel length from its end nodes' chord, scaled from the nodes' span to [-1, 1] */
+    const double h = hypot(xb[p * q + q - 1] - xb[p * q], yb[p * q + q - 1] - yb[p * q]) * 2.0 /
+                     (tq[q - 1] - tq[0]);
+    /* neighbours on each side (a degenerate panel, h = 0, gives the cap) */
+    const double kk = fmin(h < W ? ceil(0.5 * (W / h - 1.0)) : 0.0, (double)(npan / 8));
+    const int k = (int)kk;
+    o[0] = (double)k;
+    if (k <= 0) return;
+    const int64_t m = p * q + q / 2;
+    const double *const c2[2] = {cx + p * q, cy + p * q};
+    double g[2], g1[2], g2[2];
+    legendre_eval<double, 2>(c2, q, tq[q / 2], g, g1, g2, c_la, c_lb);
+    const double st = sqrt(g1[0] * g1[0] + g1[1] * g1[1]);
+    const double tx = g1[0] / st, ty = g1[1] / st;
+    const double xm = xb[m], ym = yb[m], sm = sg[m];
+    double S = 0.0;
+    for (int j = -k; j <= k; ++j) {
+        const int64_t pp = (p + j + npan) % npan;
+        for (int a = 0; a < q; ++a)
+            S = fmax(S, fabs((xb[pp * q + a] - xm) * tx + (yb[pp * q + a] - ym) * ty));
+    }
+    /* normal equations in the Legendre basis of s = xi / S (upper triangle), two right sides */
+    double A[kWideN][kWideN], be[kWideN], bm[kWideN];
+    for (int i = 0; i < kWideN; ++i) {
+        be[i] = bm[i] = 0.0;
+        for (int j = 0; j < kWideN; ++j) A[i][j] = 0.0;
+    }
+    for (int j = -k; j <= k; ++j) {
+        const int64_t pp = (p + j + npan) % npan;
+        for (int a = 0; a < q; ++a) {
+            const double dx = xb[pp * q + a] - xm, dy = yb[pp * q + a] - ym;
+            const double s = (dx * tx + dy * ty) / S, eta = dx * ty - dy * tx;
+            const double mu = sg[pp * q + a] - sm;
+            double P[kWideN];
+            P[0] = 1.0;
+            P[1] = s;
+            for (int n = 1; n + 1 < kWideN; ++n) P[n + 1] = c_la[n] * s * P[n] - c_lb[n] * P[n - 1];
+            for (int i = 0; i < kWideN; ++i) {
+                be[i] += P[i] * eta;
+                bm[i] += P[i] * mu;
+                for (int j2 = i; j2 < kWideN; ++j2) A[i][j2] += P[i] * P[j2];
+            }
+        }
+    }
+    /* Cholesky A = L L^T in place (lower triangle), then two triangular solves per side */
+    for (int j = 0; j < kWideN; ++j) {
+        double d = A[j][j];
+        for (int l = 0; l < j; ++l) d -= A[j][l] * A[j][l];
+        d = sqrt(fmax(d, 1e-300));
+        A[j][j] = d;
+        for (int i = j + 1; i < kWideN; ++i) {
+            double v = A[j][i];
+            for (int l = 0; l < j; ++l) v -= A[i][l] * A[j][l];
+            A[i][j] = v / d;
+        }
+    }
+    for (int i = 0; i < kWideN; ++i) {
+        for (int l = 0; l < i; ++l) {
+            be[i] -= A[i][l] * be[l];
+            bm[i] -= A[i][l] * bm[l];
+        }
+        be[i] /= A[i][i];
+        bm[i] /= A[i][i];
+    }
+    for (int i = kWideN - 1; i >= 0; --i) {
+        for (int l = i + 1; l < kWideN; ++l) {
+            be[i] -= A[l][i] * be[l];
+            bm[i] -= A[l][i] * bm[l];
+        }
+        be[i] /= A[i][i];
+        bm[i] /= A[i][i];
+    }
+    o[1] = S;
+    o[2] = tx;
+    o[3] = ty;
+    for (int i = 0; i < kWideN; ++i) {
+        o[4 + i] = be[i];
+        o[4 + kWideN + i] = bm[i];
+    }
+}
+
+/* tangent-line derivatives at the point x0 = (middle node) + (dx0, dy0) of panel p from its
+ * window fit: G[k] = d^(k+1) gamma / dxi^(k+1) of the boundary graph in the frame (tangent,
+ * outward normal) at x0 (G[0] = 0, G[1] = kappa0), M[k] the density's; false where the panel
+ * has no fit (its own series serves) */
+__device__ bool wide_derivs(const PanelSet &P, int64_t p, double dx0, double dy0,
+                            double (&G)[4], double (&M)[4])
+{
+    if (!P.wide) return false;
+    const double *o = P.wide + p * kWideStride;
+    if (!(o[0] > 0.0)) return false;
+    const double S = o[1], tx = o[2], ty = o[3];
+    const double s0 = (dx0 * tx + dy0 * ty) / S;
+    const double *const c[2] = {o + 4, o + 4 + kWideN};
+    double f[5][2];
+    legendre_eval4<2>(c, kWideN, s0, f);
+    /* the curve (xi, eta(xi)) of the middle node's frame with xi as its parameter: derivatives
+     * (1, e1), (0, e_k); at x0 its unit tangent T = (1, e1)/n1 and outward normal (-e1, 1)/n1 */
+    double e[5], mu[4];
+    double sc = 1.0;
+    for (int d = 1; d < 5; ++d) {
+        sc /= S;
+        e[d] = f[d][0] * sc;
+        mu[d - 1] = f[d][1] * sc;
+    }
+    const double n1 = sqrt(1.0 + e[1] * e[1]);
+    double xi[4], eta[4];
+    xi[0] = n1;
+    eta[0] = 0.0;
+    for (int d = 2; d < 5; ++d) {
+        xi[d - 1] = e[d] * e[1] / n1;
+        eta[d - 1] = e[d] / n1;
+    }
+    tangent_line(xi, eta, G);
+    tangent_line(xi, mu, M);
+    return true;
+}
+
 /* S_{L,A}: one thread per near target, the targets grouped by cell (a warp scans one cell's
  * panel list) */
 __global__ void __launch_bounds__(128) k_slp_local(int n_near, const int *__restrict__ order,
@@ -397,10 +594,105 @@ __global__ void __launch_bounds__(128) k_slp_local(int n_near, const int *__rest
     double val = 0.0;
     if (r < rl) {
         const double rho = dx * nux + dy * nuy >= 0.0 ? 1.0 : -1.0;
-        const double kappa0 = -(g1[0] * g2[1] - g1[1] * g2[0]) / (st * st * st);
+        double kappa0 = -(g1[0] * g2[1] - g1[1] * g2[0]) / (st * st * st);
         const double stt = (g1[0] * g2[0] + g1[1] * g2[1]) / st;
-        const double s0pp = (s2 - s1 * stt / st) / (st * st);
+        double s0pp = (s2 - s1 * stt / st) / (st * st);
+        double Gw[4], Mw[4];
+        if (wide_derivs(P, p, g[0], g[1], Gw, Mw)) { /* short panel: the window fit */
+            kappa0 = Gw[1];
+            s0pp = Mw[1];
+        }
         val = lemma_terms(alpha, dstar, r, rho, kappa0, s, s0pp);
+    }
+    u[i] = val;
+}
+
+/* the double-layer lemma's expansion (eq. dlp_local1) through the delta*^2 term, with the sign
+ * of the source-point normal derivative (the history part's convention: the printed expansion
+ * is the negative of this), and with the gamma'''' part of the delta*^{3/2} bracket multiplying
+ * 3 Q0 + P2 (expanding eq. dla gives that factor; the printed 3 Q0 - U3 belongs to the kappa0^3
+ * part only, and both agree on the boundary) */
+__device__ double dla_lemma_terms(double alpha, double dstar, double r, double rho, double k,
+                                  double mu0, double mu1, double mu2, double mu4, double g3,
+                                  double g4)
+{
+    const double sd = sqrt(dstar), c1 = r / sd, c2 = alpha * sd;
+    const double em = exp(-c1 * c2) * erfc(0.5 * c1 - c2);
+    const double ep = exp(c1 * c2) * erfc(0.5 * c1 + c2);
+    const double phm = em - ep, php = em + ep;
+    const double Z = 4.0 * c2 * exp(-0.25 * c1 * c1 - c2 * c2) * 0.56418958354775628695; /* 1/sqrt(pi) */
+    const double P0 = phm / c2, P1 = c1 * P0, P2 = c1 * P1, P3 = c1 * P2;
+    const double Q0 = (phm - Z) / (c2 * c2 * c2) + c1 * php / (c2 * c2), Q1 = c1 * Q0;
+    const double U0 = php, U1 = c1 * U0, U2 = c1 * U1, U3 = c1 * U2, U4 = c1 * U3;
+    const double k2 = k * k;
+    const double t0 = rho * mu0 * 0.25 * U0;
+    const double t1 = sd * k * mu0 * 0.125 * (P0 + U1);
+    const double t2 = dstar * rho * (mu2 * 0.125 * P1 + 3.0 / 32.0 * k2 * mu0 * (P1 + U2));
+    const double t3 = dstar * sd *
+                      (5.0 / 64.0 * k2 * k * mu0 * (3.0 * Q0 - U3) -
+                       mu0 * g4 / 32.0 * (3.0 * Q0 + P2) - 3.0 / 16.0 * k * mu2 * (Q0 + P2) -
+                       mu1 * g3 * 0.125 * (2.0 * Q0 + P2));
+    const double t4 = dstar * dstar * rho *
+                      (35.0 / 512.0 * k2 * k2 * mu0 * (9.0 * Q1 + 2.0 * P3 - U4) -
+                       mu4 / 32.0 * Q1 - 15.0 / 64.0 * k2 * mu2 * (Q1 + P3) -
+                       5.0 / 16.0 * k * mu1 * g3 * (2.0 * Q1 + P3) -
+                       (5.0 / 64.0 * k * mu0 * g4 + 5.0 / 96.0 * mu0 * g3 * g3) * (3.0 * Q1 + P3));
+    return t0 + t1 + t2 - t3 - t4;
+}
+
+/* D_{L,A}: one thread per near target, as k_slp_local; the curve's and the density's first four
+ * derivatives at the closest point come from the panel's Legendre series and are turned into
+ * tangent-line derivatives (kappa0 = gamma'', gamma''', gamma'''' of the boundary graph in the
+ * frame (tangent, outward normal); mu', mu'', mu'''').  A target within 1e-10 sqrt(delta*) of the
+ * boundary is on it (rho = 0: the corollary's value, eq. dlp_local2); elsewhere rho = +-1 and the
+ * value carries the layer's jump. */
+__global__ void __launch_bounds__(128) k_dla_local(int n_near, const int *__restrict__ order,
+                                                   const int *__restrict__ tcell,
+                                                   const double *__restrict__ xt,
+                                                   const double *__restrict__ yt, PanelSet P,
+                                                   double alpha, double dstar, double rl,
+                                                   double *__restrict__ u)
+{
+    const int e0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e0 >= n_near) return;
+    const int i = order[e0];
+    const double x = xt[i], y = yt[i];
+    int64_t p;
+    double td;
+    if (!closest_point(P, x, y, tcell[i], p, td)) {
+        u[i] = 0.0;
+        return;
+    }
+    const int q = P.q, h = q / 2;
+    const double *const c3[3] = {P.cx + p * q, P.cy + p * q, P.cs + p * q};
+    double f[5][3];
+    legendre_eval4<3>(c3, q, td, f);
+    const double st = sqrt(f[1][0] * f[1][0] + f[1][1] * f[1][1]);
+    const double tx = f[1][0] / st, ty = f[1][1] / st;
+    const double nux = ty, nuy = -tx; /* outward (counter-clockwise) */
+    const double dx = (x - P.xb[p * q + h]) - f[0][0], dy = (y - P.yb[p * q + h]) - f[0][1];
+    const double r = sqrt(dx * dx + dy * dy);
+    double val = 0.0;
+    if (r < rl) {
+        double xi[4], eta[4], mt[4], G[4], M[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            xi[d] = f[d + 1][0] * tx + f[d + 1][1] * ty;
+            eta[d] = f[d + 1][0] * nux + f[d + 1][1] * nuy;
+            mt[d] = f[d + 1][2];
+        }
+        tangent_line(xi, eta, G);
+        tangent_line(xi, mt, M);
+        double Gw[4], Mw[4];
+        if (wide_derivs(P, p, f[0][0], f[0][1], Gw, Mw)) /* short panel: orders >= 2 */
+            for (int d = 1; d < 4; ++d) {
+                G[d] = Gw[d];
+                M[d] = Mw[d];
+            }
+        const double side = dx * nux + dy * nuy;
+        const double rho = r <= 1e-10 * sqrt(dstar) ? 0.0 : (side >= 0.0 ? 1.0 : -1.0);
+        const double mu0 = f[0][2] + P.sref[p * q + h];
+        val = dla_lemma_terms(alpha, dstar, r, rho, G[1], mu0, M[0], M[1], M[3], G[2], G[3]);
     }
     u[i] = val;
 }
@@ -529,7 +821,9 @@ __global__ void __launch_bounds__(128) k_vp_local(int n_near, const int *__restr
         atomicAdd(nout, 1);
         return;
     }
-    const double kappa0 = (g1[0] * g2[1] - g1[1] * g2[0]) / (st * st * st);
+    double kappa0 = (g1[0] * g2[1] - g1[1] * g2[0]) / (st * st * st);
+    double Gw[4], Mw[4];
+    if (wide_derivs(P, p, g[0], g[1], Gw, Mw)) kappa0 = -Gw[1]; /* short panel: the window fit */
     const double f = fd[i], fx = fd[nt + i], fy = fd[2 * nt + i];
     const double fxx = fd[3 * nt + i], fxy = fd[4 * nt + i], fyy = fd[5 * nt + i];
     const double f_eta = fx * ex + fy * ey;
@@ -912,11 +1206,12 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
     int *d_cnt = nullptr, *d_ptr = nullptr, *d_cur = nullptr, *d_list = nullptr;
     int *d_tcell = nullptr, *d_tcnt = nullptr, *d_tptr = nullptr, *d_order = nullptr;
     int *d_nout = nullptr;
+    double *d_wide = nullptr;
     /* scratch is stream-ordered (no device-wide synchronisation on free) */
     auto cleanup = [&]() {
         for (void *b : {(void *)d_tq, (void *)d_c, (void *)d_cf, (void *)d_cnt, (void *)d_ptr,
                         (void *)d_cur, (void *)d_list, (void *)d_tcell, (void *)d_tcnt,
-                        (void *)d_tptr, (void *)d_order, (void *)d_nout})
+                        (void *)d_tptr, (void *)d_order, (void *)d_nout, (void *)d_wide})
             if (b) cudaFreeAsync(b, st);
         cudaStreamSynchronize(st);
     };
@@ -927,6 +1222,8 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
     if (e == cudaSuccess) e = cudaMallocAsync(&d_ptr, sizeof(int) * (ncell + 1), st);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_cur, sizeof(int) * ncell, st);
     if (e == cudaSuccess) e = cudaMallocAsync(&d_nout, sizeof(int), st);
+    if (e == cudaSuccess && J == 0)
+        e = cudaMallocAsync(&d_wide, sizeof(double) * kWideStride * n_panels, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_nout, 0, sizeof(int), st);
     if (e != cudaSuccess) {
         cleanup();
@@ -940,6 +1237,10 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
     if (e == cudaSuccess) {
         k_panel_series<<<(int)((nb + 255) / 256), 256, 0, st>>>(
             n_panels, q, xb, yb, sigma, d_tq + q, cx, cy, cs, cxf, cyf, xbf, ybf, xmf, ymf);
+        if (J == 0) /* window fits of panels shorter than 0.01 of the boundary's extent */
+            k_panel_wide<<<(int)((n_panels + 127) / 128), 128, 0, st>>>(
+                n_panels, q, xb, yb, sigma, cx, cy, d_tq,
+                0.01 * std::fmax(xmax - xmin, ymax - ymin), d_wide);
         e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * ncell, st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cur, 0, sizeof(int) * ncell, st);
@@ -1003,11 +1304,15 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
     P.tq = d_tq;
     P.ptr = d_ptr;
     P.list = d_list;
+    P.wide = d_wide;
     if (e == cudaSuccess && n_near > 0) {
         const int nb2 = (n_near + 127) / 128;
         if (vol)
             k_vp_local<<<nb2, 128, 0, st>>>(n_near, d_order, d_tcell, xt, yt, n_trg, fd, P, alpha,
                                             delta_star, rl, u, d_nout);
+        else if (J == 0 && dl)
+            k_dla_local<<<nb2, 128, 0, st>>>(n_near, d_order, d_tcell, xt, yt, P, alpha,
+                                             delta_star, rl, u);
         else if (J == 0)
             k_slp_local<<<nb2, 128, 0, st>>>(n_near, d_order, d_tcell, xt, yt, P, alpha,
                                              delta_star, rl, u);
@@ -1147,6 +1452,16 @@ extern "C" YK_API yk_status yk_slp_local(double alpha, double delta_star, int64_
     if (!sigma) return lfail(YK_ERR_ARG, "yk_slp_local: sigma is NULL");
     return run_local("yk_slp_local", false, 0, false, alpha, delta_star, n_panels, q, xb, yb, sigma, n_trg, xt, yt,
                      nullptr, u, stream);
+}
+
+extern "C" YK_API yk_status yk_dlp_local(double alpha, double delta_star, int64_t n_panels, int q,
+                                         const double *xb, const double *yb, const double *mu,
+                                         int64_t n_trg, const double *xt, const double *yt,
+                                         double *u, void *stream)
+{
+    if (!mu) return lfail(YK_ERR_ARG, "yk_dlp_local: mu is NULL");
+    return run_local("yk_dlp_local", false, 0, true, alpha, delta_star, n_panels, q, xb, yb, mu,
+                     n_trg, xt, yt, nullptr, u, stream);
 }
 
 extern "C" YK_API yk_status yk_vp_local(double alpha, double delta_star, int64_t n_panels, int q,

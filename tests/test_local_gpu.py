@@ -103,12 +103,13 @@ def test_slp_local_far_targets_are_zero():
     assert np.all(u == 0.0)
 
 
-# On very short panels the curvature is ill-conditioned in the node data: the FP64 rounding of the
-# node coordinates (1e-16 of |x| ~ 1), differentiated twice by the 16-point interpolant near a
-# panel end, puts ~1e-6 of relative error into kappa0 on the 6,250-panel boundary (panels of 1e-3
-# arc length); the kappa0 term is at most ~4% of S_{L,A} (at the concave tips), hence 1e-8 there —
-# still 20 times below the lemma's own O(delta*^{3/2}) truncation (~2e-7 at this delta*).
-TOL_SHORT_PANELS = 1e-8
+# On very short panels (the 6,250-panel boundary: 1e-3 of arc length) a panel's own series carries
+# the node rounding (1e-16 of |x| ~ 1) amplified by differentiation (~1e-6 of the curvature, the
+# fourth derivative lost); the kernels take the derivatives of order >= 2 there from a
+# least-squares fit over the neighbouring panels' nodes (a window of 0.01 of the boundary's
+# extent), which keeps them to ~1e-11 (curvature) and ~1e-4 (fourth derivatives): the bar is the
+# same as for coarse panels.
+TOL_SHORT_PANELS = TOL
 
 
 @pytest.mark.slow
@@ -121,7 +122,9 @@ def test_slp_local_config_two_boundary():
     xt, yt = near_targets(20000, 0.5 * rl, seed=9)
     u = run(6250, alpha, dstar, xt, yt)
     ref = OL.slp_local_starfish(alpha, dstar, OL.StarfishGeom(), OL.starfish_density, xt, yt)
-    assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) <= TOL_SHORT_PANELS
+    err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+    print(f"slp 6250 panels err={err:.3e}")
+    assert err <= TOL_SHORT_PANELS
 
 
 def test_slp_local_arguments():
@@ -132,6 +135,106 @@ def test_slp_local_arguments():
     assert ei.value.status == yk.YK_ERR_ARG
     with pytest.raises(ValueError):
         yk.slp_local(1.0, 1e-4, x, x, x, dev(np.zeros(3)), dev(np.zeros(3)), q=5)
+
+
+# ------------------------------------------------------------------------------------------------
+# double-layer local part D_{L,A} (the double-layer lemma, eq. dlp_local1, through delta*^2; the
+# oracle's readings: source-point normal derivative, the gamma^(4) factor 3 Q0 + P2)
+
+def run_dla(n_panels, alpha, dstar, xt, yt):
+    yk = _yk()
+    curve = W.Starfish()
+    xb, yb, _, tb = W.boundary_nodes(curve, n_panels, 16)
+    mu = W.boundary_density(tb)
+    u = yk.dlp_local(alpha, dstar, dev(xb), dev(yb), dev(mu), dev(xt), dev(yt), q=16)
+    torch.cuda.synchronize()
+    return u.cpu().numpy()
+
+
+@pytest.mark.parametrize("n_panels,alpha,dstar,off", [(32, 10.0, 1e-4, 0.03), (32, 1.0, 1e-5, 0.03),
+                                                      (32, 100.0, 1e-5, 0.02), (128, 10.0, 1e-5, 0.03)])
+def test_dla_local_matches_oracle(n_panels, alpha, dstar, off):
+    rl = OL.locality_radius(alpha, dstar)
+    xt, yt = near_targets(3000, min(off, 0.95 * rl), seed=5)
+    u = run_dla(n_panels, alpha, dstar, xt, yt)
+    ref = OL.dla_local_starfish(alpha, dstar, OL.StarfishGeom(), OL.starfish_density4, xt, yt)
+    err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+    assert err <= TOL, f"err={err:.3e}"
+
+
+# At the concave stretches (curvature 13.9, its peak ~0.03 wide in the curve parameter) the
+# 128-panel interpolant's third and fourth derivatives carry the node rounding amplified by the
+# differentiation (~2e-8 and ~1e-5 absolute in the curve parameter, reproduced in numpy from the
+# rounded nodes alone): the lemma from those derivatives differs from the analytic curve's by
+# ~1.2e-11, 1.5e-9 of the largest |D| of targets at 0.3 .. 0.97 of the locality radius (<= 8e-3).
+TOL_CONCAVE_DLA = 3e-9
+
+
+def test_dla_local_concave_tips_and_far_targets():
+    """Outside the concave stretches up to 0.97 of the locality radius (as for S_{L,A}), and
+    targets just beyond the radius or far away (zero)."""
+    alpha, dstar = 10.0, 3.45e-5
+    rl = OL.locality_radius(alpha, dstar)
+    g = OL.StarfishGeom()
+    rng = np.random.default_rng(23)
+    n = 2000
+    t = np.pi / 5 + 2 * np.pi * rng.integers(0, 5, n) / 5 + rng.uniform(-0.02, 0.02, n)
+    p, d1, _ = g.derivs(t)
+    nrm = np.hypot(d1[0], d1[1])
+    d = rng.uniform(0.3, 0.97, n) * rl
+    xt, yt = p[0] + d * d1[1] / nrm, p[1] - d * d1[0] / nrm
+    u = run_dla(128, alpha, dstar, xt, yt)
+    ref = OL.dla_local_starfish(alpha, dstar, g, OL.starfish_density4, xt, yt)
+    assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) <= TOL_CONCAVE_DLA
+    s = rng.choice([-1.0, 1.0], 500) * 1.05 * rl
+    tf = rng.uniform(0, 2 * np.pi, 500)
+    p, d1, _ = g.derivs(tf)
+    nrm = np.hypot(d1[0], d1[1])
+    xf = np.concatenate([p[0] + s * d1[1] / nrm, [2.5, -3.0, 0.0]])
+    yf = np.concatenate([p[1] - s * d1[0] / nrm, [0.0, 1.0, 0.0]])
+    assert np.all(run_dla(32, alpha, dstar, xf, yf) == 0.0)
+
+
+def test_dla_local_jump_across_the_boundary():
+    """The double layer's jump (the lemma's U_0 term): just outside minus just inside is mu0, and
+    a target on the boundary takes the mean of the two (the corollary's value)."""
+    alpha, dstar = 10.0, 1e-4
+    g = OL.StarfishGeom()
+    t = np.linspace(0.05, 2 * np.pi - 0.05, 400)
+    p, d1, _ = g.derivs(t)
+    nrm = np.hypot(d1[0], d1[1])
+    eps = 1e-8 * math.sqrt(dstar)
+    xo, yo = p[0] + eps * d1[1] / nrm, p[1] - eps * d1[0] / nrm
+    xi, yi = p[0] - eps * d1[1] / nrm, p[1] + eps * d1[0] / nrm
+    uo, ui, ub = (run_dla(128, alpha, dstar, x, y) for x, y in ((xo, yo), (xi, yi), (p[0], p[1])))
+    mu0 = W.boundary_density(t)
+    assert np.max(np.abs(uo - ui - mu0)) <= 1e-7 * np.max(np.abs(mu0))   # O(eps / sqrt(ds))
+    assert np.max(np.abs(ub - 0.5 * (uo + ui))) <= 1e-7 * np.max(np.abs(mu0))
+
+
+@pytest.mark.slow
+def test_dla_local_config_two_boundary():
+    # the bench's boundary: 6,250 panels x 16 nodes (derivatives from the window fits)
+    alpha = 10.0
+    import oracle.params as OP
+    dstar = OP.delta_from_mesh(alpha, 0.004467)
+    rl = OL.locality_radius(alpha, dstar)
+    xt, yt = near_targets(20000, 0.5 * rl, seed=9)
+    u = run_dla(6250, alpha, dstar, xt, yt)
+    ref = OL.dla_local_starfish(alpha, dstar, OL.StarfishGeom(), OL.starfish_density4, xt, yt)
+    err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+    print(f"dla 6250 panels err={err:.3e}")
+    assert err <= TOL_SHORT_PANELS
+
+
+def test_dla_local_arguments():
+    yk = _yk()
+    x = dev(np.zeros(32))
+    with pytest.raises(yk.YkError) as ei:
+        yk.dlp_local(1.0, -1e-4, x, x, x, dev(np.zeros(3)), dev(np.zeros(3)), q=16)
+    assert ei.value.status == yk.YK_ERR_ARG
+    with pytest.raises(ValueError):
+        yk.dlp_local(1.0, 1e-4, x, x, x, dev(np.zeros(3)), dev(np.zeros(3)), q=5)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -216,7 +319,9 @@ def test_vp_local_config_two_boundary():
     xt, yt = inside_targets(20000, rl, seed=10)
     u = run_vp(6250, alpha, dstar, xt, yt)
     ref = OL.vp_local_starfish(alpha, dstar, OL.StarfishGeom(), OL.sincos_field(), xt, yt)
-    assert np.max(np.abs(u - ref)) / np.max(np.abs(ref)) <= TOL_SHORT_PANELS
+    err = np.max(np.abs(u - ref)) / np.max(np.abs(ref))
+    print(f"vp 6250 panels err={err:.3e}")
+    assert err <= TOL_SHORT_PANELS
 
 
 def test_vp_local_arguments():
