@@ -223,7 +223,7 @@ YK_API yk_status yk_eval_longrange_dl(yk_plan_t p, const double *density, const 
  *    factor c2); kappa0 is the boundary's curvature in the (tangent, outward normal) frame, i.e.
  *    negative on a convex piece; rho = sign((x - x0) . nu0).
  *  - The boundary's derivatives at x0 come from the panel's polynomial; on a panel shorter than
- *    0.01 of the boundary's extent (where differentiating the rounded nodes would amplify their
+ *    0.006 of the boundary's extent (where differentiating the rounded nodes would amplify their
  *    rounding) those of order >= 2 come from a least-squares polynomial fit over the nodes of
  *    the neighbouring panels within about that length, in the frame of the panel's middle node.
  */

@@ -374,13 +374,13 @@ __device__ bool closest_point(const PanelSet &P, double x, double y, int c, int6
  * degree-(q-1) series, whose coefficients carry the node rounding (~1e-16 of |x|, not of the
  * panel's span): its k-th derivative amplifies that by ~(2/h)^k q^(2k) on a panel of length h,
  * ~1e-6 of the curvature and nothing usable of the fourth derivative on 1e-3-long panels.  A
- * panel shorter than the window W (0.01 of the boundary's extent) therefore also gets a
+ * panel shorter than the window W (0.006 of the boundary's extent) therefore also gets a
  * least-squares fit over the nodes of its 2k + 1 neighbouring panels (covering ~W) in the frame
  * of its middle node: the boundary graph eta(xi) and the density mu(xi), Legendre series of
  * degree kWideDeg in xi / S (S the largest |xi| of the window's nodes).  The kernels take the
  * derivatives of order >= 2 from it where it exists.  Layout per panel: k (0: no fit), S,
  * tangent (2), eta's coefficients, mu's coefficients. */
-constexpr int kWideDeg = 10;
+constexpr int kWideDeg = 8;
 constexpr int kWideN = kWideDeg + 1;
 constexpr int kWideStride = 4 + 2 * kWideN;
 
@@ -436,90 +436,144 @@ __device__ __forceinline__ void tangent_line(const double (&xi)[4], const double
              f[1] * (3.0 * t2 * t2 + 4.0 * t1 * t3) + f[0] * t4;
 }
 
-/* one thread per panel: the window fit described above (k = 0 for panels at least W long) */
-__global__ void k_panel_wide(int64_t npan, int q, const double *__restrict__ xb,
-                             const double *__restrict__ yb, const double *__restrict__ sg,
-                             const double *__restrict__ cx, const double *__restrict__ cy,
-                             const double *__restrict__ tq, double W, double *__restrict__ wide)
+/* Window fit, part 1: one warp per panel (k = 0 for panels at least W long).  The lanes stride
+ * over the window's samples, each accumulating its share of the normal equations (the Gram
+ * matrix's upper triangle and two right sides) in registers; the shares are summed through
+ * shared memory (each lane adds up two of the kWideSys columns) and written to gram[p]. */
+constexpr int kWideGram = kWideN * (kWideN + 1) / 2;
+constexpr int kWideSys = kWideGram + 2 * kWideN; /* Gram entries, then the two right sides */
+constexpr int kWideSamples = 64;
+
+__global__ void __launch_bounds__(64) k_panel_wide(int64_t npan, int q,
+                                                    const double *__restrict__ xb,
+                                                    const double *__restrict__ yb,
+                                                    const double *__restrict__ sg,
+                                                    const double *__restrict__ tq, double W,
+                                                    double *__restrict__ wide,
+                                                    double *__restrict__ gram)
+{
+    __shared__ double sh[2][32][kWideSys + 1]; /* per warp; the odd row length spreads banks */
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
+    if (p >= npan) return; /* warp-uniform; no block-wide barrier follows */
+    double *o = wide + p * kWideStride;
+    /* panel length from its end nodes' chord, scaled from the nodes' span to [-1, 1]; neighbours
+     * on each side (a degenerate panel, h = 0, gives the cap) */
+    const double h = hypot(xb[p * q + q - 1] - xb[p * q], yb[p * q + q - 1] - yb[p * q]) * 2.0 /
+                     (tq[q - 1] - tq[0]);
+    const double kk = fmin(h < W ? ceil(0.5 * (W / h - 1.0)) : 0.0, (double)(npan / 8));
+    const int k = (int)kk;
+    if (lane == 0) o[0] = (double)k;
+    if (k <= 0) return;
+    /* the frame: origin at the middle node, xi along the chord of the panel's end nodes (any
+     * direction over which the short stretch is a graph serves: the derivatives at x0 are taken
+     * in x0's own tangent-line parameter afterwards) */
+    const int64_t m = p * q + q / 2;
+    const double cxe = xb[p * q + q - 1] - xb[p * q], cye = yb[p * q + q - 1] - yb[p * q];
+    const double ce = sqrt(cxe * cxe + cye * cye);
+    const double tx = cxe / ce, ty = cye / ce;
+    const double xm = xb[m], ym = yb[m], sm = sg[m];
+    /* the window's nodes, or an even subsample of kWideSamples of them (the fit's noise grows
+     * only as the square root of the thinning) */
+    const int nn = (2 * k + 1) * q, ns = min(nn, kWideSamples);
+    auto node = [&](int j) { /* j-th sample of the window, panel p - k first */
+        const int jj = (int)(((int64_t)j * nn) / ns), jp = jj / q;
+        int64_t pp = p - k + jp;
+        pp += pp < 0 ? npan : (pp >= npan ? -npan : 0);
+        return pp * q + (jj - jp * q);
+    };
+    /* the window spans a short, nearly straight stretch: its largest |xi| is at an end sample */
+    double S = 0.0;
+    if (lane < 2) {
+        const int64_t v = node(lane ? ns - 1 : 0);
+        S = fabs((xb[v] - xm) * tx + (yb[v] - ym) * ty);
+    }
+    S = fmax(__shfl_sync(0xffffffffu, S, 0), __shfl_sync(0xffffffffu, S, 1));
+    double acc[kWideSys];
+#pragma unroll
+    for (int i = 0; i < kWideSys; ++i) acc[i] = 0.0;
+    for (int j = lane; j < ns; j += 32) {
+        const int64_t v = node(j);
+        const double dx = xb[v] - xm, dy = yb[v] - ym;
+        const double s = (dx * tx + dy * ty) / S, eta = dx * ty - dy * tx, mu = sg[v] - sm;
+        double P[kWideN];
+        P[0] = 1.0;
+        P[1] = s;
+#pragma unroll
+        for (int n = 1; n + 1 < kWideN; ++n) P[n + 1] = c_la[n] * s * P[n] - c_lb[n] * P[n - 1];
+        int a = 0;
+#pragma unroll
+        for (int i = 0; i < kWideN; ++i)
+#pragma unroll
+            for (int j2 = i; j2 < kWideN; ++j2) acc[a++] += P[i] * P[j2];
+#pragma unroll
+        for (int i = 0; i < kWideN; ++i) {
+            acc[kWideGram + i] += P[i] * eta;
+            acc[kWideGram + kWideN + i] += P[i] * mu;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kWideSys; ++i) sh[wrp][lane][i] = acc[i];
+    __syncwarp();
+    for (int c = lane; c < kWideSys; c += 32) {
+        double v = 0.0;
+        for (int l = 0; l < 32; ++l) v += sh[wrp][l][c];
+        gram[p * kWideSys + c] = v;
+    }
+    if (lane == 0) {
+        o[1] = S;
+        o[2] = tx;
+        o[3] = ty;
+    }
+}
+
+/* Window fit, part 2: one thread per panel solves its system by Cholesky (the factor in a
+ * square array) and two triangular solves per right side, writing the series' coefficients */
+__global__ void k_panel_wide_solve(int64_t npan, const double *__restrict__ gram,
+                                   double *__restrict__ wide)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npan) return;
     double *o = wide + p * kWideStride;
-    /* panel length from its end nodes' chord, scaled from the nodes' span to [-1, 1] */
-    const double h = hypot(xb[p * q + q - 1] - xb[p * q], yb[p * q + q - 1] - yb[p * q]) * 2.0 /
-                     (tq[q - 1] - tq[0]);
-    /* neighbours on each side (a degenerate panel, h = 0, gives the cap) */
-    const double kk = fmin(h < W ? ceil(0.5 * (W / h - 1.0)) : 0.0, (double)(npan / 8));
-    const int k = (int)kk;
-    o[0] = (double)k;
-    if (k <= 0) return;
-    const int64_t m = p * q + q / 2;
-    const double *const c2[2] = {cx + p * q, cy + p * q};
-    double g[2], g1[2], g2[2];
-    legendre_eval<double, 2>(c2, q, tq[q / 2], g, g1, g2, c_la, c_lb);
-    const double st = sqrt(g1[0] * g1[0] + g1[1] * g1[1]);
-    const double tx = g1[0] / st, ty = g1[1] / st;
-    const double xm = xb[m], ym = yb[m], sm = sg[m];
-    double S = 0.0;
-    for (int j = -k; j <= k; ++j) {
-        const int64_t pp = (p + j + npan) % npan;
-        for (int a = 0; a < q; ++a)
-            S = fmax(S, fabs((xb[pp * q + a] - xm) * tx + (yb[pp * q + a] - ym) * ty));
-    }
-    /* normal equations in the Legendre basis of s = xi / S (upper triangle), two right sides */
-    double A[kWideN][kWideN], be[kWideN], bm[kWideN];
-    for (int i = 0; i < kWideN; ++i) {
-        be[i] = bm[i] = 0.0;
-        for (int j = 0; j < kWideN; ++j) A[i][j] = 0.0;
-    }
-    for (int j = -k; j <= k; ++j) {
-        const int64_t pp = (p + j + npan) % npan;
-        for (int a = 0; a < q; ++a) {
-            const double dx = xb[pp * q + a] - xm, dy = yb[pp * q + a] - ym;
-            const double s = (dx * tx + dy * ty) / S, eta = dx * ty - dy * tx;
-            const double mu = sg[pp * q + a] - sm;
-            double P[kWideN];
-            P[0] = 1.0;
-            P[1] = s;
-            for (int n = 1; n + 1 < kWideN; ++n) P[n + 1] = c_la[n] * s * P[n] - c_lb[n] * P[n - 1];
-            for (int i = 0; i < kWideN; ++i) {
-                be[i] += P[i] * eta;
-                bm[i] += P[i] * mu;
-                for (int j2 = i; j2 < kWideN; ++j2) A[i][j2] += P[i] * P[j2];
-            }
+    if (!(o[0] > 0.0)) return;
+    const double *G = gram + p * kWideSys;
+    double L[kWideN][kWideN], be[kWideN], bm[kWideN];
+    {
+        int a = 0;
+        for (int i = 0; i < kWideN; ++i)
+            for (int j2 = i; j2 < kWideN; ++j2) L[j2][i] = G[a++]; /* lower triangle holds A */
+        for (int i = 0; i < kWideN; ++i) {
+            be[i] = G[kWideGram + i];
+            bm[i] = G[kWideGram + kWideN + i];
         }
     }
-    /* Cholesky A = L L^T in place (lower triangle), then two triangular solves per side */
     for (int j = 0; j < kWideN; ++j) {
-        double d = A[j][j];
-        for (int l = 0; l < j; ++l) d -= A[j][l] * A[j][l];
+        double d = L[j][j];
+        for (int l = 0; l < j; ++l) d -= L[j][l] * L[j][l];
         d = sqrt(fmax(d, 1e-300));
-        A[j][j] = d;
+        L[j][j] = d;
         for (int i = j + 1; i < kWideN; ++i) {
-            double v = A[j][i];
-            for (int l = 0; l < j; ++l) v -= A[i][l] * A[j][l];
-            A[i][j] = v / d;
+            double v = L[i][j];
+            for (int l = 0; l < j; ++l) v -= L[i][l] * L[j][l];
+            L[i][j] = v / d;
         }
     }
     for (int i = 0; i < kWideN; ++i) {
         for (int l = 0; l < i; ++l) {
-            be[i] -= A[i][l] * be[l];
-            bm[i] -= A[i][l] * bm[l];
+            be[i] -= L[i][l] * be[l];
+            bm[i] -= L[i][l] * bm[l];
         }
-        be[i] /= A[i][i];
-        bm[i] /= A[i][i];
+        be[i] /= L[i][i];
+        bm[i] /= L[i][i];
     }
     for (int i = kWideN - 1; i >= 0; --i) {
         for (int l = i + 1; l < kWideN; ++l) {
-            be[i] -= A[l][i] * be[l];
-            bm[i] -= A[l][i] * bm[l];
+            be[i] -= L[l][i] * be[l];
+            bm[i] -= L[l][i] * bm[l];
         }
-        be[i] /= A[i][i];
-        bm[i] /= A[i][i];
+        be[i] /= L[i][i];
+        bm[i] /= L[i][i];
     }
-    o[1] = S;
-    o[2] = tx;
-    o[3] = ty;
     for (int i = 0; i < kWideN; ++i) {
         o[4 + i] = be[i];
         o[4 + kWideN + i] = bm[i];
@@ -1206,12 +1260,13 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
     int *d_cnt = nullptr, *d_ptr = nullptr, *d_cur = nullptr, *d_list = nullptr;
     int *d_tcell = nullptr, *d_tcnt = nullptr, *d_tptr = nullptr, *d_order = nullptr;
     int *d_nout = nullptr;
-    double *d_wide = nullptr;
+    double *d_wide = nullptr, *d_wgram = nullptr;
     /* scratch is stream-ordered (no device-wide synchronisation on free) */
     auto cleanup = [&]() {
         for (void *b : {(void *)d_tq, (void *)d_c, (void *)d_cf, (void *)d_cnt, (void *)d_ptr,
                         (void *)d_cur, (void *)d_list, (void *)d_tcell, (void *)d_tcnt,
-                        (void *)d_tptr, (void *)d_order, (void *)d_nout, (void *)d_wide})
+                        (void *)d_tptr, (void *)d_order, (void *)d_nout, (void *)d_wide,
+                        (void *)d_wgram})
             if (b) cudaFreeAsync(b, st);
         cudaStreamSynchronize(st);
     };
@@ -1224,6 +1279,8 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
     if (e == cudaSuccess) e = cudaMallocAsync(&d_nout, sizeof(int), st);
     if (e == cudaSuccess && J == 0)
         e = cudaMallocAsync(&d_wide, sizeof(double) * kWideStride * n_panels, st);
+    if (e == cudaSuccess && J == 0)
+        e = cudaMallocAsync(&d_wgram, sizeof(double) * kWideSys * n_panels, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_nout, 0, sizeof(int), st);
     if (e != cudaSuccess) {
         cleanup();
@@ -1237,10 +1294,14 @@ yk_status run_local(const char *name, bool vol, int J, bool dl, double alpha, do
     if (e == cudaSuccess) {
         k_panel_series<<<(int)((nb + 255) / 256), 256, 0, st>>>(
             n_panels, q, xb, yb, sigma, d_tq + q, cx, cy, cs, cxf, cyf, xbf, ybf, xmf, ymf);
-        if (J == 0) /* window fits of panels shorter than 0.01 of the boundary's extent */
-            k_panel_wide<<<(int)((n_panels + 127) / 128), 128, 0, st>>>(
-                n_panels, q, xb, yb, sigma, cx, cy, d_tq,
-                0.01 * std::fmax(xmax - xmin, ymax - ymin), d_wide);
+        if (J == 0) /* window fits of panels shorter than 0.006 of the boundary's extent */
+        {
+            k_panel_wide<<<(int)((n_panels + 1) / 2), 64, 0, st>>>(
+                n_panels, q, xb, yb, sigma, d_tq,
+                0.006 * std::fmax(xmax - xmin, ymax - ymin), d_wide, d_wgram);
+            k_panel_wide_solve<<<(int)((n_panels + 127) / 128), 128, 0, st>>>(n_panels, d_wgram,
+                                                                              d_wide);
+        }
         e = cudaMemsetAsync(d_cnt, 0, sizeof(int) * ncell, st);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cur, 0, sizeof(int) * ncell, st);

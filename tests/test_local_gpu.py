@@ -106,7 +106,7 @@ def test_slp_local_far_targets_are_zero():
 # On very short panels (the 6,250-panel boundary: 1e-3 of arc length) a panel's own series carries
 # the node rounding (1e-16 of |x| ~ 1) amplified by differentiation (~1e-6 of the curvature, the
 # fourth derivative lost); the kernels take the derivatives of order >= 2 there from a
-# least-squares fit over the neighbouring panels' nodes (a window of 0.01 of the boundary's
+# least-squares fit over the neighbouring panels' nodes (a window of 0.006 of the boundary's
 # extent), which keeps them to ~1e-11 (curvature) and ~1e-4 (fourth derivatives): the bar is the
 # same as for coarse panels.
 TOL_SHORT_PANELS = TOL
