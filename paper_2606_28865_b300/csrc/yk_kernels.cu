@@ -587,38 +587,59 @@ __global__ void k_order_fill(const int *__restrict__ ptr, int ntiles, int *__res
     if (v) order[off] = t;
 }
 
-/* Shared-memory layout of the window tables in the window kernel: piece h's coefficient k of tap
- * a at h S + k WE + a, with WE = W rounded up to even (so a tap pair is one aligned 16-byte
- * load) and the piece stride S = (deg + 1) WE padded to an odd number of 16-byte slots: the lanes
- * of a warp read random pieces, and an odd stride spreads them over all bank groups instead of a
- * few. */
-/* a row holds the W taps padded with zeros to 4 ceil(W / 4) (the window kernel's four lanes per
- * point read ceil(W / 4) taps each); the piece stride is made odd in 8-byte words so the pieces
- * that lanes read spread over the banks */
+/* Shared-memory layout of the window tables in the window kernel.  Per piece, the coefficients
+ * of order <= 2 as double-float pairs and those of order >= 3 as FP32 values: over a piece (1/64
+ * of a cell) the window's k-th coefficient is at most 4e-3, 2.3e-5, 7.3e-8, 2.6e-10 of its peak
+ * for k = 1..4 at w = 12, so the orders >= 3 carry ~1e-7 of the value and an FP32 rounding of
+ * them costs ~1e-14, far below the tables' own ~1e-13.  A row holds the W taps padded with zeros
+ * to 4 ceil(W / 4) (the kernel's four lanes per point read ceil(W / 4) taps each); the piece
+ * strides are odd in words, so the pieces that the lanes of a warp read spread over the banks. */
 __host__ __device__ constexpr int win_row(int W) { return 4 * ((W + 3) / 4); }
-__host__ __device__ constexpr int win_piece_stride(int W, int D) { return (D + 1) * win_row(W) + 1; }
+/* coefficients of orders 0 .. min(D, 2) (double-float) and 3 .. D (FP32) */
+__host__ __device__ constexpr int win_ndf(int D) { return (D < 2 ? D : 2) + 1; }
+__host__ __device__ constexpr int win_nf(int D) { return D < 3 ? 0 : D - 2; }
+__host__ __device__ constexpr int win_stride_df(int W, int D) { return win_ndf(D) * win_row(W) + 1; }
+__host__ __device__ constexpr int win_stride_f(int W, int D) { return win_nf(D) * win_row(W) + 1; }
 
-/* TPL window values (taps a0 .. a0 + TPL - 1) of one coordinate by Horner in double-float on the
- * piece's polynomials (compile-time degree D; the lane's taps interleaved: TPL independent
- * chains); each step c_k + p x is one fused double-float multiply-add (exact product terms added
- * to c_k by two-sum).  Taps past the window (a >= W) read the zero pad of the row. */
+/* TPL window values (taps a0 .. a0 + TPL - 1) of one coordinate by Horner on the piece's
+ * polynomials (compile-time degree D; the lane's taps interleaved: TPL independent chains): the
+ * orders >= 3 in FP32 with the argument's high word, then c_2 + q x, c_1 + p x and c_0 + p x as
+ * fused double-float multiply-adds (exact product terms added to c_k by two-sum).  Taps past the
+ * window (a >= W) read the zero pad of the row. */
 template <int TPL, int D, int WE>
-__device__ __forceinline__ void windows_taps(const df32 *c, int a0, df32 x, df32 (&p)[TPL])
+__device__ __forceinline__ void windows_taps(const df32 *c, const float *cf, int a0, df32 x,
+                                             df32 (&p)[TPL])
 {
+    if (D >= 3) {
+        float q[TPL];
 #pragma unroll
-    for (int j = 0; j < TPL; ++j) p[j] = c[D * WE + a0 + j];
+        for (int j = 0; j < TPL; ++j) q[j] = cf[(D - 3) * WE + a0 + j];
 #pragma unroll
-    for (int k = D - 1; k >= 0; --k)
+        for (int k = D - 1; k >= 3; --k)
 #pragma unroll
-        for (int j = 0; j < TPL; ++j) p[j] = df_mul_add(c[k * WE + a0 + j], p[j], x);
+            for (int j = 0; j < TPL; ++j) q[j] = fmaf(q[j], x.hi, cf[(k - 3) * WE + a0 + j]);
+#pragma unroll
+        for (int j = 0; j < TPL; ++j) p[j] = df_mul_add(c[2 * WE + a0 + j], df32(q[j], 0.0f), x);
+#pragma unroll
+        for (int k = 1; k >= 0; --k)
+#pragma unroll
+            for (int j = 0; j < TPL; ++j) p[j] = df_mul_add(c[k * WE + a0 + j], p[j], x);
+    } else {
+#pragma unroll
+        for (int j = 0; j < TPL; ++j) p[j] = c[D * WE + a0 + j];
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k)
+#pragma unroll
+            for (int j = 0; j < TPL; ++j) p[j] = df_mul_add(c[k * WE + a0 + j], p[j], x);
+    }
 }
 
 /* double-float window values per point (see launch_frac_windows_df): four lanes per point, each
- * evaluating TPL = ceil(W / 4) consecutive taps of both coordinates by Horner in double-float on
- * the kWinPieces-piece per-tap polynomials staged in shared memory (piece h of
- * u = l0 - t + w/2 in [0, 1) is [h/P, (h+1)/P), argument x = 2P u - 2h - 1).  The four lanes of
- * a point read one piece's coefficients at consecutive taps, so a half-warp reads only four
- * pieces; the argument comes from the point's exact FP32 pair u (no FP64 arithmetic). */
+ * evaluating TPL = ceil(W / 4) consecutive taps of both coordinates on the kWinPieces-piece
+ * per-tap polynomials staged in shared memory (piece h of u = l0 - t + w/2 in [0, 1) is
+ * [h/P, (h+1)/P), argument x = 2P u - 2h - 1).  The four lanes of a point read one piece's
+ * coefficients at consecutive taps, so a half-warp reads only four pieces; the argument comes
+ * from the point's exact FP32 pair u (no FP64 arithmetic). */
 template <int W>
 __global__ void __launch_bounds__(256)
     k_frac_windows_df(int64_t n, const float4 *__restrict__ frac, const int *__restrict__ count,
@@ -627,19 +648,26 @@ __global__ void __launch_bounds__(256)
 {
     constexpr int NP = kWinPieces, D = kPieceDeg[W], WE = win_row(W);
     constexpr int TPL = (W + 3) / 4;
-    constexpr int S0 = win_piece_stride(W, D), S1 = win_piece_stride(W, D - 1);
+    constexpr int S0 = win_stride_df(W, D), S1 = win_stride_df(W, D - 1);
+    constexpr int F0 = win_stride_f(W, D), F1 = win_stride_f(W, D - 1);
     extern __shared__ __align__(16) unsigned char sm[];
     df32 *cw = reinterpret_cast<df32 *>(sm);
+    const int md = NP * S0 + (deriv ? NP * S1 : 0);
+    float *cf = reinterpret_cast<float *>(cw + md);
+    const int mf = NP * F0 + (deriv ? NP * F1 : 0);
     /* the tables (window, then derivative) in the padded layout; the pad cells are zero */
-    const int m = NP * S0 + (deriv ? NP * S1 : 0);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) cw[i] = df32(0.0f, 0.0f);
+    for (int i = threadIdx.x; i < md; i += blockDim.x) cw[i] = df32(0.0f, 0.0f);
+    for (int i = threadIdx.x; i < mf; i += blockDim.x) cf[i] = 0.0f;
     __syncthreads();
     const int n0 = NP * (D + 1) * W, n1 = deriv ? NP * D * W : 0;
     for (int i = threadIdx.x; i < n0 + n1; i += blockDim.x) {
         const bool dv = i >= n0;
         const int j = dv ? i - n0 : i, rows = dv ? D : D + 1;
         const int a = j % W, hk = j / W, h = hk / rows, k = hk - h * rows;
-        cw[(dv ? NP * S0 : 0) + h * (dv ? S1 : S0) + k * WE + a] = df32(coef[i].x, coef[i].y);
+        if (k <= 2)
+            cw[(dv ? NP * S0 : 0) + h * (dv ? S1 : S0) + k * WE + a] = df32(coef[i].x, coef[i].y);
+        else
+            cf[(dv ? NP * F0 : 0) + h * (dv ? F1 : F0) + (k - 3) * WE + a] = coef[i].x;
     }
     __syncthreads();
     const int64_t nv = count ? min(n, (int64_t)*count) : n;
@@ -682,15 +710,16 @@ __global__ void __launch_bounds__(256)
         int hx, hy;
         const df32 ax = piece_arg(fr.x, fr.y, hx), ay = piece_arg(fr.z, fr.w, hy);
         df32 p[TPL];
-        windows_taps<TPL, D, WE>(cw + hy * S0, a0, ay, p);
+        windows_taps<TPL, D, WE>(cw + hy * S0, cf + hy * F0, a0, ay, p);
         emit(0, p);
-        windows_taps<TPL, D, WE>(cw + hx * S0, a0, ax, p);
+        windows_taps<TPL, D, WE>(cw + hx * S0, cf + hx * F0, a0, ax, p);
         emit(1, p);
         if (deriv) {
             const df32 *cwd = cw + NP * S0;
-            windows_taps<TPL, D - 1, WE>(cwd + hy * S1, a0, ay, p);
+            const float *cfd = cf + NP * F0;
+            windows_taps<TPL, D - 1, WE>(cwd + hy * S1, cfd + hy * F1, a0, ay, p);
             emit(2, p);
-            windows_taps<TPL, D - 1, WE>(cwd + hx * S1, a0, ax, p);
+            windows_taps<TPL, D - 1, WE>(cwd + hx * S1, cfd + hx * F1, a0, ax, p);
             emit(3, p);
         }
     }
@@ -996,8 +1025,10 @@ cudaError_t launch_frac_windows_df(const Geom &g, int64_t n, const float4 *frac,
     if (n <= 0) return cudaSuccess;
     if (g.w < 2 || g.w > 16 || deg != kPieceDeg[g.w]) return cudaErrorInvalidValue;
     /* coefficient tables in the padded layout */
-    const size_t smem = sizeof(df32) * kWinPieces *
-                        (win_piece_stride(g.w, deg) + (deriv ? win_piece_stride(g.w, deg - 1) : 0));
+    const size_t smem =
+        sizeof(df32) * kWinPieces *
+            (win_stride_df(g.w, deg) + (deriv ? win_stride_df(g.w, deg - 1) : 0)) +
+        sizeof(float) * kWinPieces * (win_stride_f(g.w, deg) + (deriv ? win_stride_f(g.w, deg - 1) : 0));
     /* grid-stride: at most 8 CTAs of 64 points per SM of a 148-SM part, looping over the rest */
     const int blocks = (int)std::min<int64_t>((n + 63) / 64, 148 * 8);
     cudaError_t e = cudaSuccess;
