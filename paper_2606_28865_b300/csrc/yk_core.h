@@ -133,6 +133,41 @@ YK_HD df32 df_mul_add_lazy(df32 acc, df32 a, df32 b)
     return df32(s, YK_FADD(t, YK_FADD(acc.lo, e)));
 }
 
+/* Double-float with lazy normalisation, for the FFT butterflies: sums and products keep their
+ * (hi, lo) pair as computed (the exact two-sum of the high words with the low words added, or the
+ * FMA two-product), without the final fast two-sum that makes |lo| <= ulp(hi)/2.  Every operation
+ * still carries the exact rounding error of its high words, so a value keeps ~48 bits relative to
+ * the magnitudes it was formed from; where high words cancel, the low word may exceed the high one
+ * and the value then keeps 24 bits of itself, i.e. ~2^-48 of the operands (the FFT's error is
+ * relative to the transform's norm, so this costs nothing).  A stage's values are normalised
+ * once, when they are stored (df_norm).  8 FP32 operations per sum instead of 11, 4 per product
+ * instead of 7. */
+struct alignas(8) df32l {
+    float hi, lo;
+    df32l() = default;
+    YK_HD df32l(float h, float l) : hi(h), lo(l) {}
+    YK_HD explicit df32l(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+    YK_HD explicit df32l(df32 v) : hi(v.hi), lo(v.lo) {}
+};
+YK_HD df32 df_norm(df32l v) { return df_fast_two_sum(v.hi, v.lo); }
+YK_HD df32l operator+(df32l a, df32l b)
+{
+    const float s = YK_FADD(a.hi, b.hi);
+    const float bb = YK_FSUB(s, a.hi);
+    const float e = YK_FADD(YK_FSUB(a.hi, YK_FSUB(s, bb)), YK_FSUB(b.hi, bb));
+    return df32l(s, YK_FADD(e, YK_FADD(a.lo, b.lo)));
+}
+YK_HD df32l operator-(df32l a) { return df32l(-a.hi, -a.lo); }
+YK_HD df32l operator-(df32l a, df32l b) { return a + (-b); }
+YK_HD df32l operator*(df32l a, df32l b)
+{
+    const float p = YK_FMUL(a.hi, b.hi);
+    float e = YK_FFMA(a.hi, b.hi, -p);
+    e = YK_FFMA(a.hi, b.lo, e);
+    e = YK_FFMA(a.lo, b.hi, e);
+    return df32l(p, e);
+}
+
 /* ---------------------------------------------------------------------------------------- */
 /* exponential-of-semicircle window phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)), |z| <= w/2    */
 /* (the spreading kernel of the NUFFT that evaluates eqs. disrete_sigma_hat and sh_fourier)  */

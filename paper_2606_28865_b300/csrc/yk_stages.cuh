@@ -682,44 +682,61 @@ __device__ __forceinline__ df32 fold_cell_df(const Inst &d, int ty, int ly, int 
 /* floor(x / d) with the stage's multiplier (d = 1 when m == 0) */
 __device__ __forceinline__ int fdiv(int x, unsigned m) { return m ? (int)__umulhi((unsigned)x, m) : x; }
 
+/* the arithmetic of the butterflies: double-float stages compute in the lazily normalised form
+ * (df32l) and normalise once per stored value; FP32 and FP64 stages compute in their own type */
+template <typename R> struct FftArith {
+    using C = R;
+    static __device__ __forceinline__ C in(R v) { return v; }
+    static __device__ __forceinline__ R out(C v) { return v; }
+};
+template <> struct FftArith<df32> {
+    using C = df32l;
+    static __device__ __forceinline__ C in(df32 v) { return df32l(v); }
+    static __device__ __forceinline__ df32 out(df32l v) { return df_norm(v); }
+};
+
 /* one DIF stage with a compile-time radix: every butterfly of nrows rows (row stride rowlen) */
 template <int RADIX, bool INV, typename R, typename TW>
 __device__ __forceinline__ void fft_stage(cpx<R> *x, const FftStages &st, int s, const TW *tw,
                                           int nrows, int rowlen)
 {
+    using A = FftArith<R>;
+    using C = typename A::C;
     const int B = st.B[s], span = B / RADIX, nb = st.L / RADIX, step = st.tw_step[s];
     const unsigned msp = st.span_m[s], mnb = st.nb_m[s];
+    auto ld = [](cpx<R> z) { return mk<C>(A::in(z.re), A::in(z.im)); };
+    auto sto = [](cpx<C> z) { return mk<R>(A::out(z.re), A::out(z.im)); };
     for (int i = threadIdx.x; i < nrows * nb; i += blockDim.x) {
         const int row = fdiv(i, mnb), t = i - row * nb;
         const int b = fdiv(t, msp), k = t - b * span;
         cpx<R> *xr = x + (size_t)row * rowlen + b * B + k;
-        cpx<R> v[RADIX];
+        cpx<C> v[RADIX];
         if (!INV) {
 #pragma unroll
-            for (int q = 0; q < RADIX; ++q) v[q] = xr[q * span];
+            for (int q = 0; q < RADIX; ++q) v[q] = ld(xr[q * span]);
             if (RADIX == 2) dft2<-1>(v);
             else if (RADIX == 3) dft3<-1>(v);
             else if (RADIX == 4) dft4<-1>(v);
             else dft5<-1>(v);
-            xr[0] = v[0];
+            xr[0] = sto(v[0]);
 #pragma unroll
             for (int p = 1; p < RADIX; ++p) {
                 const TW w = tw[p * k * step];
-                xr[p * span] = mul(v[p], mk<R>((R)w.x, (R)w.y));
+                xr[p * span] = sto(mul(v[p], mk<C>((C)w.x, (C)w.y)));
             }
         } else {
-            v[0] = xr[0];
+            v[0] = ld(xr[0]);
 #pragma unroll
             for (int p = 1; p < RADIX; ++p) {
                 const TW w = tw[p * k * step];
-                v[p] = mulc(xr[p * span], mk<R>((R)w.x, (R)w.y));
+                v[p] = mulc(ld(xr[p * span]), mk<C>((C)w.x, (C)w.y));
             }
             if (RADIX == 2) dft2<+1>(v);
             else if (RADIX == 3) dft3<+1>(v);
             else if (RADIX == 4) dft4<+1>(v);
             else dft5<+1>(v);
 #pragma unroll
-            for (int q = 0; q < RADIX; ++q) xr[q * span] = v[q];
+            for (int q = 0; q < RADIX; ++q) xr[q * span] = sto(v[q]);
         }
     }
     __syncthreads();
