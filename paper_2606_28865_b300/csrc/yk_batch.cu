@@ -49,46 +49,59 @@ __global__ void __launch_bounds__(256)
      * tables (FFT stage lists) dynamically, which from global memory cost registers and spills */
     __shared__ __align__(16) Inst s_inst;
     static_assert(sizeof(Inst) % 16 == 0, "Inst is copied in 16-byte words");
+    int held = -1; /* the instance whose descriptor s_inst holds (items of one instance and stage
+                      are consecutive in the list, so a CTA mostly takes the same one again) */
+    /* items are claimed two at a time (one atomic for both) and run in list order; the second
+     * waits like any other item, and only for items earlier in the list, so the waits still end */
+    int q0 = 0, nq = 0; /* the claimed pair [q0, q0 + nq) */
     for (;;) {
+        if (nq == 0) {
+            if (threadIdx.x == 0) s_q = atomicAdd(head, 2);
+            __syncthreads();
+            q0 = s_q;
+            nq = 2;
+            __syncthreads(); /* s_q is rewritten below */
+        }
+        const int q = q0 + (2 - nq);
+        --nq;
+        if (q >= total) return; /* uniform */
         if (threadIdx.x == 0) {
-            const int q = atomicAdd(head, 1);
             int go = 1;
-            if (q < total) {
-                const int2 it = items[q];
-                const int stage = it.y >> 24;
-                if (stage > 0) {
-                    const int *cnt = done + it.x * yk::ST_COUNT + stage - 1;
-                    const int want = need[it.x * yk::ST_COUNT + stage - 1];
-                    long long k = 0;
-                    while (ld_acquire(cnt) < want) {
-                        if (*(volatile int *)status) {
-                            go = 0;
-                            break;
-                        }
-                        if (++k > spin_limit) {
-                            atomicOr(status, yk::ERR_WAIT_TIMEOUT);
-                            go = 0;
-                            break;
-                        }
-                        __nanosleep(200);
+            const int2 it = items[q];
+            const int stage = it.y >> 24;
+            if (stage > 0) {
+                const int *cnt = done + it.x * yk::ST_COUNT + stage - 1;
+                const int want = need[it.x * yk::ST_COUNT + stage - 1];
+                long long k = 0;
+                while (ld_acquire(cnt) < want) {
+                    if (*(volatile int *)status) {
+                        go = 0;
+                        break;
                     }
-                    __threadfence();
+                    if (++k > spin_limit) {
+                        atomicOr(status, yk::ERR_WAIT_TIMEOUT);
+                        go = 0;
+                        break;
+                    }
+                    __nanosleep(200);
                 }
-                if (*(volatile int *)status) go = 0;
+                __threadfence();
             }
-            s_q = q;
+            if (*(volatile int *)status) go = 0;
             s_go = go;
         }
         __syncthreads();
-        const int q = s_q;
-        if (q >= total) return;
         const int2 it = items[q];
         const int inst = it.x, stage = it.y >> 24, idx = it.y & 0xffffff;
         if (s_go) {
-            const int4 *src = reinterpret_cast<const int4 *>(insts + inst);
-            int4 *dst = reinterpret_cast<int4 *>(&s_inst);
-            for (int i = threadIdx.x; i < (int)(sizeof(Inst) / 16); i += blockDim.x) dst[i] = src[i];
-            __syncthreads();
+            if (inst != held) { /* uniform: every thread read the same item */
+                const int4 *src = reinterpret_cast<const int4 *>(insts + inst);
+                int4 *dst = reinterpret_cast<int4 *>(&s_inst);
+                for (int i = threadIdx.x; i < (int)(sizeof(Inst) / 16); i += blockDim.x)
+                    dst[i] = src[i];
+                held = inst;
+                __syncthreads();
+            }
             yk::run_stage_w<R, W>(s_inst, stage, idx, sm);
         }
         __syncthreads();
