@@ -202,10 +202,10 @@ YK_API yk_status yk_eval_longrange_dl(yk_plan_t p, const double *density, const 
 /*
  * yk_slp_local: the single-layer local asymptotic part S_{L,A}[sigma](x_i) = int_0^{delta_star}
  * int_boundary H(t, x_i - x') sigma(x') ds dt (Section 2.1, eq. sla) by the expansion of Section
- * 4.1 (Lemma, eq. slp_local1) through its delta_star^{3/2} term, at the closest boundary point
+ * 4.1 (Lemma, eq. slp_local1) through its delta_star^2 term, at the closest boundary point
  * found by Newton on the panel polynomial (Section 3.2).  With the history part at the same
  * delta (yk_eval_longrange with opts.delta = delta_star) it gives the single layer potential
- * S = S_{L,A} + S_H up to O(delta_star^2) near the boundary (no dyadic levels).
+ * S = S_{L,A} + S_H up to O(delta_star^{5/2}) near the boundary (no dyadic levels).
  *  - alpha > 0, delta_star > 0.
  *  - xb, yb, sigma: n_panels * q values, panel by panel, at the q Gauss-Legendre nodes of each
  *    panel's parameter t in [-1, 1] in ascending order; panels in counter-clockwise order around

@@ -3,7 +3,7 @@ TEST INFRASTRUCTURE ONLY.
 
 S_{L,A}[sigma](x) = int_0^{delta*} int_{boundary} H(t, x - x') sigma(x') ds dt, H the heat kernel of
 (-Lap + alpha^2) (Section 2.1, eq. sla), evaluated by the asymptotic expansion of Section 4.1
-(Lemma, eq. slp_local1) through its delta*^{3/2} term, at the closest boundary point x0 found by
+(Lemma, eq. slp_local1) through its delta*^2 term, at the closest boundary point x0 found by
 Newton on d/dt |x - gamma(t)|^2 = 0 (Section 3.2, closest point), here on the analytic starfish.
 
 Readings (where the printed lemma is garbled or silent):
@@ -33,9 +33,11 @@ def locality_radius(alpha: float, dstar: float) -> float:
     return s * (12.0 + 2.0 * alpha * s)
 
 
-def lemma_terms(alpha, dstar, r, rho, kappa0, s0, s0pp):
-    """The expansion of the lemma (eq. slp_local1) through the delta*^{3/2} term, vectorised."""
-    r, rho, kappa0, s0, s0pp = map(np.asarray, (r, rho, kappa0, s0, s0pp))
+def lemma_terms(alpha, dstar, r, rho, kappa0, s0, s0pp, s0p=0.0, g3=0.0, g4=0.0):
+    """The expansion of the lemma (eq. slp_local1) through its delta*^2 term, vectorised; s0p,
+    g3, g4 are sigma0', gamma0^(3) and gamma0^(4) in the tangent-line parameter (the delta*^2
+    term's only new inputs; 0 for a straight boundary, and a circle has gamma0^(3) = 0)."""
+    r, rho, kappa0, s0, s0pp, s0p, g3, g4 = map(np.asarray, (r, rho, kappa0, s0, s0pp, s0p, g3, g4))
     sd = math.sqrt(dstar)
     c1 = r / sd
     c2 = alpha * sd
@@ -47,8 +49,12 @@ def lemma_terms(alpha, dstar, r, rho, kappa0, s0, s0pp):
     P1 = c1 * P0
     P2 = c1 * P1
     Q0 = (phi_m - Z) / c2 ** 3 + c1 * phi_p / c2 ** 2
-    return (sd * s0 / 4 * P0 + dstar * rho * kappa0 * s0 / 8 * P1
-            + dstar * sd * (kappa0 ** 2 * s0 / 32 * (Q0 + 3 * P2) + s0pp / 8 * Q0))
+    P3, Q1 = c1 * P2, c1 * Q0
+    k = kappa0
+    return (sd * s0 / 4 * P0 + dstar * rho * k * s0 / 8 * P1
+            + dstar * sd * (k ** 2 * s0 / 32 * (Q0 + 3 * P2) + s0pp / 8 * Q0)
+            + dstar ** 2 * rho * (k ** 3 * s0 / 64 * (-3 * Q1 + 5 * P3)
+                                  + (3 * k * s0pp / 16 + s0p * g3 / 8 + s0 * g4 / 32) * Q1))
 
 
 class StarfishGeom:
@@ -103,17 +109,24 @@ def slp_local_starfish(alpha, dstar, geom: StarfishGeom, sigma, xt, yt):
     sigma_tt) in the curve parameter.  Targets beyond the locality radius get 0."""
     xt, yt = np.atleast_1d(xt).astype(float), np.atleast_1d(yt).astype(float)
     t = geom.closest(xt, yt)
-    g, g1, g2 = geom.derivs(t)
+    g = geom.derivs4(t)
+    g1, g2 = g[1], g[2]
     sp_ = np.hypot(g1[0], g1[1])                      # ds/dt
     nux, nuy = g1[1] / sp_, -g1[0] / sp_              # outward normal (counter-clockwise)
-    dx, dy = xt - g[0], yt - g[1]
+    dx, dy = xt - g[0][0], yt - g[0][1]
     r = np.hypot(dx, dy)
     rho = np.where(dx * nux + dy * nuy >= 0.0, 1.0, -1.0)
     kappa0 = -(g1[0] * g2[1] - g1[1] * g2[0]) / sp_ ** 3
     s0, s1, s2 = sigma(t)
     spp = (g1[0] * g2[0] + g1[1] * g2[1]) / sp_        # d2s/dt2
     s0pp = (s2 - s1 * spp / sp_) / sp_ ** 2             # second arclength derivative
-    u = lemma_terms(alpha, dstar, r, rho, kappa0, s0, s0pp)
+    # gamma0^(3), gamma0^(4) of the boundary graph and sigma0' in the tangent-line parameter
+    tx, ty = g1[0] / sp_, g1[1] / sp_
+    xi = [g[k][0] * tx + g[k][1] * ty for k in range(1, 5)]
+    eta = [g[k][0] * nux + g[k][1] * nuy for k in range(1, 5)]
+    G = tangent_line_derivs(xi, eta)
+    s0p = s1 / xi[0]
+    u = lemma_terms(alpha, dstar, r, rho, kappa0, s0, s0pp, s0p, G[2], G[3])
     return np.where(r < locality_radius(alpha, dstar), u, 0.0)
 
 

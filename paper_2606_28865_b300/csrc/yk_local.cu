@@ -1,10 +1,11 @@
 /*
- * yk_local.cu — the single-layer local asymptotic part S_{L,A}[sigma] (Section 2.1, eq. sla;
- * Section 4.1, Lemma, eq. slp_local1, through its delta*^{3/2} term) at targets near the boundary.
+ * yk_local.cu — the local asymptotic parts S_{L,A}[sigma] and D_{L,A}[mu] (Section 2.1, eqs. sla,
+ * dla; Section 4.1, the lemmas, eqs. slp_local1 and dlp_local1, through their delta*^2 terms),
+ * V_L[f] (eq. vl, the Lemma for V_L) and the dyadic corrections, at targets near the boundary.
  *
  * The boundary arrives as panels of q Gauss-Legendre nodes in the panel parameter t in [-1, 1]
  * (Section 3.2): per panel the node coordinates and the density are turned into Legendre series,
- * so gamma(t), sigma(t) and their first two derivatives are available anywhere on the panel.  Per
+ * so gamma(t), sigma(t) and their derivatives are available anywhere on the panel.  Per
  * target (one thread each): the panels within the locality radius r_loc = sqrt(d*)(12 + 2 alpha
  * sqrt(d*)) (remark on locality, Section 4.1) are listed by a cell grid; the panel with the nearest
  * node is refined by Newton on d/dt |x - gamma(t)|^2 = 0 (Section 3.2, closest point), moving to a
@@ -220,9 +221,10 @@ __device__ __forceinline__ void legendre_eval(const T *const (&c)[NS], int q, T 
     }
 }
 
-/* the lemma's expansion through the delta*^{3/2} term */
+/* the lemma's expansion (eq. slp_local1) through its delta*^2 term; s0p, g3, g4 are sigma0',
+ * gamma0''' and gamma0'''' in the tangent-line parameter */
 __device__ double lemma_terms(double alpha, double dstar, double r, double rho, double kappa0,
-                              double s0, double s0pp)
+                              double s0, double s0pp, double s0p, double g3, double g4)
 {
     const double sd = sqrt(dstar), c1 = r / sd, c2 = alpha * sd;
     const double em = exp(-c1 * c2) * erfc(0.5 * c1 - c2);
@@ -231,8 +233,12 @@ __device__ double lemma_terms(double alpha, double dstar, double r, double rho, 
     const double Z = 4.0 * c2 * exp(-0.25 * c1 * c1 - c2 * c2) * 0.56418958354775628695; /* 1/sqrt(pi) */
     const double P0 = phm / c2, P1 = c1 * P0, P2 = c1 * P1;
     const double Q0 = (phm - Z) / (c2 * c2 * c2) + c1 * php / (c2 * c2);
-    return sd * s0 * 0.25 * P0 + dstar * rho * kappa0 * s0 * 0.125 * P1 +
-           dstar * sd * (kappa0 * kappa0 * s0 / 32.0 * (Q0 + 3.0 * P2) + s0pp * 0.125 * Q0);
+    const double P3 = c1 * P2, Q1 = c1 * Q0, k = kappa0;
+    return sd * s0 * 0.25 * P0 + dstar * rho * k * s0 * 0.125 * P1 +
+           dstar * sd * (k * k * s0 / 32.0 * (Q0 + 3.0 * P2) + s0pp * 0.125 * Q0) +
+           dstar * dstar * rho *
+               (k * k * k * s0 / 64.0 * (5.0 * P3 - 3.0 * Q1) +
+                (3.0 / 16.0 * k * s0pp + 0.125 * s0p * g3 + s0 * g4 / 32.0) * Q1);
 }
 
 /* cell of each target (-1 outside the grid) and the targets per cell */
@@ -638,25 +644,35 @@ __global__ void __launch_bounds__(128) k_slp_local(int n_near, const int *__rest
     }
     const int q = P.q, h = q / 2;
     const double *const c3[3] = {P.cx + p * q, P.cy + p * q, P.cs + p * q};
-    double g[3], g1[3], g2[3];
-    legendre_eval<double, 3>(c3, q, td, g, g1, g2, c_la, c_lb);
-    const double s = g[2] + P.sref[p * q + h], s1 = g1[2], s2 = g2[2];
-    const double st = sqrt(g1[0] * g1[0] + g1[1] * g1[1]);
-    const double nux = g1[1] / st, nuy = -g1[0] / st; /* outward (counter-clockwise) */
-    const double dx = (x - P.xb[p * q + h]) - g[0], dy = (y - P.yb[p * q + h]) - g[1];
+    double f[5][3];
+    legendre_eval4<3>(c3, q, td, f);
+    const double s = f[0][2] + P.sref[p * q + h];
+    const double st = sqrt(f[1][0] * f[1][0] + f[1][1] * f[1][1]);
+    const double tx = f[1][0] / st, ty = f[1][1] / st;
+    const double nux = ty, nuy = -tx; /* outward (counter-clockwise) */
+    const double dx = (x - P.xb[p * q + h]) - f[0][0], dy = (y - P.yb[p * q + h]) - f[0][1];
     const double r = sqrt(dx * dx + dy * dy);
     double val = 0.0;
     if (r < rl) {
         const double rho = dx * nux + dy * nuy >= 0.0 ? 1.0 : -1.0;
-        double kappa0 = -(g1[0] * g2[1] - g1[1] * g2[0]) / (st * st * st);
-        const double stt = (g1[0] * g2[0] + g1[1] * g2[1]) / st;
-        double s0pp = (s2 - s1 * stt / st) / (st * st);
-        double Gw[4], Mw[4];
-        if (wide_derivs(P, p, g[0], g[1], Gw, Mw)) { /* short panel: the window fit */
-            kappa0 = Gw[1];
-            s0pp = Mw[1];
+        /* tangent-line derivatives: kappa0 = gamma'', gamma''', gamma'''' of the boundary graph,
+         * sigma0', sigma0'' (orders >= 2 from the window fit on short panels) */
+        double xi[4], eta[4], mt[4], G[4], M[4];
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            xi[d] = f[d + 1][0] * tx + f[d + 1][1] * ty;
+            eta[d] = f[d + 1][0] * nux + f[d + 1][1] * nuy;
+            mt[d] = f[d + 1][2];
         }
-        val = lemma_terms(alpha, dstar, r, rho, kappa0, s, s0pp);
+        tangent_line(xi, eta, G);
+        tangent_line(xi, mt, M);
+        double Gw[4], Mw[4];
+        if (wide_derivs(P, p, f[0][0], f[0][1], Gw, Mw))
+            for (int d = 1; d < 4; ++d) {
+                G[d] = Gw[d];
+                M[d] = Mw[d];
+            }
+        val = lemma_terms(alpha, dstar, r, rho, G[1], s, M[1], M[0], G[2], G[3]);
     }
     u[i] = val;
 }

@@ -1,9 +1,11 @@
 """Pins of the oracle's single-layer local asymptotic part S_{L,A} (Section 4.1, Lemma, eq.
-slp_local1; definition eq. sla).  Independent of the oracle's arithmetic: the exact value for a
-straight boundary with constant density (1-D scipy quadrature), the exact value for a circle with
-a two-mode density (the boundary integral reduces to modified Bessel functions, then 1-D
-quadrature), the corollary for targets on the boundary (eq. slp_local2), the small-c2 limits of
-the remark on P_m and Q_m, the locality remark, and the closest point's orthogonality.
+slp_local1 through its delta*^2 term; definition eq. sla).  Independent of the oracle's
+arithmetic: the exact value for a straight boundary with constant density (1-D scipy quadrature),
+the exact value for a circle with a two-mode density (the boundary integral reduces to modified
+Bessel functions, then 1-D quadrature) and the starfish (2-D Gauss-Legendre quadrature of eq. sla),
+both converging at the lemma's order, the corollary for targets on the boundary (eq. slp_local2),
+the small-c2 limits of the remark on P_m and Q_m, the locality remark, and the closest point's
+orthogonality.
 """
 import math
 
@@ -49,8 +51,10 @@ def test_flat_boundary_constant_density_is_exact():
 
 @pytest.mark.parametrize("alpha", [10.0, 1.0])
 def test_circle_converges_at_the_lemma_order(alpha):
-    # curved boundary, varying density: the relative error is O(delta*^{3/2}); it fixes the
-    # sign of kappa0 (curvature of the graph in the outward-normal frame: -1/R here) and Z's c2
+    # curved boundary, varying density: through the delta*^2 term the relative error is
+    # O(delta*^2) (O(delta*^{3/2}) without it); it fixes the sign of kappa0 (curvature of the
+    # graph in the outward-normal frame: -1/R here), Z's c2 and the delta*^2 term's kappa0^3 and
+    # gamma0^(4) parts (the circle's graph -xi^2/(2R) - xi^4/(8R^3): gamma0^(4) = -3/R^3)
     errs = {}
     for ds in (1e-4, 1e-5):
         worst = 0.0
@@ -58,16 +62,66 @@ def test_circle_converges_at_the_lemma_order(alpha):
             for rho in (1.0, -1.0):
                 X = 1.0 + rho * c1 * math.sqrt(ds)
                 ref = circle_exact(alpha, ds, X)
-                v = float(OL.lemma_terms(alpha, ds, abs(X - 1.0), rho, -1.0, 1.5, -2.0))
+                v = float(OL.lemma_terms(alpha, ds, abs(X - 1.0), rho, -1.0, 1.5, -2.0, 0.0,
+                                         0.0, -3.0))
                 worst = max(worst, abs(v - ref) / abs(ref))
         errs[ds] = worst
     assert all(np.isfinite(v) for v in errs.values()) and errs[1e-5] > 0, errs
-    assert errs[1e-5] <= 3e-8, errs
-    assert errs[1e-4] / errs[1e-5] >= 15.0, errs     # order 3/2 gives 31.6
+    assert errs[1e-5] <= 2e-10, errs
+    assert errs[1e-4] / errs[1e-5] >= 60.0, errs     # order 2 gives 100, order 3/2 31.6
     # the opposite curvature sign is wrong at first order
     X = 1.0 + 0.5 * math.sqrt(1e-5)
-    bad = float(OL.lemma_terms(alpha, 1e-5, X - 1.0, 1.0, +1.0, 1.5, -2.0))
+    bad = float(OL.lemma_terms(alpha, 1e-5, X - 1.0, 1.0, +1.0, 1.5, -2.0, 0.0, 0.0, 3.0))
     assert abs(bad - circle_exact(alpha, 1e-5, X)) / circle_exact(alpha, 1e-5, X) > 1e-4
+
+
+_GU = np.polynomial.legendre.leggauss(300)   # outer rule, in u = log t
+_GS = np.polynomial.legendre.leggauss(96)    # inner rule, along the boundary
+
+
+def sla_quadrature(alpha, ds, x, y, geom, s0, sigma):
+    """eq. sla at (x, y): int_0^ds int e^{-alpha^2 t - |x - gamma(s)|^2/(4t)} / (4 pi t) sigma(s)
+    |gamma'(s)| ds dt by Gauss-Legendre in u = log t on [log ds - 30, log ds] (targets at least
+    0.5 sqrt(ds) from the boundary) and, per t, over s0 +- 16 sqrt(t) / |gamma'(s0)|."""
+    xu, wu = _GU
+    xs, ws = _GS
+    lo, hi = math.log(ds) - 30.0, math.log(ds)
+    t = np.exp(0.5 * (hi - lo) * xu + 0.5 * (hi + lo))
+    wt = 0.5 * (hi - lo) * wu * t
+    _, d0, _ = geom.derivs(np.array([s0]))
+    L = 16.0 * np.sqrt(t) / math.hypot(d0[0][0], d0[1][0])
+    sv = s0 + L[:, None] * xs[None, :]
+    g, g1, _ = geom.derivs(sv)
+    ex, ey = x - g[0], y - g[1]
+    kern = (np.exp(-alpha * alpha * t[:, None] - (ex * ex + ey * ey) / (4 * t[:, None]))
+            / (4 * math.pi * t[:, None]) * sigma(sv)[0] * np.hypot(g1[0], g1[1]))
+    return float(((kern * ws[None, :]).sum(axis=1) * L * wt).sum())
+
+
+def test_starfish_converges_at_the_lemma_order():
+    # the general case: sigma0' and gamma0^(3) nonzero, so the delta*^2 term's sigma0' gamma0^(3)
+    # part is exercised too; moderate curvature (|kappa0| below ~3)
+    g = OL.StarfishGeom()
+    alpha = 10.0
+    errs = {}
+    for ds in (1e-4, 1e-5):
+        worst = 0.0
+        for t0 in (0.33, 2.9, 4.0, 5.3):
+            p, p1, _ = g.derivs(np.array([t0]))
+            nrm = math.hypot(p1[0][0], p1[1][0])
+            nx, ny = p1[1][0] / nrm, -p1[0][0] / nrm
+            for c1 in (0.5, 2.0):
+                for rho in (1.0, -1.0):
+                    d = rho * c1 * math.sqrt(ds)
+                    x, y = p[0][0] + d * nx, p[1][0] + d * ny
+                    ref = sla_quadrature(alpha, ds, x, y, g, t0, OL.starfish_density)
+                    v = float(OL.slp_local_starfish(alpha, ds, g, OL.starfish_density,
+                                                    np.array([x]), np.array([y]))[0])
+                    worst = max(worst, abs(v - ref) / abs(ref))
+        errs[ds] = worst
+    assert errs[1e-5] > 0 and errs[1e-5] <= 1e-8, errs
+    assert errs[1e-4] / errs[1e-5] >= 60.0, errs     # order 2 gives 100 (without the delta*^2
+    #                                                   term ~32)
 
 
 def test_on_boundary_corollary():
