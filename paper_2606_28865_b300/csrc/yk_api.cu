@@ -811,7 +811,7 @@ bool yk_fill_inst(const yk_plan_s *pc, yk::Inst *d)
     d->M = (int)p->M;
     d->f32 = p->precision == YK_FP32C;
     d->fft_df = p->fft_df;
-    d->rows = yk::rows_per_item(d->n, d->f32);
+    d->rows = yk::rows_per_item(d->n, d->f32, true);
     d->tile_ptr = P<int>(p->tile_ptr);
     d->order = P<int>(p->tile_order);
     d->ent_t = P<double2>(p->ent_t);

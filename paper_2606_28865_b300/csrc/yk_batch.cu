@@ -253,6 +253,12 @@ yk_status build(yk_batch_s *b)
             b->trivial_n.push_back(p->n_trg);
             continue;
         }
+        /* the row passes in items of as many rows as shared memory takes (see rows_per_item) */
+        d.rows = yk::rows_per_item(d.n, d.f32 != 0, false);
+        for (int s = 0; s < yk::ST_COUNT; ++s) {
+            d.items[s] = yk::stage_items(d, s);
+            d.smem[s] = yk::stage_smem(d, s);
+        }
         Group *gp = nullptr;
         for (Group &g : b->grp)
             if (g.f32 == (d.f32 != 0) && g.w == d.g.w) gp = &g;

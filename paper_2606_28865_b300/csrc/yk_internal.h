@@ -118,7 +118,7 @@ cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st);
 /* shared-memory and work-item sizes of each stage (host side of the kernels' layouts) */
 int stage_smem(const Inst &d, int stage);
 int stage_items(const Inst &d, int stage);
-int rows_per_item(int n, bool f32);
+int rows_per_item(int n, bool f32, bool fill_sms);
 
 /* kernel launchers (yk_kernels.cu); all enqueue on `st` and return the launch status. */
 /* The all-FP64 path's binning (FP64 grid coordinates): sources ns charges (xs, ys) then nd dipoles

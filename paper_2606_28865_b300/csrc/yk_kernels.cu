@@ -886,11 +886,18 @@ Inst blank_inst(int n, int M)
 /* ----------------------------------------------------------------------------------------- */
 /* stage geometry                                                                              */
 
-int rows_per_item(int n, bool f32)
+int rows_per_item(int n, bool f32, bool fill_sms)
 {
     const int bytes_per_row = (n / 2) * (f32 ? 8 : 16);
     int r = (96 * 1024) / bytes_per_row;
-    return r < 1 ? 1 : (r > 16 ? 16 : r);
+    r = r < 1 ? 1 : (r > 16 ? 16 : r);
+    if (!fill_sms) return r;
+    /* a launch of its own: no more rows than leave two work items per SM of a 148-SM part (FP32
+     * rows of small grids would otherwise fit 15 or 16 to a CTA and leave SMs idle: 107 CTAs at
+     * n = 1600); the batch kernel, which runs many instances' items at once, keeps the larger
+     * items (fewer items, less per-item overhead) */
+    const int fill = (n + 2 * 148 - 1) / (2 * 148);
+    return r < fill ? r : (fill < 1 ? 1 : fill);
 }
 
 int stage_items(const Inst &d, int stage)
@@ -1226,7 +1233,7 @@ cudaError_t launch_fft_t(int stage, const void *grid_in, void *grid_out, void *s
 {
     Inst d = blank_inst(n, M);
     d.f32 = sizeof(R) == 4;
-    d.rows = rows_per_item(n, d.f32);
+    d.rows = rows_per_item(n, d.f32, true);
     d.grid = stage == ST_ROW_FWD ? const_cast<void *>(grid_in) : grid_out;
     d.spec = spec;
     d.mult = mult;
