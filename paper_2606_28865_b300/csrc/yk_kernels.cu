@@ -419,9 +419,19 @@ __global__ void __launch_bounds__(256)
 {
     extern __shared__ int sh_col[]; /* [nchunks][33] */
     const int t0 = blockIdx.x * 32;
-    for (int idx = threadIdx.x; idx < nchunks * 32; idx += blockDim.x) {
-        const int c = idx >> 5, j = idx & 31;
-        sh_col[c * 33 + j] = t0 + j < ntiles ? hist[(int64_t)c * ntiles + t0 + j] : 0;
+    /* eight loads in flight per thread before their stores */
+    for (int idx0 = threadIdx.x; idx0 < nchunks * 32; idx0 += 8 * blockDim.x) {
+        int v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = idx0 + u * blockDim.x, c = idx >> 5, j = idx & 31;
+            v[u] = (idx < nchunks * 32 && t0 + j < ntiles) ? hist[(int64_t)c * ntiles + t0 + j] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = idx0 + u * blockDim.x;
+            if (idx < nchunks * 32) sh_col[(idx >> 5) * 33 + (idx & 31)] = v[u];
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -544,6 +554,35 @@ __global__ void __launch_bounds__(1024) k_scan_add(int *__restrict__ ptr, int co
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         if (base + k < count) ptr[base + k] += add;
+}
+
+/* the whole scan in one CTA for counts up to kScanSingle: blocks of kScanBlock elements in turn,
+ * each scanned as in pass 1 and offset by the running total (one launch instead of three) */
+constexpr int kScanSingle = 16 * kScanBlock;
+
+__global__ void __launch_bounds__(1024) k_scan_single(const int *__restrict__ cnt,
+                                                      int *__restrict__ ptr, int count)
+{
+    __shared__ int wt[32];
+    int carry = 0;
+    for (int b0 = 0; b0 < count; b0 += kScanBlock) {
+        const int base = b0 + threadIdx.x * 4;
+        int v[4], s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = base + k < count ? cnt[base + k] : 0;
+            s += v[k];
+        }
+        int total = 0;
+        int run = carry + block_exclusive_scan(s, wt, total);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (base + k < count) ptr[base + k] = run;
+            run += v[k];
+        }
+        carry += total;
+    }
+    if (threadIdx.x == 0) ptr[count] = carry;
 }
 
 /* heavy-first processing order of the tiles: tiles bucketed by floor(log2(entries)) and listed
@@ -974,6 +1013,12 @@ cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStrea
 {
     if (count <= 0) return cudaMemsetAsync(ptr, 0, sizeof(int), st);
     const int nb = (count + kScanBlock - 1) / kScanBlock;
+    if (count <= kScanSingle) {
+        k_scan_single<<<1, 1024, 0, st>>>(cnt, ptr, count);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemsetAsync(cur, 0, sizeof(int) * nb, st);
+        return e;
+    }
     k_scan_local<<<nb, 1024, 0, st>>>(cnt, ptr, count, cur);
     k_scan_sums<<<1, 1024, 0, st>>>(cur, nb, ptr, count);
     k_scan_add<<<nb, 1024, 0, st>>>(ptr, count, cur);
