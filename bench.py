@@ -844,10 +844,10 @@ def main():
                           f"results; bars 1e-10 (fp64) and 1e-6 (fp32c)")
 
     launches_per_eval = 5
-    # sources: count, three scan passes, fill, three for the tile order, the window values;
-    # targets: chunk histograms, column offsets, three scan passes, scatter, the window values
-    # (the launch list under profiles/ shows 16 + 5 per alpha)
-    launches_per_set = 16
+    # sources: count, scan, fill, three for the tile order, the window values; targets: chunk
+    # histograms, column offsets, scan, scatter, the window values (the launch list under
+    # profiles/ shows 12 + 5 per alpha)
+    launches_per_set = 12
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
@@ -862,7 +862,7 @@ def main():
         "e2e": {"value": pts_step * world / e2e_s, "unit": "points/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * len(alphas) * (launches_per_eval + launches_per_set),
-        "gpu_launches_what": "library kernels in the timed FP64 region (5 evaluation + 16 set-up per alpha)",
+        "gpu_launches_what": "library kernels in the timed FP64 region (5 evaluation + 12 set-up per alpha)",
         "clocks": clk,
         "stage_ms": {str(a): stage_ms[a] for a in alphas},
         "stage_ms_alone": {str(a): stage_ms_alone[a] for a in alphas},
