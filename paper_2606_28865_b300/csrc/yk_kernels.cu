@@ -557,8 +557,9 @@ __global__ void __launch_bounds__(1024) k_scan_add(int *__restrict__ ptr, int co
 }
 
 /* the whole scan in one CTA for counts up to kScanSingle: blocks of kScanBlock elements in turn,
- * each scanned as in pass 1 and offset by the running total (one launch instead of three) */
-constexpr int kScanSingle = 16 * kScanBlock;
+ * each scanned as in pass 1 and offset by the running total (one launch instead of three; beyond
+ * two blocks the serial blocks cost more than the two launches saved) */
+constexpr int kScanSingle = 2 * kScanBlock;
 
 __global__ void __launch_bounds__(1024) k_scan_single(const int *__restrict__ cnt,
                                                       int *__restrict__ ptr, int count)
@@ -1008,7 +1009,7 @@ int stage_smem(const Inst &d, int stage)
     }
 
 /* exclusive scan of cnt into ptr; cur (>= ceil(count / kScanBlock) ints) is scratch and is left
- * zeroed for the fill pass */
+ * zeroed for the fill pass.  Up to kScanSingle counts: one CTA. */
 cudaError_t launch_scan(const int *cnt, int *ptr, int count, int *cur, cudaStream_t st)
 {
     if (count <= 0) return cudaMemsetAsync(ptr, 0, sizeof(int), st);
