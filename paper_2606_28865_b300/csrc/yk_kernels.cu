@@ -801,17 +801,20 @@ template <int W> __global__ void __launch_bounds__(256) k_interp_df(Inst d)
     extern __shared__ __align__(16) unsigned char sm[];
     st_interp_df<W>(d, blockIdx.x, sm);
 }
-template <typename R> __global__ void __launch_bounds__(512) k_row_fwd(Inst d)
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads, 1024 / kRowThreads) k_row_fwd(Inst d)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     st_row_fwd<R>(d, blockIdx.x, sm);
 }
-template <typename R> __global__ void __launch_bounds__(1024) k_columns(Inst d)
+template <typename R>
+__global__ void __launch_bounds__(kColumnThreads, 1024 / kColumnThreads) k_columns(Inst d)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     st_columns<R>(d, blockIdx.x, sm);
 }
-template <typename R> __global__ void __launch_bounds__(512) k_row_inv(Inst d)
+template <typename R>
+__global__ void __launch_bounds__(kRowThreads, 1024 / kRowThreads) k_row_inv(Inst d)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     st_row_inv<R>(d, blockIdx.x, sm);
@@ -929,14 +932,16 @@ Inst blank_inst(int n, int M)
 int rows_per_item(int n, bool f32, bool fill_sms)
 {
     const int bytes_per_row = (n / 2) * (f32 ? 8 : 16);
-    int r = (96 * 1024) / bytes_per_row;
+    int r = kRowItemBytes / bytes_per_row;
     r = r < 1 ? 1 : (r > 16 ? 16 : r);
     if (!fill_sms) return r;
-    /* a launch of its own: no more rows than leave two work items per SM of a 148-SM part (FP32
-     * rows of small grids would otherwise fit 15 or 16 to a CTA and leave SMs idle: 107 CTAs at
-     * n = 1600); the batch kernel, which runs many instances' items at once, keeps the larger
-     * items (fewer items, less per-item overhead) */
-    const int fill = (n + 2 * 148 - 1) / (2 * 148);
+    /* a launch of its own: no more rows than leave 1024 / kRowThreads work items (the CTAs that
+     * share an SM at <= 64 registers) per SM of a 148-SM part (FP32 rows of small grids would
+     * otherwise fit 15 or 16 to a CTA and leave SMs idle: 107 CTAs at n = 1600); the batch
+     * kernel, which runs many instances' items at once, keeps the larger items (fewer items,
+     * less per-item overhead) */
+    const int per_sm = 1024 / kRowThreads;
+    const int fill = (n + per_sm * 148 - 1) / (per_sm * 148);
     return r < fill ? r : (fill < 1 ? 1 : fill);
 }
 
@@ -1293,13 +1298,13 @@ cudaError_t launch_fft_t(int stage, const void *grid_in, void *grid_out, void *s
     cudaError_t e = cudaSuccess;
     if (stage == ST_ROW_FWD) {
         if ((e = set_smem(k_row_fwd<R>, smem)) != cudaSuccess) return e;
-        k_row_fwd<R><<<items, 512, smem, st>>>(d);
+        k_row_fwd<R><<<items, kRowThreads, smem, st>>>(d);
     } else if (stage == ST_COLUMNS) {
         if ((e = set_smem(k_columns<R>, smem)) != cudaSuccess) return e;
-        k_columns<R><<<items, 1024, smem, st>>>(d);
+        k_columns<R><<<items, kColumnThreads, smem, st>>>(d);
     } else {
         if ((e = set_smem(k_row_inv<R>, smem)) != cudaSuccess) return e;
-        k_row_inv<R><<<items, 512, smem, st>>>(d);
+        k_row_inv<R><<<items, kRowThreads, smem, st>>>(d);
     }
     return cudaGetLastError();
 }
@@ -1424,19 +1429,19 @@ cudaError_t launch_stage(const Inst &d, int stage, cudaStream_t st)
         }
         break;
     case ST_ROW_FWD:
-        if (d.f32) YK_LAUNCH(k_row_fwd<float>, 512);
-        else if (d.fft_df) YK_LAUNCH(k_row_fwd<df32>, 512);
-        else YK_LAUNCH(k_row_fwd<double>, 512);
+        if (d.f32) YK_LAUNCH(k_row_fwd<float>, kRowThreads);
+        else if (d.fft_df) YK_LAUNCH(k_row_fwd<df32>, kRowThreads);
+        else YK_LAUNCH(k_row_fwd<double>, kRowThreads);
         break;
     case ST_COLUMNS:
-        if (d.f32) YK_LAUNCH(k_columns<float>, 1024);
-        else if (d.fft_df) YK_LAUNCH(k_columns<df32>, 1024);
-        else YK_LAUNCH(k_columns<double>, 1024);
+        if (d.f32) YK_LAUNCH(k_columns<float>, kColumnThreads);
+        else if (d.fft_df) YK_LAUNCH(k_columns<df32>, kColumnThreads);
+        else YK_LAUNCH(k_columns<double>, kColumnThreads);
         break;
     case ST_ROW_INV:
-        if (d.f32) YK_LAUNCH(k_row_inv<float>, 512);
-        else if (d.fft_df) YK_LAUNCH(k_row_inv<df32>, 512);
-        else YK_LAUNCH(k_row_inv<double>, 512);
+        if (d.f32) YK_LAUNCH(k_row_inv<float>, kRowThreads);
+        else if (d.fft_df) YK_LAUNCH(k_row_inv<df32>, kRowThreads);
+        else YK_LAUNCH(k_row_inv<double>, kRowThreads);
         break;
     default:
         if (d.f32) {
