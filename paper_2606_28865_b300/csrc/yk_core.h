@@ -133,6 +133,19 @@ YK_HD df32 df_mul_add_lazy(df32 acc, df32 a, df32 b)
     return df32(s, YK_FADD(t, YK_FADD(acc.lo, e)));
 }
 
+/* acc + a * b for an FP32 a (the two-product needs one FMA less), the pair left unnormalised as
+ * in df_mul_add_lazy */
+YK_HD df32 df_mul_add_lazy(df32 acc, float a, df32 b)
+{
+    const float p = YK_FMUL(a, b.hi);
+    float e = YK_FFMA(a, b.hi, -p);
+    e = YK_FFMA(a, b.lo, e);
+    const float s = YK_FADD(acc.hi, p);
+    const float bb = YK_FSUB(s, acc.hi);
+    const float t = YK_FADD(YK_FSUB(acc.hi, YK_FSUB(s, bb)), YK_FSUB(p, bb));
+    return df32(s, YK_FADD(t, YK_FADD(acc.lo, e)));
+}
+
 /* Double-float with lazy normalisation, for the FFT butterflies: sums and products keep their
  * (hi, lo) pair as computed (the exact two-sum of the high words with the low words added, or the
  * FMA two-product), without the final fast two-sum that makes |lo| <= ulp(hi)/2.  Every operation

@@ -644,8 +644,9 @@ __host__ __device__ constexpr int win_stride_f(int W, int D) { return win_nf(D) 
 /* TPL window values (taps a0 .. a0 + TPL - 1) of one coordinate by Horner on the piece's
  * polynomials (compile-time degree D; the lane's taps interleaved: TPL independent chains): the
  * orders >= 3 in FP32 with the argument's high word, then c_2 + q x, c_1 + p x and c_0 + p x as
- * fused double-float multiply-adds (exact product terms added to c_k by two-sum).  Taps past the
- * window (a >= W) read the zero pad of the row. */
+ * fused double-float multiply-adds (exact product terms added to c_k by two-sum) whose pairs are
+ * left unnormalised between the steps (each keeps the exact error of its high words) and
+ * normalised once at the end.  Taps past the window (a >= W) read the zero pad of the row. */
 template <int TPL, int D, int WE>
 __device__ __forceinline__ void windows_taps(const df32 *c, const float *cf, int a0, df32 x,
                                              df32 (&p)[TPL])
@@ -659,19 +660,21 @@ __device__ __forceinline__ void windows_taps(const df32 *c, const float *cf, int
 #pragma unroll
             for (int j = 0; j < TPL; ++j) q[j] = fmaf(q[j], x.hi, cf[(k - 3) * WE + a0 + j]);
 #pragma unroll
-        for (int j = 0; j < TPL; ++j) p[j] = df_mul_add(c[2 * WE + a0 + j], df32(q[j], 0.0f), x);
+        for (int j = 0; j < TPL; ++j) p[j] = df_mul_add_lazy(c[2 * WE + a0 + j], q[j], x);
 #pragma unroll
         for (int k = 1; k >= 0; --k)
 #pragma unroll
-            for (int j = 0; j < TPL; ++j) p[j] = df_mul_add(c[k * WE + a0 + j], p[j], x);
+            for (int j = 0; j < TPL; ++j) p[j] = df_mul_add_lazy(c[k * WE + a0 + j], p[j], x);
     } else {
 #pragma unroll
         for (int j = 0; j < TPL; ++j) p[j] = c[D * WE + a0 + j];
 #pragma unroll
         for (int k = D - 1; k >= 0; --k)
 #pragma unroll
-            for (int j = 0; j < TPL; ++j) p[j] = df_mul_add(c[k * WE + a0 + j], p[j], x);
+            for (int j = 0; j < TPL; ++j) p[j] = df_mul_add_lazy(c[k * WE + a0 + j], p[j], x);
     }
+#pragma unroll
+    for (int j = 0; j < TPL; ++j) p[j] = df_fast_two_sum(p[j].hi, p[j].lo);
 }
 
 /* double-float window values per point (see launch_frac_windows_df): four lanes per point, each
