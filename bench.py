@@ -846,13 +846,14 @@ def main():
     launches_per_eval = 5
 
     def launches_per_set(info):
-        # sources: count, scan, fill, three for the tile order, the window values; targets: chunk
-        # histograms, column offsets, scan, scatter, the window values (or, beyond 16,384 target
-        # tiles, count, scan, fill); a scan is one kernel up to 8,192 counts, else three
+        # sources: count, scan, fill, the tile order (one kernel up to 8,192 tiles, else three),
+        # the window values; targets: chunk histograms, column offsets, scan, scatter, the window
+        # values (or, beyond 16,384 target tiles, count, scan, fill); a scan is one kernel up to
+        # 8,192 counts, else three
         n = info["n_grid"]
         ts, tt = (n // info["tile"]) ** 2, (n // info["interp_tile"]) ** 2
         scan = lambda c: 1 if c <= 8192 else 3
-        src = 1 + scan(ts) + 1 + 3 + 1
+        src = 1 + scan(ts) + 1 + (1 if ts <= 8192 else 3) + 1
         trg = (1 + 1 + scan(tt) + 1 if tt <= 16384 else 1 + scan(tt) + 1) + 1
         return src + trg
     line = {
@@ -870,8 +871,9 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * sum(launches_per_eval + launches_per_set(plans[a].info)
                                          for a in alphas),
-        "gpu_launches_what": "library kernels in the timed FP64 region: 5 evaluation and 12 to 16 "
-                             "set-up launches per alpha (scans of up to 8,192 counts in one kernel)",
+        "gpu_launches_what": "library kernels in the timed FP64 region: 5 evaluation and 10 to 14 "
+                             "set-up launches per alpha (scans of up to 8,192 counts and tile "
+                             "orders of up to 8,192 tiles in one kernel)",
         "clocks": clk,
         "stage_ms": {str(a): stage_ms[a] for a in alphas},
         "stage_ms_alone": {str(a): stage_ms_alone[a] for a in alphas},

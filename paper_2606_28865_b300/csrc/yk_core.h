@@ -10,6 +10,7 @@
 
 #include <stdint.h>
 #include <math.h>
+#include <string.h>
 
 #if defined(__CUDACC__)
 #define YK_HD __host__ __device__ __forceinline__
@@ -179,6 +180,33 @@ YK_HD df32l operator*(df32l a, df32l b)
     e = YK_FFMA(a.hi, b.lo, e);
     e = YK_FFMA(a.lo, b.hi, e);
     return df32l(p, e);
+}
+
+/* r rounded to the nearest int64, ties to even (as llrint in the default rounding mode), on the
+ * IEEE bits with integer operations: |r| = m 2^(e - 52) with the 53-bit significand m; for
+ * e >= 52 it is the integer m << (e - 52), below that m is shifted right and the dropped bits
+ * decide the rounding.  Magnitudes of 2^63 and more (and infinities, NaN) give +-LLONG_MAX. */
+YK_HD long long round_even_ll(double r)
+{
+#if defined(__CUDA_ARCH__)
+    const long long b = __double_as_longlong(r);
+#else
+    long long b;
+    memcpy(&b, &r, sizeof b);
+#endif
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const long long m = (b & 0xfffffffffffffll) | (1ll << 52);
+    long long v;
+    if (e >= 52) {
+        v = e > 62 ? 0x7fffffffffffffffll : (m << (e - 52));
+    } else if (e < -1) {
+        v = 0; /* |r| < 1/2, zero and subnormals included */
+    } else {
+        const int s = 52 - e; /* 1 .. 53 */
+        const long long q = m >> s, rem = m & ((1ll << s) - 1), half = 1ll << (s - 1);
+        v = q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+    }
+    return b < 0 ? -v : v;
 }
 
 /* ---------------------------------------------------------------------------------------- */

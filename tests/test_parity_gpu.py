@@ -164,6 +164,32 @@ def test_point_outside_box_is_reported(small):
     plan.close()
 
 
+def test_points_on_the_box_edges_are_inside(small):
+    # the box test runs on the fixed-point coordinates (T = x 2^44 / h rounded to nearest even, on
+    # the FP64 bits in the kernel, by llrint on the host for the box's own edges): points exactly
+    # on the four edges are inside and evaluate like any other; 1e-9 beyond an edge is reported
+    yk = _yk()
+    x0, x1, y0, y1 = small.box
+    xs, ys = np.array([x0, x1, x0, x1, 0.0]), np.array([y0, y0, y1, y1, 0.0])
+    q = np.array([1.0, -0.5, 0.25, 2.0, 0.5])
+    xt, yt = np.array([x1, x0, 0.0, x0 + 1e-3]), np.array([y0, y1, y1, 0.0])
+    plan = yk.Plan(10.0, tol=TOL64, delta=0.0167, box=small.box)
+    plan.set_points(dev(xs), dev(ys), dev(np.ones(5)), dev(xt), dev(yt))
+    u = plan.eval(dev(q)).cpu().numpy()
+    plan.sync()
+    ref = oracle.direct_sum(10.0, 0.0167, xs, ys, q, xt, yt)
+    g0 = oracle.gh_hankel(10.0, 0.0167, [0.0])[0]
+    assert np.max(np.abs(u - ref)) <= TOL64 * np.sum(np.abs(q)) * g0, (u, ref)
+    plan.close()
+    for bx, by in [(x1 + 1e-9, 0.0), (x0 - 1e-9, 0.0), (0.0, y1 + 1e-9), (0.0, y0 - 1e-9)]:
+        plan = yk.Plan(10.0, tol=TOL64, delta=0.0167, box=small.box)
+        plan.set_points(dev([bx]), dev([by]), dev([1.0]), dev([0.0]), dev([0.0]))
+        with pytest.raises(yk.YkError) as ei:
+            plan.sync()
+        assert ei.value.status == yk.YK_ERR_ARG, (bx, by)
+        plan.close()
+
+
 def test_eval_before_set_points_is_a_state_error():
     yk = _yk()
     plan = yk.Plan(10.0, tol=TOL64, delta=0.0167)
