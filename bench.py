@@ -871,7 +871,7 @@ def main():
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * sum(launches_per_eval + launches_per_set(plans[a].info)
                                          for a in alphas),
-        "gpu_launches_what": "library kernels in the timed FP64 region: 5 evaluation and 10 to 14 "
+        "gpu_launches_what": "library kernels in the timed FP64 region: 5 evaluation and 10 to 16 "
                              "set-up launches per alpha (scans of up to 8,192 counts and tile "
                              "orders of up to 8,192 tiles in one kernel)",
         "clocks": clk,
