@@ -1024,8 +1024,8 @@ int stage_smem(const Inst &d, int stage)
     default: {
         const int nw = (d.wdeg + 1) * W; /* interpolation stages the window only */
         const int Ti = d.g.Ti;
-        if (d.fft_df) return 8 * (Ti + W) * (Ti + W);
-        return d.f32 ? 4 * (Ti + W) * (Ti + W)
+        if (d.fft_df) return 2 * 8 * (Ti + W) * halo_pair_pitch(Ti + W); /* the paired halo */
+        return d.f32 ? 4 * 4 * (Ti + W) * halo_quad_pitch(Ti + W) /* the four-copy halo */
                      : 8 * (Ti + W) * (Ti + W) + (d.win ? (int)sizeof(double) * nw : 0);
     }
     }

@@ -963,17 +963,55 @@ template <int W> __device__ void st_interp64(const Inst &d, int item, unsigned c
     __syncthreads();
 }
 
-/* FP32C: FP32 window values and row sums, rows combined in FP64 */
+/* the FP32 halo four times, with a row pitch PP that is a multiple of 4: copy k holds cell
+ * (X0 + c + k, Y0 + r) at r PP + c, so that any four neighbouring cells of a row are one aligned
+ * 16-byte load from copy (column mod 4).  Rows by warp, columns by lane, as stage_halo. */
+__device__ __forceinline__ void stage_halo_quad32(float *s, const float *__restrict__ grid,
+                                                  const Geom &g, int X0, int Y0, int P, int PP)
+{
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, CP = P * PP;
+    for (int r = threadIdx.x >> 5; r < P; r += nw) {
+        int gy = Y0 + r;
+        if (P > g.n) { /* a halo wider than the grid: plain modulo (not reached with n >= 2T) */
+            gy %= g.n;
+            gy += gy < 0 ? g.n : 0;
+        } else {
+            gy += gy < 0 ? g.n : (gy >= g.n ? -g.n : 0);
+        }
+        const float *__restrict__ row = grid + (size_t)gy * g.n;
+        for (int c = lane; c < P; c += 32) {
+            int gx = X0 + c;
+            if (P > g.n) {
+                gx %= g.n;
+                gx += gx < 0 ? g.n : 0;
+            } else {
+                gx += gx < 0 ? g.n : (gx >= g.n ? -g.n : 0);
+            }
+            const float v = row[gx];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c >= k) s[k * CP + r * PP + c - k] = v;
+        }
+    }
+}
+
+/* row pitch of the four-copy FP32 halo: P rounded up to a multiple of 4 (16-byte aligned rows) */
+__host__ __device__ constexpr int halo_quad_pitch(int P) { return (P + 3) & ~3; }
+
+/* FP32C: FP32 window values and row sums, rows combined in FP64.  The taps of a row are read
+ * four cells at a time (16-byte loads from the four-copy halo): a quarter of the load
+ * instructions, and a quarter-warp's 16-byte reads collide on fewer banks than a warp's 4-byte
+ * reads (the targets of a warp tap random cells). */
 template <int W> __device__ void st_interp32(const Inst &d, int item, unsigned char *sm)
 {
     float *sg = reinterpret_cast<float *>(sm);
     const Geom &g = d.g;
-    const int T = g.Ti, P = T + W, lo = W / 2;
+    const int T = g.Ti, P = T + W, lo = W / 2, PP = halo_quad_pitch(P), CP = P * PP;
     const int tyi = item / g.nti, txi = item - tyi * g.nti;
     const int beg = d.trg_ptr[item], end = d.trg_ptr[item + 1];
     if (beg == end) return;
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;
-    stage_halo<float>(sg, static_cast<const float *>(d.grid), g, X0, Y0, P);
+    stage_halo_quad32(sg, static_cast<const float *>(d.grid), g, X0, Y0, P, PP);
     __syncthreads();
     const int4 *__restrict__ trg = reinterpret_cast<const int4 *>(d.trg_t);
     const float beta = (float)g.beta, cw = (float)g.c;
@@ -986,15 +1024,26 @@ template <int W> __device__ void st_interp32(const Inst &d, int item, unsigned c
             fx[a] = es_window_stable<float>(sx + (float)a, beta, cw);
             fy[a] = es_window_stable<float>(sy + (float)a, beta, cw);
         }
-        const float *base = sg + (r.y - Y0) * P + (r.x - X0);
+        /* cells cx .. cx + W - 1 of a row (0 <= cx <= T): copy (cx mod 4) from column cx - k */
+        const int cx = r.x - X0, cy = r.y - Y0, k = cx & 3;
+        const float *base = sg + k * CP + cy * PP + (cx - k);
         /* FP32 row sums combined in double-float (the exact product of the FP32 weight and row
          * sum added by two-sum): the final accumulation keeps ~48 bits, on the FP32 pipe */
         df32 acc(0.0f, 0.0f);
 #pragma unroll
         for (int cc = 0; cc < W; ++cc) {
+            const float4 *q = reinterpret_cast<const float4 *>(base + cc * PP);
             float row = 0.0f;
 #pragma unroll
-            for (int a = 0; a < W; ++a) row = fmaf(fx[a], base[cc * P + a], row);
+            for (int a = 0; a + 3 < W; a += 4) {
+                const float4 v = q[a >> 2];
+                row = fmaf(fx[a], v.x, row);
+                row = fmaf(fx[a + 1], v.y, row);
+                row = fmaf(fx[a + 2], v.z, row);
+                row = fmaf(fx[a + 3], v.w, row);
+            }
+#pragma unroll
+            for (int a = W & ~3; a < W; ++a) row = fmaf(fx[a], base[cc * PP + a], row);
             acc = df_mul_add(acc, df32(fy[cc], 0.0f), df32(row, 0.0f));
         }
         d.u[d.trg_idx[e]] = acc.to_double();
@@ -1002,23 +1051,62 @@ template <int W> __device__ void st_interp32(const Inst &d, int item, unsigned c
     __syncthreads();
 }
 
+/* the double-float halo twice, with an even row pitch PP: copy 0 holds cell (X0 + c, Y0 + r) at
+ * r PP + c and copy 1 the cell to its right (X0 + c + 1) at the same place, so that any two
+ * neighbouring cells of a row are one aligned 16-byte load from one of the copies (copy 0 from an
+ * even column, copy 1 from an odd one).  Rows by warp, columns by lane, as stage_halo. */
+__device__ __forceinline__ void stage_halo_pair_df(df32 *s0, df32 *s1, const df32 *__restrict__ grid,
+                                                   const Geom &g, int X0, int Y0, int P, int PP)
+{
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < P; r += nw) {
+        int gy = Y0 + r;
+        if (P > g.n) { /* a halo wider than the grid: plain modulo (not reached with n >= 2T) */
+            gy %= g.n;
+            gy += gy < 0 ? g.n : 0;
+        } else {
+            gy += gy < 0 ? g.n : (gy >= g.n ? -g.n : 0);
+        }
+        const df32 *__restrict__ row = grid + (size_t)gy * g.n;
+        for (int c = lane; c < P; c += 32) {
+            int gx = X0 + c;
+            if (P > g.n) {
+                gx %= g.n;
+                gx += gx < 0 ? g.n : 0;
+            } else {
+                gx += gx < 0 ? g.n : (gx >= g.n ? -g.n : 0);
+            }
+            const df32 v = row[gx];
+            s0[r * PP + c] = v;
+            if (c > 0) s1[r * PP + c - 1] = v;
+        }
+    }
+}
+
+/* row pitch of the paired halo: P rounded up to even (16-byte aligned rows) */
+__host__ __device__ constexpr int halo_pair_pitch(int P) { return (P + 1) & ~1; }
+
 /* FP64 path, double-float arithmetic: windows and tap sums in FP32 pairs, one conversion to
- * double per target */
+ * double per target.  The taps of a row are read two cells at a time (16-byte loads from the
+ * paired halo): half the load instructions of one 8-byte load per cell, and a quarter-warp's
+ * 16-byte reads collide on fewer banks than a half-warp's 8-byte reads (the targets of a warp tap
+ * random cells). */
 template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned char *sm)
 {
     const Geom &g = d.g;
-    const int T = g.Ti, P = T + W, lo = W / 2;
-    df32 *sg = reinterpret_cast<df32 *>(sm);
+    const int T = g.Ti, P = T + W, lo = W / 2, PP = halo_pair_pitch(P);
+    df32 *s0 = reinterpret_cast<df32 *>(sm);
+    df32 *s1 = s0 + P * PP;
     const int tyi = item / g.nti, txi = item - tyi * g.nti;
     const int beg = d.trg_ptr[item], end = d.trg_ptr[item + 1];
     if (beg == end) return;
     const int X0 = txi * T - lo, Y0 = tyi * T - lo;
-    stage_halo<df32>(sg, static_cast<const df32 *>(d.grid), g, X0, Y0, P);
+    stage_halo_pair_df(s0, s1, static_cast<const df32 *>(d.grid), g, X0, Y0, P, PP);
     __syncthreads();
     const int4 *__restrict__ trg = reinterpret_cast<const int4 *>(d.trg_t);
     for (int e = beg + threadIdx.x; e < end; e += blockDim.x) {
         const int4 r = trg[e]; /* first taps (lx, ly), from the fixed-point preparation */
-        const int lx = r.x, ly = r.y;
+        const int cx = r.x - X0, cy = r.y - Y0; /* 0 <= cx, cy <= T */
         /* window values of this target, computed at yk_set_points: planes [phi_y taps | phi_x
          * taps], value k at k * pitch + e (consecutive threads read consecutive targets) */
         const float2 *wv = d.win_trg + e;
@@ -1029,15 +1117,22 @@ template <int W> __device__ void st_interp_df(const Inst &d, int item, unsigned 
             const float2 v = wv[(W + a) * pw];
             fx[a] = df32(v.x, v.y);
         }
-        const df32 *base = sg + (ly - Y0) * P + (lx - X0);
+        /* cells cx .. cx + W - 1 of a row: from copy 0 at cx (even) or copy 1 at cx - 1 (odd) */
+        const df32 *base = ((cx & 1) ? s1 + (cx - 1) : s0 + cx) + cy * PP;
         df32 acc(0.0f, 0.0f);
 #pragma unroll
         for (int c = 0; c < W; ++c) {
             /* row sum of W products with the unnormalised multiply-add (exact two-sum of the
              * high words, low words gathered), renormalised once by a full two-sum */
+            const float4 *q = reinterpret_cast<const float4 *>(base + c * PP);
             df32 row(0.0f, 0.0f);
 #pragma unroll
-            for (int a = 0; a < W; ++a) row = df_mul_add_lazy(row, fx[a], base[c * P + a]);
+            for (int a = 0; a + 1 < W; a += 2) {
+                const float4 v = q[a >> 1];
+                row = df_mul_add_lazy(row, fx[a], df32(v.x, v.y));
+                row = df_mul_add_lazy(row, fx[a + 1], df32(v.z, v.w));
+            }
+            if (W & 1) row = df_mul_add_lazy(row, fx[W - 1], base[c * PP + W - 1]);
             row = df_two_sum(row.hi, row.lo);
             const float2 wy = wv[c * pw];
             acc = df_mul_add(acc, df32(wy.x, wy.y), row);
