@@ -227,6 +227,18 @@ template <typename R> YK_HD R es_window_stable(R z, R beta, R c)
     return u <= (R)1 ? exp(-beta * u / ((R)1 + sqrt((R)1 - u))) : (R)0;
 }
 
+#if defined(__CUDACC__)
+/* es_window_stable in FP32 with CUDA's fast exponential and division intrinsics, for the FP32C
+ * kernels (target 1e-6): __expf is within 2 + 1.2 |x| ulp for the exponent x in [-beta, 0] and
+ * __fdividef within 2 ulp, so a window value is within ~1.6e-7 of the window's peak (the IEEE
+ * functions: a few ulp of the value) */
+__device__ __forceinline__ float es_window32(float z, float beta, float c)
+{
+    const float u = c * z * z;
+    return u <= 1.0f ? __expf(__fdividef(-beta * u, 1.0f + sqrtf(1.0f - u))) : 0.0f;
+}
+#endif
+
 /* first tap l0 = ceil(t - w/2) of a point at grid coordinate t; taps l0 .. l0+w-1, and the
  * window arguments z_a = l0 + a - t lie in [-w/2, w/2) */
 template <int W> YK_HD int first_tap(double t) { return (int)ceil(t - 0.5 * W); }

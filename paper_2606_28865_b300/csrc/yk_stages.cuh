@@ -567,8 +567,8 @@ __device__ void st_spread_owner32(const Inst &d, int item, unsigned char *sm)
                     const float q = (float)(d.wq[j] * d.dens[j]);
 #pragma unroll
                     for (int a = 0; a < W; ++a) {
-                        wl[a] = q * es_window_stable<float>(sy + (float)a, beta, cwin);
-                        wl[W + a] = es_window_stable<float>(sx + (float)a, beta, cwin);
+                        wl[a] = q * es_window32(sy + (float)a, beta, cwin);
+                        wl[W + a] = es_window32(sx + (float)a, beta, cwin);
                     }
                 } else {
                     /* dipole: s = -mu w nu / h; window and derivative from the FP32 polynomials */
@@ -1021,8 +1021,8 @@ template <int W> __device__ void st_interp32(const Inst &d, int item, unsigned c
         float fx[W], fy[W];
 #pragma unroll
         for (int a = 0; a < W; ++a) {
-            fx[a] = es_window_stable<float>(sx + (float)a, beta, cw);
-            fy[a] = es_window_stable<float>(sy + (float)a, beta, cw);
+            fx[a] = es_window32(sx + (float)a, beta, cw);
+            fy[a] = es_window32(sy + (float)a, beta, cw);
         }
         /* cells cx .. cx + W - 1 of a row (0 <= cx <= T): copy (cx mod 4) from column cx - k */
         const int cx = r.x - X0, cy = r.y - Y0, k = cx & 3;
