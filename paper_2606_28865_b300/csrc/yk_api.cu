@@ -484,7 +484,7 @@ void free_all(yk_plan_t p)
                      &p->trg_ptr,
                      &p->trg_cur, &p->err, &p->w_src, &p->src_t, &p->ent_t, &p->ent_j,
                      &p->trg_t, &p->trg_idx, &p->trg_tmp, &p->src_tap, &p->trg_tap,
-                     &p->trg_frac, &p->trg_hist, &p->stage_x, &p->stage_y,
+                     &p->trg_hist, &p->stage_x, &p->stage_y,
                      &p->stage_w, &p->stage_u};
     for (DevBuf *b : all) buf_free(p, *b);
     for (int r = 0; r < yk_plan_s::kEventRing; ++r)
@@ -1210,7 +1210,6 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
     if (prep) {
         YK_TRY(buf_alloc(p, p->src_tap, sizeof(int2) * (ns + nd), "source taps"));
         YK_TRY(buf_alloc(p, p->trg_tap, sizeof(int4) * nt, "target taps"));
-        if (p->fft_df) YK_TRY(buf_alloc(p, p->trg_frac, sizeof(float4) * nt, "target windows"));
         const int64_t nch = yk::hist_chunks(n_trg, p->nti * p->nti);
         if (nch > 0)
             YK_TRY(buf_alloc(p, p->trg_hist, sizeof(int) * (size_t)nch * p->nti * p->nti,
@@ -1265,9 +1264,8 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
     if (prep)
         YK_CU(yk::launch_prep_targets(g, n_trg, tx, ty, P<int4>(p->trg_tap), P<float4>(p->trg_tmp),
                                       P<int>(p->trg_cnt), P<int>(p->trg_ptr), P<int>(p->trg_cur),
-                                      P<double2>(p->trg_t),
-                                      p->fft_df ? P<float4>(p->trg_frac) : nullptr,
-                                      P<int>(p->trg_idx), P<int>(p->err), p->stream,
+                                      P<double2>(p->trg_t), nullptr, P<int>(p->trg_idx),
+                                      P<int>(p->err), p->stream,
                                       P<int>(p->trg_hist)),
               "bin targets");
     else
@@ -1278,10 +1276,14 @@ yk_status yk_set_points_dl(yk_plan_t p, int64_t n_src, const double *xs, const d
               "bin targets");
     if (p->fft_df) {
         YK_TRY(buf_alloc(p, p->win_trg, sizeof(float2) * 2 * (size_t)p->w * nt, "target windows"));
-        YK_CU(yk::launch_frac_windows_df(g, n_trg, P<float4>(p->trg_frac),
+        /* the window arguments are gathered in tile order from the preparation's copy in the
+         * original order (trg_tmp) through the targets' indices: the binning then writes no
+         * third per-target array at random slots */
+        YK_CU(yk::launch_frac_windows_df(g, n_trg, P<float4>(p->trg_tmp),
                                          P<int>(p->trg_ptr) + (size_t)p->nti * p->nti,
                                          P<float2>(p->win_pc), p->pdeg, false,
-                                         P<float2>(p->win_trg), p->stream, n_trg),
+                                         P<float2>(p->win_trg), p->stream, n_trg,
+                                         P<int>(p->trg_idx), n_trg),
               "target windows");
     }
     stage_end(p, YK_STAGE_BIN_TRG);

@@ -292,8 +292,8 @@ struct yk_plan_s {
                         preparation: the targets' window arguments, float4) */
     /* fixed-point preparation (double-float and FP32C paths): src_t holds the sources' window
      * arguments (float4) and src_tap their first taps (int2); trg_tap the targets' first taps and
-     * cell tiles (int4, original order); trg_frac the targets' window arguments in tile order */
-    DevBuf src_tap, trg_tap, trg_frac;
+     * cell tiles (int4, original order) */
+    DevBuf src_tap, trg_tap;
     DevBuf trg_hist; /* int[chunks * tiles]: the targets' histogram binning */
     /* staging copies of host arrays */
     DevBuf stage_x, stage_y, stage_w, stage_u;

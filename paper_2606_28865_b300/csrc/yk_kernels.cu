@@ -976,6 +976,10 @@ int rows_per_item(int n, bool f32, bool fill_sms)
     int r = kRowItemBytes / bytes_per_row;
     r = r < 1 ? 1 : (r > 16 ? 16 : r);
     if (!fill_sms) return r;
+    /* FP32 rows (at most 14,400 complex values, 115 KB): at most two per item, so that more CTAs
+     * hide the latency of the fold's loads (row passes -7..14% against three to six rows per item
+     * on B300 at n = 1,600 and 2,880) */
+    if (f32 && r > 2) r = 2;
     /* a launch of its own: no more rows than leave 1024 / kRowThreads work items (the CTAs that
      * share an SM at <= 64 registers) per SM of a 148-SM part (FP32 rows of small grids would
      * otherwise fit 15 or 16 to a CTA and leave SMs idle: 107 CTAs at n = 1600); the batch
