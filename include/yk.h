@@ -56,7 +56,7 @@ typedef enum {
     YK_ERR_TIMEOUT = 4,  /* a bounded device-side wait ran out */
     YK_ERR_STATE = 5,    /* call out of order (eval before set_points, ...) */
     YK_ERR_INTERNAL = 6, /* an internal consistency check failed */
-    YK_ERR_UNSUPPORTED = 7 /* a size beyond what this build handles (see yk_plan) */
+    YK_ERR_UNSUPPORTED = 7 /* a size beyond what the library handles (see yk_plan) */
 } yk_status;
 
 typedef enum {

@@ -981,7 +981,7 @@ static yk_status choose_params(double alpha, const yk_opts *o, yk_plan_s *p)
         const int nmax = o->precision == YK_FP32C ? yk::kMaxGridF32 : yk::kMaxGridF64;
         if (n > nmax)
             return fail(YK_ERR_UNSUPPORTED,
-                        "a grid of at least %lld points per axis is needed (this build supports "
+                        "a grid of at least %lld points per axis is needed (the library supports "
                         "%d at this precision): raise delta or tol, or lower the period",
                         (long long)nmin, nmax);
         if (!smooth5(n)) continue;

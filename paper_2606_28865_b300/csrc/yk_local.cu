@@ -44,7 +44,7 @@ using yk::operator+;
 using yk::operator-;
 using yk::operator*;
 
-constexpr int kMaxQ = 32;      /* nodes per panel this build accepts */
+constexpr int kMaxQ = 32;      /* nodes per panel the library accepts */
 constexpr int kMaxCells = 1 << 22;
 
 /* (2n+1)/(n+1) and n/(n+1): the Legendre recurrence without divisions */
